@@ -1,0 +1,329 @@
+"""Benchmark of the EPWI + SERTA transport hot path on GB300.
+
+One step = the whole hot path on the Al-like metal at a 48^3 k and q grid (seeded synthetic
+inputs resident on the device): H(k)/D(q) eigensolves -> +-0.3 eV window -> sieve ->
+q-batched g(k,q) interpolation with SERTA delta sums -> sigma.  The step time is the
+time-to-sigma; ``value`` is the sieved (k,q) pairs per second of that step.
+``e2e`` repeats the step through the C ABI from host buffers (setup copies H, Phi, g from
+the host; the rates, states and sigma come back to the host) inside the timed region.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--precision P] [--impl reference]
+Under torchrun (N > 1) every rank runs an independent copy of the workload (weak scaling,
+no data-path collective); rank 0 prints the line with the max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "el-ph (k,q)-pairs/s and time-to-σ, mixed-precision vs FP64 at stated error"
+WORKLOAD = dict(workload="al_like_48", system="Al-like fcc, nw=4, 3 modes, 5^3 WS-weighted Re/Rp",
+                grid=48, window_eV=0.3, smear_eV=0.02, T_K=300.0, mu="band centre", seed=2)
+CHOSEN = os.environ.get("EPWI_BENCH_PRECISION", "fp64")
+DTYPE = {"fp64": "f64", "tf32x3": "tf32x3 (f32 acc, f64 sums)", "bf16x3": "bf16x3 (f32 acc, f64 sums)",
+         "fp16x3": "fp16x3 (f32 acc, f64 sums)"}
+L2_BYTES = 129 * 2 ** 20
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mp = json.load(f)
+        return mp, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def roofline_for(precision, stats, per_launch_traffic=None):
+    """Dominant kernel: the fused Rp->q + rotation + delta kernel (one launch per chunk)."""
+    mp, src = peaks()
+    flops = stats["scatter_flops"]
+    ms = stats["ms_scatter"]
+    if precision == "fp64":
+        # FP64 ALU: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz = 1.26 TFLOP/s (GB300 FP64 rate)
+        peak = 152 * 4 * 2.07e9 / 1e12
+        bound, unit = "alu", "TFLOP/s"
+        achieved = flops / (ms * 1e-3) / 1e12
+        note = "FP64 peak derived: 152 SM x 4 flop/clk x 2.07 GHz"
+    else:
+        ratio = 0.5 if precision == "tf32x3" else 1.0
+        peak = mp["bf16_tflops"] * ratio
+        bound, unit = "tensor", "TFLOP/s"
+        achieved = 3.0 * flops / (ms * 1e-3) / 1e12      # three split products
+        note = f"{src} bf16 burst peak x {ratio}"
+    return {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak, "traffic": per_launch_traffic,
+            "kernel": "k_scatter (fused Rp->q GEMM + rotations + delta sum)",
+            "launches_per_step": stats["n_chunks"], "peak_source": note}
+
+
+class ClockSampler:
+    def __init__(self, out):
+        self.out = out
+        self.p = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.out, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            self.p.wait()
+            self.f.close()
+
+    def summary(self, device=0):
+        try:
+            rows = [r.split(",") for r in open(self.out).read().strip().splitlines()]
+        except Exception:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        rows = [[x.strip() for x in r] for r in rows if r and r[0].strip() == str(device)]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def reduce_max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------- oracle arm
+def oracle_sample(sysm, gr, nkp_sample, seed, T, eta, mu):
+    """Times the FP64 CPU oracle on a seeded sample of k-points of the workload."""
+    from oracle import epwi_oracle as O
+    ik_all, _ = gr.window_states(mu - WORKLOAD["window_eV"], mu + WORKLOAD["window_eV"])
+    kp = np.unique(ik_all)
+    pick = np.random.default_rng(seed).choice(kp, nkp_sample, replace=False)
+    t0 = time.perf_counter()
+    r = O.serta(gr, T, mu, eta, mu - WORKLOAD["window_eV"], mu + WORKLOAD["window_eV"],
+                k_subset=pick)
+    dt = time.perf_counter() - t0
+    return r["n_pairs"], dt
+
+
+def cores_used():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def build_oracle_grid():
+    from oracle import epwi_oracle as O
+    from paper_2306_16493_gb300 import synth
+    s = synth.al_like_system(WORKLOAD["seed"])
+    N = WORKLOAD["grid"]
+    gr = O.Grids(s, (N, N, N))
+    return s, gr
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        if rank != 0:
+            dist.destroy_process_group()
+            return
+    s, gr = build_oracle_grid()
+    mu = gr.band_centre()
+    T, eta = WORKLOAD["T_K"], WORKLOAD["smear_eV"]
+    nsample = args.ref_kpoints
+    for w in range(args.warmup):
+        oracle_sample(s, gr, max(1, nsample // 4), 1000 + w, T, eta, mu)
+    tot_pairs, tot_t = 0, 0.0
+    for k in range(args.steps):
+        p, dt = oracle_sample(s, gr, nsample, 2000 + k, T, eta, mu)
+        tot_pairs += p
+        tot_t += dt
+    val = tot_pairs / tot_t
+    line = {"metric": METRIC, "value": val, "unit": "pairs/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": dict(WORKLOAD, precision="fp64 CPU oracle",
+                           sample=f"{nsample} seeded k-points per step (all their q) of the 48^3 workload"),
+            "cpu_baseline": {"value": val, "unit": "pairs/s", "cores": cores_used(), "kind": "oracle",
+                             "sample": f"{nsample} k-points x {args.steps} steps, numpy FP64"},
+            "e2e": {"value": val, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2306_16493_gb300 import epwi, synth
+
+    precision = args.precision
+    s = synth.al_like_system(WORKLOAD["seed"])
+    N = WORKLOAD["grid"]
+    T, eta, win = WORKLOAD["T_K"], WORKLOAD["smear_eV"], WORKLOAD["window_eV"]
+    stream = torch.cuda.current_stream()
+    ctx = epwi.Context(precision=precision, device=local, stream=stream.cuda_stream)
+    ctx.setup(s)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        ctx.eigs(N)
+        lo, hi = ctx.band_range()
+        mu = 0.5 * (lo + hi)
+        ns, npairs = ctx.scatter_rates(T, mu, eta, mu - win, mu + win)
+        sig = ctx.conductivity()
+        return npairs, sig
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    pairs_total = 0
+    sc_ms, sc_flops, chunks = 0.0, 0.0, 0
+    launches0 = epwi.epwi_kernel_launches()
+    clocks_path = os.path.join(tempfile.gettempdir(), f"epwi_clocks_{os.getpid()}.csv")
+    with ClockSampler(clocks_path) as cs:
+        time.sleep(0.3)
+        for k in range(args.steps):
+            flush.zero_()                        # L2 flush between timed steps (not timed)
+            ev[k][0].record(stream)
+            npairs, sig = step()
+            ev[k][1].record(stream)
+            pairs_total += npairs
+            st = ctx.stats()
+            sc_ms += st["ms_scatter"]
+            sc_flops += st["scatter_flops"]
+            chunks += st["n_chunks"]
+        torch.cuda.synchronize()
+    launches = (epwi.epwi_kernel_launches() - launches0) // args.steps
+    if world > 1:
+        torch.distributed.barrier()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    ms_max = reduce_max_over_ranks(ms, world)
+    pairs_all = reduce_sum_over_ranks(float(pairs_total), world)
+    value = pairs_all / (ms_max * 1e-3)
+    clocks = cs.summary(local)
+    stats = dict(ctx.stats(), scatter_flops=sc_flops, ms_scatter=sc_ms, n_chunks=chunks)
+    roof = roofline_for(precision, stats, per_launch_traffic=None)
+
+    # ---- e2e through the C ABI with host buffers
+    e2e_steps = max(1, min(args.steps, 3))
+    h2d = sum(a.nbytes for a in (s.mass, s.Re, s.we, s.H, s.Rp, s.wp, s.Phi, s.g))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_pairs, d2h = 0, 0
+    for _ in range(e2e_steps):
+        ctx.setup(s)
+        npairs, sig = step()
+        k_idx, band, rates = ctx.rates()
+        e2e_pairs += npairs
+        d2h = k_idx.nbytes + band.nbytes + rates.nbytes + sig.nbytes
+    torch.cuda.synchronize()
+    e2e_t = time.perf_counter() - t0
+    e2e_t = reduce_max_over_ranks(e2e_t, world)
+    e2e_pairs = reduce_sum_over_ranks(float(e2e_pairs), world)
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            _, gr = build_oracle_grid()
+            mu = gr.band_centre()
+            p, dt = oracle_sample(s, gr, args.ref_kpoints, 7, T, eta, mu)
+            cpu = {"value": p / dt, "unit": "pairs/s", "cores": cores_used(), "kind": "oracle",
+                   "sample": f"{args.ref_kpoints} seeded k-points of the 48^3 workload with all their q "
+                             f"({p} pairs, {dt:.1f} s, numpy FP64; grid eigensolves excluded)"}
+        line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+                "time_to_sigma_ms": ms_max / args.steps, "pairs_per_step": pairs_total / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": DTYPE[precision], "data": "synthetic",
+                "config": dict(WORKLOAD, precision=precision, l2="flushed between timed steps (256 MiB write)",
+                               parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+                "gpu_launches": int(launches),
+                "stage_ms": {k: stats[k] for k in ("ms_eigs", "ms_sieve", "ms_restage", "ms_scatter", "ms_reduce")},
+                "roofline": roof, "clocks": clocks, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_pairs / e2e_t, "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
+                        "d2h_bytes_per_step": int(d2h)}}
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--precision", default=CHOSEN, choices=["fp64", "tf32x3", "bf16x3", "fp16x3"])
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--ref-kpoints", type=int, default=40)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,210 @@
+/*
+ * epwi.h - C ABI of the GB300 (sm_103a) electron-phonon Wannier interpolation (EPWI)
+ * transport hot path.
+ *
+ * The calls follow the problem statement of the paper (arXiv:2306.16493): Sec. III A
+ * describes the inputs (lattice, mesh density, temperature, doping; H(R_e), Phi(R_p)
+ * and g(R_e, R_p) in the Wannier basis), the preprocessing (interpolated electrons and
+ * phonons, velocities, the chemical potential, the energy-conservation sieve) and the
+ * on-the-fly EPWI loops; Sec. II B gives the interpolation formulas (Eqs. 4-7) and
+ * Sec. II C the SERTA scattering rate (Eq. 10), the conductivity (Eq. 12) and the
+ * mobility (Eq. 15).  Sec. III C (Eq. 16) fixes the evaluation order
+ * {U(k+q)[(g P^el U^dag(k)) P^ph]} u(q).
+ *
+ * Conventions for every call:
+ *  - Units: eV, Angstrom, amu, K.  Outputs: 1/tau in 1/s, sigma in S/m, mobility in
+ *    cm^2/(V s), velocities in m/s.
+ *  - All pointers are HOST pointers unless a name ends in _dev.  Arrays are C row-major.
+ *    The caller owns every input and output buffer; inputs are copied, never retained.
+ *    The context owns all device memory it allocates; epwi_destroy frees it.
+ *  - Grids are Gamma-centred Monkhorst-Pack grids; the flat index of the point
+ *    (i1, i2, i3) is (i1 * N2 + i2) * N3 + i3 and k+q is taken component-wise modulo N.
+ *  - Every call returns an epwi_status.  No C++ exception crosses the ABI.  On error the
+ *    context keeps a message (epwi_last_error).  A call made before the calls it depends
+ *    on returns EPWI_ESTATE.  A context is not thread safe: use one per host thread.
+ *  - Work is enqueued on the context's CUDA stream (epwi_options.cuda_stream, or the
+ *    legacy default stream when NULL).  Calls that return host data synchronise that
+ *    stream; the others only enqueue work unless stated.
+ */
+#ifndef EPWI_H
+#define EPWI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct epwi_ctx epwi_ctx;
+
+typedef enum {
+    EPWI_OK = 0,
+    EPWI_EINVAL = 1,      /* bad argument (NULL pointer, size, non-Hermitian H, ASR broken, ...) */
+    EPWI_ENOMEM = 2,      /* device allocation failed */
+    EPWI_ECUDA = 3,       /* a CUDA runtime call or kernel failed */
+    EPWI_ESTATE = 4,      /* call out of order (e.g. scatter_rates before eigs) */
+    EPWI_ETIMEOUT = 5,    /* a bounded device-side wait gave up */
+    EPWI_ENUMERIC = 6,    /* non-finite result or eigensolver did not converge */
+    EPWI_ETOOSMALL = 7,   /* output capacity smaller than the result */
+    EPWI_EUNSUPPORTED = 8 /* size or mode outside what this build supports */
+} epwi_status;
+
+/* Arithmetic of the g(k,q) interpolation (steps Re->k, Rp->q and the rotations).
+ * Eigensolves, delta functions, occupations and the 1/tau and sigma sums are FP64 in
+ * every mode.  EPWI_FP64 is the reference path. */
+typedef enum {
+    EPWI_FP64 = 0,   /* FP64 throughout */
+    EPWI_TF32X3 = 1, /* Rp->q GEMM on tcgen05 kind::tf32, 3-term hi/lo split, FP32 accumulate */
+    EPWI_BF16X3 = 2, /* Rp->q GEMM on tcgen05 kind::f16 with bf16 operands, 3-term split */
+    EPWI_FP16X3 = 3  /* Rp->q GEMM on tcgen05 kind::f16 with fp16 operands, 3-term split */
+} epwi_precision;
+
+typedef struct { double re, im; } epwi_c64;
+
+/* One crystal in the Wannier basis (Sec. III A inputs).  Arrays are unweighted; the
+ * lattice-vector weights we/wp multiply every Fourier sum. */
+typedef struct {
+    double lattice[9];          /* rows a1, a2, a3 in Angstrom */
+    int32_t nat;                /* atoms per cell; modes Nm = 3 nat */
+    const double *mass;         /* [nat] amu, > 0 */
+    int32_t nw;                 /* Wannier functions W */
+    int32_t nRe;                /* electron lattice vectors */
+    const int32_t *Re;          /* [nRe][3] integer lattice coordinates; -R must be present */
+    const double *we;           /* [nRe] weights */
+    const epwi_c64 *H;          /* [nRe][nw][nw] eV; H(-R) = H(R)^dagger required */
+    int32_t nRp;                /* phonon lattice vectors */
+    const int32_t *Rp;          /* [nRp][3] */
+    const double *wp;           /* [nRp] */
+    const double *Phi;          /* [nRp][3nat][3nat] eV/A^2, real; Phi(-R) = Phi(R)^T and the
+                                   acoustic sum rule sum_R w_R sum_b Phi_ab(R) = 0 required */
+    const epwi_c64 *g;          /* [nRe][nRp][3nat][nw][nw] eV/A, index [mu][i][j]: i pairs
+                                   with k+q and j with k (Eq. 7) */
+} epwi_system;
+
+typedef struct {
+    int32_t precision;          /* epwi_precision (default EPWI_FP64) */
+    double sieve_c;             /* delta cut-off |x| <= c*eta, also the sieve (default 6) */
+    double omega_min_eV;        /* modes below this energy are dropped (default 1e-4) */
+    int32_t device;             /* CUDA device ordinal (default 0) */
+    void *cuda_stream;          /* cudaStream_t, NULL = legacy default stream */
+    int32_t kpoint_chunk;       /* k-points per on-the-fly chunk, 0 = automatic */
+} epwi_options;
+
+/* Per-call statistics of the last epwi_scatter_rates (and what precedes it). */
+typedef struct {
+    int64_t n_kpoints;          /* k-points with at least one state in the window */
+    int64_t n_states;           /* states (n,k) in the window */
+    int64_t n_pairs;            /* (k,q) pairs kept by the sieve */
+    int64_t n_tiles;            /* 128-pair work tiles processed */
+    int64_t n_chunks;           /* on-the-fly k-point chunks */
+    double ms_eigs, ms_sieve, ms_restage, ms_scatter, ms_reduce;   /* device time per stage */
+    int64_t restage_bytes;      /* algorithmic bytes of the Re->k stage (g read once per chunk) */
+    double scatter_flops;       /* algorithmic flops of the Rp->q GEMM (one pass, no padding) */
+    int32_t precision;
+} epwi_stats;
+
+/* Fills *opt with the defaults listed above. */
+void epwi_default_options(epwi_options *opt);
+
+/* Creates a context on opt->device (opt may be NULL for defaults).  Errors: EINVAL, ECUDA. */
+epwi_status epwi_create(epwi_ctx **ctx, const epwi_options *opt);
+
+/* Frees all device memory of the context.  NULL is ignored. */
+void epwi_destroy(epwi_ctx *ctx);
+
+/* Message of the last failed call on this context ("" if none).  Valid until the next call. */
+const char *epwi_last_error(const epwi_ctx *ctx);
+
+/* Switches the interpolation arithmetic for subsequent epwi_scatter_rates calls. */
+epwi_status epwi_set_precision(epwi_ctx *ctx, int32_t precision);
+
+/* Switches the CUDA stream used by subsequent calls. */
+epwi_status epwi_set_stream(epwi_ctx *ctx, void *cuda_stream);
+
+/* Copies the system to the device and folds the weights in: w_R into H(R) (Eq. 4),
+ * w_R/sqrt(m_a m_b) into Phi(R) (Eq. 5), w_e w_p into g (Eq. 7); reorders g into the
+ * per-R_p column layout of the Re->k stage and keeps an FP32 copy for the split-precision
+ * modes.  Validates Hermiticity of H (1e-10 relative), Phi(-R) = Phi(R)^T, the acoustic
+ * sum rule (1e-8 relative), masses > 0 and that -R is in each set.  Replaces any previous
+ * system (eigen-tables and rates are discarded).  Synchronous. */
+epwi_status epwi_setup(epwi_ctx *ctx, const epwi_system *sys);
+
+/* Interpolates and diagonalises H(k) and D(q) on the full grids (Sec. II B, Eqs. 4-6):
+ * eps_nk (ascending), V(k) (columns), v_nk = (1/hbar) Re[V^dag dH/dk V]_nn, hbar*omega_qnu
+ * and u_{mu nu}(q) = (hbar / 2 m_mu omega_nu)^{1/2} e_{mu nu}(q) (FP64 Jacobi, one matrix per
+ * grid point).  qgrid must equal kgrid (k+q is a grid point, Sec. III E).  The least
+ * common multiple of the three grid sizes must be <= 4096.  Errors: ESTATE (no setup),
+ * EINVAL, ENUMERIC (Jacobi did not converge). */
+epwi_status epwi_eigs(epwi_ctx *ctx, const int32_t kgrid[3], const int32_t qgrid[3]);
+
+/* Smallest and largest band energy on the k grid (eV).  Synchronises. */
+epwi_status epwi_band_range(epwi_ctx *ctx, double *emin_eV, double *emax_eV);
+
+/* Valence maximum (band n_valence-1) and conduction minimum (band n_valence) over the grid. */
+epwi_status epwi_band_edges(epwi_ctx *ctx, int32_t n_valence, double *vbm_eV, double *cbm_eV);
+
+/* Chemical potential for a conduction-electron density n_c (per cm^3) at T (Sec. III A):
+ * bisection on n(mu) = (2/(N_k V)) sum_{n >= n_valence, k} f(eps_nk) to a relative
+ * residual of 1e-13.  Synchronises. */
+epwi_status epwi_find_mu(epwi_ctx *ctx, double T_K, double carriers_per_cm3,
+                         int32_t n_valence, double *mu_eV);
+
+/* Conduction-electron density (per cm^3) at mu and T, same sum as epwi_find_mu. */
+epwi_status epwi_carrier_density(epwi_ctx *ctx, double T_K, double mu_eV, int32_t n_valence,
+                                 double *n_cm3);
+
+/* SERTA scattering rates (Sec. II C, Eq. 10) for every state with emin <= eps_nk <= emax:
+ * 1/tau_nk = (2 pi/hbar)(1/N_q) sum_{q m nu} |g^nu_mn(k,q)|^2 [(N + f) delta(e_nk + w - e_mk+q)
+ *            + (1 + N - f) delta(e_nk - w - e_mk+q)],
+ * delta(x) = exp(-(x/eta)^2)/(sqrt(pi) eta) for |x| <= c eta, eta = smear_eV.
+ * Runs the sieve (Sec. III A), then the on-the-fly q-batched interpolation (Sec. III D) in
+ * k-point chunks.  Results stay on the device (see epwi_get_rates); n_states and n_pairs
+ * (either may be NULL) receive the state and sieved-pair counts.  Synchronises. */
+epwi_status epwi_scatter_rates(epwi_ctx *ctx, double T_K, double mu_eV, double smear_eV,
+                               double emin_eV, double emax_eV,
+                               int64_t *n_states, int64_t *n_pairs);
+
+/* Copies the states of the last epwi_scatter_rates (ordered by k index, then band) and
+ * their rates to host arrays of capacity >= n_states.  Any output pointer may be NULL.
+ * Errors: ESTATE (no rates), ETOOSMALL (capacity). */
+epwi_status epwi_get_rates(epwi_ctx *ctx, int64_t capacity, int32_t *k_idx, int32_t *band,
+                           double *inv_tau_s);
+
+/* sigma_ab = (2 e^2/(N_k V)) sum_{nk in window} v_a v_b tau f(1-f)/(k_B T) (Sec. II C,
+ * Eq. 12 with F = v tau), over the states of the last epwi_scatter_rates with 1/tau > 0,
+ * at the T and mu of that call.  sigma_Sm is 3x3 row-major.  Synchronises. */
+epwi_status epwi_conductivity(epwi_ctx *ctx, double sigma_Sm[9]);
+
+/* mu_ab = sigma_ab / (n e) (Sec. II C, Eq. 15) using the last conductivity. */
+epwi_status epwi_mobility(epwi_ctx *ctx, double carriers_per_cm3, double mu_cm2Vs[9]);
+
+/* Copies the eigen-tables: eps [Nk][nw], V [Nk][nw][nw] (row i, column n), vel
+ * [Nk][nw][3].  Any pointer may be NULL.  Synchronises. */
+epwi_status epwi_get_bands(epwi_ctx *ctx, double *eps, epwi_c64 *V, double *vel);
+
+/* Copies hbar*omega [Nq][Nm] (eV) and u [Nq][Nm][Nm] (A, row mu, column nu; zero columns
+ * for dropped modes).  Any pointer may be NULL.  Synchronises. */
+epwi_status epwi_get_phonons(epwi_ctx *ctx, double *omega, epwi_c64 *u);
+
+/* Sieve output of the last epwi_scatter_rates: the k-points with window states
+ * (kpts[n_kpoints]) and per k-point pair counts (counts[n_kpoints]).  Pair lists are not
+ * kept (they are built per chunk).  Errors: ESTATE, ETOOSMALL. */
+epwi_status epwi_get_sieve(epwi_ctx *ctx, int64_t capacity, int32_t *kpts, int64_t *counts);
+
+/* |g^nu_mn(k,q)|^2 (eV^2) for explicit pairs, through the same Re->k, Rp->q and rotation
+ * kernels as epwi_scatter_rates in the current precision: g2 has layout
+ * [pair][nsel][nu][m] for the bands n = band_lo .. band_lo+nsel-1 at each k.
+ * ik, iq: [npairs] grid indices; band_lo, nsel: window per pair (nsel <= nw).  For tests. */
+epwi_status epwi_g2(epwi_ctx *ctx, int64_t npairs, const int32_t *ik, const int32_t *iq,
+                    int32_t band_lo, int32_t nsel, double *g2);
+
+/* Number of kernels this library has launched in the process so far (all contexts). */
+int64_t epwi_kernel_launches(void);
+
+/* Statistics of the last epwi_scatter_rates. */
+epwi_status epwi_get_stats(epwi_ctx *ctx, epwi_stats *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EPWI_H */

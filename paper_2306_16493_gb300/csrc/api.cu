@@ -1,0 +1,537 @@
+// C ABI of libepwi (declared in include/epwi.h): argument checks, input validation,
+// weight folding and the orchestration of the device stages.  No C++ exception crosses
+// the ABI; every entry point returns an epwi_status and records a message.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "epwi_internal.cuh"
+#include "scatter.cuh"
+
+namespace {
+
+template <class F>
+epwi_status guard(epwi_ctx *c, F &&f) {
+    if (!c) return EPWI_EINVAL;
+    try {
+        EPWI_CUDA(cudaSetDevice(c->device));
+        f();
+        c->err.clear();
+        return EPWI_OK;
+    } catch (const EpwiError &e) {
+        c->err = e.msg;
+        return e.status;
+    } catch (const std::bad_alloc &) {
+        c->err = "host allocation failed";
+        return EPWI_ENOMEM;
+    } catch (...) {
+        c->err = "unexpected internal error";
+        return EPWI_ECUDA;
+    }
+}
+
+template <class T>
+void upload(DevBuf &b, const T *h, size_t n, cudaStream_t st) {
+    b.ensure(sizeof(T) * (n ? n : 1));
+    if (n) EPWI_CUDA(cudaMemcpyAsync(b.p, h, sizeof(T) * n, cudaMemcpyHostToDevice, st));
+}
+
+std::vector<int> minus_index(const int32_t *R, int n, const char *what) {
+    std::map<std::array<int, 3>, int> lut;
+    for (int i = 0; i < n; ++i) lut[{R[3 * i], R[3 * i + 1], R[3 * i + 2]}] = i;
+    std::vector<int> mi(n);
+    for (int i = 0; i < n; ++i) {
+        auto it = lut.find({-R[3 * i], -R[3 * i + 1], -R[3 * i + 2]});
+        EPWI_REQUIRE(it != lut.end(), EPWI_EINVAL, std::string(what) + ": -R missing from the set");
+        mi[i] = it->second;
+    }
+    return mi;
+}
+
+long long lcm3(long long a, long long b, long long c) {
+    auto l = [](long long x, long long y) { return x / std::gcd(x, y) * y; };
+    return l(l(a, b), c);
+}
+
+void require_sys(epwi_ctx *c) { EPWI_REQUIRE(c->have_sys, EPWI_ESTATE, "epwi_setup has not been called"); }
+void require_eigs(epwi_ctx *c) {
+    require_sys(c);
+    EPWI_REQUIRE(c->have_eigs, EPWI_ESTATE, "epwi_eigs has not been called");
+}
+void require_rates(epwi_ctx *c) {
+    require_eigs(c);
+    EPWI_REQUIRE(c->have_rates, EPWI_ESTATE, "epwi_scatter_rates has not been called");
+}
+
+}  // namespace
+
+int64_t g_epwi_launches = 0;
+
+extern "C" {
+
+int64_t epwi_kernel_launches(void) { return g_epwi_launches; }
+
+void epwi_default_options(epwi_options *opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->precision = EPWI_FP64;
+    opt->sieve_c = 6.0;
+    opt->omega_min_eV = 1e-4;
+    opt->device = 0;
+    opt->cuda_stream = nullptr;
+    opt->kpoint_chunk = 0;
+}
+
+epwi_status epwi_create(epwi_ctx **out, const epwi_options *opt) {
+    if (!out) return EPWI_EINVAL;
+    *out = nullptr;
+    epwi_ctx *c = nullptr;
+    try {
+        c = new epwi_ctx();
+    } catch (...) {
+        return EPWI_ENOMEM;
+    }
+    if (opt) c->opt = *opt;
+    else epwi_default_options(&c->opt);
+    if (!(c->opt.sieve_c > 0) || !(c->opt.omega_min_eV >= 0) || c->opt.precision < 0 ||
+        c->opt.precision > EPWI_FP16X3) {
+        delete c;
+        return EPWI_EINVAL;
+    }
+    c->device = c->opt.device;
+    c->stream = (cudaStream_t)c->opt.cuda_stream;
+    epwi_status st = guard(c, [&] {
+        int n = 0;
+        EPWI_CUDA(cudaGetDeviceCount(&n));
+        EPWI_REQUIRE(c->device >= 0 && c->device < n, EPWI_EINVAL, "no such CUDA device");
+        EPWI_CUDA(cudaSetDevice(c->device));
+        EPWI_CUDA(cudaFree(nullptr));   // create the primary context now
+    });
+    if (st != EPWI_OK) {
+        delete c;
+        return st;
+    }
+    *out = c;
+    return EPWI_OK;
+}
+
+void epwi_destroy(epwi_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    delete c;
+}
+
+const char *epwi_last_error(const epwi_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+epwi_status epwi_set_precision(epwi_ctx *c, int32_t p) {
+    return guard(c, [&] {
+        EPWI_REQUIRE(p >= EPWI_FP64 && p <= EPWI_FP16X3, EPWI_EINVAL, "unknown precision");
+        c->opt.precision = p;
+    });
+}
+
+epwi_status epwi_set_stream(epwi_ctx *c, void *s) {
+    return guard(c, [&] {
+        c->stream = (cudaStream_t)s;
+        c->opt.cuda_stream = s;
+    });
+}
+
+epwi_status epwi_setup(epwi_ctx *c, const epwi_system *s) {
+    return guard(c, [&] {
+        EPWI_REQUIRE(s, EPWI_EINVAL, "system is NULL");
+        EPWI_REQUIRE(s->nat >= 1 && 3 * s->nat <= epc::kMaxNm, EPWI_EUNSUPPORTED,
+                     "nat must be in [1, 6]");
+        EPWI_REQUIRE(s->nw >= 1 && s->nw <= epc::kMaxW, EPWI_EUNSUPPORTED, "nw must be in [1, 24]");
+        EPWI_REQUIRE(s->nRe >= 1 && s->nRp >= 1, EPWI_EINVAL, "empty lattice-vector set");
+        EPWI_REQUIRE(s->mass && s->Re && s->we && s->H && s->Rp && s->wp && s->Phi && s->g,
+                     EPWI_EINVAL, "NULL array in epwi_system");
+        const int W = s->nw, Nm = 3 * s->nat, nRe = s->nRe, nRp = s->nRp;
+        for (int a = 0; a < s->nat; ++a)
+            EPWI_REQUIRE(s->mass[a] > 0 && std::isfinite(s->mass[a]), EPWI_EINVAL, "mass must be > 0");
+        int rmax = 0;
+        for (int i = 0; i < 3 * nRe; ++i) rmax = std::max(rmax, std::abs(s->Re[i]));
+        for (int i = 0; i < 3 * nRp; ++i) rmax = std::max(rmax, std::abs(s->Rp[i]));
+        EPWI_REQUIRE(rmax <= 64, EPWI_EUNSUPPORTED, "lattice coordinates beyond |n| = 64");
+        auto mie = minus_index(s->Re, nRe, "Re");
+        auto mip = minus_index(s->Rp, nRp, "Rp");
+        // Hermiticity of H and symmetry of the weights
+        double hmax = 0, herr = 0;
+        for (int r = 0; r < nRe; ++r) {
+            EPWI_REQUIRE(s->we[r] == s->we[mie[r]], EPWI_EINVAL, "we(R) != we(-R)");
+            for (int i = 0; i < W; ++i)
+                for (int j = 0; j < W; ++j) {
+                    const epwi_c64 a = s->H[((size_t)r * W + i) * W + j];
+                    const epwi_c64 b = s->H[((size_t)mie[r] * W + j) * W + i];
+                    hmax = std::max(hmax, std::hypot(a.re, a.im));
+                    herr = std::max(herr, std::hypot(a.re - b.re, a.im + b.im));
+                }
+        }
+        EPWI_REQUIRE(herr <= 1e-10 * std::max(hmax, 1e-300), EPWI_EINVAL,
+                     "H(-R) != H(R)^dagger (relative error " + std::to_string(herr / hmax) + ")");
+        // Phi symmetry and acoustic sum rule
+        double pmax = 0, perr = 0;
+        for (int r = 0; r < nRp; ++r) {
+            EPWI_REQUIRE(s->wp[r] == s->wp[mip[r]], EPWI_EINVAL, "wp(R) != wp(-R)");
+            for (int i = 0; i < Nm; ++i)
+                for (int j = 0; j < Nm; ++j) {
+                    const double a = s->Phi[((size_t)r * Nm + i) * Nm + j];
+                    const double b = s->Phi[((size_t)mip[r] * Nm + j) * Nm + i];
+                    pmax = std::max(pmax, std::fabs(a));
+                    perr = std::max(perr, std::fabs(a - b));
+                }
+        }
+        EPWI_REQUIRE(perr <= 1e-10 * std::max(pmax, 1e-300), EPWI_EINVAL, "Phi(-R) != Phi(R)^T");
+        double asr = 0;
+        for (int i = 0; i < Nm; ++i)
+            for (int beta = 0; beta < 3; ++beta) {
+                double sum = 0;
+                for (int r = 0; r < nRp; ++r)
+                    for (int b = 0; b < s->nat; ++b)
+                        sum += s->wp[r] * s->Phi[((size_t)r * Nm + i) * Nm + 3 * b + beta];
+                asr = std::max(asr, std::fabs(sum));
+            }
+        EPWI_REQUIRE(asr <= 1e-8 * std::max(pmax, 1e-300), EPWI_EINVAL, "acoustic sum rule violated");
+
+        c->have_sys = c->have_eigs = c->have_rates = c->have_sigma = false;
+        c->nat = s->nat;
+        c->nw = W;
+        c->nm = Nm;
+        c->nRe = nRe;
+        c->nRp = nRp;
+        c->rmax = rmax;
+        std::memcpy(c->lattice, s->lattice, sizeof(c->lattice));
+        const double *A = s->lattice;
+        c->volume = std::fabs(A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                              A[2] * (A[3] * A[7] - A[4] * A[6]));
+        EPWI_REQUIRE(c->volume > 0, EPWI_EINVAL, "singular lattice");
+        // fold weights
+        std::vector<double2> Hw((size_t)nRe * W * W);
+        std::vector<double> Rc((size_t)nRe * 3);
+        for (int r = 0; r < nRe; ++r) {
+            for (int e = 0; e < W * W; ++e) {
+                const epwi_c64 h = s->H[(size_t)r * W * W + e];
+                Hw[(size_t)r * W * W + e] = make_double2(s->we[r] * h.re, s->we[r] * h.im);
+            }
+            for (int ax = 0; ax < 3; ++ax)
+                Rc[3 * r + ax] = s->Re[3 * r] * A[ax] + s->Re[3 * r + 1] * A[3 + ax] +
+                                 s->Re[3 * r + 2] * A[6 + ax];
+        }
+        std::vector<double> Pw((size_t)nRp * Nm * Nm), mm(Nm);
+        for (int i = 0; i < Nm; ++i) mm[i] = s->mass[i / 3];
+        for (int r = 0; r < nRp; ++r)
+            for (int i = 0; i < Nm; ++i)
+                for (int j = 0; j < Nm; ++j)
+                    Pw[((size_t)r * Nm + i) * Nm + j] =
+                        s->wp[r] * s->Phi[((size_t)r * Nm + i) * Nm + j] / std::sqrt(mm[i] * mm[j]);
+        const size_t ng = (size_t)nRe * nRp * Nm * W * W;
+        const size_t per_re = (size_t)nRp * Nm * W * W;
+        std::vector<double2> g64(ng);
+        std::vector<float2> g32(ng);
+        for (int re = 0; re < nRe; ++re)
+            for (int rp = 0; rp < nRp; ++rp) {
+                const double w = s->we[re] * s->wp[rp];
+                const size_t base = (size_t)re * per_re + (size_t)rp * Nm * W * W;
+                for (size_t e = 0; e < (size_t)Nm * W * W; ++e) {
+                    const epwi_c64 v = s->g[base + e];
+                    g64[base + e] = make_double2(w * v.re, w * v.im);
+                    g32[base + e] = make_float2((float)(w * v.re), (float)(w * v.im));
+                }
+            }
+        upload(c->Re, s->Re, 3 * (size_t)nRe, c->stream);
+        upload(c->Rp, s->Rp, 3 * (size_t)nRp, c->stream);
+        upload(c->Rcart, Rc.data(), Rc.size(), c->stream);
+        upload(c->Hw, Hw.data(), Hw.size(), c->stream);
+        upload(c->Phiw, Pw.data(), Pw.size(), c->stream);
+        upload(c->mode_mass, mm.data(), mm.size(), c->stream);
+        upload(c->gw64, g64.data(), g64.size(), c->stream);
+        upload(c->gw32, g32.data(), g32.size(), c->stream);
+        EPWI_CUDA(cudaStreamSynchronize(c->stream));
+        c->have_sys = true;
+    });
+}
+
+epwi_status epwi_eigs(epwi_ctx *c, const int32_t kgrid[3], const int32_t qgrid[3]) {
+    return guard(c, [&] {
+        require_sys(c);
+        EPWI_REQUIRE(kgrid && qgrid, EPWI_EINVAL, "grid is NULL");
+        for (int a = 0; a < 3; ++a) {
+            EPWI_REQUIRE(kgrid[a] >= 1 && kgrid[a] == qgrid[a], EPWI_EINVAL,
+                         "qgrid must equal kgrid and be >= 1");
+        }
+        const long long L = lcm3(kgrid[0], kgrid[1], kgrid[2]);
+        EPWI_REQUIRE(L <= epc::kMaxL, EPWI_EUNSUPPORTED, "lcm of grid sizes exceeds 4096");
+        const int64_t nk = (int64_t)kgrid[0] * kgrid[1] * kgrid[2];
+        EPWI_REQUIRE(nk < (int64_t(1) << 31), EPWI_EUNSUPPORTED, "grid larger than 2^31 points");
+        c->have_eigs = c->have_rates = c->have_sigma = false;
+        for (int a = 0; a < 3; ++a) c->ng[a] = kgrid[a];
+        c->nk = nk;
+        c->L = (int)L;
+        cudaEvent_t e0, e1;
+        EPWI_CUDA(cudaEventCreate(&e0));
+        EPWI_CUDA(cudaEventCreate(&e1));
+        cudaEventRecord(e0, c->stream);
+        launch_phase_tables(c);
+        launch_eigs(c);
+        cudaEventRecord(e1, c->stream);
+        int flag[2];
+        EPWI_CUDA(cudaMemcpyAsync(flag, c->eig_flag.p, sizeof(flag), cudaMemcpyDeviceToHost, c->stream));
+        EPWI_CUDA(cudaStreamSynchronize(c->stream));
+        cudaEventElapsedTime(&c->ms_eigs, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        EPWI_REQUIRE(flag[0] == 0 && flag[1] == 0, EPWI_ENUMERIC,
+                     "Jacobi did not converge on " + std::to_string(flag[0]) + " H(k) and " +
+                         std::to_string(flag[1]) + " D(q) matrices");
+        c->have_eigs = true;
+    });
+}
+
+epwi_status epwi_band_range(epwi_ctx *c, double *emin, double *emax) {
+    return guard(c, [&] {
+        require_eigs(c);
+        const double *e = c->eps.as<double>();
+        const int64_t n = c->nk * c->nw;
+        if (emin) *emin = device_reduce_minmax(c, e, n, 1, 0, false);
+        if (emax) *emax = device_reduce_minmax(c, e, n, 1, 0, true);
+    });
+}
+
+epwi_status epwi_band_edges(epwi_ctx *c, int32_t nv, double *vbm, double *cbm) {
+    return guard(c, [&] {
+        require_eigs(c);
+        EPWI_REQUIRE(nv >= 1 && nv < c->nw, EPWI_EINVAL, "n_valence must be in [1, nw-1]");
+        const double *e = c->eps.as<double>();
+        if (vbm) *vbm = device_reduce_minmax(c, e, c->nk, c->nw, nv - 1, true);
+        if (cbm) *cbm = device_reduce_minmax(c, e, c->nk, c->nw, nv, false);
+    });
+}
+
+epwi_status epwi_carrier_density(epwi_ctx *c, double T, double mu, int32_t nv, double *n) {
+    return guard(c, [&] {
+        require_eigs(c);
+        EPWI_REQUIRE(T > 0 && n && nv >= 0 && nv < c->nw, EPWI_EINVAL, "bad argument");
+        *n = carrier_density(c, T, mu, nv);
+    });
+}
+
+epwi_status epwi_find_mu(epwi_ctx *c, double T, double n_c, int32_t nv, double *mu_out) {
+    return guard(c, [&] {
+        require_eigs(c);
+        EPWI_REQUIRE(T > 0 && n_c > 0 && mu_out && nv >= 0 && nv < c->nw, EPWI_EINVAL, "bad argument");
+        const double *e = c->eps.as<double>();
+        double lo = device_reduce_minmax(c, e, c->nk, c->nw, nv, false) - 3.0;
+        double hi = device_reduce_minmax(c, e, c->nk, c->nw, c->nw - 1, true) + 3.0;
+        double mid = 0.5 * (lo + hi);
+        for (int it = 0; it < 400; ++it) {
+            mid = 0.5 * (lo + hi);
+            const double n = carrier_density(c, T, mid, nv);
+            if (std::fabs(n - n_c) <= 1e-13 * n_c || hi - lo <= 1e-15) break;
+            if (n < n_c) lo = mid;
+            else hi = mid;
+        }
+        *mu_out = mid;
+    });
+}
+
+epwi_status epwi_scatter_rates(epwi_ctx *c, double T, double mu, double eta, double emin,
+                               double emax, int64_t *n_states, int64_t *n_pairs) {
+    return guard(c, [&] {
+        require_eigs(c);
+        EPWI_REQUIRE(T > 0 && eta > 0 && std::isfinite(mu) && !(emin > emax), EPWI_EINVAL,
+                     "need T > 0, smear > 0, finite mu and emin <= emax");
+        c->have_rates = c->have_sigma = false;
+        c->T = T;
+        c->mu = mu;
+        c->eta = eta;
+        c->emin = emin;
+        c->emax = emax;
+        std::memset(&c->stats, 0, sizeof(c->stats));
+        c->stats.precision = c->opt.precision;
+        c->stats.ms_eigs = c->ms_eigs;
+        cudaEvent_t e0, e1;
+        EPWI_CUDA(cudaEventCreate(&e0));
+        EPWI_CUDA(cudaEventCreate(&e1));
+        cudaEventRecord(e0, c->stream);
+        build_window(c);
+        sieve_count(c);
+        cudaEventRecord(e1, c->stream);
+        EPWI_CUDA(cudaStreamSynchronize(c->stream));
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        c->stats.ms_sieve = ms;
+        occupation_tables(c);
+        if (c->nstates > 0)
+            EPWI_CUDA(cudaMemsetAsync(c->inv_tau.p, 0, sizeof(double) * c->nstates, c->stream));
+        WorkSet ws;
+        ws.nkp = c->nkp;
+        ws.kpts = c->kpts.as<int>();
+        ws.kp_state = c->kp_state.as<int64_t>();
+        ws.kp_pairs = c->kp_pairs.as<int64_t>();
+        ws.h_kp_pairs = c->h_kp_pairs;
+        ws.h_kp_state.resize(c->nkp + 1);
+        EPWI_CUDA(cudaMemcpyAsync(ws.h_kp_state.data(), c->kp_state.p, sizeof(int64_t) * (c->nkp + 1),
+                                  cudaMemcpyDeviceToHost, c->stream));
+        EPWI_CUDA(cudaStreamSynchronize(c->stream));
+        process_workset(c, ws, nullptr);
+        c->stats.n_kpoints = c->nkp;
+        c->stats.n_states = c->nstates;
+        c->stats.n_pairs = c->npairs;
+        c->stats.restage_bytes = (int64_t)c->stats.n_chunks * c->nRe * c->nRp * c->nm * c->nw *
+                                 c->nw * (c->opt.precision == EPWI_FP64 ? 16 : 8);
+        c->stats.scatter_flops = 8.0 * c->nRp * c->nm * c->nw * (double)c->npairs *
+                                 ((double)c->nstates / std::max<int64_t>(1, c->nkp));
+        if (n_states) *n_states = c->nstates;
+        if (n_pairs) *n_pairs = c->npairs;
+        c->have_rates = true;
+    });
+}
+
+epwi_status epwi_get_rates(epwi_ctx *c, int64_t cap, int32_t *k_idx, int32_t *band, double *rates) {
+    return guard(c, [&] {
+        require_rates(c);
+        EPWI_REQUIRE(cap >= c->nstates, EPWI_ETOOSMALL, "capacity below n_states");
+        const size_t n = (size_t)c->nstates;
+        if (n) {
+            if (k_idx) EPWI_CUDA(cudaMemcpyAsync(k_idx, c->st_k.p, 4 * n, cudaMemcpyDeviceToHost, c->stream));
+            if (band) EPWI_CUDA(cudaMemcpyAsync(band, c->st_n.p, 4 * n, cudaMemcpyDeviceToHost, c->stream));
+            if (rates) EPWI_CUDA(cudaMemcpyAsync(rates, c->inv_tau.p, 8 * n, cudaMemcpyDeviceToHost, c->stream));
+        }
+        EPWI_CUDA(cudaStreamSynchronize(c->stream));
+    });
+}
+
+epwi_status epwi_conductivity(epwi_ctx *c, double sigma[9]) {
+    return guard(c, [&] {
+        require_rates(c);
+        EPWI_REQUIRE(sigma, EPWI_EINVAL, "sigma is NULL");
+        conductivity(c, c->sigma);
+        for (int i = 0; i < 9; ++i) {
+            EPWI_REQUIRE(std::isfinite(c->sigma[i]), EPWI_ENUMERIC, "non-finite conductivity");
+            sigma[i] = c->sigma[i];
+        }
+        c->have_sigma = true;
+    });
+}
+
+epwi_status epwi_mobility(epwi_ctx *c, double n_c, double mob[9]) {
+    return guard(c, [&] {
+        EPWI_REQUIRE(c->have_sigma, EPWI_ESTATE, "epwi_conductivity has not been called");
+        EPWI_REQUIRE(n_c > 0 && mob, EPWI_EINVAL, "bad argument");
+        for (int i = 0; i < 9; ++i) mob[i] = c->sigma[i] / (n_c * 1e6 * epc::kECharge) * 1e4;
+    });
+}
+
+epwi_status epwi_get_bands(epwi_ctx *c, double *eps, epwi_c64 *V, double *vel) {
+    return guard(c, [&] {
+        require_eigs(c);
+        const size_t nk = (size_t)c->nk, W = (size_t)c->nw;
+        if (eps) EPWI_CUDA(cudaMemcpyAsync(eps, c->eps.p, 8 * nk * W, cudaMemcpyDeviceToHost, c->stream));
+        if (V) EPWI_CUDA(cudaMemcpyAsync(V, c->V.p, 16 * nk * W * W, cudaMemcpyDeviceToHost, c->stream));
+        if (vel) EPWI_CUDA(cudaMemcpyAsync(vel, c->vel.p, 24 * nk * W, cudaMemcpyDeviceToHost, c->stream));
+        EPWI_CUDA(cudaStreamSynchronize(c->stream));
+    });
+}
+
+epwi_status epwi_get_phonons(epwi_ctx *c, double *omega, epwi_c64 *u) {
+    return guard(c, [&] {
+        require_eigs(c);
+        const size_t nq = (size_t)c->nk, Nm = (size_t)c->nm;
+        if (omega) EPWI_CUDA(cudaMemcpyAsync(omega, c->hw.p, 8 * nq * Nm, cudaMemcpyDeviceToHost, c->stream));
+        if (u) EPWI_CUDA(cudaMemcpyAsync(u, c->u.p, 16 * nq * Nm * Nm, cudaMemcpyDeviceToHost, c->stream));
+        EPWI_CUDA(cudaStreamSynchronize(c->stream));
+    });
+}
+
+epwi_status epwi_get_sieve(epwi_ctx *c, int64_t cap, int32_t *kpts, int64_t *counts) {
+    return guard(c, [&] {
+        require_rates(c);
+        EPWI_REQUIRE(cap >= c->nkp, EPWI_ETOOSMALL, "capacity below n_kpoints");
+        if (kpts && c->nkp)
+            EPWI_CUDA(cudaMemcpyAsync(kpts, c->kpts.p, 4 * (size_t)c->nkp, cudaMemcpyDeviceToHost, c->stream));
+        EPWI_CUDA(cudaStreamSynchronize(c->stream));
+        if (counts)
+            for (int64_t p = 0; p < c->nkp; ++p) counts[p] = c->h_kp_pairs[p + 1] - c->h_kp_pairs[p];
+    });
+}
+
+epwi_status epwi_g2(epwi_ctx *c, int64_t npairs, const int32_t *ik, const int32_t *iq,
+                    int32_t band_lo, int32_t nsel, double *g2) {
+    return guard(c, [&] {
+        require_eigs(c);
+        EPWI_REQUIRE(npairs >= 1 && ik && iq && g2, EPWI_EINVAL, "bad argument");
+        EPWI_REQUIRE(band_lo >= 0 && nsel >= 1 && band_lo + nsel <= c->nw, EPWI_EINVAL, "bad band window");
+        for (int64_t p = 0; p < npairs; ++p)
+            EPWI_REQUIRE(ik[p] >= 0 && ik[p] < c->nk && iq[p] >= 0 && iq[p] < c->nk, EPWI_EINVAL,
+                         "grid index out of range");
+        std::vector<int64_t> order(npairs);
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return ik[a] < ik[b]; });
+        std::vector<int> kp, pq(npairs);
+        std::vector<int64_t> kst, kpr;
+        for (int64_t t = 0; t < npairs; ++t) {
+            const int64_t p = order[t];
+            if (kp.empty() || kp.back() != ik[p]) {
+                kp.push_back(ik[p]);
+                kpr.push_back(t);
+            }
+            pq[t] = iq[p];
+        }
+        kpr.push_back(npairs);
+        const int64_t nkp = (int64_t)kp.size();
+        for (int64_t p = 0; p <= nkp; ++p) kst.push_back(p * nsel);
+        DevBuf dk, ds, dp, dq, dout;
+        auto cleanup = [&] { dk.release(); ds.release(); dp.release(); dq.release(); dout.release(); };
+        try {
+            upload(dk, kp.data(), kp.size(), c->stream);
+            upload(ds, kst.data(), kst.size(), c->stream);
+            upload(dp, kpr.data(), kpr.size(), c->stream);
+            upload(dq, pq.data(), pq.size(), c->stream);
+            const size_t nout = (size_t)npairs * nsel * c->nm * c->nw;
+            dout.ensure(sizeof(double) * nout);
+            if (c->eta <= 0) c->eta = 1.0;   // unused by g2 mode, kept finite
+            WorkSet ws;
+            ws.nkp = nkp;
+            ws.kpts = dk.as<int>();
+            ws.kp_state = ds.as<int64_t>();
+            ws.kp_pairs = dp.as<int64_t>();
+            ws.h_kp_state = kst;
+            ws.h_kp_pairs = kpr;
+            ws.pairs_dev = dq.as<int>();
+            ws.ovr_lo = band_lo;
+            ws.ovr_nsel = nsel;
+            epwi_stats keep = c->stats;
+            process_workset(c, ws, dout.as<double>());
+            c->stats = keep;
+            std::vector<double> h(nout);
+            EPWI_CUDA(cudaMemcpyAsync(h.data(), dout.p, 8 * nout, cudaMemcpyDeviceToHost, c->stream));
+            EPWI_CUDA(cudaStreamSynchronize(c->stream));
+            const size_t per = (size_t)nsel * c->nm * c->nw;
+            for (int64_t t = 0; t < npairs; ++t)
+                std::memcpy(g2 + (size_t)order[t] * per, h.data() + (size_t)t * per, 8 * per);
+        } catch (...) {
+            cleanup();
+            throw;
+        }
+        cleanup();
+    });
+}
+
+epwi_status epwi_get_stats(epwi_ctx *c, epwi_stats *out) {
+    return guard(c, [&] {
+        EPWI_REQUIRE(out, EPWI_EINVAL, "out is NULL");
+        *out = c->stats;
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,233 @@
+// Internal declarations shared by the translation units of libepwi (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "epwi.h"
+
+// ----------------------------------------------------------------------------- constants
+// CODATA 2018.
+namespace epc {
+constexpr double kHbarEVs = 6.582119569e-16;           // eV s
+constexpr double kHbarJs = 1.054571817e-34;            // J s
+constexpr double kKbEVK = 8.617333262e-5;              // eV / K
+constexpr double kECharge = 1.602176634e-19;           // C
+constexpr double kAmuKg = 1.66053906660e-27;           // kg
+// hbar^2 / (amu A^2) in eV: (hbar omega)^2 = lambda[eV/A^2/amu] * kHbar2AmuA2
+constexpr double kHbar2AmuA2 = kHbarJs * kHbarJs / (kAmuKg * 1e-20) / kECharge;
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kTile = 128;        // pairs per work tile (one tcgen05 M=128 tile)
+constexpr int kMaxW = 24;
+constexpr int kMaxNm = 18;
+constexpr int kMaxL = 4096;       // lcm of the grid sizes (phase-table length)
+}  // namespace epc
+
+// ----------------------------------------------------------------------------- errors
+struct EpwiError {
+    epwi_status status;
+    std::string msg;
+};
+
+#define EPWI_CUDA(call)                                                                    \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            throw EpwiError{e_ == cudaErrorMemoryAllocation ? EPWI_ENOMEM : EPWI_ECUDA,    \
+                            std::string(#call) + ": " + cudaGetErrorString(e_)};          \
+        }                                                                                  \
+    } while (0)
+
+// Every kernel launch site ends with this check; it also counts the launch.
+extern int64_t g_epwi_launches;
+#define EPWI_CHECK_LAUNCH()                                                                \
+    do {                                                                                   \
+        ++g_epwi_launches;                                                                 \
+        EPWI_CUDA(cudaGetLastError());                                                     \
+    } while (0)
+
+#define EPWI_REQUIRE(cond, st, m)                                                          \
+    do {                                                                                   \
+        if (!(cond)) throw EpwiError{st, m};                                               \
+    } while (0)
+
+// ----------------------------------------------------------------------------- buffers
+// Device buffer that grows on demand and is freed with the context.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    void ensure(size_t n) {
+        if (n <= bytes && p) return;
+        release();
+        if (n == 0) n = 16;
+        EPWI_CUDA(cudaMalloc(&p, n));
+        bytes = n;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <class T> T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+// ----------------------------------------------------------------------------- context
+struct epwi_ctx {
+    epwi_options opt{};
+    cudaStream_t stream = nullptr;
+    std::string err;
+    int device = 0;
+
+    // system (after epwi_setup)
+    bool have_sys = false;
+    int nat = 0, nw = 0, nm = 0, nRe = 0, nRp = 0;
+    double lattice[9] = {0};
+    double volume = 0;             // A^3
+    int rmax = 0;                  // max |n_a| over both R-sets
+    DevBuf Re, Rp;                 // int32 [nR][3]
+    DevBuf Rcart;                  // double [nRe][3]
+    DevBuf Hw;                     // double2 [nRe][W][W], weight folded
+    DevBuf Phiw;                   // double [nRp][Nm][Nm], w_R / sqrt(m_a m_b) folded
+    DevBuf mode_mass;              // double [Nm] mass of the atom of each Cartesian mode
+    DevBuf gw64;                   // double2 [nRe][nRp*Nm*W*W], c = ((rp*Nm+mu)*W+i)*W+j
+    DevBuf gw32;                   // float2, same layout
+
+    // eigen-tables (after epwi_eigs)
+    bool have_eigs = false;
+    int ng[3] = {0, 0, 0};
+    int64_t nk = 0;
+    int L = 0;                     // lcm(N1, N2, N3)
+    DevBuf ph64;                   // double2 [L]: e^{2 pi i m / L}
+    DevBuf ph32;                   // float2 [L]
+    DevBuf eps;                    // double [Nk][W]
+    DevBuf eps32;                  // float  [Nk][W]
+    DevBuf V;                      // double2 [Nk][W][W] (row i, column n)
+    DevBuf V32;                    // float2 [Nk][W][W]
+    DevBuf vel;                    // double [Nk][W][3] m/s
+    DevBuf hw;                     // double [Nq][Nm] eV (dropped modes keep their value)
+    DevBuf hwmax32;                // float [Nq] largest kept mode energy, -1 if none
+    DevBuf u;                      // double2 [Nq][Nm][Nm] A (row mu, column nu), 0 if dropped
+    DevBuf u32;                    // float2 [Nq][Nm][Nm]
+    DevBuf eig_flag;               // int [1] non-converged count
+    float ms_eigs = 0;
+
+    // scatter-rate results
+    bool have_rates = false;
+    double T = 0, mu = 0, eta = 0, emin = 0, emax = 0;
+    int64_t nkp = 0, nstates = 0, npairs = 0;
+    DevBuf kpts;                   // int32 [nkp] k index
+    DevBuf win_lo, win_n;          // int32 [Nk] first window band, count
+    DevBuf kp_state;               // int64 [nkp+1] state offsets
+    DevBuf kp_pairs;               // int64 [nkp+1] pair offsets
+    DevBuf inv_tau;                // double [nstates]
+    DevBuf st_k, st_n;             // int32 [nstates]
+    DevBuf focc;                   // double [Nk][W] Fermi-Dirac
+    DevBuf nocc;                   // double [Nq][Nm] Bose-Einstein (0 for dropped modes)
+    std::vector<int64_t> h_kp_pairs;
+    epwi_stats stats{};
+
+    // scratch
+    DevBuf pairs;                  // int32 q index per pair of the chunk
+    DevBuf ghat;                   // per-chunk Re->k output
+    DevBuf tiles;                  // int4 per tile {kp_local, pair_begin, pair_end, 0}
+    DevBuf tile_part;              // double [tile][W] partial sums
+    DevBuf kp_tile;                // int64 [chunk kp + 1]
+    DevBuf scan_tmp;               // scan workspace
+    DevBuf red_tmp;                // reduction workspace
+    DevBuf counts;                 // int64 per kp
+
+    // conductivity
+    bool have_sigma = false;
+    double sigma[9] = {0};
+
+    ~epwi_ctx() {
+        DevBuf *all[] = {&Re, &Rp, &Rcart, &Hw, &Phiw, &mode_mass, &gw64, &gw32, &ph64, &ph32,
+                         &eps, &eps32, &V, &V32, &vel, &hw, &hwmax32, &u, &u32, &eig_flag,
+                         &kpts, &win_lo, &win_n, &kp_state, &kp_pairs, &inv_tau, &st_k,
+                         &st_n, &focc, &nocc, &pairs, &ghat, &tiles, &tile_part, &kp_tile,
+                         &scan_tmp, &red_tmp, &counts};
+        for (DevBuf *b : all) b->release();
+    }
+};
+
+// ----------------------------------------------------------------------------- complex
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 cmulc(double2 a, double2 b) {  // conj(a) * b
+    return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) {
+    return make_double2(a.x + b.x, a.y + b.y);
+}
+__host__ __device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {  // a*b + c
+    return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+__host__ __device__ __forceinline__ double2 cfmac(double2 a, double2 b, double2 c) {  // conj(a)*b + c
+    return make_double2(fma(a.x, b.x, fma(a.y, b.y, c.x)), fma(a.x, b.y, fma(-a.y, b.x, c.y)));
+}
+__host__ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cfmaf(float2 a, float2 b, float2 c) {
+    return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
+}
+__host__ __device__ __forceinline__ float2 cfmacf(float2 a, float2 b, float2 c) {  // conj(a)*b + c
+    return make_float2(fmaf(a.x, b.x, fmaf(a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(-a.y, b.x, c.y)));
+}
+
+// ----------------------------------------------------------------------------- grids
+// Per-axis phase strides of a grid point: a_x = (i_x * L / N_x) mod L, so that
+// e^{2 pi i k.R} = table[(n1 a1 + n2 a2 + n3 a3) mod L] exactly (integer reduction).
+struct GridInfo {
+    int n1, n2, n3, L, s1, s2, s3;   // s_x = L / N_x
+};
+
+__host__ __device__ __forceinline__ void grid_coords(const GridInfo &g, int64_t idx, int &i1,
+                                                     int &i2, int &i3) {
+    i3 = (int)(idx % g.n3);
+    int64_t t = idx / g.n3;
+    i2 = (int)(t % g.n2);
+    i1 = (int)(t / g.n2);
+}
+
+__host__ __device__ __forceinline__ int64_t grid_index(const GridInfo &g, int i1, int i2, int i3) {
+    return ((int64_t)i1 * g.n2 + i2) * g.n3 + i3;
+}
+
+__host__ __device__ __forceinline__ int64_t kplusq(const GridInfo &g, int64_t ik, int64_t iq) {
+    int a1, a2, a3, b1, b2, b3;
+    grid_coords(g, ik, a1, a2, a3);
+    grid_coords(g, iq, b1, b2, b3);
+    a1 += b1; if (a1 >= g.n1) a1 -= g.n1;
+    a2 += b2; if (a2 >= g.n2) a2 -= g.n2;
+    a3 += b3; if (a3 >= g.n3) a3 -= g.n3;
+    return grid_index(g, a1, a2, a3);
+}
+
+__host__ __device__ __forceinline__ int phase_index(int a1, int a2, int a3, int n1, int n2, int n3,
+                                                    int L) {
+    int t = n1 * a1 + n2 * a2 + n3 * a3;   // |n| <= 64, a < 4096: fits in int32
+    t %= L;
+    return t < 0 ? t + L : t;
+}
+
+// ----------------------------------------------------------------------------- launches
+GridInfo make_grid_info(const epwi_ctx *c);
+void launch_phase_tables(epwi_ctx *c);
+void launch_eigs(epwi_ctx *c);
+void scan_exclusive_i64(epwi_ctx *c, const int64_t *in, int64_t *out, int64_t n, int64_t *total);
+double device_reduce_minmax(epwi_ctx *c, const double *x, int64_t n, int64_t stride, int64_t off,
+                            bool want_max);
+void build_window(epwi_ctx *c);
+void sieve_count(epwi_ctx *c);
+void occupation_tables(epwi_ctx *c);
+void run_scatter(epwi_ctx *c);
+double carrier_density(epwi_ctx *c, double T, double mu, int n_valence);
+void conductivity(epwi_ctx *c, double sigma[9]);
+void run_g2(epwi_ctx *c, int64_t npairs, const int32_t *ik, const int32_t *iq, int band_lo,
+            int nsel, double *g2);

@@ -1,0 +1,96 @@
+// Cyclic two-sided Jacobi eigensolver for small complex Hermitian matrices, FP64.
+//
+// For each off-diagonal element a_pq = |a_pq| e^{i phi} the unitary plane rotation
+// U = [[c, s e^{i phi}], [-s e^{-i phi}, c]] (rows/columns p, q) zeroes it: writing
+// A = D B D^dag with D = diag(1, e^{-i phi}) and B the real symmetric 2x2 block
+// [[a_pp, |a_pq|], [|a_pq|, a_qq]], U = D J D^dag with the classical real rotation
+// J = [[c, s], [-s, c]], t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
+// zeta = (a_qq - a_pp) / (2 |a_pq|), c = 1/sqrt(1 + t^2), s = t c (Golub & Van Loan,
+// Matrix Computations, Sec. 8.5), so U^dag A U is diagonal in the (p, q) block.
+// Sweeps repeat until the off-diagonal Frobenius norm is below 1e-15 of the full norm.
+// Eigenvalues are returned ascending with the eigenvector columns of V permuted alike.
+// Accurate for near-degenerate bands and soft modes (each rotation is backward stable).
+#pragma once
+
+template <int NMAX>
+__host__ __device__ inline int jacobi_hermitian(double2 (&A)[NMAX * NMAX], double2 (&V)[NMAX * NMAX],
+                                                int n, double *w) {
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) V[i * n + j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+    int converged = 0;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0, tot = 0;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                const double m2 = A[i * n + j].x * A[i * n + j].x + A[i * n + j].y * A[i * n + j].y;
+                tot += m2;
+                if (i != j) off += m2;
+            }
+        if (off <= 1e-30 * tot || off == 0.0) {
+            converged = 1;
+            break;
+        }
+        for (int p = 0; p < n - 1; ++p) {
+            for (int q = p + 1; q < n; ++q) {
+                const double2 apq = A[p * n + q];
+                const double mag = sqrt(apq.x * apq.x + apq.y * apq.y);
+                if (mag == 0.0) continue;
+                const double app = A[p * n + p].x, aqq = A[q * n + q].x;
+                const double zeta = (aqq - app) / (2.0 * mag);
+                double t;
+                if (fabs(zeta) > 1e150) t = 0.5 / zeta;
+                else t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / sqrt(1.0 + t * t);
+                const double s = t * c;
+                const double2 e = make_double2(apq.x / mag, apq.y / mag);          // e^{i phi}
+                const double2 se = make_double2(s * e.x, s * e.y);                  // s e^{i phi}
+                const double2 sec = make_double2(s * e.x, -s * e.y);                // s e^{-i phi}
+                // columns: A <- A U, V <- V U
+                for (int r = 0; r < n; ++r) {
+                    const double2 ap = A[r * n + p], aq = A[r * n + q];
+                    // A_rp c + A_rq (-s e^{-i phi});  A_rp s e^{i phi} + A_rq c
+                    A[r * n + p] = make_double2(c * ap.x - (sec.x * aq.x - sec.y * aq.y),
+                                                c * ap.y - (sec.x * aq.y + sec.y * aq.x));
+                    A[r * n + q] = make_double2(se.x * ap.x - se.y * ap.y + c * aq.x,
+                                                se.x * ap.y + se.y * ap.x + c * aq.y);
+                    const double2 vp = V[r * n + p], vq = V[r * n + q];
+                    V[r * n + p] = make_double2(c * vp.x - (sec.x * vq.x - sec.y * vq.y),
+                                                c * vp.y - (sec.x * vq.y + sec.y * vq.x));
+                    V[r * n + q] = make_double2(se.x * vp.x - se.y * vp.y + c * vq.x,
+                                                se.x * vp.y + se.y * vp.x + c * vq.y);
+                }
+                // rows: A <- U^dag A
+                for (int col = 0; col < n; ++col) {
+                    const double2 bp = A[p * n + col], bq = A[q * n + col];
+                    // c B_p - s e^{i phi} B_q;  s e^{-i phi} B_p + c B_q
+                    A[p * n + col] = make_double2(c * bp.x - (se.x * bq.x - se.y * bq.y),
+                                                  c * bp.y - (se.x * bq.y + se.y * bq.x));
+                    A[q * n + col] = make_double2(sec.x * bp.x - sec.y * bp.y + c * bq.x,
+                                                  sec.x * bp.y + sec.y * bp.x + c * bq.y);
+                }
+                A[p * n + q] = make_double2(0, 0);
+                A[q * n + p] = make_double2(0, 0);
+                A[p * n + p] = make_double2(app - t * mag, 0);
+                A[q * n + q] = make_double2(aqq + t * mag, 0);
+            }
+        }
+    }
+    for (int i = 0; i < n; ++i) w[i] = A[i * n + i].x;
+    // selection sort, ascending, permuting the eigenvector columns
+    for (int i = 0; i < n - 1; ++i) {
+        int k = i;
+        for (int j = i + 1; j < n; ++j)
+            if (w[j] < w[k]) k = j;
+        if (k != i) {
+            const double tw = w[i];
+            w[i] = w[k];
+            w[k] = tw;
+            for (int r = 0; r < n; ++r) {
+                const double2 tv = V[r * n + i];
+                V[r * n + i] = V[r * n + k];
+                V[r * n + k] = tv;
+            }
+        }
+    }
+    return converged;
+}

@@ -1,0 +1,74 @@
+// Argument blocks of the Re->k and Rp->q kernels and the chunked work set (internal).
+#pragma once
+
+#include <vector>
+
+#include "epwi_internal.cuh"
+
+struct RestageArgs {
+    GridInfo g;
+    int W, Nm, nRe, nRp, nrow;            // nrow = nRp * Nm * W
+    const int *Re;
+    const double2 *gw64;                  // [nRe][nrow][W]
+    const float2 *gw32;
+    const double2 *ph64;
+    const float2 *ph32;
+    const double2 *V64;
+    const float2 *V32;
+    int nkp;                              // k-points of the chunk
+    const int *kpts;                      // [nkp] k index
+    const int64_t *kp_state;              // [nkp+1] global state offsets
+    int64_t s_base;                       // state offset of the chunk
+    const int *win_lo, *win_n;            // per k index
+    int ovr_lo, ovr_nsel;                 // >= 0: fixed band window (g2 mode)
+    double2 *ghat64;                      // FP64 output [state][nrow]
+    void *ghat_raw;                       // split-precision output (layout of the TC kernel)
+    int precision;
+};
+
+struct ScatterArgs {
+    GridInfo g;
+    int W, Nm, nRp, nrow;
+    const int *Rp;
+    const double2 *ph64;
+    const float2 *ph32;
+    const int4 *tiles;                    // {kp_local, pair_begin, pair_end, 0} chunk-local
+    const int *kpts;
+    const int64_t *kp_state;
+    int64_t s_base;
+    const int *win_lo, *win_n;
+    int ovr_lo, ovr_nsel;
+    const int *pairs;                     // chunk pair list: q index
+    const double2 *ghat64;
+    const void *ghat_raw;
+    const double2 *V64;
+    const float2 *V32;
+    const double2 *u64;
+    const float2 *u32;
+    const double *eps;
+    const double *hw;
+    const double *focc, *nocc;
+    double omega_min, eta, ceta;
+    double *tile_part;                    // [tile][kMaxW]
+    double *g2out;                        // g2 mode output or nullptr
+    int64_t g2_base;
+    int precision;
+};
+
+struct WorkSet {
+    int64_t nkp = 0;
+    const int *kpts = nullptr;
+    const int64_t *kp_state = nullptr;
+    const int64_t *kp_pairs = nullptr;
+    std::vector<int64_t> h_kp_state, h_kp_pairs;
+    const int *pairs_dev = nullptr;       // all pairs, or nullptr: sieve fill per chunk
+    int ovr_lo = -1, ovr_nsel = -1;
+};
+
+void process_workset(epwi_ctx *c, const WorkSet &ws, double *g2out);
+void sieve_fill_chunk(epwi_ctx *c, int64_t kp0, int64_t kp1, int *pairs);
+
+// split-precision (tcgen05) path
+size_t tc_state_bytes(const epwi_ctx *c);
+void tc_restage(epwi_ctx *c, const RestageArgs &ra);
+void tc_scatter(epwi_ctx *c, const ScatterArgs &sa, int64_t ntiles);

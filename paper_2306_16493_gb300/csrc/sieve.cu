@@ -1,0 +1,320 @@
+// Preprocessing on the device (Sec. III A): the energy window that selects the effective
+// states {k_eff}, the effective-process sieve (energy-conservation surface), prefix scans
+// and per-chunk pair lists.
+//
+// Sieve: a pair (k, q) is kept when some window band n at k, some band m at k+q, some
+// kept mode nu and a sign s satisfy |(eps_nk + s hbar omega_qnu) - eps_m,k+q| <= c eta,
+// evaluated in FP64 (the same rounding order as the oracle).  An FP32 prefilter
+// |eps_nk - eps_m,k+q| <= max_nu(omega) + c eta + 1e-4 eV rejects most candidates first;
+// it can only pass extra candidates to the exact test, never drop a kept one (FP32
+// rounding of energies below 40 eV is < 3e-6 eV).
+#include "epwi_internal.cuh"
+
+namespace {
+
+constexpr int kScanBlock = 1024;
+constexpr int kScanItems = 4;
+
+__device__ __forceinline__ int64_t warp_incl_scan(int64_t v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Exclusive scan of v across the block (blockDim.x multiple of 32, <= 1024).
+__device__ int64_t block_excl_scan(int64_t v, int64_t *sm, int64_t &total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int64_t inc = warp_incl_scan(v);
+    if (lane == 31) sm[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        int64_t s = lane < nw ? sm[lane] : 0;
+        int64_t si = warp_incl_scan(s);
+        if (lane < nw) sm[lane] = si - s;
+        if (lane == nw - 1) sm[32] = si;
+    }
+    __syncthreads();
+    int64_t r = inc - v + sm[wid];
+    total = sm[32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_scan_blocks(const int64_t *in, int64_t n, int64_t *bsum) {
+    __shared__ int64_t sm[33];
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock * kScanItems + threadIdx.x * kScanItems;
+    int64_t s = 0;
+    for (int i = 0; i < kScanItems; ++i)
+        if (base + i < n) s += in[base + i];
+    int64_t tot;
+    block_excl_scan(s, sm, tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_apply(const int64_t *in, int64_t n, const int64_t *boff, int64_t *out) {
+    __shared__ int64_t sm[33];
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock * kScanItems + threadIdx.x * kScanItems;
+    int64_t v[kScanItems];
+    int64_t s = 0;
+    for (int i = 0; i < kScanItems; ++i) {
+        v[i] = base + i < n ? in[base + i] : 0;
+        s += v[i];
+    }
+    int64_t tot;
+    int64_t run = block_excl_scan(s, sm, tot) + boff[blockIdx.x];
+    for (int i = 0; i < kScanItems; ++i) {
+        if (base + i < n) out[base + i] = run;
+        run += v[i];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) out[n] = run;
+}
+
+// ------------------------------------------------------------------- window / k_eff
+__global__ void k_window(int64_t nk, int W, const double *__restrict__ eps, double emin,
+                         double emax, int *__restrict__ lo, int *__restrict__ cnt,
+                         int64_t *__restrict__ flag) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nk) return;
+    int l = 0;
+    while (l < W && !(eps[k * W + l] >= emin)) ++l;
+    int h = l;
+    while (h < W && eps[k * W + h] <= emax) ++h;
+    lo[k] = l;
+    cnt[k] = h - l;
+    flag[k] = (h > l) ? 1 : 0;
+}
+
+__global__ void k_compact_kpts(int64_t nk, const int64_t *__restrict__ pos,
+                               const int *__restrict__ cnt, int *__restrict__ kpts,
+                               int64_t *__restrict__ nsel) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nk || cnt[k] == 0) return;
+    kpts[pos[k]] = (int)k;
+    nsel[pos[k]] = cnt[k];
+}
+
+__global__ void k_states(int64_t nkp, const int *__restrict__ kpts, const int *__restrict__ lo,
+                         const int64_t *__restrict__ soff, int *__restrict__ st_k,
+                         int *__restrict__ st_n) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nkp) return;
+    const int k = kpts[p];
+    for (int64_t s = soff[p]; s < soff[p + 1]; ++s) {
+        st_k[s] = k;
+        st_n[s] = lo[k] + (int)(s - soff[p]);
+    }
+}
+
+// ------------------------------------------------------------------- sieve
+struct SieveArgs {
+    GridInfo g;
+    int W, Nm;
+    const double *eps;
+    const float *eps32;
+    const double *hw;
+    const float *hwmax32;
+    double omega_min, ceta;
+    float lim_extra;   // c eta + prefilter margin
+};
+
+__device__ __forceinline__ bool pair_valid(const SieveArgs &a, int64_t ik, int nsel,
+                                           const double *en, const float *en32, int64_t iq) {
+    const float hm = a.hwmax32[iq];
+    if (hm < 0.f) return false;
+    const float lim = hm + a.lim_extra;
+    const int64_t ikq = kplusq(a.g, ik, iq);
+    for (int m = 0; m < a.W; ++m) {
+        const float em32 = a.eps32[ikq * a.W + m];
+        bool near = false;
+        for (int n = 0; n < nsel; ++n) near |= fabsf(en32[n] - em32) <= lim;
+        if (!near) continue;
+        const double em = a.eps[ikq * a.W + m];
+        for (int nu = 0; nu < a.Nm; ++nu) {
+            const double w = a.hw[iq * a.Nm + nu];
+            if (!(w >= a.omega_min)) continue;
+            for (int n = 0; n < nsel; ++n) {
+                const double x1 = (en[n] + w) - em;
+                const double x2 = (en[n] - w) - em;
+                if (fabs(x1) <= a.ceta || fabs(x2) <= a.ceta) return true;
+            }
+        }
+    }
+    return false;
+}
+
+__device__ __forceinline__ void load_window(const SieveArgs &a, int ik, int lo, int nsel,
+                                            double *en, float *en32) {
+    if (threadIdx.x < nsel) {
+        en[threadIdx.x] = a.eps[(int64_t)ik * a.W + lo + threadIdx.x];
+        en32[threadIdx.x] = a.eps32[(int64_t)ik * a.W + lo + threadIdx.x];
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) k_sieve_count(SieveArgs a, int64_t nkp,
+                                                     const int *__restrict__ kpts,
+                                                     const int *__restrict__ lo,
+                                                     const int *__restrict__ cnt,
+                                                     int64_t *__restrict__ counts) {
+    __shared__ double en[epc::kMaxW];
+    __shared__ float en32[epc::kMaxW];
+    __shared__ int64_t sm[33];
+    const int ik = kpts[blockIdx.x];
+    const int nsel = cnt[ik];
+    load_window(a, ik, lo[ik], nsel, en, en32);
+    const int64_t nq = (int64_t)a.g.n1 * a.g.n2 * a.g.n3;
+    int64_t c = 0;
+    for (int64_t iq = threadIdx.x; iq < nq; iq += blockDim.x) c += pair_valid(a, ik, nsel, en, en32, iq);
+    int64_t tot;
+    block_excl_scan(c, sm, tot);
+    if (threadIdx.x == 0) counts[blockIdx.x] = tot;
+}
+
+// Writes the kept q of k-points kp0 + blockIdx.x in ascending order.
+__global__ void __launch_bounds__(256) k_sieve_fill(SieveArgs a, int64_t kp0,
+                                                    const int *__restrict__ kpts,
+                                                    const int *__restrict__ lo,
+                                                    const int *__restrict__ cnt,
+                                                    const int64_t *__restrict__ kp_pairs,
+                                                    int *__restrict__ pairs) {
+    __shared__ double en[epc::kMaxW];
+    __shared__ float en32[epc::kMaxW];
+    __shared__ int64_t sm[33];
+    const int64_t kp = kp0 + blockIdx.x;
+    const int ik = kpts[kp];
+    const int nsel = cnt[ik];
+    load_window(a, ik, lo[ik], nsel, en, en32);
+    const int64_t nq = (int64_t)a.g.n1 * a.g.n2 * a.g.n3;
+    int64_t base = kp_pairs[kp] - kp_pairs[kp0];
+    const int64_t end = kp_pairs[kp + 1] - kp_pairs[kp0];
+    for (int64_t q0 = 0; q0 < nq; q0 += blockDim.x) {
+        const int64_t iq = q0 + threadIdx.x;
+        const int64_t v = (iq < nq) ? (int64_t)pair_valid(a, ik, nsel, en, en32, iq) : 0;
+        int64_t tot;
+        const int64_t off = block_excl_scan(v, sm, tot);
+        if (v && base + off < end) pairs[base + off] = (int)iq;
+        base += tot;
+    }
+}
+
+SieveArgs make_sieve_args(epwi_ctx *c) {
+    SieveArgs a;
+    a.g = make_grid_info(c);
+    a.W = c->nw;
+    a.Nm = c->nm;
+    a.eps = c->eps.as<double>();
+    a.eps32 = c->eps32.as<float>();
+    a.hw = c->hw.as<double>();
+    a.hwmax32 = c->hwmax32.as<float>();
+    a.omega_min = c->opt.omega_min_eV;
+    a.ceta = c->opt.sieve_c * c->eta;
+    a.lim_extra = (float)(a.ceta + 1e-4);
+    return a;
+}
+
+}  // namespace
+
+void scan_exclusive_i64(epwi_ctx *c, const int64_t *in, int64_t *out, int64_t n, int64_t *total) {
+    // out has n + 1 entries; out[n] = sum.  Recursive over block sums.
+    const int64_t per = (int64_t)kScanBlock * kScanItems;
+    const int64_t nb = (n + per - 1) / per;
+    if (n == 0) {
+        EPWI_CUDA(cudaMemsetAsync(out, 0, sizeof(int64_t), c->stream));
+        if (total) *total = 0;
+        return;
+    }
+    DevBuf bs, bo;
+    bs.ensure(sizeof(int64_t) * (nb + 1));
+    bo.ensure(sizeof(int64_t) * (nb + 1));
+    try {
+        k_scan_blocks<<<(unsigned)nb, kScanBlock, 0, c->stream>>>(in, n, bs.as<int64_t>());
+        EPWI_CHECK_LAUNCH();
+        if (nb > 1) {
+            scan_exclusive_i64(c, bs.as<int64_t>(), bo.as<int64_t>(), nb, nullptr);
+        } else {
+            EPWI_CUDA(cudaMemsetAsync(bo.p, 0, sizeof(int64_t), c->stream));
+        }
+        k_scan_apply<<<(unsigned)nb, kScanBlock, 0, c->stream>>>(in, n, bo.as<int64_t>(), out);
+        EPWI_CHECK_LAUNCH();
+        if (total) {
+            EPWI_CUDA(cudaMemcpyAsync(total, out + n, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                                      c->stream));
+            EPWI_CUDA(cudaStreamSynchronize(c->stream));
+        } else {
+            EPWI_CUDA(cudaStreamSynchronize(c->stream));   // bs/bo are freed on return
+        }
+    } catch (...) {
+        bs.release();
+        bo.release();
+        throw;
+    }
+    bs.release();
+    bo.release();
+}
+
+void build_window(epwi_ctx *c) {
+    const int64_t nk = c->nk;
+    c->win_lo.ensure(sizeof(int) * nk);
+    c->win_n.ensure(sizeof(int) * nk);
+    c->counts.ensure(sizeof(int64_t) * (nk + 1));
+    c->scan_tmp.ensure(sizeof(int64_t) * (nk + 1));
+    const unsigned nb = (unsigned)((nk + 255) / 256);
+    k_window<<<nb, 256, 0, c->stream>>>(nk, c->nw, c->eps.as<double>(), c->emin, c->emax,
+                                       c->win_lo.as<int>(), c->win_n.as<int>(),
+                                       c->counts.as<int64_t>());
+    EPWI_CHECK_LAUNCH();
+    int64_t nkp = 0;
+    scan_exclusive_i64(c, c->counts.as<int64_t>(), c->scan_tmp.as<int64_t>(), nk, &nkp);
+    c->nkp = nkp;
+    c->kpts.ensure(sizeof(int) * (nkp + 1));
+    c->kp_state.ensure(sizeof(int64_t) * (nkp + 1));
+    // reuse counts as the per-kp band count
+    k_compact_kpts<<<nb, 256, 0, c->stream>>>(nk, c->scan_tmp.as<int64_t>(), c->win_n.as<int>(),
+                                             c->kpts.as<int>(), c->counts.as<int64_t>());
+    EPWI_CHECK_LAUNCH();
+    int64_t nst = 0;
+    scan_exclusive_i64(c, c->counts.as<int64_t>(), c->kp_state.as<int64_t>(), nkp, &nst);
+    c->nstates = nst;
+    c->st_k.ensure(sizeof(int) * (nst + 1));
+    c->st_n.ensure(sizeof(int) * (nst + 1));
+    c->inv_tau.ensure(sizeof(double) * (nst + 1));
+    if (nkp > 0) {
+        k_states<<<(unsigned)((nkp + 255) / 256), 256, 0, c->stream>>>(
+            nkp, c->kpts.as<int>(), c->win_lo.as<int>(), c->kp_state.as<int64_t>(),
+            c->st_k.as<int>(), c->st_n.as<int>());
+        EPWI_CHECK_LAUNCH();
+    }
+}
+
+void sieve_count(epwi_ctx *c) {
+    const int64_t nkp = c->nkp;
+    c->counts.ensure(sizeof(int64_t) * (nkp + 1));
+    c->kp_pairs.ensure(sizeof(int64_t) * (nkp + 1));
+    SieveArgs a = make_sieve_args(c);
+    if (nkp > 0) {
+        k_sieve_count<<<(unsigned)nkp, 256, 0, c->stream>>>(a, nkp, c->kpts.as<int>(),
+                                                           c->win_lo.as<int>(), c->win_n.as<int>(),
+                                                           c->counts.as<int64_t>());
+        EPWI_CHECK_LAUNCH();
+    }
+    int64_t np = 0;
+    scan_exclusive_i64(c, c->counts.as<int64_t>(), c->kp_pairs.as<int64_t>(), nkp, &np);
+    c->npairs = np;
+    c->h_kp_pairs.resize(nkp + 1);
+    EPWI_CUDA(cudaMemcpyAsync(c->h_kp_pairs.data(), c->kp_pairs.p, sizeof(int64_t) * (nkp + 1),
+                              cudaMemcpyDeviceToHost, c->stream));
+    EPWI_CUDA(cudaStreamSynchronize(c->stream));
+}
+
+void sieve_fill_chunk(epwi_ctx *c, int64_t kp0, int64_t kp1, int *pairs) {
+    if (kp1 <= kp0) return;
+    SieveArgs a = make_sieve_args(c);
+    k_sieve_fill<<<(unsigned)(kp1 - kp0), 256, 0, c->stream>>>(
+        a, kp0, c->kpts.as<int>(), c->win_lo.as<int>(), c->win_n.as<int>(),
+        c->kp_pairs.as<int64_t>(), pairs);
+    EPWI_CHECK_LAUNCH();
+}

@@ -1,0 +1,327 @@
+"""Python binding of the C ABI in include/epwi.h (ctypes; argument marshalling only).
+
+Every step of the path runs in libepwi.so's CUDA kernels; this module converts numpy
+arrays to pointers and status codes to exceptions.  It raises at import time if the
+compiled library is missing: there is no CPU fallback.  The functions keep the C names
+(``epwi_create``, ``epwi_setup``, ...); ``Context`` bundles them for convenience.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libepwi.so")
+
+EPWI_FP64, EPWI_TF32X3, EPWI_BF16X3, EPWI_FP16X3 = 0, 1, 2, 3
+PRECISIONS = {"fp64": EPWI_FP64, "tf32x3": EPWI_TF32X3, "bf16x3": EPWI_BF16X3,
+              "fp16x3": EPWI_FP16X3}
+STATUS = {0: "EPWI_OK", 1: "EPWI_EINVAL", 2: "EPWI_ENOMEM", 3: "EPWI_ECUDA", 4: "EPWI_ESTATE",
+          5: "EPWI_ETIMEOUT", 6: "EPWI_ENUMERIC", 7: "EPWI_ETOOSMALL", 8: "EPWI_EUNSUPPORTED"}
+
+
+class EpwiError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class epwi_c64(C.Structure):
+    _fields_ = [("re", C.c_double), ("im", C.c_double)]
+
+
+class epwi_system(C.Structure):
+    _fields_ = [("lattice", C.c_double * 9), ("nat", C.c_int32), ("mass", C.c_void_p),
+                ("nw", C.c_int32), ("nRe", C.c_int32), ("Re", C.c_void_p), ("we", C.c_void_p),
+                ("H", C.c_void_p), ("nRp", C.c_int32), ("Rp", C.c_void_p), ("wp", C.c_void_p),
+                ("Phi", C.c_void_p), ("g", C.c_void_p)]
+
+
+class epwi_options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("sieve_c", C.c_double), ("omega_min_eV", C.c_double),
+                ("device", C.c_int32), ("cuda_stream", C.c_void_p), ("kpoint_chunk", C.c_int32)]
+
+
+class epwi_stats(C.Structure):
+    _fields_ = [("n_kpoints", C.c_int64), ("n_states", C.c_int64), ("n_pairs", C.c_int64),
+                ("n_tiles", C.c_int64), ("n_chunks", C.c_int64), ("ms_eigs", C.c_double),
+                ("ms_sieve", C.c_double), ("ms_restage", C.c_double), ("ms_scatter", C.c_double),
+                ("ms_reduce", C.c_double), ("restage_bytes", C.c_int64),
+                ("scatter_flops", C.c_double), ("precision", C.c_int32)]
+
+
+def _load() -> C.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -m paper_2306_16493_gb300.build` (needs nvcc)")
+    lib = C.CDLL(LIB_PATH)
+    P, I32, I64, D, V = C.c_void_p, C.c_int32, C.c_int64, C.c_double, None
+    sig = {
+        "epwi_default_options": (V, [P]),
+        "epwi_create": (I32, [P, P]),
+        "epwi_destroy": (V, [P]),
+        "epwi_last_error": (C.c_char_p, [P]),
+        "epwi_set_precision": (I32, [P, I32]),
+        "epwi_set_stream": (I32, [P, P]),
+        "epwi_setup": (I32, [P, P]),
+        "epwi_eigs": (I32, [P, P, P]),
+        "epwi_band_range": (I32, [P, P, P]),
+        "epwi_band_edges": (I32, [P, I32, P, P]),
+        "epwi_find_mu": (I32, [P, D, D, I32, P]),
+        "epwi_carrier_density": (I32, [P, D, D, I32, P]),
+        "epwi_scatter_rates": (I32, [P, D, D, D, D, D, P, P]),
+        "epwi_get_rates": (I32, [P, I64, P, P, P]),
+        "epwi_conductivity": (I32, [P, P]),
+        "epwi_mobility": (I32, [P, D, P]),
+        "epwi_get_bands": (I32, [P, P, P, P]),
+        "epwi_get_phonons": (I32, [P, P, P]),
+        "epwi_get_sieve": (I32, [P, I64, P, P]),
+        "epwi_g2": (I32, [P, I64, P, P, I32, I32, P]),
+        "epwi_get_stats": (I32, [P, P]),
+        "epwi_kernel_launches": (I64, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _check(ctx, st: int):
+    if st != 0:
+        msg = _lib.epwi_last_error(ctx).decode() if ctx else ""
+        raise EpwiError(st, msg)
+
+
+# ------------------------------------------------------------------ C-named functions
+def epwi_default_options() -> epwi_options:
+    o = epwi_options()
+    _lib.epwi_default_options(C.byref(o))
+    return o
+
+
+def epwi_create(options: epwi_options | None = None):
+    h = C.c_void_p()
+    st = _lib.epwi_create(C.byref(h), C.byref(options) if options is not None else None)
+    if st != 0:
+        raise EpwiError(st, "epwi_create failed")
+    return h
+
+
+def epwi_destroy(ctx):
+    _lib.epwi_destroy(ctx)
+
+
+def epwi_set_precision(ctx, precision: int):
+    _check(ctx, _lib.epwi_set_precision(ctx, int(precision)))
+
+
+def epwi_set_stream(ctx, stream: int | None):
+    _check(ctx, _lib.epwi_set_stream(ctx, C.c_void_p(stream or 0)))
+
+
+def epwi_setup(ctx, sysm):
+    """sysm: an object with the fields of synth.System (numpy arrays, unweighted)."""
+    keep = dict(
+        mass=np.ascontiguousarray(sysm.mass, np.float64),
+        Re=np.ascontiguousarray(sysm.Re, np.int32), we=np.ascontiguousarray(sysm.we, np.float64),
+        H=np.ascontiguousarray(sysm.H, np.complex128),
+        Rp=np.ascontiguousarray(sysm.Rp, np.int32), wp=np.ascontiguousarray(sysm.wp, np.float64),
+        Phi=np.ascontiguousarray(sysm.Phi, np.float64),
+        g=np.ascontiguousarray(sysm.g, np.complex128))
+    s = epwi_system()
+    s.lattice[:] = np.ascontiguousarray(sysm.lattice, np.float64).ravel().tolist()
+    s.nat = len(keep["mass"])
+    s.nw = int(sysm.nw)
+    s.nRe = len(keep["Re"])
+    s.nRp = len(keep["Rp"])
+    for k in ("mass", "Re", "we", "H", "Rp", "wp", "Phi", "g"):
+        setattr(s, k, _ptr(keep[k]))
+    _check(ctx, _lib.epwi_setup(ctx, C.byref(s)))
+
+
+def epwi_eigs(ctx, kgrid, qgrid=None):
+    k = np.ascontiguousarray(kgrid, np.int32)
+    q = np.ascontiguousarray(kgrid if qgrid is None else qgrid, np.int32)
+    _check(ctx, _lib.epwi_eigs(ctx, _ptr(k), _ptr(q)))
+
+
+def epwi_band_range(ctx):
+    lo, hi = C.c_double(), C.c_double()
+    _check(ctx, _lib.epwi_band_range(ctx, C.byref(lo), C.byref(hi)))
+    return lo.value, hi.value
+
+
+def epwi_band_edges(ctx, n_valence: int):
+    v, c = C.c_double(), C.c_double()
+    _check(ctx, _lib.epwi_band_edges(ctx, int(n_valence), C.byref(v), C.byref(c)))
+    return v.value, c.value
+
+
+def epwi_find_mu(ctx, T, n_cm3, n_valence):
+    m = C.c_double()
+    _check(ctx, _lib.epwi_find_mu(ctx, float(T), float(n_cm3), int(n_valence), C.byref(m)))
+    return m.value
+
+
+def epwi_carrier_density(ctx, T, mu, n_valence):
+    n = C.c_double()
+    _check(ctx, _lib.epwi_carrier_density(ctx, float(T), float(mu), int(n_valence), C.byref(n)))
+    return n.value
+
+
+def epwi_scatter_rates(ctx, T, mu, smear, emin, emax):
+    ns, npair = C.c_int64(), C.c_int64()
+    _check(ctx, _lib.epwi_scatter_rates(ctx, float(T), float(mu), float(smear), float(emin),
+                                        float(emax), C.byref(ns), C.byref(npair)))
+    return ns.value, npair.value
+
+
+def epwi_get_rates(ctx, n_states: int):
+    k = np.empty(n_states, np.int32)
+    b = np.empty(n_states, np.int32)
+    r = np.empty(n_states, np.float64)
+    _check(ctx, _lib.epwi_get_rates(ctx, n_states, _ptr(k), _ptr(b), _ptr(r)))
+    return k, b, r
+
+
+def epwi_conductivity(ctx):
+    s = np.empty(9, np.float64)
+    _check(ctx, _lib.epwi_conductivity(ctx, _ptr(s)))
+    return s.reshape(3, 3)
+
+
+def epwi_mobility(ctx, n_cm3):
+    m = np.empty(9, np.float64)
+    _check(ctx, _lib.epwi_mobility(ctx, float(n_cm3), _ptr(m)))
+    return m.reshape(3, 3)
+
+
+def epwi_get_bands(ctx, nk: int, nw: int):
+    e = np.empty((nk, nw))
+    V = np.empty((nk, nw, nw), np.complex128)
+    v = np.empty((nk, nw, 3))
+    _check(ctx, _lib.epwi_get_bands(ctx, _ptr(e), _ptr(V), _ptr(v)))
+    return e, V, v
+
+
+def epwi_get_phonons(ctx, nq: int, nm: int):
+    w = np.empty((nq, nm))
+    u = np.empty((nq, nm, nm), np.complex128)
+    _check(ctx, _lib.epwi_get_phonons(ctx, _ptr(w), _ptr(u)))
+    return w, u
+
+
+def epwi_get_sieve(ctx, n_kpoints: int):
+    k = np.empty(n_kpoints, np.int32)
+    c = np.empty(n_kpoints, np.int64)
+    _check(ctx, _lib.epwi_get_sieve(ctx, n_kpoints, _ptr(k), _ptr(c)))
+    return k, c
+
+
+def epwi_g2(ctx, ik, iq, band_lo: int, nsel: int, nm: int, nw: int):
+    ik = np.ascontiguousarray(ik, np.int32)
+    iq = np.ascontiguousarray(iq, np.int32)
+    out = np.empty((len(ik), nsel, nm, nw))
+    _check(ctx, _lib.epwi_g2(ctx, len(ik), _ptr(ik), _ptr(iq), int(band_lo), int(nsel), _ptr(out)))
+    return out
+
+
+def epwi_kernel_launches() -> int:
+    return int(_lib.epwi_kernel_launches())
+
+
+def epwi_get_stats(ctx) -> dict:
+    s = epwi_stats()
+    _check(ctx, _lib.epwi_get_stats(ctx, C.byref(s)))
+    return {name: getattr(s, name) for name, _ in epwi_stats._fields_}
+
+
+# ------------------------------------------------------------------ convenience wrapper
+class Context:
+    """One library context (device memory, stream, last results)."""
+
+    def __init__(self, precision="fp64", device=0, stream=None, sieve_c=6.0, omega_min=1e-4,
+                 kpoint_chunk=0):
+        o = epwi_default_options()
+        o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        o.device = device
+        o.cuda_stream = stream or 0
+        o.sieve_c = sieve_c
+        o.omega_min_eV = omega_min
+        o.kpoint_chunk = kpoint_chunk
+        self.h = epwi_create(o)
+        self.nk = self.nw = self.nm = 0
+        self.n_states = 0
+
+    def close(self):
+        if self.h:
+            epwi_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_precision(self, p):
+        epwi_set_precision(self.h, PRECISIONS[p] if isinstance(p, str) else p)
+
+    def setup(self, sysm):
+        epwi_setup(self.h, sysm)
+        self.nw, self.nm = int(sysm.nw), 3 * len(sysm.mass)
+
+    def eigs(self, grid):
+        grid = [grid] * 3 if np.isscalar(grid) else list(grid)
+        epwi_eigs(self.h, grid, grid)
+        self.nk = int(np.prod(grid))
+
+    def band_range(self):
+        return epwi_band_range(self.h)
+
+    def band_edges(self, nv):
+        return epwi_band_edges(self.h, nv)
+
+    def find_mu(self, T, n_cm3, nv):
+        return epwi_find_mu(self.h, T, n_cm3, nv)
+
+    def carrier_density(self, T, mu, nv):
+        return epwi_carrier_density(self.h, T, mu, nv)
+
+    def scatter_rates(self, T, mu, smear, emin, emax):
+        self.n_states, n_pairs = epwi_scatter_rates(self.h, T, mu, smear, emin, emax)
+        return self.n_states, n_pairs
+
+    def rates(self):
+        return epwi_get_rates(self.h, self.n_states)
+
+    def conductivity(self):
+        return epwi_conductivity(self.h)
+
+    def mobility(self, n_cm3):
+        return epwi_mobility(self.h, n_cm3)
+
+    def bands(self):
+        return epwi_get_bands(self.h, self.nk, self.nw)
+
+    def phonons(self):
+        return epwi_get_phonons(self.h, self.nk, self.nm)
+
+    def sieve(self):
+        st = self.stats()
+        return epwi_get_sieve(self.h, st["n_kpoints"])
+
+    def g2(self, ik, iq, band_lo, nsel):
+        return epwi_g2(self.h, ik, iq, band_lo, nsel, self.nm, self.nw)
+
+    def stats(self):
+        return epwi_get_stats(self.h)
