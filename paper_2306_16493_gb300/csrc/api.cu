@@ -246,6 +246,34 @@ epwi_status epwi_setup(epwi_ctx *c, const epwi_system *s) {
                     g32[base + e] = make_float2((float)(w * v.re), (float)(w * v.im));
                 }
             }
+        // Rp as a full cube [-r, r]^3 with n3 fastest enables the incremental phase index
+        // of the tensor-core kernel.
+        c->rp_cube_r = -1;
+        for (int rr = 0; rr <= 64; ++rr) {
+            const int Dd = 2 * rr + 1;
+            if ((long long)Dd * Dd * Dd != nRp) continue;
+            bool ok = true;
+            for (int k = 0; k < nRp && ok; ++k)
+                ok = s->Rp[3 * k] == k / (Dd * Dd) - rr && s->Rp[3 * k + 1] == (k / Dd) % Dd - rr &&
+                     s->Rp[3 * k + 2] == k % Dd - rr;
+            if (ok) c->rp_cube_r = rr;
+            break;
+        }
+        // |ghat(k)[rp][mu][i][n]| <= sum_Re sum_j |w g| (|V_jn| <= 1): scale fp16 operands so
+        // that this bound maps to 2^14 (no overflow, full mantissa for the split).
+        double gbound = 0;
+        for (int rp = 0; rp < nRp; ++rp)
+            for (int mi = 0; mi < Nm * W; ++mi) {
+                double sum = 0;
+                for (int re = 0; re < nRe; ++re)
+                    for (int j = 0; j < W; ++j) {
+                        const double2 v = g64[(size_t)re * per_re + ((size_t)rp * Nm * W + mi) * W + j];
+                        sum += std::hypot(v.x, v.y);
+                    }
+                gbound = std::max(gbound, sum);
+            }
+        c->tc_scale_exp = gbound > 0 ? 14 - (int)std::ceil(std::log2(gbound)) : 0;
+        c->tc_ptab_key = -1;
         upload(c->Re, s->Re, 3 * (size_t)nRe, c->stream);
         upload(c->Rp, s->Rp, 3 * (size_t)nRp, c->stream);
         upload(c->Rcart, Rc.data(), Rc.size(), c->stream);
@@ -272,6 +300,7 @@ epwi_status epwi_eigs(epwi_ctx *c, const int32_t kgrid[3], const int32_t qgrid[3
         const int64_t nk = (int64_t)kgrid[0] * kgrid[1] * kgrid[2];
         EPWI_REQUIRE(nk < (int64_t(1) << 31), EPWI_EUNSUPPORTED, "grid larger than 2^31 points");
         c->have_eigs = c->have_rates = c->have_sigma = false;
+        c->tc_ptab_key = -1;
         for (int a = 0; a < 3; ++a) c->ng[a] = kgrid[a];
         c->nk = nk;
         c->L = (int)L;
@@ -500,6 +529,15 @@ epwi_status epwi_g2(epwi_ctx *c, int64_t npairs, const int32_t *ik, const int32_
             const size_t nout = (size_t)npairs * nsel * c->nm * c->nw;
             dout.ensure(sizeof(double) * nout);
             if (c->eta <= 0) c->eta = 1.0;   // unused by g2 mode, kept finite
+            if (c->opt.precision != EPWI_FP64) {
+                // the tensor-core epilogue reads the FP32 mode-energy table; build the per-call
+                // tables if no scatter_rates call has (occupations are unused in g2 mode)
+                if (!(c->T > 0)) {
+                    c->T = 300.0;
+                    c->mu = 0.0;
+                }
+                occupation_tables(c);
+            }
             WorkSet ws;
             ws.nkp = nkp;
             ws.kpts = dk.as<int>();

@@ -140,6 +140,16 @@ struct epwi_ctx {
     DevBuf red_tmp;                // reduction workspace
     DevBuf counts;                 // int64 per kp
 
+    // split-precision (tcgen05) path
+    int rp_cube_r = -1;            // Rp is the full cube [-r, r]^3 in n3-fastest order, else -1
+    int tc_scale_exp = 0;          // fp16 operands: B scaled by 2^e (bound of |ghat| -> 2^14)
+    int tc_ptab_key = -1;
+    int tc_blocks_per_sm = 0;
+    DevBuf tc_ptab;                // pre-split phase table
+    DevBuf tc_erel, tc_f32;        // float [Nk][W]: eps - mu, Fermi-Dirac
+    DevBuf tc_n32, tc_hw32;        // float [Nq][Nm]: Bose-Einstein, mode energy (-1 dropped)
+    DevBuf tc_err;                 // int: timed-out waits in the tensor-core kernel
+
     // conductivity
     bool have_sigma = false;
     double sigma[9] = {0};
@@ -149,7 +159,8 @@ struct epwi_ctx {
                          &eps, &eps32, &V, &V32, &vel, &hw, &hwmax32, &u, &u32, &eig_flag,
                          &kpts, &win_lo, &win_n, &kp_state, &kp_pairs, &inv_tau, &st_k,
                          &st_n, &focc, &nocc, &pairs, &ghat, &tiles, &tile_part, &kp_tile,
-                         &scan_tmp, &red_tmp, &counts};
+                         &scan_tmp, &red_tmp, &counts, &tc_ptab, &tc_erel, &tc_f32,
+                         &tc_n32, &tc_hw32, &tc_err};
         for (DevBuf *b : all) b->release();
     }
 };

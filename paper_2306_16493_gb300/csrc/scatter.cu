@@ -350,6 +350,13 @@ void process_workset(epwi_ctx *c, const WorkSet &ws, double *g2out) {
         sa.g2out = g2out;
         sa.g2_base = p_base;
         sa.precision = c->opt.precision;
+        sa.nsel_max = 1;
+        if (ws.ovr_nsel >= 0) {
+            sa.nsel_max = ws.ovr_nsel;
+        } else {
+            for (int64_t p = kp0; p < kp1; ++p)
+                sa.nsel_max = std::max<int64_t>(sa.nsel_max, ws.h_kp_state[p + 1] - ws.h_kp_state[p]);
+        }
         cudaEventRecord(ev_sc.e[0], c->stream);
         if (tc) tc_scatter(c, sa, nt);
         else fp64_scatter(sa, nt, c->stream);
@@ -366,6 +373,9 @@ void process_workset(epwi_ctx *c, const WorkSet &ws, double *g2out) {
         }
         cudaEventRecord(ev_red.e[1], c->stream);
         EPWI_CUDA(cudaStreamSynchronize(c->stream));
+        if (tc && nt > 0)
+            EPWI_REQUIRE(tc_check_error(c) == 0, EPWI_ETIMEOUT,
+                         "tensor-core kernel: a bounded mbarrier wait timed out");
         c->stats.ms_sieve += ev_fill.ms();
         c->stats.ms_restage += ev_re.ms();
         c->stats.ms_scatter += ev_sc.ms();

@@ -53,6 +53,7 @@ struct ScatterArgs {
     double *g2out;                        // g2 mode output or nullptr
     int64_t g2_base;
     int precision;
+    int nsel_max;                         // largest band window of the chunk
 };
 
 struct WorkSet {
@@ -72,3 +73,5 @@ void sieve_fill_chunk(epwi_ctx *c, int64_t kp0, int64_t kp1, int *pairs);
 size_t tc_state_bytes(const epwi_ctx *c);
 void tc_restage(epwi_ctx *c, const RestageArgs &ra);
 void tc_scatter(epwi_ctx *c, const ScatterArgs &sa, int64_t ntiles);
+void tc_tables(epwi_ctx *c);
+int tc_check_error(epwi_ctx *c);

@@ -3,6 +3,7 @@
 // (Sec. III A), band extrema.  All reductions are two-pass with a fixed block count and a
 // fixed tree order, so results are bitwise reproducible for a given input size.
 #include "epwi_internal.cuh"
+#include "scatter.cuh"
 
 namespace {
 
@@ -159,6 +160,7 @@ void occupation_tables(epwi_ctx *c) {
         nk, c->nw, c->nm, c->eps.as<double>(), c->hw.as<double>(), c->mu, epc::kKbEVK * c->T,
         c->opt.omega_min_eV, c->focc.as<double>(), c->nocc.as<double>());
     EPWI_CHECK_LAUNCH();
+    if (c->opt.precision != EPWI_FP64) tc_tables(c);
 }
 
 double device_reduce_minmax(epwi_ctx *c, const double *x, int64_t n, int64_t stride, int64_t off,
