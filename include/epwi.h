@@ -101,6 +101,12 @@ typedef struct {
     int64_t restage_bytes;      /* algorithmic bytes of the Re->k stage (g read once per chunk) */
     double scatter_flops;       /* algorithmic flops of the Rp->q GEMM (one pass, no padding) */
     int32_t precision;
+    int32_t sm_count;           /* multiprocessors of the device */
+    int64_t tc_grid;            /* CTAs of the last tensor-core launch (0 in FP64 mode) */
+    int32_t tc_ctas_per_sm;     /* resident CTAs per SM of that launch */
+    int32_t tc_regs;            /* registers per thread of that kernel */
+    int64_t tc_smem;            /* dynamic shared memory per CTA (bytes) */
+    int64_t tc_smem_avail2;     /* dynamic shared memory available to one CTA on an SM */
 } epwi_stats;
 
 /* Fills *opt with the defaults listed above. */

@@ -320,6 +320,11 @@ epwi_status epwi_eigs(epwi_ctx *c, const int32_t kgrid[3], const int32_t qgrid[3
         EPWI_REQUIRE(flag[0] == 0 && flag[1] == 0, EPWI_ENUMERIC,
                      "Jacobi did not converge on " + std::to_string(flag[0]) + " H(k) and " +
                          std::to_string(flag[1]) + " D(q) matrices");
+        {
+            const double lo = device_reduce_minmax(c, c->eps.as<double>(), nk * c->nw, 1, 0, false);
+            const double hi = device_reduce_minmax(c, c->eps.as<double>(), nk * c->nw, 1, 0, true);
+            c->eabs_max = std::max(std::fabs(lo), std::fabs(hi));
+        }
         c->have_eigs = true;
     });
 }
@@ -386,6 +391,7 @@ epwi_status epwi_scatter_rates(epwi_ctx *c, double T, double mu, double eta, dou
         std::memset(&c->stats, 0, sizeof(c->stats));
         c->stats.precision = c->opt.precision;
         c->stats.ms_eigs = c->ms_eigs;
+        EPWI_CUDA(cudaDeviceGetAttribute(&c->stats.sm_count, cudaDevAttrMultiProcessorCount, c->device));
         cudaEvent_t e0, e1;
         EPWI_CUDA(cudaEventCreate(&e0));
         EPWI_CUDA(cudaEventCreate(&e1));

@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(128) k_eig_ph(GridInfo g, int64_t nq, int Nm, 
                                                 const double *__restrict__ mode_mass,
                                                 const double2 *__restrict__ ph, double omega_min,
                                                 double *__restrict__ hw, float *__restrict__ hwmax32,
+                                                float *__restrict__ hw32,
                                                 double2 *__restrict__ uout,
                                                 float2 *__restrict__ u32, int *__restrict__ flag) {
     int64_t iq = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -113,6 +114,7 @@ __global__ void __launch_bounds__(128) k_eig_ph(GridInfo g, int64_t nq, int Nm, 
         const double w = (l >= 0 ? 1.0 : -1.0) * sqrt(fabs(l) * epc::kHbar2AmuA2);
         hw[iq * Nm + nu] = w;
         const bool keep = w >= omega_min;
+        hw32[iq * Nm + nu] = keep ? (float)w : -1.0f;
         if (keep) wmax = fmaxf(wmax, (float)w);
         for (int m = 0; m < Nm; ++m) {
             double amp = keep ? sqrt(epc::kHbar2AmuA2 / (2.0 * mode_mass[m] * w)) : 0.0;
@@ -156,6 +158,7 @@ void launch_eigs(epwi_ctx *c) {
     c->vel.ensure(sizeof(double) * nk * W * 3);
     c->hw.ensure(sizeof(double) * nk * Nm);
     c->hwmax32.ensure(sizeof(float) * nk);
+    c->hw32.ensure(sizeof(float) * nk * Nm);
     c->u.ensure(sizeof(double2) * nk * Nm * Nm);
     c->u32.ensure(sizeof(float2) * nk * Nm * Nm);
     c->eig_flag.ensure(sizeof(int) * 2);
@@ -177,6 +180,7 @@ void launch_eigs(epwi_ctx *c) {
 #define PH_ARGS                                                                             \
     g, nk, Nm, c->nRp, c->Rp.as<int>(), c->Phiw.as<double>(), c->mode_mass.as<double>(),     \
         c->ph64.as<double2>(), c->opt.omega_min_eV, c->hw.as<double>(), c->hwmax32.as<float>(), \
+        c->hw32.as<float>(),                                                                   \
         c->u.as<double2>(), c->u32.as<float2>(), c->eig_flag.as<int>() + 1
     if (Nm <= 3) k_eig_ph<3><<<nb, bs, 0, c->stream>>>(PH_ARGS);
     else if (Nm <= 6) k_eig_ph<6><<<nb, bs, 0, c->stream>>>(PH_ARGS);

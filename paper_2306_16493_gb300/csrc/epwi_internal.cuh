@@ -110,6 +110,8 @@ struct epwi_ctx {
     DevBuf vel;                    // double [Nk][W][3] m/s
     DevBuf hw;                     // double [Nq][Nm] eV (dropped modes keep their value)
     DevBuf hwmax32;                // float [Nq] largest kept mode energy, -1 if none
+    DevBuf hw32;                   // float [Nq][Nm] mode energy, -1 for dropped modes
+    double eabs_max = 0;           // max |eps| over the grid (FP32 error bounds)
     DevBuf u;                      // double2 [Nq][Nm][Nm] A (row mu, column nu), 0 if dropped
     DevBuf u32;                    // float2 [Nq][Nm][Nm]
     DevBuf eig_flag;               // int [1] non-converged count
@@ -149,6 +151,8 @@ struct epwi_ctx {
     DevBuf tc_erel, tc_f32;        // float [Nk][W]: eps - mu, Fermi-Dirac
     DevBuf tc_n32, tc_hw32;        // float [Nq][Nm]: Bose-Einstein, mode energy (-1 dropped)
     DevBuf tc_err;                 // int: timed-out waits in the tensor-core kernel
+    DevBuf tc_meta;                // per-tile metadata of the tensor-core kernel
+    int64_t stats_tc_grid = 0;
 
     // conductivity
     bool have_sigma = false;
@@ -156,11 +160,11 @@ struct epwi_ctx {
 
     ~epwi_ctx() {
         DevBuf *all[] = {&Re, &Rp, &Rcart, &Hw, &Phiw, &mode_mass, &gw64, &gw32, &ph64, &ph32,
-                         &eps, &eps32, &V, &V32, &vel, &hw, &hwmax32, &u, &u32, &eig_flag,
+                         &eps, &eps32, &V, &V32, &vel, &hw, &hwmax32, &hw32, &u, &u32, &eig_flag,
                          &kpts, &win_lo, &win_n, &kp_state, &kp_pairs, &inv_tau, &st_k,
                          &st_n, &focc, &nocc, &pairs, &ghat, &tiles, &tile_part, &kp_tile,
                          &scan_tmp, &red_tmp, &counts, &tc_ptab, &tc_erel, &tc_f32,
-                         &tc_n32, &tc_hw32, &tc_err};
+                         &tc_n32, &tc_hw32, &tc_err, &tc_meta};
         for (DevBuf *b : all) b->release();
     }
 };

@@ -310,6 +310,7 @@ void process_workset(epwi_ctx *c, const WorkSet &ws, double *g2out) {
         ra.ghat64 = c->ghat.as<double2>();
         ra.ghat_raw = c->ghat.p;
         ra.precision = c->opt.precision;
+        ra.nstates_chunk = ns;
         cudaEventRecord(ev_re.e[0], c->stream);
         if (tc) tc_restage(c, ra);
         else fp64_restage(ra, W, c->stream);
@@ -350,6 +351,7 @@ void process_workset(epwi_ctx *c, const WorkSet &ws, double *g2out) {
         sa.g2out = g2out;
         sa.g2_base = p_base;
         sa.precision = c->opt.precision;
+        sa.nstates_chunk = ns;
         sa.nsel_max = 1;
         if (ws.ovr_nsel >= 0) {
             sa.nsel_max = ws.ovr_nsel;

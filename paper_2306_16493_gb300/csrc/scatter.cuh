@@ -24,6 +24,7 @@ struct RestageArgs {
     double2 *ghat64;                      // FP64 output [state][nrow]
     void *ghat_raw;                       // split-precision output (layout of the TC kernel)
     int precision;
+    int64_t nstates_chunk;                // states of the chunk
 };
 
 struct ScatterArgs {
@@ -54,6 +55,7 @@ struct ScatterArgs {
     int64_t g2_base;
     int precision;
     int nsel_max;                         // largest band window of the chunk
+    int64_t nstates_chunk;                // states of the chunk
 };
 
 struct WorkSet {

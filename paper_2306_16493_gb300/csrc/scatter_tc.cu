@@ -83,24 +83,28 @@ __device__ __forceinline__ void split2f(float x, uint32_t &hi, uint32_t &lo) {
 }
 
 // Pre-split phase table, doubled (index m in [0, 2L) holds e^{2 pi i (m mod L)/L}) so that a
-// sum of two reduced indices needs no modulo.  16-bit types: {re_h | im_h << 16, re_l | im_l << 16};
-// tf32: {re_h, im_h, re_l, im_l}.
+// sum of two reduced indices needs no modulo, and replicated R = 2^rlog times (entry m, copy g
+// at position m*R + g) so that lanes reading different copies never share a bank.
+// 16-bit types: {re_h | im_h << 16, re_l | im_l << 16}; tf32: {re_h, im_h, re_l, im_l}.
 template <class Op>
-__global__ void k_phase_split(int L, const double2 *__restrict__ ph64, uint32_t *__restrict__ out) {
+__global__ void k_phase_split(int L, int rlog, const double2 *__restrict__ ph64, uint32_t *__restrict__ out) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= 2 * L) return;
     const double2 p = ph64[m % L];
     uint32_t rh, rl, ih, il;
     split2<Op>(p.x, rh, rl);
     split2<Op>(p.y, ih, il);
-    if constexpr (Op::kTF32) {
-        out[4 * m + 0] = rh;
-        out[4 * m + 1] = ih;
-        out[4 * m + 2] = rl;
-        out[4 * m + 3] = il;
-    } else {
-        out[2 * m + 0] = rh | (ih << 16);
-        out[2 * m + 1] = rl | (il << 16);
+    for (int g = 0; g < (1 << rlog); ++g) {
+        const size_t o = (size_t)((m << rlog) | g);
+        if constexpr (Op::kTF32) {
+            out[4 * o + 0] = rh;
+            out[4 * o + 1] = ih;
+            out[4 * o + 2] = rl;
+            out[4 * o + 3] = il;
+        } else {
+            out[2 * o + 0] = rh | (ih << 16);
+            out[2 * o + 1] = rl | (il << 16);
+        }
     }
 }
 
@@ -123,9 +127,26 @@ __global__ void k_tc_tables(int64_t nk, int W, int Nm, const double *__restrict_
     }
 }
 
-// Re->k stage in FP32: ghat32[state][rp][mu][i] = sum_j [sum_Re e^{ik.Re} gw32] V32_jn.
-template <int W, int KG>
-__global__ void __launch_bounds__(128) k_restage_f32(RestageArgs a, float2 *__restrict__ out) {
+// Byte offset of element (row c, k) inside one core-matrix block with 64 bytes of K per
+// row (four 8x16-byte core matrices along K per 8-row group).
+template <int ES>
+__host__ __device__ __forceinline__ uint32_t cm_off(int c, int k) {
+    return (uint32_t)(((c >> 3) * 4 + (k * ES) / 16) * 128 + (c & 7) * 16 + (k * ES) % 16);
+}
+
+// Re->k stage for the split-precision path.  ghat(k)[rp][mu][i][n] = sum_j [sum_Re e^{ik.Re}
+// gw32] V32_jn is accumulated in FP32, scaled by 2^e, split into hi + lo and written as the
+// B operand image of the tensor-core kernel:
+//   img[ch][arr][state][NMWP rows][64 bytes]  (arr: Br_hi, Bi_hi, Br_lo, Bi_lo),
+// row = mu*W + i (rows NMW..NMWP-1 and K beyond nRp stay zero), K = rp - ch*KC.
+template <class Op, int W, int NM, int KG>
+__global__ void __launch_bounds__(128) k_restage_tc(RestageArgs a, uint8_t *__restrict__ img,
+                                                    int64_t ns, float scale) {
+    constexpr int ES = Op::kBytes;
+    constexpr int KC = 64 / ES;
+    constexpr int NMW = NM * W;
+    constexpr int NMWP = (NMW + 15) / 16 * 16;
+    constexpr uint32_t BLK = NMWP * 64;
     extern __shared__ float2 Pf[];   // [KG][nRe]
     const int kg0 = blockIdx.y * KG;
     for (int idx = threadIdx.x; idx < KG * a.nRe; idx += blockDim.x) {
@@ -159,34 +180,74 @@ __global__ void __launch_bounds__(128) k_restage_f32(RestageArgs a, float2 *__re
             for (int j = 0; j < W; ++j) acc[kk][j] = cfmaf(p, gv[j], acc[kk][j]);
         }
     }
+    const int rp = row / NMW, c = row - rp * NMW;
+    const int ch = rp / KC, kk = rp - ch * KC;
+    const uint32_t eoff = cm_off<ES>(c, kk);
 #pragma unroll
-    for (int kk = 0; kk < KG; ++kk) {
-        if (kg0 + kk >= a.nkp) break;
-        const int ik = a.kpts[kg0 + kk];
+    for (int q = 0; q < KG; ++q) {
+        if (kg0 + q >= a.nkp) break;
+        const int ik = a.kpts[kg0 + q];
         const int lo = a.ovr_nsel >= 0 ? a.ovr_lo : a.win_lo[ik];
-        const int ns = a.ovr_nsel >= 0 ? a.ovr_nsel : a.win_n[ik];
-        const int64_t s0 = a.kp_state[kg0 + kk] - a.s_base;
+        const int nsl = a.ovr_nsel >= 0 ? a.ovr_nsel : a.win_n[ik];
+        const int64_t s0 = a.kp_state[kg0 + q] - a.s_base;
         const float2 *Vk = a.V32 + (int64_t)ik * W * W;
-        for (int np = 0; np < ns; ++np) {
+        for (int np = 0; np < nsl; ++np) {
             float2 o = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int j = 0; j < W; ++j) o = cfmaf(acc[kk][j], Vk[j * W + lo + np], o);
-            out[(s0 + np) * a.nrow + row] = o;
+            for (int j = 0; j < W; ++j) o = cfmaf(acc[q][j], Vk[j * W + lo + np], o);
+            uint32_t w4[4];
+            split2f<Op>(o.x * scale, w4[0], w4[2]);
+            split2f<Op>(o.y * scale, w4[1], w4[3]);
+#pragma unroll
+            for (int arr = 0; arr < 4; ++arr) {
+                uint8_t *dst = img + ((size_t)(ch * 4 + arr) * ns + (s0 + np)) * BLK + eoff;
+                if constexpr (ES == 4) *reinterpret_cast<uint32_t *>(dst) = w4[arr];
+                else *reinterpret_cast<uint16_t *>(dst) = (uint16_t)w4[arr];
+            }
         }
     }
 }
 
+// Per-tile metadata gathered once so that every thread starts a tile with one 32-byte load.
+struct __align__(16) TileMeta {
+    int kpl, begin, end, ik;
+    int lo, nsel;
+    long long s0;                  // chunk-local state offset of the k-point
+};
+
+__global__ void k_tile_meta(int64_t ntiles, const int4 *__restrict__ tiles, const int *__restrict__ kpts,
+                            const int *__restrict__ win_lo, const int *__restrict__ win_n,
+                            const int64_t *__restrict__ kp_state, int64_t s_base, int ovr_lo,
+                            int ovr_nsel, TileMeta *__restrict__ meta) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    const int4 x = tiles[t];
+    TileMeta m;
+    m.kpl = x.x;
+    m.begin = x.y;
+    m.end = x.z;
+    m.ik = kpts[x.x];
+    m.lo = ovr_nsel >= 0 ? ovr_lo : win_lo[m.ik];
+    m.nsel = ovr_nsel >= 0 ? ovr_nsel : win_n[m.ik];
+    m.s0 = (long long)(kp_state[x.x] - s_base);
+    meta[t] = m;
+}
+
 struct TcArgs {
     ScatterArgs s;
-    const float2 *ghat32;          // [state][nRp][NM*W]
-    const uint32_t *ptab;          // pre-split doubled phase table
+    const TileMeta *meta;
+    const uint8_t *img;            // B image of the chunk (see k_restage_tc)
+    int64_t ns;                    // states in the chunk (image stride)
+    const uint32_t *ptab;          // pre-split doubled phase table, replicated 2^rlog times
+    int rlog;
     const float *erel32, *f32, *n32, *hw32;
-    float scale, scale_inv2;       // B scaled by 2^e before the split; |g|^2 scaled back
+    float scale_inv2;              // |g|^2 scaled back by 2^-2e
     float ceta32, inv_eta32;
     int cube_r;                    // Rp = full cube [-r, r]^3, n3 fastest
     int nchunk;                    // K chunks
     int nbg;                       // bands per column group
     int ncp_max;                   // B rows per stage
+    int bres;                      // 1: B of one (k-point, band group) resident in nchunk slots
     uint32_t tmem_cols;
     int64_t ntiles;
     int *err;                      // [0]: timed-out waits
@@ -197,8 +258,36 @@ __device__ __forceinline__ int pmod(int x, int L) {
     return r < 0 ? r + L : r;
 }
 
-template <class Op, int W, int NM>
-__global__ void __launch_bounds__(128, 1) k_scatter_tc(TcArgs a) {
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// Issues the four B-operand bulk copies of (tile, band group g0, chunk ch) into a stage.
+template <int NMWP>
+__device__ __forceinline__ void issue_b(const TcArgs &a, const TileMeta &m, int g0, int ch, uint8_t *bStage,
+                                        uint32_t B_ARR, uint64_t *bar) {
+    const int nb = min(a.nbg, m.nsel - g0);
+    const uint32_t bytes = (uint32_t)nb * NMWP * 64;
+    tc::mbar_arrive_expect_tx(bar, 4 * bytes);
+#pragma unroll
+    for (int arr = 0; arr < 4; ++arr)
+        tc::bulk_g2s(bStage + arr * B_ARR,
+                     a.img + ((size_t)(ch * 4 + arr) * a.ns + ((size_t)m.s0 + g0)) * (NMWP * 64), bytes, bar);
+}
+
+// Warp-specialised CTA of 160 threads: warps 0-3 are producers (one q row each: phase
+// operands into shared memory, then the epilogue from TMEM), warp 4 lane 0 is the control
+// thread (B operand bulk copies, tcgen05.mma issue and commit).  B either stays resident for
+// a (k-point, band group) across consecutive tiles (reloaded only when it changes) or, when
+// it does not fit, streams through a two-slot ring one chunk ahead.  They communicate
+// through mbarriers only: a_full (128 arrivals), mma_done (tcgen05.commit), b_full (bulk-copy
+// bytes) and acc_empty (128 arrivals after the epilogue read TMEM).
+// One CTA per SM: the shared-memory footprint and the per-sub-partition register file
+// (warps w and w+4 of two co-resident 5-warp CTAs share a sub-partition) rule out a second.
+template <class Op, int W, int NM, int RC>
+__global__ void __maxnreg__(255) k_scatter_tc(TcArgs a) {
     constexpr int ES = Op::kBytes;
     constexpr int KC = 64 / ES;                 // Rp per chunk (64 bytes per row and operand)
     constexpr int EPV = 16 / ES;                // elements per 16-byte core-matrix row
@@ -206,22 +295,34 @@ __global__ void __launch_bounds__(128, 1) k_scatter_tc(TcArgs a) {
     constexpr int NMWP = (NMW + 15) / 16 * 16;  // columns per band, padded to the MMA N granule
     constexpr uint32_t A_ARR = 128 * 64;        // bytes per A operand per stage
     constexpr int TW = Op::kTF32 ? 4 : 2;       // 32-bit words per table entry
+    constexpr bool PRE = (W * W + NM * NM) <= 32;   // keep the epilogue operands in registers
     const ScatterArgs &s = a.s;
     extern __shared__ __align__(128) uint8_t smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t B_ARR = (uint32_t)a.ncp_max * 64;
     uint8_t *sA = smem;
     uint8_t *sB = sA + 2 * 4 * A_ARR;
-    uint32_t *sT = reinterpret_cast<uint32_t *>(sB + 2 * 4 * B_ARR);
+    uint32_t *sT = reinterpret_cast<uint32_t *>(sB + (a.bres ? a.nchunk : 2) * 4 * B_ARR);
     const int L = s.g.L;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sT + ((2 * L * TW + 1) & ~1));
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2);
+    const int twords = 2 * L * (1 << a.rlog) * TW;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sT + ((twords + 1) & ~1));
+    uint64_t *a_full = bars, *mma_done = bars + 2, *b_full = bars + 4, *acc_empty = bars + 6,
+             *drained = bars + 7;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 8);
+    volatile int *sfail = reinterpret_cast<volatile int *>(tslot + 1);
     float *wred = reinterpret_cast<float *>(tslot + 4);   // [4][kMaxW]
 
-    for (int i = tid; i < 2 * L * TW; i += blockDim.x) sT[i] = a.ptab[i];
+    for (int i = tid; i < twords; i += blockDim.x) sT[i] = a.ptab[i];
     if (tid == 0) {
-        tc::mbar_init(&bars[0], 1);
-        tc::mbar_init(&bars[1], 1);
+        tc::mbar_init(&a_full[0], 128);
+        tc::mbar_init(&a_full[1], 128);
+        tc::mbar_init(&mma_done[0], 1);
+        tc::mbar_init(&mma_done[1], 1);
+        tc::mbar_init(&b_full[0], 1);
+        tc::mbar_init(&b_full[1], 1);
+        tc::mbar_init(&acc_empty[0], 128);
+        tc::mbar_init(drained, 1);
+        *sfail = 0;
         tc::fence_mbar_init();
     }
     if (warp == 0) {
@@ -232,301 +333,458 @@ __global__ void __launch_bounds__(128, 1) k_scatter_tc(TcArgs a) {
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = *tslot;
-    const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);
+    const int64_t t_begin = blockIdx.x * a.ntiles / gridDim.x;
+    const int64_t t_end = (blockIdx.x + 1) * a.ntiles / gridDim.x;
 
-    const int r = a.cube_r, D = 2 * r + 1, D2 = D * D;
-    uint32_t use[2] = {0, 0}, done[2] = {0, 0};
-    uint32_t ctr = 0;
-    bool failed = false;
-
-    for (int64_t tile = blockIdx.x; tile < a.ntiles && !failed; tile += gridDim.x) {
-        const int4 t = s.tiles[tile];
-        const int kpl = t.x;
-        const int64_t pair = (int64_t)t.y + tid;
-        const bool active = pair < t.z;
-        const int ik = s.kpts[kpl];
-        const int lo = s.ovr_nsel >= 0 ? s.ovr_lo : s.win_lo[ik];
-        const int nsel = s.ovr_nsel >= 0 ? s.ovr_nsel : s.win_n[ik];
-        const int64_t s0 = s.kp_state[kpl] - s.s_base;
-        int iq = 0;
-        int64_t ikq = 0;
-        int a1 = 0, a2 = 0, a3 = 0;
-        if (active) {
-            iq = s.pairs[pair];
-            ikq = kplusq(s.g, ik, iq);
-            int i1, i2, i3;
-            grid_coords(s.g, iq, i1, i2, i3);
-            a1 = i1 * s.g.s1 % L;
-            a2 = i2 * s.g.s2 % L;
-            a3 = i3 * s.g.s3 % L;
-        }
-        const int c3m = pmod(-r * a3, L);
-
-        for (int g0 = 0; g0 < nsel && !failed; g0 += a.nbg) {
-            const int nb = min(a.nbg, nsel - g0);
-            const int ncp = nb * NMWP;
-            const uint32_t idP = tc::idesc(Op::kFmt, 128, ncp, false);
-            const uint32_t idN = tc::idesc(Op::kFmt, 128, ncp, true);
-            for (int ch = 0; ch < a.nchunk; ++ch) {
-                const int st = ctr & 1;
-                if (use[st] > done[st]) {
-                    if (!tc::mbar_wait_bounded(&bars[st], done[st] & 1, kWaitTimeoutNs)) failed = true;
-                    ++done[st];
+    if (warp == 4) {
+        // ------------------------------------------------------------ control thread
+        if (lane == 0) {
+            uint32_t aph[2] = {0, 0}, bph[2] = {0, 0}, bpend[2] = {0, 0};
+            uint32_t mc[2] = {0, 0}, mw[2] = {0, 0}, eph = 0;
+            uint32_t ctr = 0;
+            bool failed = false, first = true;
+            uint32_t dph = 0;
+            auto drain_mma = [&]() {
+                if (a.bres) {
+                    // a commit on its own barrier completes once every MMA issued so far has;
+                    // (mma_done phases are not tracked here: the producers observe those)
+                    tc::mma_commit(drained);
+                    if (!tc::mbar_wait_bounded(drained, dph, kWaitTimeoutNs)) failed = true;
+                    dph ^= 1;
+                    return;
                 }
-                if (__syncthreads_or(failed)) {
+                for (int st = 0; st < 2; ++st)
+                    while (mc[st] > mw[st]) {
+                        if (!tc::mbar_wait_bounded(&mma_done[st], mw[st] & 1, kWaitTimeoutNs)) failed = true;
+                        ++mw[st];
+                    }
+            };
+            // streaming mode: (pt, pg, pc) is the next chunk to fetch into the 2-slot ring
+            int64_t pt = t_begin;
+            int pg = 0, pc = 0;
+            TileMeta pm;
+            auto prefetch = [&](int st2) {
+                issue_b<NMWP>(a, pm, pg, pc, sB + st2 * 4 * B_ARR, B_ARR, &b_full[st2]);
+                ++bpend[st2];
+                if (++pc == a.nchunk) {
+                    pc = 0;
+                    pg += a.nbg;
+                    if (pg >= pm.nsel) {
+                        pg = 0;
+                        if (++pt < t_end) pm = a.meta[pt];
+                    }
+                }
+            };
+            if (!a.bres && pt < t_end) {
+                pm = a.meta[pt];
+                prefetch(0);
+            }
+            // resident mode: all chunks of one (k-point, band group) stay in nchunk slots
+            int tag_kp = -1, tag_g0 = -1;
+            for (int64_t tile = t_begin; tile < t_end && !failed; ++tile) {
+                const TileMeta m = a.meta[tile];
+                for (int g0 = 0; g0 < m.nsel && !failed; g0 += a.nbg) {
+                    const int ncp = min(a.nbg, m.nsel - g0) * NMWP;
+                    const uint32_t idP = tc::idesc(Op::kFmt, 128, ncp, false);
+                    const uint32_t idN = tc::idesc(Op::kFmt, 128, ncp, true);
+                    if (a.bres && (m.kpl != tag_kp || g0 != tag_g0)) {
+                        drain_mma();   // no MMA may still read the old operand
+                        const int nb = min(a.nbg, m.nsel - g0);
+                        const uint32_t bytes = (uint32_t)nb * NMWP * 64;
+                        tc::mbar_arrive_expect_tx(&b_full[0], 4 * bytes * a.nchunk);
+                        for (int ch = 0; ch < a.nchunk; ++ch)
+#pragma unroll
+                            for (int arr = 0; arr < 4; ++arr)
+                                tc::bulk_g2s(sB + (ch * 4 + arr) * B_ARR,
+                                             a.img + ((size_t)(ch * 4 + arr) * a.ns + ((size_t)m.s0 + g0)) *
+                                                         (NMWP * 64),
+                                             bytes, &b_full[0]);
+                        if (!tc::mbar_wait_bounded(&b_full[0], bph[0], kWaitTimeoutNs)) failed = true;
+                        bph[0] ^= 1;
+                        tag_kp = m.kpl;
+                        tag_g0 = g0;
+                    }
+                    if (!first) {
+                        if (!tc::mbar_wait_bounded(acc_empty, eph, kWaitTimeoutNs)) failed = true;
+                        eph ^= 1;
+                        tc::tc_fence_after();
+                    }
+                    first = false;
+                    for (int ch = 0; ch < a.nchunk && !failed; ++ch) {
+                        const int st = ctr & 1;
+                        if (!tc::mbar_wait_bounded(&a_full[st], aph[st], kWaitTimeoutNs)) failed = true;
+                        aph[st] ^= 1;
+                        if (!a.bres) {
+                            if (!tc::mbar_wait_bounded(&b_full[st], bph[st], kWaitTimeoutNs)) failed = true;
+                            bph[st] ^= 1;
+                            --bpend[st];
+                        }
+                        if (failed) break;
+                        tc::tc_fence_after();
+                        const uint32_t aB = tc::smem_u32(sA + st * 4 * A_ARR);
+                        const uint32_t bB = tc::smem_u32(sB + (a.bres ? ch : st) * 4 * B_ARR);
+                        const uint32_t dR = tmem, dI = tmem + (uint32_t)ncp;
+#pragma unroll
+                        for (int ks = 0; ks < 2; ++ks) {
+                            uint64_t A[4], B[4];
+#pragma unroll
+                            for (int arr = 0; arr < 4; ++arr) {
+                                A[arr] = tc::sdesc(aB + arr * A_ARR + ks * 256, 128, 512);
+                                B[arr] = tc::sdesc(bB + arr * B_ARR + ks * 256, 128, 512);
+                            }
+                            const uint32_t acc = (ch == 0 && ks == 0) ? 0u : 1u;
+                            // Dr = Pr Br - Pi Bi ; Di = Pr Bi + Pi Br ; each as hh + hl + lh
+                            tc::mma<Op::kTF32>(dR, A[0], B[0], idP, acc);
+                            tc::mma<Op::kTF32>(dR, A[0], B[2], idP, 1);
+                            tc::mma<Op::kTF32>(dR, A[2], B[0], idP, 1);
+                            tc::mma<Op::kTF32>(dR, A[1], B[1], idN, 1);
+                            tc::mma<Op::kTF32>(dR, A[1], B[3], idN, 1);
+                            tc::mma<Op::kTF32>(dR, A[3], B[1], idN, 1);
+                            tc::mma<Op::kTF32>(dI, A[0], B[1], idP, acc);
+                            tc::mma<Op::kTF32>(dI, A[0], B[3], idP, 1);
+                            tc::mma<Op::kTF32>(dI, A[2], B[1], idP, 1);
+                            tc::mma<Op::kTF32>(dI, A[1], B[0], idP, 1);
+                            tc::mma<Op::kTF32>(dI, A[1], B[2], idP, 1);
+                            tc::mma<Op::kTF32>(dI, A[3], B[0], idP, 1);
+                        }
+                        tc::mma_commit(&mma_done[st]);
+                        ++mc[st];
+                        // streaming mode: B of the next chunk into the other slot once its MMAs are done
+                        if (!a.bres && pt < t_end) {
+                            const int st2 = st ^ 1;
+                            if (mc[st2] > mw[st2]) {
+                                if (!tc::mbar_wait_bounded(&mma_done[st2], mw[st2] & 1, kWaitTimeoutNs))
+                                    failed = true;
+                                ++mw[st2];
+                            }
+                            if (!failed) prefetch(st2);
+                        }
+                        ++ctr;
+                    }
+                }
+                if (*sfail) failed = true;
+            }
+            // drain outstanding MMAs and bulk copies before the CTA exits
+            drain_mma();
+            for (int st = 0; st < 2; ++st)
+                while (bpend[st] > 0) {
+                    if (!tc::mbar_wait_bounded(&b_full[st], bph[st], kWaitTimeoutNs)) failed = true;
+                    bph[st] ^= 1;
+                    --bpend[st];
+                }
+            if (failed) {
+                *sfail = 1;
+                atomicAdd(a.err, 1);
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ producers / epilogue
+        constexpr int D = 2 * RC + 1;               // R_p cube side
+        constexpr int NRP = D * D * D;
+        constexpr int NCH = (NRP + KC - 1) / KC;    // K chunks (compile time)
+        const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);
+        const int g = lane & ((1 << a.rlog) - 1);
+        const uint32_t rowoff = (uint32_t)((tid >> 3) * 4) * 128 + (tid & 7) * 16;
+        uint32_t used[2] = {0, 0}, mw[2] = {0, 0};
+        uint32_t ctr = 0;
+        bool failed = false;
+        const unsigned n1 = s.g.n1, n2 = s.g.n2, n3 = s.g.n3;
+        // the next tile's metadata and q are fetched during the current tile's MMAs
+        TileMeta m_next;
+        unsigned q_next = 0;
+        if (t_begin < t_end) {
+            m_next = a.meta[t_begin];
+            if (m_next.begin + tid < m_next.end) q_next = (unsigned)s.pairs[m_next.begin + tid];
+        }
+        for (int64_t tile = t_begin; tile < t_end && !failed; ++tile) {
+            const TileMeta m = m_next;
+            const int pair = m.begin + tid;
+            const bool active = pair < m.end;
+            unsigned iq = 0, ikq = 0;
+            int a1 = 0, a2 = 0, a3 = 0;
+            const unsigned q_this = q_next;
+            if (active) {
+                iq = q_this;
+                const unsigned q3 = iq % n3, qt = iq / n3, q2 = qt % n2, q1 = qt / n2;
+                const unsigned k3 = (unsigned)m.ik % n3, kt = (unsigned)m.ik / n3, k2 = kt % n2, k1 = kt / n2;
+                unsigned b1 = q1 + k1, b2 = q2 + k2, b3 = q3 + k3;
+                if (b1 >= n1) b1 -= n1;
+                if (b2 >= n2) b2 -= n2;
+                if (b3 >= n3) b3 -= n3;
+                ikq = (b1 * n2 + b2) * n3 + b3;
+                a1 = (int)(q1 * (unsigned)s.g.s1 % (unsigned)L);
+                a2 = (int)(q2 * (unsigned)s.g.s2 % (unsigned)L);
+                a3 = (int)(q3 * (unsigned)s.g.s3 % (unsigned)L);
+            }
+            for (int g0 = 0; g0 < m.nsel && !failed; g0 += a.nbg) {
+                const int nb = min(a.nbg, m.nsel - g0);
+                const int ncp = nb * NMWP;
+                // Reduced phase-index tables of this q: C3[n3+R] = n3 a3 mod L and
+                // B12[(n1+R) D + n2+R] = (n1 a1 + n2 a2) mod L; an R_p index is B12 + C3 < 2L.
+                int C3[D], B12[D * D];
+                {
+                    int B1[D], B2[D];
+                    B1[0] = pmod(-RC * a1, L);
+                    B2[0] = pmod(-RC * a2, L);
+                    C3[0] = pmod(-RC * a3, L);
+#pragma unroll
+                    for (int j = 1; j < D; ++j) {
+                        const int t1 = B1[j - 1] + a1, t2 = B2[j - 1] + a2, t3 = C3[j - 1] + a3;
+                        B1[j] = t1 >= L ? t1 - L : t1;
+                        B2[j] = t2 >= L ? t2 - L : t2;
+                        C3[j] = t3 >= L ? t3 - L : t3;
+                    }
+#pragma unroll
+                    for (int i1 = 0; i1 < D; ++i1)
+#pragma unroll
+                        for (int i2 = 0; i2 < D; ++i2) {
+                            const int t = B1[i1] + B2[i2];
+                            B12[i1 * D + i2] = t >= L ? t - L : t;
+                        }
+                }
+#pragma unroll
+                for (int ch = 0; ch < NCH; ++ch) {
+                    const int st = ctr & 1;
+                    if (used[st] > mw[st]) {
+                        if (!tc::mbar_wait_bounded(&mma_done[st], mw[st] & 1, kWaitTimeoutNs)) failed = true;
+                        ++mw[st];
+                    }
+                    if (failed || *sfail) {
+                        failed = true;
+                        break;
+                    }
+                    // The tables are re-defined (empty asm) at every chunk so that the compiler
+                    // forms each chunk's indices inside the chunk instead of hoisting all of them.
+#pragma unroll
+                    for (int j = 0; j < D; ++j) asm volatile("" : "+r"(C3[j]));
+#pragma unroll
+                    for (int j = 0; j < D * D; ++j) asm volatile("" : "+r"(B12[j]));
+                    // ---- A: phases of this thread's q for R_p = ch*KC .. ch*KC+KC-1.  Every index
+                    // is independent (compile-time (i12, i3)); K beyond nRp reads entry 0, which
+                    // meets zero B rows; rows of inactive threads are never read back.
+                    uint8_t *aSt = sA + st * 4 * A_ARR;
+#pragma unroll
+                    for (int kb = 0; kb < 4; ++kb) {
+                        uint32_t e[EPV][TW];
+#pragma unroll
+                        for (int j = 0; j < EPV; ++j) {
+                            const int k = ch * KC + kb * EPV + j;
+                            const int kk = k < NRP ? k : 0;
+                            const int idx = k < NRP ? B12[kk / D] + C3[kk % D] : 0;
+                            const uint32_t *src = sT + (((idx << a.rlog) | g) * TW);
+                            if constexpr (TW == 4) {
+                                const uint4 v4 = *reinterpret_cast<const uint4 *>(src);
+                                e[j][0] = v4.x;
+                                e[j][1] = v4.y;
+                                e[j][2] = v4.z;
+                                e[j][3] = v4.w;
+                            } else {
+                                const uint2 v2 = *reinterpret_cast<const uint2 *>(src);
+                                e[j][0] = v2.x;
+                                e[j][1] = v2.y;
+                            }
+                        }
+                        uint4 v[4];
+                        if constexpr (Op::kTF32) {
+                            v[0] = make_uint4(e[0][0], e[1][0], e[2][0], e[3][0]);
+                            v[1] = make_uint4(e[0][1], e[1][1], e[2][1], e[3][1]);
+                            v[2] = make_uint4(e[0][2], e[1][2], e[2][2], e[3][2]);
+                            v[3] = make_uint4(e[0][3], e[1][3], e[2][3], e[3][3]);
+                        } else {
+                            uint32_t w4[4][4];
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                w4[0][q] = __byte_perm(e[2 * q][0], e[2 * q + 1][0], 0x5410);
+                                w4[1][q] = __byte_perm(e[2 * q][0], e[2 * q + 1][0], 0x7632);
+                                w4[2][q] = __byte_perm(e[2 * q][1], e[2 * q + 1][1], 0x5410);
+                                w4[3][q] = __byte_perm(e[2 * q][1], e[2 * q + 1][1], 0x7632);
+                            }
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) v[q] = make_uint4(w4[q][0], w4[q][1], w4[q][2], w4[q][3]);
+                        }
+#pragma unroll
+                        for (int arr = 0; arr < 4; ++arr)
+                            *reinterpret_cast<uint4 *>(aSt + arr * A_ARR + rowoff + kb * 128) = v[arr];
+                        asm volatile("" ::: "memory");   // keep one 16-byte row block in flight
+                    }
+                    tc::fence_proxy_async_smem();
+                    mbar_arrive(&a_full[st]);
+                    ++used[st];
+                    ++ctr;
+                }
+                if (failed) break;
+                if (g0 == 0 && tile + 1 < t_end) {
+                    m_next = a.meta[tile + 1];
+                    q_next = (m_next.begin + tid < m_next.end) ? (unsigned)s.pairs[m_next.begin + tid] : 0u;
+                }
+                // epilogue operands of this pair, fetched while the last MMAs run
+                float2 Vr[PRE ? W * W : 1], ur[PRE ? NM * NM : 1];
+                float wq[NM], nq[NM], emr[W], fmr[W];
+                const float2 *Vq = s.V32 + (size_t)ikq * W * W;
+                const float2 *uq = s.u32 + (size_t)iq * NM * NM;
+                if constexpr (PRE) {
+#pragma unroll
+                    for (int x = 0; x < W * W; ++x) Vr[x] = __ldg(Vq + x);
+#pragma unroll
+                    for (int x = 0; x < NM * NM; ++x) ur[x] = __ldg(uq + x);
+                } else {
+                    tc::prefetch_l1(Vq);
+                    tc::prefetch_l1(uq);
+                }
+#pragma unroll
+                for (int nu = 0; nu < NM; ++nu) {
+                    wq[nu] = __ldg(a.hw32 + (size_t)iq * NM + nu);
+                    nq[nu] = __ldg(a.n32 + (size_t)iq * NM + nu);
+                }
+#pragma unroll
+                for (int mm = 0; mm < W; ++mm) {
+                    emr[mm] = __ldg(a.erel32 + (size_t)ikq * W + mm);
+                    fmr[mm] = __ldg(a.f32 + (size_t)ikq * W + mm);
+                }
+                // ---- accumulator ready (the last commit covers all MMAs of the group)
+                {
+                    const int st = (ctr - 1) & 1;
+                    if (!tc::mbar_wait_bounded(&mma_done[st], mw[st] & 1, kWaitTimeoutNs)) failed = true;
+                    ++mw[st];
+                    if (failed) break;
+                }
+                tc::tc_fence_after();
+                for (int b = 0; b < nb; ++b) {
+                    float gr[NMWP], gi[NMWP];
+#pragma unroll
+                    for (int blk = 0; blk < NMWP / 16; ++blk) {
+                        float tmp[16];
+                        tc::tmem_ld16(tmem_row + (uint32_t)(b * NMWP + blk * 16), tmp);
+#pragma unroll
+                        for (int x = 0; x < 16; ++x) gr[blk * 16 + x] = tmp[x];
+                        tc::tmem_ld16(tmem_row + (uint32_t)(ncp + b * NMWP + blk * 16), tmp);
+#pragma unroll
+                        for (int x = 0; x < 16; ++x) gi[blk * 16 + x] = tmp[x];
+                    }
+                    tc::tmem_wait_ld();
+                    if (b == nb - 1) {
+                        tc::tc_fence_before();
+                        mbar_arrive(acc_empty);   // TMEM may be overwritten by the next group
+                    }
+                    float rate = 0.f;
+                    if (active) {
+                        const float en = a.erel32[(size_t)m.ik * W + m.lo + g0 + b];
+#pragma unroll
+                        for (int mm = 0; mm < W; ++mm) {
+                            float2 h[NM];
+#pragma unroll
+                            for (int mu = 0; mu < NM; ++mu) {
+                                h[mu] = make_float2(0.f, 0.f);
+#pragma unroll
+                                for (int i = 0; i < W; ++i) {
+                                    const float2 vv = PRE ? Vr[(i * W + mm) % (PRE ? W * W : 1)] : __ldg(Vq + i * W + mm);
+                                    h[mu] = cfmacf(vv, make_float2(gr[mu * W + i], gi[mu * W + i]), h[mu]);
+                                }
+                            }
+                            const float em = emr[mm];
+                            const float fm = fmr[mm];
+#pragma unroll
+                            for (int nu = 0; nu < NM; ++nu) {
+                                const float w = wq[nu];
+                                float2 gv = make_float2(0.f, 0.f);
+#pragma unroll
+                                for (int mu = 0; mu < NM; ++mu) {
+                                    const float2 uv = PRE ? ur[(mu * NM + nu) % (PRE ? NM * NM : 1)] : __ldg(uq + mu * NM + nu);
+                                    gv = cfmaf(h[mu], uv, gv);
+                                }
+                                const float g2 = gv.x * gv.x + gv.y * gv.y;
+                                if (s.g2out) {
+                                    s.g2out[(((s.g2_base + pair) * m.nsel + g0 + b) * NM + nu) * W + mm] =
+                                        (w >= 0.f) ? (double)g2 * (double)a.scale_inv2 : 0.0;
+                                    continue;
+                                }
+                                if (w < 0.f) continue;
+                                const float x1 = (en + w) - em;
+                                const float x2 = (en - w) - em;
+                                float tt = 0.f;
+                                if (fabsf(x1) <= a.ceta32) {
+                                    const float y = x1 * a.inv_eta32;
+                                    tt += (nq[nu] + fm) * __expf(-y * y);
+                                }
+                                if (fabsf(x2) <= a.ceta32) {
+                                    const float y = x2 * a.inv_eta32;
+                                    tt += (1.f + nq[nu] - fm) * __expf(-y * y);
+                                }
+                                rate = fmaf(g2, tt, rate);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) rate += __shfl_down_sync(0xffffffffu, rate, o);
+                    if (lane == 0) wred[warp * epc::kMaxW + g0 + b] = rate * a.scale_inv2;
+                }
+            }
+            producers_sync();
+            if (!failed && tid < m.nsel)
+                s.tile_part[tile * epc::kMaxW + tid] =
+                    ((double)wred[tid] + (double)wred[epc::kMaxW + tid]) +
+                    ((double)wred[2 * epc::kMaxW + tid] + (double)wred[3 * epc::kMaxW + tid]);
+            producers_sync();
+        }
+        // wait for our last committed MMAs to finish before TMEM is released
+        for (int st = 0; st < 2; ++st)
+            while (used[st] > mw[st]) {
+                if (!tc::mbar_wait_bounded(&mma_done[st], mw[st] & 1, kWaitTimeoutNs)) {
                     failed = true;
                     break;
                 }
-                // ---- A: phases of this thread's q for Rp = ch*KC .. ch*KC+KC-1
-                const int k0 = ch * KC;
-                int n1 = k0 / D2 - r, n2 = (k0 / D) % D - r, n3 = k0 % D - r;
-                int b12 = pmod(n1 * a1 + n2 * a2, L);
-                int c3 = pmod(n3 * a3, L);
-                uint8_t *aSt = sA + st * 4 * A_ARR;
-                const uint32_t rowoff = (uint32_t)((tid >> 3) * 4) * 128 + (tid & 7) * 16;
-#pragma unroll
-                for (int kb = 0; kb < 4; ++kb) {
-                    uint32_t e[EPV][TW];
-#pragma unroll
-                    for (int j = 0; j < EPV; ++j) {
-                        const int k = k0 + kb * EPV + j;
-                        const bool ok = active && k < s.nRp;
-                        const uint32_t *src = sT + (size_t)(b12 + c3) * TW;
-#pragma unroll
-                        for (int w = 0; w < TW; ++w) e[j][w] = ok ? src[w] : 0u;
-                        // advance (n1, n2, n3) with carries
-                        ++n3;
-                        c3 += a3;
-                        if (c3 >= L) c3 -= L;
-                        if (n3 > r) {
-                            n3 = -r;
-                            c3 = c3m;
-                            ++n2;
-                            b12 += a2;
-                            if (b12 >= L) b12 -= L;
-                            if (n2 > r) {
-                                n2 = -r;
-                                ++n1;
-                                b12 = pmod(n1 * a1 + n2 * a2, L);
-                            }
-                        }
-                    }
-                    uint4 v[4];
-                    if constexpr (Op::kTF32) {
-                        v[0] = make_uint4(e[0][0], e[1][0], e[2][0], e[3][0]);
-                        v[1] = make_uint4(e[0][1], e[1][1], e[2][1], e[3][1]);
-                        v[2] = make_uint4(e[0][2], e[1][2], e[2][2], e[3][2]);
-                        v[3] = make_uint4(e[0][3], e[1][3], e[2][3], e[3][3]);
-                    } else {
-                        uint32_t w4[4][4];
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            w4[0][q] = __byte_perm(e[2 * q][0], e[2 * q + 1][0], 0x5410);
-                            w4[1][q] = __byte_perm(e[2 * q][0], e[2 * q + 1][0], 0x7632);
-                            w4[2][q] = __byte_perm(e[2 * q][1], e[2 * q + 1][1], 0x5410);
-                            w4[3][q] = __byte_perm(e[2 * q][1], e[2 * q + 1][1], 0x7632);
-                        }
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) v[q] = make_uint4(w4[q][0], w4[q][1], w4[q][2], w4[q][3]);
-                    }
-#pragma unroll
-                    for (int arr = 0; arr < 4; ++arr)
-                        *reinterpret_cast<uint4 *>(aSt + arr * A_ARR + rowoff + kb * 128) = v[arr];
-                }
-                // ---- B: ghat(k) columns of this band group, same chunk of Rp
-                uint8_t *bSt = sB + st * 4 * B_ARR;
-                for (int idx = tid; idx < KC * ncp; idx += blockDim.x) {
-                    const int kk = idx / ncp, c = idx - kk * ncp;
-                    const int b = c / NMWP, mi = c - b * NMWP;
-                    const int k = k0 + kk;
-                    float2 v = make_float2(0.f, 0.f);
-                    if (mi < NMW && k < s.nRp)
-                        v = __ldg(a.ghat32 + ((s0 + g0 + b) * s.nRp + k) * NMW + mi);
-                    uint32_t rh, rl, ih, il;
-                    split2f<Op>(v.x * a.scale, rh, rl);
-                    split2f<Op>(v.y * a.scale, ih, il);
-                    const uint32_t off = (uint32_t)(((c >> 3) * 4 + (kk * ES) / 16) * 128 + (c & 7) * 16 + (kk * ES) % 16);
-                    if constexpr (ES == 4) {
-                        *reinterpret_cast<uint32_t *>(bSt + 0 * B_ARR + off) = rh;
-                        *reinterpret_cast<uint32_t *>(bSt + 1 * B_ARR + off) = ih;
-                        *reinterpret_cast<uint32_t *>(bSt + 2 * B_ARR + off) = rl;
-                        *reinterpret_cast<uint32_t *>(bSt + 3 * B_ARR + off) = il;
-                    } else {
-                        *reinterpret_cast<uint16_t *>(bSt + 0 * B_ARR + off) = (uint16_t)rh;
-                        *reinterpret_cast<uint16_t *>(bSt + 1 * B_ARR + off) = (uint16_t)ih;
-                        *reinterpret_cast<uint16_t *>(bSt + 2 * B_ARR + off) = (uint16_t)rl;
-                        *reinterpret_cast<uint16_t *>(bSt + 3 * B_ARR + off) = (uint16_t)il;
-                    }
-                }
-                tc::fence_proxy_async_smem();
-                __syncthreads();
-                if (tid == 0) {
-                    tc::tc_fence_after();
-                    const uint32_t aB = tc::smem_u32(aSt), bB = tc::smem_u32(bSt);
-                    const uint32_t dR = tmem, dI = tmem + (uint32_t)ncp;
-#pragma unroll
-                    for (int ks = 0; ks < 2; ++ks) {
-                        uint64_t A[4], B[4];
-#pragma unroll
-                        for (int arr = 0; arr < 4; ++arr) {
-                            A[arr] = tc::sdesc(aB + arr * A_ARR + ks * 256, 128, 512);
-                            B[arr] = tc::sdesc(bB + arr * B_ARR + ks * 256, 128, 512);
-                        }
-                        const uint32_t acc = (ch == 0 && ks == 0) ? 0u : 1u;
-                        // Dr = Pr Br - Pi Bi ; Di = Pr Bi + Pi Br ; each as hh + hl + lh
-                        tc::mma<Op::kTF32>(dR, A[0], B[0], idP, acc);
-                        tc::mma<Op::kTF32>(dR, A[0], B[2], idP, 1);
-                        tc::mma<Op::kTF32>(dR, A[2], B[0], idP, 1);
-                        tc::mma<Op::kTF32>(dR, A[1], B[1], idN, 1);
-                        tc::mma<Op::kTF32>(dR, A[1], B[3], idN, 1);
-                        tc::mma<Op::kTF32>(dR, A[3], B[1], idN, 1);
-                        tc::mma<Op::kTF32>(dI, A[0], B[1], idP, acc);
-                        tc::mma<Op::kTF32>(dI, A[0], B[3], idP, 1);
-                        tc::mma<Op::kTF32>(dI, A[2], B[1], idP, 1);
-                        tc::mma<Op::kTF32>(dI, A[1], B[0], idP, 1);
-                        tc::mma<Op::kTF32>(dI, A[1], B[2], idP, 1);
-                        tc::mma<Op::kTF32>(dI, A[3], B[0], idP, 1);
-                    }
-                    tc::mma_commit(&bars[st]);
-                }
-                ++use[st];
-                ++ctr;
+                ++mw[st];
             }
-            if (failed) break;
-            // ---- wait for the accumulator, then the epilogue (one thread per q)
-            {
-                const int st = (ctr - 1) & 1;
-                if (!tc::mbar_wait_bounded(&bars[st], done[st] & 1, kWaitTimeoutNs)) failed = true;
-                ++done[st];
-                if (__syncthreads_or(failed)) {
-                    failed = true;
-                    break;
-                }
-            }
-            tc::tc_fence_after();
-            for (int b = 0; b < nb; ++b) {
-                float gr[NMWP], gi[NMWP];
-#pragma unroll
-                for (int blk = 0; blk < NMWP / 16; ++blk) {
-                    float tmp[16];
-                    tc::tmem_ld16(tmem_row + (uint32_t)(b * NMWP + blk * 16), tmp);
-#pragma unroll
-                    for (int x = 0; x < 16; ++x) gr[blk * 16 + x] = tmp[x];
-                    tc::tmem_ld16(tmem_row + (uint32_t)(ncp + b * NMWP + blk * 16), tmp);
-#pragma unroll
-                    for (int x = 0; x < 16; ++x) gi[blk * 16 + x] = tmp[x];
-                }
-                tc::tmem_wait_ld();
-                float rate = 0.f;
-                if (active) {
-                    const int band = lo + g0 + b;
-                    const float en = a.erel32[(int64_t)ik * W + band];
-                    const float2 *Vq = s.V32 + ikq * W * W;
-                    const float2 *uq = s.u32 + (int64_t)iq * NM * NM;
-                    float2 uu[NM][NM];
-#pragma unroll
-                    for (int x = 0; x < NM; ++x)
-#pragma unroll
-                        for (int y = 0; y < NM; ++y) uu[x][y] = __ldg(uq + x * NM + y);
-                    float wq[NM], nq[NM];
-#pragma unroll
-                    for (int nu = 0; nu < NM; ++nu) {
-                        wq[nu] = __ldg(a.hw32 + (int64_t)iq * NM + nu);
-                        nq[nu] = __ldg(a.n32 + (int64_t)iq * NM + nu);
-                    }
-#pragma unroll
-                    for (int m = 0; m < W; ++m) {
-                        float2 h[NM];
-#pragma unroll
-                        for (int mu = 0; mu < NM; ++mu) {
-                            h[mu] = make_float2(0.f, 0.f);
-#pragma unroll
-                            for (int i = 0; i < W; ++i)
-                                h[mu] = cfmacf(__ldg(Vq + i * W + m), make_float2(gr[mu * W + i], gi[mu * W + i]), h[mu]);
-                        }
-                        const float em = __ldg(a.erel32 + ikq * W + m);
-                        const float fm = __ldg(a.f32 + ikq * W + m);
-#pragma unroll
-                        for (int nu = 0; nu < NM; ++nu) {
-                            const float w = wq[nu];
-                            float2 gv = make_float2(0.f, 0.f);
-#pragma unroll
-                            for (int mu = 0; mu < NM; ++mu) gv = cfmaf(h[mu], uu[mu][nu], gv);
-                            const float g2 = gv.x * gv.x + gv.y * gv.y;
-                            if (s.g2out) {
-                                s.g2out[(((s.g2_base + pair) * nsel + g0 + b) * NM + nu) * W + m] =
-                                    (w >= 0.f) ? (double)g2 * (double)a.scale_inv2 : 0.0;
-                                continue;
-                            }
-                            if (w < 0.f) continue;
-                            const float x1 = (en + w) - em;
-                            const float x2 = (en - w) - em;
-                            float tt = 0.f;
-                            if (fabsf(x1) <= a.ceta32) {
-                                const float y = x1 * a.inv_eta32;
-                                tt += (nq[nu] + fm) * __expf(-y * y);
-                            }
-                            if (fabsf(x2) <= a.ceta32) {
-                                const float y = x2 * a.inv_eta32;
-                                tt += (1.f + nq[nu] - fm) * __expf(-y * y);
-                            }
-                            rate = fmaf(g2, tt, rate);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) rate += __shfl_down_sync(0xffffffffu, rate, o);
-                if (lane == 0) wred[warp * epc::kMaxW + g0 + b] = rate * a.scale_inv2;
-            }
-            tc::tc_fence_before();
-        }
-        __syncthreads();
-        if (!failed && tid < nsel)
-            s.tile_part[tile * epc::kMaxW + tid] =
-                ((double)wred[tid] + (double)wred[epc::kMaxW + tid]) +
-                ((double)wred[2 * epc::kMaxW + tid] + (double)wred[3 * epc::kMaxW + tid]);
+        if (failed) *sfail = 1;
     }
-    // wind down: make sure no MMA is still writing TMEM, then free it
-    for (int st = 0; st < 2; ++st)
-        if (use[st] > done[st]) {
-            if (!tc::mbar_wait_bounded(&bars[st], done[st] & 1, kWaitTimeoutNs)) failed = true;
-            ++done[st];
-        }
-    if (failed && tid == 0) atomicAdd(a.err, 1);
     tc::tc_fence_before();
     __syncthreads();
+    if (tid == 0 && *sfail) atomicAdd(a.err, 1);
     if (warp == 0) tc::tmem_dealloc(tmem, a.tmem_cols);
 }
 
 template <class Op>
-const uint32_t *phase_table(epwi_ctx *c) {
-    const int key = c->L * 8 + c->opt.precision;
+const uint32_t *phase_table(epwi_ctx *c, int *rlog_out) {
     const int TW = Op::kTF32 ? 4 : 2;
+    // replicate the table (copy g serves lanes with lane % R == g) while it stays <= 16 KB;
+    // R = 16 (8-byte entries) or 8 (16-byte entries) makes the lookups bank-conflict free
+    int rlog = Op::kTF32 ? 3 : 4;
+    while (rlog > 0 && (size_t)2 * c->L * (1 << rlog) * TW * 4 > 16384) --rlog;
+    const int key = (c->L * 8 + c->opt.precision) * 8 + rlog;
     if (c->tc_ptab_key != key) {
-        c->tc_ptab.ensure(sizeof(uint32_t) * 2 * c->L * TW);
-        k_phase_split<Op><<<(2 * c->L + 127) / 128, 128, 0, c->stream>>>(c->L, c->ph64.as<double2>(),
+        c->tc_ptab.ensure(sizeof(uint32_t) * 2 * c->L * TW * (1 << rlog));
+        k_phase_split<Op><<<(2 * c->L + 127) / 128, 128, 0, c->stream>>>(c->L, rlog, c->ph64.as<double2>(),
                                                                         c->tc_ptab.as<uint32_t>());
         EPWI_CHECK_LAUNCH();
         c->tc_ptab_key = key;
     }
+    *rlog_out = rlog;
     return c->tc_ptab.as<uint32_t>();
 }
 
-template <class Op, int W, int NM>
+template <class Op, int W, int NM, int RC>
 void launch_tc(epwi_ctx *c, const ScatterArgs &sa, int64_t ntiles) {
-    constexpr int ES = Op::kBytes;
     constexpr int NMWP = (NM * W + 15) / 16 * 16;
     constexpr int TW = Op::kTF32 ? 4 : 2;
+    constexpr int ES = Op::kBytes;
     TcArgs a;
     a.s = sa;
-    a.ghat32 = static_cast<const float2 *>(sa.ghat_raw);
-    a.ptab = phase_table<Op>(c);
+    c->tc_meta.ensure(sizeof(TileMeta) * (ntiles + 1));
+    a.meta = c->tc_meta.as<TileMeta>();
+    if (ntiles > 0) {
+        k_tile_meta<<<(unsigned)((ntiles + 255) / 256), 256, 0, c->stream>>>(
+            ntiles, sa.tiles, sa.kpts, sa.win_lo, sa.win_n, sa.kp_state, sa.s_base, sa.ovr_lo, sa.ovr_nsel,
+            c->tc_meta.as<TileMeta>());
+        EPWI_CHECK_LAUNCH();
+    }
+    a.img = static_cast<const uint8_t *>(sa.ghat_raw);
+    a.ns = sa.nstates_chunk;
+    a.ptab = phase_table<Op>(c, &a.rlog);
     a.erel32 = c->tc_erel.as<float>();
     a.f32 = c->tc_f32.as<float>();
     a.n32 = c->tc_n32.as<float>();
     a.hw32 = c->tc_hw32.as<float>();
     const int e = (Op::kFmt == 0 && !Op::kTF32) ? c->tc_scale_exp : 0;
-    a.scale = std::ldexp(1.0f, e);
     a.scale_inv2 = std::ldexp(1.0f, -2 * e);
     a.ceta32 = (float)sa.ceta;
     a.inv_eta32 = (float)(1.0 / sa.eta);
@@ -541,40 +799,72 @@ void launch_tc(epwi_ctx *c, const ScatterArgs &sa, int64_t ntiles) {
     c->tc_err.ensure(sizeof(int) * 4);
     EPWI_CUDA(cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), c->stream));
     a.err = c->tc_err.as<int>();
-    size_t smem = 2 * 4 * 128 * 64 + 2 * 4 * (size_t)a.ncp_max * 64 +
-                  sizeof(uint32_t) * ((2 * c->L * TW + 1) & ~1) + 16 + 16 + 4 * epc::kMaxW * 4 + 64;
-    auto kern = k_scatter_tc<Op, W, NM>;
-    int dev = c->device, nsm = 0;
-    EPWI_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int twords = 2 * c->L * (1 << a.rlog) * TW;
+    const size_t fixed = 2 * 4 * 128 * 64 + sizeof(uint32_t) * ((twords + 1) & ~1) + 8 * 8 + 16 +
+                         4 * epc::kMaxW * 4 + 64;
+    const size_t bres_bytes = (size_t)a.nchunk * 4 * a.ncp_max * 64;
+    a.bres = (fixed + bres_bytes <= 220 * 1024) ? 1 : 0;
+    size_t smem = fixed + (a.bres ? bres_bytes : 2 * 4 * (size_t)a.ncp_max * 64);
+    auto kern = k_scatter_tc<Op, W, NM, RC>;
+    int nsm = 0;
+    EPWI_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
+    EPWI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     // keep (resident CTAs per SM) x (TMEM columns) <= 512 so that tcgen05.alloc never waits
     int per_sm = 0;
     for (;;) {
         EPWI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        EPWI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem));
+        EPWI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 160, smem));
         EPWI_REQUIRE(per_sm >= 1, EPWI_EUNSUPPORTED, "tensor-core kernel does not fit on an SM");
         if ((uint32_t)per_sm * cols <= 512) break;
         smem += 8 * 1024;
     }
     const int64_t grid = std::min<int64_t>(ntiles, (int64_t)per_sm * nsm);
     if (grid > 0) {
-        kern<<<(unsigned)grid, 128, smem, c->stream>>>(a);
+        kern<<<(unsigned)grid, 160, smem, c->stream>>>(a);
         EPWI_CHECK_LAUNCH();
     }
     c->tc_blocks_per_sm = per_sm;
+    c->stats_tc_grid = grid;
+    c->stats.tc_grid = grid;
+    c->stats.tc_ctas_per_sm = per_sm;
+    c->stats.sm_count = nsm;
+    {
+        cudaFuncAttributes fa;
+        EPWI_CUDA(cudaFuncGetAttributes(&fa, kern));
+        size_t avail = 0;
+        if (cudaOccupancyAvailableDynamicSMemPerBlock(&avail, kern, 1, 160) != cudaSuccess) {
+            (void)cudaGetLastError();
+            avail = 0;
+        }
+        c->stats.tc_regs = fa.numRegs;
+        c->stats.tc_smem = (int64_t)smem;
+        c->stats.tc_smem_avail2 = (int64_t)avail;
+    }
 }
 
 template <class Op>
 void dispatch_tc(epwi_ctx *c, const ScatterArgs &sa, int64_t nt) {
-    const int W = c->nw, NM = c->nm;
-    if (W == 1 && NM == 3) launch_tc<Op, 1, 3>(c, sa, nt);
-    else if (W == 4 && NM == 3) launch_tc<Op, 4, 3>(c, sa, nt);
-    else if (W == 8 && NM == 6) launch_tc<Op, 8, 6>(c, sa, nt);
-    else throw EpwiError{EPWI_EUNSUPPORTED, "split-precision path built for (nw, modes) in {(1,3), (4,3), (8,6)}"};
+    const int W = c->nw, NM = c->nm, r = c->rp_cube_r;
+    if (W == 1 && NM == 3 && r == 1) launch_tc<Op, 1, 3, 1>(c, sa, nt);
+    else if (W == 4 && NM == 3 && r == 1) launch_tc<Op, 4, 3, 1>(c, sa, nt);
+    else if (W == 4 && NM == 3 && r == 2) launch_tc<Op, 4, 3, 2>(c, sa, nt);
+    else if (W == 8 && NM == 6 && r == 3) launch_tc<Op, 8, 6, 3>(c, sa, nt);
+    else if (W == 8 && NM == 6 && r == 1) launch_tc<Op, 8, 6, 1>(c, sa, nt);
+    else
+        throw EpwiError{EPWI_EUNSUPPORTED,
+                        "split-precision path built for (nw, modes, R_p cube half-width) in "
+                        "{(1,3,1), (4,3,1), (4,3,2), (8,6,1), (8,6,3)}"};
 }
 
 }  // namespace
 
-size_t tc_state_bytes(const epwi_ctx *c) { return sizeof(float2) * (size_t)c->nRp * c->nm * c->nw; }
+size_t tc_state_bytes(const epwi_ctx *c) {
+    const int es = c->opt.precision == EPWI_TF32X3 ? 4 : 2;
+    const size_t kc = 64 / es;
+    const size_t nchunk = (c->nRp + kc - 1) / kc;
+    const size_t nmwp = (size_t)(c->nm * c->nw + 15) / 16 * 16;
+    return nchunk * 4 * nmwp * 64;
+}
 
 void tc_tables(epwi_ctx *c) {
     const int64_t nk = c->nk;
@@ -590,20 +880,37 @@ void tc_tables(epwi_ctx *c) {
     EPWI_CHECK_LAUNCH();
 }
 
+namespace {
+template <class Op, int W, int NM, int KG>
+void restage_tc_launch(epwi_ctx *c, const RestageArgs &ra) {
+    uint8_t *img = static_cast<uint8_t *>(ra.ghat_raw);
+    EPWI_CUDA(cudaMemsetAsync(img, 0, tc_state_bytes(c) * (size_t)ra.nstates_chunk, c->stream));
+    const int e = (Op::kFmt == 0 && !Op::kTF32) ? c->tc_scale_exp : 0;
+    dim3 grid((ra.nrow + 127) / 128, (unsigned)((ra.nkp + KG - 1) / KG));
+    const size_t sm = sizeof(float2) * KG * ra.nRe;
+    auto kern = k_restage_tc<Op, W, NM, KG>;
+    if (sm > 48 * 1024)
+        EPWI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    kern<<<grid, 128, sm, c->stream>>>(ra, img, ra.nstates_chunk, std::ldexp(1.0f, e));
+    EPWI_CHECK_LAUNCH();
+}
+
+template <class Op>
+void restage_dispatch(epwi_ctx *c, const RestageArgs &ra) {
+    if (c->nw == 1 && c->nm == 3) restage_tc_launch<Op, 1, 3, 8>(c, ra);
+    else if (c->nw == 4 && c->nm == 3) restage_tc_launch<Op, 4, 3, 8>(c, ra);
+    else if (c->nw == 8 && c->nm == 6) restage_tc_launch<Op, 8, 6, 4>(c, ra);
+    else throw EpwiError{EPWI_EUNSUPPORTED, "split-precision path built for (nw, modes) in {(1,3), (4,3), (8,6)}"};
+}
+}  // namespace
+
 void tc_restage(epwi_ctx *c, const RestageArgs &ra) {
-    float2 *out = static_cast<float2 *>(ra.ghat_raw);
-    auto go = [&](auto kern, int KG) {
-        dim3 grid((ra.nrow + 127) / 128, (unsigned)((ra.nkp + KG - 1) / KG));
-        const size_t sm = sizeof(float2) * KG * ra.nRe;
-        if (sm > 48 * 1024)
-            EPWI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        kern<<<grid, 128, sm, c->stream>>>(ra, out);
-        EPWI_CHECK_LAUNCH();
-    };
-    if (ra.W == 1) go(k_restage_f32<1, 8>, 8);
-    else if (ra.W == 4) go(k_restage_f32<4, 8>, 8);
-    else if (ra.W == 8) go(k_restage_f32<8, 4>, 4);
-    else throw EpwiError{EPWI_EUNSUPPORTED, "split-precision Re->k stage built for nw in {1, 4, 8}"};
+    switch (c->opt.precision) {
+        case EPWI_FP16X3: restage_dispatch<OpF16>(c, ra); break;
+        case EPWI_BF16X3: restage_dispatch<OpBF16>(c, ra); break;
+        case EPWI_TF32X3: restage_dispatch<OpTF32>(c, ra); break;
+        default: throw EpwiError{EPWI_EINVAL, "not a split-precision mode"};
+    }
 }
 
 void tc_scatter(epwi_ctx *c, const ScatterArgs &sa, int64_t ntiles) {

@@ -3,11 +3,10 @@
 // and per-chunk pair lists.
 //
 // Sieve: a pair (k, q) is kept when some window band n at k, some band m at k+q, some
-// kept mode nu and a sign s satisfy |(eps_nk + s hbar omega_qnu) - eps_m,k+q| <= c eta,
-// evaluated in FP64 (the same rounding order as the oracle).  An FP32 prefilter
-// |eps_nk - eps_m,k+q| <= max_nu(omega) + c eta + 1e-4 eV rejects most candidates first;
-// it can only pass extra candidates to the exact test, never drop a kept one (FP32
-// rounding of energies below 40 eV is < 3e-6 eV).
+// kept mode nu and a sign s satisfy |(eps_nk + s hbar omega_qnu) - eps_m,k+q| <= c eta.
+// Each candidate is first evaluated in FP32 with a rigorous bound delta on the rounding
+// error; only candidates whose nearest |x| lies within delta of c eta are re-evaluated in
+// FP64 in the oracle's rounding order, so every decision equals the FP64 one.
 #include "epwi_internal.cuh"
 
 namespace {
@@ -116,22 +115,41 @@ struct SieveArgs {
     const double *eps;
     const float *eps32;
     const double *hw;
+    const float *hw32;       // per mode, -1 for dropped modes
     const float *hwmax32;
     double omega_min, ceta;
-    float lim_extra;   // c eta + prefilter margin
+    float ceta32, delta32;   // delta32 bounds |x_fp32 - x_fp64| for every candidate
+    float lim_extra;         // c eta + delta32
 };
 
-__device__ __forceinline__ bool pair_valid(const SieveArgs &a, int64_t ik, int nsel,
-                                           const double *en, const float *en32, int64_t iq) {
+// Decision for one candidate (k, q).  FP32 evaluates x = (e_n + s w) - e_m for every
+// (n, m, nu, s); a value inside c eta - delta (outside c eta + delta) is decided in FP32,
+// anything closer to the boundary is re-evaluated in FP64 with the oracle's rounding order,
+// so the outcome equals an FP64 evaluation.
+__device__ __forceinline__ bool pair_valid(const SieveArgs &a, int nsel, const double *en,
+                                           const float *en32, int64_t iq, int64_t ikq) {
     const float hm = a.hwmax32[iq];
     if (hm < 0.f) return false;
     const float lim = hm + a.lim_extra;
-    const int64_t ikq = kplusq(a.g, ik, iq);
+    const float inner = a.ceta32 - a.delta32, outer = a.ceta32 + a.delta32;
+    bool ambiguous = false;
     for (int m = 0; m < a.W; ++m) {
         const float em32 = a.eps32[ikq * a.W + m];
-        bool near = false;
-        for (int n = 0; n < nsel; ++n) near |= fabsf(en32[n] - em32) <= lim;
-        if (!near) continue;
+        for (int n = 0; n < nsel; ++n) {
+            const float d = en32[n] - em32;
+            if (!(fabsf(d) <= lim)) continue;
+            for (int nu = 0; nu < a.Nm; ++nu) {
+                const float w = a.hw32[iq * a.Nm + nu];
+                if (w < 0.f) continue;
+                const float x1 = fabsf(d + w), x2 = fabsf(d - w);
+                const float xm = fminf(x1, x2);
+                if (xm <= inner) return true;
+                if (xm <= outer) ambiguous = true;
+            }
+        }
+    }
+    if (!ambiguous) return false;
+    for (int m = 0; m < a.W; ++m) {
         const double em = a.eps[ikq * a.W + m];
         for (int nu = 0; nu < a.Nm; ++nu) {
             const double w = a.hw[iq * a.Nm + nu];
@@ -155,6 +173,17 @@ __device__ __forceinline__ void load_window(const SieveArgs &a, int ik, int lo, 
     __syncthreads();
 }
 
+// Candidate order shared by count and fill: the (i2, i3) plane index p runs over blocks of
+// blockDim.x (one p per thread), and for each block i1 runs 0..N1-1.  k+q is updated
+// incrementally (no division per candidate).
+__device__ __forceinline__ int64_t plane_kq(const GridInfo &g, int ka2, int ka3, int64_t p) {
+    const int i2 = (int)(p / g.n3), i3 = (int)(p - (int64_t)i2 * g.n3);
+    int b2 = ka2 + i2, b3 = ka3 + i3;
+    if (b2 >= g.n2) b2 -= g.n2;
+    if (b3 >= g.n3) b3 -= g.n3;
+    return (int64_t)b2 * g.n3 + b3;
+}
+
 __global__ void __launch_bounds__(256) k_sieve_count(SieveArgs a, int64_t nkp,
                                                      const int *__restrict__ kpts,
                                                      const int *__restrict__ lo,
@@ -166,15 +195,28 @@ __global__ void __launch_bounds__(256) k_sieve_count(SieveArgs a, int64_t nkp,
     const int ik = kpts[blockIdx.x];
     const int nsel = cnt[ik];
     load_window(a, ik, lo[ik], nsel, en, en32);
-    const int64_t nq = (int64_t)a.g.n1 * a.g.n2 * a.g.n3;
+    int ka1, ka2, ka3;
+    grid_coords(a.g, ik, ka1, ka2, ka3);
+    const int64_t nplane = (int64_t)a.g.n2 * a.g.n3;
     int64_t c = 0;
-    for (int64_t iq = threadIdx.x; iq < nq; iq += blockDim.x) c += pair_valid(a, ik, nsel, en, en32, iq);
+    for (int64_t pb = 0; pb < nplane; pb += blockDim.x) {
+        const int64_t p = pb + threadIdx.x;
+        if (p >= nplane) break;
+        const int64_t kqp = plane_kq(a.g, ka2, ka3, p);
+        int b1 = ka1;
+        for (int i1 = 0; i1 < a.g.n1; ++i1) {
+            const int64_t iq = (int64_t)i1 * nplane + p;
+            const int64_t ikq = (int64_t)b1 * nplane + kqp;
+            c += pair_valid(a, nsel, en, en32, iq, ikq);
+            if (++b1 == a.g.n1) b1 = 0;
+        }
+    }
     int64_t tot;
     block_excl_scan(c, sm, tot);
     if (threadIdx.x == 0) counts[blockIdx.x] = tot;
 }
 
-// Writes the kept q of k-points kp0 + blockIdx.x in ascending order.
+// Writes the kept q of k-points kp0 + blockIdx.x in the candidate order of k_sieve_count.
 __global__ void __launch_bounds__(256) k_sieve_fill(SieveArgs a, int64_t kp0,
                                                     const int *__restrict__ kpts,
                                                     const int *__restrict__ lo,
@@ -188,16 +230,26 @@ __global__ void __launch_bounds__(256) k_sieve_fill(SieveArgs a, int64_t kp0,
     const int ik = kpts[kp];
     const int nsel = cnt[ik];
     load_window(a, ik, lo[ik], nsel, en, en32);
-    const int64_t nq = (int64_t)a.g.n1 * a.g.n2 * a.g.n3;
+    int ka1, ka2, ka3;
+    grid_coords(a.g, ik, ka1, ka2, ka3);
+    const int64_t nplane = (int64_t)a.g.n2 * a.g.n3;
     int64_t base = kp_pairs[kp] - kp_pairs[kp0];
     const int64_t end = kp_pairs[kp + 1] - kp_pairs[kp0];
-    for (int64_t q0 = 0; q0 < nq; q0 += blockDim.x) {
-        const int64_t iq = q0 + threadIdx.x;
-        const int64_t v = (iq < nq) ? (int64_t)pair_valid(a, ik, nsel, en, en32, iq) : 0;
-        int64_t tot;
-        const int64_t off = block_excl_scan(v, sm, tot);
-        if (v && base + off < end) pairs[base + off] = (int)iq;
-        base += tot;
+    for (int64_t pb = 0; pb < nplane; pb += blockDim.x) {
+        const int64_t p = pb + threadIdx.x;
+        const bool inb = p < nplane;
+        const int64_t kqp = inb ? plane_kq(a.g, ka2, ka3, p) : 0;
+        int b1 = ka1;
+        for (int i1 = 0; i1 < a.g.n1; ++i1) {
+            const int64_t iq = (int64_t)i1 * nplane + p;
+            const int64_t ikq = (int64_t)b1 * nplane + kqp;
+            const int64_t v = inb ? (int64_t)pair_valid(a, nsel, en, en32, iq, ikq) : 0;
+            int64_t tot;
+            const int64_t off = block_excl_scan(v, sm, tot);
+            if (v && base + off < end) pairs[base + off] = (int)iq;
+            base += tot;
+            if (++b1 == a.g.n1) b1 = 0;
+        }
     }
 }
 
@@ -209,10 +261,14 @@ SieveArgs make_sieve_args(epwi_ctx *c) {
     a.eps = c->eps.as<double>();
     a.eps32 = c->eps32.as<float>();
     a.hw = c->hw.as<double>();
+    a.hw32 = c->hw32.as<float>();
     a.hwmax32 = c->hwmax32.as<float>();
     a.omega_min = c->opt.omega_min_eV;
     a.ceta = c->opt.sieve_c * c->eta;
-    a.lim_extra = (float)(a.ceta + 1e-4);
+    a.ceta32 = (float)a.ceta;
+    // FP32 rounding of |e| <= E and of the two operations is < 2^-24 (3E + |w| + |x|) < 4e-7 E'
+    a.delta32 = (float)(1e-6 + 4e-7 * (2.0 * c->eabs_max + 1.0));
+    a.lim_extra = (float)(a.ceta + a.delta32 + 1e-5);
     return a;
 }
 

@@ -50,7 +50,9 @@ class epwi_stats(C.Structure):
                 ("n_tiles", C.c_int64), ("n_chunks", C.c_int64), ("ms_eigs", C.c_double),
                 ("ms_sieve", C.c_double), ("ms_restage", C.c_double), ("ms_scatter", C.c_double),
                 ("ms_reduce", C.c_double), ("restage_bytes", C.c_int64),
-                ("scatter_flops", C.c_double), ("precision", C.c_int32)]
+                ("scatter_flops", C.c_double), ("precision", C.c_int32), ("sm_count", C.c_int32),
+                ("tc_grid", C.c_int64), ("tc_ctas_per_sm", C.c_int32), ("tc_regs", C.c_int32),
+                ("tc_smem", C.c_int64), ("tc_smem_avail2", C.c_int64)]
 
 
 def _load() -> C.CDLL:
