@@ -7,7 +7,8 @@
 //       Pr_hi, Pi_hi, Pr_lo, Pi_lo (x = hi + lo, hi = round(x), lo = round(x - hi));
 //   B = ghat(k) (Rp x columns), columns (band n, mode-component mu, Wannier i), split alike;
 //   D = A B in TMEM, FP32: Dr = Pr Br - Pi Bi, Di = Pr Bi + Pi Br, each product as
-//       hi*hi + hi*lo + lo*hi (the lo*lo term, ~2^-22 relative for fp16/tf32, is dropped).
+//       hi*hi + hi*lo + lo*hi (the lo*lo term, ~2^-22 relative for fp16/tf32, is dropped),
+//       issued as four wide MMAs per K step against B concatenated along N (see k_scatter_tc).
 // K (= Rp) is streamed in chunks of 64 bytes per row through a two-stage shared-memory ring:
 // the threads write chunk c+1 while the tensor core multiplies chunk c.  After the last
 // chunk every thread loads its row of D (tcgen05.ld), rotates it by V(k+q)^dag and u(q) in
@@ -137,7 +138,7 @@ __host__ __device__ __forceinline__ uint32_t cm_off(int c, int k) {
 // Re->k stage for the split-precision path.  ghat(k)[rp][mu][i][n] = sum_j [sum_Re e^{ik.Re}
 // gw32] V32_jn is accumulated in FP32, scaled by 2^e, split into hi + lo and written as the
 // B operand image of the tensor-core kernel:
-//   img[ch][arr][state][NMWP rows][64 bytes]  (arr: Br_hi, Bi_hi, Br_lo, Bi_lo),
+//   img[ch][arr][state][NMWP rows][64 bytes]  (arr: Br_hi, Bi_hi, Br_lo, Bi_lo, -Bi_hi, -Bi_lo),
 // row = mu*W + i (rows NMW..NMWP-1 and K beyond nRp stay zero), K = rp - ch*KC.
 template <class Op, int W, int NM, int KG>
 __global__ void __launch_bounds__(128) k_restage_tc(RestageArgs a, uint8_t *__restrict__ img,
@@ -195,14 +196,17 @@ __global__ void __launch_bounds__(128) k_restage_tc(RestageArgs a, uint8_t *__re
             float2 o = make_float2(0.f, 0.f);
 #pragma unroll
             for (int j = 0; j < W; ++j) o = cfmaf(acc[q][j], Vk[j * W + lo + np], o);
-            uint32_t w4[4];
-            split2f<Op>(o.x * scale, w4[0], w4[2]);
-            split2f<Op>(o.y * scale, w4[1], w4[3]);
+            uint32_t w6[6];
+            split2f<Op>(o.x * scale, w6[0], w6[2]);
+            split2f<Op>(o.y * scale, w6[1], w6[3]);
+            const uint32_t sign = ES == 4 ? 0x80000000u : 0x8000u;
+            w6[4] = w6[1] ^ sign;
+            w6[5] = w6[3] ^ sign;
 #pragma unroll
-            for (int arr = 0; arr < 4; ++arr) {
-                uint8_t *dst = img + ((size_t)(ch * 4 + arr) * ns + (s0 + np)) * BLK + eoff;
-                if constexpr (ES == 4) *reinterpret_cast<uint32_t *>(dst) = w4[arr];
-                else *reinterpret_cast<uint16_t *>(dst) = (uint16_t)w4[arr];
+            for (int arr = 0; arr < 6; ++arr) {
+                uint8_t *dst = img + ((size_t)(ch * 6 + arr) * ns + (s0 + np)) * BLK + eoff;
+                if constexpr (ES == 4) *reinterpret_cast<uint32_t *>(dst) = w6[arr];
+                else *reinterpret_cast<uint16_t *>(dst) = (uint16_t)w6[arr];
             }
         }
     }
@@ -248,6 +252,8 @@ struct TcArgs {
     int nbg;                       // bands per column group
     int ncp_max;                   // B rows per stage
     int bres;                      // 1: B of one (k-point, band group) resident in nchunk slots
+    int nsa;                       // A stages in TMEM
+    uint32_t a_col0;               // first TMEM column of the A stages (after the accumulator)
     uint32_t tmem_cols;
     int64_t ntiles;
     int *err;                      // [0]: timed-out waits
@@ -264,17 +270,29 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 
 __device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
-// Issues the four B-operand bulk copies of (tile, band group g0, chunk ch) into a stage.
+// B slot of one chunk: V1 = [Br_hi | Bi_hi | Br_lo | Bi_lo] then V2 = [-Bi_hi | Br_hi | -Bi_lo | Br_lo],
+// each part ncp rows of 64 bytes; these are the image arrays in this order.
+__constant__ int kSlotArr[8] = {0, 1, 2, 3, 4, 0, 5, 2};
+
+// Issues the eight bulk copies of (k-point state s0, band group g0, chunk ch) into a slot
+// (bytes counted on bar by the caller's expect_tx).
 template <int NMWP>
-__device__ __forceinline__ void issue_b(const TcArgs &a, const TileMeta &m, int g0, int ch, uint8_t *bStage,
-                                        uint32_t B_ARR, uint64_t *bar) {
-    const int nb = min(a.nbg, m.nsel - g0);
+__device__ __forceinline__ void copy_b(const TcArgs &a, long long s0, int g0, int nb, int ch, uint8_t *slot,
+                                       uint64_t *bar) {
     const uint32_t bytes = (uint32_t)nb * NMWP * 64;
-    tc::mbar_arrive_expect_tx(bar, 4 * bytes);
 #pragma unroll
-    for (int arr = 0; arr < 4; ++arr)
-        tc::bulk_g2s(bStage + arr * B_ARR,
-                     a.img + ((size_t)(ch * 4 + arr) * a.ns + ((size_t)m.s0 + g0)) * (NMWP * 64), bytes, bar);
+    for (int pos = 0; pos < 8; ++pos)
+        tc::bulk_g2s(slot + pos * bytes,
+                     a.img + ((size_t)(ch * 6 + kSlotArr[pos]) * a.ns + ((size_t)s0 + g0)) * (NMWP * 64), bytes,
+                     bar);
+}
+
+template <int NMWP>
+__device__ __forceinline__ void issue_b(const TcArgs &a, const TileMeta &m, int g0, int ch, uint8_t *slot,
+                                        uint64_t *bar) {
+    const int nb = min(a.nbg, m.nsel - g0);
+    tc::mbar_arrive_expect_tx(bar, 8u * nb * NMWP * 64);
+    copy_b<NMWP>(a, m.s0, g0, nb, ch, slot, bar);
 }
 
 // Warp-specialised CTA of 160 threads: warps 0-3 are producers (one q row each: phase
@@ -282,8 +300,9 @@ __device__ __forceinline__ void issue_b(const TcArgs &a, const TileMeta &m, int 
 // thread (B operand bulk copies, tcgen05.mma issue and commit).  B either stays resident for
 // a (k-point, band group) across consecutive tiles (reloaded only when it changes) or, when
 // it does not fit, streams through a two-slot ring one chunk ahead.  They communicate
-// through mbarriers only: a_full (128 arrivals), mma_done (tcgen05.commit), b_full (bulk-copy
-// bytes) and acc_empty (128 arrivals after the epilogue read TMEM).
+// through mbarriers only: a_full (one elected arrival per producer warp), mma_done
+// (tcgen05.commit), b_full (bulk-copy bytes) and acc_empty (per-warp arrivals after the
+// epilogue read TMEM).  A streams through 2 or 3 shared-memory stages.
 // One CTA per SM: the shared-memory footprint and the per-sub-partition register file
 // (warps w and w+4 of two co-resident 5-warp CTAs share a sub-partition) rule out a second.
 template <class Op, int W, int NM, int RC>
@@ -293,34 +312,34 @@ __global__ void __maxnreg__(255) k_scatter_tc(TcArgs a) {
     constexpr int EPV = 16 / ES;                // elements per 16-byte core-matrix row
     constexpr int NMW = NM * W;
     constexpr int NMWP = (NMW + 15) / 16 * 16;  // columns per band, padded to the MMA N granule
-    constexpr uint32_t A_ARR = 128 * 64;        // bytes per A operand per stage
+    constexpr uint32_t A_COLS = 16;             // TMEM columns per A operand per stage (64 bytes)
     constexpr int TW = Op::kTF32 ? 4 : 2;       // 32-bit words per table entry
     constexpr bool PRE = (W * W + NM * NM) <= 32;   // keep the epilogue operands in registers
     const ScatterArgs &s = a.s;
     extern __shared__ __align__(128) uint8_t smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t B_ARR = (uint32_t)a.ncp_max * 64;
-    uint8_t *sA = smem;
-    uint8_t *sB = sA + 2 * 4 * A_ARR;
-    uint32_t *sT = reinterpret_cast<uint32_t *>(sB + (a.bres ? a.nchunk : 2) * 4 * B_ARR);
+    const uint32_t B_SLOT = 8u * (uint32_t)a.ncp_max * 64;   // one chunk of V1 and V2
+    const int NSA = a.nsa;                      // A stages in TMEM (2 or 3)
+    uint8_t *sB = smem;
+    uint32_t *sT = reinterpret_cast<uint32_t *>(sB + (a.bres ? a.nchunk : 2) * B_SLOT);
     const int L = s.g.L;
     const int twords = 2 * L * (1 << a.rlog) * TW;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sT + ((twords + 1) & ~1));
-    uint64_t *a_full = bars, *mma_done = bars + 2, *b_full = bars + 4, *acc_empty = bars + 6,
-             *drained = bars + 7;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 8);
+    uint64_t *a_full = bars, *mma_done = bars + 3, *b_full = bars + 6, *acc_empty = bars + 8,
+             *drained = bars + 9;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 10);
     volatile int *sfail = reinterpret_cast<volatile int *>(tslot + 1);
     float *wred = reinterpret_cast<float *>(tslot + 4);   // [4][kMaxW]
 
     for (int i = tid; i < twords; i += blockDim.x) sT[i] = a.ptab[i];
     if (tid == 0) {
-        tc::mbar_init(&a_full[0], 128);
-        tc::mbar_init(&a_full[1], 128);
-        tc::mbar_init(&mma_done[0], 1);
-        tc::mbar_init(&mma_done[1], 1);
+        for (int i = 0; i < 3; ++i) {
+            tc::mbar_init(&a_full[i], 4);     // one elected arrival per producer warp
+            tc::mbar_init(&mma_done[i], 1);
+        }
         tc::mbar_init(&b_full[0], 1);
         tc::mbar_init(&b_full[1], 1);
-        tc::mbar_init(&acc_empty[0], 128);
+        tc::mbar_init(&acc_empty[0], 4);
         tc::mbar_init(drained, 1);
         *sfail = 0;
         tc::fence_mbar_init();
@@ -333,14 +352,15 @@ __global__ void __maxnreg__(255) k_scatter_tc(TcArgs a) {
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = *tslot;
+    const uint32_t tmem_a = tmem + a.a_col0;     // A stages: NSA x 4 operands x 16 columns
     const int64_t t_begin = blockIdx.x * a.ntiles / gridDim.x;
     const int64_t t_end = (blockIdx.x + 1) * a.ntiles / gridDim.x;
 
     if (warp == 4) {
         // ------------------------------------------------------------ control thread
         if (lane == 0) {
-            uint32_t aph[2] = {0, 0}, bph[2] = {0, 0}, bpend[2] = {0, 0};
-            uint32_t mc[2] = {0, 0}, mw[2] = {0, 0}, eph = 0;
+            uint32_t aph[3] = {0, 0, 0}, bph[2] = {0, 0}, bpend[2] = {0, 0};
+            uint32_t mc[3] = {0, 0, 0}, mw[3] = {0, 0, 0}, eph = 0;
             uint32_t ctr = 0;
             bool failed = false, first = true;
             uint32_t dph = 0;
@@ -353,7 +373,7 @@ __global__ void __maxnreg__(255) k_scatter_tc(TcArgs a) {
                     dph ^= 1;
                     return;
                 }
-                for (int st = 0; st < 2; ++st)
+                for (int st = 0; st < NSA; ++st)
                     while (mc[st] > mw[st]) {
                         if (!tc::mbar_wait_bounded(&mma_done[st], mw[st] & 1, kWaitTimeoutNs)) failed = true;
                         ++mw[st];
@@ -364,7 +384,7 @@ __global__ void __maxnreg__(255) k_scatter_tc(TcArgs a) {
             int pg = 0, pc = 0;
             TileMeta pm;
             auto prefetch = [&](int st2) {
-                issue_b<NMWP>(a, pm, pg, pc, sB + st2 * 4 * B_ARR, B_ARR, &b_full[st2]);
+                issue_b<NMWP>(a, pm, pg, pc, sB + st2 * B_SLOT, &b_full[st2]);
                 ++bpend[st2];
                 if (++pc == a.nchunk) {
                     pc = 0;
@@ -385,20 +405,13 @@ __global__ void __maxnreg__(255) k_scatter_tc(TcArgs a) {
                 const TileMeta m = a.meta[tile];
                 for (int g0 = 0; g0 < m.nsel && !failed; g0 += a.nbg) {
                     const int ncp = min(a.nbg, m.nsel - g0) * NMWP;
-                    const uint32_t idP = tc::idesc(Op::kFmt, 128, ncp, false);
-                    const uint32_t idN = tc::idesc(Op::kFmt, 128, ncp, true);
+                    const uint32_t id4 = tc::idesc(Op::kFmt, 128, 4 * ncp, false);
+                    const uint32_t id2 = tc::idesc(Op::kFmt, 128, 2 * ncp, false);
                     if (a.bres && (m.kpl != tag_kp || g0 != tag_g0)) {
                         drain_mma();   // no MMA may still read the old operand
                         const int nb = min(a.nbg, m.nsel - g0);
-                        const uint32_t bytes = (uint32_t)nb * NMWP * 64;
-                        tc::mbar_arrive_expect_tx(&b_full[0], 4 * bytes * a.nchunk);
-                        for (int ch = 0; ch < a.nchunk; ++ch)
-#pragma unroll
-                            for (int arr = 0; arr < 4; ++arr)
-                                tc::bulk_g2s(sB + (ch * 4 + arr) * B_ARR,
-                                             a.img + ((size_t)(ch * 4 + arr) * a.ns + ((size_t)m.s0 + g0)) *
-                                                         (NMWP * 64),
-                                             bytes, &b_full[0]);
+                        tc::mbar_arrive_expect_tx(&b_full[0], 8u * nb * NMWP * 64 * a.nchunk);
+                        for (int ch = 0; ch < a.nchunk; ++ch) copy_b<NMWP>(a, m.s0, g0, nb, ch, sB + ch * B_SLOT, &b_full[0]);
                         if (!tc::mbar_wait_bounded(&b_full[0], bph[0], kWaitTimeoutNs)) failed = true;
                         bph[0] ^= 1;
                         tag_kp = m.kpl;
@@ -411,7 +424,7 @@ __global__ void __maxnreg__(255) k_scatter_tc(TcArgs a) {
                     }
                     first = false;
                     for (int ch = 0; ch < a.nchunk && !failed; ++ch) {
-                        const int st = ctr & 1;
+                        const int st = ctr % NSA;   // A stage; streaming mode has NSA = 2 = B slots
                         if (!tc::mbar_wait_bounded(&a_full[st], aph[st], kWaitTimeoutNs)) failed = true;
                         aph[st] ^= 1;
                         if (!a.bres) {
@@ -421,31 +434,23 @@ __global__ void __maxnreg__(255) k_scatter_tc(TcArgs a) {
                         }
                         if (failed) break;
                         tc::tc_fence_after();
-                        const uint32_t aB = tc::smem_u32(sA + st * 4 * A_ARR);
-                        const uint32_t bB = tc::smem_u32(sB + (a.bres ? ch : st) * 4 * B_ARR);
-                        const uint32_t dR = tmem, dI = tmem + (uint32_t)ncp;
+                        const uint32_t aT = tmem_a + (uint32_t)(st * 4 * A_COLS);
+                        const uint32_t bV1 = tc::smem_u32(sB + (a.bres ? ch : st) * B_SLOT);
+                        const uint32_t bV2 = bV1 + 4u * (uint32_t)ncp * 64;
 #pragma unroll
                         for (int ks = 0; ks < 2; ++ks) {
-                            uint64_t A[4], B[4];
-#pragma unroll
-                            for (int arr = 0; arr < 4; ++arr) {
-                                A[arr] = tc::sdesc(aB + arr * A_ARR + ks * 256, 128, 512);
-                                B[arr] = tc::sdesc(bB + arr * B_ARR + ks * 256, 128, 512);
-                            }
+                            // A in TMEM: Pr_hi, Pi_hi, Pr_lo, Pi_lo; 32 bytes of K per MMA
+                            const uint32_t Arh = aT + ks * 8, Aih = aT + A_COLS + ks * 8;
+                            const uint32_t Arl = aT + 2 * A_COLS + ks * 8, Ail = aT + 3 * A_COLS + ks * 8;
+                            const uint64_t B1 = tc::sdesc(bV1 + ks * 256, 128, 512);
+                            const uint64_t B2 = tc::sdesc(bV2 + ks * 256, 128, 512);
                             const uint32_t acc = (ch == 0 && ks == 0) ? 0u : 1u;
-                            // Dr = Pr Br - Pi Bi ; Di = Pr Bi + Pi Br ; each as hh + hl + lh
-                            tc::mma<Op::kTF32>(dR, A[0], B[0], idP, acc);
-                            tc::mma<Op::kTF32>(dR, A[0], B[2], idP, 1);
-                            tc::mma<Op::kTF32>(dR, A[2], B[0], idP, 1);
-                            tc::mma<Op::kTF32>(dR, A[1], B[1], idN, 1);
-                            tc::mma<Op::kTF32>(dR, A[1], B[3], idN, 1);
-                            tc::mma<Op::kTF32>(dR, A[3], B[1], idN, 1);
-                            tc::mma<Op::kTF32>(dI, A[0], B[1], idP, acc);
-                            tc::mma<Op::kTF32>(dI, A[0], B[3], idP, 1);
-                            tc::mma<Op::kTF32>(dI, A[2], B[1], idP, 1);
-                            tc::mma<Op::kTF32>(dI, A[1], B[0], idP, 1);
-                            tc::mma<Op::kTF32>(dI, A[1], B[2], idP, 1);
-                            tc::mma<Op::kTF32>(dI, A[3], B[0], idP, 1);
+                            // D = [Dr_hi | Di_hi | Dr_lo | Di_lo]:  Pr_hi V1 + Pi_hi V2 fills all four
+                            // (hi*hi and hi*lo), Pr_lo V1 + Pi_lo V2 on the first half adds lo*hi.
+                            tc::mma_ta<Op::kTF32>(tmem, Arh, B1, id4, acc);
+                            tc::mma_ta<Op::kTF32>(tmem, Aih, B2, id4, 1);
+                            tc::mma_ta<Op::kTF32>(tmem, Arl, B1, id2, 1);
+                            tc::mma_ta<Op::kTF32>(tmem, Ail, B2, id2, 1);
                         }
                         tc::mma_commit(&mma_done[st]);
                         ++mc[st];
@@ -484,8 +489,7 @@ __global__ void __maxnreg__(255) k_scatter_tc(TcArgs a) {
         constexpr int NCH = (NRP + KC - 1) / KC;    // K chunks (compile time)
         const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);
         const int g = lane & ((1 << a.rlog) - 1);
-        const uint32_t rowoff = (uint32_t)((tid >> 3) * 4) * 128 + (tid & 7) * 16;
-        uint32_t used[2] = {0, 0}, mw[2] = {0, 0};
+        uint32_t used[3] = {0, 0, 0}, mw[3] = {0, 0, 0};
         uint32_t ctr = 0;
         bool failed = false;
         const unsigned n1 = s.g.n1, n2 = s.g.n2, n3 = s.g.n3;
@@ -544,7 +548,7 @@ __global__ void __maxnreg__(255) k_scatter_tc(TcArgs a) {
                 }
 #pragma unroll
                 for (int ch = 0; ch < NCH; ++ch) {
-                    const int st = ctr & 1;
+                    const int st = ctr % NSA;
                     if (used[st] > mw[st]) {
                         if (!tc::mbar_wait_bounded(&mma_done[st], mw[st] & 1, kWaitTimeoutNs)) failed = true;
                         ++mw[st];
@@ -553,6 +557,7 @@ __global__ void __maxnreg__(255) k_scatter_tc(TcArgs a) {
                         failed = true;
                         break;
                     }
+                    tc::tc_fence_after();   // the stage's previous MMAs have completed
                     // The tables are re-defined (empty asm) at every chunk so that the compiler
                     // forms each chunk's indices inside the chunk instead of hoisting all of them.
 #pragma unroll
@@ -562,7 +567,7 @@ __global__ void __maxnreg__(255) k_scatter_tc(TcArgs a) {
                     // ---- A: phases of this thread's q for R_p = ch*KC .. ch*KC+KC-1.  Every index
                     // is independent (compile-time (i12, i3)); K beyond nRp reads entry 0, which
                     // meets zero B rows; rows of inactive threads are never read back.
-                    uint8_t *aSt = sA + st * 4 * A_ARR;
+                    const uint32_t aT = tmem_a + ((uint32_t)(warp * 32) << 16) + (uint32_t)(st * 4 * A_COLS);
 #pragma unroll
                     for (int kb = 0; kb < 4; ++kb) {
                         uint32_t e[EPV][TW];
@@ -603,12 +608,13 @@ __global__ void __maxnreg__(255) k_scatter_tc(TcArgs a) {
                             for (int q = 0; q < 4; ++q) v[q] = make_uint4(w4[q][0], w4[q][1], w4[q][2], w4[q][3]);
                         }
 #pragma unroll
-                        for (int arr = 0; arr < 4; ++arr)
-                            *reinterpret_cast<uint4 *>(aSt + arr * A_ARR + rowoff + kb * 128) = v[arr];
+                        for (int arr = 0; arr < 4; ++arr) tc::tmem_st4(aT + (uint32_t)(arr * A_COLS + kb * 4), v[arr]);
                         asm volatile("" ::: "memory");   // keep one 16-byte row block in flight
                     }
-                    tc::fence_proxy_async_smem();
-                    mbar_arrive(&a_full[st]);
+                    tc::tmem_wait_st();
+                    tc::tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&a_full[st]);
                     ++used[st];
                     ++ctr;
                 }
@@ -643,7 +649,7 @@ __global__ void __maxnreg__(255) k_scatter_tc(TcArgs a) {
                 }
                 // ---- accumulator ready (the last commit covers all MMAs of the group)
                 {
-                    const int st = (ctr - 1) & 1;
+                    const int st = (ctr - 1) % NSA;
                     if (!tc::mbar_wait_bounded(&mma_done[st], mw[st] & 1, kWaitTimeoutNs)) failed = true;
                     ++mw[st];
                     if (failed) break;
@@ -653,18 +659,22 @@ __global__ void __maxnreg__(255) k_scatter_tc(TcArgs a) {
                     float gr[NMWP], gi[NMWP];
 #pragma unroll
                     for (int blk = 0; blk < NMWP / 16; ++blk) {
-                        float tmp[16];
-                        tc::tmem_ld16(tmem_row + (uint32_t)(b * NMWP + blk * 16), tmp);
+                        float t0[16], t1[16];
+                        const uint32_t c0 = tmem_row + (uint32_t)(b * NMWP + blk * 16);
+                        tc::tmem_ld16(c0, t0);
+                        tc::tmem_ld16(c0 + 2 * ncp, t1);
 #pragma unroll
-                        for (int x = 0; x < 16; ++x) gr[blk * 16 + x] = tmp[x];
-                        tc::tmem_ld16(tmem_row + (uint32_t)(ncp + b * NMWP + blk * 16), tmp);
+                        for (int x = 0; x < 16; ++x) gr[blk * 16 + x] = t0[x] + t1[x];
+                        tc::tmem_ld16(c0 + ncp, t0);
+                        tc::tmem_ld16(c0 + 3 * ncp, t1);
 #pragma unroll
-                        for (int x = 0; x < 16; ++x) gi[blk * 16 + x] = tmp[x];
+                        for (int x = 0; x < 16; ++x) gi[blk * 16 + x] = t0[x] + t1[x];
                     }
                     tc::tmem_wait_ld();
                     if (b == nb - 1) {
                         tc::tc_fence_before();
-                        mbar_arrive(acc_empty);   // TMEM may be overwritten by the next group
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(acc_empty);   // TMEM may be overwritten now
                     }
                     float rate = 0.f;
                     if (active) {
@@ -727,7 +737,7 @@ __global__ void __maxnreg__(255) k_scatter_tc(TcArgs a) {
             producers_sync();
         }
         // wait for our last committed MMAs to finish before TMEM is released
-        for (int st = 0; st < 2; ++st)
+        for (int st = 0; st < NSA; ++st)
             while (used[st] > mw[st]) {
                 if (!tc::mbar_wait_bounded(&mma_done[st], mw[st] & 1, kWaitTimeoutNs)) {
                     failed = true;
@@ -790,21 +800,25 @@ void launch_tc(epwi_ctx *c, const ScatterArgs &sa, int64_t ntiles) {
     a.inv_eta32 = (float)(1.0 / sa.eta);
     a.cube_r = c->rp_cube_r;
     a.nchunk = (c->nRp + 64 / ES - 1) / (64 / ES);
-    a.nbg = std::max(1, 128 / NMWP);
+    a.nbg = std::max(1, 64 / NMWP);   // 4 ncp <= 256 columns per MMA
     a.ncp_max = std::min(sa.nsel_max, a.nbg) * NMWP;
+    // TMEM: accumulator [0, 2 ncp_max) then NSA A stages of 4 operands x 16 columns
+    a.nsa = 3;
+    a.a_col0 = (uint32_t)((4 * a.ncp_max + 15) / 16 * 16);
     uint32_t cols = 32;
-    while (cols < (uint32_t)(2 * a.ncp_max)) cols <<= 1;
+    while (cols < a.a_col0 + (uint32_t)(a.nsa * 4 * 16)) cols <<= 1;
+    EPWI_REQUIRE(cols <= 512, EPWI_EUNSUPPORTED, "tensor-core kernel needs more than 512 TMEM columns");
     a.tmem_cols = cols;
     a.ntiles = ntiles;
     c->tc_err.ensure(sizeof(int) * 4);
     EPWI_CUDA(cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), c->stream));
     a.err = c->tc_err.as<int>();
     const int twords = 2 * c->L * (1 << a.rlog) * TW;
-    const size_t fixed = 2 * 4 * 128 * 64 + sizeof(uint32_t) * ((twords + 1) & ~1) + 8 * 8 + 16 +
-                         4 * epc::kMaxW * 4 + 64;
-    const size_t bres_bytes = (size_t)a.nchunk * 4 * a.ncp_max * 64;
-    a.bres = (fixed + bres_bytes <= 220 * 1024) ? 1 : 0;
-    size_t smem = fixed + (a.bres ? bres_bytes : 2 * 4 * (size_t)a.ncp_max * 64);
+    const size_t fixed = sizeof(uint32_t) * ((twords + 1) & ~1) + 10 * 8 + 16 + 4 * epc::kMaxW * 4 + 64;
+    const size_t bres_bytes = (size_t)a.nchunk * 8 * a.ncp_max * 64;
+    a.bres = (fixed + bres_bytes <= 200 * 1024) ? 1 : 0;
+    if (!a.bres) a.nsa = 2;   // streaming B uses the A stage index as its slot index
+    size_t smem = fixed + (a.bres ? bres_bytes : 2 * 8 * (size_t)a.ncp_max * 64);
     auto kern = k_scatter_tc<Op, W, NM, RC>;
     int nsm = 0;
     EPWI_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
@@ -863,7 +877,7 @@ size_t tc_state_bytes(const epwi_ctx *c) {
     const size_t kc = 64 / es;
     const size_t nchunk = (c->nRp + kc - 1) / kc;
     const size_t nmwp = (size_t)(c->nm * c->nw + 15) / 16 * 16;
-    return nchunk * 4 * nmwp * 64;
+    return nchunk * 6 * nmwp * 64;
 }
 
 void tc_tables(epwi_ctx *c) {
