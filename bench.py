@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 METRIC = "el-ph (k,q)-pairs/s and time-to-σ, mixed-precision vs FP64 at stated error"
 WORKLOAD = dict(workload="al_like_48", system="Al-like fcc, nw=4, 3 modes, 5^3 WS-weighted Re/Rp",
                 grid=48, window_eV=0.3, smear_eV=0.02, T_K=300.0, mu="band centre", seed=2)
-CHOSEN = os.environ.get("EPWI_BENCH_PRECISION", "fp64")
+CHOSEN = "fp16x3"
 DTYPE = {"fp64": "f64", "tf32x3": "tf32x3 (f32 acc, f64 sums)", "bf16x3": "bf16x3 (f32 acc, f64 sums)",
          "fp16x3": "fp16x3 (f32 acc, f64 sums)"}
 L2_BYTES = 129 * 2 ** 20

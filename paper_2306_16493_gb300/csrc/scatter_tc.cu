@@ -253,7 +253,8 @@ struct TcArgs {
     int ncp_max;                   // B rows per stage
     int bres;                      // 1: B of one (k-point, band group) resident in nchunk slots
     int nsa;                       // A stages in TMEM
-    uint32_t a_col0;               // first TMEM column of the A stages (after the accumulator)
+    uint32_t a_col0;               // first TMEM column of the A stages (after the accumulators)
+    uint32_t acc_cols;             // TMEM columns of one accumulator buffer
     uint32_t tmem_cols;
     int64_t ntiles;
     int *err;                      // [0]: timed-out waits
@@ -268,7 +269,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
 }
 
-__device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void epilogue_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 // B slot of one chunk: V1 = [Br_hi | Bi_hi | Br_lo | Bi_lo] then V2 = [-Bi_hi | Br_hi | -Bi_lo | Br_lo],
 // each part ncp rows of 64 bytes; these are the image arrays in this order.
@@ -295,18 +296,21 @@ __device__ __forceinline__ void issue_b(const TcArgs &a, const TileMeta &m, int 
     copy_b<NMWP>(a, m.s0, g0, nb, ch, slot, bar);
 }
 
-// Warp-specialised CTA of 160 threads: warps 0-3 are producers (one q row each: phase
-// operands into shared memory, then the epilogue from TMEM), warp 4 lane 0 is the control
-// thread (B operand bulk copies, tcgen05.mma issue and commit).  B either stays resident for
-// a (k-point, band group) across consecutive tiles (reloaded only when it changes) or, when
-// it does not fit, streams through a two-slot ring one chunk ahead.  They communicate
-// through mbarriers only: a_full (one elected arrival per producer warp), mma_done
-// (tcgen05.commit), b_full (bulk-copy bytes) and acc_empty (per-warp arrivals after the
-// epilogue read TMEM).  A streams through 2 or 3 shared-memory stages.
-// One CTA per SM: the shared-memory footprint and the per-sub-partition register file
-// (warps w and w+4 of two co-resident 5-warp CTAs share a sub-partition) rule out a second.
+// Warp-specialised CTA of 288 threads, one per SM:
+//   warps 0-3  A producers: one q row each; phase operands (Pr_hi, Pi_hi, Pr_lo, Pi_lo) written
+//              to TMEM with tcgen05.st, K streamed through NSA TMEM stages;
+//   warps 4-7  epilogue: one q row each; accumulator rows read with tcgen05.ld, rotated and
+//              delta-weighted in FP32, tile sums in FP64;
+//   warp 8     lane 0 is the control thread: B operand bulk copies, tcgen05.mma issue/commit.
+// The accumulator is double-buffered in TMEM, so the A producers and the MMAs of one band
+// group run while the epilogue warps drain the previous one.  Roles talk through mbarriers
+// only: a_full (one arrival per producer warp), mma_done (commit per chunk), b_full (bulk-copy
+// bytes), acc_full (commit per group) and acc_empty (one arrival per epilogue warp).
+// B either stays resident for a (k-point, band group) across consecutive tiles (reloaded
+// only when it changes) or, when it does not fit, streams through two slots one chunk ahead.
+// 9 warps put at most 3 on a sub-partition: <= 168 registers per thread.
 template <class Op, int W, int NM, int RC>
-__global__ void __maxnreg__(255) k_scatter_tc(TcArgs a) {
+__global__ void __maxnreg__(168) k_scatter_tc(TcArgs a) {
     constexpr int ES = Op::kBytes;
     constexpr int KC = 64 / ES;                 // Rp per chunk (64 bytes per row and operand)
     constexpr int EPV = 16 / ES;                // elements per 16-byte core-matrix row
@@ -315,19 +319,22 @@ __global__ void __maxnreg__(255) k_scatter_tc(TcArgs a) {
     constexpr uint32_t A_COLS = 16;             // TMEM columns per A operand per stage (64 bytes)
     constexpr int TW = Op::kTF32 ? 4 : 2;       // 32-bit words per table entry
     constexpr bool PRE = (W * W + NM * NM) <= 32;   // keep the epilogue operands in registers
+    constexpr int D = 2 * RC + 1;               // R_p cube side
+    constexpr int NRP = D * D * D;
+    constexpr int NCH = (NRP + KC - 1) / KC;    // K chunks (compile time)
     const ScatterArgs &s = a.s;
     extern __shared__ __align__(128) uint8_t smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t B_SLOT = 8u * (uint32_t)a.ncp_max * 64;   // one chunk of V1 and V2
-    const int NSA = a.nsa;                      // A stages in TMEM (2 or 3)
+    const int NSA = a.nsa;                      // A stages in TMEM
     uint8_t *sB = smem;
     uint32_t *sT = reinterpret_cast<uint32_t *>(sB + (a.bres ? a.nchunk : 2) * B_SLOT);
     const int L = s.g.L;
     const int twords = 2 * L * (1 << a.rlog) * TW;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sT + ((twords + 1) & ~1));
-    uint64_t *a_full = bars, *mma_done = bars + 3, *b_full = bars + 6, *acc_empty = bars + 8,
-             *drained = bars + 9;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 10);
+    uint64_t *a_full = bars, *mma_done = bars + 3, *b_full = bars + 6, *acc_full = bars + 8,
+             *acc_empty = bars + 10, *drained = bars + 12;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 13);
     volatile int *sfail = reinterpret_cast<volatile int *>(tslot + 1);
     float *wred = reinterpret_cast<float *>(tslot + 4);   // [4][kMaxW]
 
@@ -337,9 +344,11 @@ __global__ void __maxnreg__(255) k_scatter_tc(TcArgs a) {
             tc::mbar_init(&a_full[i], 4);     // one elected arrival per producer warp
             tc::mbar_init(&mma_done[i], 1);
         }
-        tc::mbar_init(&b_full[0], 1);
-        tc::mbar_init(&b_full[1], 1);
-        tc::mbar_init(&acc_empty[0], 4);
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&b_full[i], 1);
+            tc::mbar_init(&acc_full[i], 1);
+            tc::mbar_init(&acc_empty[i], 4);  // one elected arrival per epilogue warp
+        }
         tc::mbar_init(drained, 1);
         *sfail = 0;
         tc::fence_mbar_init();
@@ -352,22 +361,22 @@ __global__ void __maxnreg__(255) k_scatter_tc(TcArgs a) {
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = *tslot;
+    const uint32_t acc_cols = a.acc_cols;        // columns of one accumulator buffer
     const uint32_t tmem_a = tmem + a.a_col0;     // A stages: NSA x 4 operands x 16 columns
     const int64_t t_begin = blockIdx.x * a.ntiles / gridDim.x;
     const int64_t t_end = (blockIdx.x + 1) * a.ntiles / gridDim.x;
+    const unsigned n1 = s.g.n1, n2 = s.g.n2, n3 = s.g.n3;
 
-    if (warp == 4) {
+    if (warp == 8) {
         // ------------------------------------------------------------ control thread
         if (lane == 0) {
             uint32_t aph[3] = {0, 0, 0}, bph[2] = {0, 0}, bpend[2] = {0, 0};
-            uint32_t mc[3] = {0, 0, 0}, mw[3] = {0, 0, 0}, eph = 0;
-            uint32_t ctr = 0;
-            bool failed = false, first = true;
-            uint32_t dph = 0;
+            uint32_t mc[3] = {0, 0, 0}, mw[3] = {0, 0, 0}, eph[2] = {0, 0};
+            uint32_t ctr = 0, gctr = 0, dph = 0;
+            bool failed = false;
             auto drain_mma = [&]() {
                 if (a.bres) {
-                    // a commit on its own barrier completes once every MMA issued so far has;
-                    // (mma_done phases are not tracked here: the producers observe those)
+                    // a commit on its own barrier completes once every MMA issued so far has
                     tc::mma_commit(drained);
                     if (!tc::mbar_wait_bounded(drained, dph, kWaitTimeoutNs)) failed = true;
                     dph ^= 1;
@@ -399,7 +408,6 @@ __global__ void __maxnreg__(255) k_scatter_tc(TcArgs a) {
                 pm = a.meta[pt];
                 prefetch(0);
             }
-            // resident mode: all chunks of one (k-point, band group) stay in nchunk slots
             int tag_kp = -1, tag_g0 = -1;
             for (int64_t tile = t_begin; tile < t_end && !failed; ++tile) {
                 const TileMeta m = a.meta[tile];
@@ -417,12 +425,13 @@ __global__ void __maxnreg__(255) k_scatter_tc(TcArgs a) {
                         tag_kp = m.kpl;
                         tag_g0 = g0;
                     }
-                    if (!first) {
-                        if (!tc::mbar_wait_bounded(acc_empty, eph, kWaitTimeoutNs)) failed = true;
-                        eph ^= 1;
-                        tc::tc_fence_after();
+                    const int ab = gctr & 1;
+                    if (gctr >= 2) {   // the epilogue has drained this buffer (two groups ago)
+                        if (!tc::mbar_wait_bounded(&acc_empty[ab], eph[ab], kWaitTimeoutNs)) failed = true;
+                        eph[ab] ^= 1;
                     }
-                    first = false;
+                    tc::tc_fence_after();
+                    const uint32_t dacc = tmem + (uint32_t)ab * acc_cols;
                     for (int ch = 0; ch < a.nchunk && !failed; ++ch) {
                         const int st = ctr % NSA;   // A stage; streaming mode has NSA = 2 = B slots
                         if (!tc::mbar_wait_bounded(&a_full[st], aph[st], kWaitTimeoutNs)) failed = true;
@@ -447,10 +456,10 @@ __global__ void __maxnreg__(255) k_scatter_tc(TcArgs a) {
                             const uint32_t acc = (ch == 0 && ks == 0) ? 0u : 1u;
                             // D = [Dr_hi | Di_hi | Dr_lo | Di_lo]:  Pr_hi V1 + Pi_hi V2 fills all four
                             // (hi*hi and hi*lo), Pr_lo V1 + Pi_lo V2 on the first half adds lo*hi.
-                            tc::mma_ta<Op::kTF32>(tmem, Arh, B1, id4, acc);
-                            tc::mma_ta<Op::kTF32>(tmem, Aih, B2, id4, 1);
-                            tc::mma_ta<Op::kTF32>(tmem, Arl, B1, id2, 1);
-                            tc::mma_ta<Op::kTF32>(tmem, Ail, B2, id2, 1);
+                            tc::mma_ta<Op::kTF32>(dacc, Arh, B1, id4, acc);
+                            tc::mma_ta<Op::kTF32>(dacc, Aih, B2, id4, 1);
+                            tc::mma_ta<Op::kTF32>(dacc, Arl, B1, id2, 1);
+                            tc::mma_ta<Op::kTF32>(dacc, Ail, B2, id2, 1);
                         }
                         tc::mma_commit(&mma_done[st]);
                         ++mc[st];
@@ -466,10 +475,11 @@ __global__ void __maxnreg__(255) k_scatter_tc(TcArgs a) {
                         }
                         ++ctr;
                     }
+                    if (!failed) tc::mma_commit(&acc_full[ab]);   // this group's accumulator is ready
+                    ++gctr;
                 }
                 if (*sfail) failed = true;
             }
-            // drain outstanding MMAs and bulk copies before the CTA exits
             drain_mma();
             for (int st = 0; st < 2; ++st)
                 while (bpend[st] > 0) {
@@ -482,18 +492,12 @@ __global__ void __maxnreg__(255) k_scatter_tc(TcArgs a) {
                 atomicAdd(a.err, 1);
             }
         }
-    } else {
-        // ------------------------------------------------------------ producers / epilogue
-        constexpr int D = 2 * RC + 1;               // R_p cube side
-        constexpr int NRP = D * D * D;
-        constexpr int NCH = (NRP + KC - 1) / KC;    // K chunks (compile time)
-        const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);
+    } else if (warp < 4) {
+        // ------------------------------------------------------------ A producers
         const int g = lane & ((1 << a.rlog) - 1);
         uint32_t used[3] = {0, 0, 0}, mw[3] = {0, 0, 0};
         uint32_t ctr = 0;
         bool failed = false;
-        const unsigned n1 = s.g.n1, n2 = s.g.n2, n3 = s.g.n3;
-        // the next tile's metadata and q are fetched during the current tile's MMAs
         TileMeta m_next;
         unsigned q_next = 0;
         if (t_begin < t_end) {
@@ -502,27 +506,20 @@ __global__ void __maxnreg__(255) k_scatter_tc(TcArgs a) {
         }
         for (int64_t tile = t_begin; tile < t_end && !failed; ++tile) {
             const TileMeta m = m_next;
-            const int pair = m.begin + tid;
-            const bool active = pair < m.end;
-            unsigned iq = 0, ikq = 0;
+            const bool active = m.begin + tid < m.end;
+            const unsigned iq = q_next;
+            if (tile + 1 < t_end) {
+                m_next = a.meta[tile + 1];
+                q_next = 0;
+            }
             int a1 = 0, a2 = 0, a3 = 0;
-            const unsigned q_this = q_next;
             if (active) {
-                iq = q_this;
                 const unsigned q3 = iq % n3, qt = iq / n3, q2 = qt % n2, q1 = qt / n2;
-                const unsigned k3 = (unsigned)m.ik % n3, kt = (unsigned)m.ik / n3, k2 = kt % n2, k1 = kt / n2;
-                unsigned b1 = q1 + k1, b2 = q2 + k2, b3 = q3 + k3;
-                if (b1 >= n1) b1 -= n1;
-                if (b2 >= n2) b2 -= n2;
-                if (b3 >= n3) b3 -= n3;
-                ikq = (b1 * n2 + b2) * n3 + b3;
                 a1 = (int)(q1 * (unsigned)s.g.s1 % (unsigned)L);
                 a2 = (int)(q2 * (unsigned)s.g.s2 % (unsigned)L);
                 a3 = (int)(q3 * (unsigned)s.g.s3 % (unsigned)L);
             }
             for (int g0 = 0; g0 < m.nsel && !failed; g0 += a.nbg) {
-                const int nb = min(a.nbg, m.nsel - g0);
-                const int ncp = nb * NMWP;
                 // Reduced phase-index tables of this q: C3[n3+R] = n3 a3 mod L and
                 // B12[(n1+R) D + n2+R] = (n1 a1 + n2 a2) mod L; an R_p index is B12 + C3 < 2L.
                 int C3[D], B12[D * D];
@@ -617,50 +614,95 @@ __global__ void __maxnreg__(255) k_scatter_tc(TcArgs a) {
                     if (lane == 0) mbar_arrive(&a_full[st]);
                     ++used[st];
                     ++ctr;
+                    if (ch == 0 && g0 == 0 && tile + 1 < t_end)
+                        q_next = (m_next.begin + tid < m_next.end) ? (unsigned)s.pairs[m_next.begin + tid] : 0u;
                 }
-                if (failed) break;
-                if (g0 == 0 && tile + 1 < t_end) {
-                    m_next = a.meta[tile + 1];
-                    q_next = (m_next.begin + tid < m_next.end) ? (unsigned)s.pairs[m_next.begin + tid] : 0u;
+            }
+        }
+        for (int st = 0; st < NSA; ++st)
+            while (used[st] > mw[st]) {
+                if (!tc::mbar_wait_bounded(&mma_done[st], mw[st] & 1, kWaitTimeoutNs)) {
+                    failed = true;
+                    break;
                 }
-                // epilogue operands of this pair, fetched while the last MMAs run
-                float2 Vr[PRE ? W * W : 1], ur[PRE ? NM * NM : 1];
-                float wq[NM], nq[NM], emr[W], fmr[W];
-                const float2 *Vq = s.V32 + (size_t)ikq * W * W;
-                const float2 *uq = s.u32 + (size_t)iq * NM * NM;
-                if constexpr (PRE) {
+                ++mw[st];
+            }
+        if (failed) *sfail = 1;
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int et = tid - 128;                  // row of the tile (TMEM lane)
+        const int ew = warp - 4;                   // lane quarter
+        const uint32_t tmem_row = tmem + ((uint32_t)(ew * 32) << 16);
+        uint32_t fph[2] = {0, 0};
+        uint32_t gctr = 0;
+        bool failed = false;
+        TileMeta m_next;
+        unsigned q_next = 0;
+        if (t_begin < t_end) {
+            m_next = a.meta[t_begin];
+            if (m_next.begin + et < m_next.end) q_next = (unsigned)s.pairs[m_next.begin + et];
+        }
+        for (int64_t tile = t_begin; tile < t_end && !failed; ++tile) {
+            const TileMeta m = m_next;
+            const int pair = m.begin + et;
+            const bool active = pair < m.end;
+            const unsigned iq = active ? q_next : 0u;
+            if (tile + 1 < t_end) m_next = a.meta[tile + 1];
+            unsigned ikq = 0;
+            {
+                const unsigned q3 = iq % n3, qt = iq / n3, q2 = qt % n2, q1 = qt / n2;
+                const unsigned k3 = (unsigned)m.ik % n3, kt = (unsigned)m.ik / n3, k2 = kt % n2, k1 = kt / n2;
+                unsigned b1 = q1 + k1, b2 = q2 + k2, b3 = q3 + k3;
+                if (b1 >= n1) b1 -= n1;
+                if (b2 >= n2) b2 -= n2;
+                if (b3 >= n3) b3 -= n3;
+                ikq = (b1 * n2 + b2) * n3 + b3;
+            }
+            // epilogue operands of this pair, fetched while the MMAs of this tile run
+            float2 Vr[PRE ? W * W : 1], ur[PRE ? NM * NM : 1];
+            float wq[NM], nq[NM], emr[W], fmr[W];
+            const float2 *Vq = s.V32 + (size_t)ikq * W * W;
+            const float2 *uq = s.u32 + (size_t)iq * NM * NM;
+            if constexpr (PRE) {
 #pragma unroll
-                    for (int x = 0; x < W * W; ++x) Vr[x] = __ldg(Vq + x);
+                for (int x = 0; x < W * W; ++x) Vr[x] = __ldg(Vq + x);
 #pragma unroll
-                    for (int x = 0; x < NM * NM; ++x) ur[x] = __ldg(uq + x);
-                } else {
-                    tc::prefetch_l1(Vq);
-                    tc::prefetch_l1(uq);
-                }
+                for (int x = 0; x < NM * NM; ++x) ur[x] = __ldg(uq + x);
+            } else {
+                tc::prefetch_l1(Vq);
+                tc::prefetch_l1(uq);
+            }
 #pragma unroll
-                for (int nu = 0; nu < NM; ++nu) {
-                    wq[nu] = __ldg(a.hw32 + (size_t)iq * NM + nu);
-                    nq[nu] = __ldg(a.n32 + (size_t)iq * NM + nu);
-                }
+            for (int nu = 0; nu < NM; ++nu) {
+                wq[nu] = __ldg(a.hw32 + (size_t)iq * NM + nu);
+                nq[nu] = __ldg(a.n32 + (size_t)iq * NM + nu);
+            }
 #pragma unroll
-                for (int mm = 0; mm < W; ++mm) {
-                    emr[mm] = __ldg(a.erel32 + (size_t)ikq * W + mm);
-                    fmr[mm] = __ldg(a.f32 + (size_t)ikq * W + mm);
-                }
-                // ---- accumulator ready (the last commit covers all MMAs of the group)
-                {
-                    const int st = (ctr - 1) % NSA;
-                    if (!tc::mbar_wait_bounded(&mma_done[st], mw[st] & 1, kWaitTimeoutNs)) failed = true;
-                    ++mw[st];
-                    if (failed) break;
+            for (int mm = 0; mm < W; ++mm) {
+                emr[mm] = __ldg(a.erel32 + (size_t)ikq * W + mm);
+                fmr[mm] = __ldg(a.f32 + (size_t)ikq * W + mm);
+            }
+            if (tile + 1 < t_end)
+                q_next = (m_next.begin + et < m_next.end) ? (unsigned)s.pairs[m_next.begin + et] : 0u;
+            for (int g0 = 0; g0 < m.nsel && !failed; g0 += a.nbg) {
+                const int nb = min(a.nbg, m.nsel - g0);
+                const int ncp = nb * NMWP;
+                const int ab = gctr & 1;
+                if (!tc::mbar_wait_bounded(&acc_full[ab], fph[ab], kWaitTimeoutNs)) failed = true;
+                fph[ab] ^= 1;
+                ++gctr;
+                if (failed || *sfail) {
+                    failed = true;
+                    break;
                 }
                 tc::tc_fence_after();
+                const uint32_t arow = tmem_row + (uint32_t)ab * acc_cols;
                 for (int b = 0; b < nb; ++b) {
                     float gr[NMWP], gi[NMWP];
 #pragma unroll
                     for (int blk = 0; blk < NMWP / 16; ++blk) {
                         float t0[16], t1[16];
-                        const uint32_t c0 = tmem_row + (uint32_t)(b * NMWP + blk * 16);
+                        const uint32_t c0 = arow + (uint32_t)(b * NMWP + blk * 16);
                         tc::tmem_ld16(c0, t0);
                         tc::tmem_ld16(c0 + 2 * ncp, t1);
 #pragma unroll
@@ -674,7 +716,7 @@ __global__ void __maxnreg__(255) k_scatter_tc(TcArgs a) {
                     if (b == nb - 1) {
                         tc::tc_fence_before();
                         __syncwarp();
-                        if (lane == 0) mbar_arrive(acc_empty);   // TMEM may be overwritten now
+                        if (lane == 0) mbar_arrive(&acc_empty[ab]);   // buffer free for the MMAs
                     }
                     float rate = 0.f;
                     if (active) {
@@ -726,25 +768,16 @@ __global__ void __maxnreg__(255) k_scatter_tc(TcArgs a) {
                     }
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) rate += __shfl_down_sync(0xffffffffu, rate, o);
-                    if (lane == 0) wred[warp * epc::kMaxW + g0 + b] = rate * a.scale_inv2;
+                    if (lane == 0) wred[ew * epc::kMaxW + g0 + b] = rate * a.scale_inv2;
                 }
             }
-            producers_sync();
-            if (!failed && tid < m.nsel)
-                s.tile_part[tile * epc::kMaxW + tid] =
-                    ((double)wred[tid] + (double)wred[epc::kMaxW + tid]) +
-                    ((double)wred[2 * epc::kMaxW + tid] + (double)wred[3 * epc::kMaxW + tid]);
-            producers_sync();
+            epilogue_sync();
+            if (!failed && et < m.nsel)
+                s.tile_part[tile * epc::kMaxW + et] =
+                    ((double)wred[et] + (double)wred[epc::kMaxW + et]) +
+                    ((double)wred[2 * epc::kMaxW + et] + (double)wred[3 * epc::kMaxW + et]);
+            epilogue_sync();
         }
-        // wait for our last committed MMAs to finish before TMEM is released
-        for (int st = 0; st < NSA; ++st)
-            while (used[st] > mw[st]) {
-                if (!tc::mbar_wait_bounded(&mma_done[st], mw[st] & 1, kWaitTimeoutNs)) {
-                    failed = true;
-                    break;
-                }
-                ++mw[st];
-            }
         if (failed) *sfail = 1;
     }
     tc::tc_fence_before();
@@ -800,11 +833,12 @@ void launch_tc(epwi_ctx *c, const ScatterArgs &sa, int64_t ntiles) {
     a.inv_eta32 = (float)(1.0 / sa.eta);
     a.cube_r = c->rp_cube_r;
     a.nchunk = (c->nRp + 64 / ES - 1) / (64 / ES);
-    a.nbg = std::max(1, 64 / NMWP);   // 4 ncp <= 256 columns per MMA
+    a.nbg = std::max(1, 48 / NMWP);   // 4 ncp <= 192: two accumulators + A stages fit 512 columns
     a.ncp_max = std::min(sa.nsel_max, a.nbg) * NMWP;
-    // TMEM: accumulator [0, 2 ncp_max) then NSA A stages of 4 operands x 16 columns
-    a.nsa = 3;
-    a.a_col0 = (uint32_t)((4 * a.ncp_max + 15) / 16 * 16);
+    // TMEM: two accumulators of 4 ncp_max columns, then NSA A stages of 4 operands x 16 columns
+    a.acc_cols = (uint32_t)((4 * a.ncp_max + 15) / 16 * 16);
+    a.a_col0 = 2 * a.acc_cols;
+    a.nsa = (a.a_col0 + 3 * 64 <= 512) ? 3 : 2;
     uint32_t cols = 32;
     while (cols < a.a_col0 + (uint32_t)(a.nsa * 4 * 16)) cols <<= 1;
     EPWI_REQUIRE(cols <= 512, EPWI_EUNSUPPORTED, "tensor-core kernel needs more than 512 TMEM columns");
@@ -814,7 +848,7 @@ void launch_tc(epwi_ctx *c, const ScatterArgs &sa, int64_t ntiles) {
     EPWI_CUDA(cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), c->stream));
     a.err = c->tc_err.as<int>();
     const int twords = 2 * c->L * (1 << a.rlog) * TW;
-    const size_t fixed = sizeof(uint32_t) * ((twords + 1) & ~1) + 10 * 8 + 16 + 4 * epc::kMaxW * 4 + 64;
+    const size_t fixed = sizeof(uint32_t) * ((twords + 1) & ~1) + 13 * 8 + 16 + 4 * epc::kMaxW * 4 + 64;
     const size_t bres_bytes = (size_t)a.nchunk * 8 * a.ncp_max * 64;
     a.bres = (fixed + bres_bytes <= 200 * 1024) ? 1 : 0;
     if (!a.bres) a.nsa = 2;   // streaming B uses the A stage index as its slot index
@@ -827,14 +861,14 @@ void launch_tc(epwi_ctx *c, const ScatterArgs &sa, int64_t ntiles) {
     int per_sm = 0;
     for (;;) {
         EPWI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        EPWI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 160, smem));
+        EPWI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 288, smem));
         EPWI_REQUIRE(per_sm >= 1, EPWI_EUNSUPPORTED, "tensor-core kernel does not fit on an SM");
         if ((uint32_t)per_sm * cols <= 512) break;
         smem += 8 * 1024;
     }
     const int64_t grid = std::min<int64_t>(ntiles, (int64_t)per_sm * nsm);
     if (grid > 0) {
-        kern<<<(unsigned)grid, 160, smem, c->stream>>>(a);
+        kern<<<(unsigned)grid, 288, smem, c->stream>>>(a);
         EPWI_CHECK_LAUNCH();
     }
     c->tc_blocks_per_sm = per_sm;
@@ -846,7 +880,7 @@ void launch_tc(epwi_ctx *c, const ScatterArgs &sa, int64_t ntiles) {
         cudaFuncAttributes fa;
         EPWI_CUDA(cudaFuncGetAttributes(&fa, kern));
         size_t avail = 0;
-        if (cudaOccupancyAvailableDynamicSMemPerBlock(&avail, kern, 1, 160) != cudaSuccess) {
+        if (cudaOccupancyAvailableDynamicSMemPerBlock(&avail, kern, 1, 288) != cudaSuccess) {
             (void)cudaGetLastError();
             avail = 0;
         }
