@@ -204,6 +204,27 @@ epwi_status epwi_get_sieve(epwi_ctx *ctx, int64_t capacity, int32_t *kpts, int64
 epwi_status epwi_g2(epwi_ctx *ctx, int64_t npairs, const int32_t *ik, const int32_t *iq,
                     int32_t band_lo, int32_t nsel, double *g2);
 
+/* Conductivity from per-state DEVICE arrays, allocating no device memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call cudaMalloc, such as a
+ * host framework that owns all device memory through its own pool, or a service that must
+ * not allocate after start-up (cudaMalloc/cudaFree may synchronise the device and can fail
+ * under memory pressure mid-run).  Same sum as epwi_conductivity:
+ *   sigma_ab = (2 e^2/(N_k V)) sum_s v_a v_b f(1-f)/(k_B T) / (1/tau_s), states with 1/tau_s = 0
+ *   skipped, f = Fermi-Dirac(eps_s; mu, T).
+ * eps_dev [n_states] eV, vel_dev [n_states][3] m/s, inv_tau_dev [n_states] 1/s, all device
+ * pointers owned by the caller; sigma_dev: 9 doubles (3x3 row-major) in device memory, written
+ * on cuda_stream (NULL = legacy default stream); the call only enqueues work.  nk is N_k of the
+ * grid, volume_A3 the cell volume.  Scratch is a fixed 48 KiB device array in the library
+ * (held by every GPU that loads it until exit); n_states above 4,194,304 returns
+ * EPWI_EUNSUPPORTED.  The first call on each device resolves the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.  All calls share
+ * the array: calls that overlap on the GPU race.  Errors: EINVAL (NULL pointer, T <= 0,
+ * volume <= 0, nk < 1), EUNSUPPORTED (too many states), ECUDA (launch or symbol lookup). */
+epwi_status epwi_conductivity_noalloc(int64_t n_states, const double *eps_dev, const double *vel_dev,
+                                      const double *inv_tau_dev, double mu_eV, double T_K,
+                                      double volume_A3, int64_t nk, void *cuda_stream,
+                                      double *sigma_dev);
+
 /* Number of kernels this library has launched in the process so far (all contexts). */
 int64_t epwi_kernel_launches(void);
 

@@ -84,6 +84,7 @@ def _load() -> C.CDLL:
         "epwi_g2": (I32, [P, I64, P, P, I32, I32, P]),
         "epwi_get_stats": (I32, [P, P]),
         "epwi_kernel_launches": (I64, []),
+        "epwi_conductivity_noalloc": (I32, [I64, P, P, P, D, D, D, I64, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -237,6 +238,18 @@ def epwi_g2(ctx, ik, iq, band_lo: int, nsel: int, nm: int, nw: int):
     out = np.empty((len(ik), nsel, nm, nw))
     _check(ctx, _lib.epwi_g2(ctx, len(ik), _ptr(ik), _ptr(iq), int(band_lo), int(nsel), _ptr(out)))
     return out
+
+
+def epwi_conductivity_noalloc(n_states: int, eps_dev: int, vel_dev: int, inv_tau_dev: int,
+                              mu_eV: float, T_K: float, volume_A3: float, nk: int, stream: int | None,
+                              sigma_dev: int):
+    """Device-pointer variant of epwi_conductivity that allocates nothing (pointers as ints)."""
+    st = _lib.epwi_conductivity_noalloc(int(n_states), C.c_void_p(eps_dev), C.c_void_p(vel_dev),
+                                        C.c_void_p(inv_tau_dev), float(mu_eV), float(T_K),
+                                        float(volume_A3), int(nk), C.c_void_p(stream or 0),
+                                        C.c_void_p(sigma_dev))
+    if st != 0:
+        raise EpwiError(st, "epwi_conductivity_noalloc failed")
 
 
 def epwi_kernel_launches() -> int:
