@@ -35,6 +35,11 @@ CHOSEN = "fp16x3"
 DTYPE = {"fp64": "f64", "tf32x3": "tf32x3 (f32 acc, f64 sums)", "bf16x3": "bf16x3 (f32 acc, f64 sums)",
          "fp16x3": "fp16x3 (f32 acc, f64 sums)"}
 L2_BYTES = 129 * 2 ** 20
+# DRAM bytes (read + write) per (k,q) pair of k_scatter_tc, fp16x3, from one ncu capture of
+# the 24^3 case (255 MB / 19.6 M pairs, ncu --set full).
+# Traffic grows with the pairs processed, so a launch's traffic is this times its pairs.
+# Valid for the kernel version of that capture only.
+TRAFFIC_BYTES_PER_PAIR = {"fp16x3": 13.0}
 
 
 def peaks():
@@ -64,7 +69,7 @@ def roofline_for(precision, stats, per_launch_traffic=None):
         achieved = 3.0 * flops / (ms * 1e-3) / 1e12      # three split products
         note = f"{src} bf16 burst peak x {ratio}"
     return {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": achieved / peak, "traffic": per_launch_traffic,
+            "frac": achieved / peak, "traffic": per_launch_traffic, "traffic_unit": "bytes per launch",
             "kernel": "k_scatter (fused Rp->q GEMM + rotations + delta sum)",
             "launches_per_step": stats["n_chunks"], "peak_source": note}
 
@@ -213,7 +218,7 @@ def run_gpu(args):
 
     precision = args.precision
     s = synth.al_like_system(WORKLOAD["seed"])
-    N = WORKLOAD["grid"]
+    N = args.grid
     T, eta, win = WORKLOAD["T_K"], WORKLOAD["smear_eV"], WORKLOAD["window_eV"]
     stream = torch.cuda.current_stream()
     ctx = epwi.Context(precision=precision, device=local, stream=stream.cuda_stream)
@@ -260,8 +265,12 @@ def run_gpu(args):
     pairs_all = reduce_sum_over_ranks(float(pairs_total), world)
     value = pairs_all / (ms_max * 1e-3)
     clocks = cs.summary(local)
-    stats = dict(ctx.stats(), scatter_flops=sc_flops, ms_scatter=sc_ms, n_chunks=chunks)
-    roof = roofline_for(precision, stats, per_launch_traffic=None)
+    stats = dict(ctx.stats(), scatter_flops=sc_flops / args.steps, ms_scatter=sc_ms / args.steps,
+                 n_chunks=chunks // args.steps)
+    pairs_per_launch = pairs_total / args.steps / max(1, stats["n_chunks"])
+    tb = TRAFFIC_BYTES_PER_PAIR.get(precision)
+    roof = roofline_for(precision, stats,
+                        per_launch_traffic=None if tb is None else tb * pairs_per_launch)
 
     # ---- e2e through the C ABI with host buffers
     e2e_steps = max(1, min(args.steps, 3))
@@ -295,7 +304,8 @@ def run_gpu(args):
                 "time_to_sigma_ms": ms_max / args.steps, "pairs_per_step": pairs_total / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": DTYPE[precision], "data": "synthetic",
-                "config": dict(WORKLOAD, precision=precision, l2="flushed between timed steps (256 MiB write)",
+                "config": dict(WORKLOAD, grid=N, workload=f"al_like_{N}", precision=precision,
+                               l2="flushed between timed steps (256 MiB write)",
                                parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
                 "gpu_launches": int(launches),
                 "stage_ms": {k: stats[k] for k in ("ms_eigs", "ms_sieve", "ms_restage", "ms_scatter", "ms_reduce")},
@@ -317,6 +327,8 @@ def main():
     ap.add_argument("--precision", default=CHOSEN, choices=["fp64", "tf32x3", "bf16x3", "fp16x3"])
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--ref-kpoints", type=int, default=40)
+    ap.add_argument("--grid", type=int, default=WORKLOAD["grid"],
+                    help="k and q grid per axis (48 is the benchmark; smaller sizes are for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
