@@ -209,15 +209,14 @@ def sieve_k(gr: Grids, ik: int, bands_n, eta, c=6.0):
     return iq[ok]
 
 
-def inv_tau_k(gr: Grids, ik: int, bands_n, T, mu, eta, c=6.0, q_list=None):
-    """SERTA scattering rates 1/tau_nk (s^-1) for the states n in ``bands_n`` at k
-    (Sec. II C, Eq. 10, with 1/N_q and Gaussian delta).  Returns (rates, n_pairs)."""
+def pair_terms_k(gr: Grids, ik: int, bands_n, T, mu, eta, c, q_list) -> np.ndarray:
+    """The summand of Eq. 10 for one k before the q and mode sums:
+    t[q, nu, n] = sum_m |g^nu_mn(k,q)|^2 [(N + f) delta(x+) + (1 + N - f) delta(x-)] in eV
+    (Sec. II C, Eq. 10), for the q in ``q_list`` and the bands ``bands_n``."""
     bands_n = np.asarray(bands_n)
-    if q_list is None:
-        q_list = sieve_k(gr, ik, bands_n, eta, c)
-    rates = np.zeros(len(bands_n))
+    q_list = np.asarray(q_list, dtype=np.int64)
     if len(q_list) == 0:
-        return rates, 0
+        return np.zeros((0, gr.hw.shape[1], len(bands_n)))
     ikq = kq_index(ik, q_list, gr.ngrid)
     g = g_matrix(gr.sys, gr.frac[ik], gr.frac[q_list], gr.V[ik][:, bands_n],
                  gr.V[ikq], gr.u[q_list])                          # [q, nu, m, n]
@@ -233,7 +232,25 @@ def inv_tau_k(gr: Grids, ik: int, bands_n, T, mu, eta, c=6.0, q_list=None):
     occ_emi = 1.0 + N[:, :, None, None] - fm[:, None, :, None]
     term = g2 * (occ_abs * delta_gauss(x_abs, eta, c) + occ_emi * delta_gauss(x_emi, eta, c))
     term = term * keep[:, :, None, None]
-    rates = term.sum(axis=(0, 1, 2)) * (2.0 * math.pi / HBAR_EVS) / gr.nk
+    return term.sum(axis=2)
+
+
+def inv_tau_k(gr: Grids, ik: int, bands_n, T, mu, eta, c=6.0, q_list=None, q_weights=None):
+    """SERTA scattering rates 1/tau_nk (s^-1) for the states n in ``bands_n`` at k
+    (Sec. II C, Eq. 10, with 1/N_q and Gaussian delta).  Returns (rates, n_pairs).
+
+    With ``q_weights`` the q sum is the weighted sum sum_q w_q t(q) over ``q_list`` (an
+    importance-sampling estimate of the full sum when w_q = count_q / (S p(q)))."""
+    bands_n = np.asarray(bands_n)
+    if q_list is None:
+        q_list = sieve_k(gr, ik, bands_n, eta, c)
+    rates = np.zeros(len(bands_n))
+    if len(q_list) == 0:
+        return rates, 0
+    t = pair_terms_k(gr, ik, bands_n, T, mu, eta, c, q_list)       # [q, nu, n]
+    if q_weights is not None:
+        t = t * np.asarray(q_weights, float)[:, None, None]
+    rates = t.sum(axis=(0, 1)) * (2.0 * math.pi / HBAR_EVS) / gr.nk
     return rates, len(q_list)
 
 
