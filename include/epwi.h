@@ -107,6 +107,9 @@ typedef struct {
     int32_t tc_regs;            /* registers per thread of that kernel */
     int64_t tc_smem;            /* dynamic shared memory per CTA (bytes) */
     int64_t tc_smem_avail2;     /* dynamic shared memory available to one CTA on an SM */
+    double ms_proposal;         /* importance sampling: network scores and cell tables */
+    double ms_sampling;         /* importance sampling: draws, merge and weights */
+    double proposal_flops;      /* importance sampling: network flops (2 per multiply-add) */
 } epwi_stats;
 
 /* Fills *opt with the defaults listed above. */
@@ -224,6 +227,94 @@ epwi_status epwi_conductivity_noalloc(int64_t n_states, const double *eps_dev, c
                                       const double *inv_tau_dev, double mu_eV, double T_K,
                                       double volume_A3, int64_t nk, void *cuda_stream,
                                       double *sigma_dev);
+
+/* ---------------------------------------------------------------------------------------
+ * Learned q-proposal and importance-sampled rates.  The paper has no learned part: it sums
+ * the SERTA rate (Sec. II C, Eq. 10) over every sieved q.  These calls estimate that q sum by
+ * importance sampling instead.  Per k-point, S grid points q are drawn from a proposal p > 0,
+ * and the rate is (2 pi/hbar)(1/N_q) sum over the distinct drawn q of c_q / (S p(q)) t(q),
+ * where c_q is how often q was drawn and t is the summand of Eq. 10.  This is unbiased for
+ * any proposal that is positive wherever t is.
+ *
+ * The learned proposal uses a network 9 -> 128 -> 128 -> 128 -> 1 with SiLU hidden
+ * activations, BF16 weights and FP32 arithmetic.  Its inputs are:
+ *   - k and q as fractional coordinates mapped to [-1/2, 1/2) and doubled;
+ *   - (eps_nk - mu) / 0.25 eV;
+ *   - n / nw;
+ *   - nu / (3 nat).
+ * It is trained on the normalised log(t + floor) of the terms on the context's current grid.
+ *
+ * Parameters are EPWI_MLP_NPARAM floats, stored in this order: W1 [128][9], b1 [128],
+ * W2 [128][128], b2, W3 [128][128], b3, w4 [128], b4 [1].
+ * ------------------------------------------------------------------------------------- */
+#define EPWI_MLP_NPARAM 34433
+
+typedef enum { EPWI_PROPOSAL_UNIFORM = 0, EPWI_PROPOSAL_LEARNED = 1 } epwi_proposal;
+
+typedef struct {
+    int32_t epochs;             /* passes over the training set (default 60) */
+    int32_t batch;              /* samples per Adam step, <= 65536 (default 4096) */
+    double lr;                  /* Adam step size; cosine decay to lr/20 (default 2e-3) */
+    double background;          /* uniformly drawn (k,q) pairs per sieved pair (default 1) */
+    double floor_rel;           /* targets are log(t + floor_rel * max t) (default 1e-8) */
+    uint64_t seed;              /* initialisation, background draw and shuffles (default 1) */
+} epwi_mlp_train_options;
+
+void epwi_mlp_default_train_options(epwi_mlp_train_options *opt);
+
+/* Builds the training set on the current grid and trains the network with Adam.
+ * Needs epwi_eigs.  The training set is every sieved (k,q) pair of the window [emin, emax],
+ * plus background pairs drawn uniformly, times every window band and mode.  Its targets come
+ * from the FP64 kernels at (T, mu, smear).  The network is initialised from opt->seed unless
+ * parameters were set or trained before.  final_loss (may be NULL) receives the mean of
+ * (yhat - y)^2 / 2 over the training set.  Errors: ESTATE, EINVAL (empty window),
+ * EUNSUPPORTED (more than 2^26 sieved pairs). */
+epwi_status epwi_mlp_train(epwi_ctx *ctx, double T_K, double mu_eV, double smear_eV,
+                           double emin_eV, double emax_eV, const epwi_mlp_train_options *opt,
+                           double *final_loss);
+
+/* Sets the parameters (host, EPWI_MLP_NPARAM floats, layout above).  They become the FP32
+ * master copy; the network computes with their BF16 rounding.  The output scale becomes 1 and
+ * the shift 0. */
+epwi_status epwi_mlp_set_params(epwi_ctx *ctx, const float *params);
+/* The BF16-rounded parameters the network computes with (host, EPWI_MLP_NPARAM floats), and the
+ * output affine map log t = scale * yhat + shift (either pointer may be NULL). */
+epwi_status epwi_mlp_get_params(epwi_ctx *ctx, float *params, double *scale, double *shift);
+/* Network output yhat for n host samples x [n][9] -> y [n] (reference SIMT kernels). */
+epwi_status epwi_mlp_forward(epwi_ctx *ctx, int64_t n, const float *x, float *y);
+/* One forward and backward pass over n <= 65536 host samples: loss = (1/2n) sum (yhat - y)^2,
+ * grad [EPWI_MLP_NPARAM] = dloss/dparams (host), with respect to the BF16-rounded parameters. */
+epwi_status epwi_mlp_loss_grad(epwi_ctx *ctx, int64_t n, const float *x, const float *y,
+                               double *loss, float *grad);
+/* The training set of the last epwi_mlp_train.  A size query when every pointer is NULL;
+ * otherwise capacity must be >= n.  Per sample it gives:
+ *   ids [n][4]: (k index, q index, band, mode);
+ *   t [n]: the FP64 term of Eq. 10 (eV);
+ *   x [n][9]: the features;
+ *   y [n]: the normalised log target. */
+epwi_status epwi_mlp_get_training_set(epwi_ctx *ctx, int64_t capacity, int32_t *ids, double *t,
+                                      float *x, float *y, int64_t *n);
+
+/* Importance-sampled 1/tau for every state in the window [emin, emax], S = samples_per_k draws
+ * per k-point.  Needs epwi_eigs; for EPWI_PROPOSAL_LEARNED also a trained or set network.
+ *   - Proposal EPWI_PROPOSAL_UNIFORM: p = 1/N_q.
+ *   - Proposal EPWI_PROPOSAL_LEARNED: cells of cell_stride^3 grid points, one around every
+ *     cell_stride-th point.  cell_stride must divide every grid dimension.  For each state
+ *     the network scores every cell centre and mode, and
+ *       p_n(q) = alpha/N_q + (1 - alpha) P_n(cell(q)) / cell_stride^3, with 0 < alpha <= 1.
+ *     The bands of one k share one draw from the band mixture.
+ * The weighted pairs run through the FP64 kernels whatever the context precision.  The result
+ * replaces the rates of epwi_scatter_rates: epwi_get_rates, epwi_conductivity and
+ * epwi_get_stats (n_pairs = distinct drawn pairs) read it.  Errors: ESTATE, EINVAL. */
+epwi_status epwi_scatter_rates_is(epwi_ctx *ctx, double T_K, double mu_eV, double smear_eV,
+                                  double emin_eV, double emax_eV, int64_t samples_per_k,
+                                  double alpha, int32_t cell_stride, int32_t proposal,
+                                  uint64_t seed, int64_t *n_states, int64_t *n_pairs);
+/* The distinct drawn pairs of the last epwi_scatter_rates_is: k index, q index and weight
+ * c_q / (S p(q)) per pair, grouped by k-point in window order and ascending q within a k-point.
+ * A size query when every output pointer is NULL; otherwise capacity must be >= n. */
+epwi_status epwi_get_is_pairs(epwi_ctx *ctx, int64_t capacity, int32_t *ik, int32_t *iq,
+                              double *weight, int64_t *n);
 
 /* Number of kernels this library has launched in the process so far (all contexts). */
 int64_t epwi_kernel_launches(void);

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "epwi_internal.cuh"
+#include "mlp.cuh"
 #include "scatter.cuh"
 
 namespace {
@@ -382,7 +383,7 @@ epwi_status epwi_scatter_rates(epwi_ctx *c, double T, double mu, double eta, dou
         require_eigs(c);
         EPWI_REQUIRE(T > 0 && eta > 0 && std::isfinite(mu) && !(emin > emax), EPWI_EINVAL,
                      "need T > 0, smear > 0, finite mu and emin <= emax");
-        c->have_rates = c->have_sigma = false;
+        c->have_rates = c->have_sigma = c->have_is = false;
         c->T = T;
         c->mu = mu;
         c->eta = eta;
@@ -491,6 +492,7 @@ epwi_status epwi_get_phonons(epwi_ctx *c, double *omega, epwi_c64 *u) {
 epwi_status epwi_get_sieve(epwi_ctx *c, int64_t cap, int32_t *kpts, int64_t *counts) {
     return guard(c, [&] {
         require_rates(c);
+        EPWI_REQUIRE(!c->have_is, EPWI_ESTATE, "the last rates came from importance sampling");
         EPWI_REQUIRE(cap >= c->nkp, EPWI_ETOOSMALL, "capacity below n_kpoints");
         if (kpts && c->nkp)
             EPWI_CUDA(cudaMemcpyAsync(kpts, c->kpts.p, 4 * (size_t)c->nkp, cudaMemcpyDeviceToHost, c->stream));
@@ -568,6 +570,163 @@ epwi_status epwi_g2(epwi_ctx *c, int64_t npairs, const int32_t *ik, const int32_
             throw;
         }
         cleanup();
+    });
+}
+
+void epwi_mlp_default_train_options(epwi_mlp_train_options *o) {
+    if (!o) return;
+    o->epochs = 60;
+    o->batch = 4096;
+    o->lr = 2e-3;
+    o->background = 1.0;
+    o->floor_rel = 1e-8;
+    o->seed = 1;
+}
+
+epwi_status epwi_mlp_train(epwi_ctx *c, double T, double mu, double eta, double emin, double emax,
+                           const epwi_mlp_train_options *opt, double *final_loss) {
+    return guard(c, [&] {
+        require_eigs(c);
+        EPWI_REQUIRE(T > 0 && eta > 0 && std::isfinite(mu) && !(emin > emax), EPWI_EINVAL,
+                     "need T > 0, smear > 0, finite mu and emin <= emax");
+        epwi_mlp_train_options o;
+        epwi_mlp_default_train_options(&o);
+        if (opt) o = *opt;
+        EPWI_REQUIRE(o.epochs >= 0 && o.batch >= 1 && o.batch <= mlp::kMaxBatch && o.lr > 0 &&
+                         o.background >= 0 && o.floor_rel > 0,
+                     EPWI_EINVAL, "bad training options");
+        mlp_train(c, T, mu, eta, emin, emax, o, final_loss);
+    });
+}
+
+epwi_status epwi_mlp_set_params(epwi_ctx *c, const float *params) {
+    return guard(c, [&] {
+        EPWI_REQUIRE(params, EPWI_EINVAL, "params is NULL");
+        mlp_set_master(c, params);
+        c->mlp->out_scale = 1.0;
+        c->mlp->out_shift = 0.0;
+    });
+}
+
+epwi_status epwi_mlp_get_params(epwi_ctx *c, float *params, double *scale, double *shift) {
+    return guard(c, [&] {
+        EPWI_REQUIRE(c->mlp && c->mlp->ready, EPWI_ESTATE, "the network has no parameters yet");
+        if (params) {
+            EPWI_CUDA(cudaMemcpyAsync(params, c->mlp->w.p, sizeof(float) * mlp::kNParam,
+                                      cudaMemcpyDeviceToHost, c->stream));
+            EPWI_CUDA(cudaStreamSynchronize(c->stream));
+        }
+        if (scale) *scale = c->mlp->out_scale;
+        if (shift) *shift = c->mlp->out_shift;
+    });
+}
+
+epwi_status epwi_mlp_forward(epwi_ctx *c, int64_t n, const float *x, float *y) {
+    return guard(c, [&] {
+        EPWI_REQUIRE(c->mlp && c->mlp->ready, EPWI_ESTATE, "the network has no parameters yet");
+        EPWI_REQUIRE(n >= 0 && (n == 0 || (x && y)), EPWI_EINVAL, "bad argument");
+        if (n == 0) return;
+        DevBuf dx, dy;
+        try {
+            upload(dx, x, (size_t)n * mlp::kIn, c->stream);
+            dy.ensure(sizeof(float) * n);
+            mlp_forward(c, n, dx.as<float>(), dy.as<float>());
+            EPWI_CUDA(cudaMemcpyAsync(y, dy.p, sizeof(float) * n, cudaMemcpyDeviceToHost, c->stream));
+            EPWI_CUDA(cudaStreamSynchronize(c->stream));
+        } catch (...) {
+            cudaStreamSynchronize(c->stream);
+            dx.release();
+            dy.release();
+            throw;
+        }
+        dx.release();
+        dy.release();
+    });
+}
+
+epwi_status epwi_mlp_loss_grad(epwi_ctx *c, int64_t n, const float *x, const float *y,
+                               double *loss, float *grad) {
+    return guard(c, [&] {
+        EPWI_REQUIRE(c->mlp && c->mlp->ready, EPWI_ESTATE, "the network has no parameters yet");
+        EPWI_REQUIRE(n >= 1 && n <= mlp::kMaxBatch && x && y, EPWI_EINVAL, "bad argument");
+        DevBuf dx, dy;
+        try {
+            upload(dx, x, (size_t)n * mlp::kIn, c->stream);
+            upload(dy, y, (size_t)n, c->stream);
+            const double L = mlp_loss_grad(c, n, dx.as<float>(), dy.as<float>(), true);
+            if (loss) *loss = L;
+            if (grad)
+                EPWI_CUDA(cudaMemcpyAsync(grad, c->mlp->grad.p, sizeof(float) * mlp::kNParam,
+                                          cudaMemcpyDeviceToHost, c->stream));
+            EPWI_CUDA(cudaStreamSynchronize(c->stream));
+        } catch (...) {
+            cudaStreamSynchronize(c->stream);
+            dx.release();
+            dy.release();
+            throw;
+        }
+        dx.release();
+        dy.release();
+    });
+}
+
+epwi_status epwi_mlp_get_training_set(epwi_ctx *c, int64_t cap, int32_t *ids, double *t,
+                                      float *x, float *y, int64_t *n) {
+    return guard(c, [&] {
+        EPWI_REQUIRE(c->mlp && c->mlp->n_train > 0, EPWI_ESTATE, "epwi_mlp_train has not been called");
+        const int64_t nt = c->mlp->n_train;
+        if (n) *n = nt;
+        if (!ids && !t && !x && !y) return;
+        EPWI_REQUIRE(cap >= nt, EPWI_ETOOSMALL, "capacity below the training-set size");
+        MlpState &m = *c->mlp;
+        if (ids) EPWI_CUDA(cudaMemcpyAsync(ids, m.ids.p, 16 * (size_t)nt, cudaMemcpyDeviceToHost, c->stream));
+        if (t) EPWI_CUDA(cudaMemcpyAsync(t, m.T64.p, 8 * (size_t)nt, cudaMemcpyDeviceToHost, c->stream));
+        if (x) EPWI_CUDA(cudaMemcpyAsync(x, m.X.p, 4 * (size_t)nt * mlp::kIn, cudaMemcpyDeviceToHost, c->stream));
+        if (y) EPWI_CUDA(cudaMemcpyAsync(y, m.Y.p, 4 * (size_t)nt, cudaMemcpyDeviceToHost, c->stream));
+        EPWI_CUDA(cudaStreamSynchronize(c->stream));
+    });
+}
+
+epwi_status epwi_scatter_rates_is(epwi_ctx *c, double T, double mu, double eta, double emin,
+                                  double emax, int64_t S, double alpha, int32_t stride,
+                                  int32_t proposal, uint64_t seed, int64_t *n_states,
+                                  int64_t *n_pairs) {
+    return guard(c, [&] {
+        require_eigs(c);
+        EPWI_REQUIRE(T > 0 && eta > 0 && std::isfinite(mu) && !(emin > emax), EPWI_EINVAL,
+                     "need T > 0, smear > 0, finite mu and emin <= emax");
+        EPWI_REQUIRE(S >= 1 && S <= (int64_t(1) << 30), EPWI_EINVAL, "samples_per_k out of range");
+        EPWI_REQUIRE(proposal == EPWI_PROPOSAL_UNIFORM || proposal == EPWI_PROPOSAL_LEARNED,
+                     EPWI_EINVAL, "unknown proposal");
+        if (proposal == EPWI_PROPOSAL_LEARNED) {
+            EPWI_REQUIRE(c->mlp && c->mlp->ready, EPWI_ESTATE, "the network has no parameters yet");
+            EPWI_REQUIRE(alpha > 0 && alpha <= 1, EPWI_EINVAL, "alpha must be in (0, 1]");
+            EPWI_REQUIRE(stride >= 1 && c->ng[0] % stride == 0 && c->ng[1] % stride == 0 &&
+                             c->ng[2] % stride == 0,
+                         EPWI_EINVAL, "cell_stride must divide every grid dimension");
+        }
+        run_is(c, T, mu, eta, emin, emax, S, alpha, stride, proposal, seed);
+        if (n_states) *n_states = c->nstates;
+        if (n_pairs) *n_pairs = c->npairs;
+    });
+}
+
+epwi_status epwi_get_is_pairs(epwi_ctx *c, int64_t cap, int32_t *ik, int32_t *iq, double *w,
+                              int64_t *n) {
+    return guard(c, [&] {
+        EPWI_REQUIRE(c->have_is, EPWI_ESTATE, "epwi_scatter_rates_is has not been called");
+        const int64_t np = c->npairs;
+        if (n) *n = np;
+        if (!ik && !iq && !w) return;
+        EPWI_REQUIRE(cap >= np, EPWI_ETOOSMALL, "capacity below the pair count");
+        if (iq && np) EPWI_CUDA(cudaMemcpyAsync(iq, c->is_pairs.p, 4 * (size_t)np, cudaMemcpyDeviceToHost, c->stream));
+        if (w && np) EPWI_CUDA(cudaMemcpyAsync(w, c->is_w.p, 8 * (size_t)np, cudaMemcpyDeviceToHost, c->stream));
+        std::vector<int> kp(c->nkp);
+        if (c->nkp) EPWI_CUDA(cudaMemcpyAsync(kp.data(), c->kpts.p, 4 * (size_t)c->nkp, cudaMemcpyDeviceToHost, c->stream));
+        EPWI_CUDA(cudaStreamSynchronize(c->stream));
+        if (ik)
+            for (int64_t p = 0; p < c->nkp; ++p)
+                for (int64_t j = c->h_is_kp_pairs[p]; j < c->h_is_kp_pairs[p + 1]; ++j) ik[j] = kp[p];
     });
 }
 

@@ -76,6 +76,9 @@ struct DevBuf {
 };
 
 // ----------------------------------------------------------------------------- context
+struct MlpState;                    // learned q-proposal network (mlp.cuh)
+void mlp_free(MlpState *m);
+
 struct epwi_ctx {
     epwi_options opt{};
     cudaStream_t stream = nullptr;
@@ -158,14 +161,24 @@ struct epwi_ctx {
     bool have_sigma = false;
     double sigma[9] = {0};
 
+    // learned proposal and importance-sampled rates
+    MlpState *mlp = nullptr;
+    bool have_is = false;
+    DevBuf is_pairs;               // int32 q index per sampled pair (all k-points)
+    DevBuf is_w;                   // double weight count / (S p(q)) per sampled pair
+    DevBuf is_kp_pairs;            // int64 [nkp+1] pair offsets of the sampled pairs
+    std::vector<int64_t> h_is_kp_pairs;
+
     ~epwi_ctx() {
         DevBuf *all[] = {&Re, &Rp, &Rcart, &Hw, &Phiw, &mode_mass, &gw64, &gw32, &ph64, &ph32,
                          &eps, &eps32, &V, &V32, &vel, &hw, &hwmax32, &hw32, &u, &u32, &eig_flag,
                          &kpts, &win_lo, &win_n, &kp_state, &kp_pairs, &inv_tau, &st_k,
                          &st_n, &focc, &nocc, &pairs, &ghat, &tiles, &tile_part, &kp_tile,
                          &scan_tmp, &red_tmp, &counts, &tc_ptab, &tc_erel, &tc_f32,
-                         &tc_n32, &tc_hw32, &tc_err, &tc_meta};
+                         &tc_n32, &tc_hw32, &tc_err, &tc_meta, &is_pairs, &is_w,
+                         &is_kp_pairs};
         for (DevBuf *b : all) b->release();
+        mlp_free(mlp);
     }
 };
 

@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(128) k_restage_fp64(RestageArgs a) {
     }
 }
 
-template <int WT, int NMT>
+template <int WT, int NMT, bool TERMS>
 __global__ void __launch_bounds__(128) k_scatter_fp64(ScatterArgs a) {
     constexpr int WM = WT ? WT : epc::kMaxW;
     constexpr int NMM = NMT ? NMT : epc::kMaxNm;
@@ -94,6 +94,9 @@ __global__ void __launch_bounds__(128) k_scatter_fp64(ScatterArgs a) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int np = 0; np < nsel; ++np) {
         double rate = 0;
+        double tacc[TERMS ? NMM : 1];
+        if (TERMS)
+            for (int nu = 0; nu < Nm; ++nu) tacc[nu] = 0;
         if (active) {
             double2 G[NMM][WM];
             for (int mu = 0; mu < Nm; ++mu)
@@ -140,10 +143,21 @@ __global__ void __launch_bounds__(128) k_scatter_fp64(ScatterArgs a) {
                         const double y = x2 / a.eta;
                         term += (1.0 + N - fm) * exp(-y * y);
                     }
-                    rate += g2 * term;
+                    if (TERMS) tacc[nu] += g2 * term;
+                    else rate += g2 * term;
                 }
             }
         }
+        if (TERMS) {
+            // terms mode: sum_m |g|^2 [(N + f) delta(x+) + (1 + N - f) delta(x-)] per mode
+            if (active) {
+                const double inv_norm = 1.0 / (sqrt(epc::kPi) * a.eta);
+                double *o = a.tout + ((a.g2_base + pair) * a.tstride + np) * Nm;
+                for (int nu = 0; nu < Nm; ++nu) o[nu] = tacc[nu] * inv_norm;
+            }
+            continue;
+        }
+        if (a.pair_w && active) rate *= a.pair_w[pair];
         for (int o = 16; o > 0; o >>= 1) rate += __shfl_down_sync(0xffffffffu, rate, o);
         if (lane == 0) red[wid][np] = rate;
     }
@@ -205,7 +219,8 @@ void launch_fp64_pair(const RestageArgs &ra, const ScatterArgs &sa, int64_t ntil
 template <int WT, int NMT>
 void launch_fp64_scatter(const ScatterArgs &sa, int64_t ntiles, cudaStream_t st) {
     if (ntiles > 0) {
-        k_scatter_fp64<WT, NMT><<<(unsigned)ntiles, 128, 0, st>>>(sa);
+        if (sa.tout) k_scatter_fp64<WT, NMT, true><<<(unsigned)ntiles, 128, 0, st>>>(sa);
+        else k_scatter_fp64<WT, NMT, false><<<(unsigned)ntiles, 128, 0, st>>>(sa);
         EPWI_CHECK_LAUNCH();
     }
 }
@@ -238,10 +253,12 @@ void sieve_fill_chunk(epwi_ctx *c, int64_t kp0, int64_t kp1, int *pairs);
 // Processes the work set ws (k-points with their pair lists) chunk by chunk.  In rates mode
 // it writes inv_tau for every state of the work set; in g2 mode (g2out != nullptr) it writes
 // |g|^2 per pair instead.
-void process_workset(epwi_ctx *c, const WorkSet &ws, double *g2out) {
+void process_workset(epwi_ctx *c, const WorkSet &ws, double *g2out, double *tout, int tstride) {
     const int W = c->nw, Nm = c->nm;
     const int64_t nrow = (int64_t)c->nRp * Nm * W;
     const bool tc = c->opt.precision != EPWI_FP64;
+    EPWI_REQUIRE(!tc || (!tout && !ws.pair_w), EPWI_EINVAL,
+                 "pair weights and per-pair terms need the FP64 path");
     // chunk limits: pairs and Re->k output size
     const int64_t max_pairs = int64_t(1) << 27;
     const size_t state_bytes = tc ? tc_state_bytes(c) : sizeof(double2) * nrow;
@@ -350,6 +367,9 @@ void process_workset(epwi_ctx *c, const WorkSet &ws, double *g2out) {
         sa.tile_part = c->tile_part.as<double>();
         sa.g2out = g2out;
         sa.g2_base = p_base;
+        sa.pair_w = ws.pair_w ? ws.pair_w + p_base : nullptr;
+        sa.tout = tout;
+        sa.tstride = tstride;
         sa.precision = c->opt.precision;
         sa.nstates_chunk = ns;
         sa.nsel_max = 1;
@@ -365,7 +385,7 @@ void process_workset(epwi_ctx *c, const WorkSet &ws, double *g2out) {
         cudaEventRecord(ev_sc.e[1], c->stream);
         // 4. reduce
         cudaEventRecord(ev_red.e[0], c->stream);
-        if (!g2out && nkpc > 0) {
+        if (!g2out && !tout && nkpc > 0) {
             const double pref = 2.0 * epc::kPi / epc::kHbarEVs / (double)c->nk /
                                 (sqrt(epc::kPi) * c->eta);
             k_reduce_tiles<<<(unsigned)((nkpc + 127) / 128), 128, 0, c->stream>>>(

@@ -52,7 +52,11 @@ struct ScatterArgs {
     double omega_min, eta, ceta;
     double *tile_part;                    // [tile][kMaxW]
     double *g2out;                        // g2 mode output or nullptr
-    int64_t g2_base;
+    int64_t g2_base;                      // global index of the chunk's first pair
+    const double *pair_w;                 // per chunk pair weight (importance sampling) or nullptr
+    double *tout;                         // terms mode output or nullptr:
+                                          // tout[(pair * tstride + np) * Nm + nu]
+    int tstride;
     int precision;
     int nsel_max;                         // largest band window of the chunk
     int64_t nstates_chunk;                // states of the chunk
@@ -65,10 +69,15 @@ struct WorkSet {
     const int64_t *kp_pairs = nullptr;
     std::vector<int64_t> h_kp_state, h_kp_pairs;
     const int *pairs_dev = nullptr;       // all pairs, or nullptr: sieve fill per chunk
+    const double *pair_w = nullptr;       // per pair weight of pairs_dev (FP64 path only)
     int ovr_lo = -1, ovr_nsel = -1;
 };
 
-void process_workset(epwi_ctx *c, const WorkSet &ws, double *g2out);
+// Rates mode (g2out == tout == nullptr): writes inv_tau for every state of the work set.
+// g2 mode: |g|^2 per pair.  Terms mode (FP64 path): the summand of the SERTA rate per pair,
+// band and mode, tout[(pair * tstride + np) * Nm + nu].
+void process_workset(epwi_ctx *c, const WorkSet &ws, double *g2out, double *tout = nullptr,
+                     int tstride = 0);
 void sieve_fill_chunk(epwi_ctx *c, int64_t kp0, int64_t kp1, int *pairs);
 
 // split-precision (tcgen05) path

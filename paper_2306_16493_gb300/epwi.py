@@ -52,7 +52,18 @@ class epwi_stats(C.Structure):
                 ("ms_reduce", C.c_double), ("restage_bytes", C.c_int64),
                 ("scatter_flops", C.c_double), ("precision", C.c_int32), ("sm_count", C.c_int32),
                 ("tc_grid", C.c_int64), ("tc_ctas_per_sm", C.c_int32), ("tc_regs", C.c_int32),
-                ("tc_smem", C.c_int64), ("tc_smem_avail2", C.c_int64)]
+                ("tc_smem", C.c_int64), ("tc_smem_avail2", C.c_int64),
+                ("ms_proposal", C.c_double), ("ms_sampling", C.c_double),
+                ("proposal_flops", C.c_double)]
+
+
+class epwi_mlp_train_options(C.Structure):
+    _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_double),
+                ("background", C.c_double), ("floor_rel", C.c_double), ("seed", C.c_uint64)]
+
+
+EPWI_MLP_NPARAM = 34433
+EPWI_PROPOSAL_UNIFORM, EPWI_PROPOSAL_LEARNED = 0, 1
 
 
 def _load() -> C.CDLL:
@@ -85,6 +96,15 @@ def _load() -> C.CDLL:
         "epwi_get_stats": (I32, [P, P]),
         "epwi_kernel_launches": (I64, []),
         "epwi_conductivity_noalloc": (I32, [I64, P, P, P, D, D, D, I64, P, P]),
+        "epwi_mlp_default_train_options": (V, [P]),
+        "epwi_mlp_train": (I32, [P, D, D, D, D, D, P, P]),
+        "epwi_mlp_set_params": (I32, [P, P]),
+        "epwi_mlp_get_params": (I32, [P, P, P, P]),
+        "epwi_mlp_forward": (I32, [P, I64, P, P]),
+        "epwi_mlp_loss_grad": (I32, [P, I64, P, P, P, P]),
+        "epwi_mlp_get_training_set": (I32, [P, I64, P, P, P, P, P]),
+        "epwi_scatter_rates_is": (I32, [P, D, D, D, D, D, I64, D, I32, I32, C.c_uint64, P, P]),
+        "epwi_get_is_pairs": (I32, [P, I64, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -262,6 +282,81 @@ def epwi_get_stats(ctx) -> dict:
     return {name: getattr(s, name) for name, _ in epwi_stats._fields_}
 
 
+def epwi_mlp_default_train_options() -> epwi_mlp_train_options:
+    o = epwi_mlp_train_options()
+    _lib.epwi_mlp_default_train_options(C.byref(o))
+    return o
+
+
+def epwi_mlp_train(ctx, T, mu, smear, emin, emax, options: epwi_mlp_train_options | None = None):
+    o = options or epwi_mlp_default_train_options()
+    loss = C.c_double()
+    _check(ctx, _lib.epwi_mlp_train(ctx, T, mu, smear, emin, emax, C.byref(o), C.byref(loss)))
+    return loss.value
+
+
+def epwi_mlp_set_params(ctx, params):
+    p = np.ascontiguousarray(params, np.float32)
+    assert p.size == EPWI_MLP_NPARAM
+    _check(ctx, _lib.epwi_mlp_set_params(ctx, _ptr(p)))
+
+
+def epwi_mlp_get_params(ctx):
+    p = np.empty(EPWI_MLP_NPARAM, np.float32)
+    sc, sh = C.c_double(), C.c_double()
+    _check(ctx, _lib.epwi_mlp_get_params(ctx, _ptr(p), C.byref(sc), C.byref(sh)))
+    return p, sc.value, sh.value
+
+
+def epwi_mlp_forward(ctx, x):
+    x = np.ascontiguousarray(x, np.float32).reshape(-1, 9)
+    y = np.empty(len(x), np.float32)
+    _check(ctx, _lib.epwi_mlp_forward(ctx, len(x), _ptr(x), _ptr(y)))
+    return y
+
+
+def epwi_mlp_loss_grad(ctx, x, y):
+    x = np.ascontiguousarray(x, np.float32).reshape(-1, 9)
+    y = np.ascontiguousarray(y, np.float32)
+    g = np.empty(EPWI_MLP_NPARAM, np.float32)
+    loss = C.c_double()
+    _check(ctx, _lib.epwi_mlp_loss_grad(ctx, len(x), _ptr(x), _ptr(y), C.byref(loss), _ptr(g)))
+    return loss.value, g
+
+
+def epwi_mlp_get_training_set(ctx):
+    n = C.c_int64()
+    _check(ctx, _lib.epwi_mlp_get_training_set(ctx, 0, None, None, None, None, C.byref(n)))
+    m = n.value
+    ids = np.empty((m, 4), np.int32)
+    t = np.empty(m)
+    x = np.empty((m, 9), np.float32)
+    y = np.empty(m, np.float32)
+    _check(ctx, _lib.epwi_mlp_get_training_set(ctx, m, _ptr(ids), _ptr(t), _ptr(x), _ptr(y),
+                                               C.byref(n)))
+    return ids, t, x, y
+
+
+def epwi_scatter_rates_is(ctx, T, mu, smear, emin, emax, samples_per_k, alpha=0.1,
+                          cell_stride=1, proposal=EPWI_PROPOSAL_LEARNED, seed=1):
+    ns, npairs = C.c_int64(), C.c_int64()
+    _check(ctx, _lib.epwi_scatter_rates_is(ctx, T, mu, smear, emin, emax, int(samples_per_k),
+                                           float(alpha), int(cell_stride), int(proposal),
+                                           int(seed), C.byref(ns), C.byref(npairs)))
+    return ns.value, npairs.value
+
+
+def epwi_get_is_pairs(ctx):
+    n = C.c_int64()
+    _check(ctx, _lib.epwi_get_is_pairs(ctx, 0, None, None, None, C.byref(n)))
+    m = n.value
+    ik = np.empty(m, np.int32)
+    iq = np.empty(m, np.int32)
+    w = np.empty(m)
+    _check(ctx, _lib.epwi_get_is_pairs(ctx, m, _ptr(ik), _ptr(iq), _ptr(w), C.byref(n)))
+    return ik, iq, w
+
+
 # ------------------------------------------------------------------ convenience wrapper
 class Context:
     """One library context (device memory, stream, last results)."""
@@ -342,3 +437,17 @@ class Context:
 
     def stats(self):
         return epwi_get_stats(self.h)
+
+    def mlp_train(self, T, mu, smear, emin, emax, **opts):
+        o = epwi_mlp_default_train_options()
+        for k, v in opts.items():
+            setattr(o, k, v)
+        return epwi_mlp_train(self.h, T, mu, smear, emin, emax, o)
+
+    def scatter_rates_is(self, T, mu, smear, emin, emax, samples_per_k, alpha=0.1,
+                         cell_stride=1, proposal="learned", seed=1):
+        pr = {"uniform": EPWI_PROPOSAL_UNIFORM, "learned": EPWI_PROPOSAL_LEARNED}[proposal]
+        self.n_states, n_pairs = epwi_scatter_rates_is(self.h, T, mu, smear, emin, emax,
+                                                       samples_per_k, alpha, cell_stride, pr,
+                                                       seed)
+        return self.n_states, n_pairs

@@ -1,0 +1,213 @@
+"""Learned q-proposal on the GPU against the oracle (oracle/mlp_oracle.py, epwi_oracle.py):
+network forward and gradients, the FP64 training terms, the importance-sampling weights and
+the weighted rates, unbiasedness over seeds, and the gain of the learned proposal over the
+uniform one."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import epwi_oracle as O
+from oracle import mlp_oracle as M
+from paper_2306_16493_gb300 import synth
+from tests.parity import group_sums
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def epwi():
+    from paper_2306_16493_gb300 import epwi as E
+    return E
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, float) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _random_params(seed, scale=0.25):
+    rng = np.random.default_rng(seed)
+    p = rng.normal(0, scale, M.N_PARAM).astype(np.float32)
+    return p
+
+
+@pytest.mark.parametrize("n", [1, 37, 1000, 65536])
+def test_mlp_forward_and_gradient_vs_oracle(epwi, n):
+    """FP32 forward/backward on the BF16-rounded weights vs FP64 backprop on the same values:
+    1e-5 relative per parameter block (norm-wise) and on the loss."""
+    ctx = epwi.Context()
+    epwi.epwi_mlp_set_params(ctx.h, _random_params(7))
+    w, scale, shift = epwi.epwi_mlp_get_params(ctx.h)
+    assert np.array_equal(w, M.round_bf16(_random_params(7))) and scale == 1.0 and shift == 0.0
+    rng = np.random.default_rng(n)
+    X = rng.uniform(-1, 1, (n, 9)).astype(np.float32)
+    Y = rng.normal(0, 1, n).astype(np.float32)
+    y_ref, _ = M.forward(w.astype(np.float64), X)
+    y = epwi.epwi_mlp_forward(ctx.h, X)
+    assert _rel(y, y_ref) <= 1e-5
+    loss, g = epwi.epwi_mlp_loss_grad(ctx.h, X, Y)
+    loss_ref, g_ref = M.loss_grad(w.astype(np.float64), X, Y.astype(np.float64))
+    assert abs(loss - loss_ref) <= 1e-6 * loss_ref
+    o = 0
+    for name, shp in M.SHAPES:
+        k = int(np.prod(shp))
+        err = _rel(g[o:o + k], g_ref[o:o + k])
+        assert err <= 1e-5, (name, err)
+        o += k
+
+
+def _tiny_ctx(epwi, grid=6):
+    sysm = synth.tiny_system(1)
+    ctx = epwi.Context()
+    ctx.setup(sysm)
+    ctx.eigs(grid)
+    gr = O.Grids(sysm, (grid,) * 3)
+    return sysm, ctx, gr
+
+
+def test_training_terms_and_features_vs_oracle(epwi):
+    """The training set's FP64 terms t_nu(k,q,n) of Eq. 10 match the oracle's (summed over
+    modes and degenerate bands: the gauge-invariant sums) to 1e-10; its features are
+    bit-identical to the oracle's."""
+    sysm, ctx, gr = _tiny_ctx(epwi)
+    T, eta = 300.0, 0.05
+    mu = gr.band_centre()
+    ctx.mlp_train(T, mu, eta, mu - 0.5, mu + 0.5, epochs=0, background=0.5, seed=3)
+    ids, t, x, y = epwi.epwi_mlp_get_training_set(ctx.h)
+    ik, iq, band, mode = ids.T
+    assert np.array_equal(x, M.features(gr.ngrid, ik, iq, gr.eps[ik, band] - mu, band, mode,
+                                        sysm.nw, gr.hw.shape[1]))
+    worst, checked = 0.0, 0
+    for k in np.unique(ik):
+        sel = ik == k
+        qs = np.unique(iq[sel])
+        bands = np.unique(band[sel])
+        ref = O.pair_terms_k(gr, int(k), bands, T, mu, eta, 6.0, qs).sum(axis=1)   # [q, n]
+        got = np.zeros_like(ref)
+        qi = np.searchsorted(qs, iq[sel])
+        bi = np.searchsorted(bands, band[sel])
+        # duplicated (background) pairs repeat their terms: count each (q, n, nu) once
+        seen = set()
+        for a, b_, m_, v in zip(qi, bi, mode[sel], t[sel]):
+            if (a, b_, m_) in seen:
+                continue
+            seen.add((a, b_, m_))
+            got[a, b_] += v
+        scale = np.abs(ref).max() + 1e-300
+        for j in range(len(qs)):
+            gg = group_sums(np.zeros(len(bands), int), bands, got[j], gr.eps[k][None, :])
+            rr = group_sums(np.zeros(len(bands), int), bands, ref[j], gr.eps[k][None, :])
+            for key in rr:
+                worst = max(worst, abs(gg[key] - rr[key]) / max(abs(rr[key]), 1e-9 * scale))
+                checked += 1
+    assert checked > 1000 and worst <= 1e-10, (worst, checked)
+    assert (t >= 0).all() and (t > 0).mean() > 0.2
+
+
+def test_is_uniform_weighted_rates_vs_oracle(epwi):
+    """Uniform proposal: counts are integers summing to S per k-point, and the weighted FP64
+    rates equal the oracle's weighted sum over the same pairs to 1e-10."""
+    sysm, ctx, gr = _tiny_ctx(epwi)
+    T, eta = 300.0, 0.05
+    mu = gr.band_centre()
+    S = 300
+    ns, npairs = ctx.scatter_rates_is(T, mu, eta, mu - 0.3, mu + 0.3, S, proposal="uniform",
+                                      seed=11)
+    ik, iq, w = epwi.epwi_get_is_pairs(ctx.h)
+    counts = w * S / gr.nk
+    assert np.allclose(counts, np.round(counts), rtol=0, atol=1e-9)
+    for k in np.unique(ik):
+        assert int(round(counts[ik == k].sum())) == S
+        q = iq[ik == k]
+        assert np.all(np.diff(q) > 0)
+    k_s, b_s, r = ctx.rates()
+    worst = 0.0
+    for k in np.unique(k_s):
+        bands = b_s[k_s == k]
+        sel = ik == k
+        ref, _ = O.inv_tau_k(gr, int(k), bands, T, mu, eta, q_list=iq[sel], q_weights=w[sel])
+        got = r[k_s == k]
+        gs = group_sums(np.zeros(len(bands), int), bands, got, gr.eps[k][None, :])
+        rs = group_sums(np.zeros(len(bands), int), bands, ref, gr.eps[k][None, :])
+        for key in rs:
+            worst = max(worst, abs(gs[key] - rs[key]) / max(abs(rs[key]), 1e-30))
+    assert worst <= 1e-10, worst
+
+
+def _full_rates(ctx, T, mu, eta, emin, emax):
+    ctx.scatter_rates(T, mu, eta, emin, emax)
+    k, b, r = ctx.rates()
+    return k, b, r
+
+
+def test_is_learned_weights_and_unbiasedness(epwi):
+    """Learned proposal on the tiny system: the weights are c / (S p) with p the oracle's
+    band-mixture probability from the same network (counts integral to 1e-4, summing to S),
+    and the mean over 32 seeds of the summed rates is within 4 standard errors of the
+    full-grid FP64 sum."""
+    sysm, ctx, gr = _tiny_ctx(epwi)
+    T, eta = 300.0, 0.05
+    mu = gr.band_centre()
+    lo, hi = mu - 0.3, mu + 0.3
+    ctx.mlp_train(T, mu, eta, lo, hi, epochs=20, seed=5)
+    params, scale, shift = epwi.epwi_mlp_get_params(ctx.h)
+    S, s, alpha = 200, 2, 0.2
+    ctx.scatter_rates_is(T, mu, eta, lo, hi, S, alpha=alpha, cell_stride=s, seed=1)
+    ik, iq, w = epwi.epwi_get_is_pairs(ctx.h)
+    k_s, b_s, _ = ctx.rates()
+    cen = M.cell_centres(gr.ngrid, s)
+    Nm = gr.hw.shape[1]
+    for k in np.unique(ik)[:12]:
+        bands = b_s[k_s == k]
+        probs = []
+        for b in bands:
+            X = M.features(gr.ngrid, np.full(len(cen) * Nm, k), np.repeat(cen, Nm),
+                           gr.eps[k, b] - mu, b, np.tile(np.arange(Nm), len(cen)), sysm.nw, Nm)
+            yh, _ = M.forward(params.astype(np.float64), X)
+            probs.append(M.cell_probs(scale * yh.reshape(len(cen), Nm)))
+        sel = ik == k
+        p = M.p_mix(iq[sel], gr.ngrid, s, alpha, np.array(probs))
+        c = w[sel] * S * p
+        assert np.allclose(c, np.round(c), rtol=1e-4, atol=0), np.abs(c - np.round(c)).max()
+        assert int(round(c.sum())) == S
+    _, _, full = _full_rates(ctx, T, mu, eta, lo, hi)
+    tot = full.sum()
+    est = []
+    for seed in range(32):
+        ctx.scatter_rates_is(T, mu, eta, lo, hi, S, alpha=alpha, cell_stride=s, seed=100 + seed)
+        est.append(ctx.rates()[2].sum())
+    est = np.array(est)
+    se = est.std(ddof=1) / math.sqrt(len(est))
+    assert abs(est.mean() - tot) <= 4 * se + 1e-12 * tot, (est.mean(), tot, se)
+
+
+def test_learned_proposal_gain_si_like(epwi):
+    """Si-like system: train on a coarse grid, estimate 1/tau on a finer one.  At equal S the
+    learned proposal's error against the full-grid FP64 rates is several times smaller than
+    the uniform proposal's (the gain this test reports and bounds)."""
+    sysm = synth.si_like_system(3)
+    ctx = epwi.Context()
+    ctx.setup(sysm)
+    T, eta = 300.0, 0.01
+    ctx.eigs(16)
+    mu16 = ctx.find_mu(T, 1e18, sysm.n_valence)
+    _, cbm16 = ctx.band_edges(sysm.n_valence)
+    loss = ctx.mlp_train(T, mu16, eta, cbm16, cbm16 + 0.25, epochs=60, seed=2)
+    ctx.eigs(24)
+    mu = ctx.find_mu(T, 1e18, sysm.n_valence)
+    _, cbm = ctx.band_edges(sysm.n_valence)
+    lo, hi = cbm, cbm + 0.25
+    _, _, full = _full_rates(ctx, T, mu, eta, lo, hi)
+    S = 2000
+    err = {}
+    for prop, kw in (("uniform", {}), ("learned", dict(alpha=0.1, cell_stride=2))):
+        e = []
+        for seed in range(4):
+            ctx.scatter_rates_is(T, mu, eta, lo, hi, S, proposal=prop, seed=7 + seed, **kw)
+            r = ctx.rates()[2]
+            e.append(np.sqrt(np.mean(((r - full) / full) ** 2)))
+        err[prop] = float(np.mean(e))
+    gain = err["uniform"] / err["learned"]
+    print(f"training loss {loss:.3f}; rms relative error uniform {err['uniform']:.3e} "
+          f"learned {err['learned']:.3e}; gain {gain:.1f}x (variance {gain ** 2:.0f}x)")
+    assert gain >= 3.0, err
