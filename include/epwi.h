@@ -252,8 +252,8 @@ epwi_status epwi_conductivity_noalloc(int64_t n_states, const double *eps_dev, c
 typedef enum { EPWI_PROPOSAL_UNIFORM = 0, EPWI_PROPOSAL_LEARNED = 1 } epwi_proposal;
 
 typedef struct {
-    int32_t epochs;             /* passes over the training set (default 60) */
-    int32_t batch;              /* samples per Adam step, <= 65536 (default 4096) */
+    int32_t epochs;             /* passes over the training set (default 100) */
+    int32_t batch;              /* samples per Adam step, <= 65536 (default 512) */
     double lr;                  /* Adam step size; cosine decay to lr/20 (default 2e-3) */
     double background;          /* uniformly drawn (k,q) pairs per sieved pair (default 1) */
     double floor_rel;           /* targets are log(t + floor_rel * max t) (default 1e-8) */
@@ -267,8 +267,12 @@ void epwi_mlp_default_train_options(epwi_mlp_train_options *opt);
  * plus background pairs drawn uniformly, times every window band and mode.  Its targets come
  * from the FP64 kernels at (T, mu, smear).  The network is initialised from opt->seed unless
  * parameters were set or trained before.  final_loss (may be NULL) receives the mean of
- * (yhat - y)^2 / 2 over the training set.  Errors: ESTATE, EINVAL (empty window),
- * EUNSUPPORTED (more than 2^26 sieved pairs). */
+ * (yhat - y)^2 / 2 over the training set.
+ * The terms are Gaussians of width smear in energy, so on a coarse grid they are spikes at
+ * its q points.  A network trained on them transfers poorly to a finer grid.  Training with a
+ * smear of 2-4x the production one spreads them into a shell the network can learn; the
+ * estimate stays unbiased whatever the proposal.
+ * Errors: ESTATE, EINVAL (empty window), EUNSUPPORTED (more than 2^26 sieved pairs). */
 epwi_status epwi_mlp_train(epwi_ctx *ctx, double T_K, double mu_eV, double smear_eV,
                            double emin_eV, double emax_eV, const epwi_mlp_train_options *opt,
                            double *final_loss);

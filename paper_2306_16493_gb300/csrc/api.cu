@@ -575,8 +575,8 @@ epwi_status epwi_g2(epwi_ctx *c, int64_t npairs, const int32_t *ik, const int32_
 
 void epwi_mlp_default_train_options(epwi_mlp_train_options *o) {
     if (!o) return;
-    o->epochs = 60;
-    o->batch = 4096;
+    o->epochs = 100;
+    o->batch = 512;
     o->lr = 2e-3;
     o->background = 1.0;
     o->floor_rel = 1e-8;

@@ -26,6 +26,7 @@
 
 #include "mlp.cuh"
 #include "scatter.cuh"
+#include "sieve.cuh"
 
 namespace {
 using namespace mlp;
@@ -225,9 +226,10 @@ struct SampleArgs {
     const int *kpts;               // chunk k-points
     const int64_t *kp_state;       // global state offsets of the chunk k-points
     int64_t s_base;                // first state of the chunk
-    const int *win_n;
+    const int *win_lo, *win_n;
     const double *cdf, *tot;       // per chunk state (learned proposal only)
     int *counts;                   // [kp_local][nq]
+    SieveArgs sv;                  // drawn q failing the sieve have t = 0 and are dropped
 };
 
 __device__ __forceinline__ uint64_t draw_key(uint64_t seed, int ik, int64_t s) {
@@ -298,12 +300,23 @@ __device__ __forceinline__ int64_t block_excl_scan_i64(int64_t v, int64_t *sm, i
     return ex;
 }
 
-__global__ void __launch_bounds__(256) k_is_count(int64_t nq, const int *__restrict__ counts,
-                                                  int64_t *__restrict__ out) {
+// A drawn q is evaluated when the sieve keeps (k, q); otherwise every term t(k, q) is zero.
+__device__ __forceinline__ bool keep_draw(const SampleArgs &a, int ik, int nsel, const double *en,
+                                          const float *en32, int64_t q) {
+    return pair_valid(a.sv, nsel, en, en32, q, kplusq(a.g, ik, q));
+}
+
+__global__ void __launch_bounds__(256) k_is_count(SampleArgs a, int64_t *__restrict__ out) {
     __shared__ int64_t sm[33];
-    const int *cn = counts + (int64_t)blockIdx.x * nq;
+    __shared__ double en[epc::kMaxW];
+    __shared__ float en32[epc::kMaxW];
+    const int ik = a.kpts[blockIdx.x];
+    const int nsel = a.win_n[ik];
+    load_window(a.sv, ik, a.win_lo[ik], nsel, en, en32);
+    const int *cn = a.counts + (int64_t)blockIdx.x * a.nq;
     int64_t c = 0;
-    for (int64_t q = threadIdx.x; q < nq; q += blockDim.x) c += cn[q] > 0;
+    for (int64_t q = threadIdx.x; q < a.nq; q += blockDim.x)
+        c += cn[q] > 0 && keep_draw(a, ik, nsel, en, en32, q);
     int64_t tot;
     block_excl_scan_i64(c, sm, tot);
     if (threadIdx.x == 0) out[blockIdx.x] = tot;
@@ -314,16 +327,19 @@ __global__ void __launch_bounds__(256) k_is_count(int64_t nq, const int *__restr
 __global__ void __launch_bounds__(256) k_is_fill(SampleArgs a, const int64_t *__restrict__ off,
                                                  int *__restrict__ pairs, double *__restrict__ w) {
     __shared__ int64_t sm[33];
+    __shared__ double en[epc::kMaxW];
+    __shared__ float en32[epc::kMaxW];
     const int64_t kpl = blockIdx.x;
     const int ik = a.kpts[kpl];
     const int nwin = a.win_n[ik];
+    load_window(a.sv, ik, a.win_lo[ik], nwin, en, en32);
     const int64_t st0 = a.kp_state[kpl] - a.s_base;
     const int *cn = a.counts + kpl * a.nq;
     int64_t base = off[kpl];
     const double inv_s3 = 1.0 / ((double)a.s * a.s * a.s);
     for (int64_t q0 = 0; q0 < a.nq; q0 += blockDim.x) {
         const int64_t q = q0 + threadIdx.x;
-        const int cnt = q < a.nq ? cn[q] : 0;
+        const int cnt = q < a.nq && cn[q] > 0 && keep_draw(a, ik, nwin, en, en32, q) ? cn[q] : 0;
         int64_t tot;
         const int64_t ex = block_excl_scan_i64(cnt > 0, sm, tot);
         if (cnt > 0) {
@@ -583,7 +599,9 @@ void run_is(epwi_ctx *c, double T, double mu, double eta, double emin, double em
             sa.kpts = c->kpts.as<int>() + kp0;
             sa.kp_state = c->kp_state.as<int64_t>() + kp0;
             sa.s_base = s0;
+            sa.win_lo = c->win_lo.as<int>();
             sa.win_n = c->win_n.as<int>();
+            sa.sv = make_sieve_args(c);
             sa.cdf = nullptr;
             sa.tot = nullptr;
             if (learned && nsc > 0) {
@@ -645,7 +663,7 @@ void run_is(epwi_ctx *c, double T, double mu, double eta, double emin, double em
             }
             cnt.ensure(sizeof(int64_t) * (nkc + 1));
             off.ensure(sizeof(int64_t) * (nkc + 1));
-            k_is_count<<<(unsigned)nkc, 256, 0, st>>>(nq, counts.as<int>(), cnt.as<int64_t>());
+            k_is_count<<<(unsigned)nkc, 256, 0, st>>>(sa, cnt.as<int64_t>());
             EPWI_CHECK_LAUNCH();
             int64_t npc = 0;
             scan_exclusive_i64(c, cnt.as<int64_t>(), off.as<int64_t>(), nkc, &npc);

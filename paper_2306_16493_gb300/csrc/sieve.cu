@@ -8,6 +8,7 @@
 // error; only candidates whose nearest |x| lies within delta of c eta are re-evaluated in
 // FP64 in the oracle's rounding order, so every decision equals the FP64 one.
 #include "epwi_internal.cuh"
+#include "sieve.cuh"
 
 namespace {
 
@@ -108,71 +109,6 @@ __global__ void k_states(int64_t nkp, const int *__restrict__ kpts, const int *_
     }
 }
 
-// ------------------------------------------------------------------- sieve
-struct SieveArgs {
-    GridInfo g;
-    int W, Nm;
-    const double *eps;
-    const float *eps32;
-    const double *hw;
-    const float *hw32;       // per mode, -1 for dropped modes
-    const float *hwmax32;
-    double omega_min, ceta;
-    float ceta32, delta32;   // delta32 bounds |x_fp32 - x_fp64| for every candidate
-    float lim_extra;         // c eta + delta32
-};
-
-// Decision for one candidate (k, q).  FP32 evaluates x = (e_n + s w) - e_m for every
-// (n, m, nu, s); a value inside c eta - delta (outside c eta + delta) is decided in FP32,
-// anything closer to the boundary is re-evaluated in FP64 with the oracle's rounding order,
-// so the outcome equals an FP64 evaluation.
-__device__ __forceinline__ bool pair_valid(const SieveArgs &a, int nsel, const double *en,
-                                           const float *en32, int64_t iq, int64_t ikq) {
-    const float hm = a.hwmax32[iq];
-    if (hm < 0.f) return false;
-    const float lim = hm + a.lim_extra;
-    const float inner = a.ceta32 - a.delta32, outer = a.ceta32 + a.delta32;
-    bool ambiguous = false;
-    for (int m = 0; m < a.W; ++m) {
-        const float em32 = a.eps32[ikq * a.W + m];
-        for (int n = 0; n < nsel; ++n) {
-            const float d = en32[n] - em32;
-            if (!(fabsf(d) <= lim)) continue;
-            for (int nu = 0; nu < a.Nm; ++nu) {
-                const float w = a.hw32[iq * a.Nm + nu];
-                if (w < 0.f) continue;
-                const float x1 = fabsf(d + w), x2 = fabsf(d - w);
-                const float xm = fminf(x1, x2);
-                if (xm <= inner) return true;
-                if (xm <= outer) ambiguous = true;
-            }
-        }
-    }
-    if (!ambiguous) return false;
-    for (int m = 0; m < a.W; ++m) {
-        const double em = a.eps[ikq * a.W + m];
-        for (int nu = 0; nu < a.Nm; ++nu) {
-            const double w = a.hw[iq * a.Nm + nu];
-            if (!(w >= a.omega_min)) continue;
-            for (int n = 0; n < nsel; ++n) {
-                const double x1 = (en[n] + w) - em;
-                const double x2 = (en[n] - w) - em;
-                if (fabs(x1) <= a.ceta || fabs(x2) <= a.ceta) return true;
-            }
-        }
-    }
-    return false;
-}
-
-__device__ __forceinline__ void load_window(const SieveArgs &a, int ik, int lo, int nsel,
-                                            double *en, float *en32) {
-    if (threadIdx.x < nsel) {
-        en[threadIdx.x] = a.eps[(int64_t)ik * a.W + lo + threadIdx.x];
-        en32[threadIdx.x] = a.eps32[(int64_t)ik * a.W + lo + threadIdx.x];
-    }
-    __syncthreads();
-}
-
 // Candidate order shared by count and fill: the (i2, i3) plane index p runs over blocks of
 // blockDim.x (one p per thread), and for each block i1 runs 0..N1-1.  k+q is updated
 // incrementally (no division per candidate).
@@ -253,6 +189,8 @@ __global__ void __launch_bounds__(256) k_sieve_fill(SieveArgs a, int64_t kp0,
     }
 }
 
+}  // namespace
+
 SieveArgs make_sieve_args(epwi_ctx *c) {
     SieveArgs a;
     a.g = make_grid_info(c);
@@ -271,8 +209,6 @@ SieveArgs make_sieve_args(epwi_ctx *c) {
     a.lim_extra = (float)(a.ceta + a.delta32 + 1e-5);
     return a;
 }
-
-}  // namespace
 
 void scan_exclusive_i64(epwi_ctx *c, const int64_t *in, int64_t *out, int64_t n, int64_t *total) {
     // out has n + 1 entries; out[n] = sum.  Recursive over block sums.

@@ -1,0 +1,71 @@
+// Energy-conservation sieve predicate (internal), shared by the sieve kernels and the
+// importance-sampling path (Sec. III A).
+#pragma once
+
+#include "epwi_internal.cuh"
+
+struct SieveArgs {
+    GridInfo g;
+    int W, Nm;
+    const double *eps;
+    const float *eps32;
+    const double *hw;
+    const float *hw32;       // per mode, -1 for dropped modes
+    const float *hwmax32;
+    double omega_min, ceta;
+    float ceta32, delta32;   // delta32 bounds |x_fp32 - x_fp64| for every candidate
+    float lim_extra;         // c eta + delta32
+};
+
+// Decision for one candidate (k, q).  FP32 evaluates x = (e_n + s w) - e_m for every
+// (n, m, nu, s); a value inside c eta - delta (outside c eta + delta) is decided in FP32,
+// anything closer to the boundary is re-evaluated in FP64 with the oracle's rounding order,
+// so the outcome equals an FP64 evaluation.
+__device__ __forceinline__ bool pair_valid(const SieveArgs &a, int nsel, const double *en,
+                                           const float *en32, int64_t iq, int64_t ikq) {
+    const float hm = a.hwmax32[iq];
+    if (hm < 0.f) return false;
+    const float lim = hm + a.lim_extra;
+    const float inner = a.ceta32 - a.delta32, outer = a.ceta32 + a.delta32;
+    bool ambiguous = false;
+    for (int m = 0; m < a.W; ++m) {
+        const float em32 = a.eps32[ikq * a.W + m];
+        for (int n = 0; n < nsel; ++n) {
+            const float d = en32[n] - em32;
+            if (!(fabsf(d) <= lim)) continue;
+            for (int nu = 0; nu < a.Nm; ++nu) {
+                const float w = a.hw32[iq * a.Nm + nu];
+                if (w < 0.f) continue;
+                const float x1 = fabsf(d + w), x2 = fabsf(d - w);
+                const float xm = fminf(x1, x2);
+                if (xm <= inner) return true;
+                if (xm <= outer) ambiguous = true;
+            }
+        }
+    }
+    if (!ambiguous) return false;
+    for (int m = 0; m < a.W; ++m) {
+        const double em = a.eps[ikq * a.W + m];
+        for (int nu = 0; nu < a.Nm; ++nu) {
+            const double w = a.hw[iq * a.Nm + nu];
+            if (!(w >= a.omega_min)) continue;
+            for (int n = 0; n < nsel; ++n) {
+                const double x1 = (en[n] + w) - em;
+                const double x2 = (en[n] - w) - em;
+                if (fabs(x1) <= a.ceta || fabs(x2) <= a.ceta) return true;
+            }
+        }
+    }
+    return false;
+}
+
+__device__ __forceinline__ void load_window(const SieveArgs &a, int ik, int lo, int nsel,
+                                            double *en, float *en32) {
+    if (threadIdx.x < nsel) {
+        en[threadIdx.x] = a.eps[(int64_t)ik * a.W + lo + threadIdx.x];
+        en32[threadIdx.x] = a.eps32[(int64_t)ik * a.W + lo + threadIdx.x];
+    }
+    __syncthreads();
+}
+
+SieveArgs make_sieve_args(epwi_ctx *c);

@@ -46,7 +46,7 @@ def test_host_only_defaults():
     o = epwi.epwi_default_options()
     assert o.precision == epwi.EPWI_FP64 and o.sieve_c == 6.0 and o.omega_min_eV == 1e-4
     t = epwi.epwi_mlp_default_train_options()
-    assert (t.epochs, t.batch, t.lr, t.background, t.floor_rel, t.seed) == (60, 4096, 2e-3, 1.0,
+    assert (t.epochs, t.batch, t.lr, t.background, t.floor_rel, t.seed) == (100, 512, 2e-3, 1.0,
                                                                             1e-8, 1)
 
 

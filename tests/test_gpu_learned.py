@@ -105,8 +105,9 @@ def test_training_terms_and_features_vs_oracle(epwi):
 
 
 def test_is_uniform_weighted_rates_vs_oracle(epwi):
-    """Uniform proposal: counts are integers summing to S per k-point, and the weighted FP64
-    rates equal the oracle's weighted sum over the same pairs to 1e-10."""
+    """Uniform proposal: counts are integers, at most S per k-point; the evaluated pairs are
+    drawn q that the sieve keeps (the others have t = 0); the weighted FP64 rates equal the
+    oracle's weighted sum over the same pairs to 1e-10."""
     sysm, ctx, gr = _tiny_ctx(epwi)
     T, eta = 300.0, 0.05
     mu = gr.band_centre()
@@ -116,11 +117,12 @@ def test_is_uniform_weighted_rates_vs_oracle(epwi):
     ik, iq, w = epwi.epwi_get_is_pairs(ctx.h)
     counts = w * S / gr.nk
     assert np.allclose(counts, np.round(counts), rtol=0, atol=1e-9)
+    k_s, b_s, r = ctx.rates()
     for k in np.unique(ik):
-        assert int(round(counts[ik == k].sum())) == S
+        assert int(round(counts[ik == k].sum())) <= S
         q = iq[ik == k]
         assert np.all(np.diff(q) > 0)
-    k_s, b_s, r = ctx.rates()
+        assert np.isin(q, O.sieve_k(gr, int(k), b_s[k_s == k], eta)).all()
     worst = 0.0
     for k in np.unique(k_s):
         bands = b_s[k_s == k]
@@ -169,7 +171,7 @@ def test_is_learned_weights_and_unbiasedness(epwi):
         p = M.p_mix(iq[sel], gr.ngrid, s, alpha, np.array(probs))
         c = w[sel] * S * p
         assert np.allclose(c, np.round(c), rtol=1e-4, atol=0), np.abs(c - np.round(c)).max()
-        assert int(round(c.sum())) == S
+        assert int(round(c.sum())) <= S
     _, _, full = _full_rates(ctx, T, mu, eta, lo, hi)
     tot = full.sum()
     est = []
@@ -182,9 +184,10 @@ def test_is_learned_weights_and_unbiasedness(epwi):
 
 
 def test_learned_proposal_gain_si_like(epwi):
-    """Si-like system: train on a coarse grid, estimate 1/tau on a finer one.  At equal S the
-    learned proposal's error against the full-grid FP64 rates is several times smaller than
-    the uniform proposal's (the gain this test reports and bounds)."""
+    """Si-like system: train on a 16^3 grid with a 4x broadened delta, estimate 1/tau on 24^3
+    with the production smearing.  At equal S the learned proposal's rms error against the
+    full-grid FP64 rates is several times smaller than the uniform proposal's (the gain this
+    test reports and bounds)."""
     sysm = synth.si_like_system(3)
     ctx = epwi.Context()
     ctx.setup(sysm)
@@ -192,7 +195,7 @@ def test_learned_proposal_gain_si_like(epwi):
     ctx.eigs(16)
     mu16 = ctx.find_mu(T, 1e18, sysm.n_valence)
     _, cbm16 = ctx.band_edges(sysm.n_valence)
-    loss = ctx.mlp_train(T, mu16, eta, cbm16, cbm16 + 0.25, epochs=60, seed=2)
+    loss = ctx.mlp_train(T, mu16, 4 * eta, cbm16 - 0.05, cbm16 + 0.3, seed=2)
     ctx.eigs(24)
     mu = ctx.find_mu(T, 1e18, sysm.n_valence)
     _, cbm = ctx.band_edges(sysm.n_valence)
@@ -200,7 +203,7 @@ def test_learned_proposal_gain_si_like(epwi):
     _, _, full = _full_rates(ctx, T, mu, eta, lo, hi)
     S = 2000
     err = {}
-    for prop, kw in (("uniform", {}), ("learned", dict(alpha=0.1, cell_stride=2))):
+    for prop, kw in (("uniform", {}), ("learned", dict(alpha=0.1, cell_stride=1))):
         e = []
         for seed in range(4):
             ctx.scatter_rates_is(T, mu, eta, lo, hi, S, proposal=prop, seed=7 + seed, **kw)
@@ -210,4 +213,4 @@ def test_learned_proposal_gain_si_like(epwi):
     gain = err["uniform"] / err["learned"]
     print(f"training loss {loss:.3f}; rms relative error uniform {err['uniform']:.3e} "
           f"learned {err['learned']:.3e}; gain {gain:.1f}x (variance {gain ** 2:.0f}x)")
-    assert gain >= 3.0, err
+    assert gain >= 4.0, err
