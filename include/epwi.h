@@ -320,6 +320,66 @@ epwi_status epwi_scatter_rates_is(epwi_ctx *ctx, double T_K, double mu_eV, doubl
 epwi_status epwi_get_is_pairs(epwi_ctx *ctx, int64_t capacity, int32_t *ik, int32_t *iq,
                               double *weight, int64_t *n);
 
+/* ---------------------------------------------------------------------------------------
+ * Batches of uneven systems.  Each system brings its own nw, nat, R-sets and grid.
+ *
+ * epwi_batch_plan runs each system's eigensolves, window and sieve count, then picks a tile
+ * shape per system: the pairs per work item M_t and the K chunk of the Rp sum.  The
+ * autotuner chooses it by timing candidates on a sample of each class (nw, 3 nat, n_Rp) and
+ * caches the choice per class for the process.  The plan then captures one CUDA graph.  In
+ * the graph, each system gets its eigensolves, sieve fill and FP32 Re->k stage.  Then ONE
+ * persistent kernel works through a queue of (system, k-point, band, block of q) items
+ * covering every system.  Per item it runs the Rp->q product, the rotations and the delta
+ * sum of Eq. 10 in FP32, writing one FP64 sum per item.  Fixed-order FP64 reductions then
+ * give 1/tau and sigma (Eq. 12) per system.  epwi_batch_run launches the graph.
+ *
+ * Limits: nw * 3 nat <= 512, states with an item queue below 2^31 items.
+ * ------------------------------------------------------------------------------------- */
+typedef struct epwi_batch epwi_batch;
+
+typedef struct {
+    int64_t n_systems, n_states, n_pairs, n_items;
+    int64_t graph_nodes;        /* nodes of the captured step */
+    int64_t persistent_ctas;    /* CTAs of the persistent kernel */
+    int64_t smem_bytes;         /* its dynamic shared memory per CTA */
+    int64_t runs;               /* graph launches so far */
+    double ms_plan;             /* device time of the planning pass (incl. autotuning) */
+    double ms_graph;            /* last graph launch, whole step */
+    double ms_persistent;       /* last graph launch, the persistent kernel */
+    double scatter_flops;       /* algorithmic flops of the Rp->q products (one pass) */
+    double restage_flops;       /* algorithmic flops of the Re->k stages */
+} epwi_batch_stats;
+
+/* Creates a batch on opt->device (NULL: defaults).  With opt->cuda_stream NULL the batch makes
+ * its own non-blocking stream. */
+epwi_status epwi_batch_create(epwi_batch **batch, const epwi_options *opt);
+void epwi_batch_destroy(epwi_batch *batch);
+const char *epwi_batch_last_error(const epwi_batch *batch);
+/* Copies and validates nsys systems (as epwi_setup) with their Gamma-centred grids
+ * grids[nsys][3]. */
+epwi_status epwi_batch_setup(epwi_batch *batch, int32_t nsys, const epwi_system *systems,
+                             const int32_t *grids);
+/* Plans the step for temperature T, chemical potentials mu[nsys], smearing and per-system
+ * windows [emin, emax]; autotune_tiles != 0 runs the autotuner (otherwise a default shape,
+ * or the one set by epwi_batch_set_tile).  n_pairs (may be NULL) receives the sieved pairs
+ * of all systems. */
+epwi_status epwi_batch_plan(epwi_batch *batch, double T_K, const double *mu_eV, double smear_eV,
+                            const double *emin_eV, const double *emax_eV, int32_t autotune_tiles,
+                            int64_t *n_pairs);
+/* One step (one graph launch); sigma (host, [nsys][9] S/m, may be NULL) receives every
+ * system's conductivity. */
+epwi_status epwi_batch_run(epwi_batch *batch, double *sigma);
+/* 1/tau of system s after a run (layout as epwi_get_rates; size query with NULL outputs). */
+epwi_status epwi_batch_get_rates(epwi_batch *batch, int32_t s, int64_t capacity, int32_t *k_idx,
+                                 int32_t *band, double *inv_tau_s, int64_t *n_states);
+/* Forces the tile shape of system s for the next plan (mt = 0 clears it). */
+epwi_status epwi_batch_set_tile(epwi_batch *batch, int32_t s, int32_t mt, int32_t kc);
+/* Tile shape of system s in the current plan; source: 0 default, 1 autotuned now, 2 from
+ * the autotuner's cache, 3 set by epwi_batch_set_tile. */
+epwi_status epwi_batch_get_tile(epwi_batch *batch, int32_t s, int32_t *mt, int32_t *kc,
+                                int32_t *source);
+epwi_status epwi_batch_get_stats(epwi_batch *batch, epwi_batch_stats *out);
+
 /* Number of kernels this library has launched in the process so far (all contexts). */
 int64_t epwi_kernel_launches(void);
 

@@ -1,0 +1,949 @@
+// Many systems of uneven size in one step.  Each system has its own nw, nat, R-sets and grid.
+//
+// Planning runs each system's eigensolves, window and sieve count, allocates everything, and
+// builds one work queue.  A queue item is (system, k-point, window band, block of M_t
+// sieved q).  A step is then one CUDA graph:
+//   1. per system: phase table, H(k)/D(q) eigensolves, occupations, sieve fill, and the FP32
+//      Re->k stage (Eq. 16, inner bracket);
+//   2. ONE persistent kernel.  Its CTAs take queue items through an atomic counter and do,
+//      per item, the Rp->q product, the rotations by V(k+q) and u(q), and the Gaussian
+//      delta sum of the SERTA rate (Eq. 16, Eq. 10) in FP32.  Each item's sum is written in
+//      FP64 to its own slot;
+//   3. fixed-order FP64 reductions of the slots into 1/tau, then sigma per system (Eq. 12).
+// The queue is ordered by per-item cost, largest first.  Results do not depend on which CTA
+// takes which item: every item has its own output slot and the sums run in item order.
+//
+// Each system has its own tile shape: the pairs per item M_t and the K chunk of the Rp sum.
+// An autotuner picks it by timing the persistent kernel on a sample of each class
+// (W, N_m, n_Rp) and caches the choice per class for the process.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "epwi_internal.cuh"
+#include "scatter.cuh"
+
+namespace {
+
+constexpr int kBT = 256;          // threads of the persistent kernel
+constexpr int kAcc = 32;          // complex accumulators per thread (Rp->q stage)
+constexpr int kMaxMt = 512;       // pairs per item, upper bound
+constexpr int kNmB = 18;          // modes, upper bound
+constexpr size_t kSmemCap = 200 * 1024;
+
+struct BSys {
+    GridInfo g;
+    int W, Nm, nRp, NW;           // NW = Nm * W columns of the Rp->q product
+    int CW, RG;                   // columns per thread group (<= 256), row groups = 256 / CW
+    int Mt, KC;                   // tile shape: pairs per item, K chunk
+    const int *Rp;
+    const float2 *ph32;
+    const float2 *V32;
+    const float2 *u32;
+    const float *erel, *f32, *n32, *hw32;
+    const float2 *ghat;           // [state][nRp][Nm][W]
+    const int *pairs;             // sieved q of every k-point, grouped by k-point
+    const int64_t *kp_pairs;      // [nkp + 1]
+    const int *kpts, *win_lo;
+    const int64_t *kp_state;      // [nkp + 1]
+    float inv_eta, ceta;
+};
+
+struct BItem {
+    int sys, kp, np, p0, cnt;
+    int pad[3];
+};
+
+__host__ __device__ inline void col_groups(int NW, int &CW, int &RG) {
+    CW = NW < kBT ? NW : kBT;
+    RG = kBT / CW;
+}
+
+// Re->k stage in FP32: ghat(k)[rp][mu][i][n] = sum_j [sum_Re w e^{ik.Re} g_ij^mu(Re,Rp)] V_jn(k)
+// for the window bands n; KG k-points per block share every read of g.
+template <int WT, int KG>
+__global__ void __launch_bounds__(128) k_restage_f32(GridInfo g, int W_, int nRe, int nrow,
+                                                     const int *__restrict__ Re,
+                                                     const float2 *__restrict__ gw,
+                                                     const float2 *__restrict__ ph,
+                                                     const float2 *__restrict__ V32, int nkp,
+                                                     const int *__restrict__ kpts,
+                                                     const int64_t *__restrict__ kp_state,
+                                                     const int *__restrict__ win_lo,
+                                                     const int *__restrict__ win_n,
+                                                     float2 *__restrict__ ghat) {
+    constexpr int WM = WT ? WT : epc::kMaxW;
+    const int W = WT ? WT : W_;
+    extern __shared__ float2 P[];   // [KG][nRe]
+    const int kg0 = blockIdx.y * KG;
+    for (int idx = threadIdx.x; idx < KG * nRe; idx += blockDim.x) {
+        const int kk = idx / nRe, r = idx % nRe;
+        float2 p = make_float2(0.f, 0.f);
+        if (kg0 + kk < nkp) {
+            int i1, i2, i3;
+            grid_coords(g, kpts[kg0 + kk], i1, i2, i3);
+            p = ph[phase_index(i1 * g.s1 % g.L, i2 * g.s2 % g.L, i3 * g.s3 % g.L, Re[3 * r],
+                               Re[3 * r + 1], Re[3 * r + 2], g.L)];
+        }
+        P[idx] = p;
+    }
+    __syncthreads();
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= nrow) return;
+    float2 acc[KG][WM];
+#pragma unroll
+    for (int kk = 0; kk < KG; ++kk)
+        for (int j = 0; j < W; ++j) acc[kk][j] = make_float2(0.f, 0.f);
+    const float2 *gr = gw + (size_t)row * W;
+    for (int r = 0; r < nRe; ++r) {
+        float2 gv[WM];
+        for (int j = 0; j < W; ++j) gv[j] = gr[(size_t)r * nrow * W + j];
+#pragma unroll
+        for (int kk = 0; kk < KG; ++kk) {
+            const float2 p = P[kk * nRe + r];
+            for (int j = 0; j < W; ++j) acc[kk][j] = cfmaf(p, gv[j], acc[kk][j]);
+        }
+    }
+#pragma unroll
+    for (int kk = 0; kk < KG; ++kk) {
+        if (kg0 + kk >= nkp) break;
+        const int ik = kpts[kg0 + kk];
+        const int lo = win_lo[ik], ns = win_n[ik];
+        const int64_t s0 = kp_state[kg0 + kk];
+        const float2 *Vk = V32 + (int64_t)ik * W * W;
+        for (int np = 0; np < ns; ++np) {
+            float2 o = make_float2(0.f, 0.f);
+            for (int j = 0; j < W; ++j) o = cfmaf(acc[kk][j], Vk[j * W + lo + np], o);
+            ghat[(s0 + np) * (int64_t)nrow + row] = o;
+        }
+    }
+}
+
+// The persistent kernel: CTAs take queue items until the queue is empty.
+__global__ void __launch_bounds__(kBT, 1) k_batch_scatter(const BSys *__restrict__ systems,
+                                                         const BItem *__restrict__ items,
+                                                         const int *__restrict__ order,
+                                                         int nitems, int *__restrict__ counter,
+                                                         double *__restrict__ part) {
+    extern __shared__ float2 sm[];
+    __shared__ int s_item;
+    __shared__ int sq[kMaxMt];
+    __shared__ int sa[3][kMaxMt];
+    __shared__ double sred[kBT / 32];
+    const int t = threadIdx.x;
+    for (;;) {
+        if (t == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= nitems) break;
+        const int slot = order[it];
+        const BItem I = items[slot];
+        const BSys &S = systems[I.sys];
+        const int W = S.W, Nm = S.Nm, NW = S.NW, KC = S.KC, cnt = I.cnt;
+        const int ik = S.kpts[I.kp];
+        const int64_t st = S.kp_state[I.kp] + I.np;
+        const int band = S.win_lo[ik] + I.np;
+        const float2 *gh = S.ghat + st * (int64_t)S.nRp * NW;
+        const int *pl = S.pairs + S.kp_pairs[I.kp] + I.p0;
+        for (int p = t; p < cnt; p += kBT) {
+            const int iq = pl[p];
+            int i1, i2, i3;
+            grid_coords(S.g, iq, i1, i2, i3);
+            sq[p] = iq;
+            sa[0][p] = i1 * S.g.s1 % S.g.L;
+            sa[1][p] = i2 * S.g.s2 % S.g.L;
+            sa[2][p] = i3 * S.g.s3 % S.g.L;
+        }
+        float2 *P = sm;                          // [Mt][KC]
+        float2 *Cs = sm + (size_t)S.Mt * KC;     // [Mt][NW]
+        const int cg = t % S.CW, rg = t / S.CW;
+        const bool tact = rg < S.RG;
+        const int ncol = (NW + S.CW - 1) / S.CW;            // 1 or 2
+        const int npt = (cnt + S.RG - 1) / S.RG;            // pairs per thread
+        float2 acc[kAcc];
+#pragma unroll
+        for (int a = 0; a < kAcc; ++a) acc[a] = make_float2(0.f, 0.f);
+        __syncthreads();
+        // ---- Rp -> q: C[p][mu, i] = sum_Rp e^{i q_p . Rp} ghat[Rp][mu][i]
+        for (int r0 = 0; r0 < S.nRp; r0 += KC) {
+            const int kc = min(KC, S.nRp - r0);
+            for (int e = t; e < cnt * KC; e += kBT) {
+                const int p = e / KC, kk = e - p * KC;
+                float2 v = make_float2(0.f, 0.f);
+                if (kk < kc) {
+                    const int *R = S.Rp + 3 * (r0 + kk);
+                    v = S.ph32[phase_index(sa[0][p], sa[1][p], sa[2][p], R[0], R[1], R[2], S.g.L)];
+                }
+                P[e] = v;
+            }
+            __syncthreads();
+            if (tact) {
+                for (int kk = 0; kk < kc; ++kk) {
+                    const float2 *gr = gh + (int64_t)(r0 + kk) * NW;
+                    const float2 g0 = gr[cg];
+                    const float2 g1 = (ncol > 1 && cg + S.CW < NW) ? gr[cg + S.CW] : make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int a = 0; a < kAcc; ++a) {
+                        const int i = ncol == 1 ? a : (a >> 1);
+                        const int p = rg + i * S.RG;
+                        if (i < npt && p < cnt) {
+                            const float2 pv = P[p * KC + kk];
+                            acc[a] = cfmaf(pv, (ncol == 1 || (a & 1) == 0) ? g0 : g1, acc[a]);
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (tact) {
+#pragma unroll
+            for (int a = 0; a < kAcc; ++a) {
+                const int i = ncol == 1 ? a : (a >> 1);
+                const int j = ncol == 1 ? 0 : (a & 1);
+                const int p = rg + i * S.RG, c = cg + j * S.CW;
+                if (i < npt && p < cnt && c < NW) Cs[(size_t)p * NW + c] = acc[a];
+            }
+        }
+        __syncthreads();
+        // ---- rotations and the delta sum: one (pair, m) per thread
+        const float en = S.erel[(int64_t)ik * W + band];
+        float rate = 0.f;
+        for (int u = t; u < cnt * W; u += kBT) {
+            const int p = u / W, m = u - p * W;
+            const int iq = sq[p];
+            const int64_t ikq = kplusq(S.g, ik, iq);
+            const float2 *Vq = S.V32 + ikq * W * W;
+            const float2 *Cp = Cs + (size_t)p * NW;
+            float2 h[kNmB];
+#pragma unroll
+            for (int mu = 0; mu < kNmB; ++mu) {
+                h[mu] = make_float2(0.f, 0.f);
+                if (mu < Nm)
+                    for (int i = 0; i < W; ++i) h[mu] = cfmacf(Vq[i * W + m], Cp[mu * W + i], h[mu]);
+            }
+            const float em = S.erel[ikq * W + m];
+            const float fm = S.f32[ikq * W + m];
+            const float2 *uq = S.u32 + (int64_t)iq * Nm * Nm;
+            for (int nu = 0; nu < Nm; ++nu) {
+                const float w = S.hw32[(int64_t)iq * Nm + nu];
+                if (w < 0.f) continue;
+                const float x1 = (en + w) - em, x2 = (en - w) - em;
+                const bool t1 = fabsf(x1) <= S.ceta, t2 = fabsf(x2) <= S.ceta;
+                if (!t1 && !t2) continue;
+                float2 gv = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int mu = 0; mu < kNmB; ++mu)
+                    if (mu < Nm) gv = cfmaf(h[mu], uq[mu * Nm + nu], gv);
+                const float g2 = gv.x * gv.x + gv.y * gv.y;
+                const float N = S.n32[(int64_t)iq * Nm + nu];
+                float term = 0.f;
+                if (t1) {
+                    const float y = x1 * S.inv_eta;
+                    term += (N + fm) * expf(-y * y);
+                }
+                if (t2) {
+                    const float y = x2 * S.inv_eta;
+                    term += (1.f + N - fm) * expf(-y * y);
+                }
+                rate = fmaf(g2, term, rate);
+            }
+        }
+        double r = rate;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+        if ((t & 31) == 0) sred[t >> 5] = r;
+        __syncthreads();
+        if (t == 0) {
+            double s = 0;
+            for (int w = 0; w < kBT / 32; ++w) s += sred[w];
+            part[slot] = s;
+        }
+    }
+}
+
+// 1/tau of every batch state: pref of its system times the sum of its items' slots in order.
+__global__ void k_batch_reduce(int64_t ns, const int64_t *__restrict__ state_item,
+                               const int *__restrict__ state_sys, const double *__restrict__ pref,
+                               const double *__restrict__ part, double *__restrict__ inv_tau) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= ns) return;
+    double v = 0;
+    for (int64_t i = state_item[s]; i < state_item[s + 1]; ++i) v += part[i];
+    inv_tau[s] = pref[state_sys[s]] * v;
+}
+
+struct SigmaDesc {
+    int64_t ns, s0;               // states of the system, first batch state
+    int W;
+    const int *st_k, *st_n;
+    const double *eps, *vel;
+    double mu, kT, pref;
+};
+
+// sigma per system (one block each): fixed-order FP64 sums of v_a v_b tau f(1-f)/kT.
+__global__ void __launch_bounds__(256) k_batch_sigma(const SigmaDesc *__restrict__ d,
+                                                     const double *__restrict__ inv_tau,
+                                                     double *__restrict__ sigma) {
+    __shared__ double sm[6][256];
+    const SigmaDesc D = d[blockIdx.x];
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    for (int64_t s = threadIdx.x; s < D.ns; s += 256) {
+        const double r = inv_tau[D.s0 + s];
+        if (!(r > 0)) continue;
+        const int k = D.st_k[s], n = D.st_n[s];
+        const double x = (D.eps[(int64_t)k * D.W + n] - D.mu) / D.kT;
+        const double ex = exp(-fabs(x));
+        const double f = x > 0 ? ex / (1.0 + ex) : 1.0 / (1.0 + ex);
+        const double w = f * (1.0 - f) / r;
+        const double *vv = D.vel + ((int64_t)k * D.W + n) * 3;
+        v[0] += w * vv[0] * vv[0];
+        v[1] += w * vv[1] * vv[1];
+        v[2] += w * vv[2] * vv[2];
+        v[3] += w * vv[0] * vv[1];
+        v[4] += w * vv[0] * vv[2];
+        v[5] += w * vv[1] * vv[2];
+    }
+    for (int j = 0; j < 6; ++j) sm[j][threadIdx.x] = v[j];
+    __syncthreads();
+    for (int st = 128; st > 0; st >>= 1) {
+        if (threadIdx.x < st)
+            for (int j = 0; j < 6; ++j) sm[j][threadIdx.x] += sm[j][threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double h[6] = {sm[0][0], sm[1][0], sm[2][0], sm[3][0], sm[4][0], sm[5][0]};
+        const double tt[9] = {h[0], h[3], h[4], h[3], h[1], h[5], h[4], h[5], h[2]};
+        for (int i = 0; i < 9; ++i) sigma[blockIdx.x * 9 + i] = D.pref * tt[i];
+    }
+}
+
+size_t smem_bytes(int Mt, int KC, int NW) { return sizeof(float2) * ((size_t)Mt * KC + (size_t)Mt * NW); }
+
+bool tile_ok(int Mt, int KC, int NW) {
+    int CW, RG;
+    col_groups(NW, CW, RG);
+    const int ncol = (NW + CW - 1) / CW;
+    const int npt = (Mt + RG - 1) / RG;
+    return Mt >= 1 && Mt <= kMaxMt && ncol <= 2 && npt * ncol <= kAcc &&
+           smem_bytes(Mt, KC, NW) <= kSmemCap;
+}
+
+using TileKey = std::tuple<int, int, int>;           // (W, Nm, nRp)
+std::map<TileKey, std::pair<int, int>> g_tile_cache;  // autotuned (Mt, KC) per class
+
+}  // namespace
+
+// ------------------------------------------------------------------------------ batch
+struct epwi_batch {
+    epwi_options opt{};
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    std::vector<epwi_ctx *> sys;
+    std::vector<std::array<int, 3>> grids;
+    bool planned = false;
+    double T = 0, eta = 0;
+    std::vector<double> mu, emin, emax;
+    // per system device data of the step
+    std::vector<DevBuf> pairs, ghat;
+    std::vector<std::vector<int64_t>> h_state;
+    std::vector<BSys> hsys;
+    std::vector<int> tile_src;               // 0 default, 1 autotuned, 2 cached, 3 set
+    std::vector<std::pair<int, int>> forced; // tiles set by epwi_batch_set_tile (0: none)
+    DevBuf d_sys, d_items, d_order, d_counter, d_part, d_state_item, d_state_sys, d_pref;
+    DevBuf d_inv_tau, d_sigdesc, d_sigma;
+    std::vector<int64_t> sys_state0;
+    int64_t nitems = 0, nstates = 0, npairs = 0;
+    size_t smem = 0;
+    int grid_ctas = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    epwi_batch_stats stats{};
+
+    void drop_graph() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        exec = nullptr;
+        graph = nullptr;
+    }
+    ~epwi_batch() {
+        drop_graph();
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
+        for (auto &b : pairs) b.release();
+        for (auto &b : ghat) b.release();
+        DevBuf *all[] = {&d_sys, &d_items, &d_order, &d_counter, &d_part, &d_state_item,
+                         &d_state_sys, &d_pref, &d_inv_tau, &d_sigdesc, &d_sigma};
+        for (DevBuf *b : all) b->release();
+        for (epwi_ctx *c : sys) epwi_destroy(c);
+        if (own_stream && stream) cudaStreamDestroy(stream);
+    }
+};
+
+namespace {
+
+template <class F>
+epwi_status bguard(epwi_batch *b, F &&f) {
+    if (!b) return EPWI_EINVAL;
+    try {
+        EPWI_CUDA(cudaSetDevice(b->device));
+        f();
+        b->err.clear();
+        return EPWI_OK;
+    } catch (const EpwiError &e) {
+        b->err = e.msg;
+        return e.status;
+    } catch (const std::bad_alloc &) {
+        b->err = "host allocation failed";
+        return EPWI_ENOMEM;
+    } catch (...) {
+        b->err = "unexpected internal error";
+        return EPWI_ECUDA;
+    }
+}
+
+void check(epwi_ctx *c, epwi_status st, const char *what) {
+    if (st != EPWI_OK)
+        throw EpwiError{st, std::string(what) + ": " + epwi_last_error(c)};
+}
+
+template <class T>
+void put(DevBuf &b, const std::vector<T> &v, cudaStream_t st) {
+    b.ensure(sizeof(T) * (v.size() + 1));
+    if (!v.empty())
+        EPWI_CUDA(cudaMemcpyAsync(b.p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st));
+}
+
+void restage(epwi_batch *b, int s) {
+    epwi_ctx *c = b->sys[s];
+    const int64_t nrow = (int64_t)c->nRp * c->nm * c->nw;
+    GridInfo g = make_grid_info(c);
+    const int nkp = (int)c->nkp;
+    if (nkp == 0) return;
+#define RS_ARGS                                                                                   \
+    g, c->nw, c->nRe, (int)nrow, c->Re.as<int>(), c->gw32.as<float2>(), c->ph32.as<float2>(),      \
+        c->V32.as<float2>(), nkp, c->kpts.as<int>(), c->kp_state.as<int64_t>(), c->win_lo.as<int>(), \
+        c->win_n.as<int>(), b->ghat[s].as<float2>()
+#define RS_LAUNCH(WT, KG)                                                                         \
+    do {                                                                                          \
+        dim3 grid((unsigned)((nrow + 127) / 128), (unsigned)((nkp + KG - 1) / KG));               \
+        const size_t sm = sizeof(float2) * KG * c->nRe;                                           \
+        static size_t sm_set = 48 * 1024;   /* raised before any capture (planning runs first) */ \
+        if (sm > sm_set) {                                                                        \
+            EPWI_CUDA(cudaFuncSetAttribute(k_restage_f32<WT, KG>,                                 \
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)); \
+            sm_set = sm;                                                                          \
+        }                                                                                         \
+        k_restage_f32<WT, KG><<<grid, 128, sm, b->stream>>>(RS_ARGS);                              \
+        EPWI_CHECK_LAUNCH();                                                                      \
+    } while (0)
+    if (c->nw == 4) RS_LAUNCH(4, 8);
+    else if (c->nw == 8) RS_LAUNCH(8, 4);
+    else if (c->nw == 16) RS_LAUNCH(16, 2);
+    else if (c->nw == 24) RS_LAUNCH(24, 1);
+    else RS_LAUNCH(0, 1);
+#undef RS_LAUNCH
+#undef RS_ARGS
+}
+
+// The per-system work that precedes the persistent kernel in every step.
+void system_prologue(epwi_batch *b, int s) {
+    epwi_ctx *c = b->sys[s];
+    launch_phase_tables(c);
+    launch_eigs(c);
+    occupation_tables(c);
+    tc_tables(c);
+    sieve_fill_chunk(c, 0, c->nkp, b->pairs[s].as<int>());
+    restage(b, s);
+}
+
+// Items of system s in (k-point, band, q block) order, with their states' item offsets.
+void build_items(epwi_batch *b, int s, int Mt, std::vector<BItem> &items,
+                 std::vector<int64_t> &state_item) {
+    epwi_ctx *c = b->sys[s];
+    const auto &hs = b->h_state[s];
+    for (int64_t kp = 0; kp < c->nkp; ++kp) {
+        const int64_t np = c->h_kp_pairs[kp + 1] - c->h_kp_pairs[kp];
+        const int ns = (int)(hs[kp + 1] - hs[kp]);
+        for (int n = 0; n < ns; ++n) {
+            state_item.push_back((int64_t)items.size());
+            for (int64_t p0 = 0; p0 < np; p0 += Mt) {
+                BItem it{};
+                it.sys = s;
+                it.kp = (int)kp;
+                it.np = n;
+                it.p0 = (int)p0;
+                it.cnt = (int)std::min<int64_t>(Mt, np - p0);
+                items.push_back(it);
+            }
+        }
+    }
+}
+
+void fill_bsys(epwi_batch *b, int s, int Mt, int KC, BSys &d) {
+    epwi_ctx *c = b->sys[s];
+    d.g = make_grid_info(c);
+    d.W = c->nw;
+    d.Nm = c->nm;
+    d.nRp = c->nRp;
+    d.NW = c->nw * c->nm;
+    col_groups(d.NW, d.CW, d.RG);
+    d.Mt = Mt;
+    d.KC = KC;
+    d.Rp = c->Rp.as<int>();
+    d.ph32 = c->ph32.as<float2>();
+    d.V32 = c->V32.as<float2>();
+    d.u32 = c->u32.as<float2>();
+    d.erel = c->tc_erel.as<float>();
+    d.f32 = c->tc_f32.as<float>();
+    d.n32 = c->tc_n32.as<float>();
+    d.hw32 = c->tc_hw32.as<float>();
+    d.ghat = b->ghat[s].as<float2>();
+    d.pairs = b->pairs[s].as<int>();
+    d.kp_pairs = c->kp_pairs.as<int64_t>();
+    d.kpts = c->kpts.as<int>();
+    d.win_lo = c->win_lo.as<int>();
+    d.kp_state = c->kp_state.as<int64_t>();
+    d.inv_eta = (float)(1.0 / c->eta);
+    d.ceta = (float)(c->opt.sieve_c * c->eta);
+}
+
+int persistent_grid(epwi_batch *b, size_t smem) {
+    int nsm = 0, per = 0;
+    EPWI_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device));
+    EPWI_CUDA(cudaFuncSetAttribute(k_batch_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)std::max<size_t>(smem, 1)));
+    EPWI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_scatter, kBT, smem));
+    EPWI_REQUIRE(per >= 1, EPWI_EUNSUPPORTED, "persistent kernel does not fit on an SM");
+    return nsm * per;
+}
+
+// Times the persistent kernel for system s with tile (Mt, KC) on up to `sample` items.
+float time_tile(epwi_batch *b, int s, int Mt, int KC, int64_t sample, int64_t *pairs_out) {
+    std::vector<BItem> items;
+    std::vector<int64_t> si;
+    build_items(b, s, Mt, items, si);
+    if ((int64_t)items.size() > sample) items.resize(sample);
+    int64_t pairs = 0;
+    for (auto &it : items) pairs += it.cnt;
+    *pairs_out = pairs;
+    if (items.empty()) return 0.f;
+    for (auto &it : items) it.sys = 0;
+    BSys d;
+    fill_bsys(b, s, Mt, KC, d);
+    std::vector<BSys> v(1, d);
+    std::vector<int> order(items.size());
+    std::iota(order.begin(), order.end(), 0);
+    DevBuf ds, di, dord, dc, dp;
+    float best = 1e30f;
+    try {
+        put(ds, v, b->stream);
+        put(di, items, b->stream);
+        put(dord, order, b->stream);
+        dc.ensure(sizeof(int));
+        dp.ensure(sizeof(double) * items.size());
+        const size_t sm = smem_bytes(Mt, KC, d.NW);
+        const int grid = persistent_grid(b, sm);
+        for (int rep = 0; rep < 3; ++rep) {
+            EPWI_CUDA(cudaMemsetAsync(dc.p, 0, sizeof(int), b->stream));
+            cudaEventRecord(b->ev[0], b->stream);
+            k_batch_scatter<<<grid, kBT, sm, b->stream>>>(ds.as<BSys>(), di.as<BItem>(),
+                                                         dord.as<int>(), (int)items.size(),
+                                                         dc.as<int>(), dp.as<double>());
+            EPWI_CHECK_LAUNCH();
+            cudaEventRecord(b->ev[1], b->stream);
+            EPWI_CUDA(cudaEventSynchronize(b->ev[1]));
+            float ms = 0;
+            cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]);
+            if (rep > 0) best = std::min(best, ms);
+        }
+    } catch (...) {
+        cudaStreamSynchronize(b->stream);
+        ds.release(); di.release(); dord.release(); dc.release(); dp.release();
+        throw;
+    }
+    EPWI_CUDA(cudaStreamSynchronize(b->stream));
+    ds.release(); di.release(); dord.release(); dc.release(); dp.release();
+    return best;
+}
+
+std::pair<int, int> default_tile(int NW) {
+    static const int mts[] = {128, 64, 32, 16, 8, 4, 2, 1};
+    for (int mt : mts)
+        if (tile_ok(mt, 32, NW)) return {mt, 32};
+    return {1, 16};
+}
+
+std::pair<int, int> autotune(epwi_batch *b, int s, int &src) {
+    epwi_ctx *c = b->sys[s];
+    const TileKey key{c->nw, c->nm, c->nRp};
+    auto it = g_tile_cache.find(key);
+    if (it != g_tile_cache.end()) {
+        src = 2;
+        return it->second;
+    }
+    const int NW = c->nw * c->nm;
+    std::pair<int, int> best = default_tile(NW);
+    double best_t = 1e300;
+    for (int mt : {16, 32, 64, 128, 256}) {
+        for (int kc : {16, 32, 64}) {
+            if (!tile_ok(mt, kc, NW)) continue;
+            int64_t pairs = 0;
+            const float ms = time_tile(b, s, mt, kc, 4096, &pairs);
+            if (pairs == 0) continue;
+            const double per = ms / (double)pairs;
+            if (per < best_t) {
+                best_t = per;
+                best = {mt, kc};
+            }
+        }
+    }
+    src = 1;
+    if (best_t < 1e300) g_tile_cache[key] = best;
+    return best;
+}
+
+void plan(epwi_batch *b, bool tune) {
+    b->drop_graph();
+    b->planned = false;
+    const int ns = (int)b->sys.size();
+    cudaStream_t st = b->stream;
+    b->pairs.resize(ns);
+    b->ghat.resize(ns);
+    b->h_state.assign(ns, {});
+    b->hsys.assign(ns, BSys{});
+    b->tile_src.assign(ns, 0);
+    std::vector<std::pair<int, int>> tiles(ns);
+    int64_t npairs = 0, nstates = 0;
+    double ms_plan = 0;
+    cudaEvent_t p0 = nullptr, p1 = nullptr;
+    EPWI_CUDA(cudaEventCreate(&p0));
+    EPWI_CUDA(cudaEventCreate(&p1));
+    struct EvGuard {
+        cudaEvent_t a, b;
+        ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); }
+    } evg{p0, p1};
+    cudaEventRecord(p0, st);
+    for (int s = 0; s < ns; ++s) {
+        epwi_ctx *c = b->sys[s];
+        c->T = b->T;
+        c->mu = b->mu[s];
+        c->eta = b->eta;
+        c->emin = b->emin[s];
+        c->emax = b->emax[s];
+        const int g3[3] = {b->grids[s][0], b->grids[s][1], b->grids[s][2]};
+        check(c, epwi_eigs(c, g3, g3), "epwi_eigs");
+        build_window(c);
+        sieve_count(c);
+        occupation_tables(c);
+        tc_tables(c);
+        b->h_state[s].resize(c->nkp + 1);
+        EPWI_CUDA(cudaMemcpyAsync(b->h_state[s].data(), c->kp_state.p, sizeof(int64_t) * (c->nkp + 1),
+                                  cudaMemcpyDeviceToHost, st));
+        EPWI_CUDA(cudaStreamSynchronize(st));
+        b->pairs[s].ensure(sizeof(int) * (c->npairs + 1));
+        const int64_t nrow = (int64_t)c->nRp * c->nm * c->nw;
+        b->ghat[s].ensure(sizeof(float2) * (size_t)nrow * (c->nstates + 1));
+        sieve_fill_chunk(c, 0, c->nkp, b->pairs[s].as<int>());
+        restage(b, s);
+        npairs += c->npairs;
+        nstates += c->nstates;
+    }
+    EPWI_CUDA(cudaStreamSynchronize(st));
+    // tile shapes
+    for (int s = 0; s < ns; ++s) {
+        epwi_ctx *c = b->sys[s];
+        const int NW = c->nw * c->nm;
+        if ((int)b->forced.size() == ns && b->forced[s].first > 0) {
+            tiles[s] = b->forced[s];
+            b->tile_src[s] = 3;
+        } else if (tune && c->npairs > 0) {
+            tiles[s] = autotune(b, s, b->tile_src[s]);
+        } else {
+            tiles[s] = default_tile(NW);
+        }
+        EPWI_REQUIRE(tile_ok(tiles[s].first, tiles[s].second, NW), EPWI_EUNSUPPORTED,
+                     "no tile shape fits this system (nw * modes too large)");
+    }
+    // queue: items of every system, state offsets, per-item cost order
+    std::vector<BItem> items;
+    std::vector<int64_t> state_item;
+    std::vector<int> state_sys;
+    std::vector<double> pref(ns);
+    b->sys_state0.assign(ns + 1, 0);
+    size_t smem = 0;
+    for (int s = 0; s < ns; ++s) {
+        epwi_ctx *c = b->sys[s];
+        b->sys_state0[s] = (int64_t)state_item.size();
+        build_items(b, s, tiles[s].first, items, state_item);
+        state_sys.resize(state_item.size(), s);
+        fill_bsys(b, s, tiles[s].first, tiles[s].second, b->hsys[s]);
+        pref[s] = 2.0 * epc::kPi / epc::kHbarEVs / (double)c->nk / (std::sqrt(epc::kPi) * c->eta);
+        smem = std::max(smem, smem_bytes(tiles[s].first, tiles[s].second, c->nw * c->nm));
+    }
+    b->sys_state0[ns] = (int64_t)state_item.size();
+    state_item.push_back((int64_t)items.size());
+    std::vector<double> cost(ns);
+    for (int s = 0; s < ns; ++s) {
+        const BSys &d = b->hsys[s];
+        cost[s] = (double)d.nRp * d.NW + 2.0 * d.W * (d.NW + d.Nm * d.Nm);
+    }
+    std::vector<int> order(items.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return cost[items[x].sys] * items[x].cnt > cost[items[y].sys] * items[y].cnt;
+    });
+    EPWI_REQUIRE(items.size() < (size_t)INT32_MAX, EPWI_EUNSUPPORTED, "more than 2^31 queue items");
+    put(b->d_sys, b->hsys, st);
+    put(b->d_items, items, st);
+    put(b->d_order, order, st);
+    put(b->d_state_item, state_item, st);
+    put(b->d_state_sys, state_sys, st);
+    put(b->d_pref, pref, st);
+    b->d_counter.ensure(sizeof(int));
+    b->d_part.ensure(sizeof(double) * (items.size() + 1));
+    b->d_inv_tau.ensure(sizeof(double) * (nstates + 1));
+    std::vector<SigmaDesc> sd(ns);
+    for (int s = 0; s < ns; ++s) {
+        epwi_ctx *c = b->sys[s];
+        const double kT = epc::kKbEVK * c->T;
+        sd[s] = SigmaDesc{c->nstates, b->sys_state0[s], c->nw, c->st_k.as<int>(), c->st_n.as<int>(),
+                          c->eps.as<double>(), c->vel.as<double>(), c->mu, kT,
+                          2.0 * epc::kECharge * epc::kECharge /
+                              ((double)c->nk * c->volume * 1e-30 * kT * epc::kECharge)};
+    }
+    put(b->d_sigdesc, sd, st);
+    b->d_sigma.ensure(sizeof(double) * 9 * ns);
+    b->nitems = (int64_t)items.size();
+    b->nstates = nstates;
+    b->npairs = npairs;
+    b->smem = smem;
+    b->grid_ctas = persistent_grid(b, smem);
+    cudaEventRecord(p1, st);
+    EPWI_CUDA(cudaStreamSynchronize(st));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, p0, p1);
+    ms_plan = ms;
+    // capture the step
+    EPWI_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+    try {
+        for (int s = 0; s < ns; ++s) system_prologue(b, s);
+        EPWI_CUDA(cudaMemsetAsync(b->d_counter.p, 0, sizeof(int), st));
+        EPWI_CUDA(cudaEventRecord(b->ev[2], st));
+        if (b->nitems > 0) {
+            k_batch_scatter<<<b->grid_ctas, kBT, b->smem, st>>>(
+                b->d_sys.as<BSys>(), b->d_items.as<BItem>(), b->d_order.as<int>(), (int)b->nitems,
+                b->d_counter.as<int>(), b->d_part.as<double>());
+            EPWI_CHECK_LAUNCH();
+        }
+        EPWI_CUDA(cudaEventRecord(b->ev[3], st));
+        if (nstates > 0) {
+            k_batch_reduce<<<(unsigned)((nstates + 255) / 256), 256, 0, st>>>(
+                nstates, b->d_state_item.as<int64_t>(), b->d_state_sys.as<int>(),
+                b->d_pref.as<double>(), b->d_part.as<double>(), b->d_inv_tau.as<double>());
+            EPWI_CHECK_LAUNCH();
+        }
+        k_batch_sigma<<<ns, 256, 0, st>>>(b->d_sigdesc.as<SigmaDesc>(), b->d_inv_tau.as<double>(),
+                                          b->d_sigma.as<double>());
+        EPWI_CHECK_LAUNCH();
+    } catch (...) {
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(st, &g);
+        if (g) cudaGraphDestroy(g);
+        throw;
+    }
+    EPWI_CUDA(cudaStreamEndCapture(st, &b->graph));
+    EPWI_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));
+    size_t nodes = 0;
+    EPWI_CUDA(cudaGraphGetNodes(b->graph, nullptr, &nodes));
+    std::memset(&b->stats, 0, sizeof(b->stats));
+    b->stats.n_systems = ns;
+    b->stats.n_states = nstates;
+    b->stats.n_pairs = npairs;
+    b->stats.n_items = b->nitems;
+    b->stats.graph_nodes = (int64_t)nodes;
+    b->stats.persistent_ctas = b->grid_ctas;
+    b->stats.smem_bytes = (int64_t)smem;
+    b->stats.ms_plan = ms_plan;
+    double fl = 0, rfl = 0;
+    for (int s = 0; s < ns; ++s) {
+        epwi_ctx *c = b->sys[s];
+        const double nbar = (double)c->nstates / std::max<int64_t>(1, c->nkp);
+        fl += 8.0 * c->nRp * c->nm * c->nw * (double)c->npairs * nbar;
+        rfl += 8.0 * c->nRe * c->nRp * c->nm * (double)c->nw * c->nw * c->nkp;
+    }
+    b->stats.scatter_flops = fl;
+    b->stats.restage_flops = rfl;
+    b->planned = true;
+}
+
+}  // namespace
+
+extern "C" {
+
+epwi_status epwi_batch_create(epwi_batch **out, const epwi_options *opt) {
+    if (!out) return EPWI_EINVAL;
+    *out = nullptr;
+    epwi_batch *b = nullptr;
+    try {
+        b = new epwi_batch();
+    } catch (...) {
+        return EPWI_ENOMEM;
+    }
+    if (opt) b->opt = *opt;
+    else epwi_default_options(&b->opt);
+    b->opt.precision = EPWI_FP64;    // the eigen-tables; the batch kernels are FP32
+    b->device = b->opt.device;
+    epwi_status st = bguard(b, [&] {
+        int n = 0;
+        EPWI_CUDA(cudaGetDeviceCount(&n));
+        EPWI_REQUIRE(b->device >= 0 && b->device < n, EPWI_EINVAL, "no such CUDA device");
+        EPWI_CUDA(cudaSetDevice(b->device));
+        if (b->opt.cuda_stream) {
+            b->stream = (cudaStream_t)b->opt.cuda_stream;
+        } else {
+            EPWI_CUDA(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+            b->own_stream = true;
+        }
+        b->opt.cuda_stream = b->stream;
+        for (auto &e : b->ev) EPWI_CUDA(cudaEventCreate(&e));
+    });
+    if (st != EPWI_OK) {
+        delete b;
+        return st;
+    }
+    *out = b;
+    return EPWI_OK;
+}
+
+void epwi_batch_destroy(epwi_batch *b) { delete b; }
+
+const char *epwi_batch_last_error(const epwi_batch *b) { return b ? b->err.c_str() : "null batch"; }
+
+epwi_status epwi_batch_setup(epwi_batch *b, int32_t nsys, const epwi_system *systems,
+                             const int32_t *grids) {
+    return bguard(b, [&] {
+        EPWI_REQUIRE(nsys >= 1 && systems && grids, EPWI_EINVAL, "bad argument");
+        b->drop_graph();
+        b->planned = false;
+        for (epwi_ctx *c : b->sys) epwi_destroy(c);
+        b->sys.clear();
+        b->grids.clear();
+        b->forced.clear();
+        for (int s = 0; s < nsys; ++s) {
+            epwi_ctx *c = nullptr;
+            EPWI_REQUIRE(epwi_create(&c, &b->opt) == EPWI_OK, EPWI_ECUDA, "context creation failed");
+            b->sys.push_back(c);
+            check(c, epwi_setup(c, &systems[s]), "epwi_setup");
+            for (int a = 0; a < 3; ++a)
+                EPWI_REQUIRE(grids[3 * s + a] >= 1, EPWI_EINVAL, "grid sizes must be >= 1");
+            b->grids.push_back({grids[3 * s], grids[3 * s + 1], grids[3 * s + 2]});
+        }
+    });
+}
+
+epwi_status epwi_batch_plan(epwi_batch *b, double T, const double *mu, double smear,
+                            const double *emin, const double *emax, int32_t autotune_tiles,
+                            int64_t *n_pairs) {
+    return bguard(b, [&] {
+        EPWI_REQUIRE(!b->sys.empty(), EPWI_ESTATE, "epwi_batch_setup has not been called");
+        EPWI_REQUIRE(T > 0 && smear > 0 && mu && emin && emax, EPWI_EINVAL, "bad argument");
+        const int ns = (int)b->sys.size();
+        b->T = T;
+        b->eta = smear;
+        b->mu.assign(mu, mu + ns);
+        b->emin.assign(emin, emin + ns);
+        b->emax.assign(emax, emax + ns);
+        for (int s = 0; s < ns; ++s)
+            EPWI_REQUIRE(std::isfinite(mu[s]) && !(emin[s] > emax[s]), EPWI_EINVAL,
+                         "need finite mu and emin <= emax");
+        plan(b, autotune_tiles != 0);
+        if (n_pairs) *n_pairs = b->npairs;
+    });
+}
+
+epwi_status epwi_batch_run(epwi_batch *b, double *sigma) {
+    return bguard(b, [&] {
+        EPWI_REQUIRE(b->planned && b->exec, EPWI_ESTATE, "epwi_batch_plan has not been called");
+        cudaEvent_t e0, e1;
+        EPWI_CUDA(cudaEventCreate(&e0));
+        EPWI_CUDA(cudaEventCreate(&e1));
+        cudaEventRecord(e0, b->stream);
+        EPWI_CUDA(cudaGraphLaunch(b->exec, b->stream));
+        cudaEventRecord(e1, b->stream);
+        const int ns = (int)b->sys.size();
+        if (sigma)
+            EPWI_CUDA(cudaMemcpyAsync(sigma, b->d_sigma.p, sizeof(double) * 9 * ns,
+                                      cudaMemcpyDeviceToHost, b->stream));
+        EPWI_CUDA(cudaStreamSynchronize(b->stream));
+        float ms = 0, msk = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventElapsedTime(&msk, b->ev[2], b->ev[3]);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        b->stats.ms_graph = ms;
+        b->stats.ms_persistent = msk;
+        b->stats.runs += 1;
+    });
+}
+
+epwi_status epwi_batch_get_rates(epwi_batch *b, int32_t s, int64_t cap, int32_t *k_idx,
+                                 int32_t *band, double *rates, int64_t *n) {
+    return bguard(b, [&] {
+        EPWI_REQUIRE(b->planned && b->stats.runs > 0, EPWI_ESTATE, "epwi_batch_run has not been called");
+        EPWI_REQUIRE(s >= 0 && s < (int)b->sys.size(), EPWI_EINVAL, "no such system");
+        epwi_ctx *c = b->sys[s];
+        const int64_t ns = c->nstates;
+        if (n) *n = ns;
+        if (!k_idx && !band && !rates) return;
+        EPWI_REQUIRE(cap >= ns, EPWI_ETOOSMALL, "capacity below n_states");
+        if (ns) {
+            if (k_idx) EPWI_CUDA(cudaMemcpyAsync(k_idx, c->st_k.p, 4 * ns, cudaMemcpyDeviceToHost, b->stream));
+            if (band) EPWI_CUDA(cudaMemcpyAsync(band, c->st_n.p, 4 * ns, cudaMemcpyDeviceToHost, b->stream));
+            if (rates)
+                EPWI_CUDA(cudaMemcpyAsync(rates, b->d_inv_tau.as<double>() + b->sys_state0[s], 8 * ns,
+                                          cudaMemcpyDeviceToHost, b->stream));
+        }
+        EPWI_CUDA(cudaStreamSynchronize(b->stream));
+    });
+}
+
+epwi_status epwi_batch_get_tile(epwi_batch *b, int32_t s, int32_t *mt, int32_t *kc,
+                                int32_t *source) {
+    return bguard(b, [&] {
+        EPWI_REQUIRE(b->planned, EPWI_ESTATE, "epwi_batch_plan has not been called");
+        EPWI_REQUIRE(s >= 0 && s < (int)b->sys.size(), EPWI_EINVAL, "no such system");
+        if (mt) *mt = b->hsys[s].Mt;
+        if (kc) *kc = b->hsys[s].KC;
+        if (source) *source = b->tile_src[s];
+    });
+}
+
+epwi_status epwi_batch_set_tile(epwi_batch *b, int32_t s, int32_t mt, int32_t kc) {
+    return bguard(b, [&] {
+        EPWI_REQUIRE(s >= 0 && s < (int)b->sys.size(), EPWI_EINVAL, "no such system");
+        epwi_ctx *c = b->sys[s];
+        EPWI_REQUIRE(mt == 0 || tile_ok(mt, kc, c->nw * c->nm), EPWI_EINVAL,
+                     "tile shape does not fit this system");
+        b->forced.resize(b->sys.size(), {0, 0});
+        b->forced[s] = {mt, kc};
+    });
+}
+
+epwi_status epwi_batch_get_stats(epwi_batch *b, epwi_batch_stats *out) {
+    return bguard(b, [&] {
+        EPWI_REQUIRE(out, EPWI_EINVAL, "out is NULL");
+        *out = b->stats;
+    });
+}
+
+}  // extern "C"

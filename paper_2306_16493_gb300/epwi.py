@@ -62,6 +62,14 @@ class epwi_mlp_train_options(C.Structure):
                 ("background", C.c_double), ("floor_rel", C.c_double), ("seed", C.c_uint64)]
 
 
+class epwi_batch_stats(C.Structure):
+    _fields_ = [("n_systems", C.c_int64), ("n_states", C.c_int64), ("n_pairs", C.c_int64),
+                ("n_items", C.c_int64), ("graph_nodes", C.c_int64), ("persistent_ctas", C.c_int64),
+                ("smem_bytes", C.c_int64), ("runs", C.c_int64), ("ms_plan", C.c_double),
+                ("ms_graph", C.c_double), ("ms_persistent", C.c_double),
+                ("scatter_flops", C.c_double), ("restage_flops", C.c_double)]
+
+
 EPWI_MLP_NPARAM = 34433
 EPWI_PROPOSAL_UNIFORM, EPWI_PROPOSAL_LEARNED = 0, 1
 
@@ -105,6 +113,16 @@ def _load() -> C.CDLL:
         "epwi_mlp_get_training_set": (I32, [P, I64, P, P, P, P, P]),
         "epwi_scatter_rates_is": (I32, [P, D, D, D, D, D, I64, D, I32, I32, C.c_uint64, P, P]),
         "epwi_get_is_pairs": (I32, [P, I64, P, P, P, P]),
+        "epwi_batch_create": (I32, [P, P]),
+        "epwi_batch_destroy": (V, [P]),
+        "epwi_batch_last_error": (C.c_char_p, [P]),
+        "epwi_batch_setup": (I32, [P, I32, P, P]),
+        "epwi_batch_plan": (I32, [P, D, P, D, P, P, I32, P]),
+        "epwi_batch_run": (I32, [P, P]),
+        "epwi_batch_get_rates": (I32, [P, I32, I64, P, P, P, P]),
+        "epwi_batch_set_tile": (I32, [P, I32, I32, I32]),
+        "epwi_batch_get_tile": (I32, [P, I32, P, P, P]),
+        "epwi_batch_get_stats": (I32, [P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -153,8 +171,9 @@ def epwi_set_stream(ctx, stream: int | None):
     _check(ctx, _lib.epwi_set_stream(ctx, C.c_void_p(stream or 0)))
 
 
-def epwi_setup(ctx, sysm):
-    """sysm: an object with the fields of synth.System (numpy arrays, unweighted)."""
+def _system_struct(sysm):
+    """epwi_system for sysm (an object with the fields of synth.System) and the arrays it
+    points into (keep them alive while the struct is in use)."""
     keep = dict(
         mass=np.ascontiguousarray(sysm.mass, np.float64),
         Re=np.ascontiguousarray(sysm.Re, np.int32), we=np.ascontiguousarray(sysm.we, np.float64),
@@ -170,6 +189,12 @@ def epwi_setup(ctx, sysm):
     s.nRp = len(keep["Rp"])
     for k in ("mass", "Re", "we", "H", "Rp", "wp", "Phi", "g"):
         setattr(s, k, _ptr(keep[k]))
+    return s, keep
+
+
+def epwi_setup(ctx, sysm):
+    """sysm: an object with the fields of synth.System (numpy arrays, unweighted)."""
+    s, keep = _system_struct(sysm)
     _check(ctx, _lib.epwi_setup(ctx, C.byref(s)))
 
 
@@ -355,6 +380,87 @@ def epwi_get_is_pairs(ctx):
     w = np.empty(m)
     _check(ctx, _lib.epwi_get_is_pairs(ctx, m, _ptr(ik), _ptr(iq), _ptr(w), C.byref(n)))
     return ik, iq, w
+
+
+def _bcheck(b, st: int):
+    if st != 0:
+        msg = _lib.epwi_batch_last_error(b).decode() if b else ""
+        raise EpwiError(st, msg)
+
+
+class Batch:
+    """Uneven systems in one planned step (epwi_batch_* calls)."""
+
+    def __init__(self, device=0, stream=None):
+        o = epwi_default_options()
+        o.device = device
+        o.cuda_stream = stream or 0
+        h = C.c_void_p()
+        st = _lib.epwi_batch_create(C.byref(h), C.byref(o))
+        if st != 0:
+            raise EpwiError(st, "epwi_batch_create failed")
+        self.h = h
+        self.nsys = 0
+        self._keep = []
+
+    def close(self):
+        if self.h:
+            _lib.epwi_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def setup(self, systems, grids):
+        arr = (epwi_system * len(systems))()
+        keep = []
+        for i, sysm in enumerate(systems):
+            arr[i], k = _system_struct(sysm)
+            keep.append(k)
+        g = np.ascontiguousarray(np.asarray(grids, np.int32).reshape(-1, 3))
+        _bcheck(self.h, _lib.epwi_batch_setup(self.h, len(systems), arr, _ptr(g)))
+        self.nsys = len(systems)
+        self._keep = keep
+
+    def plan(self, T, mu, smear, emin, emax, autotune=True):
+        mu = np.ascontiguousarray(mu, float)
+        lo = np.ascontiguousarray(emin, float)
+        hi = np.ascontiguousarray(emax, float)
+        n = C.c_int64()
+        _bcheck(self.h, _lib.epwi_batch_plan(self.h, T, _ptr(mu), smear, _ptr(lo), _ptr(hi),
+                                             int(bool(autotune)), C.byref(n)))
+        return n.value
+
+    def run(self):
+        sig = np.empty((self.nsys, 3, 3))
+        _bcheck(self.h, _lib.epwi_batch_run(self.h, _ptr(sig)))
+        return sig
+
+    def rates(self, s):
+        n = C.c_int64()
+        _bcheck(self.h, _lib.epwi_batch_get_rates(self.h, s, 0, None, None, None, C.byref(n)))
+        k = np.empty(n.value, np.int32)
+        b = np.empty(n.value, np.int32)
+        r = np.empty(n.value)
+        _bcheck(self.h, _lib.epwi_batch_get_rates(self.h, s, n.value, _ptr(k), _ptr(b), _ptr(r),
+                                                  C.byref(n)))
+        return k, b, r
+
+    def set_tile(self, s, mt, kc):
+        _bcheck(self.h, _lib.epwi_batch_set_tile(self.h, s, mt, kc))
+
+    def tile(self, s):
+        mt, kc, src = C.c_int32(), C.c_int32(), C.c_int32()
+        _bcheck(self.h, _lib.epwi_batch_get_tile(self.h, s, C.byref(mt), C.byref(kc), C.byref(src)))
+        return mt.value, kc.value, src.value
+
+    def stats(self):
+        st = epwi_batch_stats()
+        _bcheck(self.h, _lib.epwi_batch_get_stats(self.h, C.byref(st)))
+        return {name: getattr(st, name) for name, _ in epwi_batch_stats._fields_}
 
 
 # ------------------------------------------------------------------ convenience wrapper
