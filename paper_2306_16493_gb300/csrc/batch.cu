@@ -738,14 +738,15 @@ void plan(epwi_batch *b, bool tune) {
     try {
         for (int s = 0; s < ns; ++s) system_prologue(b, s);
         EPWI_CUDA(cudaMemsetAsync(b->d_counter.p, 0, sizeof(int), st));
-        EPWI_CUDA(cudaEventRecord(b->ev[2], st));
+        // external event records become graph nodes (a plain record inside a capture does not)
+        EPWI_CUDA(cudaEventRecordWithFlags(b->ev[2], st, cudaEventRecordExternal));
         if (b->nitems > 0) {
             k_batch_scatter<<<b->grid_ctas, kBT, b->smem, st>>>(
                 b->d_sys.as<BSys>(), b->d_items.as<BItem>(), b->d_order.as<int>(), (int)b->nitems,
                 b->d_counter.as<int>(), b->d_part.as<double>());
             EPWI_CHECK_LAUNCH();
         }
-        EPWI_CUDA(cudaEventRecord(b->ev[3], st));
+        EPWI_CUDA(cudaEventRecordWithFlags(b->ev[3], st, cudaEventRecordExternal));
         if (nstates > 0) {
             k_batch_reduce<<<(unsigned)((nstates + 255) / 256), 256, 0, st>>>(
                 nstates, b->d_state_item.as<int64_t>(), b->d_state_sys.as<int>(),
@@ -886,8 +887,8 @@ epwi_status epwi_batch_run(epwi_batch *b, double *sigma) {
                                       cudaMemcpyDeviceToHost, b->stream));
         EPWI_CUDA(cudaStreamSynchronize(b->stream));
         float ms = 0, msk = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        cudaEventElapsedTime(&msk, b->ev[2], b->ev[3]);
+        EPWI_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        EPWI_CUDA(cudaEventElapsedTime(&msk, b->ev[2], b->ev[3]));
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         b->stats.ms_graph = ms;
