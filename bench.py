@@ -319,6 +319,155 @@ def run_gpu(args):
         print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------------- other workloads
+BATCH = dict(workload="batch64", systems="64 seeded cells s = 16a+4b+c: nat=[1,2,4,6][c], "
+             "nw=[4,8,16,24][b], grid=[24,36,48,60][a]^3 / scale, R cube side=[3,5,7][(a+b+c)%3]",
+             window_eV=0.2, smear_eV=0.02, T_K=300.0, mu="band centre per system")
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SM x 128 FP32 lanes x FMA x 2.07 GHz
+
+
+def run_batch(args):
+    """64 uneven systems, one graph launch per step (persistent work-queue kernel)."""
+    import torch
+    from paper_2306_16493_gb300 import epwi, synth
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()             # the batch's graph runs on this stream
+    torch.cuda.set_stream(stream)
+    T, eta, win = BATCH["T_K"], BATCH["smear_eV"], BATCH["window_eV"]
+    t0 = time.perf_counter()
+    b = epwi.Batch(stream=stream.cuda_stream)
+    h2d, grids = 0, []
+    for s in range(64):
+        sysm, N = synth.batch_system(s)
+        Nr = max(2, N // args.batch_scale)
+        b.add(sysm, (Nr, Nr, Nr))
+        h2d += sum(a.nbytes for a in (sysm.mass, sysm.Re, sysm.we, sysm.H, sysm.Rp, sysm.wp,
+                                      sysm.Phi, sysm.g))
+        grids.append(Nr)
+        del sysm
+    t_setup = time.perf_counter() - t0
+    mu = np.array([0.5 * sum(b.band_range(s)) for s in range(64)])
+    t1 = time.perf_counter()
+    npairs = b.plan(T, mu, eta, mu - win, mu + win, autotune=True)
+    sig = b.run()
+    t_first = time.perf_counter() - t1
+    for _ in range(args.warmup):
+        b.run()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    launches0 = epwi.epwi_kernel_launches()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    pers = []
+    clocks_path = os.path.join(tempfile.gettempdir(), f"epwi_clocks_{os.getpid()}.csv")
+    with ClockSampler(clocks_path) as cs:
+        time.sleep(0.3)
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            sig = b.run()
+            ev[k][1].record(stream)
+            pers.append(b.stats()["ms_persistent"])
+        torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(c) for a, c in ev) / args.steps
+    st = b.stats()
+    ms_p = sum(pers) / len(pers)
+    achieved = st["scatter_flops"] / (ms_p * 1e-3) / 1e12
+    tiles = [b.tile(s) for s in range(64)]
+    line = {"metric": "batched el-ph (k,q)-pairs/s over 64 uneven systems (one graph launch per step)",
+            "value": npairs / (ms * 1e-3), "unit": "pairs/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "time_to_sigma_ms": ms, "pairs_per_step": npairs,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (f64 sums)", "data": "synthetic",
+            "config": dict(BATCH, scale=args.batch_scale, grids=grids,
+                           l2="flushed between timed steps (256 MiB write)"),
+            "gpu_launches": int((epwi.epwi_kernel_launches() - launches0) / max(1, args.steps)),
+            "graph": {"nodes": st["graph_nodes"], "persistent_ctas": st["persistent_ctas"],
+                      "items": st["n_items"], "smem_bytes": st["smem_bytes"]},
+            "stage_ms": {"persistent": ms_p, "rest_of_graph": ms - ms_p, "plan": st["ms_plan"]},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                         "kernel": "k_batch_scatter (persistent, FP32 SIMT)",
+                         "peak_source": "FP32 derived: 152 SM x 128 lanes x 2 flop x 2.07 GHz"},
+            "restage_flops": st["restage_flops"],
+            "tiles": {"autotuned": sum(1 for t in tiles if t[2] in (1, 2)),
+                      "shapes": sorted({f"{t[0]}x{t[1]}" for t in tiles})},
+            "clocks": cs.summary(0),
+            "e2e": {"value": npairs / (t_setup + t_first), "unit": "pairs/s",
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 64 * 9 * 8,
+                    "note": "host arrays -> sigma once: setup of 64 systems + plan (autotune) + first run"},
+            "cpu_baseline": None}
+    b.close()
+    print(json.dumps(line), flush=True)
+
+
+def run_learned(args):
+    """Learned q-proposal on the Si-like system: train at 24^3, importance-sample 1/tau at
+    100^3, compare with the full-grid FP64 and fp16x3 results."""
+    import torch
+    from paper_2306_16493_gb300 import epwi, synth
+    torch.cuda.set_device(0)
+    sysm = synth.si_like_system(3)
+    T, eta = 300.0, 0.01
+    ctx = epwi.Context()
+    ctx.setup(sysm)
+    ctx.eigs(24)
+    mu24 = ctx.find_mu(T, 1e18, sysm.n_valence)
+    _, cbm24 = ctx.band_edges(sysm.n_valence)
+    t0 = time.perf_counter()
+    loss = ctx.mlp_train(T, mu24, 4 * eta, cbm24 - 0.05, cbm24 + 0.3, seed=2)
+    t_train = time.perf_counter() - t0
+    ntrain = len(epwi.epwi_mlp_get_training_set(ctx.h)[1])
+    N = args.learned_grid
+    ctx.eigs(N)
+    mu = ctx.find_mu(T, 1e18, sysm.n_valence)
+    _, cbm = ctx.band_edges(sysm.n_valence)
+    lo, hi = cbm, cbm + 0.25
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t
+
+    res = {}
+    for prec in ("fp64", "fp16x3"):
+        ctx.set_precision(prec)
+        ctx.scatter_rates(T, mu, eta, lo, hi)             # warm-up
+        dt = timed(lambda: ctx.scatter_rates(T, mu, eta, lo, hi))
+        r = ctx.rates()[2]
+        if prec == "fp64":
+            full = r
+        res[prec] = {"s": dt, "pairs": ctx.stats()["n_pairs"],
+                     "rms_rel_err": float(np.sqrt(np.mean(((r - full) / full) ** 2)))}
+    ctx.set_precision("fp64")
+    for S in args.learned_samples:
+        for name, kw in (("uniform", dict(proposal="uniform")),
+                         ("learned", dict(proposal="learned", alpha=0.1, cell_stride=args.learned_stride))):
+            errs, dts = [], []
+            for seed in range(2):
+                dts.append(timed(lambda: ctx.scatter_rates_is(T, mu, eta, lo, hi, S, seed=11 + seed, **kw)))
+                r = ctx.rates()[2]
+                errs.append(float(np.sqrt(np.mean(((r - full) / full) ** 2))))
+            st = ctx.stats()
+            res[f"{name}_S{S}"] = {"s": min(dts), "pairs": st["n_pairs"], "rms_rel_err": float(np.mean(errs)),
+                                   "ms_proposal": st["ms_proposal"], "ms_sampling": st["ms_sampling"],
+                                   "ms_scatter": st["ms_scatter"],
+                                   "proposal_tflops": st["proposal_flops"] / max(1e-9, st["ms_proposal"]) / 1e9}
+    S = args.learned_samples[-1]
+    line = {"metric": "importance-sampled 1/tau with the learned q-proposal: time and rms error vs the "
+                      "full-grid FP64 rates", "value": res[f"learned_S{S}"]["s"] * 1e3, "unit": "ms",
+            "higher_is_better": False, "n_gpus": 1, "steps": 2, "warmup": 1, "data": "synthetic",
+            "dtype": "bf16 weights f32 network, f64 estimator", "vs_baseline": None,
+            "config": {"workload": f"si_like_{N}_learned", "train_grid": 24, "train_smear_eV": 4 * eta,
+                       "smear_eV": eta, "T_K": T, "n_c_cm3": 1e18, "window": "[CBM, CBM+0.25]",
+                       "cell_stride": args.learned_stride, "alpha": 0.1, "samples_per_k": args.learned_samples},
+            "training": {"samples": ntrain, "loss": loss, "s": t_train},
+            "results": res}
+    ctx.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -330,9 +479,20 @@ def main():
     ap.add_argument("--grid", type=int, default=WORKLOAD["grid"],
                     help="k and q grid per axis (48 is the benchmark; smaller sizes are for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="al_like", choices=["al_like", "batch64", "si_like_learned"],
+                    help="al_like: the benchmark; batch64 and si_like_learned: the batched and "
+                         "learned-proposal workloads (reported separately)")
+    ap.add_argument("--batch-scale", type=int, default=3, help="batch64: grid divisor")
+    ap.add_argument("--learned-grid", type=int, default=100)
+    ap.add_argument("--learned-stride", type=int, default=4)
+    ap.add_argument("--learned-samples", type=int, nargs="+", default=[10000, 100000])
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch64":
+        run_batch(args)
+    elif args.workload == "si_like_learned":
+        run_learned(args)
     else:
         run_gpu(args)
 

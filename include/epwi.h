@@ -359,6 +359,13 @@ const char *epwi_batch_last_error(const epwi_batch *batch);
  * grids[nsys][3]. */
 epwi_status epwi_batch_setup(epwi_batch *batch, int32_t nsys, const epwi_system *systems,
                              const int32_t *grids);
+/* Appends one system with its grid[3]; its host arrays may be freed when the call returns.
+ * index (may be NULL) receives its position in the batch. */
+epwi_status epwi_batch_add(epwi_batch *batch, const epwi_system *sys, const int32_t *grid,
+                           int32_t *index);
+/* Band range (min, max of eps over all bands) of system s on its grid, for choosing mu and
+ * windows before planning (runs that system's eigensolves). */
+epwi_status epwi_batch_band_range(epwi_batch *batch, int32_t s, double *emin, double *emax);
 /* Plans the step for temperature T, chemical potentials mu[nsys], smearing and per-system
  * windows [emin, emax]; autotune_tiles != 0 runs the autotuner (otherwise a default shape,
  * or the one set by epwi_batch_set_tile).  n_pairs (may be NULL) receives the sieved pairs

@@ -9,6 +9,7 @@
 #include <new>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "epwi_internal.cuh"
@@ -35,6 +36,18 @@ epwi_status guard(epwi_ctx *c, F &&f) {
         c->err = "unexpected internal error";
         return EPWI_ECUDA;
     }
+}
+
+// f(i) for i in [0, n) on the host's hardware threads (static contiguous split).
+template <class F>
+void parallel_for(int n, F &&f) {
+    const int nt = std::max(1, std::min<int>(n, (int)std::thread::hardware_concurrency()));
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; ++t)
+        th.emplace_back([&, t] {
+            for (int i = (int)((int64_t)n * t / nt); i < (int)((int64_t)n * (t + 1) / nt); ++i) f(i);
+        });
+    for (auto &x : th) x.join();
 }
 
 template <class T>
@@ -235,18 +248,19 @@ epwi_status epwi_setup(epwi_ctx *c, const epwi_system *s) {
                         s->wp[r] * s->Phi[((size_t)r * Nm + i) * Nm + j] / std::sqrt(mm[i] * mm[j]);
         const size_t ng = (size_t)nRe * nRp * Nm * W * W;
         const size_t per_re = (size_t)nRp * Nm * W * W;
-        std::vector<double2> g64(ng);
+        std::vector<double2> g64(c->keep_g64 ? ng : 0);
         std::vector<float2> g32(ng);
-        for (int re = 0; re < nRe; ++re)
+        parallel_for(nRe, [&](int re) {
             for (int rp = 0; rp < nRp; ++rp) {
                 const double w = s->we[re] * s->wp[rp];
                 const size_t base = (size_t)re * per_re + (size_t)rp * Nm * W * W;
                 for (size_t e = 0; e < (size_t)Nm * W * W; ++e) {
                     const epwi_c64 v = s->g[base + e];
-                    g64[base + e] = make_double2(w * v.re, w * v.im);
+                    if (c->keep_g64) g64[base + e] = make_double2(w * v.re, w * v.im);
                     g32[base + e] = make_float2((float)(w * v.re), (float)(w * v.im));
                 }
             }
+        });
         // Rp as a full cube [-r, r]^3 with n3 fastest enables the incremental phase index
         // of the tensor-core kernel.
         c->rp_cube_r = -1;
@@ -262,17 +276,22 @@ epwi_status epwi_setup(epwi_ctx *c, const epwi_system *s) {
         }
         // |ghat(k)[rp][mu][i][n]| <= sum_Re sum_j |w g| (|V_jn| <= 1): scale fp16 operands so
         // that this bound maps to 2^14 (no overflow, full mantissa for the split).
-        double gbound = 0;
-        for (int rp = 0; rp < nRp; ++rp)
+        std::vector<double> rp_bound(nRp, 0.0);
+        parallel_for(nRp, [&](int rp) {
             for (int mi = 0; mi < Nm * W; ++mi) {
                 double sum = 0;
-                for (int re = 0; re < nRe; ++re)
+                for (int re = 0; re < nRe; ++re) {
+                    const double w = s->we[re] * s->wp[rp];
                     for (int j = 0; j < W; ++j) {
-                        const double2 v = g64[(size_t)re * per_re + ((size_t)rp * Nm * W + mi) * W + j];
-                        sum += std::hypot(v.x, v.y);
+                        const epwi_c64 v = s->g[(size_t)re * per_re + ((size_t)rp * Nm * W + mi) * W + j];
+                        sum += std::hypot(w * v.re, w * v.im);
                     }
-                gbound = std::max(gbound, sum);
+                }
+                rp_bound[rp] = std::max(rp_bound[rp], sum);
             }
+        });
+        double gbound = 0;
+        for (double v : rp_bound) gbound = std::max(gbound, v);
         c->tc_scale_exp = gbound > 0 ? 14 - (int)std::ceil(std::log2(gbound)) : 0;
         c->tc_ptab_key = -1;
         upload(c->Re, s->Re, 3 * (size_t)nRe, c->stream);
@@ -281,7 +300,8 @@ epwi_status epwi_setup(epwi_ctx *c, const epwi_system *s) {
         upload(c->Hw, Hw.data(), Hw.size(), c->stream);
         upload(c->Phiw, Pw.data(), Pw.size(), c->stream);
         upload(c->mode_mass, mm.data(), mm.size(), c->stream);
-        upload(c->gw64, g64.data(), g64.size(), c->stream);
+        if (c->keep_g64) upload(c->gw64, g64.data(), g64.size(), c->stream);
+        else c->gw64.release();
         upload(c->gw32, g32.data(), g32.size(), c->stream);
         EPWI_CUDA(cudaStreamSynchronize(c->stream));
         c->have_sys = true;

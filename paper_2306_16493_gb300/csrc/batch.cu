@@ -553,7 +553,7 @@ float time_tile(epwi_batch *b, int s, int Mt, int KC, int64_t sample, int64_t *p
         dp.ensure(sizeof(double) * items.size());
         const size_t sm = smem_bytes(Mt, KC, d.NW);
         const int grid = persistent_grid(b, sm);
-        for (int rep = 0; rep < 3; ++rep) {
+        for (int rep = 0; rep < 2; ++rep) {
             EPWI_CUDA(cudaMemsetAsync(dc.p, 0, sizeof(int), b->stream));
             cudaEventRecord(b->ev[0], b->stream);
             k_batch_scatter<<<grid, kBT, sm, b->stream>>>(ds.as<BSys>(), di.as<BItem>(),
@@ -595,10 +595,10 @@ std::pair<int, int> autotune(epwi_batch *b, int s, int &src) {
     std::pair<int, int> best = default_tile(NW);
     double best_t = 1e300;
     for (int mt : {16, 32, 64, 128, 256}) {
-        for (int kc : {16, 32, 64}) {
+        for (int kc : {16, 32}) {
             if (!tile_ok(mt, kc, NW)) continue;
             int64_t pairs = 0;
-            const float ms = time_tile(b, s, mt, kc, 4096, &pairs);
+            const float ms = time_tile(b, s, mt, kc, 1024, &pairs);
             if (pairs == 0) continue;
             const double per = ms / (double)pairs;
             if (per < best_t) {
@@ -830,6 +830,20 @@ void epwi_batch_destroy(epwi_batch *b) { delete b; }
 
 const char *epwi_batch_last_error(const epwi_batch *b) { return b ? b->err.c_str() : "null batch"; }
 
+namespace {
+void add_system(epwi_batch *b, const epwi_system *sys, const int32_t *grid) {
+    for (int a = 0; a < 3; ++a) EPWI_REQUIRE(grid[a] >= 1, EPWI_EINVAL, "grid sizes must be >= 1");
+    b->drop_graph();
+    b->planned = false;
+    epwi_ctx *c = nullptr;
+    EPWI_REQUIRE(epwi_create(&c, &b->opt) == EPWI_OK, EPWI_ECUDA, "context creation failed");
+    b->sys.push_back(c);
+    c->keep_g64 = false;             // the batch stages g in FP32 only
+    check(c, epwi_setup(c, sys), "epwi_setup");
+    b->grids.push_back({grid[0], grid[1], grid[2]});
+}
+}  // namespace
+
 epwi_status epwi_batch_setup(epwi_batch *b, int32_t nsys, const epwi_system *systems,
                              const int32_t *grids) {
     return bguard(b, [&] {
@@ -840,15 +854,16 @@ epwi_status epwi_batch_setup(epwi_batch *b, int32_t nsys, const epwi_system *sys
         b->sys.clear();
         b->grids.clear();
         b->forced.clear();
-        for (int s = 0; s < nsys; ++s) {
-            epwi_ctx *c = nullptr;
-            EPWI_REQUIRE(epwi_create(&c, &b->opt) == EPWI_OK, EPWI_ECUDA, "context creation failed");
-            b->sys.push_back(c);
-            check(c, epwi_setup(c, &systems[s]), "epwi_setup");
-            for (int a = 0; a < 3; ++a)
-                EPWI_REQUIRE(grids[3 * s + a] >= 1, EPWI_EINVAL, "grid sizes must be >= 1");
-            b->grids.push_back({grids[3 * s], grids[3 * s + 1], grids[3 * s + 2]});
-        }
+        for (int s = 0; s < nsys; ++s) add_system(b, &systems[s], grids + 3 * s);
+    });
+}
+
+epwi_status epwi_batch_add(epwi_batch *b, const epwi_system *sys, const int32_t *grid,
+                           int32_t *index) {
+    return bguard(b, [&] {
+        EPWI_REQUIRE(sys && grid, EPWI_EINVAL, "bad argument");
+        add_system(b, sys, grid);
+        if (index) *index = (int32_t)b->sys.size() - 1;
     });
 }
 
@@ -937,6 +952,16 @@ epwi_status epwi_batch_set_tile(epwi_batch *b, int32_t s, int32_t mt, int32_t kc
                      "tile shape does not fit this system");
         b->forced.resize(b->sys.size(), {0, 0});
         b->forced[s] = {mt, kc};
+    });
+}
+
+epwi_status epwi_batch_band_range(epwi_batch *b, int32_t s, double *emin, double *emax) {
+    return bguard(b, [&] {
+        EPWI_REQUIRE(s >= 0 && s < (int)b->sys.size(), EPWI_EINVAL, "no such system");
+        epwi_ctx *c = b->sys[s];
+        const int g3[3] = {b->grids[s][0], b->grids[s][1], b->grids[s][2]};
+        check(c, epwi_eigs(c, g3, g3), "epwi_eigs");
+        check(c, epwi_band_range(c, emin, emax), "epwi_band_range");
     });
 }
 

@@ -98,6 +98,7 @@ struct epwi_ctx {
     DevBuf mode_mass;              // double [Nm] mass of the atom of each Cartesian mode
     DevBuf gw64;                   // double2 [nRe][nRp*Nm*W*W], c = ((rp*Nm+mu)*W+i)*W+j
     DevBuf gw32;                   // float2, same layout
+    bool keep_g64 = true;          // false: FP32 copy only (members of a batch)
 
     // eigen-tables (after epwi_eigs)
     bool have_eigs = false;

@@ -118,6 +118,8 @@ def _load() -> C.CDLL:
         "epwi_batch_last_error": (C.c_char_p, [P]),
         "epwi_batch_setup": (I32, [P, I32, P, P]),
         "epwi_batch_plan": (I32, [P, D, P, D, P, P, I32, P]),
+        "epwi_batch_add": (I32, [P, P, P, P]),
+        "epwi_batch_band_range": (I32, [P, I32, P, P]),
         "epwi_batch_run": (I32, [P, P]),
         "epwi_batch_get_rates": (I32, [P, I32, I64, P, P, P, P]),
         "epwi_batch_set_tile": (I32, [P, I32, I32, I32]),
@@ -424,6 +426,20 @@ class Batch:
         _bcheck(self.h, _lib.epwi_batch_setup(self.h, len(systems), arr, _ptr(g)))
         self.nsys = len(systems)
         self._keep = keep
+
+    def add(self, sysm, grid):
+        """Appends one system (its arrays may be dropped afterwards); returns its index."""
+        s, keep = _system_struct(sysm)
+        g = np.ascontiguousarray(np.asarray(grid, np.int32).reshape(3))
+        idx = C.c_int32()
+        _bcheck(self.h, _lib.epwi_batch_add(self.h, C.byref(s), _ptr(g), C.byref(idx)))
+        self.nsys = idx.value + 1
+        return idx.value
+
+    def band_range(self, s):
+        lo, hi = C.c_double(), C.c_double()
+        _bcheck(self.h, _lib.epwi_batch_band_range(self.h, s, C.byref(lo), C.byref(hi)))
+        return lo.value, hi.value
 
     def plan(self, T, mu, smear, emin, emax, autotune=True):
         mu = np.ascontiguousarray(mu, float)

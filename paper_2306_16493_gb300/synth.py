@@ -83,8 +83,44 @@ class SplitMix64:
 
     def complex_normal(self, shape, sigma=1.0) -> np.ndarray:
         n = int(np.prod(shape))
-        z = self.normal(2 * n)
-        return (sigma / math.sqrt(2.0)) * (z[0::2] + 1j * z[1::2]).reshape(shape)
+        if n < self._CHUNK:
+            z = self.normal(2 * n)
+            return (sigma / math.sqrt(2.0)) * (z[0::2] + 1j * z[1::2]).reshape(shape)
+        return self._complex_normal_chunked(n, sigma).reshape(shape)
+
+    # Large draws: element j of complex_normal depends only on the stream values at counter
+    # offsets j + 1 (u1) and n + j + 1 (u2), so chunks are computed independently, in
+    # threads, with the same elementwise operations as ``normal`` (identical results).
+    _CHUNK = 1 << 21
+
+    def _complex_normal_chunked(self, n: int, sigma: float) -> np.ndarray:
+        from concurrent.futures import ThreadPoolExecutor
+        import os
+
+        out = np.empty(n, np.complex128)
+        s0 = self.state
+        scale = sigma / math.sqrt(2.0)
+
+        def draw(start, count):
+            with np.errstate(over="ignore"):
+                z = s0 + np.arange(start + 1, start + count + 1, dtype=np.uint64) * self._GAMMA
+                z = (z ^ (z >> np.uint64(30))) * self._M1
+                z = (z ^ (z >> np.uint64(27))) * self._M2
+                z = z ^ (z >> np.uint64(31))
+            return (z >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+        def work(a):
+            b = min(n, a + self._CHUNK)
+            u1 = 1.0 - draw(a, b - a)
+            u2 = draw(n + a, b - a)
+            r = np.sqrt(-2.0 * np.log(u1))
+            out[a:b] = scale * (r * np.cos(2.0 * np.pi * u2) + 1j * (r * np.sin(2.0 * np.pi * u2)))
+
+        with ThreadPoolExecutor(max_workers=max(1, os.cpu_count() or 1)) as ex:
+            list(ex.map(work, range(0, n, self._CHUNK)))
+        with np.errstate(over="ignore"):
+            self.state = self.state + np.uint64(2 * n) * self._GAMMA
+        return out
 
 
 @dataclasses.dataclass
