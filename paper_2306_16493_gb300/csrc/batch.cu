@@ -65,64 +65,95 @@ __host__ __device__ inline void col_groups(int NW, int &CW, int &RG) {
     RG = kBT / CW;
 }
 
-// Re->k stage in FP32: ghat(k)[rp][mu][i][n] = sum_j [sum_Re w e^{ik.Re} g_ij^mu(Re,Rp)] V_jn(k)
-// for the window bands n; KG k-points per block share every read of g.
-template <int WT, int KG>
-__global__ void __launch_bounds__(128) k_restage_f32(GridInfo g, int W_, int nRe, int nrow,
-                                                     const int *__restrict__ Re,
-                                                     const float2 *__restrict__ gw,
-                                                     const float2 *__restrict__ ph,
-                                                     const float2 *__restrict__ V32, int nkp,
-                                                     const int *__restrict__ kpts,
-                                                     const int64_t *__restrict__ kp_state,
-                                                     const int *__restrict__ win_lo,
-                                                     const int *__restrict__ win_n,
-                                                     float2 *__restrict__ ghat) {
-    constexpr int WM = WT ? WT : epc::kMaxW;
-    const int W = WT ? WT : W_;
-    extern __shared__ float2 P[];   // [KG][nRe]
-    const int kg0 = blockIdx.y * KG;
-    for (int idx = threadIdx.x; idx < KG * nRe; idx += blockDim.x) {
-        const int kk = idx / nRe, r = idx % nRe;
-        float2 p = make_float2(0.f, 0.f);
-        if (kg0 + kk < nkp) {
-            int i1, i2, i3;
-            grid_coords(g, kpts[kg0 + kk], i1, i2, i3);
-            p = ph[phase_index(i1 * g.s1 % g.L, i2 * g.s2 % g.L, i3 * g.s3 % g.L, Re[3 * r],
-                               Re[3 * r + 1], Re[3 * r + 2], g.L)];
-        }
-        P[idx] = p;
+// Re->k stage in FP32, two kernels per chunk of k-points.
+// 1. Gk[k][c] = sum_Re w e^{ik.Re} g[Re][c] over the flattened c = (rp, mu, i, j): KB
+//    k-points per block share every read of g (one 8-byte load per Re feeds KB complex FMAs).
+// 2. ghat(k)[state][rp][mu][i] = sum_j Gk[k][(rp, mu, i), j] V_jn(k) for the window bands n.
+constexpr int kKB = 32;           // k-points per block of the first kernel
+constexpr int kRC = 64;           // Re per shared-memory chunk
+
+__global__ void __launch_bounds__(256) k_gk_f32(int64_t C, int nRe, GridInfo g,
+                                                const int *__restrict__ Re,
+                                                const float2 *__restrict__ gw,
+                                                const float2 *__restrict__ ph, int nkc,
+                                                const int *__restrict__ kpts,
+                                                float2 *__restrict__ Gk) {
+    __shared__ float2 P[kKB][kRC];
+    __shared__ int ka[kKB][3];
+    const int t = threadIdx.x;
+    const int kb0 = blockIdx.y * kKB;
+    const int64_t c = (int64_t)blockIdx.x * 256 + t;
+    if (t < kKB) {
+        int i1 = 0, i2 = 0, i3 = 0;
+        if (kb0 + t < nkc) grid_coords(g, kpts[kb0 + t], i1, i2, i3);
+        ka[t][0] = i1 * g.s1 % g.L;
+        ka[t][1] = i2 * g.s2 % g.L;
+        ka[t][2] = i3 * g.s3 % g.L;
     }
-    __syncthreads();
-    const int row = blockIdx.x * blockDim.x + threadIdx.x;
-    if (row >= nrow) return;
-    float2 acc[KG][WM];
+    float2 acc[kKB];
 #pragma unroll
-    for (int kk = 0; kk < KG; ++kk)
-        for (int j = 0; j < W; ++j) acc[kk][j] = make_float2(0.f, 0.f);
-    const float2 *gr = gw + (size_t)row * W;
-    for (int r = 0; r < nRe; ++r) {
-        float2 gv[WM];
-        for (int j = 0; j < W; ++j) gv[j] = gr[(size_t)r * nrow * W + j];
-#pragma unroll
-        for (int kk = 0; kk < KG; ++kk) {
-            const float2 p = P[kk * nRe + r];
-            for (int j = 0; j < W; ++j) acc[kk][j] = cfmaf(p, gv[j], acc[kk][j]);
+    for (int kk = 0; kk < kKB; ++kk) acc[kk] = make_float2(0.f, 0.f);
+    for (int r0 = 0; r0 < nRe; r0 += kRC) {
+        const int rc = min(kRC, nRe - r0);
+        __syncthreads();
+        for (int e = t; e < kKB * kRC; e += 256) {
+            const int kk = e / kRC, rr = e % kRC;
+            float2 v = make_float2(0.f, 0.f);
+            if (rr < rc && kb0 + kk < nkc) {
+                const int *R = Re + 3 * (r0 + rr);
+                v = ph[phase_index(ka[kk][0], ka[kk][1], ka[kk][2], R[0], R[1], R[2], g.L)];
+            }
+            P[kk][rr] = v;
         }
-    }
+        __syncthreads();
+        if (c < C) {
+            const float2 *gc = gw + (int64_t)r0 * C + c;
+#pragma unroll 4
+            for (int rr = 0; rr < rc; ++rr) {
+                const float2 gv = gc[(int64_t)rr * C];
 #pragma unroll
-    for (int kk = 0; kk < KG; ++kk) {
-        if (kg0 + kk >= nkp) break;
-        const int ik = kpts[kg0 + kk];
-        const int lo = win_lo[ik], ns = win_n[ik];
-        const int64_t s0 = kp_state[kg0 + kk];
-        const float2 *Vk = V32 + (int64_t)ik * W * W;
-        for (int np = 0; np < ns; ++np) {
-            float2 o = make_float2(0.f, 0.f);
-            for (int j = 0; j < W; ++j) o = cfmaf(acc[kk][j], Vk[j * W + lo + np], o);
-            ghat[(s0 + np) * (int64_t)nrow + row] = o;
+                for (int kk = 0; kk < kKB; ++kk) acc[kk] = cfmaf(P[kk][rr], gv, acc[kk]);
+            }
         }
     }
+    if (c < C)
+#pragma unroll
+        for (int kk = 0; kk < kKB; ++kk)
+            if (kb0 + kk < nkc) Gk[(int64_t)(kb0 + kk) * C + c] = acc[kk];
+}
+
+__global__ void k_gk_rotate(int nkc, int nrow, int W, const float2 *__restrict__ Gk,
+                            const float2 *__restrict__ V32, const int *__restrict__ kpts,
+                            const int64_t *__restrict__ kp_state, const int *__restrict__ win_lo,
+                            const int *__restrict__ win_n, float2 *__restrict__ ghat) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)nkc * nrow) return;
+    const int kk = (int)(e / nrow), row = (int)(e % nrow);
+    const int ik = kpts[kk];
+    const int lo = win_lo[ik], ns = win_n[ik];
+    const float2 *gr = Gk + (int64_t)kk * nrow * W + (int64_t)row * W;
+    const float2 *Vk = V32 + (int64_t)ik * W * W;
+    const int64_t s0 = kp_state[kk];
+    for (int np = 0; np < ns; ++np) {
+        float2 o = make_float2(0.f, 0.f);
+        for (int j = 0; j < W; ++j) o = cfmaf(gr[j], Vk[j * W + lo + np], o);
+        ghat[(s0 + np) * (int64_t)nrow + row] = o;
+    }
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void cp_async_16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 // The persistent kernel: CTAs take queue items until the queue is empty.
@@ -161,8 +192,11 @@ __global__ void __launch_bounds__(kBT, 1) k_batch_scatter(const BSys *__restrict
             sa[1][p] = i2 * S.g.s2 % S.g.L;
             sa[2][p] = i3 * S.g.s3 % S.g.L;
         }
-        float2 *P = sm;                          // [Mt][KC]
-        float2 *Cs = sm + (size_t)S.Mt * KC;     // [Mt][NW]
+        // shared memory: two K chunks of ghat [KC][NW], phases [Mt][KC+1], product [Mt][NW]
+        float2 *Gs = sm;
+        float2 *P = sm + (size_t)2 * KC * NW;
+        float2 *Cs = P + (size_t)S.Mt * (KC + 1);
+        const int KP = KC + 1;
         const int cg = t % S.CW, rg = t / S.CW;
         const bool tact = rg < S.RG;
         const int ncol = (NW + S.CW - 1) / S.CW;            // 1 or 2
@@ -171,9 +205,26 @@ __global__ void __launch_bounds__(kBT, 1) k_batch_scatter(const BSys *__restrict
 #pragma unroll
         for (int a = 0; a < kAcc; ++a) acc[a] = make_float2(0.f, 0.f);
         __syncthreads();
-        // ---- Rp -> q: C[p][mu, i] = sum_Rp e^{i q_p . Rp} ghat[Rp][mu][i]
-        for (int r0 = 0; r0 < S.nRp; r0 += KC) {
-            const int kc = min(KC, S.nRp - r0);
+        // ---- Rp -> q: C[p][mu, i] = sum_Rp e^{i q_p . Rp} ghat[Rp][mu][i]; the K chunks of
+        // ghat are copied to shared memory with cp.async, one chunk ahead of the compute
+        const int nch = (S.nRp + KC - 1) / KC;
+        auto issue = [&](int ch) {
+            if (ch < nch) {
+                const int r0 = ch * KC, kc = min(KC, S.nRp - r0);
+                const float2 *src = gh + (int64_t)r0 * NW;
+                float2 *dst = Gs + (size_t)(ch & 1) * KC * NW;
+                if ((NW & 1) == 0) {
+                    for (int e = t; e < kc * NW / 2; e += kBT) cp_async_16(dst + 2 * e, src + 2 * e);
+                } else {
+                    for (int e = t; e < kc * NW; e += kBT) cp_async_8(dst + e, src + e);
+                }
+            }
+            cp_async_commit_group();
+        };
+        issue(0);
+        for (int ch = 0; ch < nch; ++ch) {
+            issue(ch + 1);
+            const int r0 = ch * KC, kc = min(KC, S.nRp - r0);
             for (int e = t; e < cnt * KC; e += kBT) {
                 const int p = e / KC, kk = e - p * KC;
                 float2 v = make_float2(0.f, 0.f);
@@ -181,20 +232,22 @@ __global__ void __launch_bounds__(kBT, 1) k_batch_scatter(const BSys *__restrict
                     const int *R = S.Rp + 3 * (r0 + kk);
                     v = S.ph32[phase_index(sa[0][p], sa[1][p], sa[2][p], R[0], R[1], R[2], S.g.L)];
                 }
-                P[e] = v;
+                P[p * KP + kk] = v;
             }
+            cp_async_wait_group<1>();
             __syncthreads();
             if (tact) {
+                const float2 *G = Gs + (size_t)(ch & 1) * KC * NW;
                 for (int kk = 0; kk < kc; ++kk) {
-                    const float2 *gr = gh + (int64_t)(r0 + kk) * NW;
-                    const float2 g0 = gr[cg];
-                    const float2 g1 = (ncol > 1 && cg + S.CW < NW) ? gr[cg + S.CW] : make_float2(0.f, 0.f);
+                    const float2 g0 = G[kk * NW + cg];
+                    const float2 g1 = (ncol > 1 && cg + S.CW < NW) ? G[kk * NW + cg + S.CW]
+                                                                  : make_float2(0.f, 0.f);
 #pragma unroll
                     for (int a = 0; a < kAcc; ++a) {
                         const int i = ncol == 1 ? a : (a >> 1);
                         const int p = rg + i * S.RG;
                         if (i < npt && p < cnt) {
-                            const float2 pv = P[p * KC + kk];
+                            const float2 pv = P[p * KP + kk];
                             acc[a] = cfmaf(pv, (ncol == 1 || (a & 1) == 0) ? g0 : g1, acc[a]);
                         }
                     }
@@ -202,6 +255,7 @@ __global__ void __launch_bounds__(kBT, 1) k_batch_scatter(const BSys *__restrict
             }
             __syncthreads();
         }
+        cp_async_wait_group<0>();
         if (tact) {
 #pragma unroll
             for (int a = 0; a < kAcc; ++a) {
@@ -324,7 +378,9 @@ __global__ void __launch_bounds__(256) k_batch_sigma(const SigmaDesc *__restrict
     }
 }
 
-size_t smem_bytes(int Mt, int KC, int NW) { return sizeof(float2) * ((size_t)Mt * KC + (size_t)Mt * NW); }
+size_t smem_bytes(int Mt, int KC, int NW) {
+    return sizeof(float2) * ((size_t)2 * KC * NW + (size_t)Mt * (KC + 1) + (size_t)Mt * NW);
+}
 
 bool tile_ok(int Mt, int KC, int NW) {
     int CW, RG;
@@ -360,6 +416,7 @@ struct epwi_batch {
     std::vector<std::pair<int, int>> forced; // tiles set by epwi_batch_set_tile (0: none)
     DevBuf d_sys, d_items, d_order, d_counter, d_part, d_state_item, d_state_sys, d_pref;
     DevBuf d_inv_tau, d_sigdesc, d_sigma;
+    DevBuf d_gk;                             // Re->k scratch, reused by every system
     std::vector<int64_t> sys_state0;
     int64_t nitems = 0, nstates = 0, npairs = 0;
     size_t smem = 0;
@@ -382,7 +439,7 @@ struct epwi_batch {
         for (auto &b : pairs) b.release();
         for (auto &b : ghat) b.release();
         DevBuf *all[] = {&d_sys, &d_items, &d_order, &d_counter, &d_part, &d_state_item,
-                         &d_state_sys, &d_pref, &d_inv_tau, &d_sigdesc, &d_sigma};
+                         &d_state_sys, &d_pref, &d_inv_tau, &d_sigdesc, &d_sigma, &d_gk};
         for (DevBuf *b : all) b->release();
         for (epwi_ctx *c : sys) epwi_destroy(c);
         if (own_stream && stream) cudaStreamDestroy(stream);
@@ -423,36 +480,35 @@ void put(DevBuf &b, const std::vector<T> &v, cudaStream_t st) {
         EPWI_CUDA(cudaMemcpyAsync(b.p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st));
 }
 
+// Chunk of k-points per pass of the two-kernel Re->k stage (the scratch Gk holds
+// chunk * nRp * Nm * W^2 complex FP32 values).
+int64_t restage_chunk(const epwi_ctx *c) {
+    const int64_t C = (int64_t)c->nRp * c->nm * c->nw * c->nw;
+    const int64_t kch = std::max<int64_t>(kKB, ((int64_t(1) << 31) / (8 * C)) / kKB * kKB);
+    return std::min<int64_t>(kch, std::max<int64_t>(c->nkp, 1));
+}
+
 void restage(epwi_batch *b, int s) {
     epwi_ctx *c = b->sys[s];
     const int64_t nrow = (int64_t)c->nRp * c->nm * c->nw;
+    const int64_t C = nrow * c->nw;
     GridInfo g = make_grid_info(c);
-    const int nkp = (int)c->nkp;
-    if (nkp == 0) return;
-#define RS_ARGS                                                                                   \
-    g, c->nw, c->nRe, (int)nrow, c->Re.as<int>(), c->gw32.as<float2>(), c->ph32.as<float2>(),      \
-        c->V32.as<float2>(), nkp, c->kpts.as<int>(), c->kp_state.as<int64_t>(), c->win_lo.as<int>(), \
-        c->win_n.as<int>(), b->ghat[s].as<float2>()
-#define RS_LAUNCH(WT, KG)                                                                         \
-    do {                                                                                          \
-        dim3 grid((unsigned)((nrow + 127) / 128), (unsigned)((nkp + KG - 1) / KG));               \
-        const size_t sm = sizeof(float2) * KG * c->nRe;                                           \
-        static size_t sm_set = 48 * 1024;   /* raised before any capture (planning runs first) */ \
-        if (sm > sm_set) {                                                                        \
-            EPWI_CUDA(cudaFuncSetAttribute(k_restage_f32<WT, KG>,                                 \
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)); \
-            sm_set = sm;                                                                          \
-        }                                                                                         \
-        k_restage_f32<WT, KG><<<grid, 128, sm, b->stream>>>(RS_ARGS);                              \
-        EPWI_CHECK_LAUNCH();                                                                      \
-    } while (0)
-    if (c->nw == 4) RS_LAUNCH(4, 8);
-    else if (c->nw == 8) RS_LAUNCH(8, 4);
-    else if (c->nw == 16) RS_LAUNCH(16, 2);
-    else if (c->nw == 24) RS_LAUNCH(24, 1);
-    else RS_LAUNCH(0, 1);
-#undef RS_LAUNCH
-#undef RS_ARGS
+    const int64_t nkp = c->nkp;
+    const int64_t kch = restage_chunk(c);
+    for (int64_t k0 = 0; k0 < nkp; k0 += kch) {
+        const int nkc = (int)std::min(kch, nkp - k0);
+        dim3 grid((unsigned)((C + 255) / 256), (unsigned)((nkc + kKB - 1) / kKB));
+        k_gk_f32<<<grid, 256, 0, b->stream>>>(C, c->nRe, g, c->Re.as<int>(), c->gw32.as<float2>(),
+                                               c->ph32.as<float2>(), nkc, c->kpts.as<int>() + k0,
+                                               b->d_gk.as<float2>());
+        EPWI_CHECK_LAUNCH();
+        const int64_t n2 = (int64_t)nkc * nrow;
+        k_gk_rotate<<<(unsigned)((n2 + 255) / 256), 256, 0, b->stream>>>(
+            nkc, (int)nrow, c->nw, b->d_gk.as<float2>(), c->V32.as<float2>(), c->kpts.as<int>() + k0,
+            c->kp_state.as<int64_t>() + k0, c->win_lo.as<int>(), c->win_n.as<int>(),
+            b->ghat[s].as<float2>());
+        EPWI_CHECK_LAUNCH();
+    }
 }
 
 // The per-system work that precedes the persistent kernel in every step.
@@ -653,6 +709,14 @@ void plan(epwi_batch *b, bool tune) {
         b->pairs[s].ensure(sizeof(int) * (c->npairs + 1));
         const int64_t nrow = (int64_t)c->nRp * c->nm * c->nw;
         b->ghat[s].ensure(sizeof(float2) * (size_t)nrow * (c->nstates + 1));
+        {
+            // grow-only scratch: sized before any capture so that captured passes never allocate
+            const size_t gk = sizeof(float2) * (size_t)restage_chunk(c) * nrow * c->nw;
+            if (gk > b->d_gk.bytes) {
+                EPWI_CUDA(cudaStreamSynchronize(st));
+                b->d_gk.ensure(gk);
+            }
+        }
         sieve_fill_chunk(c, 0, c->nkp, b->pairs[s].as<int>());
         restage(b, s);
         npairs += c->npairs;
