@@ -337,7 +337,8 @@ def run_batch(args):
     t0 = time.perf_counter()
     b = epwi.Batch(stream=stream.cuda_stream)
     h2d, grids = 0, []
-    for s in range(64):
+    members = [int(x) for x in args.batch_systems.split(",")] if args.batch_systems else range(64)
+    for s in members:
         sysm, N = synth.batch_system(s)
         Nr = max(2, N // args.batch_scale)
         b.add(sysm, (Nr, Nr, Nr))
@@ -346,9 +347,10 @@ def run_batch(args):
         grids.append(Nr)
         del sysm
     t_setup = time.perf_counter() - t0
-    mu = np.array([0.5 * sum(b.band_range(s)) for s in range(64)])
+    nsys = len(grids)
+    mu = np.array([0.5 * sum(b.band_range(s)) for s in range(nsys)])
     t1 = time.perf_counter()
-    npairs = b.plan(T, mu, eta, mu - win, mu + win, autotune=True)
+    npairs = b.plan(T, mu, eta, mu - win, mu + win, autotune=not args.no_autotune)
     sig = b.run()
     t_first = time.perf_counter() - t1
     for _ in range(args.warmup):
@@ -371,13 +373,13 @@ def run_batch(args):
     st = b.stats()
     ms_p = sum(pers) / len(pers)
     achieved = st["scatter_flops"] / (ms_p * 1e-3) / 1e12
-    tiles = [b.tile(s) for s in range(64)]
+    tiles = [b.tile(s) for s in range(nsys)]
     line = {"metric": "batched el-ph (k,q)-pairs/s over 64 uneven systems (one graph launch per step)",
             "value": npairs / (ms * 1e-3), "unit": "pairs/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "time_to_sigma_ms": ms, "pairs_per_step": npairs,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 (f64 sums)", "data": "synthetic",
-            "config": dict(BATCH, scale=args.batch_scale, grids=grids,
+            "config": dict(BATCH, scale=args.batch_scale, grids=grids, members=list(members),
                            l2="flushed between timed steps (256 MiB write)"),
             # one graph launch per step; its nodes are this library's kernels plus a few
             # memset and event-record nodes
@@ -394,7 +396,7 @@ def run_batch(args):
                       "shapes": sorted({f"{t[0]}x{t[1]}" for t in tiles})},
             "clocks": cs.summary(0),
             "e2e": {"value": npairs / (t_setup + t_first), "unit": "pairs/s",
-                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 64 * 9 * 8,
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": nsys * 9 * 8,
                     "note": "host arrays -> sigma once: setup of 64 systems + plan (autotune) + first run"},
             "cpu_baseline": None}
     b.close()
@@ -484,6 +486,8 @@ def main():
                     help="al_like: the benchmark; batch64 and si_like_learned: the batched and "
                          "learned-proposal workloads (reported separately)")
     ap.add_argument("--batch-scale", type=int, default=3, help="batch64: grid divisor")
+    ap.add_argument("--batch-systems", default="", help="batch64: comma-separated subset (profiling)")
+    ap.add_argument("--no-autotune", action="store_true", help="batch64: default tile shapes")
     ap.add_argument("--learned-grid", type=int, default=100)
     ap.add_argument("--learned-stride", type=int, default=4)
     ap.add_argument("--learned-samples", type=int, nargs="+", default=[10000, 100000])

@@ -238,18 +238,28 @@ __global__ void __launch_bounds__(kBT, 1) k_batch_scatter(const BSys *__restrict
             __syncthreads();
             if (tact) {
                 const float2 *G = Gs + (size_t)(ch & 1) * KC * NW;
-                for (int kk = 0; kk < kc; ++kk) {
-                    const float2 g0 = G[kk * NW + cg];
-                    const float2 g1 = (ncol > 1 && cg + S.CW < NW) ? G[kk * NW + cg + S.CW]
-                                                                  : make_float2(0.f, 0.f);
+                const int nv = min(npt, (cnt - rg + S.RG - 1) / S.RG);   // valid pairs
+                if (ncol == 1) {
+                    for (int kk = 0; kk < kc; ++kk) {
+                        const float2 g0 = G[kk * NW + cg];
+                        const float2 *pk = P + rg * KP + kk;
 #pragma unroll
-                    for (int a = 0; a < kAcc; ++a) {
-                        const int i = ncol == 1 ? a : (a >> 1);
-                        const int p = rg + i * S.RG;
-                        if (i < npt && p < cnt) {
-                            const float2 pv = P[p * KP + kk];
-                            acc[a] = cfmaf(pv, (ncol == 1 || (a & 1) == 0) ? g0 : g1, acc[a]);
-                        }
+                        for (int i = 0; i < kAcc; ++i)
+                            if (i < nv) acc[i] = cfmaf(pk[i * S.RG * KP], g0, acc[i]);
+                    }
+                } else {
+                    const bool c1 = cg + S.CW < NW;
+                    for (int kk = 0; kk < kc; ++kk) {
+                        const float2 g0 = G[kk * NW + cg];
+                        const float2 g1 = c1 ? G[kk * NW + cg + S.CW] : make_float2(0.f, 0.f);
+                        const float2 *pk = P + rg * KP + kk;
+#pragma unroll
+                        for (int i = 0; i < kAcc / 2; ++i)
+                            if (i < nv) {
+                                const float2 pv = pk[i * S.RG * KP];
+                                acc[2 * i] = cfmaf(pv, g0, acc[2 * i]);
+                                acc[2 * i + 1] = cfmaf(pv, g1, acc[2 * i + 1]);
+                            }
                     }
                 }
             }
@@ -277,10 +287,12 @@ __global__ void __launch_bounds__(kBT, 1) k_batch_scatter(const BSys *__restrict
             const float2 *Cp = Cs + (size_t)p * NW;
             float2 h[kNmB];
 #pragma unroll
-            for (int mu = 0; mu < kNmB; ++mu) {
-                h[mu] = make_float2(0.f, 0.f);
-                if (mu < Nm)
-                    for (int i = 0; i < W; ++i) h[mu] = cfmacf(Vq[i * W + m], Cp[mu * W + i], h[mu]);
+            for (int mu = 0; mu < kNmB; ++mu) h[mu] = make_float2(0.f, 0.f);
+            for (int i = 0; i < W; ++i) {             // one load of V_im(k+q) per i
+                const float2 v = Vq[i * W + m];
+#pragma unroll
+                for (int mu = 0; mu < kNmB; ++mu)
+                    if (mu < Nm) h[mu] = cfmacf(v, Cp[mu * W + i], h[mu]);
             }
             const float em = S.erel[ikq * W + m];
             const float fm = S.f32[ikq * W + m];
