@@ -129,6 +129,8 @@ struct epwi_ctx {
     DevBuf win_lo, win_n;          // int32 [Nk] first window band, count
     DevBuf kp_state;               // int64 [nkp+1] state offsets
     DevBuf kp_pairs;               // int64 [nkp+1] pair offsets
+    DevBuf sieve_mask;             // uint32 [nkp][mask_words]: sieve decisions of the count
+    int64_t mask_words = 0;        // words per k-point (0: no mask, the fill re-evaluates)
     DevBuf inv_tau;                // double [nstates]
     DevBuf st_k, st_n;             // int32 [nstates]
     DevBuf focc;                   // double [Nk][W] Fermi-Dirac
@@ -177,7 +179,7 @@ struct epwi_ctx {
                          &st_n, &focc, &nocc, &pairs, &ghat, &tiles, &tile_part, &kp_tile,
                          &scan_tmp, &red_tmp, &counts, &tc_ptab, &tc_erel, &tc_f32,
                          &tc_n32, &tc_hw32, &tc_err, &tc_meta, &is_pairs, &is_w,
-                         &is_kp_pairs};
+                         &is_kp_pairs, &sieve_mask};
         for (DevBuf *b : all) b->release();
         mlp_free(mlp);
     }

@@ -13,6 +13,7 @@
 namespace {
 
 constexpr int kScanBlock = 1024;
+constexpr int kSieveBlock = 256;  // threads of the sieve kernels (fixes the candidate order)
 constexpr int kScanItems = 4;
 
 __device__ __forceinline__ int64_t warp_incl_scan(int64_t v) {
@@ -120,11 +121,16 @@ __device__ __forceinline__ int64_t plane_kq(const GridInfo &g, int ka2, int ka3,
     return (int64_t)b2 * g.n3 + b3;
 }
 
+// Counts the kept q of each k-point.  With mask != nullptr it also records every decision:
+// the candidate of thread t at (plane block pb, i1) is bit t % 32 of word
+// ((pb / blockDim.x) * N1 + i1) * (blockDim.x / 32) + t / 32 of the k-point's row.
 __global__ void __launch_bounds__(256) k_sieve_count(SieveArgs a, int64_t nkp,
                                                      const int *__restrict__ kpts,
                                                      const int *__restrict__ lo,
                                                      const int *__restrict__ cnt,
-                                                     int64_t *__restrict__ counts) {
+                                                     int64_t *__restrict__ counts,
+                                                     uint32_t *__restrict__ mask,
+                                                     int64_t words_per_kp) {
     __shared__ double en[epc::kMaxW];
     __shared__ float en32[epc::kMaxW];
     __shared__ int64_t sm[33];
@@ -134,22 +140,65 @@ __global__ void __launch_bounds__(256) k_sieve_count(SieveArgs a, int64_t nkp,
     int ka1, ka2, ka3;
     grid_coords(a.g, ik, ka1, ka2, ka3);
     const int64_t nplane = (int64_t)a.g.n2 * a.g.n3;
+    const int wpb = blockDim.x >> 5;
+    uint32_t *mrow = mask ? mask + (int64_t)blockIdx.x * words_per_kp : nullptr;
     int64_t c = 0;
     for (int64_t pb = 0; pb < nplane; pb += blockDim.x) {
         const int64_t p = pb + threadIdx.x;
-        if (p >= nplane) break;
-        const int64_t kqp = plane_kq(a.g, ka2, ka3, p);
+        const bool inb = p < nplane;
+        const int64_t kqp = inb ? plane_kq(a.g, ka2, ka3, p) : 0;
         int b1 = ka1;
         for (int i1 = 0; i1 < a.g.n1; ++i1) {
             const int64_t iq = (int64_t)i1 * nplane + p;
             const int64_t ikq = (int64_t)b1 * nplane + kqp;
-            c += pair_valid(a, nsel, en, en32, iq, ikq);
+            const bool v = inb && pair_valid(a, nsel, en, en32, iq, ikq);
+            c += v;
+            if (mrow) {
+                const uint32_t bits = __ballot_sync(0xffffffffu, v);
+                if ((threadIdx.x & 31) == 0)
+                    mrow[((pb / blockDim.x) * a.g.n1 + i1) * wpb + (threadIdx.x >> 5)] = bits;
+            }
             if (++b1 == a.g.n1) b1 = 0;
         }
     }
     int64_t tot;
     block_excl_scan(c, sm, tot);
     if (threadIdx.x == 0) counts[blockIdx.x] = tot;
+}
+
+// Pair lists from the decision mask of k_sieve_count, in the same candidate order: each
+// thread takes one mask word, the block scans the word populations in word order, and
+// every thread writes the q of its word's set bits in bit order.
+__global__ void __launch_bounds__(256) k_sieve_fill_mask(GridInfo g, int64_t kp0,
+                                                         const uint32_t *__restrict__ mask,
+                                                         int64_t words_per_kp, int count_block,
+                                                         const int64_t *__restrict__ kp_pairs,
+                                                         int *__restrict__ pairs) {
+    __shared__ int64_t sm[33];
+    const int64_t kp = kp0 + blockIdx.x;
+    const uint32_t *mrow = mask + kp * words_per_kp;
+    const int64_t nplane = (int64_t)g.n2 * g.n3;
+    const int wpb = count_block >> 5;
+    int64_t base = kp_pairs[kp] - kp_pairs[kp0];
+    for (int64_t w0 = 0; w0 < words_per_kp; w0 += blockDim.x) {
+        const int64_t w = w0 + threadIdx.x;
+        uint32_t bits = w < words_per_kp ? mrow[w] : 0u;
+        int64_t tot;
+        const int64_t off = block_excl_scan((int64_t)__popc(bits), sm, tot);
+        if (bits) {
+            const int64_t grp = w / wpb;                 // (plane block, i1) group
+            const int64_t pbi = grp / g.n1, i1 = grp % g.n1;
+            const int64_t t0 = (w % wpb) * 32;
+            int64_t o = base + off;
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1;
+                const int64_t p = pbi * count_block + t0 + b;
+                pairs[o++] = (int)(i1 * nplane + p);
+            }
+        }
+        base += tot;
+    }
 }
 
 // Writes the kept q of k-points kp0 + blockIdx.x in the candidate order of k_sieve_count.
@@ -287,10 +336,16 @@ void sieve_count(epwi_ctx *c) {
     c->counts.ensure(sizeof(int64_t) * (nkp + 1));
     c->kp_pairs.ensure(sizeof(int64_t) * (nkp + 1));
     SieveArgs a = make_sieve_args(c);
+    // decision mask for the fill when it fits in 2 GiB (else the fill re-evaluates)
+    const int64_t nplane = (int64_t)c->ng[1] * c->ng[2];
+    const int64_t words = ((nplane + kSieveBlock - 1) / kSieveBlock) * c->ng[0] * (kSieveBlock / 32);
+    c->mask_words = (nkp > 0 && words * nkp * 4 <= (int64_t(1) << 31)) ? words : 0;
+    if (c->mask_words) c->sieve_mask.ensure(sizeof(uint32_t) * words * nkp);
     if (nkp > 0) {
-        k_sieve_count<<<(unsigned)nkp, 256, 0, c->stream>>>(a, nkp, c->kpts.as<int>(),
-                                                           c->win_lo.as<int>(), c->win_n.as<int>(),
-                                                           c->counts.as<int64_t>());
+        k_sieve_count<<<(unsigned)nkp, kSieveBlock, 0, c->stream>>>(
+            a, nkp, c->kpts.as<int>(), c->win_lo.as<int>(), c->win_n.as<int>(),
+            c->counts.as<int64_t>(), c->mask_words ? c->sieve_mask.as<uint32_t>() : nullptr,
+            c->mask_words);
         EPWI_CHECK_LAUNCH();
     }
     int64_t np = 0;
@@ -304,6 +359,13 @@ void sieve_count(epwi_ctx *c) {
 
 void sieve_fill_chunk(epwi_ctx *c, int64_t kp0, int64_t kp1, int *pairs) {
     if (kp1 <= kp0) return;
+    if (c->mask_words) {
+        k_sieve_fill_mask<<<(unsigned)(kp1 - kp0), 256, 0, c->stream>>>(
+            make_grid_info(c), kp0, c->sieve_mask.as<uint32_t>(), c->mask_words, kSieveBlock,
+            c->kp_pairs.as<int64_t>(), pairs);
+        EPWI_CHECK_LAUNCH();
+        return;
+    }
     SieveArgs a = make_sieve_args(c);
     k_sieve_fill<<<(unsigned)(kp1 - kp0), 256, 0, c->stream>>>(
         a, kp0, c->kpts.as<int>(), c->win_lo.as<int>(), c->win_n.as<int>(),
