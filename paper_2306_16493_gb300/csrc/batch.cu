@@ -35,7 +35,7 @@ constexpr int kBT = 256;          // threads of the persistent kernel
 constexpr int kAcc = 32;          // complex accumulators per thread (Rp->q stage)
 constexpr int kMaxMt = 512;       // pairs per item, upper bound
 constexpr int kNmB = 18;          // modes, upper bound
-constexpr size_t kSmemCap = 200 * 1024;
+constexpr size_t kSmemCap = 100 * 1024;   // two CTAs per SM (228 KB per SM)
 
 struct BSys {
     GridInfo g;
@@ -157,7 +157,7 @@ __device__ __forceinline__ void cp_async_wait_group() {
 }
 
 // The persistent kernel: CTAs take queue items until the queue is empty.
-__global__ void __launch_bounds__(kBT, 1) k_batch_scatter(const BSys *__restrict__ systems,
+__global__ void __launch_bounds__(kBT, 2) k_batch_scatter(const BSys *__restrict__ systems,
                                                          const BItem *__restrict__ items,
                                                          const int *__restrict__ order,
                                                          int nitems, int *__restrict__ counter,
@@ -647,8 +647,9 @@ float time_tile(epwi_batch *b, int s, int Mt, int KC, int64_t sample, int64_t *p
 std::pair<int, int> default_tile(int NW) {
     static const int mts[] = {128, 64, 32, 16, 8, 4, 2, 1};
     for (int mt : mts)
-        if (tile_ok(mt, 32, NW)) return {mt, 32};
-    return {1, 16};
+        for (int kc : {32, 16, 8, 4})
+            if (tile_ok(mt, kc, NW)) return {mt, kc};
+    return {1, 4};
 }
 
 std::pair<int, int> autotune(epwi_batch *b, int s, int &src) {
@@ -662,8 +663,8 @@ std::pair<int, int> autotune(epwi_batch *b, int s, int &src) {
     const int NW = c->nw * c->nm;
     std::pair<int, int> best = default_tile(NW);
     double best_t = 1e300;
-    for (int mt : {16, 32, 64, 128, 256}) {
-        for (int kc : {16, 32}) {
+    for (int mt : {8, 16, 32, 64, 128, 256}) {
+        for (int kc : {8, 16, 32}) {
             if (!tile_ok(mt, kc, NW)) continue;
             int64_t pairs = 0;
             const float ms = time_tile(b, s, mt, kc, 1024, &pairs);

@@ -126,6 +126,152 @@ __global__ void __launch_bounds__(128) k_eig_ph(GridInfo g, int64_t nq, int Nm, 
     hwmax32[iq] = wmax;
 }
 
+// Warp-per-matrix variants for large matrices (W >= 16, Nm >= 12): the matrix lives in
+// shared memory (row stride n + 1), lane r builds row r of the Fourier sum, and the
+// warp-parallel Jacobi diagonalises it.  Outputs are those of the one-thread kernels.
+constexpr int kWarpsPerBlock = 4;
+
+struct WarpScratch {
+    double2 *A, *V;
+    double *w;
+    int *perm;
+    JRot *rot;
+};
+
+__device__ inline WarpScratch warp_scratch(uint8_t *base, int n) {
+    const int ld = n + 1;
+    const size_t per = sizeof(double2) * 2 * n * ld + sizeof(double) * 32 + sizeof(int) * 32 +
+                       sizeof(JRot) * 16;
+    uint8_t *b = base + (threadIdx.x >> 5) * ((per + 15) & ~size_t(15));
+    WarpScratch ws;
+    ws.A = reinterpret_cast<double2 *>(b);
+    ws.V = ws.A + n * ld;
+    ws.w = reinterpret_cast<double *>(ws.V + n * ld);
+    ws.perm = reinterpret_cast<int *>(ws.w + 32);
+    ws.rot = reinterpret_cast<JRot *>(ws.perm + 32);
+    return ws;
+}
+
+size_t warp_scratch_bytes(int n) {
+    const size_t per = sizeof(double2) * 2 * n * (n + 1) + sizeof(double) * 32 + sizeof(int) * 32 +
+                       sizeof(JRot) * 16;
+    return kWarpsPerBlock * ((per + 15) & ~size_t(15));
+}
+
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) k_eig_el_warp(
+    GridInfo g, int64_t nk, int W, int nR, const int *__restrict__ R, const double *__restrict__ Rcart,
+    const double2 *__restrict__ Hw, const double2 *__restrict__ ph, double *__restrict__ eps,
+    float *__restrict__ eps32, double2 *__restrict__ Vout, float2 *__restrict__ V32,
+    double *__restrict__ vel, int *__restrict__ flag) {
+    extern __shared__ __align__(16) uint8_t wsm[];
+    const int lane = threadIdx.x & 31;
+    const int64_t ik = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (ik >= nk) return;                      // whole warps leave together
+    WarpScratch S = warp_scratch(wsm, W);
+    const int ld = W + 1;
+    int i1, i2, i3;
+    grid_coords(g, ik, i1, i2, i3);
+    const int a1 = (int)((int64_t)i1 * g.s1 % g.L), a2 = (int)((int64_t)i2 * g.s2 % g.L),
+              a3 = (int)((int64_t)i3 * g.s3 % g.L);
+    if (lane < W) {
+        for (int j = 0; j < W; ++j) S.A[lane * ld + j] = make_double2(0, 0);
+        for (int r = 0; r < nR; ++r) {
+            const double2 p = ph[phase_index(a1, a2, a3, R[3 * r], R[3 * r + 1], R[3 * r + 2], g.L)];
+            const double2 *h = Hw + (size_t)r * W * W + lane * W;
+            for (int j = 0; j < W; ++j) S.A[lane * ld + j] = cfma(p, h[j], S.A[lane * ld + j]);
+        }
+    }
+    __syncwarp();
+    const int ok = jacobi_hermitian_warp(S.A, S.V, W, ld, S.w, S.rot, S.perm);
+    if (lane == 0 && !ok) atomicAdd(flag, 1);
+    if (lane < W) {
+        eps[ik * W + lane] = S.w[lane];
+        eps32[ik * W + lane] = (float)S.w[lane];
+        for (int n = 0; n < W; ++n) {
+            const double2 v = S.V[lane * ld + n];
+            Vout[ik * W * W + lane * W + n] = v;
+            V32[ik * W * W + lane * W + n] = make_float2((float)v.x, (float)v.y);
+        }
+    }
+    // v_n,a = (1/hbar) Re[V^dag (sum_R w_R i R_a e^{ik.R} H(R)) V]_nn, one axis at a time;
+    // the derivative matrix reuses A (lane = row), then lane n contracts column n
+    for (int ax = 0; ax < 3; ++ax) {
+        __syncwarp();
+        if (lane < W) {
+            for (int j = 0; j < W; ++j) S.A[lane * ld + j] = make_double2(0, 0);
+            for (int r = 0; r < nR; ++r) {
+                const double2 p = ph[phase_index(a1, a2, a3, R[3 * r], R[3 * r + 1], R[3 * r + 2], g.L)];
+                const double ra = Rcart[3 * r + ax];
+                const double2 ip = make_double2(-ra * p.y, ra * p.x);
+                const double2 *h = Hw + (size_t)r * W * W + lane * W;
+                for (int j = 0; j < W; ++j) S.A[lane * ld + j] = cfma(ip, h[j], S.A[lane * ld + j]);
+            }
+        }
+        __syncwarp();
+        if (lane < W) {
+            const int n = lane;
+            double acc = 0;
+            for (int i = 0; i < W; ++i) {
+                double2 t = make_double2(0, 0);
+                for (int j = 0; j < W; ++j) t = cfma(S.A[i * ld + j], S.V[j * ld + n], t);
+                acc += S.V[i * ld + n].x * t.x + S.V[i * ld + n].y * t.y;
+            }
+            vel[(ik * W + n) * 3 + ax] = acc / epc::kHbarEVs * 1e-10;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) k_eig_ph_warp(
+    GridInfo g, int64_t nq, int Nm, int nR, const int *__restrict__ R, const double *__restrict__ Phiw,
+    const double *__restrict__ mode_mass, const double2 *__restrict__ ph, double omega_min,
+    double *__restrict__ hw, float *__restrict__ hwmax32, float *__restrict__ hw32,
+    double2 *__restrict__ uout, float2 *__restrict__ u32, int *__restrict__ flag) {
+    extern __shared__ __align__(16) uint8_t wsm[];
+    const int lane = threadIdx.x & 31;
+    const int64_t iq = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (iq >= nq) return;
+    WarpScratch S = warp_scratch(wsm, Nm);
+    const int ld = Nm + 1;
+    int i1, i2, i3;
+    grid_coords(g, iq, i1, i2, i3);
+    const int a1 = (int)((int64_t)i1 * g.s1 % g.L), a2 = (int)((int64_t)i2 * g.s2 % g.L),
+              a3 = (int)((int64_t)i3 * g.s3 % g.L);
+    if (lane < Nm) {
+        for (int j = 0; j < Nm; ++j) S.A[lane * ld + j] = make_double2(0, 0);
+        for (int r = 0; r < nR; ++r) {
+            const double2 p = ph[phase_index(a1, a2, a3, R[3 * r], R[3 * r + 1], R[3 * r + 2], g.L)];
+            const double *f = Phiw + (size_t)r * Nm * Nm + lane * Nm;
+            for (int j = 0; j < Nm; ++j) {
+                S.A[lane * ld + j].x = fma(p.x, f[j], S.A[lane * ld + j].x);
+                S.A[lane * ld + j].y = fma(p.y, f[j], S.A[lane * ld + j].y);
+            }
+        }
+    }
+    __syncwarp();
+    const int ok = jacobi_hermitian_warp(S.A, S.V, Nm, ld, S.w, S.rot, S.perm);
+    if (lane == 0 && !ok) atomicAdd(flag, 1);
+    // lane = mode nu
+    float wmax = -1.f;
+    if (lane < Nm) {
+        const int nu = lane;
+        const double l = S.w[nu];
+        const double w = (l >= 0 ? 1.0 : -1.0) * sqrt(fabs(l) * epc::kHbar2AmuA2);
+        hw[iq * Nm + nu] = w;
+        const bool keep = w >= omega_min;
+        hw32[iq * Nm + nu] = keep ? (float)w : -1.0f;
+        if (keep) wmax = (float)w;
+        for (int m = 0; m < Nm; ++m) {
+            const double amp = keep ? sqrt(epc::kHbar2AmuA2 / (2.0 * mode_mass[m] * w)) : 0.0;
+            const double2 e = S.V[m * ld + nu];
+            const double2 v = make_double2(e.x * amp, e.y * amp);
+            uout[iq * Nm * Nm + m * Nm + nu] = v;
+            u32[iq * Nm * Nm + m * Nm + nu] = make_float2((float)v.x, (float)v.y);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) wmax = fmaxf(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+    if (lane == 0) hwmax32[iq] = wmax;
+}
+
 }  // namespace
 
 GridInfo make_grid_info(const epwi_ctx *c) {
@@ -146,6 +292,17 @@ void launch_phase_tables(epwi_ctx *c) {
     k_phase_tables<<<(c->L + 127) / 128, 128, 0, c->stream>>>(c->L, c->ph64.as<double2>(),
                                                                c->ph32.as<float2>());
     EPWI_CHECK_LAUNCH();
+}
+
+// Raises a kernel's dynamic shared-memory limit the first time a larger size is needed
+// (the first launch of each size happens outside any stream capture).
+template <class K>
+void set_smem_once(K kern, size_t bytes) {
+    static size_t set = 48 * 1024;
+    if (bytes > set) {
+        EPWI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+        set = bytes;
+    }
 }
 
 void launch_eigs(epwi_ctx *c) {
@@ -170,11 +327,15 @@ void launch_eigs(epwi_ctx *c) {
     g, nk, W, c->nRe, c->Re.as<int>(), c->Rcart.as<double>(), c->Hw.as<double2>(),            \
         c->ph64.as<double2>(), c->eps.as<double>(), c->eps32.as<float>(), c->V.as<double2>(), \
         c->V32.as<float2>(), c->vel.as<double>(), c->eig_flag.as<int>()
+    const unsigned nbw = (unsigned)((nk + kWarpsPerBlock - 1) / kWarpsPerBlock);
     if (W <= 1) k_eig_el<1><<<nb, bs, 0, c->stream>>>(EL_ARGS);
     else if (W <= 4) k_eig_el<4><<<nb, bs, 0, c->stream>>>(EL_ARGS);
     else if (W <= 8) k_eig_el<8><<<nb, bs, 0, c->stream>>>(EL_ARGS);
-    else if (W <= 16) k_eig_el<16><<<nb, bs, 0, c->stream>>>(EL_ARGS);
-    else k_eig_el<24><<<nb, bs, 0, c->stream>>>(EL_ARGS);
+    else {
+        const size_t sm = warp_scratch_bytes(W);
+        set_smem_once(k_eig_el_warp, sm);
+        k_eig_el_warp<<<nbw, 32 * kWarpsPerBlock, sm, c->stream>>>(EL_ARGS);
+    }
 #undef EL_ARGS
     EPWI_CHECK_LAUNCH();
 #define PH_ARGS                                                                             \
@@ -184,8 +345,11 @@ void launch_eigs(epwi_ctx *c) {
         c->u.as<double2>(), c->u32.as<float2>(), c->eig_flag.as<int>() + 1
     if (Nm <= 3) k_eig_ph<3><<<nb, bs, 0, c->stream>>>(PH_ARGS);
     else if (Nm <= 6) k_eig_ph<6><<<nb, bs, 0, c->stream>>>(PH_ARGS);
-    else if (Nm <= 12) k_eig_ph<12><<<nb, bs, 0, c->stream>>>(PH_ARGS);
-    else k_eig_ph<18><<<nb, bs, 0, c->stream>>>(PH_ARGS);
+    else {
+        const size_t sm = warp_scratch_bytes(Nm);
+        set_smem_once(k_eig_ph_warp, sm);
+        k_eig_ph_warp<<<nbw, 32 * kWarpsPerBlock, sm, c->stream>>>(PH_ARGS);
+    }
 #undef PH_ARGS
     EPWI_CHECK_LAUNCH();
 }

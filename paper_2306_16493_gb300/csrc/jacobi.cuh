@@ -94,3 +94,163 @@ __host__ __device__ inline int jacobi_hermitian(double2 (&A)[NMAX * NMAX], doubl
     }
     return converged;
 }
+
+// Warp-parallel variant for n <= 32 (one warp per matrix, matrices in shared memory with
+// row stride ld = n + 1).  The same rotation and stopping rule as jacobi_hermitian, applied in
+// the parallel (round-robin) ordering: in each of the n' - 1 rounds of a sweep (n' = n rounded
+// up to even), the n'/2 disjoint index pairs are rotated at once.  Disjoint rotations commute,
+// and each pair's 2x2 block depends on its own rotation only, so every round zeroes its
+// pairs' off-diagonal elements exactly as the sequential sweep does.  Lane r updates row r of
+// A and V for the column rotations; lane c updates column c of A for the row rotations.
+// Returns 1 on convergence; w receives the eigenvalues in ascending order (lane 0 sorts) and
+// V's columns are permuted alike.  All lanes of the warp must call it.
+struct JRot {
+    int p, q;
+    double c, s, ex, ey, app, aqq, tm;
+};
+
+__device__ inline int jacobi_hermitian_warp(double2 *A, double2 *V, int n, int ld, double *w,
+                                            JRot *rot, int *perm) {
+    const int lane = threadIdx.x & 31;
+    for (int j = 0; j < n; ++j)
+        if (lane < n) V[lane * ld + j] = make_double2(lane == j ? 1.0 : 0.0, 0.0);
+    __syncwarp();
+    const int np = (n + 1) & ~1;          // players of the round robin (one dummy if n is odd)
+    int converged = 0;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0, tot = 0;
+        if (lane < n)
+            for (int j = 0; j < n; ++j) {
+                const double2 a = A[lane * ld + j];
+                const double m2 = a.x * a.x + a.y * a.y;
+                tot += m2;
+                if (j != lane) off += m2;
+            }
+        for (int o = 16; o > 0; o >>= 1) {
+            off += __shfl_xor_sync(0xffffffffu, off, o);
+            tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        }
+        if (off <= 1e-30 * tot || off == 0.0) {
+            converged = 1;
+            break;
+        }
+        for (int r = 0; r < np - 1; ++r) {
+            // pair lane: (np-1, r) for lane 0, ((r+k) mod (np-1), (r-k) mod (np-1)) for lane k
+            if (lane < np / 2) {
+                int p, q;
+                if (lane == 0) {
+                    p = np - 1;
+                    q = r;
+                } else {
+                    p = (r + lane) % (np - 1);
+                    q = (r - lane + (np - 1)) % (np - 1);
+                }
+                if (p > q) {
+                    const int t = p;
+                    p = q;
+                    q = t;
+                }
+                JRot R;
+                R.p = p;
+                R.q = q;
+                R.c = 1.0;
+                R.s = 0.0;
+                R.ex = 1.0;
+                R.ey = 0.0;
+                R.tm = 0.0;
+                R.app = R.aqq = 0.0;
+                if (q < n) {                        // a pair with the dummy does nothing
+                    const double2 apq = A[p * ld + q];
+                    const double mag = sqrt(apq.x * apq.x + apq.y * apq.y);
+                    R.app = A[p * ld + p].x;
+                    R.aqq = A[q * ld + q].x;
+                    if (mag != 0.0) {
+                        const double zeta = (R.aqq - R.app) / (2.0 * mag);
+                        double t;
+                        if (fabs(zeta) > 1e150) t = 0.5 / zeta;
+                        else t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                        R.c = 1.0 / sqrt(1.0 + t * t);
+                        R.s = t * R.c;
+                        R.ex = apq.x / mag;
+                        R.ey = apq.y / mag;
+                        R.tm = t * mag;
+                    } else {
+                        R.q = n;                    // nothing to rotate
+                    }
+                } else {
+                    R.q = n;
+                }
+                rot[lane] = R;
+            }
+            __syncwarp();
+            // columns: A <- A U, V <- V U (lane = row)
+            if (lane < n)
+                for (int k = 0; k < np / 2; ++k) {
+                    const JRot R = rot[k];
+                    if (R.q >= n) continue;
+                    const double sx = R.s * R.ex, sy = R.s * R.ey;   // s e^{i phi}
+                    const double2 ap = A[lane * ld + R.p], aq = A[lane * ld + R.q];
+                    A[lane * ld + R.p] = make_double2(R.c * ap.x - (sx * aq.x + sy * aq.y),
+                                                      R.c * ap.y - (sx * aq.y - sy * aq.x));
+                    A[lane * ld + R.q] = make_double2(sx * ap.x - sy * ap.y + R.c * aq.x,
+                                                      sx * ap.y + sy * ap.x + R.c * aq.y);
+                    const double2 vp = V[lane * ld + R.p], vq = V[lane * ld + R.q];
+                    V[lane * ld + R.p] = make_double2(R.c * vp.x - (sx * vq.x + sy * vq.y),
+                                                      R.c * vp.y - (sx * vq.y - sy * vq.x));
+                    V[lane * ld + R.q] = make_double2(sx * vp.x - sy * vp.y + R.c * vq.x,
+                                                      sx * vp.y + sy * vp.x + R.c * vq.y);
+                }
+            __syncwarp();
+            // rows: A <- U^dag A (lane = column)
+            if (lane < n)
+                for (int k = 0; k < np / 2; ++k) {
+                    const JRot R = rot[k];
+                    if (R.q >= n) continue;
+                    const double sx = R.s * R.ex, sy = R.s * R.ey;
+                    const double2 bp = A[R.p * ld + lane], bq = A[R.q * ld + lane];
+                    A[R.p * ld + lane] = make_double2(R.c * bp.x - (sx * bq.x - sy * bq.y),
+                                                      R.c * bp.y - (sx * bq.y + sy * bq.x));
+                    A[R.q * ld + lane] = make_double2(sx * bp.x + sy * bp.y + R.c * bq.x,
+                                                      sx * bp.y - sy * bp.x + R.c * bq.y);
+                }
+            __syncwarp();
+            if (lane < np / 2) {
+                const JRot R = rot[lane];
+                if (R.q < n) {
+                    A[R.p * ld + R.q] = make_double2(0, 0);
+                    A[R.q * ld + R.p] = make_double2(0, 0);
+                    A[R.p * ld + R.p] = make_double2(R.app - R.tm, 0);
+                    A[R.q * ld + R.q] = make_double2(R.aqq + R.tm, 0);
+                }
+            }
+            __syncwarp();
+        }
+    }
+    if (lane == 0) {
+        for (int i = 0; i < n; ++i) {
+            w[i] = A[i * ld + i].x;
+            perm[i] = i;
+        }
+        for (int i = 0; i < n - 1; ++i) {      // selection sort, ascending
+            int k = i;
+            for (int j = i + 1; j < n; ++j)
+                if (w[j] < w[k]) k = j;
+            if (k != i) {
+                const double tw = w[i];
+                w[i] = w[k];
+                w[k] = tw;
+                const int tp = perm[i];
+                perm[i] = perm[k];
+                perm[k] = tp;
+            }
+        }
+    }
+    __syncwarp();
+    // permute the columns of V (lane = row), through A's row as scratch
+    if (lane < n) {
+        for (int j = 0; j < n; ++j) A[lane * ld + j] = V[lane * ld + perm[j]];
+        for (int j = 0; j < n; ++j) V[lane * ld + j] = A[lane * ld + j];
+    }
+    __syncwarp();
+    return converged;
+}

@@ -36,7 +36,9 @@ def _proj_err(Va, Vb, ea, tol=1e-6):
 
 
 @pytest.mark.parametrize("make,N", [(synth.tiny_system, 8), (synth.al_like_system, 10),
-                                    (synth.si_like_system, 6)])
+                                    (synth.si_like_system, 6),
+                                    (lambda: synth.batch_system(10)[0], 5),    # nw 16, 12 modes
+                                    (lambda: synth.batch_system(15)[0], 5)])   # nw 24, 18 modes
 def test_eigs_parity(epwi, make, N):
     s = make()
     ctx = epwi.Context()
@@ -61,6 +63,22 @@ def test_eigs_parity(epwi, make, N):
                      gr.u / np.maximum(np.linalg.norm(gr.u, axis=1, keepdims=True), 1e-300),
                      np.where(keep, gr.hw, -1e3 * np.arange(gr.hw.shape[1]))) < 1e-9
     ctx.close()
+
+
+def test_large_matrices_rates_parity(epwi):
+    """nw = 24 and 18 modes (the warp-per-matrix eigensolver and the generic FP64 kernels):
+    1/tau and sigma vs the oracle at 1e-10 on a non-cubic grid."""
+    s = synth.batch_system(15)[0]
+    grid = (3, 4, 5)
+    gr = O.Grids(s, grid)
+    mu = gr.band_centre()
+    T, eta = 300.0, 0.05
+    out = gpu_run(s, grid, T, mu, eta, mu - 1.0, mu + 1.0)
+    ora = oracle_run(gr, T, mu, eta, mu - 1.0, mu + 1.0)
+    err, n = compare_rates(out, ora, gr.eps, TOL)
+    assert n > 0 and err < TOL, err
+    assert rel_frob(out["sigma"], ora["sigma"]) < TOL
+    out["ctx"].close()
 
 
 def test_tb_dp_closed_form_through_gpu(epwi):
