@@ -87,7 +87,7 @@ def test_batch_tile_shapes_agree(epwi, batch_setup):
     """Two forced tile shapes per system give the same rates up to FP32 summation order."""
     b, systems, grids, grs, mu = batch_setup
     out = []
-    for mt, kc in ((8, 8), (16, 16)):
+    for mt, kc in ((8, 8), (4, 4)):
         for s in range(len(systems)):
             b.set_tile(s, mt, kc)
         b.plan(T, mu, ETA, mu - 1.0, mu + 1.0, autotune=False)
