@@ -307,7 +307,8 @@ epwi_status epwi_mlp_get_training_set(epwi_ctx *ctx, int64_t capacity, int32_t *
  *     the network scores every cell centre and mode, and
  *       p_n(q) = alpha/N_q + (1 - alpha) P_n(cell(q)) / cell_stride^3, with 0 < alpha <= 1.
  *     The bands of one k share one draw from the band mixture.
- * The weighted pairs run through the FP64 kernels whatever the context precision.  The result
+ * The weighted pairs run through the kernels of the context's precision (FP64, or a split
+ * tensor-core mode with the weight applied per pair in FP32).  The result
  * replaces the rates of epwi_scatter_rates: epwi_get_rates, epwi_conductivity and
  * epwi_get_stats (n_pairs = distinct drawn pairs) read it.  Errors: ESTATE, EINVAL. */
 epwi_status epwi_scatter_rates_is(epwi_ctx *ctx, double T_K, double mu_eV, double smear_eV,

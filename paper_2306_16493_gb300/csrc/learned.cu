@@ -4,8 +4,8 @@
 // estimate of that q sum is built instead: S grid points q_s are drawn per k from a proposal
 // p(q) > 0, and sum_q t(q) is estimated by (1/S) sum_s t(q_s) / p(q_s).  Repeated draws are
 // merged, so a distinct q drawn c times gets the weight c / (S p(q)).  The weighted pairs then
-// go through the plain FP64 interpolation and SERTA kernels.  The estimate is unbiased for
-// any p that is positive wherever t is.
+// go through the plain interpolation and SERTA kernels of the context's precision.  The
+// estimate is unbiased for any p that is positive wherever t is.
 //
 // Two proposals are available.
 //  * uniform: p = 1 / N_q.
@@ -549,7 +549,6 @@ void mlp_train(epwi_ctx *c, double T, double mu, double eta, double emin, double
 void run_is(epwi_ctx *c, double T, double mu, double eta, double emin, double emax,
             int64_t S, double alpha, int stride, int proposal, uint64_t seed) {
     set_transport_params(c, T, mu, eta, emin, emax);
-    PrecisionGuard pg(c);
     cudaStream_t st = c->stream;
     cudaEvent_t e0, e1, e2;
     EPWI_CUDA(cudaEventCreate(&e0));
@@ -703,7 +702,7 @@ void run_is(epwi_ctx *c, double T, double mu, double eta, double emin, double em
         if (c->nstates > 0)
             EPWI_CUDA(cudaMemsetAsync(c->inv_tau.p, 0, sizeof(double) * c->nstates, st));
         std::memset(&c->stats, 0, sizeof(c->stats));
-        c->stats.precision = EPWI_FP64;
+        c->stats.precision = c->opt.precision;
         c->stats.ms_eigs = c->ms_eigs;
         EPWI_CUDA(cudaDeviceGetAttribute(&c->stats.sm_count, cudaDevAttrMultiProcessorCount, c->device));
         WorkSet ws;

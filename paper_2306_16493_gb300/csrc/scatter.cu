@@ -257,8 +257,7 @@ void process_workset(epwi_ctx *c, const WorkSet &ws, double *g2out, double *tout
     const int W = c->nw, Nm = c->nm;
     const int64_t nrow = (int64_t)c->nRp * Nm * W;
     const bool tc = c->opt.precision != EPWI_FP64;
-    EPWI_REQUIRE(!tc || (!tout && !ws.pair_w), EPWI_EINVAL,
-                 "pair weights and per-pair terms need the FP64 path");
+    EPWI_REQUIRE(!tc || !tout, EPWI_EINVAL, "per-pair terms need the FP64 path");
     // chunk limits: pairs and Re->k output size
     const int64_t max_pairs = int64_t(1) << 27;
     const size_t state_bytes = tc ? tc_state_bytes(c) : sizeof(double2) * nrow;

@@ -765,6 +765,7 @@ __global__ void __maxnreg__(168) k_scatter_tc(TcArgs a) {
                                 rate = fmaf(g2, tt, rate);
                             }
                         }
+                        if (s.pair_w) rate *= (float)s.pair_w[pair];   // importance-sampling weight
                     }
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) rate += __shfl_down_sync(0xffffffffu, rate, o);

@@ -214,3 +214,24 @@ def test_learned_proposal_gain_si_like(epwi):
     print(f"training loss {loss:.3f}; rms relative error uniform {err['uniform']:.3e} "
           f"learned {err['learned']:.3e}; gain {gain:.1f}x (variance {gain ** 2:.0f}x)")
     assert gain >= 4.0, err
+
+
+def test_is_split_precision_matches_fp64(epwi):
+    """The same draws evaluated by the fp16x3 tensor-core kernels (weights applied per pair in
+    FP32) agree with the FP64 evaluation within the mixed-precision bound (1e-4)."""
+    sysm, ctx, gr = _tiny_ctx(epwi, grid=8)
+    T, eta = 300.0, 0.05
+    mu = gr.band_centre()
+    out = {}
+    for prec in ("fp64", "fp16x3"):
+        ctx.set_precision(prec)
+        ctx.scatter_rates_is(T, mu, eta, mu - 0.3, mu + 0.3, 400, proposal="uniform", seed=21)
+        out[prec] = (epwi.epwi_get_is_pairs(ctx.h), ctx.rates())
+    (ik0, iq0, w0), (k0, b0, r0) = out["fp64"]
+    (ik1, iq1, w1), (k1, b1, r1) = out["fp16x3"]
+    assert np.array_equal(iq0, iq1) and np.array_equal(w0, w1)
+    gs0 = group_sums(k0.astype(int), b0.astype(int), r0, gr.eps)
+    gs1 = group_sums(k1.astype(int), b1.astype(int), r1, gr.eps)
+    scale = max(abs(v) for v in gs0.values())
+    worst = max(abs(gs1[k] - v) / max(abs(v), 1e-6 * scale) for k, v in gs0.items())
+    assert worst <= 1e-4, worst
