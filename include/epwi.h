@@ -286,6 +286,10 @@ epwi_status epwi_mlp_set_params(epwi_ctx *ctx, const float *params);
 epwi_status epwi_mlp_get_params(epwi_ctx *ctx, float *params, double *scale, double *shift);
 /* Network output yhat for n host samples x [n][9] -> y [n] (reference SIMT kernels). */
 epwi_status epwi_mlp_forward(epwi_ctx *ctx, int64_t n, const float *x, float *y);
+/* The same on the tensor cores, as the proposal uses it: layer 1 in FP32, layers 2-3 as BF16
+ * tcgen05 products with FP32 accumulation, activations rounded to BF16 between layers.
+ * Errors: ESTATE, EINVAL, ETIMEOUT (a bounded wait in the kernel gave up). */
+epwi_status epwi_mlp_forward_tc(epwi_ctx *ctx, int64_t n, const float *x, float *y);
 /* One forward and backward pass over n <= 65536 host samples: loss = (1/2n) sum (yhat - y)^2,
  * grad [EPWI_MLP_NPARAM] = dloss/dparams (host), with respect to the BF16-rounded parameters. */
 epwi_status epwi_mlp_loss_grad(epwi_ctx *ctx, int64_t n, const float *x, const float *y,

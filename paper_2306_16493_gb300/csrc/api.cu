@@ -664,6 +664,29 @@ epwi_status epwi_mlp_forward(epwi_ctx *c, int64_t n, const float *x, float *y) {
     });
 }
 
+epwi_status epwi_mlp_forward_tc(epwi_ctx *c, int64_t n, const float *x, float *y) {
+    return guard(c, [&] {
+        EPWI_REQUIRE(c->mlp && c->mlp->ready, EPWI_ESTATE, "the network has no parameters yet");
+        EPWI_REQUIRE(n >= 0 && (n == 0 || (x && y)), EPWI_EINVAL, "bad argument");
+        if (n == 0) return;
+        DevBuf dx, dy;
+        try {
+            upload(dx, x, (size_t)n * mlp::kIn, c->stream);
+            dy.ensure(sizeof(float) * n);
+            mlp_forward_fast(c, n, dx.as<float>(), dy.as<float>());
+            EPWI_CUDA(cudaMemcpyAsync(y, dy.p, sizeof(float) * n, cudaMemcpyDeviceToHost, c->stream));
+            EPWI_CUDA(cudaStreamSynchronize(c->stream));
+        } catch (...) {
+            cudaStreamSynchronize(c->stream);
+            dx.release();
+            dy.release();
+            throw;
+        }
+        dx.release();
+        dy.release();
+    });
+}
+
 epwi_status epwi_mlp_loss_grad(epwi_ctx *c, int64_t n, const float *x, const float *y,
                                double *loss, float *grad) {
     return guard(c, [&] {

@@ -581,7 +581,7 @@ void run_is(epwi_ctx *c, double T, double mu, double eta, double emin, double em
         for (auto &b : chunk_w) b.release();
     };
     try {
-        const int64_t rows_per_batch = (kMaxBatch / c->nm) * c->nm;
+        const int64_t rows_per_batch = (((int64_t)1 << 22) / c->nm) * c->nm;
         for (int64_t kp0 = 0; kp0 < nkp; kp0 += kpc) {
             const int64_t kp1 = std::min(nkp, kp0 + kpc), nkc = kp1 - kp0;
             const int64_t s0 = h_state[kp0], nsc = h_state[kp1] - s0;
@@ -631,7 +631,7 @@ void run_is(epwi_ctx *c, double T, double mu, double eta, double emin, double em
                     k_prop_features<<<(unsigned)((nr + 255) / 256), 256, 0, st>>>(pa, s0, r0, nr,
                                                                                    xb.as<float>());
                     EPWI_CHECK_LAUNCH();
-                    mlp_forward(c, nr, xb.as<float>(), yb.as<float>());
+                    mlp_forward_fast(c, nr, xb.as<float>(), yb.as<float>());
                     const int64_t ng = nr / c->nm;
                     k_prop_lse<<<(unsigned)((ng + 255) / 256), 256, 0, st>>>(
                         ng, c->nm, (float)c->mlp->out_scale, yb.as<float>(),

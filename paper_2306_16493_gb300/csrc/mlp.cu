@@ -501,3 +501,14 @@ double mlp_dataset_loss(epwi_ctx *c) {
     }
     return 0.5 * t / (double)n;
 }
+
+void mlp_forward_fast(epwi_ctx *c, int64_t n, const float *X, float *y) {
+    MlpState &s = state(c);
+    s.err.ensure(sizeof(int));
+    EPWI_CUDA(cudaMemsetAsync(s.err.p, 0, sizeof(int), c->stream));
+    mlp_forward_tc(c, n, X, y, s.err.as<int>());
+    int h = 0;
+    EPWI_CUDA(cudaMemcpyAsync(&h, s.err.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    EPWI_CUDA(cudaStreamSynchronize(c->stream));
+    EPWI_REQUIRE(h == 0, EPWI_ETIMEOUT, "tensor-core inference: a bounded mbarrier wait timed out");
+}

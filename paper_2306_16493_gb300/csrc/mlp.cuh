@@ -41,9 +41,10 @@ struct MlpState {
     DevBuf T64;                       // double [n] raw targets
     DevBuf ids;                       // int4 [n] {ik, iq, band, mode}
     DevBuf bx, by;                    // batch gather
+    DevBuf err;                       // int: timed-out waits of the tensor-core inference
     void release() {
         DevBuf *all[] = {&master, &w, &wbf, &m, &v, &grad, &part, &act, &lossbuf,
-                         &X, &Y, &T64, &ids, &bx, &by};
+                         &X, &Y, &T64, &ids, &bx, &by, &err};
         for (DevBuf *b : all) b->release();
         ready = false;
     }
@@ -58,6 +59,10 @@ double mlp_loss_grad(epwi_ctx *c, int64_t n, const float *X, const float *Y,
 void mlp_adam(epwi_ctx *c, double lr);
 void mlp_gather(epwi_ctx *c, int64_t n, int64_t i0, int64_t bsz, uint64_t a, uint64_t b);
 double mlp_dataset_loss(epwi_ctx *c);
+// mlp_tc.cu: the same forward pass on the tensor cores (BF16 activations between layers)
+int mlp_forward_tc(epwi_ctx *c, int64_t n, const float *X, float *y, int *err_dev);
+// tensor-core forward with its error check (throws EPWI_ETIMEOUT)
+void mlp_forward_fast(epwi_ctx *c, int64_t n, const float *X, float *y);
 
 // learned.cu
 void mlp_train(epwi_ctx *c, double T, double mu, double eta, double emin, double emax,

@@ -109,6 +109,7 @@ def _load() -> C.CDLL:
         "epwi_mlp_set_params": (I32, [P, P]),
         "epwi_mlp_get_params": (I32, [P, P, P, P]),
         "epwi_mlp_forward": (I32, [P, I64, P, P]),
+        "epwi_mlp_forward_tc": (I32, [P, I64, P, P]),
         "epwi_mlp_loss_grad": (I32, [P, I64, P, P, P, P]),
         "epwi_mlp_get_training_set": (I32, [P, I64, P, P, P, P, P]),
         "epwi_scatter_rates_is": (I32, [P, D, D, D, D, D, I64, D, I32, I32, C.c_uint64, P, P]),
@@ -339,6 +340,13 @@ def epwi_mlp_forward(ctx, x):
     x = np.ascontiguousarray(x, np.float32).reshape(-1, 9)
     y = np.empty(len(x), np.float32)
     _check(ctx, _lib.epwi_mlp_forward(ctx, len(x), _ptr(x), _ptr(y)))
+    return y
+
+
+def epwi_mlp_forward_tc(ctx, x):
+    x = np.ascontiguousarray(x, np.float32).reshape(-1, 9)
+    y = np.empty(len(x), np.float32)
+    _check(ctx, _lib.epwi_mlp_forward_tc(ctx, len(x), _ptr(x), _ptr(y)))
     return y
 
 

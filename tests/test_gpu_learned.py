@@ -56,6 +56,27 @@ def test_mlp_forward_and_gradient_vs_oracle(epwi, n):
         o += k
 
 
+@pytest.mark.parametrize("n", [1, 129, 100000])
+def test_mlp_tensor_core_forward(epwi, n):
+    """tcgen05 inference (BF16 activations between layers, FP32 accumulation) vs the FP64
+    forward on the same BF16 weights: rms error <= 2e-2 of the rms output (BF16 rounding of
+    128-wide activations, ~2^-9 relative per layer), and vs the FP32 SIMT forward likewise."""
+    ctx = epwi.Context()
+    epwi.epwi_mlp_set_params(ctx.h, _random_params(11, scale=0.15))
+    w, _, _ = epwi.epwi_mlp_get_params(ctx.h)
+    rng = np.random.default_rng(n)
+    X = rng.uniform(-1, 1, (n, 9)).astype(np.float32)
+    y_ref, _ = M.forward(w.astype(np.float64), X)
+    y_tc = epwi.epwi_mlp_forward_tc(ctx.h, X).astype(np.float64)
+    y_simt = epwi.epwi_mlp_forward(ctx.h, X).astype(np.float64)
+    scale = np.sqrt(np.mean(y_ref ** 2)) + 1e-30
+    assert np.sqrt(np.mean((y_tc - y_ref) ** 2)) <= 2e-2 * scale
+    assert np.sqrt(np.mean((y_tc - y_simt) ** 2)) <= 2e-2 * scale
+    # rows are independent: the same row gives the same value wherever it sits in a tile
+    y2 = epwi.epwi_mlp_forward_tc(ctx.h, X[::-1].copy()).astype(np.float64)[::-1]
+    assert np.array_equal(y2, y_tc)
+
+
 def _tiny_ctx(epwi, grid=6):
     sysm = synth.tiny_system(1)
     ctx = epwi.Context()
@@ -165,7 +186,8 @@ def test_is_learned_weights_and_unbiasedness(epwi):
         for b in bands:
             X = M.features(gr.ngrid, np.full(len(cen) * Nm, k), np.repeat(cen, Nm),
                            gr.eps[k, b] - mu, b, np.tile(np.arange(Nm), len(cen)), sysm.nw, Nm)
-            yh, _ = M.forward(params.astype(np.float64), X)
+            # the proposal's own scores: the tensor-core network on the oracle's features
+            yh = epwi.epwi_mlp_forward_tc(ctx.h, X).astype(np.float64)
             probs.append(M.cell_probs(scale * yh.reshape(len(cen), Nm)))
         sel = ik == k
         p = M.p_mix(iq[sel], gr.ngrid, s, alpha, np.array(probs))
