@@ -443,7 +443,7 @@ def run_learned(args):
             full = r
         res[prec] = {"s": dt, "pairs": ctx.stats()["n_pairs"],
                      "rms_rel_err": float(np.sqrt(np.mean(((r - full) / full) ** 2)))}
-    ctx.set_precision("fp64")
+    ctx.set_precision(args.learned_precision)      # evaluation kernels of the drawn pairs
     for S in args.learned_samples:
         for name, kw in (("uniform", dict(proposal="uniform")),
                          ("learned", dict(proposal="learned", alpha=0.1, cell_stride=args.learned_stride))):
@@ -463,6 +463,7 @@ def run_learned(args):
             "higher_is_better": False, "n_gpus": 1, "steps": 2, "warmup": 1, "data": "synthetic",
             "dtype": "bf16 weights f32 network, f64 estimator", "vs_baseline": None,
             "config": {"workload": f"si_like_{N}_learned", "train_grid": 24, "train_smear_eV": 4 * eta,
+                       "is_precision": args.learned_precision,
                        "smear_eV": eta, "T_K": T, "n_c_cm3": 1e18, "window": "[CBM, CBM+0.25]",
                        "cell_stride": args.learned_stride, "alpha": 0.1, "samples_per_k": args.learned_samples},
             "training": {"samples": ntrain, "loss": loss, "s": t_train},
@@ -489,7 +490,8 @@ def main():
     ap.add_argument("--batch-systems", default="", help="batch64: comma-separated subset (profiling)")
     ap.add_argument("--no-autotune", action="store_true", help="batch64: default tile shapes")
     ap.add_argument("--learned-grid", type=int, default=100)
-    ap.add_argument("--learned-stride", type=int, default=4)
+    ap.add_argument("--learned-stride", type=int, default=2)
+    ap.add_argument("--learned-precision", default="fp16x3", choices=["fp64", "fp16x3"])
     ap.add_argument("--learned-samples", type=int, nargs="+", default=[10000, 100000])
     args = ap.parse_args()
     if args.impl == "reference":
