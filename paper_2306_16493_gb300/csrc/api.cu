@@ -100,6 +100,7 @@ void epwi_default_options(epwi_options *opt) {
     opt->device = 0;
     opt->cuda_stream = nullptr;
     opt->kpoint_chunk = 0;
+    opt->tc_a_operand = 0;
 }
 
 epwi_status epwi_create(epwi_ctx **out, const epwi_options *opt) {
@@ -120,6 +121,7 @@ epwi_status epwi_create(epwi_ctx **out, const epwi_options *opt) {
     }
     c->device = c->opt.device;
     c->stream = (cudaStream_t)c->opt.cuda_stream;
+    c->tc_gather = c->opt.tc_a_operand == 0;
     epwi_status st = guard(c, [&] {
         int n = 0;
         EPWI_CUDA(cudaGetDeviceCount(&n));
@@ -294,6 +296,7 @@ epwi_status epwi_setup(epwi_ctx *c, const epwi_system *s) {
         for (double v : rp_bound) gbound = std::max(gbound, v);
         c->tc_scale_exp = gbound > 0 ? 14 - (int)std::ceil(std::log2(gbound)) : 0;
         c->tc_ptab_key = -1;
+        c->tc_arows_key = -1;
         upload(c->Re, s->Re, 3 * (size_t)nRe, c->stream);
         upload(c->Rp, s->Rp, 3 * (size_t)nRp, c->stream);
         upload(c->Rcart, Rc.data(), Rc.size(), c->stream);
@@ -322,6 +325,7 @@ epwi_status epwi_eigs(epwi_ctx *c, const int32_t kgrid[3], const int32_t qgrid[3
         EPWI_REQUIRE(nk < (int64_t(1) << 31), EPWI_EUNSUPPORTED, "grid larger than 2^31 points");
         c->have_eigs = c->have_rates = c->have_sigma = false;
         c->tc_ptab_key = -1;
+        c->tc_arows_key = -1;
         for (int a = 0; a < 3; ++a) c->ng[a] = kgrid[a];
         c->nk = nk;
         c->L = (int)L;

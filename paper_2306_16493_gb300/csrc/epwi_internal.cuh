@@ -158,6 +158,9 @@ struct epwi_ctx {
     DevBuf tc_n32, tc_hw32;        // float [Nq][Nm]: Bose-Einstein, mode energy (-1 dropped)
     DevBuf tc_err;                 // int: timed-out waits in the tensor-core kernel
     DevBuf tc_meta;                // per-tile metadata of the tensor-core kernel
+    DevBuf tc_arows;               // gathered-A mode: split phase rows of every grid point
+    int64_t tc_arows_key = -1;
+    bool tc_gather = true;         // use the gathered-A mode where it applies
     int64_t stats_tc_grid = 0;
 
     // conductivity
@@ -179,7 +182,7 @@ struct epwi_ctx {
                          &st_n, &focc, &nocc, &pairs, &ghat, &tiles, &tile_part, &kp_tile,
                          &scan_tmp, &red_tmp, &counts, &tc_ptab, &tc_erel, &tc_f32,
                          &tc_n32, &tc_hw32, &tc_err, &tc_meta, &is_pairs, &is_w,
-                         &is_kp_pairs, &sieve_mask};
+                         &is_kp_pairs, &sieve_mask, &tc_arows};
         for (DevBuf *b : all) b->release();
         mlp_free(mlp);
     }

@@ -109,6 +109,52 @@ __global__ void k_phase_split(int L, int rlog, const double2 *__restrict__ ph64,
     }
 }
 
+// Split phase rows for the gathered-A mode, one per grid point q: the four operands
+// Pr_hi, Pi_hi, Pr_lo, Pi_lo of e^{i q.Rp} for Rp = 0 .. kpad-1 in the cube order of the
+// tensor-core kernel (n3 fastest, n in [-RC, RC]), 16-bit types only.  Entries come from the
+// same pre-split table as the in-kernel generation (copy 0), so the operand bits are those of
+// the TMEM path; K beyond nRp takes entry 0, which meets zero B rows.
+template <int RC>
+__global__ void k_phase_rows(int64_t nq, GridInfo g, int kpad, int rlog,
+                             const uint32_t *__restrict__ ptab, uint8_t *__restrict__ rows) {
+    constexpr int D = 2 * RC + 1;
+    constexpr int NRP = D * D * D;
+    const int npc = kpad / 8;                       // 16-byte pieces per operand
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nq * npc) return;
+    const int64_t q = t / npc;
+    const int piece = (int)(t % npc);
+    int i1, i2, i3;
+    grid_coords(g, q, i1, i2, i3);
+    const int a1 = i1 * g.s1 % g.L, a2 = i2 * g.s2 % g.L, a3 = i3 * g.s3 % g.L;
+    uint16_t v[4][8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int k = piece * 8 + j;
+        int idx = 0;
+        if (k < NRP) {
+            const int n1 = k / (D * D) - RC, n2 = (k / D) % D - RC, n3 = k % D - RC;
+            int x = (n1 * a1 + n2 * a2 + n3 * a3) % g.L;
+            idx = x < 0 ? x + g.L : x;
+        }
+        const uint32_t w0 = ptab[(size_t)(idx << rlog) * 2], w1 = ptab[(size_t)(idx << rlog) * 2 + 1];
+        v[0][j] = (uint16_t)(w0 & 0xffffu);
+        v[1][j] = (uint16_t)(w0 >> 16);
+        v[2][j] = (uint16_t)(w1 & 0xffffu);
+        v[3][j] = (uint16_t)(w1 >> 16);
+    }
+    uint8_t *row = rows + q * (int64_t)(4 * kpad * 2);
+#pragma unroll
+    for (int arr = 0; arr < 4; ++arr) {
+        uint4 u;
+        u.x = v[arr][0] | ((uint32_t)v[arr][1] << 16);
+        u.y = v[arr][2] | ((uint32_t)v[arr][3] << 16);
+        u.z = v[arr][4] | ((uint32_t)v[arr][5] << 16);
+        u.w = v[arr][6] | ((uint32_t)v[arr][7] << 16);
+        *reinterpret_cast<uint4 *>(row + arr * kpad * 2 + piece * 16) = u;
+    }
+}
+
 // FP32 per-call tables: energies relative to mu, occupations, mode energies (-1 if dropped).
 __global__ void k_tc_tables(int64_t nk, int W, int Nm, const double *__restrict__ eps,
                             const double *__restrict__ hw, const double *__restrict__ focc,
@@ -258,11 +304,23 @@ struct TcArgs {
     uint32_t tmem_cols;
     int64_t ntiles;
     int *err;                      // [0]: timed-out waits
+    const uint8_t *arows;          // gathered-A mode: split phase rows [q][4 operands][kpad]
+    int64_t arow_bytes;            // bytes per q row (4 * arr_bytes)
+    int arr_bytes;                 // bytes per operand (kpad * 2)
 };
 
 __device__ __forceinline__ int pmod(int x, int L) {
     int r = x % L;
     return r < 0 ? r + L : r;
+}
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
@@ -309,7 +367,7 @@ __device__ __forceinline__ void issue_b(const TcArgs &a, const TileMeta &m, int 
 // B either stays resident for a (k-point, band group) across consecutive tiles (reloaded
 // only when it changes) or, when it does not fit, streams through two slots one chunk ahead.
 // 9 warps put at most 3 on a sub-partition: <= 168 registers per thread.
-template <class Op, int W, int NM, int RC>
+template <class Op, int W, int NM, int RC, bool AG>
 __global__ void __maxnreg__(168) k_scatter_tc(TcArgs a) {
     constexpr int ES = Op::kBytes;
     constexpr int KC = 64 / ES;                 // Rp per chunk (64 bytes per row and operand)
@@ -327,11 +385,16 @@ __global__ void __maxnreg__(168) k_scatter_tc(TcArgs a) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t B_SLOT = 8u * (uint32_t)a.ncp_max * 64;   // one chunk of V1 and V2
     const int NSA = a.nsa;                      // A stages in TMEM
+    // shared memory: B slots, then either the phase table (A generated into TMEM) or the
+    // A stages (gathered-A mode: NSA x 4 operands x 128 rows x 64 bytes), then barriers
+    constexpr uint32_t A_OP = 128 * 64;                     // one operand of one A stage
     uint8_t *sB = smem;
     uint32_t *sT = reinterpret_cast<uint32_t *>(sB + (a.bres ? a.nchunk : 2) * B_SLOT);
+    uint8_t *sA = reinterpret_cast<uint8_t *>(sT);
     const int L = s.g.L;
-    const int twords = 2 * L * (1 << a.rlog) * TW;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sT + ((twords + 1) & ~1));
+    const int twords = AG ? 0 : 2 * L * (1 << a.rlog) * TW;
+    uint64_t *bars = AG ? reinterpret_cast<uint64_t *>(sA + (size_t)a.nsa * 4 * A_OP)
+                        : reinterpret_cast<uint64_t *>(sT + ((twords + 1) & ~1));
     uint64_t *a_full = bars, *mma_done = bars + 3, *b_full = bars + 6, *acc_full = bars + 8,
              *acc_empty = bars + 10, *drained = bars + 12;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 13);
@@ -443,23 +506,32 @@ __global__ void __maxnreg__(168) k_scatter_tc(TcArgs a) {
                         }
                         if (failed) break;
                         tc::tc_fence_after();
-                        const uint32_t aT = tmem_a + (uint32_t)(st * 4 * A_COLS);
                         const uint32_t bV1 = tc::smem_u32(sB + (a.bres ? ch : st) * B_SLOT);
                         const uint32_t bV2 = bV1 + 4u * (uint32_t)ncp * 64;
 #pragma unroll
                         for (int ks = 0; ks < 2; ++ks) {
-                            // A in TMEM: Pr_hi, Pi_hi, Pr_lo, Pi_lo; 32 bytes of K per MMA
-                            const uint32_t Arh = aT + ks * 8, Aih = aT + A_COLS + ks * 8;
-                            const uint32_t Arl = aT + 2 * A_COLS + ks * 8, Ail = aT + 3 * A_COLS + ks * 8;
                             const uint64_t B1 = tc::sdesc(bV1 + ks * 256, 128, 512);
                             const uint64_t B2 = tc::sdesc(bV2 + ks * 256, 128, 512);
                             const uint32_t acc = (ch == 0 && ks == 0) ? 0u : 1u;
                             // D = [Dr_hi | Di_hi | Dr_lo | Di_lo]:  Pr_hi V1 + Pi_hi V2 fills all four
                             // (hi*hi and hi*lo), Pr_lo V1 + Pi_lo V2 on the first half adds lo*hi.
-                            tc::mma_ta<Op::kTF32>(dacc, Arh, B1, id4, acc);
-                            tc::mma_ta<Op::kTF32>(dacc, Aih, B2, id4, 1);
-                            tc::mma_ta<Op::kTF32>(dacc, Arl, B1, id2, 1);
-                            tc::mma_ta<Op::kTF32>(dacc, Ail, B2, id2, 1);
+                            if constexpr (AG) {
+                                // A in shared memory (canonical layout, 32 bytes of K per MMA)
+                                const uint32_t aS = tc::smem_u32(sA + (size_t)st * 4 * A_OP) + ks * 256;
+                                tc::mma<Op::kTF32>(dacc, tc::sdesc(aS, 128, 512), B1, id4, acc);
+                                tc::mma<Op::kTF32>(dacc, tc::sdesc(aS + A_OP, 128, 512), B2, id4, 1);
+                                tc::mma<Op::kTF32>(dacc, tc::sdesc(aS + 2 * A_OP, 128, 512), B1, id2, 1);
+                                tc::mma<Op::kTF32>(dacc, tc::sdesc(aS + 3 * A_OP, 128, 512), B2, id2, 1);
+                            } else {
+                                // A in TMEM: Pr_hi, Pi_hi, Pr_lo, Pi_lo
+                                const uint32_t aT = tmem_a + (uint32_t)(st * 4 * A_COLS);
+                                const uint32_t Arh = aT + ks * 8, Aih = aT + A_COLS + ks * 8;
+                                const uint32_t Arl = aT + 2 * A_COLS + ks * 8, Ail = aT + 3 * A_COLS + ks * 8;
+                                tc::mma_ta<Op::kTF32>(dacc, Arh, B1, id4, acc);
+                                tc::mma_ta<Op::kTF32>(dacc, Aih, B2, id4, 1);
+                                tc::mma_ta<Op::kTF32>(dacc, Arl, B1, id2, 1);
+                                tc::mma_ta<Op::kTF32>(dacc, Ail, B2, id2, 1);
+                            }
                         }
                         tc::mma_commit(&mma_done[st]);
                         ++mc[st];
@@ -511,6 +583,52 @@ __global__ void __maxnreg__(168) k_scatter_tc(TcArgs a) {
             if (tile + 1 < t_end) {
                 m_next = a.meta[tile + 1];
                 q_next = 0;
+            }
+            if constexpr (AG) {
+                // ---- gathered A: copy this row's precomputed split phases chunk by chunk.
+                // Inactive rows copy the row of q = 0 (finite values; their results are unread).
+                const uint8_t *arow = a.arows + (size_t)(active ? iq : 0u) * a.arow_bytes;
+                for (int g0 = 0; g0 < m.nsel && !failed; g0 += a.nbg) {
+                    int pend = -1;                  // stage whose copies are in flight
+                    for (int ch = 0; ch < NCH; ++ch) {
+                        const int st = ctr % NSA;
+                        if (used[st] > mw[st]) {
+                            if (!tc::mbar_wait_bounded(&mma_done[st], mw[st] & 1, kWaitTimeoutNs)) failed = true;
+                            ++mw[st];
+                        }
+                        if (failed || *sfail) {
+                            failed = true;
+                            break;
+                        }
+                        uint8_t *dst = sA + (size_t)st * 4 * A_OP + ((tid >> 3) * 4) * 128 + (tid & 7) * 16;
+                        const uint8_t *src = arow + ch * 64;
+#pragma unroll
+                        for (int arr = 0; arr < 4; ++arr)
+#pragma unroll
+                            for (int kb = 0; kb < 4; ++kb)
+                                cp_async16(dst + arr * A_OP + kb * 128, src + arr * a.arr_bytes + kb * 16);
+                        cp_async_commit();
+                        if (pend >= 0) {
+                            // the previous chunk has landed: make it visible to the tensor core
+                            cp_async_wait<1>();
+                            tc::fence_proxy_async_smem();
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(&a_full[pend]);
+                        }
+                        pend = st;
+                        ++used[st];
+                        ++ctr;
+                        if (ch == 0 && g0 == 0 && tile + 1 < t_end)
+                            q_next = (m_next.begin + tid < m_next.end) ? (unsigned)s.pairs[m_next.begin + tid] : 0u;
+                    }
+                    cp_async_wait<0>();
+                    if (pend >= 0 && !failed) {
+                        tc::fence_proxy_async_smem();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&a_full[pend]);
+                    }
+                }
+                continue;
             }
             int a1 = 0, a2 = 0, a3 = 0;
             if (active) {
@@ -806,7 +924,23 @@ const uint32_t *phase_table(epwi_ctx *c, int *rlog_out) {
     return c->tc_ptab.as<uint32_t>();
 }
 
-template <class Op, int W, int NM, int RC>
+// Gathered-A mode: split phase rows of every grid point (built once per grid and precision).
+template <class Op, int RC>
+const uint8_t *phase_rows(epwi_ctx *c, int nchunk, int rlog, const uint32_t *ptab) {
+    const int kpad = nchunk * (64 / Op::kBytes);
+    const int64_t key = ((((int64_t)c->nk * 4096 + c->L) * 8 + c->opt.precision) * 64 + kpad) * 8 + rlog;
+    if (c->tc_arows_key != key) {
+        c->tc_arows.ensure((size_t)c->nk * 4 * kpad * 2);
+        const int64_t nt = c->nk * (kpad / 8);
+        k_phase_rows<RC><<<(unsigned)((nt + 255) / 256), 256, 0, c->stream>>>(
+            c->nk, make_grid_info(c), kpad, rlog, ptab, c->tc_arows.as<uint8_t>());
+        EPWI_CHECK_LAUNCH();
+        c->tc_arows_key = key;
+    }
+    return c->tc_arows.as<uint8_t>();
+}
+
+template <class Op, int W, int NM, int RC, bool AG>
 void launch_tc(epwi_ctx *c, const ScatterArgs &sa, int64_t ntiles) {
     constexpr int NMWP = (NM * W + 15) / 16 * 16;
     constexpr int TW = Op::kTF32 ? 4 : 2;
@@ -836,25 +970,37 @@ void launch_tc(epwi_ctx *c, const ScatterArgs &sa, int64_t ntiles) {
     a.nchunk = (c->nRp + 64 / ES - 1) / (64 / ES);
     a.nbg = std::max(1, 48 / NMWP);   // 4 ncp <= 192: two accumulators + A stages fit 512 columns
     a.ncp_max = std::min(sa.nsel_max, a.nbg) * NMWP;
-    // TMEM: two accumulators of 4 ncp_max columns, then NSA A stages of 4 operands x 16 columns
+    // TMEM: two accumulators of 4 ncp_max columns, then (A generated in-kernel) NSA A stages
+    // of 4 operands x 16 columns; gathered A lives in shared memory instead
     a.acc_cols = (uint32_t)((4 * a.ncp_max + 15) / 16 * 16);
     a.a_col0 = 2 * a.acc_cols;
-    a.nsa = (a.a_col0 + 3 * 64 <= 512) ? 3 : 2;
+    a.nsa = AG ? 3 : ((a.a_col0 + 3 * 64 <= 512) ? 3 : 2);
     uint32_t cols = 32;
-    while (cols < a.a_col0 + (uint32_t)(a.nsa * 4 * 16)) cols <<= 1;
+    while (cols < a.a_col0 + (AG ? 0u : (uint32_t)(a.nsa * 4 * 16))) cols <<= 1;
     EPWI_REQUIRE(cols <= 512, EPWI_EUNSUPPORTED, "tensor-core kernel needs more than 512 TMEM columns");
     a.tmem_cols = cols;
     a.ntiles = ntiles;
     c->tc_err.ensure(sizeof(int) * 4);
     EPWI_CUDA(cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), c->stream));
     a.err = c->tc_err.as<int>();
-    const int twords = 2 * c->L * (1 << a.rlog) * TW;
+    const int twords = AG ? 0 : 2 * c->L * (1 << a.rlog) * TW;
+    const size_t a_stage = AG ? (size_t)4 * 128 * 64 : 0;          // gathered A, per stage
     const size_t fixed = sizeof(uint32_t) * ((twords + 1) & ~1) + 13 * 8 + 16 + 4 * epc::kMaxW * 4 + 64;
     const size_t bres_bytes = (size_t)a.nchunk * 8 * a.ncp_max * 64;
-    a.bres = (fixed + bres_bytes <= 200 * 1024) ? 1 : 0;
+    const size_t cap = AG ? 220 * 1024 : 200 * 1024;
+    a.bres = (fixed + bres_bytes + 2 * a_stage <= cap) ? 1 : 0;
     if (!a.bres) a.nsa = 2;   // streaming B uses the A stage index as its slot index
-    size_t smem = fixed + (a.bres ? bres_bytes : 2 * 8 * (size_t)a.ncp_max * 64);
-    auto kern = k_scatter_tc<Op, W, NM, RC>;
+    else if (AG && fixed + bres_bytes + 3 * a_stage > cap) a.nsa = 2;
+    size_t smem = fixed + (a.bres ? bres_bytes : 2 * 8 * (size_t)a.ncp_max * 64) + a.nsa * a_stage;
+    a.arows = nullptr;
+    a.arow_bytes = 0;
+    a.arr_bytes = 0;
+    if constexpr (AG) {
+        a.arows = phase_rows<Op, RC>(c, a.nchunk, a.rlog, a.ptab);
+        a.arr_bytes = a.nchunk * 64;
+        a.arow_bytes = 4 * (int64_t)a.arr_bytes;
+    }
+    auto kern = k_scatter_tc<Op, W, NM, RC, AG>;
     int nsm = 0;
     EPWI_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
     EPWI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
@@ -891,14 +1037,29 @@ void launch_tc(epwi_ctx *c, const ScatterArgs &sa, int64_t ntiles) {
     }
 }
 
+// Gathered A (precomputed split phase rows) for the 16-bit types while the rows of the whole
+// grid take at most 16 GiB; A generated in-kernel into TMEM otherwise.
+template <class Op, int W, int NM, int RC>
+void launch_any(epwi_ctx *c, const ScatterArgs &sa, int64_t nt) {
+    constexpr int D = 2 * RC + 1;
+    const int64_t kpad = ((D * D * D + 64 / Op::kBytes - 1) / (64 / Op::kBytes)) * (64 / Op::kBytes);
+    if constexpr (!Op::kTF32) {
+        if (c->tc_gather && (int64_t)c->nk * 4 * kpad * 2 <= (int64_t(16) << 30)) {
+            launch_tc<Op, W, NM, RC, true>(c, sa, nt);
+            return;
+        }
+    }
+    launch_tc<Op, W, NM, RC, false>(c, sa, nt);
+}
+
 template <class Op>
 void dispatch_tc(epwi_ctx *c, const ScatterArgs &sa, int64_t nt) {
     const int W = c->nw, NM = c->nm, r = c->rp_cube_r;
-    if (W == 1 && NM == 3 && r == 1) launch_tc<Op, 1, 3, 1>(c, sa, nt);
-    else if (W == 4 && NM == 3 && r == 1) launch_tc<Op, 4, 3, 1>(c, sa, nt);
-    else if (W == 4 && NM == 3 && r == 2) launch_tc<Op, 4, 3, 2>(c, sa, nt);
-    else if (W == 8 && NM == 6 && r == 3) launch_tc<Op, 8, 6, 3>(c, sa, nt);
-    else if (W == 8 && NM == 6 && r == 1) launch_tc<Op, 8, 6, 1>(c, sa, nt);
+    if (W == 1 && NM == 3 && r == 1) launch_any<Op, 1, 3, 1>(c, sa, nt);
+    else if (W == 4 && NM == 3 && r == 1) launch_any<Op, 4, 3, 1>(c, sa, nt);
+    else if (W == 4 && NM == 3 && r == 2) launch_any<Op, 4, 3, 2>(c, sa, nt);
+    else if (W == 8 && NM == 6 && r == 3) launch_any<Op, 8, 6, 3>(c, sa, nt);
+    else if (W == 8 && NM == 6 && r == 1) launch_any<Op, 8, 6, 1>(c, sa, nt);
     else
         throw EpwiError{EPWI_EUNSUPPORTED,
                         "split-precision path built for (nw, modes, R_p cube half-width) in "

@@ -126,3 +126,29 @@ def test_al_like_48_sampled_split(epwi):
     ref64 = gpu_run(s, (N, N, N), T, mu, eta, mu - 0.3, mu + 0.3, precision="fp64", ctx=ctx)
     assert rel_frob(out["sigma"], ref64["sigma"]) < RATE_TOL
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp16x3", "bf16x3"])
+@pytest.mark.parametrize("make,N", [(synth.al_like_system, (10, 10, 10)),
+                                    (synth.si_like_system, (6, 5, 4)),
+                                    (synth.tiny_system, (7, 7, 7))])
+def test_gathered_and_generated_phase_operands_agree(epwi, prec, make, N):
+    """The precomputed split phase rows gathered into shared memory give the rates of the
+    per-tile generation into TMEM: the same operand bits, so agreement to FP32 summation
+    order (<= 1e-6), and both meet the FP64 oracle bound."""
+    s = make()
+    gr = O.Grids(s, N)
+    mu = gr.band_centre()
+    T, eta = 300.0, 0.05
+    lo, hi = (mu - 0.5, mu + 0.5) if s.nw <= 4 else (-np.inf, np.inf)
+    res = {}
+    for mode in (0, 1):
+        res[mode] = gpu_run(s, N, T, mu, eta, lo, hi, precision=prec, tc_a_operand=mode)
+    a, b = res[0]["inv_tau"], res[1]["inv_tau"]
+    assert np.array_equal(res[0]["ik"], res[1]["ik"]) and np.array_equal(res[0]["n"], res[1]["n"])
+    assert np.allclose(a, b, rtol=1e-6, atol=1e-6 * np.abs(b).max())
+    ora = oracle_run(gr, T, mu, eta, lo, hi)
+    err, n = compare_rates(res[0], ora, gr.eps, RATE_TOL)
+    assert n > 0 and err < RATE_TOL, err
+    for r in res.values():
+        r["ctx"].close()
