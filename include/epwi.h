@@ -88,10 +88,10 @@ typedef struct {
     int32_t device;             /* CUDA device ordinal (default 0) */
     void *cuda_stream;          /* cudaStream_t, NULL = legacy default stream */
     int32_t kpoint_chunk;       /* k-points per on-the-fly chunk, 0 = automatic */
-    int32_t tc_a_operand;       /* split modes, phase operand A: 0 = precomputed split rows of
-                                   every q gathered into shared memory (fp16x3, bf16x3, when the
-                                   rows take <= 16 GiB), else generated per tile into TMEM;
-                                   1 = always generated per tile (default 0) */
+    int32_t tc_a_operand;       /* split modes, phase operand A: 0 = generated per tile into
+                                   TMEM (default); 1 = precomputed split rows of every q gathered
+                                   into shared memory (fp16x3, bf16x3, when the rows take
+                                   <= 16 GiB; measured slower on the 48^3 benchmark) */
 } epwi_options;
 
 /* Per-call statistics of the last epwi_scatter_rates (and what precedes it). */

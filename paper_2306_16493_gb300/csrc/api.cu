@@ -121,7 +121,7 @@ epwi_status epwi_create(epwi_ctx **out, const epwi_options *opt) {
     }
     c->device = c->opt.device;
     c->stream = (cudaStream_t)c->opt.cuda_stream;
-    c->tc_gather = c->opt.tc_a_operand == 0;
+    c->tc_gather = c->opt.tc_a_operand == 1;
     epwi_status st = guard(c, [&] {
         int n = 0;
         EPWI_CUDA(cudaGetDeviceCount(&n));

@@ -160,7 +160,7 @@ struct epwi_ctx {
     DevBuf tc_meta;                // per-tile metadata of the tensor-core kernel
     DevBuf tc_arows;               // gathered-A mode: split phase rows of every grid point
     int64_t tc_arows_key = -1;
-    bool tc_gather = true;         // use the gathered-A mode where it applies
+    bool tc_gather = false;        // use the gathered-A mode where it applies
     int64_t stats_tc_grid = 0;
 
     // conductivity

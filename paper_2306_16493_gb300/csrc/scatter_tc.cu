@@ -1037,8 +1037,11 @@ void launch_tc(epwi_ctx *c, const ScatterArgs &sa, int64_t ntiles) {
     }
 }
 
-// Gathered A (precomputed split phase rows) for the 16-bit types while the rows of the whole
-// grid take at most 16 GiB; A generated in-kernel into TMEM otherwise.
+// A generated per tile into TMEM (default), or, when the context asks for it, gathered from
+// precomputed split phase rows (16-bit types, rows of the whole grid <= 16 GiB).  On the
+// 48^3 Al-like benchmark the gathered mode is slower (583 vs 424 ms per step): the kernel is
+// bound by the instruction issue of all roles together, and the gathers add L2 traffic and
+// latency in front of every MMA.
 template <class Op, int W, int NM, int RC>
 void launch_any(epwi_ctx *c, const ScatterArgs &sa, int64_t nt) {
     constexpr int D = 2 * RC + 1;
