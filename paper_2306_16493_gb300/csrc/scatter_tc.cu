@@ -400,10 +400,6 @@ __global__ void __maxnreg__(168) k_scatter_tc(TcArgs a) {
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 13);
     volatile int *sfail = reinterpret_cast<volatile int *>(tslot + 1);
     float *wred = reinterpret_cast<float *>(tslot + 4);   // [4][kMaxW]
-    // epilogue operand buffer (PRE): [W^2 + NM^2][128] float2, then [2 NM + 2 W][128] float
-    float2 *sEV = reinterpret_cast<float2 *>(
-        (reinterpret_cast<uintptr_t>(wred + 4 * epc::kMaxW) + 15) & ~uintptr_t(15));
-    float *sEF = reinterpret_cast<float *>(sEV + (PRE ? (W * W + NM * NM) * 128 : 0));
 
     for (int i = tid; i < twords; i += blockDim.x) sT[i] = a.ptab[i];
     if (tid == 0) {
@@ -780,51 +776,30 @@ __global__ void __maxnreg__(168) k_scatter_tc(TcArgs a) {
                 if (b3 >= n3) b3 -= n3;
                 ikq = (b1 * n2 + b2) * n3 + b3;
             }
-            // epilogue operands of this pair, fetched while the MMAs of this tile run.  Small
-            // systems (PRE) copy them with cp.async into this thread's column of a
-            // structure-of-arrays buffer in shared memory (no registers held across the wait,
-            // conflict-free reads); larger ones are read from L1/L2 at use.
+            // epilogue operands of this pair, fetched while the MMAs of this tile run
+            float2 Vr[PRE ? W * W : 1], ur[PRE ? NM * NM : 1];
+            float wq[NM], nq[NM], emr[W], fmr[W];
             const float2 *Vq = s.V32 + (size_t)ikq * W * W;
             const float2 *uq = s.u32 + (size_t)iq * NM * NM;
-            float wq[PRE ? 1 : NM], nq[PRE ? 1 : NM], emr[PRE ? 1 : W], fmr[PRE ? 1 : W];
             if constexpr (PRE) {
 #pragma unroll
-                for (int x = 0; x < W * W; ++x) tc::cp_async8(sEV + x * 128 + et, Vq + x);
+                for (int x = 0; x < W * W; ++x) Vr[x] = __ldg(Vq + x);
 #pragma unroll
-                for (int x = 0; x < NM * NM; ++x) tc::cp_async8(sEV + (W * W + x) * 128 + et, uq + x);
-#pragma unroll
-                for (int nu = 0; nu < NM; ++nu) {
-                    tc::cp_async4(sEF + nu * 128 + et, a.hw32 + (size_t)iq * NM + nu);
-                    tc::cp_async4(sEF + (NM + nu) * 128 + et, a.n32 + (size_t)iq * NM + nu);
-                }
-#pragma unroll
-                for (int mm = 0; mm < W; ++mm) {
-                    tc::cp_async4(sEF + (2 * NM + mm) * 128 + et, a.erel32 + (size_t)ikq * W + mm);
-                    tc::cp_async4(sEF + (2 * NM + W + mm) * 128 + et, a.f32 + (size_t)ikq * W + mm);
-                }
-                cp_async_commit();
+                for (int x = 0; x < NM * NM; ++x) ur[x] = __ldg(uq + x);
             } else {
                 tc::prefetch_l1(Vq);
                 tc::prefetch_l1(uq);
-#pragma unroll
-                for (int nu = 0; nu < NM; ++nu) {
-                    wq[nu] = __ldg(a.hw32 + (size_t)iq * NM + nu);
-                    nq[nu] = __ldg(a.n32 + (size_t)iq * NM + nu);
-                }
-#pragma unroll
-                for (int mm = 0; mm < W; ++mm) {
-                    emr[mm] = __ldg(a.erel32 + (size_t)ikq * W + mm);
-                    fmr[mm] = __ldg(a.f32 + (size_t)ikq * W + mm);
-                }
             }
-            // operand accessors (shared memory for PRE, registers / L1 otherwise)
-            auto Vat = [&](int x) -> float2 { if constexpr (PRE) return sEV[x * 128 + et]; else return __ldg(Vq + x); };
-            auto Uat = [&](int x) -> float2 { if constexpr (PRE) return sEV[(W * W + x) * 128 + et]; else return __ldg(uq + x); };
-            auto Wat = [&](int nu) -> float { if constexpr (PRE) return sEF[nu * 128 + et]; else return wq[nu]; };
-            auto Nat = [&](int nu) -> float { if constexpr (PRE) return sEF[(NM + nu) * 128 + et]; else return nq[nu]; };
-            auto Eat = [&](int mm) -> float { if constexpr (PRE) return sEF[(2 * NM + mm) * 128 + et]; else return emr[mm]; };
-            auto Fat = [&](int mm) -> float { if constexpr (PRE) return sEF[(2 * NM + W + mm) * 128 + et]; else return fmr[mm]; };
-            bool staged = !PRE;
+#pragma unroll
+            for (int nu = 0; nu < NM; ++nu) {
+                wq[nu] = __ldg(a.hw32 + (size_t)iq * NM + nu);
+                nq[nu] = __ldg(a.n32 + (size_t)iq * NM + nu);
+            }
+#pragma unroll
+            for (int mm = 0; mm < W; ++mm) {
+                emr[mm] = __ldg(a.erel32 + (size_t)ikq * W + mm);
+                fmr[mm] = __ldg(a.f32 + (size_t)ikq * W + mm);
+            }
             if (tile + 1 < t_end)
                 q_next = (m_next.begin + et < m_next.end) ? (unsigned)s.pairs[m_next.begin + et] : 0u;
             for (int g0 = 0; g0 < m.nsel && !failed; g0 += a.nbg) {
@@ -839,10 +814,6 @@ __global__ void __maxnreg__(168) k_scatter_tc(TcArgs a) {
                     break;
                 }
                 tc::tc_fence_after();
-                if (!staged) {
-                    cp_async_wait<0>();          // this thread's operand copies have landed
-                    staged = true;
-                }
                 const uint32_t arow = tmem_row + (uint32_t)ab * acc_cols;
                 for (int b = 0; b < nb; ++b) {
                     float gr[NMWP], gi[NMWP];
@@ -876,18 +847,21 @@ __global__ void __maxnreg__(168) k_scatter_tc(TcArgs a) {
                                 h[mu] = make_float2(0.f, 0.f);
 #pragma unroll
                                 for (int i = 0; i < W; ++i) {
-                                    const float2 vv = Vat(i * W + mm);
+                                    const float2 vv = PRE ? Vr[(i * W + mm) % (PRE ? W * W : 1)] : __ldg(Vq + i * W + mm);
                                     h[mu] = cfmacf(vv, make_float2(gr[mu * W + i], gi[mu * W + i]), h[mu]);
                                 }
                             }
-                            const float em = Eat(mm);
-                            const float fm = Fat(mm);
+                            const float em = emr[mm];
+                            const float fm = fmr[mm];
 #pragma unroll
                             for (int nu = 0; nu < NM; ++nu) {
-                                const float w = Wat(nu);
+                                const float w = wq[nu];
                                 float2 gv = make_float2(0.f, 0.f);
 #pragma unroll
-                                for (int mu = 0; mu < NM; ++mu) gv = cfmaf(h[mu], Uat(mu * NM + nu), gv);
+                                for (int mu = 0; mu < NM; ++mu) {
+                                    const float2 uv = PRE ? ur[(mu * NM + nu) % (PRE ? NM * NM : 1)] : __ldg(uq + mu * NM + nu);
+                                    gv = cfmaf(h[mu], uv, gv);
+                                }
                                 const float g2 = gv.x * gv.x + gv.y * gv.y;
                                 if (s.g2out) {
                                     s.g2out[(((s.g2_base + pair) * m.nsel + g0 + b) * NM + nu) * W + mm] =
@@ -900,11 +874,11 @@ __global__ void __maxnreg__(168) k_scatter_tc(TcArgs a) {
                                 float tt = 0.f;
                                 if (fabsf(x1) <= a.ceta32) {
                                     const float y = x1 * a.inv_eta32;
-                                    tt += (Nat(nu) + fm) * __expf(-y * y);
+                                    tt += (nq[nu] + fm) * __expf(-y * y);
                                 }
                                 if (fabsf(x2) <= a.ceta32) {
                                     const float y = x2 * a.inv_eta32;
-                                    tt += (1.f + Nat(nu) - fm) * __expf(-y * y);
+                                    tt += (1.f + nq[nu] - fm) * __expf(-y * y);
                                 }
                                 rate = fmaf(g2, tt, rate);
                             }
@@ -1011,10 +985,7 @@ void launch_tc(epwi_ctx *c, const ScatterArgs &sa, int64_t ntiles) {
     a.err = c->tc_err.as<int>();
     const int twords = AG ? 0 : 2 * c->L * (1 << a.rlog) * TW;
     const size_t a_stage = AG ? (size_t)4 * 128 * 64 : 0;          // gathered A, per stage
-    constexpr bool PRE = (W * W + NM * NM) <= 32;
-    const size_t stage_e = PRE ? (size_t)128 * ((W * W + NM * NM) * 8 + (2 * NM + 2 * W) * 4) : 0;
-    const size_t fixed = sizeof(uint32_t) * ((twords + 1) & ~1) + 13 * 8 + 16 + 4 * epc::kMaxW * 4 + 64 +
-                         stage_e;
+    const size_t fixed = sizeof(uint32_t) * ((twords + 1) & ~1) + 13 * 8 + 16 + 4 * epc::kMaxW * 4 + 64;
     const size_t bres_bytes = (size_t)a.nchunk * 8 * a.ncp_max * 64;
     const size_t cap = AG ? 220 * 1024 : 200 * 1024;
     a.bres = (fixed + bres_bytes + 2 * a_stage <= cap) ? 1 : 0;
