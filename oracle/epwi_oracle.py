@@ -288,6 +288,33 @@ def conductivity(volume_A3, nk, v, inv_tau, eps, mu, T) -> np.ndarray:
     return 2.0 * E_CHARGE ** 2 / (nk * volume_A3 * 1e-30 * kT_J) * s
 
 
+def transport_coefficients(volume_A3, nk, v, inv_tau, eps, mu, T):
+    """sigma (S/m), Seebeck S (V/K) and electronic thermal conductivity kappa_e (W/(m K)) from
+    the zeroth, first and second energy moments of the SERTA sum (Sec. II C, Eqs. 12-14, with
+    F = F^0 = v tau):
+        sigma        = (2 q^2 / (N_k V)) sum v v tau (-df/de),
+        nu = sigma S = (2 q / (T V N_k)) sum (e - mu) v v tau (-df/de),   q = -e (electrons),
+        kappa_0      = (2 / (T V N_k)) sum (e - mu)^2 v v tau (-df/de),
+        S = sigma^-1 nu,  kappa_e = kappa_0 - T nu sigma^-1 nu
+    (the tensor form of kappa_0 - T sigma S^2).  States with 1/tau = 0 are left out."""
+    ok = inv_tau > 0
+    tau = np.where(ok, 1.0 / np.where(ok, inv_tau, 1.0), 0.0)
+    f = fermi(eps, mu, T)
+    kT_J = KB_EVK * T * E_CHARGE
+    w = tau * f * (1.0 - f) / kT_J                                    # tau (-df/de), s / J
+    de_J = (np.asarray(eps, float) - mu) * E_CHARGE                    # e - mu in J
+    vol = nk * volume_A3 * 1e-30
+    m0 = np.einsum("s,sa,sb->ab", w, v, v)
+    m1 = np.einsum("s,sa,sb->ab", w * de_J, v, v)
+    m2 = np.einsum("s,sa,sb->ab", w * de_J ** 2, v, v)
+    sigma = 2.0 * E_CHARGE ** 2 / vol * m0
+    nu = 2.0 * (-E_CHARGE) / (T * vol) * m1
+    kappa0 = 2.0 / (T * vol) * m2
+    seebeck = np.linalg.solve(sigma, nu)
+    kappa_e = kappa0 - T * nu @ seebeck
+    return sigma, seebeck, kappa_e
+
+
 def carrier_density(eps_cb, nk, volume_A3, mu, T) -> float:
     """Conduction electrons per cm^3: (2 / (N_k V)) sum_{n >= n_v, k} f(eps_nk)."""
     return 2.0 * fermi(eps_cb, mu, T).sum() / (nk * volume_A3 * 1e-24)

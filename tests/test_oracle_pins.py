@@ -337,3 +337,47 @@ def test_conductivity_symmetric_psd(tiny):
     sig = O.conductivity(tiny.volume, gr.nk, v, res["inv_tau"], gr.eps[res["ik"], res["n"]], mu, T)
     assert np.allclose(sig, sig.T, rtol=1e-14, atol=0)
     assert np.linalg.eigvalsh(sig).min() > -1e-12 * np.trace(sig)
+
+
+# ------------------------------------------------------------------ Seebeck and kappa_e
+def _parabolic_states(n, kmax, m_eff=1.0):
+    """States of an isotropic parabolic band eps = hbar^2 k^2 / 2m sampled on a uniform cubic
+    k-mesh (|k_a| <= kmax, 1/A), with v = hbar k / m in m/s."""
+    k1 = np.linspace(-kmax, kmax, n)
+    kx, ky, kz = np.meshgrid(k1, k1, k1, indexing="ij")
+    k = np.stack([kx.ravel(), ky.ravel(), kz.ravel()], -1)                  # 1/A
+    hb2_2m = O.HBAR_JS ** 2 / (2 * m_eff * 9.1093837015e-31) / O.E_CHARGE * 1e20   # eV A^2
+    eps = hb2_2m * (k ** 2).sum(1)
+    v = O.HBAR_JS * k * 1e10 / (m_eff * 9.1093837015e-31)                   # m/s
+    return eps, v
+
+
+def test_seebeck_nondegenerate_parabolic_band():
+    """Boltzmann statistics, constant tau, parabolic band: S = -(k_B/e)(5/2 - eta),
+    eta = mu / k_B T (band edge at 0)."""
+    T = 300.0
+    kT = O.KB_EVK * T
+    eps, v = _parabolic_states(121, 0.35)
+    assert eps.max() > 25 * kT                   # the mesh covers the thermal tail
+    for eta in (-4.0, -6.0):
+        mu = eta * kT
+        sig, S, kap = O.transport_coefficients(10.0, len(eps), v, np.full(len(eps), 1e13), eps, mu, T)
+        ref = -(O.KB_EVK) * (2.5 - eta)          # k_B / e in V/K equals k_B in eV/K
+        assert abs(S[0, 0] / ref - 1) < 1e-2, (S[0, 0], ref)
+        assert abs(S[1, 1] / S[0, 0] - 1) < 1e-6 and abs(S[0, 1]) < 1e-6 * abs(S[0, 0])
+
+
+def test_wiedemann_franz_degenerate_parabolic_band():
+    """Degenerate electrons, constant tau: kappa_e / (sigma T) -> L0 = (pi^2/3)(k_B/e)^2 with
+    Sommerfeld corrections O((k_B T / E_F)^2); the thermopower is Mott's -(pi^2/2)(k_B/e)
+    (k_B T / E_F) for sigma(E) ~ E^{3/2}."""
+    T, EF = 300.0, 1.0
+    kT = O.KB_EVK * T
+    eps, v = _parabolic_states(161, 0.62)
+    sel = np.abs(eps - EF) < 20 * kT
+    eps, v = eps[sel], v[sel]
+    sig, S, kap = O.transport_coefficients(10.0, 1000, v, np.full(len(eps), 1e14), eps, EF, T)
+    L0 = np.pi ** 2 / 3 * O.KB_EVK ** 2
+    assert abs(kap[0, 0] / (sig[0, 0] * T) / L0 - 1) < 2e-2
+    mott = -(np.pi ** 2 / 2) * O.KB_EVK * kT / EF
+    assert abs(S[0, 0] / mott - 1) < 5e-2, (S[0, 0], mott)
