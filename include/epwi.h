@@ -396,6 +396,17 @@ epwi_status epwi_batch_get_tile(epwi_batch *batch, int32_t s, int32_t *mt, int32
                                 int32_t *source);
 epwi_status epwi_batch_get_stats(epwi_batch *batch, epwi_batch_stats *out);
 
+/* Transport tensors of the last epwi_scatter_rates or epwi_scatter_rates_is (Sec. II C,
+ * Eqs. 12-14, with F = v tau).  Let w = tau f(1-f)/(k_B T).  Then:
+ *   sigma        = (2 e^2/(N_k V)) sum w v v                      [S/m];
+ *   nu = sigma S = (2 q/(T V N_k)) sum (eps - mu) w v v, q = -e   [A/(m K)];
+ *   kappa_0      = (2/(T V N_k)) sum (eps - mu)^2 w v v           [W/(m K)];
+ *   S = sigma^-1 nu                                               [V/K];
+ *   kappa_e = kappa_0 - T nu sigma^-1 nu, the tensor form of kappa_0 - T sigma S^2.
+ * Outputs are row-major 3x3 (any pointer may be NULL).  The three moments come from one
+ * fixed-order FP64 device reduction.  Errors: ESTATE; ENUMERIC (singular sigma). */
+epwi_status epwi_transport(epwi_ctx *ctx, double sigma[9], double seebeck[9], double kappa_e[9]);
+
 /* Number of kernels this library has launched in the process so far (all contexts). */
 int64_t epwi_kernel_launches(void);
 

@@ -484,6 +484,68 @@ epwi_status epwi_conductivity(epwi_ctx *c, double sigma[9]) {
     });
 }
 
+// 3x3 solve x = A^-1 b (row-major, all three columns of b), Gaussian elimination with
+// partial pivoting.
+static void solve3(const double A_[9], const double B_[9], double X[9]) {
+    double A[9], B[9];
+    std::memcpy(A, A_, sizeof(A));
+    std::memcpy(B, B_, sizeof(B));
+    int piv[3] = {0, 1, 2};
+    for (int col = 0; col < 3; ++col) {
+        int best = col;
+        for (int r = col + 1; r < 3; ++r)
+            if (std::fabs(A[piv[r] * 3 + col]) > std::fabs(A[piv[best] * 3 + col])) best = r;
+        std::swap(piv[col], piv[best]);
+        const double d = A[piv[col] * 3 + col];
+        EPWI_REQUIRE(d != 0.0, EPWI_ENUMERIC, "singular conductivity tensor");
+        for (int r = col + 1; r < 3; ++r) {
+            const double f = A[piv[r] * 3 + col] / d;
+            for (int j = 0; j < 3; ++j) {
+                A[piv[r] * 3 + j] -= f * A[piv[col] * 3 + j];
+                B[piv[r] * 3 + j] -= f * B[piv[col] * 3 + j];
+            }
+        }
+    }
+    for (int j = 0; j < 3; ++j)
+        for (int col = 2; col >= 0; --col) {
+            double v = B[piv[col] * 3 + j];
+            for (int k = col + 1; k < 3; ++k) v -= A[piv[col] * 3 + k] * X[k * 3 + j];
+            X[col * 3 + j] = v / A[piv[col] * 3 + col];
+        }
+}
+
+epwi_status epwi_transport(epwi_ctx *c, double sigma[9], double seebeck[9], double kappa_e[9]) {
+    return guard(c, [&] {
+        require_rates(c);
+        double m[3][9];
+        transport_moments(c, m);
+        const double e = epc::kECharge;
+        const double kT_J = epc::kKbEVK * c->T * e;
+        const double vol = (double)c->nk * c->volume * 1e-30;
+        const double pref = 2.0 * e * e / (vol * kT_J);   // sigma per unit of the zeroth moment
+        double sig[9], nu[9], k0[9];
+        for (int i = 0; i < 9; ++i) {
+            sig[i] = pref * m[0][i];
+            nu[i] = -pref * m[1][i] / c->T;                // q = -e: electrons
+            k0[i] = pref * m[2][i] / c->T;
+        }
+        double S[9];
+        solve3(sig, nu, S);
+        for (int i = 0; i < 9; ++i) {
+            EPWI_REQUIRE(std::isfinite(sig[i]) && std::isfinite(S[i]), EPWI_ENUMERIC, "non-finite result");
+            if (sigma) sigma[i] = sig[i];
+            if (seebeck) seebeck[i] = S[i];
+        }
+        if (kappa_e)
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    double t = 0;
+                    for (int k = 0; k < 3; ++k) t += nu[i * 3 + k] * S[k * 3 + j];
+                    kappa_e[i * 3 + j] = k0[i * 3 + j] - c->T * t;
+                }
+    });
+}
+
 epwi_status epwi_mobility(epwi_ctx *c, double n_c, double mob[9]) {
     return guard(c, [&] {
         EPWI_REQUIRE(c->have_sigma, EPWI_ESTATE, "epwi_conductivity has not been called");

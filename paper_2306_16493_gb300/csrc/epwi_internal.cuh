@@ -263,5 +263,6 @@ void occupation_tables(epwi_ctx *c);
 void run_scatter(epwi_ctx *c);
 double carrier_density(epwi_ctx *c, double T, double mu, int n_valence);
 void conductivity(epwi_ctx *c, double sigma[9]);
+void transport_moments(epwi_ctx *c, double m[3][9]);
 void run_g2(epwi_ctx *c, int64_t npairs, const int32_t *ik, const int32_t *iq, int band_lo,
             int nsel, double *g2);

@@ -71,6 +71,38 @@ __global__ void __launch_bounds__(kRedThreads) k_sigma_part(
         for (int j = 0; j < 6; ++j) part[blockIdx.x * 6 + j] = v[j];
 }
 
+// Energy moments p = 0, 1, 2 of the SERTA transport sum (Sec. II C, Eqs. 12-14): for each
+// state, w = tau f(1-f) and x = eps - mu (eV); sums of w x^p v_a v_b for the six components
+// xx yy zz xy xz yz, stored p-major.
+__global__ void __launch_bounds__(kRedThreads) k_moments_part(
+    int64_t ns, int W, const int *__restrict__ st_k, const int *__restrict__ st_n,
+    const double *__restrict__ inv_tau, const double *__restrict__ eps,
+    const double *__restrict__ vel, double mu, double kT, double *__restrict__ part) {
+    __shared__ double sm[18 * kRedThreads];
+    const int64_t per = (ns + gridDim.x - 1) / gridDim.x;
+    const int64_t b0 = per * blockIdx.x, b1 = min(ns, b0 + per);
+    double v[18];
+    for (int j = 0; j < 18; ++j) v[j] = 0;
+    for (int64_t s = b0 + threadIdx.x; s < b1; s += blockDim.x) {
+        const double r = inv_tau[s];
+        if (!(r > 0)) continue;
+        const int64_t idx = (int64_t)st_k[s] * W + st_n[s];
+        const double f = fermi(eps[idx], mu, kT);
+        const double w0 = f * (1.0 - f) / r;
+        const double x = eps[idx] - mu;
+        const double vx = vel[idx * 3], vy = vel[idx * 3 + 1], vz = vel[idx * 3 + 2];
+        const double c[6] = {vx * vx, vy * vy, vz * vz, vx * vy, vx * vz, vy * vz};
+        double w = w0;
+        for (int p = 0; p < 3; ++p) {
+            for (int j = 0; j < 6; ++j) v[p * 6 + j] += w * c[j];
+            w *= x;
+        }
+    }
+    block_sum<18>(v, sm);
+    if (threadIdx.x == 0)
+        for (int j = 0; j < 18; ++j) part[blockIdx.x * 18 + j] = v[j];
+}
+
 template <int NV>
 __global__ void __launch_bounds__(kRedThreads) k_final_sum(int nb, const double *__restrict__ part,
                                                            double *__restrict__ out) {
@@ -217,4 +249,29 @@ void conductivity(epwi_ctx *c, double sigma[9]) {
     const double pref = 2.0 * epc::kECharge * epc::kECharge / ((double)c->nk * c->volume * 1e-30 * kT_J);
     const double s[9] = {h[0], h[3], h[4], h[3], h[1], h[5], h[4], h[5], h[2]};
     for (int i = 0; i < 9; ++i) sigma[i] = pref * s[i];
+}
+
+// sum over states of tau f(1-f) (eps - mu)^p v_a v_b, p = 0, 1, 2 (eV^p m^2/s), as three
+// symmetric 3x3 tensors m[p][9].
+void transport_moments(epwi_ctx *c, double m[3][9]) {
+    const int64_t ns = c->nstates;
+    const int nb = red_blocks(ns);
+    c->red_tmp.ensure(sizeof(double) * (18 * nb + 32));
+    double *part = c->red_tmp.as<double>();
+    double *out = part + 18 * nb;
+    const double kT = epc::kKbEVK * c->T;
+    k_moments_part<<<nb, kRedThreads, 0, c->stream>>>(ns, c->nw, c->st_k.as<int>(), c->st_n.as<int>(),
+                                                      c->inv_tau.as<double>(), c->eps.as<double>(),
+                                                      c->vel.as<double>(), c->mu, kT, part);
+    EPWI_CHECK_LAUNCH();
+    k_final_sum<18><<<1, kRedThreads, 0, c->stream>>>(nb, part, out);
+    EPWI_CHECK_LAUNCH();
+    double h[18];
+    EPWI_CUDA(cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    EPWI_CUDA(cudaStreamSynchronize(c->stream));
+    for (int p = 0; p < 3; ++p) {
+        const double *q = h + 6 * p;
+        const double t[9] = {q[0], q[3], q[4], q[3], q[1], q[5], q[4], q[5], q[2]};
+        for (int i = 0; i < 9; ++i) m[p][i] = t[i];
+    }
 }

@@ -98,6 +98,7 @@ def _load() -> C.CDLL:
         "epwi_get_rates": (I32, [P, I64, P, P, P]),
         "epwi_conductivity": (I32, [P, P]),
         "epwi_mobility": (I32, [P, D, P]),
+        "epwi_transport": (I32, [P, P, P, P]),
         "epwi_get_bands": (I32, [P, P, P, P]),
         "epwi_get_phonons": (I32, [P, P, P]),
         "epwi_get_sieve": (I32, [P, I64, P, P]),
@@ -550,6 +551,12 @@ class Context:
 
     def conductivity(self):
         return epwi_conductivity(self.h)
+
+    def transport(self):
+        """(sigma [S/m], Seebeck [V/K], kappa_e [W/(m K)]) as 3x3 arrays."""
+        sig, S, kap = np.empty((3, 3)), np.empty((3, 3)), np.empty((3, 3))
+        _check(self.h, _lib.epwi_transport(self.h, _ptr(sig), _ptr(S), _ptr(kap)))
+        return sig, S, kap
 
     def mobility(self, n_cm3):
         return epwi_mobility(self.h, n_cm3)

@@ -241,3 +241,33 @@ def test_edge_cases(epwi):
     with pytest.raises(epwi.EpwiError):
         ctx.eigs((4, 4, 0))
     ctx.close()
+
+
+@pytest.mark.parametrize("which", ["tiny", "si"])
+def test_seebeck_and_kappa_parity(epwi, which):
+    """sigma, Seebeck and kappa_e (Eqs. 12-14) from the GPU moments vs the oracle: 1e-10."""
+    T = 300.0
+    if which == "tiny":
+        s = synth.tiny_system(1)
+        N, eta = 8, 0.05
+        gr = O.Grids(s, (N,) * 3)
+        mu = gr.band_centre()
+        lo, hi = -np.inf, np.inf
+    else:
+        s = synth.si_like_system(3)
+        N, eta = 12, 0.01
+        gr = O.Grids(s, (N,) * 3)
+        cbm = gr.eps[:, s.n_valence].min()
+        mu = O.find_mu(gr.eps[:, s.n_valence:], gr.nk, s.volume, 1e18, T)
+        lo, hi = cbm, cbm + 0.25
+    out = gpu_run(s, (N,) * 3, T, mu, eta, lo, hi)
+    sig, S, kap = out["ctx"].transport()
+    ora = oracle_run(gr, T, mu, eta, lo, hi)
+    v = gr.velocities(ora["ik"], ora["n"])
+    sr, Sr, kr = O.transport_coefficients(s.volume, gr.nk, v, ora["inv_tau"],
+                                          gr.eps[ora["ik"], ora["n"]], mu, T)
+    assert rel_frob(sig, sr) < TOL
+    assert rel_frob(S, Sr) < TOL and rel_frob(kap, kr) < TOL
+    if which == "si":
+        assert (np.diag(S) < 0).all()          # electrons: negative thermopower
+    out["ctx"].close()
