@@ -521,26 +521,36 @@ void mlp_train(epwi_ctx *c, double T, double mu, double eta, double emin, double
     EPWI_CHECK_LAUNCH();
     m.out_scale = sd;
     m.out_shift = mean;
-    // Adam on shuffled mini-batches; the learning rate follows a cosine from lr to lr / 20
-    const int64_t B = std::min<int64_t>(std::max<int64_t>(o.batch, 1), kMaxBatch);
+    // Adam on shuffled mini-batches of B samples (the last batch of an epoch wraps around the
+    // permutation); the learning rate follows a cosine from lr to lr / 20.  The per-step
+    // scalars go into a table; one captured graph replays every step.
+    const int64_t B = std::min<int64_t>(std::min<int64_t>(std::max<int64_t>(o.batch, 1), kMaxBatch), n);
     const int64_t steps_per_epoch = (n + B - 1) / B;
     const int64_t total = steps_per_epoch * std::max(o.epochs, 0);
-    int64_t step = 0;
+    std::vector<StepParams> steps;
+    steps.reserve((size_t)total);
+    const int64_t t0 = m.step;                       // Adam steps taken before this call
     for (int ep = 0; ep < o.epochs; ++ep) {
         // shuffle: i -> (a i + b) mod n with gcd(a, n) = 1
         uint64_t h = host_mix64(o.seed + 0x632be59bd9b4e019ull * (uint64_t)(ep + 1));
         uint64_t a = 1 + (h % (uint64_t)n);
         while (std::gcd(a, (uint64_t)n) != 1) a = a % (uint64_t)n + 1;
         const uint64_t b = host_mix64(h) % (uint64_t)n;
-        for (int64_t i0 = 0; i0 < n; i0 += B, ++step) {
-            const int64_t bsz = std::min(B, n - i0);
-            mlp_gather(c, n, i0, bsz, a, b);
-            mlp_loss_grad(c, bsz, m.bx.as<float>(), m.by.as<float>(), false);
+        for (int64_t i0 = 0; i0 < n; i0 += B) {
+            const int64_t step = (int64_t)steps.size();
             const double frac = total > 1 ? (double)step / (double)(total - 1) : 1.0;
-            const double lr = o.lr * (0.05 + 0.95 * 0.5 * (1.0 + std::cos(epc::kPi * frac)));
-            mlp_adam(c, lr);
+            const double t = (double)(t0 + step + 1);
+            StepParams sp{};
+            sp.i0 = i0;
+            sp.a = a;
+            sp.b = b;
+            sp.lr = (float)(o.lr * (0.05 + 0.95 * 0.5 * (1.0 + std::cos(epc::kPi * frac))));
+            sp.bc1 = (float)(1.0 - std::pow(0.9, t));
+            sp.bc2 = (float)(1.0 - std::pow(0.999, t));
+            steps.push_back(sp);
         }
     }
+    mlp_train_graph(c, steps, B);
     const double L = mlp_dataset_loss(c);
     if (final_loss) *final_loss = L;
 }

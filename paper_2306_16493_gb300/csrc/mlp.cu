@@ -1,7 +1,9 @@
 // Training kernels of the learned q-proposal network (SIMT, FP32 arithmetic on BF16-rounded
 // weights): dense layers with SiLU, the least-squares loss, back-propagation by the chain
-// rule, Adam (Kingma & Ba 2015, Algorithm 1), initialisation and the batch gather of the
-// training loop.  The same dense-layer kernels give the reference forward pass.
+// rule, Adam (Kingma & Ba 2015, Algorithm 1), initialisation and the batch gather.  One
+// training step (gather, forward, back-propagation, Adam) is captured as a CUDA graph and
+// replayed for every step; the step-dependent scalars come from a per-step table indexed by
+// a device counter.  The same dense-layer kernels give the reference forward pass.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -256,32 +258,43 @@ __global__ void k_init(uint64_t seed, float *__restrict__ master) {
     master[i] = (float)((2.0 * u - 1.0) * lim);
 }
 
-// Adam update of every parameter, then the bf16 forward copy.
-__global__ void k_adam(int64_t np, float *__restrict__ master, const float *__restrict__ grad,
-                       float *__restrict__ m, float *__restrict__ v, float lr, float b1, float b2,
-                       float eps, float bc1, float bc2, float *__restrict__ w,
-                       uint16_t *__restrict__ wbf) {
+
+// Training-step kernels driven by a per-step parameter table and a device step counter, so
+// that one captured graph replays every step.
+__global__ void k_gather_step(const StepParams *__restrict__ sp, const int64_t *__restrict__ ctr,
+                              int64_t n, int64_t bsz, const float *__restrict__ X,
+                              const float *__restrict__ Y, float *__restrict__ bx,
+                              float *__restrict__ by) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= bsz) return;
+    const StepParams p = sp[*ctr];
+    // a full batch every step: positions past the end of the permutation wrap around
+    const uint64_t i = (uint64_t)((p.i0 + j) % n);
+    const uint64_t idx = (p.a * i + p.b) % (uint64_t)n;
+    for (int f = 0; f < kIn; ++f) bx[j * kIn + f] = X[idx * kIn + f];
+    by[j] = Y[idx];
+}
+
+__global__ void k_adam_step(const StepParams *__restrict__ sp, const int64_t *__restrict__ ctr,
+                            int64_t np, float *__restrict__ master, const float *__restrict__ grad,
+                            float *__restrict__ m, float *__restrict__ v, float b1, float b2, float eps,
+                            float *__restrict__ w, uint16_t *__restrict__ wbf) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= np) return;
+    const StepParams p = sp[*ctr];
     const float g = grad[i];
     const float mi = b1 * m[i] + (1.f - b1) * g;
     const float vi = b2 * v[i] + (1.f - b2) * g * g;
     m[i] = mi;
     v[i] = vi;
-    const float x = master[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+    const float x = master[i] - p.lr * (mi / p.bc1) / (sqrtf(vi / p.bc2) + eps);
     master[i] = x;
-    store_rounded(i, x, w, wbf);
+    const __nv_bfloat16 bv = __float2bfloat16_rn(x);
+    w[i] = __bfloat162float(bv);
+    wbf[i] = __bfloat16_as_ushort(bv);
 }
 
-__global__ void k_gather(int64_t n, int64_t i0, int64_t bsz, uint64_t a, uint64_t b,
-                         const float *__restrict__ X, const float *__restrict__ Y,
-                         float *__restrict__ bx, float *__restrict__ by) {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= bsz) return;
-    const uint64_t idx = (a * (uint64_t)(i0 + j) + b) % (uint64_t)n;
-    for (int f = 0; f < kIn; ++f) bx[j * kIn + f] = X[idx * kIn + f];
-    by[j] = Y[idx];
-}
+__global__ void k_step_advance(int64_t *ctr) { *ctr += 1; }
 
 MlpState &state(epwi_ctx *c) {
     if (!c->mlp) c->mlp = new MlpState();
@@ -465,27 +478,6 @@ double mlp_loss_grad(epwi_ctx *c, int64_t n, const float *X, const float *Y, boo
     return want_loss ? 0.5 * sum_sq(c, n, a.yhat, Y) / (double)n : 0.0;
 }
 
-void mlp_adam(epwi_ctx *c, double lr) {
-    MlpState &s = state(c);
-    s.step += 1;
-    const double b1 = 0.9, b2 = 0.999;
-    const float bc1 = (float)(1.0 - std::pow(b1, (double)s.step));
-    const float bc2 = (float)(1.0 - std::pow(b2, (double)s.step));
-    k_adam<<<(unsigned)((kNParam + 255) / 256), 256, 0, c->stream>>>(
-        kNParam, s.master.as<float>(), s.grad.as<float>(), s.m.as<float>(), s.v.as<float>(),
-        (float)lr, (float)b1, (float)b2, 1e-8f, bc1, bc2, s.w.as<float>(), s.wbf.as<uint16_t>());
-    EPWI_CHECK_LAUNCH();
-}
-
-void mlp_gather(epwi_ctx *c, int64_t n, int64_t i0, int64_t bsz, uint64_t a, uint64_t b) {
-    MlpState &s = state(c);
-    s.bx.ensure(sizeof(float) * kIn * kMaxBatch);
-    s.by.ensure(sizeof(float) * kMaxBatch);
-    k_gather<<<(unsigned)((bsz + 255) / 256), 256, 0, c->stream>>>(
-        n, i0, bsz, a, b, s.X.as<float>(), s.Y.as<float>(), s.bx.as<float>(), s.by.as<float>());
-    EPWI_CHECK_LAUNCH();
-}
-
 // Mean squared residual (1/2n) sum (yhat - y)^2 over the whole training set.
 double mlp_dataset_loss(epwi_ctx *c) {
     MlpState &s = state(c);
@@ -511,4 +503,62 @@ void mlp_forward_fast(epwi_ctx *c, int64_t n, const float *X, float *y) {
     EPWI_CUDA(cudaMemcpyAsync(&h, s.err.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     EPWI_CUDA(cudaStreamSynchronize(c->stream));
     EPWI_REQUIRE(h == 0, EPWI_ETIMEOUT, "tensor-core inference: a bounded mbarrier wait timed out");
+}
+
+// Replays one captured training step (gather, forward, back-propagation, Adam, counter) for
+// every entry of the step table.
+void mlp_train_graph(epwi_ctx *c, const std::vector<StepParams> &steps, int64_t B) {
+    MlpState &s = state(c);
+    const int64_t n = s.n_train;
+    if (steps.empty() || n == 0) return;
+    s.bx.ensure(sizeof(float) * kIn * kMaxBatch);
+    s.by.ensure(sizeof(float) * kMaxBatch);
+    DevBuf sp, ctr;
+    sp.ensure(sizeof(StepParams) * steps.size());
+    ctr.ensure(sizeof(int64_t));
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    auto cleanup = [&] {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        sp.release();
+        ctr.release();
+    };
+    try {
+        EPWI_CUDA(cudaMemcpyAsync(sp.p, steps.data(), sizeof(StepParams) * steps.size(),
+                                  cudaMemcpyHostToDevice, c->stream));
+        EPWI_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(int64_t), c->stream));
+        // one un-captured pass sizes every buffer of the step
+        mlp_loss_grad(c, B, s.bx.as<float>(), s.by.as<float>(), false);
+        EPWI_CUDA(cudaStreamSynchronize(c->stream));
+        EPWI_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
+        try {
+            k_gather_step<<<(unsigned)((B + 255) / 256), 256, 0, c->stream>>>(
+                sp.as<StepParams>(), ctr.as<int64_t>(), n, B, s.X.as<float>(), s.Y.as<float>(),
+                s.bx.as<float>(), s.by.as<float>());
+            EPWI_CHECK_LAUNCH();
+            mlp_loss_grad(c, B, s.bx.as<float>(), s.by.as<float>(), false);
+            k_adam_step<<<(unsigned)((kNParam + 255) / 256), 256, 0, c->stream>>>(
+                sp.as<StepParams>(), ctr.as<int64_t>(), kNParam, s.master.as<float>(), s.grad.as<float>(),
+                s.m.as<float>(), s.v.as<float>(), 0.9f, 0.999f, 1e-8f, s.w.as<float>(), s.wbf.as<uint16_t>());
+            EPWI_CHECK_LAUNCH();
+            k_step_advance<<<1, 1, 0, c->stream>>>(ctr.as<int64_t>());
+            EPWI_CHECK_LAUNCH();
+        } catch (...) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(c->stream, &g);
+            if (g) cudaGraphDestroy(g);
+            throw;
+        }
+        EPWI_CUDA(cudaStreamEndCapture(c->stream, &graph));
+        EPWI_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+        for (size_t k = 0; k < steps.size(); ++k) EPWI_CUDA(cudaGraphLaunch(exec, c->stream));
+        EPWI_CUDA(cudaStreamSynchronize(c->stream));
+        s.step += (int64_t)steps.size();
+    } catch (...) {
+        cudaStreamSynchronize(c->stream);
+        cleanup();
+        throw;
+    }
+    cleanup();
 }

@@ -6,6 +6,8 @@
 
 #include "epwi_internal.cuh"
 
+#include <vector>
+
 namespace mlp {
 constexpr int kIn = 9;
 constexpr int kHid = 128;
@@ -22,6 +24,14 @@ constexpr int64_t kNParam = ob4 + 1;
 constexpr double kEScale = 0.25;                    // eV, scale of the energy input
 constexpr int kMaxBatch = 1 << 16;                  // rows of one training step
 }  // namespace mlp
+
+// Step-dependent scalars of one training step (graph-replayed training).
+struct StepParams {
+    int64_t i0;                       // first position of the batch in the epoch's permutation
+    uint64_t a, b;                    // permutation i -> (a i + b) mod n
+    float lr, bc1, bc2;               // Adam step size and bias corrections 1 - beta^t
+    float pad;
+};
 
 // Network state kept in the context.
 struct MlpState {
@@ -56,9 +66,8 @@ void mlp_set_master(epwi_ctx *c, const float *host_params);
 void mlp_forward(epwi_ctx *c, int64_t n, const float *X, float *yhat);
 double mlp_loss_grad(epwi_ctx *c, int64_t n, const float *X, const float *Y,
                      bool want_loss = true);
-void mlp_adam(epwi_ctx *c, double lr);
-void mlp_gather(epwi_ctx *c, int64_t n, int64_t i0, int64_t bsz, uint64_t a, uint64_t b);
 double mlp_dataset_loss(epwi_ctx *c);
+void mlp_train_graph(epwi_ctx *c, const std::vector<StepParams> &steps, int64_t B);
 // mlp_tc.cu: the same forward pass on the tensor cores (BF16 activations between layers)
 int mlp_forward_tc(epwi_ctx *c, int64_t n, const float *X, float *y, int *err_dev);
 // tensor-core forward with its error check (throws EPWI_ETIMEOUT)
