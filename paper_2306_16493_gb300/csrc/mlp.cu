@@ -511,6 +511,26 @@ void mlp_train_graph(epwi_ctx *c, const std::vector<StepParams> &steps, int64_t 
     MlpState &s = state(c);
     const int64_t n = s.n_train;
     if (steps.empty() || n == 0) return;
+    // capture and replay on a private stream (the legacy default stream cannot be captured);
+    // it first waits for the work already queued on the context's stream
+    struct StreamSwap {
+        epwi_ctx *c;
+        cudaStream_t saved, own = nullptr;
+        explicit StreamSwap(epwi_ctx *cc) : c(cc), saved(cc->stream) {
+            EPWI_CUDA(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
+            cudaEvent_t ev;
+            EPWI_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+            EPWI_CUDA(cudaEventRecord(ev, saved));
+            EPWI_CUDA(cudaStreamWaitEvent(own, ev, 0));
+            cudaEventDestroy(ev);
+            c->stream = own;
+        }
+        ~StreamSwap() {
+            cudaStreamSynchronize(own);
+            c->stream = saved;
+            cudaStreamDestroy(own);
+        }
+    } swap(c);
     s.bx.ensure(sizeof(float) * kIn * kMaxBatch);
     s.by.ensure(sizeof(float) * kMaxBatch);
     DevBuf sp, ctr;
