@@ -1,4 +1,4 @@
-"""GPU FP64 path vs the FP64 oracle, element by element on seeded inputs (spec bar:
+"""GPU FP64 path vs the FP64 oracle, element by element on seeded inputs (bar:
 1e-10 relative on 1/tau degenerate-group sums and on sigma)."""
 import numpy as np
 import pytest
