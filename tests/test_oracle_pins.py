@@ -381,3 +381,38 @@ def test_wiedemann_franz_degenerate_parabolic_band():
     assert abs(kap[0, 0] / (sig[0, 0] * T) / L0 - 1) < 2e-2
     mott = -(np.pi ** 2 / 2) * O.KB_EVK * kT / EF
     assert abs(S[0, 0] / mott - 1) < 5e-2, (S[0, 0], mott)
+
+
+def test_oracle_matches_stored_golden_values():
+    """Regression pin: the oracle reproduces tests/golden/tiny_6_serta.txt (written by
+    tests/golden/make_golden.py from the oracle) to 1e-9 on degenerate-group sums of 1/tau and
+    on the transport tensors (headroom for platform eigensolver rounding)."""
+    import os
+    from tests.parity import group_sums
+    path = os.path.join(os.path.dirname(__file__), "golden", "tiny_6_serta.txt")
+    rows, meta = [], {}
+    for line in open(path):
+        if line.startswith("#"):
+            continue
+        parts = line.split()
+        if parts[0] in ("mu", "n_pairs", "sigma", "seebeck", "kappa_e"):
+            meta[parts[0]] = np.array([float(x) for x in parts[1:]])
+        else:
+            rows.append((int(parts[0]), int(parts[1]), float(parts[2])))
+    s = synth.tiny_system(1)
+    gr = O.Grids(s, (6, 6, 6))
+    mu = gr.band_centre()
+    assert abs(mu - meta["mu"][0]) < 1e-12
+    T, eta = 300.0, 0.05
+    r = O.serta(gr, T, mu, eta, -np.inf, np.inf)
+    assert r["n_pairs"] == int(meta["n_pairs"][0])
+    ik = np.array([x[0] for x in rows])
+    n = np.array([x[1] for x in rows])
+    ref = group_sums(ik, n, np.array([x[2] for x in rows]), gr.eps)
+    got = group_sums(r["ik"], r["n"], r["inv_tau"], gr.eps)
+    assert ref.keys() == got.keys()
+    assert max(abs(got[k] - v) / abs(v) for k, v in ref.items()) < 1e-9
+    v = gr.velocities(r["ik"], r["n"])
+    sig, S, kap = O.transport_coefficients(s.volume, gr.nk, v, r["inv_tau"], gr.eps[r["ik"], r["n"]], mu, T)
+    for name, t in (("sigma", sig), ("seebeck", S), ("kappa_e", kap)):
+        assert np.linalg.norm(t.ravel() - meta[name]) <= 1e-9 * np.linalg.norm(meta[name]), name
