@@ -253,6 +253,158 @@ void sieve_fill_chunk(epwi_ctx *c, int64_t kp0, int64_t kp1, int *pairs);
 // Processes the work set ws (k-points with their pair lists) chunk by chunk.  In rates mode
 // it writes inv_tau for every state of the work set; in g2 mode (g2out != nullptr) it writes
 // |g|^2 per pair instead.
+namespace {
+
+// One chunk of k-points kp0 .. kp1-1 of a work set: its pair list (chunk-local, q index per
+// pair), the device pair offsets of its k-points (kp_pairs[kp - kp0] - p_off is the first
+// local pair of kp), its global pair index base and its states.
+struct ChunkView {
+    int64_t kp0, kp1;
+    const int *pairs;
+    const int64_t *kp_pairs;
+    int64_t p_off;
+    int64_t np;
+    int64_t g_base;                       // global index of the chunk's first pair
+    int64_t s_base, ns;
+};
+
+struct StageTimers {
+    Ev fill, re, sc, red;
+};
+
+// Tiles, Re->k, Rp->q with rotations and the delta sum, and the reduction of one chunk.
+int64_t run_chunk(epwi_ctx *c, const WorkSet &ws, const ChunkView &cv, double *g2out, double *tout,
+                  int tstride, StageTimers &tm) {
+    const int W = c->nw, Nm = c->nm;
+    const int64_t nrow = (int64_t)c->nRp * Nm * W;
+    const bool tc = c->opt.precision != EPWI_FP64;
+    const size_t state_bytes = tc ? tc_state_bytes(c) : sizeof(double2) * nrow;
+    GridInfo g = make_grid_info(c);
+    const int64_t nkpc = cv.kp1 - cv.kp0;
+    // tiles
+    c->kp_tile.ensure(sizeof(int64_t) * (nkpc + 1));
+    c->scan_tmp.ensure(sizeof(int64_t) * (nkpc + 1));
+    k_tiles_count<<<(unsigned)((nkpc + 255) / 256), 256, 0, c->stream>>>(
+        nkpc, cv.kp_pairs, cv.p_off, c->scan_tmp.as<int64_t>());
+    EPWI_CHECK_LAUNCH();
+    int64_t nt = 0;
+    scan_exclusive_i64(c, c->scan_tmp.as<int64_t>(), c->kp_tile.as<int64_t>(), nkpc, &nt);
+    c->tiles.ensure(sizeof(int4) * (nt + 1));
+    c->tile_part.ensure(sizeof(double) * epc::kMaxW * (nt + 1));
+    k_tiles_fill<<<(unsigned)((nkpc + 255) / 256), 256, 0, c->stream>>>(
+        nkpc, cv.kp_pairs, cv.p_off, c->kp_tile.as<int64_t>(), c->tiles.as<int4>());
+    EPWI_CHECK_LAUNCH();
+    cudaEventRecord(tm.fill.e[1], c->stream);
+    // Re->k
+    c->ghat.ensure(state_bytes * (cv.ns + 1));
+    RestageArgs ra;
+    ra.g = g;
+    ra.W = W;
+    ra.Nm = Nm;
+    ra.nRe = c->nRe;
+    ra.nRp = c->nRp;
+    ra.nrow = (int)nrow;
+    ra.Re = c->Re.as<int>();
+    ra.gw64 = c->gw64.as<double2>();
+    ra.gw32 = c->gw32.as<float2>();
+    ra.ph64 = c->ph64.as<double2>();
+    ra.ph32 = c->ph32.as<float2>();
+    ra.V64 = c->V.as<double2>();
+    ra.V32 = c->V32.as<float2>();
+    ra.nkp = (int)nkpc;
+    ra.kpts = ws.kpts + cv.kp0;
+    ra.kp_state = ws.kp_state + cv.kp0;
+    ra.s_base = cv.s_base;
+    ra.win_lo = c->win_lo.as<int>();
+    ra.win_n = c->win_n.as<int>();
+    ra.ovr_lo = ws.ovr_lo;
+    ra.ovr_nsel = ws.ovr_nsel;
+    ra.ghat64 = c->ghat.as<double2>();
+    ra.ghat_raw = c->ghat.p;
+    ra.precision = c->opt.precision;
+    ra.nstates_chunk = cv.ns;
+    cudaEventRecord(tm.re.e[0], c->stream);
+    if (tc) tc_restage(c, ra);
+    else fp64_restage(ra, W, c->stream);
+    cudaEventRecord(tm.re.e[1], c->stream);
+    // Rp->q + rotations + delta sum
+    ScatterArgs sa;
+    sa.g = g;
+    sa.W = W;
+    sa.Nm = Nm;
+    sa.nRp = c->nRp;
+    sa.nrow = (int)nrow;
+    sa.Rp = c->Rp.as<int>();
+    sa.ph64 = c->ph64.as<double2>();
+    sa.ph32 = c->ph32.as<float2>();
+    sa.tiles = c->tiles.as<int4>();
+    sa.kpts = ws.kpts + cv.kp0;
+    sa.kp_state = ws.kp_state + cv.kp0;
+    sa.s_base = cv.s_base;
+    sa.win_lo = c->win_lo.as<int>();
+    sa.win_n = c->win_n.as<int>();
+    sa.ovr_lo = ws.ovr_lo;
+    sa.ovr_nsel = ws.ovr_nsel;
+    sa.pairs = cv.pairs;
+    sa.ghat64 = c->ghat.as<double2>();
+    sa.ghat_raw = c->ghat.p;
+    sa.V64 = c->V.as<double2>();
+    sa.V32 = c->V32.as<float2>();
+    sa.u64 = c->u.as<double2>();
+    sa.u32 = c->u32.as<float2>();
+    sa.eps = c->eps.as<double>();
+    sa.hw = c->hw.as<double>();
+    sa.focc = g2out ? nullptr : c->focc.as<double>();
+    sa.nocc = g2out ? nullptr : c->nocc.as<double>();
+    sa.omega_min = c->opt.omega_min_eV;
+    sa.eta = c->eta > 0 ? c->eta : 1.0;
+    sa.ceta = c->opt.sieve_c * c->eta;
+    sa.tile_part = c->tile_part.as<double>();
+    sa.g2out = g2out;
+    sa.g2_base = cv.g_base;
+    sa.pair_w = ws.pair_w ? ws.pair_w + cv.g_base : nullptr;
+    sa.tout = tout;
+    sa.tstride = tstride;
+    sa.precision = c->opt.precision;
+    sa.nstates_chunk = cv.ns;
+    sa.nsel_max = 1;
+    if (ws.ovr_nsel >= 0) {
+        sa.nsel_max = ws.ovr_nsel;
+    } else {
+        for (int64_t p = cv.kp0; p < cv.kp1; ++p)
+            sa.nsel_max = std::max<int64_t>(sa.nsel_max, ws.h_kp_state[p + 1] - ws.h_kp_state[p]);
+    }
+    cudaEventRecord(tm.sc.e[0], c->stream);
+    if (tc) tc_scatter(c, sa, nt);
+    else fp64_scatter(sa, nt, c->stream);
+    cudaEventRecord(tm.sc.e[1], c->stream);
+    // reduce
+    cudaEventRecord(tm.red.e[0], c->stream);
+    if (!g2out && !tout && nkpc > 0) {
+        const double pref = 2.0 * epc::kPi / epc::kHbarEVs / (double)c->nk /
+                            (sqrt(epc::kPi) * c->eta);
+        k_reduce_tiles<<<(unsigned)((nkpc + 127) / 128), 128, 0, c->stream>>>(
+            nkpc, ws.kpts + cv.kp0, c->win_n.as<int>(), ws.kp_state + cv.kp0, c->kp_tile.as<int64_t>(),
+            c->tile_part.as<double>(), pref, c->inv_tau.as<double>());
+        EPWI_CHECK_LAUNCH();
+    }
+    cudaEventRecord(tm.red.e[1], c->stream);
+    EPWI_CUDA(cudaStreamSynchronize(c->stream));
+    if (tc && nt > 0)
+        EPWI_REQUIRE(tc_check_error(c) == 0, EPWI_ETIMEOUT,
+                     "tensor-core kernel: a bounded mbarrier wait timed out");
+    c->stats.ms_sieve += tm.fill.ms();
+    c->stats.ms_restage += tm.re.ms();
+    c->stats.ms_scatter += tm.sc.ms();
+    c->stats.ms_reduce += tm.red.ms();
+    return nt;
+}
+
+}  // namespace
+
+// Processes the work set ws (k-points with their pair lists) chunk by chunk.  In rates mode
+// it writes inv_tau for every state of the work set; in g2 mode (g2out != nullptr) it writes
+// |g|^2 per pair instead.
 void process_workset(epwi_ctx *c, const WorkSet &ws, double *g2out, double *tout, int tstride) {
     const int W = c->nw, Nm = c->nm;
     const int64_t nrow = (int64_t)c->nRp * Nm * W;
@@ -263,8 +415,7 @@ void process_workset(epwi_ctx *c, const WorkSet &ws, double *g2out, double *tout
     const size_t state_bytes = tc ? tc_state_bytes(c) : sizeof(double2) * nrow;
     const int64_t max_states = std::max<int64_t>(1, (int64_t)((size_t(3) << 30) / state_bytes));
     const int64_t kp_cap = c->opt.kpoint_chunk > 0 ? c->opt.kpoint_chunk : (int64_t)1 << 40;
-    GridInfo g = make_grid_info(c);
-    Ev ev_fill, ev_re, ev_sc, ev_red;
+    StageTimers tm;
     int64_t kp0 = 0, nchunks = 0, ntiles_total = 0;
     while (kp0 < ws.nkp) {
         int64_t kp1 = kp0 + 1;
@@ -272,136 +423,23 @@ void process_workset(epwi_ctx *c, const WorkSet &ws, double *g2out, double *tout
                ws.h_kp_pairs[kp1 + 1] - ws.h_kp_pairs[kp0] <= max_pairs &&
                ws.h_kp_state[kp1 + 1] - ws.h_kp_state[kp0] <= max_states)
             ++kp1;
-        const int64_t nkpc = kp1 - kp0;
-        const int64_t p_base = ws.h_kp_pairs[kp0];
-        const int64_t np = ws.h_kp_pairs[kp1] - p_base;
-        const int64_t s_base = ws.h_kp_state[kp0];
-        const int64_t ns = ws.h_kp_state[kp1] - s_base;
-        // 1. pairs of the chunk
-        cudaEventRecord(ev_fill.e[0], c->stream);
-        const int *pairs = ws.pairs_dev ? ws.pairs_dev + p_base : nullptr;
-        if (!pairs) {
-            c->pairs.ensure(sizeof(int) * (np + 1));
+        ChunkView cv;
+        cv.kp0 = kp0;
+        cv.kp1 = kp1;
+        cv.p_off = ws.h_kp_pairs[kp0];
+        cv.g_base = cv.p_off;
+        cv.np = ws.h_kp_pairs[kp1] - cv.p_off;
+        cv.s_base = ws.h_kp_state[kp0];
+        cv.ns = ws.h_kp_state[kp1] - cv.s_base;
+        cv.kp_pairs = ws.kp_pairs + kp0;
+        cudaEventRecord(tm.fill.e[0], c->stream);
+        cv.pairs = ws.pairs_dev ? ws.pairs_dev + cv.p_off : nullptr;
+        if (!cv.pairs) {
+            c->pairs.ensure(sizeof(int) * (cv.np + 1));
             sieve_fill_chunk(c, kp0, kp1, c->pairs.as<int>());
-            pairs = c->pairs.as<int>();
+            cv.pairs = c->pairs.as<int>();
         }
-        // tiles
-        c->kp_tile.ensure(sizeof(int64_t) * (nkpc + 1));
-        c->scan_tmp.ensure(sizeof(int64_t) * (nkpc + 1));
-        k_tiles_count<<<(unsigned)((nkpc + 255) / 256), 256, 0, c->stream>>>(
-            nkpc, ws.kp_pairs + kp0, p_base, c->scan_tmp.as<int64_t>());
-        EPWI_CHECK_LAUNCH();
-        int64_t nt = 0;
-        scan_exclusive_i64(c, c->scan_tmp.as<int64_t>(), c->kp_tile.as<int64_t>(), nkpc, &nt);
-        c->tiles.ensure(sizeof(int4) * (nt + 1));
-        c->tile_part.ensure(sizeof(double) * epc::kMaxW * (nt + 1));
-        k_tiles_fill<<<(unsigned)((nkpc + 255) / 256), 256, 0, c->stream>>>(
-            nkpc, ws.kp_pairs + kp0, p_base, c->kp_tile.as<int64_t>(), c->tiles.as<int4>());
-        EPWI_CHECK_LAUNCH();
-        cudaEventRecord(ev_fill.e[1], c->stream);
-        // 2. Re->k
-        c->ghat.ensure(state_bytes * (ns + 1));
-        RestageArgs ra;
-        ra.g = g;
-        ra.W = W;
-        ra.Nm = Nm;
-        ra.nRe = c->nRe;
-        ra.nRp = c->nRp;
-        ra.nrow = (int)nrow;
-        ra.Re = c->Re.as<int>();
-        ra.gw64 = c->gw64.as<double2>();
-        ra.gw32 = c->gw32.as<float2>();
-        ra.ph64 = c->ph64.as<double2>();
-        ra.ph32 = c->ph32.as<float2>();
-        ra.V64 = c->V.as<double2>();
-        ra.V32 = c->V32.as<float2>();
-        ra.nkp = (int)nkpc;
-        ra.kpts = ws.kpts + kp0;
-        ra.kp_state = ws.kp_state + kp0;
-        ra.s_base = s_base;
-        ra.win_lo = c->win_lo.as<int>();
-        ra.win_n = c->win_n.as<int>();
-        ra.ovr_lo = ws.ovr_lo;
-        ra.ovr_nsel = ws.ovr_nsel;
-        ra.ghat64 = c->ghat.as<double2>();
-        ra.ghat_raw = c->ghat.p;
-        ra.precision = c->opt.precision;
-        ra.nstates_chunk = ns;
-        cudaEventRecord(ev_re.e[0], c->stream);
-        if (tc) tc_restage(c, ra);
-        else fp64_restage(ra, W, c->stream);
-        cudaEventRecord(ev_re.e[1], c->stream);
-        // 3. Rp->q + rotations + delta sum
-        ScatterArgs sa;
-        sa.g = g;
-        sa.W = W;
-        sa.Nm = Nm;
-        sa.nRp = c->nRp;
-        sa.nrow = (int)nrow;
-        sa.Rp = c->Rp.as<int>();
-        sa.ph64 = c->ph64.as<double2>();
-        sa.ph32 = c->ph32.as<float2>();
-        sa.tiles = c->tiles.as<int4>();
-        sa.kpts = ws.kpts + kp0;
-        sa.kp_state = ws.kp_state + kp0;
-        sa.s_base = s_base;
-        sa.win_lo = c->win_lo.as<int>();
-        sa.win_n = c->win_n.as<int>();
-        sa.ovr_lo = ws.ovr_lo;
-        sa.ovr_nsel = ws.ovr_nsel;
-        sa.pairs = pairs;
-        sa.ghat64 = c->ghat.as<double2>();
-        sa.ghat_raw = c->ghat.p;
-        sa.V64 = c->V.as<double2>();
-        sa.V32 = c->V32.as<float2>();
-        sa.u64 = c->u.as<double2>();
-        sa.u32 = c->u32.as<float2>();
-        sa.eps = c->eps.as<double>();
-        sa.hw = c->hw.as<double>();
-        sa.focc = g2out ? nullptr : c->focc.as<double>();
-        sa.nocc = g2out ? nullptr : c->nocc.as<double>();
-        sa.omega_min = c->opt.omega_min_eV;
-        sa.eta = c->eta > 0 ? c->eta : 1.0;
-        sa.ceta = c->opt.sieve_c * c->eta;
-        sa.tile_part = c->tile_part.as<double>();
-        sa.g2out = g2out;
-        sa.g2_base = p_base;
-        sa.pair_w = ws.pair_w ? ws.pair_w + p_base : nullptr;
-        sa.tout = tout;
-        sa.tstride = tstride;
-        sa.precision = c->opt.precision;
-        sa.nstates_chunk = ns;
-        sa.nsel_max = 1;
-        if (ws.ovr_nsel >= 0) {
-            sa.nsel_max = ws.ovr_nsel;
-        } else {
-            for (int64_t p = kp0; p < kp1; ++p)
-                sa.nsel_max = std::max<int64_t>(sa.nsel_max, ws.h_kp_state[p + 1] - ws.h_kp_state[p]);
-        }
-        cudaEventRecord(ev_sc.e[0], c->stream);
-        if (tc) tc_scatter(c, sa, nt);
-        else fp64_scatter(sa, nt, c->stream);
-        cudaEventRecord(ev_sc.e[1], c->stream);
-        // 4. reduce
-        cudaEventRecord(ev_red.e[0], c->stream);
-        if (!g2out && !tout && nkpc > 0) {
-            const double pref = 2.0 * epc::kPi / epc::kHbarEVs / (double)c->nk /
-                                (sqrt(epc::kPi) * c->eta);
-            k_reduce_tiles<<<(unsigned)((nkpc + 127) / 128), 128, 0, c->stream>>>(
-                nkpc, ws.kpts + kp0, c->win_n.as<int>(), ws.kp_state + kp0, c->kp_tile.as<int64_t>(),
-                c->tile_part.as<double>(), pref, c->inv_tau.as<double>());
-            EPWI_CHECK_LAUNCH();
-        }
-        cudaEventRecord(ev_red.e[1], c->stream);
-        EPWI_CUDA(cudaStreamSynchronize(c->stream));
-        if (tc && nt > 0)
-            EPWI_REQUIRE(tc_check_error(c) == 0, EPWI_ETIMEOUT,
-                         "tensor-core kernel: a bounded mbarrier wait timed out");
-        c->stats.ms_sieve += ev_fill.ms();
-        c->stats.ms_restage += ev_re.ms();
-        c->stats.ms_scatter += ev_sc.ms();
-        c->stats.ms_reduce += ev_red.ms();
-        ntiles_total += nt;
+        ntiles_total += run_chunk(c, ws, cv, g2out, tout, tstride, tm);
         ++nchunks;
         kp0 = kp1;
     }
