@@ -16,6 +16,7 @@ no blocking or fusion beyond what the equations state:
   {U(k+q)[(g P^el U^dag(k)) P^ph]} u(q)                                  (Sec. II B Eq. 7; Sec. III C Eq. 16)
 * SERTA 1/tau_nk with Gaussian delta functions                           (Sec. II C, Eq. 10)
 * sigma, mobility                                                        (Sec. II C, Eqs. 12, 15)
+* iterative BTE for the mean free paths F                                (Sec. II C, iteration eq.)
 * effective-process sieve by energy conservation                         (Sec. III A)
 
 Equation numbers count the numbered displays of the paper in order (Eq. 1 is the
@@ -209,14 +210,14 @@ def sieve_k(gr: Grids, ik: int, bands_n, eta, c=6.0):
     return iq[ok]
 
 
-def pair_terms_k(gr: Grids, ik: int, bands_n, T, mu, eta, c, q_list) -> np.ndarray:
-    """The summand of Eq. 10 for one k before the q and mode sums:
-    t[q, nu, n] = sum_m |g^nu_mn(k,q)|^2 [(N + f) delta(x+) + (1 + N - f) delta(x-)] in eV
-    (Sec. II C, Eq. 10), for the q in ``q_list`` and the bands ``bands_n``."""
+def pair_terms_full_k(gr: Grids, ik: int, bands_n, T, mu, eta, c, q_list) -> np.ndarray:
+    """The summand of Eq. 10 for one k, resolved in q, mode and final band:
+    t[q, nu, m, n] = |g^nu_mn(k,q)|^2 [(N + f_m) delta(x+) + (1 + N - f_m) delta(x-)] in eV
+    (Sec. II C, Eq. 10), for the q in ``q_list`` and the initial bands ``bands_n``."""
     bands_n = np.asarray(bands_n)
     q_list = np.asarray(q_list, dtype=np.int64)
     if len(q_list) == 0:
-        return np.zeros((0, gr.hw.shape[1], len(bands_n)))
+        return np.zeros((0, gr.hw.shape[1], gr.eps.shape[1], len(bands_n)))
     ikq = kq_index(ik, q_list, gr.ngrid)
     g = g_matrix(gr.sys, gr.frac[ik], gr.frac[q_list], gr.V[ik][:, bands_n],
                  gr.V[ikq], gr.u[q_list])                          # [q, nu, m, n]
@@ -231,8 +232,13 @@ def pair_terms_k(gr: Grids, ik: int, bands_n, T, mu, eta, c, q_list) -> np.ndarr
     occ_abs = N[:, :, None, None] + fm[:, None, :, None]
     occ_emi = 1.0 + N[:, :, None, None] - fm[:, None, :, None]
     term = g2 * (occ_abs * delta_gauss(x_abs, eta, c) + occ_emi * delta_gauss(x_emi, eta, c))
-    term = term * keep[:, :, None, None]
-    return term.sum(axis=2)
+    return term * keep[:, :, None, None]
+
+
+def pair_terms_k(gr: Grids, ik: int, bands_n, T, mu, eta, c, q_list) -> np.ndarray:
+    """The summand of Eq. 10 for one k before the q and mode sums:
+    t[q, nu, n] = sum_m |g^nu_mn(k,q)|^2 [(N + f) delta(x+) + (1 + N - f) delta(x-)] in eV."""
+    return pair_terms_full_k(gr, ik, bands_n, T, mu, eta, c, q_list).sum(axis=2)
 
 
 def inv_tau_k(gr: Grids, ik: int, bands_n, T, mu, eta, c=6.0, q_list=None, q_weights=None):
@@ -307,6 +313,88 @@ def transport_coefficients(volume_A3, nk, v, inv_tau, eps, mu, T):
     m0 = np.einsum("s,sa,sb->ab", w, v, v)
     m1 = np.einsum("s,sa,sb->ab", w * de_J, v, v)
     m2 = np.einsum("s,sa,sb->ab", w * de_J ** 2, v, v)
+    sigma = 2.0 * E_CHARGE ** 2 / vol * m0
+    nu = 2.0 * (-E_CHARGE) / (T * vol) * m1
+    kappa0 = 2.0 / (T * vol) * m2
+    seebeck = np.linalg.solve(sigma, nu)
+    kappa_e = kappa0 - T * nu @ seebeck
+    return sigma, seebeck, kappa_e
+
+
+# ------------------------------------------------------------------- iterative BTE
+def ibte(gr: Grids, T, mu, eta, emin, emax, c=6.0, max_iter=200, tol=1e-12):
+    """Iterative solution of the linearised BTE for the mean free paths F (Sec. II C, the
+    iteration equation after Eq. 10):
+
+        F^0_nk = v_nk tau_nk,
+        F^{i+1}_nk = F^0_nk + tau_nk sum_{q p m} (Gamma^+ + Gamma^-)_{nk -> m k+q} F^i_{m k+q}.
+
+    The paper's Gamma are the equilibrium transition rates with f_nk (1 - f_nk) divided out.
+    By detailed balance, f_n (1 - f_m) N = f_n (1 - f_n) (N + f_m) on the absorption shell and
+    f_n (1 - f_m)(1 + N) = f_n (1 - f_n)(1 + N - f_m) on the emission shell, so Gamma^+ and
+    Gamma^- are exactly the two terms of the SERTA summand of Eq. 10 for the final state
+    (m, k+q) and mode p, and 1/tau_nk is the sum of Gamma over all final states.
+
+    The states are those of the energy window (the order of ``serta``).  Final states outside
+    the window keep their share of 1/tau but carry F = 0 in the in-scattering sum.  The
+    iteration stops when max |F^{i+1} - F^i| <= tol max |F^{i+1}| or after ``max_iter``
+    applications.  Returns dict(ik, n, inv_tau, A (CSR, s^-1, rows = initial states, columns =
+    final states), F0, F, iters)."""
+    import scipy.sparse as sp
+
+    ik_all, n_all = gr.window_states(emin, emax)
+    ns = len(ik_all)
+    pos = -np.ones(gr.eps.shape, np.int64)
+    pos[ik_all, n_all] = np.arange(ns)
+    pref = 2.0 * math.pi / HBAR_EVS / gr.nk
+    inv_tau = np.zeros(ns)
+    rows, cols, vals = [], [], []
+    for ik in np.unique(ik_all):
+        nsel = n_all[ik_all == ik]
+        q = sieve_k(gr, int(ik), nsel, eta, c)
+        if len(q) == 0:
+            continue
+        t = pair_terms_full_k(gr, int(ik), nsel, T, mu, eta, c, q).sum(axis=1) * pref   # [q, m, n]
+        i_rows = pos[ik, nsel]
+        inv_tau[i_rows] = t.sum(axis=(0, 1))
+        j = pos[kq_index(int(ik), q, gr.ngrid)]                     # [q, m] final-state index
+        qi, m = np.nonzero(j >= 0)
+        for a, r in enumerate(i_rows):
+            rows.append(np.full(len(qi), r))
+            cols.append(j[qi, m])
+            vals.append(t[qi, m, a])
+    cat = (lambda x, dt: np.concatenate(x).astype(dt) if x else np.zeros(0, dt))
+    A = sp.csr_matrix((cat(vals, float), (cat(rows, np.int64), cat(cols, np.int64))), shape=(ns, ns))
+    v = gr.velocities(ik_all, n_all)
+    ok = inv_tau > 0
+    tau = np.where(ok, 1.0 / np.where(ok, inv_tau, 1.0), 0.0)
+    F0 = tau[:, None] * v
+    F = F0.copy()
+    iters = 0
+    for iters in range(1, max_iter + 1):
+        Fn = F0 + tau[:, None] * (A @ F)
+        change = np.abs(Fn - F).max() if ns else 0.0
+        scale = np.abs(Fn).max() if ns else 0.0
+        F = Fn
+        if change <= tol * scale:
+            break
+    return dict(ik=ik_all, n=n_all, inv_tau=inv_tau, A=A, F0=F0, F=F, iters=iters)
+
+
+def transport_from_F(volume_A3, nk, v, F, eps, mu, T):
+    """sigma, Seebeck S and kappa_e from the mean free paths F (Sec. II C, Eqs. 12-14):
+        m_p[a, b] = sum (e - mu)^p v_a F_b (-df/de),
+        sigma = (2 e^2 / (N_k V)) m_0,  nu = sigma S = (2 (-e) / (T V N_k)) m_1,
+        kappa_0 = (2 / (T V N_k)) m_2,  S = sigma^-1 nu,  kappa_e = kappa_0 - T nu sigma^-1 nu.
+    With F = v tau this is ``transport_coefficients``."""
+    f = fermi(eps, mu, T)
+    kT_J = KB_EVK * T * E_CHARGE
+    w = f * (1.0 - f) / kT_J
+    de_J = (np.asarray(eps, float) - mu) * E_CHARGE
+    vol = nk * volume_A3 * 1e-30
+    m0 = np.einsum("s,sa,sb->ab", w, v, F)
+    m1 = np.einsum("s,sa,sb->ab", w * de_J, v, F)
+    m2 = np.einsum("s,sa,sb->ab", w * de_J ** 2, v, F)
     sigma = 2.0 * E_CHARGE ** 2 / vol * m0
     nu = 2.0 * (-E_CHARGE) / (T * vol) * m1
     kappa0 = 2.0 / (T * vol) * m2

@@ -351,6 +351,29 @@ def si_like_system(seed: int = 3) -> System:
                        n_valence=4, gap_ev=1.1)
 
 
+def einstein_system(t_ev: float = 0.5, a: float = 3.0, spring: float = 5.0,
+                    g_ev_a: float = 0.05) -> System:
+    """Isotropic-scattering test crystal: simple cubic, one s-like Wannier function with
+    nearest-neighbour hopping -t (eps(k) = -2t sum_i cos 2 pi k_i), one atom of 27 amu held by
+    an on-site spring only (three degenerate, dispersionless modes), and a coupling that is
+    local in both lattice vectors (only Re = Rp = 0, the same real value for each Cartesian
+    direction).  3^3 R-sets with unit weights.  No random numbers."""
+    R, w = r_cube(1, False)
+    nR = len(R)
+    H = np.zeros((nR, 1, 1), complex)
+    for i, v in enumerate(R.tolist()):
+        if sum(abs(x) for x in v) == 1:
+            H[i, 0, 0] = -t_ev
+    i0 = int(np.nonzero((R == 0).all(axis=1))[0][0])
+    Phi = np.zeros((nR, 3, 3))
+    Phi[i0] = spring * np.eye(3)
+    g = np.zeros((nR, nR, 3, 1, 1), complex)
+    g[i0, i0, :, 0, 0] = g_ev_a
+    return System(name="einstein", lattice=a * np.eye(3), tau=np.zeros((1, 3)),
+                  mass=np.array([27.0]), nw=1, Re=R.copy(), we=w.copy(), H=H, Rp=R.copy(),
+                  wp=w.copy(), Phi=Phi, g=g, n_valence=0, seed=0)
+
+
 def batch_system(s: int) -> tuple[System, int]:
     """System s (0..63) of the uneven batch: s = 16 a + 4 b + c.
 
