@@ -116,6 +116,22 @@ typedef struct {
     double proposal_flops;      /* importance sampling: network flops (2 per multiply-add) */
 } epwi_stats;
 
+/* Statistics of the last epwi_ibte. */
+typedef struct {
+    int64_t n_states;           /* states (n,k) in the window */
+    int64_t n_pairs;            /* (k,q) pairs kept by the sieve */
+    int64_t n_entries;          /* stored Gamma values: sum over pairs of n_window(k) x
+                                   n_window(k+q) */
+    int32_t entry_bytes;        /* 8 (FP64 path) or 4 (split-precision paths) */
+    int32_t iters;              /* iterations done */
+    double change;              /* max |F^i - F^(i-1)| / max |F^i| after the last iteration */
+    double ms_rates;            /* window, sieve, interpolation, 1/tau and the Gamma capture */
+    double ms_iterate;          /* every iteration: step kernels and convergence reads */
+    double ms_step;             /* mean device time of one step kernel */
+    double bytes_per_step;      /* algorithmic bytes of one step: q list, Gamma, F0, tau, F
+                                   read and written once */
+} epwi_ibte_stats;
+
 /* Fills *opt with the defaults listed above. */
 void epwi_default_options(epwi_options *opt);
 
@@ -406,6 +422,37 @@ epwi_status epwi_batch_get_stats(epwi_batch *batch, epwi_batch_stats *out);
  * Outputs are row-major 3x3 (any pointer may be NULL).  The three moments come from one
  * fixed-order FP64 device reduction.  Errors: ESTATE; ENUMERIC (singular sigma). */
 epwi_status epwi_transport(epwi_ctx *ctx, double sigma[9], double seebeck[9], double kappa_e[9]);
+
+/* Iterative Boltzmann transport equation (Sec. II C, the iteration equation after Eq. 10).
+ *   F^0_nk = v_nk tau_nk;
+ *   F^(i+1)_nk = F^0_nk + tau_nk sum_{q p m} Gamma_{nk -> m,k+q} F^i_{m,k+q}.
+ * Gamma is the equilibrium transition rate with f_nk (1 - f_nk) divided out.  By detailed
+ * balance it equals the summand of Eq. 10 for the final state (m, k+q) and mode p, summed
+ * over the two signs.  1/tau_nk is therefore the sum of Gamma over all final states.
+ *
+ * The call runs what epwi_scatter_rates runs for (T, mu, smear, emin, emax), which also
+ * leaves 1/tau for epwi_get_rates and epwi_transport.  During the interpolation it stores
+ * Gamma for final states inside the window, as one block [n in window(k)][m in
+ * window(k+q)] per sieved pair, in pair order.  Blocks are FP64 on the FP64 path and FP32
+ * on the split paths.  Final states outside the window keep their share of 1/tau and carry
+ * F = 0.  States with 1/tau = 0 have F = 0.
+ *
+ * The step is one kernel per iteration: one block per window k-point, fixed-order sums, so
+ * the result is deterministic.  It stops when max |F^(i+1) - F^i| <= tol max |F^(i+1)|, or
+ * after max_iter steps (max_iter = 0: F = F^0).
+ *
+ * iters, change: steps done and the last relative change (either may be NULL).
+ * Errors: ESTATE (no eigs); EINVAL (T, smear, window, max_iter < 0, tol < 0); ENOMEM. */
+epwi_status epwi_ibte(epwi_ctx *ctx, double T, double mu, double smear, double emin, double emax,
+                      int32_t max_iter, double tol, int32_t *iters, double *change);
+/* Mean free paths F [n_states][3] in m after epwi_ibte, in the state order of epwi_get_rates.
+ * Errors: ESTATE; ETOOSMALL (capacity below n_states). */
+epwi_status epwi_get_mfp(epwi_ctx *ctx, int64_t capacity, double *F);
+/* sigma, Seebeck and kappa_e from F (Sec. II C, Eqs. 12-14): the moments of epwi_transport
+ * with tau v_a v_b replaced by v_a F_b (a full 3x3 tensor; v_a is the row).  Errors: ESTATE;
+ * ENUMERIC. */
+epwi_status epwi_ibte_transport(epwi_ctx *ctx, double sigma[9], double seebeck[9], double kappa_e[9]);
+epwi_status epwi_get_ibte_stats(epwi_ctx *ctx, epwi_ibte_stats *out);
 
 /* Number of kernels this library has launched in the process so far (all contexts). */
 int64_t epwi_kernel_launches(void);

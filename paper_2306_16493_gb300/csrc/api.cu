@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <chrono>
 #include <cstring>
 #include <map>
 #include <new>
@@ -401,59 +402,172 @@ epwi_status epwi_find_mu(epwi_ctx *c, double T, double n_c, int32_t nv, double *
     });
 }
 
+static void solve3(const double A_[9], const double B_[9], double X[9]);
+
+namespace {
+
+// Window, sieve count, occupation tables and the work set of a rates call (Sec. III A);
+// 1/tau is zeroed.
+WorkSet begin_rates(epwi_ctx *c, double T, double mu, double eta, double emin, double emax) {
+    require_eigs(c);
+    EPWI_REQUIRE(T > 0 && eta > 0 && std::isfinite(mu) && !(emin > emax), EPWI_EINVAL,
+                 "need T > 0, smear > 0, finite mu and emin <= emax");
+    c->have_rates = c->have_sigma = c->have_is = c->have_ibte = false;
+    c->T = T;
+    c->mu = mu;
+    c->eta = eta;
+    c->emin = emin;
+    c->emax = emax;
+    std::memset(&c->stats, 0, sizeof(c->stats));
+    c->stats.precision = c->opt.precision;
+    c->stats.ms_eigs = c->ms_eigs;
+    EPWI_CUDA(cudaDeviceGetAttribute(&c->stats.sm_count, cudaDevAttrMultiProcessorCount, c->device));
+    cudaEvent_t e0, e1;
+    EPWI_CUDA(cudaEventCreate(&e0));
+    EPWI_CUDA(cudaEventCreate(&e1));
+    cudaEventRecord(e0, c->stream);
+    build_window(c);
+    sieve_count(c);
+    cudaEventRecord(e1, c->stream);
+    EPWI_CUDA(cudaStreamSynchronize(c->stream));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->stats.ms_sieve = ms;
+    occupation_tables(c);
+    if (c->nstates > 0)
+        EPWI_CUDA(cudaMemsetAsync(c->inv_tau.p, 0, sizeof(double) * c->nstates, c->stream));
+    WorkSet ws;
+    ws.nkp = c->nkp;
+    ws.kpts = c->kpts.as<int>();
+    ws.kp_state = c->kp_state.as<int64_t>();
+    ws.kp_pairs = c->kp_pairs.as<int64_t>();
+    ws.h_kp_pairs = c->h_kp_pairs;
+    ws.h_kp_state.resize(c->nkp + 1);
+    EPWI_CUDA(cudaMemcpyAsync(ws.h_kp_state.data(), c->kp_state.p, sizeof(int64_t) * (c->nkp + 1),
+                              cudaMemcpyDeviceToHost, c->stream));
+    EPWI_CUDA(cudaStreamSynchronize(c->stream));
+    return ws;
+}
+
+void end_rates(epwi_ctx *c) {
+    c->stats.n_kpoints = c->nkp;
+    c->stats.n_states = c->nstates;
+    c->stats.n_pairs = c->npairs;
+    c->stats.restage_bytes = (int64_t)c->stats.n_chunks * c->nRe * c->nRp * c->nm * c->nw *
+                             c->nw * (c->opt.precision == EPWI_FP64 ? 16 : 8);
+    c->stats.scatter_flops = 8.0 * c->nRp * c->nm * c->nw * (double)c->npairs *
+                             ((double)c->nstates / std::max<int64_t>(1, c->nkp));
+    c->have_rates = true;
+}
+
+// sigma, S and kappa_e from the three energy moments (Sec. II C, Eqs. 12-14)
+void finish_transport(epwi_ctx *c, const double (&m)[3][9], double *sigma, double *seebeck,
+                      double *kappa_e) {
+    const double e = epc::kECharge;
+    const double kT_J = epc::kKbEVK * c->T * e;
+    const double vol = (double)c->nk * c->volume * 1e-30;
+    const double pref = 2.0 * e * e / (vol * kT_J);   // sigma per unit of the zeroth moment
+    double sig[9], nu[9], k0[9];
+    for (int i = 0; i < 9; ++i) {
+        sig[i] = pref * m[0][i];
+        nu[i] = -pref * m[1][i] / c->T;                // q = -e: electrons
+        k0[i] = pref * m[2][i] / c->T;
+    }
+    double S[9];
+    solve3(sig, nu, S);
+    for (int i = 0; i < 9; ++i) {
+        EPWI_REQUIRE(std::isfinite(sig[i]) && std::isfinite(S[i]), EPWI_ENUMERIC, "non-finite result");
+        if (sigma) sigma[i] = sig[i];
+        if (seebeck) seebeck[i] = S[i];
+    }
+    if (kappa_e)
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double t = 0;
+                for (int k = 0; k < 3; ++k) t += nu[i * 3 + k] * S[k * 3 + j];
+                kappa_e[i * 3 + j] = k0[i * 3 + j] - c->T * t;
+            }
+}
+
+}  // namespace
+
 epwi_status epwi_scatter_rates(epwi_ctx *c, double T, double mu, double eta, double emin,
                                double emax, int64_t *n_states, int64_t *n_pairs) {
     return guard(c, [&] {
-        require_eigs(c);
-        EPWI_REQUIRE(T > 0 && eta > 0 && std::isfinite(mu) && !(emin > emax), EPWI_EINVAL,
-                     "need T > 0, smear > 0, finite mu and emin <= emax");
-        c->have_rates = c->have_sigma = c->have_is = false;
-        c->T = T;
-        c->mu = mu;
-        c->eta = eta;
-        c->emin = emin;
-        c->emax = emax;
-        std::memset(&c->stats, 0, sizeof(c->stats));
-        c->stats.precision = c->opt.precision;
-        c->stats.ms_eigs = c->ms_eigs;
-        EPWI_CUDA(cudaDeviceGetAttribute(&c->stats.sm_count, cudaDevAttrMultiProcessorCount, c->device));
+        WorkSet ws = begin_rates(c, T, mu, eta, emin, emax);
+        process_workset(c, ws, nullptr);
+        end_rates(c);
+        if (n_states) *n_states = c->nstates;
+        if (n_pairs) *n_pairs = c->npairs;
+    });
+}
+
+epwi_status epwi_ibte(epwi_ctx *c, double T, double mu, double eta, double emin, double emax,
+                      int32_t max_iter, double tol, int32_t *iters, double *change) {
+    return guard(c, [&] {
+        EPWI_REQUIRE(max_iter >= 0 && tol >= 0 && std::isfinite(tol), EPWI_EINVAL,
+                     "need max_iter >= 0 and a finite tol >= 0");
         cudaEvent_t e0, e1;
         EPWI_CUDA(cudaEventCreate(&e0));
         EPWI_CUDA(cudaEventCreate(&e1));
-        cudaEventRecord(e0, c->stream);
-        build_window(c);
-        sieve_count(c);
-        cudaEventRecord(e1, c->stream);
-        EPWI_CUDA(cudaStreamSynchronize(c->stream));
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
+        try {
+            std::memset(&c->ib_stats, 0, sizeof(c->ib_stats));
+            cudaEventRecord(e0, c->stream);
+            WorkSet ws = begin_rates(c, T, mu, eta, emin, emax);
+            ibte_prepare(c, ws);
+            process_workset(c, ws, nullptr);
+            cudaEventRecord(e1, c->stream);
+            EPWI_CUDA(cudaStreamSynchronize(c->stream));
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            end_rates(c);
+            c->ib_stats.ms_rates = ms;
+            c->ib_stats.n_states = c->nstates;
+            c->ib_stats.n_pairs = c->npairs;
+            const auto t0 = std::chrono::steady_clock::now();
+            ibte_iterate(c, max_iter, tol);
+            c->ib_stats.ms_iterate =
+                std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        } catch (...) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            throw;
+        }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        c->stats.ms_sieve = ms;
-        occupation_tables(c);
-        if (c->nstates > 0)
-            EPWI_CUDA(cudaMemsetAsync(c->inv_tau.p, 0, sizeof(double) * c->nstates, c->stream));
-        WorkSet ws;
-        ws.nkp = c->nkp;
-        ws.kpts = c->kpts.as<int>();
-        ws.kp_state = c->kp_state.as<int64_t>();
-        ws.kp_pairs = c->kp_pairs.as<int64_t>();
-        ws.h_kp_pairs = c->h_kp_pairs;
-        ws.h_kp_state.resize(c->nkp + 1);
-        EPWI_CUDA(cudaMemcpyAsync(ws.h_kp_state.data(), c->kp_state.p, sizeof(int64_t) * (c->nkp + 1),
-                                  cudaMemcpyDeviceToHost, c->stream));
+        c->have_ibte = true;
+        if (iters) *iters = c->ib_stats.iters;
+        if (change) *change = c->ib_stats.change;
+    });
+}
+
+epwi_status epwi_get_mfp(epwi_ctx *c, int64_t cap, double *F) {
+    return guard(c, [&] {
+        EPWI_REQUIRE(c->have_ibte, EPWI_ESTATE, "epwi_ibte has not been called");
+        EPWI_REQUIRE(cap >= c->nstates, EPWI_ETOOSMALL, "capacity below n_states");
+        EPWI_REQUIRE(F || c->nstates == 0, EPWI_EINVAL, "F is NULL");
+        if (c->nstates)
+            EPWI_CUDA(cudaMemcpyAsync(F, c->ib_F.p, sizeof(double) * 3 * c->nstates, cudaMemcpyDeviceToHost,
+                                      c->stream));
         EPWI_CUDA(cudaStreamSynchronize(c->stream));
-        process_workset(c, ws, nullptr);
-        c->stats.n_kpoints = c->nkp;
-        c->stats.n_states = c->nstates;
-        c->stats.n_pairs = c->npairs;
-        c->stats.restage_bytes = (int64_t)c->stats.n_chunks * c->nRe * c->nRp * c->nm * c->nw *
-                                 c->nw * (c->opt.precision == EPWI_FP64 ? 16 : 8);
-        c->stats.scatter_flops = 8.0 * c->nRp * c->nm * c->nw * (double)c->npairs *
-                                 ((double)c->nstates / std::max<int64_t>(1, c->nkp));
-        if (n_states) *n_states = c->nstates;
-        if (n_pairs) *n_pairs = c->npairs;
-        c->have_rates = true;
+    });
+}
+
+epwi_status epwi_ibte_transport(epwi_ctx *c, double sigma[9], double seebeck[9], double kappa_e[9]) {
+    return guard(c, [&] {
+        EPWI_REQUIRE(c->have_ibte, EPWI_ESTATE, "epwi_ibte has not been called");
+        double m[3][9];
+        transport_moments_F(c, c->ib_F.as<double>(), m);
+        finish_transport(c, m, sigma, seebeck, kappa_e);
+    });
+}
+
+epwi_status epwi_get_ibte_stats(epwi_ctx *c, epwi_ibte_stats *out) {
+    return guard(c, [&] {
+        EPWI_REQUIRE(out, EPWI_EINVAL, "out is NULL");
+        *out = c->ib_stats;
     });
 }
 
@@ -519,30 +633,7 @@ epwi_status epwi_transport(epwi_ctx *c, double sigma[9], double seebeck[9], doub
         require_rates(c);
         double m[3][9];
         transport_moments(c, m);
-        const double e = epc::kECharge;
-        const double kT_J = epc::kKbEVK * c->T * e;
-        const double vol = (double)c->nk * c->volume * 1e-30;
-        const double pref = 2.0 * e * e / (vol * kT_J);   // sigma per unit of the zeroth moment
-        double sig[9], nu[9], k0[9];
-        for (int i = 0; i < 9; ++i) {
-            sig[i] = pref * m[0][i];
-            nu[i] = -pref * m[1][i] / c->T;                // q = -e: electrons
-            k0[i] = pref * m[2][i] / c->T;
-        }
-        double S[9];
-        solve3(sig, nu, S);
-        for (int i = 0; i < 9; ++i) {
-            EPWI_REQUIRE(std::isfinite(sig[i]) && std::isfinite(S[i]), EPWI_ENUMERIC, "non-finite result");
-            if (sigma) sigma[i] = sig[i];
-            if (seebeck) seebeck[i] = S[i];
-        }
-        if (kappa_e)
-            for (int i = 0; i < 3; ++i)
-                for (int j = 0; j < 3; ++j) {
-                    double t = 0;
-                    for (int k = 0; k < 3; ++k) t += nu[i * 3 + k] * S[k * 3 + j];
-                    kappa_e[i * 3 + j] = k0[i * 3 + j] - c->T * t;
-                }
+        finish_transport(c, m, sigma, seebeck, kappa_e);
     });
 }
 

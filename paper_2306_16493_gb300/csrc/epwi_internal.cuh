@@ -175,6 +175,16 @@ struct epwi_ctx {
     DevBuf is_kp_pairs;            // int64 [nkp+1] pair offsets of the sampled pairs
     std::vector<int64_t> h_is_kp_pairs;
 
+    // iterative BTE: Gamma in pair blocks, mean free paths
+    bool have_ibte = false;
+    DevBuf ib_pairs;               // int32 q index per pair (all k-points of the window)
+    DevBuf ib_goff;                // int64 [npairs + 1] first Gamma entry of each pair
+    DevBuf ib_gam;                 // double (FP64 path) or float: per pair [n][m in window(k+q)]
+    DevBuf ib_kpos;                // int32 [Nk] window k-point of each grid point, -1 outside
+    DevBuf ib_F0, ib_F, ib_Fn;     // double [nstates][3] m: v tau, current and next iterate
+    DevBuf ib_red;                 // uint64 [2]: bit patterns of max |dF| and max |F|
+    epwi_ibte_stats ib_stats{};
+
     ~epwi_ctx() {
         DevBuf *all[] = {&Re, &Rp, &Rcart, &Hw, &Phiw, &mode_mass, &gw64, &gw32, &ph64, &ph32,
                          &eps, &eps32, &V, &V32, &vel, &hw, &hwmax32, &hw32, &u, &u32, &eig_flag,
@@ -182,7 +192,8 @@ struct epwi_ctx {
                          &st_n, &focc, &nocc, &pairs, &ghat, &tiles, &tile_part, &kp_tile,
                          &scan_tmp, &red_tmp, &counts, &tc_ptab, &tc_erel, &tc_f32,
                          &tc_n32, &tc_hw32, &tc_err, &tc_meta, &is_pairs, &is_w,
-                         &is_kp_pairs, &sieve_mask, &tc_arows};
+                         &is_kp_pairs, &sieve_mask, &tc_arows, &ib_pairs, &ib_goff, &ib_gam,
+                         &ib_kpos, &ib_F0, &ib_F, &ib_Fn, &ib_red};
         for (DevBuf *b : all) b->release();
         mlp_free(mlp);
     }
@@ -264,5 +275,6 @@ void run_scatter(epwi_ctx *c);
 double carrier_density(epwi_ctx *c, double T, double mu, int n_valence);
 void conductivity(epwi_ctx *c, double sigma[9]);
 void transport_moments(epwi_ctx *c, double m[3][9]);
+void transport_moments_F(epwi_ctx *c, const double *F, double m[3][9]);
 void run_g2(epwi_ctx *c, int64_t npairs, const int32_t *ik, const int32_t *iq, int band_lo,
             int nsel, double *g2);

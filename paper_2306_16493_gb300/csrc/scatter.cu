@@ -112,7 +112,9 @@ __global__ void __launch_bounds__(128) k_scatter_fp64(ScatterArgs a) {
             const double en = a.eps[(int64_t)ik * W + lo + np];
             const double2 *Vq = a.V64 + ikq * W * W;
             const double2 *uq = a.u64 + (int64_t)iq * Nm * Nm;
+            const int lokq = a.gam64 ? a.win_lo[ikq] : 0, nwkq = a.gam64 ? a.win_n[ikq] : 0;
             for (int m = 0; m < W; ++m) {
+                double gm = 0;                    // Gamma capture: sum over modes
                 double2 h[NMM];
                 for (int mu = 0; mu < Nm; ++mu) {
                     h[mu] = make_double2(0, 0);
@@ -145,7 +147,10 @@ __global__ void __launch_bounds__(128) k_scatter_fp64(ScatterArgs a) {
                     }
                     if (TERMS) tacc[nu] += g2 * term;
                     else rate += g2 * term;
+                    gm += g2 * term;
                 }
+                if (!TERMS && a.gam64 && m >= lokq && m < lokq + nwkq)
+                    a.gam64[a.goff[pair] + (int64_t)np * nwkq + (m - lokq)] = gm;
             }
         }
         if (TERMS) {
@@ -365,6 +370,9 @@ int64_t run_chunk(epwi_ctx *c, const WorkSet &ws, const ChunkView &cv, double *g
     sa.pair_w = ws.pair_w ? ws.pair_w + cv.g_base : nullptr;
     sa.tout = tout;
     sa.tstride = tstride;
+    sa.gam32 = ws.gam32;
+    sa.gam64 = ws.gam64;
+    sa.goff = ws.goff ? ws.goff + cv.g_base : nullptr;
     sa.precision = c->opt.precision;
     sa.nstates_chunk = cv.ns;
     sa.nsel_max = 1;

@@ -57,6 +57,9 @@ struct ScatterArgs {
     double *tout;                         // terms mode output or nullptr:
                                           // tout[(pair * tstride + np) * Nm + nu]
     int tstride;
+    float *gam32;                         // Gamma capture (split paths) or nullptr
+    double *gam64;                        // Gamma capture (FP64 path) or nullptr
+    const int64_t *goff;                  // chunk pair -> first Gamma entry (with a capture)
     int precision;
     int nsel_max;                         // largest band window of the chunk
     int64_t nstates_chunk;                // states of the chunk
@@ -70,6 +73,12 @@ struct WorkSet {
     std::vector<int64_t> h_kp_state, h_kp_pairs;
     const int *pairs_dev = nullptr;       // all pairs, or nullptr: sieve fill per chunk
     const double *pair_w = nullptr;       // per pair weight of pairs_dev (FP64 path only)
+    // Gamma capture of the iterative BTE (rates mode): for every pair, the block
+    // [n in window(k)][m in window(k+q)] of sum_nu |g|^2 [occupation x exp] starting at
+    // goff[pair] (global pair index), in gam64 (FP64 path) or gam32 (split paths)
+    float *gam32 = nullptr;
+    double *gam64 = nullptr;
+    const int64_t *goff = nullptr;
     int ovr_lo = -1, ovr_nsel = -1;
 };
 
@@ -86,3 +95,8 @@ void tc_restage(epwi_ctx *c, const RestageArgs &ra);
 void tc_scatter(epwi_ctx *c, const ScatterArgs &sa, int64_t ntiles);
 void tc_tables(epwi_ctx *c);
 int tc_check_error(epwi_ctx *c);
+
+// Iterative BTE: pair list, Gamma layout and storage of the current window (sets the Gamma
+// capture of ws); iteration from F0 = v tau into ib_F.
+void ibte_prepare(epwi_ctx *c, WorkSet &ws);
+void ibte_iterate(epwi_ctx *c, int max_iter, double tol);

@@ -367,7 +367,7 @@ __device__ __forceinline__ void issue_b(const TcArgs &a, const TileMeta &m, int 
 // B either stays resident for a (k-point, band group) across consecutive tiles (reloaded
 // only when it changes) or, when it does not fit, streams through two slots one chunk ahead.
 // 9 warps put at most 3 on a sub-partition: <= 168 registers per thread.
-template <class Op, int W, int NM, int RC, bool AG>
+template <class Op, int W, int NM, int RC, bool AG, bool GAM>
 __global__ void __maxnreg__(168) k_scatter_tc(TcArgs a) {
     constexpr int ES = Op::kBytes;
     constexpr int KC = 64 / ES;                 // Rp per chunk (64 bytes per row and operand)
@@ -800,6 +800,15 @@ __global__ void __maxnreg__(168) k_scatter_tc(TcArgs a) {
                 emr[mm] = __ldg(a.erel32 + (size_t)ikq * W + mm);
                 fmr[mm] = __ldg(a.f32 + (size_t)ikq * W + mm);
             }
+            int lokq = 0, nwkq = 0;
+            int64_t goffp = 0;
+            if constexpr (GAM) {
+                if (active) {
+                    lokq = __ldg(s.win_lo + ikq);
+                    nwkq = __ldg(s.win_n + ikq);
+                    goffp = s.goff[pair];
+                }
+            }
             if (tile + 1 < t_end)
                 q_next = (m_next.begin + et < m_next.end) ? (unsigned)s.pairs[m_next.begin + et] : 0u;
             for (int g0 = 0; g0 < m.nsel && !failed; g0 += a.nbg) {
@@ -853,6 +862,7 @@ __global__ void __maxnreg__(168) k_scatter_tc(TcArgs a) {
                             }
                             const float em = emr[mm];
                             const float fm = fmr[mm];
+                            float gm = 0.f;      // Gamma capture: sum over modes
 #pragma unroll
                             for (int nu = 0; nu < NM; ++nu) {
                                 const float w = wq[nu];
@@ -881,6 +891,11 @@ __global__ void __maxnreg__(168) k_scatter_tc(TcArgs a) {
                                     tt += (1.f + nq[nu] - fm) * __expf(-y * y);
                                 }
                                 rate = fmaf(g2, tt, rate);
+                                if constexpr (GAM) gm = fmaf(g2, tt, gm);
+                            }
+                            if constexpr (GAM) {
+                                if (mm >= lokq && mm < lokq + nwkq)
+                                    s.gam32[goffp + (int64_t)(g0 + b) * nwkq + (mm - lokq)] = gm * a.scale_inv2;
                             }
                         }
                         if (s.pair_w) rate *= (float)s.pair_w[pair];   // importance-sampling weight
@@ -940,7 +955,7 @@ const uint8_t *phase_rows(epwi_ctx *c, int nchunk, int rlog, const uint32_t *pta
     return c->tc_arows.as<uint8_t>();
 }
 
-template <class Op, int W, int NM, int RC, bool AG>
+template <class Op, int W, int NM, int RC, bool AG, bool GAM = false>
 void launch_tc(epwi_ctx *c, const ScatterArgs &sa, int64_t ntiles) {
     constexpr int NMWP = (NM * W + 15) / 16 * 16;
     constexpr int TW = Op::kTF32 ? 4 : 2;
@@ -1000,7 +1015,7 @@ void launch_tc(epwi_ctx *c, const ScatterArgs &sa, int64_t ntiles) {
         a.arr_bytes = a.nchunk * 64;
         a.arow_bytes = 4 * (int64_t)a.arr_bytes;
     }
-    auto kern = k_scatter_tc<Op, W, NM, RC, AG>;
+    auto kern = k_scatter_tc<Op, W, NM, RC, AG, GAM>;
     int nsm = 0;
     EPWI_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
     EPWI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
@@ -1046,6 +1061,10 @@ template <class Op, int W, int NM, int RC>
 void launch_any(epwi_ctx *c, const ScatterArgs &sa, int64_t nt) {
     constexpr int D = 2 * RC + 1;
     const int64_t kpad = ((D * D * D + 64 / Op::kBytes - 1) / (64 / Op::kBytes)) * (64 / Op::kBytes);
+    if (sa.gam32) {                          // Gamma capture of the iterative BTE
+        launch_tc<Op, W, NM, RC, false, true>(c, sa, nt);
+        return;
+    }
     if constexpr (!Op::kTF32) {
         if (c->tc_gather && (int64_t)c->nk * 4 * kpad * 2 <= (int64_t(16) << 30)) {
             launch_tc<Op, W, NM, RC, true>(c, sa, nt);

@@ -103,6 +103,31 @@ __global__ void __launch_bounds__(kRedThreads) k_moments_part(
         for (int j = 0; j < 18; ++j) part[blockIdx.x * 18 + j] = v[j];
 }
 
+// Energy moment p of the transport sum with the mean free paths F (iterative BTE): sums of
+// f(1-f) x^p v_a F_b over the window states, nine components a-major.
+__global__ void __launch_bounds__(kRedThreads) k_moments_F_part(
+    int64_t ns, int W, int p, const int *__restrict__ st_k, const int *__restrict__ st_n,
+    const double *__restrict__ eps, const double *__restrict__ vel, const double *__restrict__ F,
+    double mu, double kT, double *__restrict__ part) {
+    __shared__ double sm[9 * kRedThreads];
+    const int64_t per = (ns + gridDim.x - 1) / gridDim.x;
+    const int64_t b0 = per * blockIdx.x, b1 = min(ns, b0 + per);
+    double v[9];
+    for (int j = 0; j < 9; ++j) v[j] = 0;
+    for (int64_t s = b0 + threadIdx.x; s < b1; s += blockDim.x) {
+        const int64_t idx = (int64_t)st_k[s] * W + st_n[s];
+        const double f = fermi(eps[idx], mu, kT);
+        const double x = eps[idx] - mu;
+        double w = f * (1.0 - f);
+        for (int q = 0; q < p; ++q) w *= x;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) v[a * 3 + b] += w * vel[idx * 3 + a] * F[s * 3 + b];
+    }
+    block_sum<9>(v, sm);
+    if (threadIdx.x == 0)
+        for (int j = 0; j < 9; ++j) part[blockIdx.x * 9 + j] = v[j];
+}
+
 template <int NV>
 __global__ void __launch_bounds__(kRedThreads) k_final_sum(int nb, const double *__restrict__ part,
                                                            double *__restrict__ out) {
@@ -273,5 +298,26 @@ void transport_moments(epwi_ctx *c, double m[3][9]) {
         const double *q = h + 6 * p;
         const double t[9] = {q[0], q[3], q[4], q[3], q[1], q[5], q[4], q[5], q[2]};
         for (int i = 0; i < 9; ++i) m[p][i] = t[i];
+    }
+}
+
+// Moments p = 0, 1, 2 of the transport sum with v tau replaced by the mean free paths F
+// (iterative BTE): m[p][a*3+b] = sum f(1-f) (eps - mu)^p v_a F_b.
+void transport_moments_F(epwi_ctx *c, const double *F, double m[3][9]) {
+    const int64_t ns = c->nstates;
+    const int nb = red_blocks(ns);
+    c->red_tmp.ensure(sizeof(double) * (9 * nb + 32));
+    double *part = c->red_tmp.as<double>();
+    double *out = part + 9 * nb;
+    const double kT = epc::kKbEVK * c->T;
+    for (int p = 0; p < 3; ++p) {
+        k_moments_F_part<<<nb, kRedThreads, 0, c->stream>>>(ns, c->nw, p, c->st_k.as<int>(),
+                                                            c->st_n.as<int>(), c->eps.as<double>(),
+                                                            c->vel.as<double>(), F, c->mu, kT, part);
+        EPWI_CHECK_LAUNCH();
+        k_final_sum<9><<<1, kRedThreads, 0, c->stream>>>(nb, part, out);
+        EPWI_CHECK_LAUNCH();
+        EPWI_CUDA(cudaMemcpyAsync(m[p], out, sizeof(double) * 9, cudaMemcpyDeviceToHost, c->stream));
+        EPWI_CUDA(cudaStreamSynchronize(c->stream));
     }
 }

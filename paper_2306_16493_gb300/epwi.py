@@ -58,6 +58,13 @@ class epwi_stats(C.Structure):
                 ("proposal_flops", C.c_double)]
 
 
+class epwi_ibte_stats(C.Structure):
+    _fields_ = [("n_states", C.c_int64), ("n_pairs", C.c_int64), ("n_entries", C.c_int64),
+                ("entry_bytes", C.c_int32), ("iters", C.c_int32), ("change", C.c_double),
+                ("ms_rates", C.c_double), ("ms_iterate", C.c_double), ("ms_step", C.c_double),
+                ("bytes_per_step", C.c_double)]
+
+
 class epwi_mlp_train_options(C.Structure):
     _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_double),
                 ("background", C.c_double), ("floor_rel", C.c_double), ("seed", C.c_uint64)]
@@ -99,6 +106,10 @@ def _load() -> C.CDLL:
         "epwi_conductivity": (I32, [P, P]),
         "epwi_mobility": (I32, [P, D, P]),
         "epwi_transport": (I32, [P, P, P, P]),
+        "epwi_ibte": (I32, [P, D, D, D, D, D, I32, D, P, P]),
+        "epwi_get_mfp": (I32, [P, I64, P]),
+        "epwi_ibte_transport": (I32, [P, P, P, P]),
+        "epwi_get_ibte_stats": (I32, [P, P]),
         "epwi_get_bands": (I32, [P, P, P, P]),
         "epwi_get_phonons": (I32, [P, P, P]),
         "epwi_get_sieve": (I32, [P, I64, P, P]),
@@ -310,6 +321,32 @@ def epwi_get_stats(ctx) -> dict:
     s = epwi_stats()
     _check(ctx, _lib.epwi_get_stats(ctx, C.byref(s)))
     return {name: getattr(s, name) for name, _ in epwi_stats._fields_}
+
+
+def epwi_ibte(ctx, T, mu, smear, emin, emax, max_iter=100, tol=1e-8):
+    """Iterative BTE; returns (iterations, last relative change)."""
+    it, ch = C.c_int32(), C.c_double()
+    _check(ctx, _lib.epwi_ibte(ctx, T, mu, smear, emin, emax, int(max_iter), float(tol),
+                               C.byref(it), C.byref(ch)))
+    return it.value, ch.value
+
+
+def epwi_get_mfp(ctx, n_states) -> np.ndarray:
+    F = np.empty((max(int(n_states), 0), 3))
+    _check(ctx, _lib.epwi_get_mfp(ctx, int(n_states), _ptr(F)))
+    return F
+
+
+def epwi_ibte_transport(ctx):
+    sig, S, kap = np.empty((3, 3)), np.empty((3, 3)), np.empty((3, 3))
+    _check(ctx, _lib.epwi_ibte_transport(ctx, _ptr(sig), _ptr(S), _ptr(kap)))
+    return sig, S, kap
+
+
+def epwi_get_ibte_stats(ctx) -> dict:
+    s = epwi_ibte_stats()
+    _check(ctx, _lib.epwi_get_ibte_stats(ctx, C.byref(s)))
+    return {name: getattr(s, name) for name, _ in epwi_ibte_stats._fields_}
 
 
 def epwi_mlp_default_train_options() -> epwi_mlp_train_options:
@@ -560,6 +597,23 @@ class Context:
 
     def mobility(self, n_cm3):
         return epwi_mobility(self.h, n_cm3)
+
+    def ibte(self, T, mu, smear, emin, emax, max_iter=100, tol=1e-8):
+        """Iterative BTE (also leaves the SERTA rates); returns (iterations, change)."""
+        it, ch = epwi_ibte(self.h, T, mu, smear, emin, emax, max_iter, tol)
+        self.n_states = epwi_get_ibte_stats(self.h)["n_states"]
+        return it, ch
+
+    def mfp(self):
+        """Mean free paths F [n_states, 3] (m) of the last ibte call, in rates order."""
+        return epwi_get_mfp(self.h, self.n_states)
+
+    def ibte_transport(self):
+        """(sigma, Seebeck, kappa_e) from the mean free paths, as 3x3 arrays."""
+        return epwi_ibte_transport(self.h)
+
+    def ibte_stats(self):
+        return epwi_get_ibte_stats(self.h)
 
     def bands(self):
         return epwi_get_bands(self.h, self.nk, self.nw)
