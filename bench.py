@@ -472,6 +472,119 @@ def run_learned(args):
     print(json.dumps(line), flush=True)
 
 
+IBTE = dict(workload="al_like_tr_48_ibte",
+            system="Al-like fcc, nw=4, 3 modes, 5^3 WS-weighted Re/Rp, real H(R) and g (time-reversal "
+                   "symmetric)", grid=48, window_eV=0.3, smear_eV=0.02, T_K=300.0, mu="band centre", seed=2)
+
+
+def run_ibte(args):
+    """Iterative BTE on the time-reversal-symmetric Al-like metal: one step = eigensolves ->
+    window -> sieve -> interpolation with 1/tau and the Gamma capture -> iterations to the
+    tolerance -> sigma from F.  value = sieved pairs / step time."""
+    import torch
+    from paper_2306_16493_gb300 import epwi, synth
+    torch.cuda.set_device(0)
+    precision = args.precision
+    s = synth.time_reversal_symmetric(synth.al_like_system(IBTE["seed"]))
+    N = args.grid
+    T, eta, win = IBTE["T_K"], IBTE["smear_eV"], IBTE["window_eV"]
+    stream = torch.cuda.current_stream()
+    ctx = epwi.Context(precision=precision, device=0, stream=stream.cuda_stream)
+    ctx.setup(s)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        ctx.eigs(N)
+        lo, hi = ctx.band_range()
+        mu = 0.5 * (lo + hi)
+        it, ch = ctx.ibte(T, mu, eta, mu - win, mu + win, max_iter=args.ibte_iters, tol=args.ibte_tol)
+        sig = ctx.ibte_transport()[0]
+        return ctx.ibte_stats(), sig, mu
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    launches0 = epwi.epwi_kernel_launches()
+    sts = []
+    clocks_path = os.path.join(tempfile.gettempdir(), f"epwi_clocks_{os.getpid()}.csv")
+    with ClockSampler(clocks_path) as cs:
+        time.sleep(0.3)
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            st, sig, mu = step()
+            ev[k][1].record(stream)
+            sts.append(dict(st, ms_scatter=ctx.stats()["ms_scatter"], scatter_flops=ctx.stats()["scatter_flops"],
+                            n_chunks=ctx.stats()["n_chunks"]))
+        torch.cuda.synchronize()
+    launches = (epwi.epwi_kernel_launches() - launches0) // args.steps
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    st = sts[-1]
+    pairs = st["n_pairs"]
+    mp, src = peaks()
+    ms_step = statistics.mean(x["ms_step"] for x in sts)
+    achieved = st["bytes_per_step"] / (ms_step * 1e-3) / 1e9
+    roof_step = {"bound": "hbm", "achieved": achieved, "peak": mp["hbm_gbs"], "unit": "GB/s",
+                 "frac": achieved / mp["hbm_gbs"], "traffic": None,
+                 "kernel": "k_ib_step (one BTE iteration: q list, Gamma blocks, F gathers)",
+                 "launches_per_step": st["iters"], "peak_source": f"{src} HBM copy bandwidth"}
+    roof_sc = roofline_for(precision, dict(scatter_flops=statistics.mean(x["scatter_flops"] for x in sts),
+                                           ms_scatter=statistics.mean(x["ms_scatter"] for x in sts),
+                                           n_chunks=st["n_chunks"]))
+    it_ms = statistics.mean(x["ms_step"] * x["iters"] for x in sts)
+    sc_ms = statistics.mean(x["ms_scatter"] for x in sts)
+    roof, roof_other = (roof_sc, roof_step) if sc_ms >= it_ms else (roof_step, roof_sc)
+
+    # e2e: host arrays -> sigma and F on the host, through the C ABI
+    e2e_steps = max(1, min(args.steps, 2))
+    h2d = sum(a.nbytes for a in (s.mass, s.Re, s.we, s.H, s.Rp, s.wp, s.Phi, s.g))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    d2h = 0
+    for _ in range(e2e_steps):
+        ctx.setup(s)
+        st_e, sig, _ = step()
+        F = ctx.mfp()
+        d2h = F.nbytes + sig.nbytes
+    torch.cuda.synchronize()
+    e2e_t = (time.perf_counter() - t0) / e2e_steps
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import epwi_oracle as O
+        n_cpu = 12
+        gr = O.Grids(s, (n_cpu,) * 3)
+        mu_c = gr.band_centre()
+        t0 = time.perf_counter()
+        ref = O.ibte(gr, T, mu_c, eta, mu_c - win, mu_c + win, max_iter=args.ibte_iters, tol=args.ibte_tol)
+        dt = time.perf_counter() - t0
+        npairs_c = int(sum(len(O.sieve_k(gr, int(k), ref["n"][ref["ik"] == k], eta)) for k in np.unique(ref["ik"])))
+        cpu = {"value": npairs_c / dt, "unit": "pairs/s", "cores": cores_used(), "kind": "oracle",
+               "sample": f"the whole oracle solve at {n_cpu}^3 ({npairs_c} pairs, {ref['iters']} iterations, "
+                         f"{dt:.1f} s, numpy FP64; the iteration couples every k-point, so no k subset)"}
+    line = {"metric": "el-ph (k,q)-pairs/s and time-to-σ of the iterative BTE", "value": pairs / (ms * 1e-3),
+            "unit": "pairs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[precision],
+            "data": "synthetic",
+            "config": dict(IBTE, grid=N, workload=f"al_like_tr_{N}_ibte", precision=precision,
+                           max_iter=args.ibte_iters, tol=args.ibte_tol,
+                           l2="flushed between timed steps (256 MiB write)", parallelism="single GPU"),
+            "gpu_launches": int(launches),
+            "ibte": {"iters": st["iters"], "change": st["change"], "n_states": st["n_states"],
+                     "n_pairs": pairs, "gamma_entries": st["n_entries"], "entry_bytes": st["entry_bytes"],
+                     "ms_rates": statistics.mean(x["ms_rates"] for x in sts),
+                     "ms_iterate": statistics.mean(x["ms_iterate"] for x in sts), "ms_step_kernel": ms_step,
+                     "bytes_per_step_kernel": st["bytes_per_step"],
+                     "sigma_diag_S_per_m": [float(sig[i, i]) for i in range(3)]},
+            "roofline": roof, "roofline_other": roof_other, "clocks": cs.summary(0), "cpu_baseline": cpu,
+            "e2e": {"value": pairs / e2e_t, "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)}}
+    ctx.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -483,7 +596,8 @@ def main():
     ap.add_argument("--grid", type=int, default=WORKLOAD["grid"],
                     help="k and q grid per axis (48 is the benchmark; smaller sizes are for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="al_like", choices=["al_like", "batch64", "si_like_learned"],
+    ap.add_argument("--workload", default="al_like",
+                    choices=["al_like", "batch64", "si_like_learned", "al_like_ibte"],
                     help="al_like: the benchmark; batch64 and si_like_learned: the batched and "
                          "learned-proposal workloads (reported separately)")
     ap.add_argument("--batch-scale", type=int, default=3, help="batch64: grid divisor")
@@ -493,6 +607,8 @@ def main():
     ap.add_argument("--learned-stride", type=int, default=2)
     ap.add_argument("--learned-precision", default="fp16x3", choices=["fp64", "fp16x3"])
     ap.add_argument("--learned-samples", type=int, nargs="+", default=[10000, 100000])
+    ap.add_argument("--ibte-iters", type=int, default=200, help="al_like_ibte: iteration cap")
+    ap.add_argument("--ibte-tol", type=float, default=1e-6, help="al_like_ibte: max |dF| / max |F|")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -500,6 +616,8 @@ def main():
         run_batch(args)
     elif args.workload == "si_like_learned":
         run_learned(args)
+    elif args.workload == "al_like_ibte":
+        run_ibte(args)
     else:
         run_gpu(args)
 

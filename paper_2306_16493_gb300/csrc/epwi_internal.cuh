@@ -182,6 +182,7 @@ struct epwi_ctx {
     DevBuf ib_gam;                 // double (FP64 path) or float: per pair [n][m in window(k+q)]
     DevBuf ib_kpos;                // int32 [Nk] window k-point of each grid point, -1 outside
     DevBuf ib_F0, ib_F, ib_Fn;     // double [nstates][3] m: v tau, current and next iterate
+    DevBuf ib_F32, ib_Fn32;        // float4 [nstates]: FP32 copies of ib_F, ib_Fn (split paths)
     DevBuf ib_red;                 // uint64 [2]: bit patterns of max |dF| and max |F|
     epwi_ibte_stats ib_stats{};
 
@@ -193,7 +194,7 @@ struct epwi_ctx {
                          &scan_tmp, &red_tmp, &counts, &tc_ptab, &tc_erel, &tc_f32,
                          &tc_n32, &tc_hw32, &tc_err, &tc_meta, &is_pairs, &is_w,
                          &is_kp_pairs, &sieve_mask, &tc_arows, &ib_pairs, &ib_goff, &ib_gam,
-                         &ib_kpos, &ib_F0, &ib_F, &ib_Fn, &ib_red};
+                         &ib_kpos, &ib_F0, &ib_F, &ib_Fn, &ib_red, &ib_F32, &ib_Fn32};
         for (DevBuf *b : all) b->release();
         mlp_free(mlp);
     }

@@ -7,11 +7,19 @@
 // the summand of Eq. 10 without its constant 2 pi / (hbar N_q sqrt(pi) eta), which the step
 // applies once per state.
 //
-// Step: one block per window k-point, four warps splitting its pairs into contiguous ranges.
-// A warp takes 32 pairs at a time; a warp scan of the block sizes n_k x n_{k+q} gives each
-// lane its block, and the lane accumulates Gamma[n][m] F_{m,k+q} for its pair.  Per-state
-// sums are reduced in a fixed order (lanes by a butterfly, then warps in index order), so the
-// result does not depend on scheduling.
+// After the capture each pair's q index is replaced in place by a step code: the first state
+// of the final k-point's window (sb) and its band count (nw), (sb << 5) | nw.  The step then
+// reads one word per pair and needs no grid arithmetic or table lookups.
+//
+// Step: one block per window k-point, eight warps splitting its pairs into contiguous ranges,
+// the k-point's bands taken in register groups of 1, 2, 4 or 8 (the smallest that covers the
+// crystal's bands) with the inner loop specialised to the group's exact band count.  With
+// FP32 Gamma (split paths) the lanes accumulate and reduce in FP32 from an FP32 copy of F;
+// the sum over warps, the per-state update and F itself are FP64.
+// A warp takes 32 pairs at a time (the next 32 codes are loaded ahead); a warp scan of the
+// block sizes n_k x n_{k+q} gives each lane its block, and the lane accumulates
+// Gamma[n][m] F_{m,k+q} for its pair.  Per-state sums are reduced in a fixed order (lanes by a
+// butterfly, then warps in index order), so the result does not depend on scheduling.
 #include <algorithm>
 #include <cstring>
 
@@ -20,9 +28,9 @@
 
 namespace {
 
-constexpr int kIbThreads = 128;
+constexpr int kIbThreads = 256;
 constexpr int kIbWarps = kIbThreads / 32;
-constexpr int kIbBands = 8;     // bands of k accumulated in registers at a time
+constexpr int kIbMaxBands = 8;  // bands of k accumulated in registers at a time (at most)
 
 __global__ void k_ib_kpos(int64_t nkp, const int *__restrict__ kpts, int *__restrict__ kpos) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -40,38 +48,113 @@ __global__ void k_ib_sizes(GridInfo g, const int *__restrict__ kpts, const int *
         sizes[p] = (int64_t)nsel * win_n[kplusq(g, ik, pairs[p])];
 }
 
+// q index -> step code (sb << 5) | nw of the final k-point, in place; one block per k-point
+__global__ void k_ib_encode(GridInfo g, const int *__restrict__ kpts, const int *__restrict__ win_n,
+                            const int *__restrict__ kpos, const int64_t *__restrict__ kp_state,
+                            const int64_t *__restrict__ kp_pairs, unsigned *__restrict__ code) {
+    const int kp = blockIdx.x;
+    const int ik = kpts[kp];
+    for (int64_t p = kp_pairs[kp] + threadIdx.x; p < kp_pairs[kp + 1]; p += blockDim.x) {
+        const int64_t ikq = kplusq(g, ik, (int)code[p]);
+        const unsigned nw = (unsigned)win_n[ikq];
+        const unsigned sb = nw ? (unsigned)kp_state[kpos[ikq]] : 0u;
+        code[p] = (sb << 5) | nw;
+    }
+}
+
 // F0 = v tau (tau = 1 / (1/tau), 0 where 1/tau = 0); F = F0
 __global__ void k_ib_f0(int64_t ns, int W, const int *__restrict__ st_k, const int *__restrict__ st_n,
                         const double *__restrict__ inv_tau, const double *__restrict__ vel,
-                        double *__restrict__ F0, double *__restrict__ F) {
+                        double *__restrict__ F0, double *__restrict__ F, float4 *__restrict__ F32) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= ns) return;
     const double r = inv_tau[s];
     const double tau = r > 0 ? 1.0 / r : 0.0;
     const int64_t idx = (int64_t)st_k[s] * W + st_n[s];
+    float4 f32 = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int a = 0; a < 3; ++a) {
         const double f = vel[idx * 3 + a] * tau;
         F0[s * 3 + a] = f;
         F[s * 3 + a] = f;
+        reinterpret_cast<float *>(&f32)[a] = (float)f;
     }
+    if (F32) F32[s] = f32;
 }
 
 template <typename GT>
 struct StepArgs {
-    GridInfo g;
-    const int *kpts, *win_n, *kpos;
+    const int *kpts, *win_n;
     const int64_t *kp_state, *kp_pairs, *goff;
-    const int *pairs;
+    const unsigned *code;                 // per pair (sb << 5) | nw
     const GT *gam;
     const double *inv_tau, *F0, *Fin;
     double *Fout;
+    const float4 *Fin32;                  // FP32 copy of Fin (split paths), w unused
+    float4 *Fout32;
     double pref;                          // 2 pi / (hbar N_q sqrt(pi) eta), s^-1 per eV^2
     unsigned long long *red;              // [2] max |dF|, max |F| as bit patterns
 };
 
-template <typename GT>
-__global__ void __launch_bounds__(kIbThreads) k_ib_step(StepArgs<GT> a) {
-    __shared__ double part[kIbWarps][kIbBands][3];
+// Accumulation type of the lane and warp sums: FP64 with FP64 Gamma; FP32 with FP32 Gamma
+// (GB300 issues FP64 at 1/64 of the FP32 rate, so FP64 sums would bind the split paths on
+// the FP64 pipe).  The sum over warps is FP64.
+template <typename GT> struct Acc { using T = double; };
+template <> struct Acc<float> { using T = float; };
+
+__device__ __forceinline__ void load_F(const StepArgs<double> &a, int64_t s, double &x, double &y, double &z) {
+    const double *f = a.Fin + s * 3;
+    x = __ldg(f);
+    y = __ldg(f + 1);
+    z = __ldg(f + 2);
+}
+__device__ __forceinline__ void load_F(const StepArgs<float> &a, int64_t s, float &x, float &y, float &z) {
+    const float4 f = __ldg(a.Fin32 + s);
+    x = f.x;
+    y = f.y;
+    z = f.z;
+}
+
+// The warp's pairs [wb, we) for the bands b0 .. b0+NBX-1 of the k-point: y[n] += sum over the
+// pairs and final bands m of Gamma[b0+n][m] F_m.
+template <typename GT, int NB, int NBX>
+__device__ __forceinline__ void step_pairs(const StepArgs<GT> &a, int nsel, int b0, int64_t wb, int64_t we,
+                                           int lane, typename Acc<GT>::T (&y)[NB][3]) {
+    using AT = typename Acc<GT>::T;
+    int64_t off = wb < we ? a.goff[wb] : 0;
+    unsigned cnext = wb + lane < we ? __ldg(a.code + wb + lane) : 0u;
+    for (int64_t pb = wb; pb < we; pb += 32) {
+        const unsigned code = cnext;
+        cnext = pb + 32 + lane < we ? __ldg(a.code + pb + 32 + lane) : 0u;
+        const int nw = (int)(code & 31u);
+        const int64_t sb = (int64_t)(code >> 5);
+        const int size = nsel * nw;
+        int incl = size;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int tot = __shfl_sync(0xffffffffu, incl, 31);
+        const GT *gb = a.gam + off + (incl - size) + (int64_t)b0 * nw;
+        for (int j = 0; j < nw; ++j) {
+            AT fx, fy, fz;
+            load_F(a, sb + j, fx, fy, fz);
+#pragma unroll
+            for (int n = 0; n < NBX; ++n) {
+                const AT gv = (AT)__ldg(gb + n * nw + j);
+                y[n][0] = fma(gv, fx, y[n][0]);
+                y[n][1] = fma(gv, fy, y[n][1]);
+                y[n][2] = fma(gv, fz, y[n][2]);
+            }
+        }
+        off += tot;
+    }
+}
+
+template <typename GT, int kIbBands>
+__global__ void __launch_bounds__(kIbThreads, kIbBands <= 2 ? 4 : (kIbBands <= 4 ? 3 : 2)) k_ib_step(StepArgs<GT> a) {
+    using AT = typename Acc<GT>::T;
+    __shared__ AT part[kIbWarps][kIbBands][3];
     const int kp = blockIdx.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int ik = a.kpts[kp];
@@ -82,61 +165,43 @@ __global__ void __launch_bounds__(kIbThreads) k_ib_step(StepArgs<GT> a) {
     double dmax = 0, fmax_ = 0;
     for (int b0 = 0; b0 < nsel; b0 += kIbBands) {
         const int nb = min(kIbBands, nsel - b0);
-        double y[kIbBands][3];
+        AT y[kIbBands][3];
 #pragma unroll
         for (int n = 0; n < kIbBands; ++n) y[n][0] = y[n][1] = y[n][2] = 0;
-        int64_t off = wb < we ? a.goff[wb] : 0;
-        for (int64_t pb = wb; pb < we; pb += 32) {
-            const int64_t p = pb + lane;
-            int nw = 0;
-            int64_t sb = 0;
-            if (p < we) {
-                const int64_t ikq = kplusq(a.g, ik, a.pairs[p]);
-                nw = a.win_n[ikq];
-                if (nw > 0) sb = a.kp_state[a.kpos[ikq]];
-            }
-            const int size = nsel * nw;
-            int incl = size;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int t = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += t;
-            }
-            const int tot = __shfl_sync(0xffffffffu, incl, 31);
-            const GT *gb = a.gam + off + (incl - size) + (int64_t)b0 * nw;
-            for (int j = 0; j < nw; ++j) {
-                const double fx = a.Fin[(sb + j) * 3], fy = a.Fin[(sb + j) * 3 + 1],
-                             fz = a.Fin[(sb + j) * 3 + 2];
-#pragma unroll
-                for (int n = 0; n < kIbBands; ++n) {
-                    if (n < nb) {
-                        const double gv = (double)gb[n * nw + j];
-                        y[n][0] = fma(gv, fx, y[n][0]);
-                        y[n][1] = fma(gv, fy, y[n][1]);
-                        y[n][2] = fma(gv, fz, y[n][2]);
-                    }
-                }
-            }
-            off += tot;
+        // exact band count of this group (uniform over the block)
+        switch (nb) {
+        case 1: step_pairs<GT, kIbBands, 1>(a, nsel, b0, wb, we, lane, y); break;
+        case 2: if constexpr (kIbBands >= 2) step_pairs<GT, kIbBands, 2>(a, nsel, b0, wb, we, lane, y); break;
+        case 3: if constexpr (kIbBands >= 3) step_pairs<GT, kIbBands, 3>(a, nsel, b0, wb, we, lane, y); break;
+        case 4: if constexpr (kIbBands >= 4) step_pairs<GT, kIbBands, 4>(a, nsel, b0, wb, we, lane, y); break;
+        default:
+            if constexpr (kIbBands > 4) step_pairs<GT, kIbBands, kIbBands>(a, nsel, b0, wb, we, lane, y);
+            break;
         }
+        // lanes: butterfly in the accumulation type; warps: FP64 in index order
 #pragma unroll
-        for (int n = 0; n < kIbBands; ++n)
+        for (int n = 0; n < kIbBands; ++n) {
+            if (n >= nb) break;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                double v = y[n][c];
+                AT v = y[n][c];
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
                 if (lane == 0) part[wid][n][c] = v;
             }
+        }
         __syncthreads();
         if (threadIdx.x < nb * 3) {
             const int n = threadIdx.x / 3, c = threadIdx.x % 3;
-            const double sum = (part[0][n][c] + part[1][n][c]) + (part[2][n][c] + part[3][n][c]);
+            double sum = 0;
+#pragma unroll
+            for (int w = 0; w < kIbWarps; ++w) sum += (double)part[w][n][c];
             const int64_t s = s0 + b0 + n;
             const double r = a.inv_tau[s];
             const double tau = r > 0 ? 1.0 / r : 0.0;
             const double f = a.F0[s * 3 + c] + tau * (a.pref * sum);
             a.Fout[s * 3 + c] = f;
+            if (a.Fout32) reinterpret_cast<float *>(a.Fout32 + s)[c] = (float)f;
             dmax = fmax(dmax, fabs(f - a.Fin[s * 3 + c]));
             fmax_ = fmax(fmax_, fabs(f));
         }
@@ -150,24 +215,29 @@ __global__ void __launch_bounds__(kIbThreads) k_ib_step(StepArgs<GT> a) {
 }
 
 template <typename GT>
-void launch_step(epwi_ctx *c, const double *Fin, double *Fout) {
+void launch_step(epwi_ctx *c, const double *Fin, double *Fout, const float4 *Fin32, float4 *Fout32) {
     StepArgs<GT> a;
-    a.g = make_grid_info(c);
     a.kpts = c->kpts.as<int>();
     a.win_n = c->win_n.as<int>();
-    a.kpos = c->ib_kpos.as<int>();
     a.kp_state = c->kp_state.as<int64_t>();
     a.kp_pairs = c->kp_pairs.as<int64_t>();
     a.goff = c->ib_goff.as<int64_t>();
-    a.pairs = c->ib_pairs.as<int>();
+    a.code = c->ib_pairs.as<unsigned>();
     a.gam = c->ib_gam.as<GT>();
     a.inv_tau = c->inv_tau.as<double>();
     a.F0 = c->ib_F0.as<double>();
     a.Fin = Fin;
     a.Fout = Fout;
+    a.Fin32 = Fin32;
+    a.Fout32 = Fout32;
     a.pref = 2.0 * epc::kPi / epc::kHbarEVs / (double)c->nk / (sqrt(epc::kPi) * c->eta);
     a.red = c->ib_red.as<unsigned long long>();
-    k_ib_step<GT><<<(unsigned)c->nkp, kIbThreads, 0, c->stream>>>(a);
+    // band group: the smallest of 1, 2, 4, 8 covering the bands (wider windows loop)
+    const unsigned grid = (unsigned)c->nkp;
+    if (c->nw <= 1) k_ib_step<GT, 1><<<grid, kIbThreads, 0, c->stream>>>(a);
+    else if (c->nw <= 2) k_ib_step<GT, 2><<<grid, kIbThreads, 0, c->stream>>>(a);
+    else if (c->nw <= 4) k_ib_step<GT, 4><<<grid, kIbThreads, 0, c->stream>>>(a);
+    else k_ib_step<GT, kIbMaxBands><<<grid, kIbThreads, 0, c->stream>>>(a);
     EPWI_CHECK_LAUNCH();
 }
 
@@ -223,11 +293,23 @@ void ibte_iterate(epwi_ctx *c, int max_iter, double tol) {
     c->ib_F0.ensure(sizeof(double) * 3 * (ns + 1));
     c->ib_F.ensure(sizeof(double) * 3 * (ns + 1));
     c->ib_Fn.ensure(sizeof(double) * 3 * (ns + 1));
+    if (!fp64) {
+        c->ib_F32.ensure(sizeof(float4) * (ns + 1));
+        c->ib_Fn32.ensure(sizeof(float4) * (ns + 1));
+    }
     c->ib_red.ensure(sizeof(unsigned long long) * 2);
+    // the captured pairs' q indices become step codes (the capture is done with them)
+    EPWI_REQUIRE(ns < (int64_t(1) << 27), EPWI_EUNSUPPORTED, "iterative BTE needs fewer than 2^27 states");
+    if (c->nkp > 0) {
+        k_ib_encode<<<(unsigned)c->nkp, 256, 0, c->stream>>>(
+            make_grid_info(c), c->kpts.as<int>(), c->win_n.as<int>(), c->ib_kpos.as<int>(),
+            c->kp_state.as<int64_t>(), c->kp_pairs.as<int64_t>(), c->ib_pairs.as<unsigned>());
+        EPWI_CHECK_LAUNCH();
+    }
     if (ns > 0) {
         k_ib_f0<<<(unsigned)((ns + 255) / 256), 256, 0, c->stream>>>(
             ns, c->nw, c->st_k.as<int>(), c->st_n.as<int>(), c->inv_tau.as<double>(), c->vel.as<double>(),
-            c->ib_F0.as<double>(), c->ib_F.as<double>());
+            c->ib_F0.as<double>(), c->ib_F.as<double>(), fp64 ? nullptr : c->ib_F32.as<float4>());
         EPWI_CHECK_LAUNCH();
     }
     cudaEvent_t e0, e1;
@@ -246,8 +328,9 @@ void ibte_iterate(epwi_ctx *c, int max_iter, double tol) {
         for (it = 0; it < max_iter && c->nkp > 0;) {
             EPWI_CUDA(cudaMemsetAsync(c->ib_red.p, 0, sizeof(unsigned long long) * 2, c->stream));
             EPWI_CUDA(cudaEventRecord(e0, c->stream));
-            if (fp64) launch_step<double>(c, c->ib_F.as<double>(), c->ib_Fn.as<double>());
-            else launch_step<float>(c, c->ib_F.as<double>(), c->ib_Fn.as<double>());
+            if (fp64) launch_step<double>(c, c->ib_F.as<double>(), c->ib_Fn.as<double>(), nullptr, nullptr);
+            else launch_step<float>(c, c->ib_F.as<double>(), c->ib_Fn.as<double>(), c->ib_F32.as<float4>(),
+                                    c->ib_Fn32.as<float4>());
             EPWI_CUDA(cudaEventRecord(e1, c->stream));
             EPWI_CUDA(cudaMemcpyAsync(h, c->ib_red.p, sizeof(unsigned long long) * 2, cudaMemcpyDeviceToHost,
                                       c->stream));
@@ -257,6 +340,7 @@ void ibte_iterate(epwi_ctx *c, int max_iter, double tol) {
             ms_steps += ms;
             ++it;
             std::swap(c->ib_F, c->ib_Fn);
+            std::swap(c->ib_F32, c->ib_Fn32);
             double dmax, fmax_;
             std::memcpy(&dmax, &h[0], sizeof(double));
             std::memcpy(&fmax_, &h[1], sizeof(double));
@@ -273,7 +357,7 @@ void ibte_iterate(epwi_ctx *c, int max_iter, double tol) {
     c->ib_stats.iters = it;
     c->ib_stats.change = change;
     c->ib_stats.ms_step = it > 0 ? ms_steps / it : 0.0;
-    // one step reads the q list and Gamma once, F0, 1/tau and F at the states, writes F
+    // one step reads the pair codes and Gamma once, F0, 1/tau and F at the states, writes F
     c->ib_stats.bytes_per_step = 4.0 * (double)c->npairs +
                                  (double)c->ib_stats.entry_bytes * (double)c->ib_stats.n_entries +
                                  8.0 * (double)ns * (3 + 1 + 3 + 3);

@@ -351,6 +351,16 @@ def si_like_system(seed: int = 3) -> System:
                        n_valence=4, gap_ev=1.1)
 
 
+def time_reversal_symmetric(sysm: System) -> System:
+    """The same crystal with real Wannier-basis H(R) and g(Re, Rp) (their real parts).
+
+    With H(-R) = H(R)^T real, H(-k) = H(k)^* and eps(-k) = eps(k), v(-k) = -v(k); with real g,
+    |g(-k,-q)| = |g(k,q)|.  A Gamma-centred grid is closed under k -> -k, so every sum of an
+    odd function of k vanishes exactly, as for a crystal with time-reversal symmetry."""
+    return dataclasses.replace(sysm, name=sysm.name + "_tr", H=sysm.H.real.astype(complex),
+                               g=sysm.g.real.astype(complex))
+
+
 def einstein_system(t_ev: float = 0.5, a: float = 3.0, spring: float = 5.0,
                     g_ev_a: float = 0.05) -> System:
     """Isotropic-scattering test crystal: simple cubic, one s-like Wannier function with

@@ -133,3 +133,20 @@ def test_chunking_and_repeat_are_bitwise_identical(tiny6):
     c = _run(s, (6, 6, 6), mu, lo, hi, eta, 12, 0.0)
     assert np.array_equal(a["F"], b["F"]) and np.array_equal(a["F"], c["F"])
     assert np.array_equal(a["r"], b["r"])
+
+
+def test_fp64_time_reversal_symmetric_metal_converges_to_the_oracle():
+    """Real H(R) and g: the drive of the number-conserving mode vanishes and the iteration
+    converges in tens of steps; converged F and sigma match the oracle."""
+    s = synth.time_reversal_symmetric(synth.al_like_system())
+    gr, mu, lo, hi, eta = _case(s, (10, 10, 10), 0.3, 0.05)
+    ref = O.ibte(gr, T, mu, eta, lo, hi, max_iter=500, tol=1e-11)
+    assert ref["iters"] < 200
+    res = _run(s, (10, 10, 10), mu, lo, hi, eta, 500, 1e-11)
+    o = _ordered(res, ref)
+    assert abs(res["it"] - ref["iters"]) <= 1
+    assert np.abs(res["F"][o] - ref["F"]).max() <= 1e-9 * np.abs(ref["F"]).max()
+    v = gr.velocities(ref["ik"], ref["n"])
+    e = gr.eps[ref["ik"], ref["n"]]
+    sig = O.transport_from_F(s.volume, gr.nk, v, ref["F"], e, mu, T)[0]
+    assert np.abs(res["tr"][0] - sig).max() <= 1e-9 * np.abs(sig).max()

@@ -125,3 +125,23 @@ def test_transport_from_vtau_is_the_serta_transport(tiny5):
     b = O.transport_coefficients(gr.sys.volume, gr.nk, v, ref["inv_tau"], e, mu, T)
     for x, y in zip(a, b):
         assert np.allclose(x, y, rtol=1e-12, atol=1e-12 * np.abs(y).max())
+
+
+def test_time_reversal_inputs_cancel_the_number_mode_drive():
+    """With real H(R) and g, eps(-k) = eps(k) and v(-k) = -v(k) on the Gamma-centred grid, so
+    sum f(1-f) v over the window vanishes and the iteration converges quickly; with the
+    complex inputs it does not vanish."""
+    base = synth.al_like_system()
+    for sysm, zero in ((synth.time_reversal_symmetric(base), True), (base, False)):
+        gr = O.Grids(sysm, (8, 8, 8))
+        mu = gr.band_centre()
+        ik, n = gr.window_states(mu - 0.3, mu + 0.3)
+        v = gr.velocities(ik, n)
+        f = O.fermi(gr.eps[ik, n], mu, T)
+        w = (f * (1 - f))[:, None]
+        drive = np.abs((w * v).sum(axis=0)).max() / np.abs(w * v).sum(axis=0).max()
+        assert (drive < 1e-12) == zero
+    gr = O.Grids(synth.time_reversal_symmetric(base), (8, 8, 8))
+    mu = gr.band_centre()
+    res = O.ibte(gr, T, mu, 0.05, mu - 0.3, mu + 0.3, max_iter=500, tol=1e-10)
+    assert res["iters"] < 200
