@@ -22,6 +22,7 @@
 // butterfly, then warps in index order), so the result does not depend on scheduling.
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 
 #include "epwi_internal.cuh"
 #include "scatter.cuh"
@@ -93,6 +94,7 @@ struct StepArgs {
     float4 *Fout32;
     double pref;                          // 2 pi / (hbar N_q sqrt(pi) eta), s^-1 per eV^2
     unsigned long long *red;              // [2] max |dF|, max |F| as bit patterns
+    int narrow;                           // every window has <= 4 bands: narrow-window path
 };
 
 // Accumulation type of the lane and warp sums: FP64 with FP64 Gamma; FP32 with FP32 Gamma
@@ -151,6 +153,71 @@ __device__ __forceinline__ void step_pairs(const StepArgs<GT> &a, int nsel, int 
     }
 }
 
+// Narrow windows (every k+q window <= JMAX bands, this group NBX bands): each lane takes PPL
+// pairs per round (pairs pb + i*32 + lane), issues all their F and Gamma loads (predicated on
+// the pair's band count) before any multiply, so PPL x JMAX loads are in flight per lane.
+template <typename GT, int NB, int NBX, int JMAX, int PPL>
+__device__ __forceinline__ void step_pairs_narrow(const StepArgs<GT> &a, int nsel, int b0, int64_t wb,
+                                                  int64_t we, int lane, typename Acc<GT>::T (&y)[NB][3]) {
+    using AT = typename Acc<GT>::T;
+    int64_t off = wb < we ? a.goff[wb] : 0;
+    unsigned cnext[PPL];
+#pragma unroll
+    for (int i = 0; i < PPL; ++i) {
+        const int64_t p = wb + i * 32 + lane;
+        cnext[i] = p < we ? __ldg(a.code + p) : 0u;
+    }
+    for (int64_t pb = wb; pb < we; pb += 32 * PPL) {
+        unsigned cd[PPL];
+        int64_t base[PPL];
+#pragma unroll
+        for (int i = 0; i < PPL; ++i) {
+            cd[i] = cnext[i];
+            const int64_t p = pb + 32 * PPL + i * 32 + lane;
+            cnext[i] = p < we ? __ldg(a.code + p) : 0u;
+        }
+#pragma unroll
+        for (int i = 0; i < PPL; ++i) {
+            const int size = nsel * (int)(cd[i] & 31u);
+            int incl = size;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            base[i] = off + (incl - size);
+            off += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        AT f[PPL][JMAX][3], g[PPL][JMAX][NBX];
+#pragma unroll
+        for (int i = 0; i < PPL; ++i) {
+            const int nw = (int)(cd[i] & 31u);
+            const int64_t sb = (int64_t)(cd[i] >> 5);
+#pragma unroll
+            for (int j = 0; j < JMAX; ++j) {
+                f[i][j][0] = f[i][j][1] = f[i][j][2] = 0;
+#pragma unroll
+                for (int n = 0; n < NBX; ++n) g[i][j][n] = 0;
+                if (j < nw) {
+                    load_F(a, sb + j, f[i][j][0], f[i][j][1], f[i][j][2]);
+#pragma unroll
+                    for (int n = 0; n < NBX; ++n) g[i][j][n] = (AT)__ldg(a.gam + base[i] + (int64_t)(b0 + n) * nw + j);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < PPL; ++i)
+#pragma unroll
+            for (int j = 0; j < JMAX; ++j)
+#pragma unroll
+                for (int n = 0; n < NBX; ++n) {
+                    y[n][0] = fma(g[i][j][n], f[i][j][0], y[n][0]);
+                    y[n][1] = fma(g[i][j][n], f[i][j][1], y[n][1]);
+                    y[n][2] = fma(g[i][j][n], f[i][j][2], y[n][2]);
+                }
+    }
+}
+
 template <typename GT, int kIbBands>
 __global__ void __launch_bounds__(kIbThreads, kIbBands <= 2 ? 4 : (kIbBands <= 4 ? 3 : 2)) k_ib_step(StepArgs<GT> a) {
     using AT = typename Acc<GT>::T;
@@ -169,7 +236,15 @@ __global__ void __launch_bounds__(kIbThreads, kIbBands <= 2 ? 4 : (kIbBands <= 4
 #pragma unroll
         for (int n = 0; n < kIbBands; ++n) y[n][0] = y[n][1] = y[n][2] = 0;
         // exact band count of this group (uniform over the block)
-        switch (nb) {
+        // narrow-window path: FP32 Gamma and 4-band groups (the register budget of the other
+        // instantiations has no room for its staged loads)
+        constexpr bool kNarrow = std::is_same<GT, float>::value && kIbBands == 4;
+        if (kNarrow && a.narrow && nb <= 2) {
+            if constexpr (kNarrow) {
+                if (nb == 1) step_pairs_narrow<GT, kIbBands, 1, 4, 2>(a, nsel, b0, wb, we, lane, y);
+                else step_pairs_narrow<GT, kIbBands, 2, 4, 2>(a, nsel, b0, wb, we, lane, y);
+            }
+        } else switch (nb) {
         case 1: step_pairs<GT, kIbBands, 1>(a, nsel, b0, wb, we, lane, y); break;
         case 2: if constexpr (kIbBands >= 2) step_pairs<GT, kIbBands, 2>(a, nsel, b0, wb, we, lane, y); break;
         case 3: if constexpr (kIbBands >= 3) step_pairs<GT, kIbBands, 3>(a, nsel, b0, wb, we, lane, y); break;
@@ -231,6 +306,7 @@ void launch_step(epwi_ctx *c, const double *Fin, double *Fout, const float4 *Fin
     a.Fin32 = Fin32;
     a.Fout32 = Fout32;
     a.pref = 2.0 * epc::kPi / epc::kHbarEVs / (double)c->nk / (sqrt(epc::kPi) * c->eta);
+    a.narrow = c->nw <= 4;
     a.red = c->ib_red.as<unsigned long long>();
     // band group: the smallest of 1, 2, 4, 8 covering the bands (wider windows loop)
     const unsigned grid = (unsigned)c->nkp;
