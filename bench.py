@@ -585,6 +585,61 @@ def run_ibte(args):
     print(json.dumps(line), flush=True)
 
 
+def run_kbatch(args):
+    """Ordering ablation (Sec. III C, Table 3): the same FP64 rates call with the q-batch and
+    the k-batch interpolation order on the Al-like metal."""
+    import torch
+    from paper_2306_16493_gb300 import epwi, synth
+    torch.cuda.set_device(0)
+    s = synth.al_like_system(WORKLOAD["seed"])
+    N = args.ablation_grid
+    T, eta, win = WORKLOAD["T_K"], WORKLOAD["smear_eV"], WORKLOAD["window_eV"]
+    stream = torch.cuda.current_stream()
+    res = {}
+    for ordering in ("q-batch", "k-batch"):
+        ctx = epwi.Context(precision="fp64", device=0, stream=stream.cuda_stream, ordering=ordering)
+        ctx.setup(s)
+        ctx.eigs(N)
+        lo, hi = ctx.band_range()
+        mu = 0.5 * (lo + hi)
+        for _ in range(args.warmup):
+            ctx.scatter_rates(T, mu, eta, mu - win, mu + win)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        sts = []
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            ctx.scatter_rates(T, mu, eta, mu - win, mu + win)
+            ev[k][1].record(stream)
+            sts.append(ctx.stats())
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+        st = sts[-1]
+        interp = statistics.mean(x["ms_restage"] + x["ms_scatter"] for x in sts)
+        res[ordering] = {"ms_rates_call": ms, "ms_interpolation": interp,
+                         "ms_restage": statistics.mean(x["ms_restage"] for x in sts),
+                         "ms_scatter": statistics.mean(x["ms_scatter"] for x in sts),
+                         "pairs": st["n_pairs"], "pairs_per_s": st["n_pairs"] / (ms * 1e-3),
+                         "tiles": st["n_tiles"], "interp_tflops": st["scatter_flops"] / (interp * 1e-3) / 1e12,
+                         "rates": ctx.rates()[2], "n_k": st["n_states"] / max(1, st["n_kpoints"])}
+        ctx.close()
+    q, k = res["q-batch"], res["k-batch"]
+    k.pop("n_k")
+    rq, rk = q.pop("rates"), k.pop("rates")
+    rel = float(np.abs(rq - rk).max() / np.abs(rq).max())
+    nbar = q.pop("n_k")
+    line = {"metric": "k-batch / q-batch time of the interpolation stages (Re->k + Rp->q), FP64",
+            "value": k["ms_interpolation"] / q["ms_interpolation"], "unit": "x", "higher_is_better": True,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None,
+            "config": dict(WORKLOAD, grid=N, workload=f"al_like_{N}_ordering_ablation", precision="fp64"),
+            "rates_call_ratio": k["ms_rates_call"] / q["ms_rates_call"],
+            "q_batch": q, "k_batch": k, "max_rel_rate_difference": rel,
+            "mean_window_bands_n_k": nbar,
+            "predicted_mac_ratio": (s.nw / nbar) * (len(s.Re) / len(s.Rp))}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -597,7 +652,7 @@ def main():
                     help="k and q grid per axis (48 is the benchmark; smaller sizes are for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="al_like",
-                    choices=["al_like", "batch64", "si_like_learned", "al_like_ibte"],
+                    choices=["al_like", "batch64", "si_like_learned", "al_like_ibte", "ordering_ablation"],
                     help="al_like: the benchmark; batch64 and si_like_learned: the batched and "
                          "learned-proposal workloads (reported separately)")
     ap.add_argument("--batch-scale", type=int, default=3, help="batch64: grid divisor")
@@ -609,6 +664,7 @@ def main():
     ap.add_argument("--learned-samples", type=int, nargs="+", default=[10000, 100000])
     ap.add_argument("--ibte-iters", type=int, default=200, help="al_like_ibte: iteration cap")
     ap.add_argument("--ibte-tol", type=float, default=1e-6, help="al_like_ibte: max |dF| / max |F|")
+    ap.add_argument("--ablation-grid", type=int, default=24, help="ordering_ablation: grid per axis")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -618,6 +674,8 @@ def main():
         run_learned(args)
     elif args.workload == "al_like_ibte":
         run_ibte(args)
+    elif args.workload == "ordering_ablation":
+        run_kbatch(args)
     else:
         run_gpu(args)
 

@@ -92,6 +92,12 @@ typedef struct {
                                    TMEM (default); 1 = precomputed split rows of every q gathered
                                    into shared memory (fp16x3, bf16x3, when the rows take
                                    <= 16 GiB; measured slower on the 48^3 benchmark) */
+    int32_t ordering;           /* interpolation order of epwi_scatter_rates (Sec. III C):
+                                   0 = q-batch (default): Re->k once per k-point, Rp->q per pair;
+                                   1 = k-batch, the ordering the paper compares against (Table 3):
+                                   Rp->q (with u(q)) once per q-point, Re->k and both rotations
+                                   per pair.  k-batch is FP64 only (EUNSUPPORTED otherwise), for
+                                   nw <= 8 and <= 6 modes; same rates within rounding */
 } epwi_options;
 
 /* Per-call statistics of the last epwi_scatter_rates (and what precedes it). */

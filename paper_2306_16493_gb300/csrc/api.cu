@@ -102,6 +102,7 @@ void epwi_default_options(epwi_options *opt) {
     opt->cuda_stream = nullptr;
     opt->kpoint_chunk = 0;
     opt->tc_a_operand = 0;
+    opt->ordering = 0;
 }
 
 epwi_status epwi_create(epwi_ctx **out, const epwi_options *opt) {
@@ -496,9 +497,15 @@ void finish_transport(epwi_ctx *c, const double (&m)[3][9], double *sigma, doubl
 epwi_status epwi_scatter_rates(epwi_ctx *c, double T, double mu, double eta, double emin,
                                double emax, int64_t *n_states, int64_t *n_pairs) {
     return guard(c, [&] {
+        EPWI_REQUIRE(c->opt.ordering == 0 || c->opt.ordering == 1, EPWI_EINVAL, "ordering must be 0 or 1");
+        EPWI_REQUIRE(c->opt.ordering == 0 || c->opt.precision == EPWI_FP64, EPWI_EUNSUPPORTED,
+                     "the k-batch ordering is FP64 only");
         WorkSet ws = begin_rates(c, T, mu, eta, emin, emax);
-        process_workset(c, ws, nullptr);
+        if (c->opt.ordering == 1) process_kbatch(c);
+        else process_workset(c, ws, nullptr);
         end_rates(c);
+        if (c->opt.ordering == 1)      // per pair: n_Re x N_m x W x W complex MACs instead
+            c->stats.scatter_flops = 8.0 * c->nRe * c->nm * c->nw * c->nw * (double)c->npairs;
         if (n_states) *n_states = c->nstates;
         if (n_pairs) *n_pairs = c->npairs;
     });

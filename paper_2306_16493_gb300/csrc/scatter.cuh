@@ -100,3 +100,6 @@ int tc_check_error(epwi_ctx *c);
 // capture of ws); iteration from F0 = v tau into ib_F.
 void ibte_prepare(epwi_ctx *c, WorkSet &ws);
 void ibte_iterate(epwi_ctx *c, int max_iter, double tol);
+
+// Rates of the current window by the k-batch ordering (FP64 ablation); fills inv_tau.
+void process_kbatch(epwi_ctx *c);

@@ -43,7 +43,7 @@ class epwi_system(C.Structure):
 class epwi_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("sieve_c", C.c_double), ("omega_min_eV", C.c_double),
                 ("device", C.c_int32), ("cuda_stream", C.c_void_p), ("kpoint_chunk", C.c_int32),
-                ("tc_a_operand", C.c_int32)]
+                ("tc_a_operand", C.c_int32), ("ordering", C.c_int32)]
 
 
 class epwi_stats(C.Structure):
@@ -531,7 +531,7 @@ class Context:
     """One library context (device memory, stream, last results)."""
 
     def __init__(self, precision="fp64", device=0, stream=None, sieve_c=6.0, omega_min=1e-4,
-                 kpoint_chunk=0, tc_a_operand=0):
+                 kpoint_chunk=0, tc_a_operand=0, ordering="q-batch"):
         o = epwi_default_options()
         o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         o.device = device
@@ -540,6 +540,7 @@ class Context:
         o.omega_min_eV = omega_min
         o.kpoint_chunk = kpoint_chunk
         o.tc_a_operand = tc_a_operand
+        o.ordering = {"q-batch": 0, "k-batch": 1}[ordering] if isinstance(ordering, str) else int(ordering)
         self.h = epwi_create(o)
         self.nk = self.nw = self.nm = 0
         self.n_states = 0
