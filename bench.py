@@ -33,7 +33,7 @@ WORKLOAD = dict(workload="al_like_48", system="Al-like fcc, nw=4, 3 modes, 5^3 W
                 grid=48, window_eV=0.3, smear_eV=0.02, T_K=300.0, mu="band centre", seed=2)
 CHOSEN = "fp16x3"
 DTYPE = {"fp64": "f64", "tf32x3": "tf32x3 (f32 acc, f64 sums)", "bf16x3": "bf16x3 (f32 acc, f64 sums)",
-         "fp16x3": "fp16x3 (f32 acc, f64 sums)"}
+         "fp16x3": "fp16x3 (f32 acc, f64 sums)", "fp32": "f32 (sum-factorised, f64 sums)"}
 L2_BYTES = 129 * 2 ** 20
 # DRAM bytes (read + write) per (k,q) pair of k_scatter_tc, fp16x3, from one ncu capture of
 # the 24^3 case (255 MB / 19.6 M pairs, ncu --set full).
@@ -62,6 +62,12 @@ def roofline_for(precision, stats, per_launch_traffic=None):
         bound, unit = "alu", "TFLOP/s"
         achieved = flops / (ms * 1e-3) / 1e12
         note = "FP64 peak derived: 152 SM x 4 flop/clk x 2.07 GHz"
+    elif precision == "fp32":
+        # sum-factorised FP32 kernel: CUDA-core FMA peak, 152 SM x 128 lanes x 2 flop x 2.07 GHz
+        peak = FP32_PEAK_TFLOPS
+        bound, unit = "alu", "TFLOP/s"
+        achieved = flops / (ms * 1e-3) / 1e12
+        note = "FP32 peak derived: 152 SM x 128 FMA lanes x 2 flop x 2.07 GHz"
     else:
         ratio = 0.5 if precision == "tf32x3" else 1.0
         peak = mp["bf16_tflops"] * ratio
@@ -70,7 +76,8 @@ def roofline_for(precision, stats, per_launch_traffic=None):
         note = f"{src} bf16 burst peak x {ratio}"
     return {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
             "frac": achieved / peak, "traffic": per_launch_traffic, "traffic_unit": "bytes per launch",
-            "kernel": "k_scatter (fused Rp->q GEMM + rotations + delta sum)",
+            "kernel": ("k_scatter_sf (sum-factorised Rp->q + rotations + delta sum)" if precision == "fp32"
+                       else "k_scatter (fused Rp->q GEMM + rotations + delta sum)"),
             "launches_per_step": stats["n_chunks"], "peak_source": note}
 
 
@@ -645,7 +652,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--precision", default=CHOSEN, choices=["fp64", "tf32x3", "bf16x3", "fp16x3"])
+    ap.add_argument("--precision", default=CHOSEN, choices=["fp64", "tf32x3", "bf16x3", "fp16x3", "fp32"])
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--ref-kpoints", type=int, default=40)
     ap.add_argument("--grid", type=int, default=WORKLOAD["grid"],

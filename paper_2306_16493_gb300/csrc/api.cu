@@ -117,7 +117,7 @@ epwi_status epwi_create(epwi_ctx **out, const epwi_options *opt) {
     if (opt) c->opt = *opt;
     else epwi_default_options(&c->opt);
     if (!(c->opt.sieve_c > 0) || !(c->opt.omega_min_eV >= 0) || c->opt.precision < 0 ||
-        c->opt.precision > EPWI_FP16X3) {
+        c->opt.precision > EPWI_FP32) {
         delete c;
         return EPWI_EINVAL;
     }
@@ -151,7 +151,7 @@ const char *epwi_last_error(const epwi_ctx *c) { return c ? c->err.c_str() : "nu
 
 epwi_status epwi_set_precision(epwi_ctx *c, int32_t p) {
     return guard(c, [&] {
-        EPWI_REQUIRE(p >= EPWI_FP64 && p <= EPWI_FP16X3, EPWI_EINVAL, "unknown precision");
+        EPWI_REQUIRE(p >= EPWI_FP64 && p <= EPWI_FP32, EPWI_EINVAL, "unknown precision");
         c->opt.precision = p;
     });
 }
@@ -458,8 +458,15 @@ void end_rates(epwi_ctx *c) {
     c->stats.n_pairs = c->npairs;
     c->stats.restage_bytes = (int64_t)c->stats.n_chunks * c->nRe * c->nRp * c->nm * c->nw *
                              c->nw * (c->opt.precision == EPWI_FP64 ? 16 : 8);
-    c->stats.scatter_flops = 8.0 * c->nRp * c->nm * c->nw * (double)c->npairs *
-                             ((double)c->nstates / std::max<int64_t>(1, c->nkp));
+    const double nbar = (double)c->nstates / std::max<int64_t>(1, c->nkp);
+    c->stats.scatter_flops = 8.0 * c->nRp * c->nm * c->nw * (double)c->npairs * nbar;
+    if (c->opt.precision == EPWI_FP32 && c->rp_cube_r >= 0) {
+        // per (pair, band): the R3 sum, U(k+q) and u(q) rotations (the per-block and per-run
+        // sums are shared and not counted)
+        const double D = 2 * c->rp_cube_r + 1, X = (double)c->nm * c->nw;
+        c->stats.scatter_flops = 8.0 * (D * X + (double)c->nw * c->nw * c->nm + (double)c->nm * c->nm * c->nw) *
+                                 (double)c->npairs * nbar;
+    }
     c->have_rates = true;
 }
 
@@ -516,6 +523,8 @@ epwi_status epwi_ibte(epwi_ctx *c, double T, double mu, double eta, double emin,
     return guard(c, [&] {
         EPWI_REQUIRE(max_iter >= 0 && tol >= 0 && std::isfinite(tol), EPWI_EINVAL,
                      "need max_iter >= 0 and a finite tol >= 0");
+        EPWI_REQUIRE(c->opt.precision != EPWI_FP32, EPWI_EUNSUPPORTED,
+                     "the iterative BTE runs in FP64 or a split precision");
         cudaEvent_t e0, e1;
         EPWI_CUDA(cudaEventCreate(&e0));
         EPWI_CUDA(cudaEventCreate(&e1));

@@ -159,6 +159,7 @@ struct epwi_ctx {
     DevBuf tc_err;                 // int: timed-out waits in the tensor-core kernel
     DevBuf tc_meta;                // per-tile metadata of the tensor-core kernel
     DevBuf tc_arows;               // gathered-A mode: split phase rows of every grid point
+    DevBuf sf_items;               // fp32 mode: (k-point, band) work items of a chunk
     int64_t tc_arows_key = -1;
     bool tc_gather = false;        // use the gathered-A mode where it applies
     int64_t stats_tc_grid = 0;
@@ -194,7 +195,7 @@ struct epwi_ctx {
                          &scan_tmp, &red_tmp, &counts, &tc_ptab, &tc_erel, &tc_f32,
                          &tc_n32, &tc_hw32, &tc_err, &tc_meta, &is_pairs, &is_w,
                          &is_kp_pairs, &sieve_mask, &tc_arows, &ib_pairs, &ib_goff, &ib_gam,
-                         &ib_kpos, &ib_F0, &ib_F, &ib_Fn, &ib_red, &ib_F32, &ib_Fn32};
+                         &ib_kpos, &ib_F0, &ib_F, &ib_Fn, &ib_red, &ib_F32, &ib_Fn32, &sf_items};
         for (DevBuf *b : all) b->release();
         mlp_free(mlp);
     }

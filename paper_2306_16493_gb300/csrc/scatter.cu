@@ -282,23 +282,26 @@ int64_t run_chunk(epwi_ctx *c, const WorkSet &ws, const ChunkView &cv, double *g
                   int tstride, StageTimers &tm) {
     const int W = c->nw, Nm = c->nm;
     const int64_t nrow = (int64_t)c->nRp * Nm * W;
-    const bool tc = c->opt.precision != EPWI_FP64;
-    const size_t state_bytes = tc ? tc_state_bytes(c) : sizeof(double2) * nrow;
+    const bool sf = c->opt.precision == EPWI_FP32;
+    const bool tc = !sf && c->opt.precision != EPWI_FP64;
+    const size_t state_bytes = sf ? sf_state_bytes(c) : tc ? tc_state_bytes(c) : sizeof(double2) * nrow;
     GridInfo g = make_grid_info(c);
     const int64_t nkpc = cv.kp1 - cv.kp0;
-    // tiles
-    c->kp_tile.ensure(sizeof(int64_t) * (nkpc + 1));
-    c->scan_tmp.ensure(sizeof(int64_t) * (nkpc + 1));
-    k_tiles_count<<<(unsigned)((nkpc + 255) / 256), 256, 0, c->stream>>>(
-        nkpc, cv.kp_pairs, cv.p_off, c->scan_tmp.as<int64_t>());
-    EPWI_CHECK_LAUNCH();
+    // tiles (the fp32 mode works per (k-point, band) instead)
     int64_t nt = 0;
-    scan_exclusive_i64(c, c->scan_tmp.as<int64_t>(), c->kp_tile.as<int64_t>(), nkpc, &nt);
-    c->tiles.ensure(sizeof(int4) * (nt + 1));
-    c->tile_part.ensure(sizeof(double) * epc::kMaxW * (nt + 1));
-    k_tiles_fill<<<(unsigned)((nkpc + 255) / 256), 256, 0, c->stream>>>(
-        nkpc, cv.kp_pairs, cv.p_off, c->kp_tile.as<int64_t>(), c->tiles.as<int4>());
-    EPWI_CHECK_LAUNCH();
+    if (!sf) {
+        c->kp_tile.ensure(sizeof(int64_t) * (nkpc + 1));
+        c->scan_tmp.ensure(sizeof(int64_t) * (nkpc + 1));
+        k_tiles_count<<<(unsigned)((nkpc + 255) / 256), 256, 0, c->stream>>>(
+            nkpc, cv.kp_pairs, cv.p_off, c->scan_tmp.as<int64_t>());
+        EPWI_CHECK_LAUNCH();
+        scan_exclusive_i64(c, c->scan_tmp.as<int64_t>(), c->kp_tile.as<int64_t>(), nkpc, &nt);
+        c->tiles.ensure(sizeof(int4) * (nt + 1));
+        c->tile_part.ensure(sizeof(double) * epc::kMaxW * (nt + 1));
+        k_tiles_fill<<<(unsigned)((nkpc + 255) / 256), 256, 0, c->stream>>>(
+            nkpc, cv.kp_pairs, cv.p_off, c->kp_tile.as<int64_t>(), c->tiles.as<int4>());
+        EPWI_CHECK_LAUNCH();
+    }
     cudaEventRecord(tm.fill.e[1], c->stream);
     // Re->k
     c->ghat.ensure(state_bytes * (cv.ns + 1));
@@ -329,7 +332,8 @@ int64_t run_chunk(epwi_ctx *c, const WorkSet &ws, const ChunkView &cv, double *g
     ra.precision = c->opt.precision;
     ra.nstates_chunk = cv.ns;
     cudaEventRecord(tm.re.e[0], c->stream);
-    if (tc) tc_restage(c, ra);
+    if (sf) sf_restage(c, ra);
+    else if (tc) tc_restage(c, ra);
     else fp64_restage(ra, W, c->stream);
     cudaEventRecord(tm.re.e[1], c->stream);
     // Rp->q + rotations + delta sum
@@ -383,12 +387,18 @@ int64_t run_chunk(epwi_ctx *c, const WorkSet &ws, const ChunkView &cv, double *g
             sa.nsel_max = std::max<int64_t>(sa.nsel_max, ws.h_kp_state[p + 1] - ws.h_kp_state[p]);
     }
     cudaEventRecord(tm.sc.e[0], c->stream);
-    if (tc) tc_scatter(c, sa, nt);
-    else fp64_scatter(sa, nt, c->stream);
+    if (sf) {
+        std::vector<int64_t> hks(ws.h_kp_state.begin() + cv.kp0, ws.h_kp_state.begin() + cv.kp1 + 1);
+        sf_scatter(c, sa, nkpc, cv.kp_pairs, cv.p_off, hks);
+    } else if (tc) {
+        tc_scatter(c, sa, nt);
+    } else {
+        fp64_scatter(sa, nt, c->stream);
+    }
     cudaEventRecord(tm.sc.e[1], c->stream);
-    // reduce
+    // reduce (the fp32 mode wrote 1/tau already)
     cudaEventRecord(tm.red.e[0], c->stream);
-    if (!g2out && !tout && nkpc > 0) {
+    if (!sf && !g2out && !tout && nkpc > 0) {
         const double pref = 2.0 * epc::kPi / epc::kHbarEVs / (double)c->nk /
                             (sqrt(epc::kPi) * c->eta);
         k_reduce_tiles<<<(unsigned)((nkpc + 127) / 128), 128, 0, c->stream>>>(
@@ -416,11 +426,15 @@ int64_t run_chunk(epwi_ctx *c, const WorkSet &ws, const ChunkView &cv, double *g
 void process_workset(epwi_ctx *c, const WorkSet &ws, double *g2out, double *tout, int tstride) {
     const int W = c->nw, Nm = c->nm;
     const int64_t nrow = (int64_t)c->nRp * Nm * W;
-    const bool tc = c->opt.precision != EPWI_FP64;
+    const bool sf = c->opt.precision == EPWI_FP32;
+    const bool tc = !sf && c->opt.precision != EPWI_FP64;
     EPWI_REQUIRE(!tc || !tout, EPWI_EINVAL, "per-pair terms need the FP64 path");
+    EPWI_REQUIRE(!sf || (!g2out && !tout && !ws.pair_w && !ws.gam32 && !ws.gam64 && ws.ovr_nsel < 0),
+                 EPWI_EUNSUPPORTED, "the fp32 mode serves the sieved rates of epwi_scatter_rates only");
+    if (sf) sf_check(c);
     // chunk limits: pairs and Re->k output size
     const int64_t max_pairs = int64_t(1) << 27;
-    const size_t state_bytes = tc ? tc_state_bytes(c) : sizeof(double2) * nrow;
+    const size_t state_bytes = sf ? sf_state_bytes(c) : tc ? tc_state_bytes(c) : sizeof(double2) * nrow;
     const int64_t max_states = std::max<int64_t>(1, (int64_t)((size_t(3) << 30) / state_bytes));
     const int64_t kp_cap = c->opt.kpoint_chunk > 0 ? c->opt.kpoint_chunk : (int64_t)1 << 40;
     StageTimers tm;

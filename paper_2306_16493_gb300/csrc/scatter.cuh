@@ -103,3 +103,10 @@ void ibte_iterate(epwi_ctx *c, int max_iter, double tol);
 
 // Rates of the current window by the k-batch ordering (FP64 ablation); fills inv_tau.
 void process_kbatch(epwi_ctx *c);
+
+// fp32 mode (sum-factorised Rp->q, scatter_sf.cu)
+size_t sf_state_bytes(const epwi_ctx *c);
+void sf_check(const epwi_ctx *c);
+void sf_restage(epwi_ctx *c, const RestageArgs &ra);
+void sf_scatter(epwi_ctx *c, const ScatterArgs &sa, int64_t nkp, const int64_t *kp_pairs_local, int64_t p_off,
+                const std::vector<int64_t> &h_kp_state_chunk);

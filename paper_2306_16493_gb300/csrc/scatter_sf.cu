@@ -1,0 +1,364 @@
+// Sum-factorised Rp->q stage in FP32 (precision EPWI_FP32), fused with the rotations and the
+// delta sum of Eq. 10.
+//
+// R_p is the full cube [-r, r]^3, so the phase of Eq. 16 factorises per axis:
+// e^{iq.Rp} = e1(q1, R1) e2(q2, R2) e3(q3, R3) with e_a(x, R) = e^{2 pi i x R / N_a}.  The sum
+// over the cube is then three nested sums of D = 2r + 1 terms, and each is done where its
+// result can be shared.  The sieve lists the pairs of a k-point in plane blocks pb of 256
+// consecutive (q2, q3) combinations, then by q1, then by combination.
+//   Y[R1][R3][j]  = sum_R2 e2(q2_j, R2) ghat[R1, R2, R3]   once per plane block (its q2 values j)
+//   U[R3][j]      = sum_R1 e1(q1, R1) Y[R1][R3][j]          once per run (plane block, q1)
+//   G             = sum_R3 e3(q3, R3) U[R3][j(q)]           per pair
+// with ghat = (g P^el) U^dag(k) from the FP32 Re->k stage, every column (mu, i) at once.  A
+// pair costs D N_m W complex MACs instead of D^3 N_m W.  Then, per pair, come the rotations
+// U(k+q) [.] u(q), |g|^2 and the two delta terms, in FP32.
+//
+// One CTA per (window k-point, band), eight warps.  Warps take the runs of a plane block
+// round-robin by q1.  Lane sums are FP32 within a run; the run sums go into per-warp FP64
+// accumulators, which are added in warp order, so the result is deterministic.
+#include <algorithm>
+
+#include "epwi_internal.cuh"
+#include "scatter.cuh"
+#include "sieve.cuh"
+
+namespace {
+
+constexpr int kSfThreads = 256;
+constexpr int kSfWarps = kSfThreads / 32;
+
+// Re->k in FP32: ghat32[state][row] = sum_j [sum_Re w e^{ik.Re} g(Re)[row][j]] V_{j, lo+n}(k),
+// row = (rp N_m + mu) W + i; one thread per row, KG k-points per block row.
+template <int WT, int KG>
+__global__ void __launch_bounds__(128) k_restage_f32(RestageArgs a, float2 *__restrict__ out) {
+    constexpr int WM = WT ? WT : epc::kMaxW;
+    const int W = WT ? WT : a.W;
+    extern __shared__ float2 P32[];                 // [KG][nRe]
+    const int kg0 = blockIdx.y * KG;
+    for (int idx = threadIdx.x; idx < KG * a.nRe; idx += blockDim.x) {
+        const int kk = idx / a.nRe, r = idx % a.nRe;
+        float2 p = make_float2(0.f, 0.f);
+        if (kg0 + kk < a.nkp) {
+            int i1, i2, i3;
+            grid_coords(a.g, a.kpts[kg0 + kk], i1, i2, i3);
+            p = a.ph32[phase_index(i1 * a.g.s1 % a.g.L, i2 * a.g.s2 % a.g.L, i3 * a.g.s3 % a.g.L,
+                                   a.Re[3 * r], a.Re[3 * r + 1], a.Re[3 * r + 2], a.g.L)];
+        }
+        P32[idx] = p;
+    }
+    __syncthreads();
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= a.nrow) return;
+    float2 acc[KG][WM];
+    for (int kk = 0; kk < KG; ++kk)
+        for (int j = 0; j < W; ++j) acc[kk][j] = make_float2(0.f, 0.f);
+    const float2 *gw = a.gw32 + (size_t)row * W;
+    for (int r = 0; r < a.nRe; ++r) {
+        float2 gv[WM];
+        for (int j = 0; j < W; ++j) gv[j] = gw[(size_t)r * a.nrow * W + j];
+        for (int kk = 0; kk < KG; ++kk) {
+            const float2 p = P32[kk * a.nRe + r];
+            for (int j = 0; j < W; ++j) acc[kk][j] = cfmaf(p, gv[j], acc[kk][j]);
+        }
+    }
+    for (int kk = 0; kk < KG; ++kk) {
+        if (kg0 + kk >= a.nkp) break;
+        const int ik = a.kpts[kg0 + kk];
+        const int lo = a.win_lo[ik], ns = a.win_n[ik];
+        const int64_t s0 = a.kp_state[kg0 + kk] - a.s_base;
+        const float2 *Vk = a.V32 + (int64_t)ik * W * W;
+        for (int np = 0; np < ns; ++np) {
+            float2 o = make_float2(0.f, 0.f);
+            for (int j = 0; j < W; ++j) o = cfmaf(acc[kk][j], Vk[j * W + lo + np], o);
+            out[(s0 + np) * a.nrow + row] = o;
+        }
+    }
+}
+
+struct SfArgs {
+    GridInfo g;
+    int64_t nplane;                 // N2 N3
+    int nq2max;                     // largest count of q2 values in one plane block
+    const float2 *ph32;             // e^{2 pi i m / L}
+    const float2 *ghat;             // [state - s_base][D^3][N_m][W]
+    const int *kpts, *win_lo, *win_n;
+    const int64_t *kp_state;        // chunk k-points' first states (global)
+    int64_t s_base;
+    const int64_t *kp_pairs;        // chunk-local pair offsets, minus p_off
+    int64_t p_off;
+    const int *pairs;               // chunk pair list: q index
+    const float2 *V32, *u32;
+    const float *erel, *f32, *n32, *hw32;
+    float ceta32, inv_eta32;
+    double pref;                    // 2 pi / (hbar N_q sqrt(pi) eta)
+    double *inv_tau;
+    const int2 *items;              // {chunk kp, band}
+};
+
+__device__ __forceinline__ float2 axis_phase(const float2 *ph, int x, int s, int R, int L) {
+    int t = ((x * s) % L) * R % L;
+    if (t < 0) t += L;
+    return ph[t];
+}
+
+// first position in [lo, hi) whose key is >= key (keys ascending)
+template <typename F>
+__device__ __forceinline__ int64_t lower_bound(int64_t lo, int64_t hi, int64_t key, F keyof) {
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (keyof(mid) < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <int W, int NM, int RC>
+__global__ void __launch_bounds__(kSfThreads) k_scatter_sf(SfArgs a) {
+    constexpr int D = 2 * RC + 1;
+    constexpr int X = NM * W;                    // columns (mu, i)
+    extern __shared__ float2 sm[];
+    const int Q = a.nq2max;
+    float2 *gk = sm;                             // [D^3][X]
+    float2 *Y = gk + D * D * D * X;              // [D (R1)][D (R3)][Q][X]
+    float2 *Uall = Y + D * D * Q * X;            // [warp][D (R3)][Q][X]
+    __shared__ double wsum[kSfWarps];
+    const int2 item = a.items[blockIdx.x];
+    const int kp = item.x, n = item.y;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float2 *U = Uall + (size_t)wid * D * Q * X;
+    const int ik = a.kpts[kp];
+    const int lo = a.win_lo[ik];
+    const int W_ = W;
+    const int64_t s = a.kp_state[kp] + n;        // global state
+    const float2 *gs = a.ghat + (size_t)(s - a.s_base) * D * D * D * X;
+    for (int e = threadIdx.x; e < D * D * D * X; e += kSfThreads) gk[e] = gs[e];
+    const int N1 = a.g.n1, N2 = a.g.n2, N3 = a.g.n3, L = a.g.L;
+    const int64_t nplane = a.nplane;
+    const int64_t pb_n = (nplane + kSieveBlock - 1) / kSieveBlock;
+    const int64_t P0 = a.kp_pairs[kp] - a.p_off, P1 = a.kp_pairs[kp + 1] - a.p_off;
+    const int *pl = a.pairs;
+    auto pbof = [&](int64_t p) -> int64_t { return ((int64_t)pl[p] % nplane) / kSieveBlock; };
+    int k1, k2, k3;
+    grid_coords(a.g, ik, k1, k2, k3);
+    const float en = a.erel[(int64_t)ik * W_ + lo + n];
+    double wacc = 0;                             // this warp's run sums
+    __syncthreads();
+    int64_t seg0 = P0;
+    for (int64_t pb = 0; pb < pb_n && seg0 < P1; ++pb) {
+        // the plane block's pairs [seg0, seg1)
+        const int64_t seg1 = lower_bound(seg0, P1, pb + 1, pbof);
+        if (seg1 == seg0) continue;
+        const int64_t c_lo = pb * kSieveBlock, c_hi = min(nplane, c_lo + kSieveBlock) - 1;
+        const int q2lo = (int)(c_lo / N3), nq2 = (int)(c_hi / N3) - q2lo + 1;
+        // Y over this block's q2 values (all threads)
+        for (int e = threadIdx.x; e < D * D * nq2 * X; e += kSfThreads) {
+            const int col = e % X, t = e / X;
+            const int j = t % nq2, r13 = t / nq2;
+            const int R3 = r13 % D, R1 = r13 / D;
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int R2 = 0; R2 < D; ++R2) {
+                const float2 p = axis_phase(a.ph32, q2lo + j, a.g.s2, R2 - RC, L);
+                acc = cfmaf(p, gk[((R1 * D + R2) * D + R3) * X + col], acc);
+            }
+            Y[((R1 * D + R3) * Q + j) * X + col] = acc;
+        }
+        __syncthreads();
+        // runs: warp w takes q1 = w, w + 8, ...
+        for (int q1 = wid; q1 < N1; q1 += kSfWarps) {
+            // the run: q in [q1 nplane + c_lo, q1 nplane + c_hi]
+            const int64_t key0 = (int64_t)q1 * nplane + c_lo;
+            auto qof = [&](int64_t p) -> int64_t { return (int64_t)pl[p]; };
+            const int64_t r0 = lower_bound(seg0, seg1, key0, qof);
+            const int64_t r1 = lower_bound(r0, seg1, key0 + (c_hi - c_lo) + 1, qof);
+            if (r1 == r0) continue;
+            // U for this q1
+            for (int e = lane; e < D * nq2 * X; e += 32) {
+                const int col = e % X, t = e / X;
+                const int j = t % nq2, R3 = t / nq2;
+                float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int R1 = 0; R1 < D; ++R1) {
+                    const float2 p = axis_phase(a.ph32, q1, a.g.s1, R1 - RC, L);
+                    acc = cfmaf(p, Y[((R1 * D + R3) * Q + j) * X + col], acc);
+                }
+                U[(R3 * Q + j) * X + col] = acc;
+            }
+            __syncwarp();
+            float rate = 0.f;
+            for (int64_t p = r0 + lane; p < r1; p += 32) {
+                const int q = pl[p];
+                const int c = q % (int)nplane;
+                const int q2 = c / N3, q3 = c % N3;
+                const int j = q2 - q2lo;
+                if ((unsigned)j >= (unsigned)nq2) continue;   // not this run's block (never in sieve order)
+                float2 G[X];
+#pragma unroll
+                for (int x = 0; x < X; ++x) G[x] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int R3 = 0; R3 < D; ++R3) {
+                    const float2 p3 = axis_phase(a.ph32, q3, a.g.s3, R3 - RC, L);
+                    const float2 *u_ = U + (R3 * Q + j) * X;
+#pragma unroll
+                    for (int x = 0; x < X; ++x) G[x] = cfmaf(p3, u_[x], G[x]);
+                }
+                // k + q
+                int b1 = k1 + q / (int)nplane, b2 = k2 + q2, b3 = k3 + q3;
+                if (b1 >= N1) b1 -= N1;
+                if (b2 >= N2) b2 -= N2;
+                if (b3 >= N3) b3 -= N3;
+                const int64_t ikq = ((int64_t)b1 * N2 + b2) * N3 + b3;
+                const float2 *Vq = a.V32 + ikq * W * W;
+                const float2 *uq = a.u32 + (int64_t)q * NM * NM;
+                float wq[NM], nq[NM];
+#pragma unroll
+                for (int nu = 0; nu < NM; ++nu) {
+                    wq[nu] = __ldg(a.hw32 + (int64_t)q * NM + nu);
+                    nq[nu] = __ldg(a.n32 + (int64_t)q * NM + nu);
+                }
+                float2 ur[NM * NM];
+#pragma unroll
+                for (int x = 0; x < NM * NM; ++x) ur[x] = __ldg(uq + x);
+#pragma unroll
+                for (int m = 0; m < W; ++m) {
+                    float2 h[NM];
+#pragma unroll
+                    for (int mu = 0; mu < NM; ++mu) {
+                        h[mu] = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int i = 0; i < W; ++i) h[mu] = cfmacf(__ldg(Vq + i * W + m), G[mu * W + i], h[mu]);
+                    }
+                    const float em = __ldg(a.erel + ikq * W + m);
+                    const float fm = __ldg(a.f32 + ikq * W + m);
+#pragma unroll
+                    for (int nu = 0; nu < NM; ++nu) {
+                        const float w = wq[nu];
+                        if (w < 0.f) continue;
+                        float2 gv = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int mu = 0; mu < NM; ++mu) gv = cfmaf(h[mu], ur[mu * NM + nu], gv);
+                        const float g2 = gv.x * gv.x + gv.y * gv.y;
+                        const float x1 = (en + w) - em;
+                        const float x2 = (en - w) - em;
+                        float tt = 0.f;
+                        if (fabsf(x1) <= a.ceta32) {
+                            const float y = x1 * a.inv_eta32;
+                            tt += (nq[nu] + fm) * __expf(-y * y);
+                        }
+                        if (fabsf(x2) <= a.ceta32) {
+                            const float y = x2 * a.inv_eta32;
+                            tt += (1.f + nq[nu] - fm) * __expf(-y * y);
+                        }
+                        rate = fmaf(g2, tt, rate);
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) rate += __shfl_xor_sync(0xffffffffu, rate, o);
+            wacc += (double)rate;
+            __syncwarp();                        // U is rewritten by the next run
+        }
+        __syncthreads();                         // Y is rewritten by the next plane block
+        seg0 = seg1;
+    }
+    if (lane == 0) wsum[wid] = wacc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int w = 0; w < kSfWarps; ++w) t += wsum[w];
+        a.inv_tau[s] = a.pref * t;
+    }
+}
+
+size_t sf_smem(int D, int X, int Q) {
+    return sizeof(float2) * ((size_t)D * D * D * X + (size_t)D * D * Q * X + (size_t)kSfWarps * D * Q * X);
+}
+
+template <int W, int NM, int RC>
+void launch_sf(epwi_ctx *c, const SfArgs &a, int nitems) {
+    const size_t sm = sf_smem(2 * RC + 1, NM * W, a.nq2max);
+    EPWI_REQUIRE(sm <= 200 * 1024, EPWI_EUNSUPPORTED,
+                 "fp32 mode: the plane-block tables of this grid do not fit in shared memory");
+    EPWI_CUDA(cudaFuncSetAttribute(k_scatter_sf<W, NM, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    if (nitems > 0) {
+        k_scatter_sf<W, NM, RC><<<(unsigned)nitems, kSfThreads, sm, c->stream>>>(a);
+        EPWI_CHECK_LAUNCH();
+    }
+}
+
+}  // namespace
+
+size_t sf_state_bytes(const epwi_ctx *c) { return sizeof(float2) * (size_t)c->nRp * c->nm * c->nw; }
+
+void sf_check(const epwi_ctx *c) {
+    const int W = c->nw, NM = c->nm, r = c->rp_cube_r;
+    EPWI_REQUIRE(r >= 0, EPWI_EUNSUPPORTED, "fp32 mode needs R_p to be the full cube [-r, r]^3");
+    EPWI_REQUIRE((W == 4 && NM == 3 && (r == 1 || r == 2)) || (W == 1 && NM == 3 && r == 1),
+                 EPWI_EUNSUPPORTED, "fp32 mode built for (nw, modes, R_p half-width) in {(4,3,1), (4,3,2), (1,3,1)}");
+}
+
+void sf_restage(epwi_ctx *c, const RestageArgs &ra) {
+    const int W = ra.W;
+    float2 *out = static_cast<float2 *>(ra.ghat_raw);
+    auto go = [&](auto kern, int KG) {
+        dim3 grid((ra.nrow + 127) / 128, (unsigned)((ra.nkp + KG - 1) / KG));
+        const size_t sm = sizeof(float2) * KG * ra.nRe;
+        if (sm > 48 * 1024) EPWI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        kern<<<grid, 128, sm, c->stream>>>(ra, out);
+        EPWI_CHECK_LAUNCH();
+    };
+    if (W == 4) go(k_restage_f32<4, 8>, 8);
+    else if (W == 1) go(k_restage_f32<1, 8>, 8);
+    else go(k_restage_f32<0, 1>, 1);
+}
+
+// Rates of the chunk's states: one CTA per (k-point, band), written straight into inv_tau.
+void sf_scatter(epwi_ctx *c, const ScatterArgs &sa, int64_t nkp, const int64_t *kp_pairs_local, int64_t p_off,
+                const std::vector<int64_t> &h_kp_state_chunk) {
+    const int W = c->nw, NM = c->nm, r = c->rp_cube_r;
+    SfArgs a;
+    a.g = sa.g;
+    a.nplane = (int64_t)sa.g.n2 * sa.g.n3;
+    int q2max = 1;
+    for (int64_t pb = 0; pb * kSieveBlock < a.nplane; ++pb) {
+        const int64_t c0 = pb * kSieveBlock, c1 = std::min<int64_t>(a.nplane, c0 + kSieveBlock) - 1;
+        q2max = std::max<int>(q2max, (int)(c1 / sa.g.n3 - c0 / sa.g.n3 + 1));
+    }
+    a.nq2max = q2max;
+    a.ph32 = sa.ph32;
+    a.ghat = static_cast<const float2 *>(sa.ghat_raw);
+    a.kpts = sa.kpts;
+    a.win_lo = sa.win_lo;
+    a.win_n = sa.win_n;
+    a.kp_state = sa.kp_state;
+    a.s_base = sa.s_base;
+    a.kp_pairs = kp_pairs_local;
+    a.p_off = p_off;
+    a.pairs = sa.pairs;
+    a.V32 = sa.V32;
+    a.u32 = sa.u32;
+    a.erel = c->tc_erel.as<float>();
+    a.f32 = c->tc_f32.as<float>();
+    a.n32 = c->tc_n32.as<float>();
+    a.hw32 = c->tc_hw32.as<float>();
+    a.ceta32 = (float)sa.ceta;
+    a.inv_eta32 = (float)(1.0 / sa.eta);
+    a.pref = 2.0 * epc::kPi / epc::kHbarEVs / (double)c->nk / (sqrt(epc::kPi) * sa.eta);
+    a.inv_tau = c->inv_tau.as<double>();
+    // items: (chunk k-point, band), k-point major
+    std::vector<int2> items;
+    for (int64_t p = 0; p < nkp; ++p)
+        for (int64_t n = 0; n < h_kp_state_chunk[p + 1] - h_kp_state_chunk[p]; ++n) items.push_back(make_int2((int)p, (int)n));
+    c->sf_items.ensure(sizeof(int2) * (items.size() + 1));
+    if (!items.empty())
+        EPWI_CUDA(cudaMemcpyAsync(c->sf_items.p, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice,
+                                  c->stream));
+    a.items = c->sf_items.as<int2>();
+    const int ni = (int)items.size();
+    if (W == 4 && NM == 3 && r == 2) launch_sf<4, 3, 2>(c, a, ni);
+    else if (W == 4 && NM == 3 && r == 1) launch_sf<4, 3, 1>(c, a, ni);
+    else if (W == 1 && NM == 3 && r == 1) launch_sf<1, 3, 1>(c, a, ni);
+    else sf_check(c);
+    // the host vector of items must outlive the copy
+    EPWI_CUDA(cudaStreamSynchronize(c->stream));
+}

@@ -13,7 +13,6 @@
 namespace {
 
 constexpr int kScanBlock = 1024;
-constexpr int kSieveBlock = 256;  // threads of the sieve kernels (fixes the candidate order)
 constexpr int kScanItems = 4;
 
 __device__ __forceinline__ int64_t warp_incl_scan(int64_t v) {

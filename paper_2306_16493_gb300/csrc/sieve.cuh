@@ -4,6 +4,11 @@
 
 #include "epwi_internal.cuh"
 
+// Threads of the sieve kernels.  This fixes the candidate order of every pair list the sieve
+// writes: for each k-point, plane blocks pb of kSieveBlock consecutive (q2, q3) combinations,
+// then q1, then the combination; the sum-factorised interpolation relies on that order.
+constexpr int kSieveBlock = 256;
+
 struct SieveArgs {
     GridInfo g;
     int W, Nm;

@@ -14,11 +14,11 @@ import numpy as np
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libepwi.so")
 
-EPWI_FP64, EPWI_TF32X3, EPWI_BF16X3, EPWI_FP16X3 = 0, 1, 2, 3
+EPWI_FP64, EPWI_TF32X3, EPWI_BF16X3, EPWI_FP16X3, EPWI_FP32 = 0, 1, 2, 3, 4
 #: split-precision (tcgen05) modes built into this library
 SPLIT_MODES = ("fp16x3", "tf32x3", "bf16x3")
 PRECISIONS = {"fp64": EPWI_FP64, "tf32x3": EPWI_TF32X3, "bf16x3": EPWI_BF16X3,
-              "fp16x3": EPWI_FP16X3}
+              "fp16x3": EPWI_FP16X3, "fp32": EPWI_FP32}
 STATUS = {0: "EPWI_OK", 1: "EPWI_EINVAL", 2: "EPWI_ENOMEM", 3: "EPWI_ECUDA", 4: "EPWI_ESTATE",
           5: "EPWI_ETIMEOUT", 6: "EPWI_ENUMERIC", 7: "EPWI_ETOOSMALL", 8: "EPWI_EUNSUPPORTED"}
 

@@ -1,0 +1,70 @@
+"""GPU parity of the fp32 mode: FP32 Re->k, the Rp->q sum factorised over the axes of the R_p
+cube (per plane block, per q1 run, per pair), FP32 rotations and delta terms, FP64 sums per
+state.  Compared with the FP64 oracle on cubic and non-cubic grids (ragged plane blocks and
+runs), with the FP64 GPU path, across k-point chunking and repeated runs."""
+import numpy as np
+import pytest
+
+from oracle import epwi_oracle as O
+from paper_2306_16493_gb300 import epwi, synth
+
+pytestmark = pytest.mark.gpu
+T = 300.0
+TOL = 1e-5          # FP32 interpolation and delta terms, FP64 sums
+
+
+def _rates(system, grid, mu, eta, lo, hi, precision="fp32", chunk=0):
+    ctx = epwi.Context(precision=precision, device=0, kpoint_chunk=chunk)
+    ctx.setup(system)
+    ctx.eigs(grid)
+    ns, npairs = ctx.scatter_rates(T, mu, eta, lo, hi)
+    k, b, r = ctx.rates()
+    ctx.close()
+    o = np.lexsort((b, k))
+    return k[o], b[o], r[o], npairs
+
+
+@pytest.mark.parametrize("name,grid,half,eta", [
+    ("tiny", (6, 6, 6), None, 0.05),
+    ("tiny", (3, 4, 5), None, 0.05),
+    ("al_like", (10, 10, 10), 0.3, 0.05),
+    ("al_like", (12, 7, 9), 0.3, 0.05),
+    ("al_like", (6, 18, 17), 0.3, 0.04),
+])
+def test_fp32_matches_the_oracle(name, grid, half, eta):
+    s = getattr(synth, f"{name}_system")()
+    gr = O.Grids(s, grid)
+    mu = gr.band_centre()
+    lo, hi = (-1e9, 1e9) if half is None else (mu - half, mu + half)
+    ref = O.serta(gr, T, mu, eta, lo, hi)
+    k, b, r, npairs = _rates(s, grid, mu, eta, lo, hi)
+    assert np.array_equal(k, ref["ik"]) and np.array_equal(b, ref["n"]) and npairs == ref["n_pairs"]
+    assert np.abs(r - ref["inv_tau"]).max() <= TOL * ref["inv_tau"].max()
+
+
+def test_fp32_against_fp64_gpu_and_determinism():
+    s = synth.al_like_system()
+    gr = O.Grids(s, (16, 16, 16))
+    mu = gr.band_centre()
+    args = (s, (16, 16, 16), mu, 0.03, mu - 0.3, mu + 0.3)
+    a = _rates(*args, precision="fp64")
+    b = _rates(*args)
+    c = _rates(*args, chunk=37)
+    d = _rates(*args)
+    assert np.abs(a[2] - b[2]).max() <= TOL * a[2].max()
+    assert np.array_equal(b[2], c[2]) and np.array_equal(b[2], d[2])
+
+
+def test_fp32_refuses_what_it_does_not_serve():
+    ctx = epwi.Context(precision="fp32", device=0)
+    ctx.setup(synth.si_like_system())
+    ctx.eigs(4)
+    with pytest.raises(epwi.EpwiError):
+        ctx.scatter_rates(T, 0.0, 0.05, -1e9, 1e9)
+    ctx.close()
+    ctx = epwi.Context(precision="fp32", device=0)
+    ctx.setup(synth.tiny_system())
+    ctx.eigs(4)
+    with pytest.raises(epwi.EpwiError):
+        ctx.ibte(T, 0.0, 0.05, -1e9, 1e9, max_iter=2)
+    ctx.close()
