@@ -113,14 +113,21 @@ __device__ __forceinline__ int64_t lower_bound(int64_t lo, int64_t hi, int64_t k
 }
 
 template <int W, int NM, int RC>
-__global__ void __launch_bounds__(kSfThreads) k_scatter_sf(SfArgs a) {
+__global__ void __launch_bounds__(kSfThreads, 2) k_scatter_sf(SfArgs a) {
     constexpr int D = 2 * RC + 1;
     constexpr int X = NM * W;                    // columns (mu, i)
     extern __shared__ float2 sm[];
     const int Q = a.nq2max;
+    const int N1 = a.g.n1, N2 = a.g.n2, N3 = a.g.n3, L = a.g.L;
     float2 *gk = sm;                             // [D^3][X]
     float2 *Y = gk + D * D * D * X;              // [D (R1)][D (R3)][Q][X]
     float2 *Uall = Y + D * D * Q * X;            // [warp][D (R3)][Q][X]
+    float2 *E1 = Uall + kSfWarps * D * Q * X;    // [N1][D] axis phases e^{2 pi i x R / N}
+    float2 *E2 = E1 + N1 * D;                    // [N2][D]
+    float2 *E3 = E2 + N2 * D;                    // [N3][D]
+    int *cq = reinterpret_cast<int *>(E3 + N3 * D);   // [kSieveBlock]: (j << 16) | q3 of combination c_lo + t
+    int *rs = cq + kSieveBlock;                  // [N1]: run start (relative to the block), -1 if none
+    int *re = rs + N1;                           // [N1]: run end
     __shared__ double wsum[kSfWarps];
     const int2 item = a.items[blockIdx.x];
     const int kp = item.x, n = item.y;
@@ -128,83 +135,97 @@ __global__ void __launch_bounds__(kSfThreads) k_scatter_sf(SfArgs a) {
     float2 *U = Uall + (size_t)wid * D * Q * X;
     const int ik = a.kpts[kp];
     const int lo = a.win_lo[ik];
-    const int W_ = W;
     const int64_t s = a.kp_state[kp] + n;        // global state
     const float2 *gs = a.ghat + (size_t)(s - a.s_base) * D * D * D * X;
     for (int e = threadIdx.x; e < D * D * D * X; e += kSfThreads) gk[e] = gs[e];
-    const int N1 = a.g.n1, N2 = a.g.n2, N3 = a.g.n3, L = a.g.L;
-    const int64_t nplane = a.nplane;
-    const int64_t pb_n = (nplane + kSieveBlock - 1) / kSieveBlock;
+    for (int e = threadIdx.x; e < (N1 + N2 + N3) * D; e += kSfThreads) {
+        const int R = e % D - RC, x = e / D;
+        float2 v;
+        if (x < N1) v = axis_phase(a.ph32, x, a.g.s1, R, L);
+        else if (x < N1 + N2) v = axis_phase(a.ph32, x - N1, a.g.s2, R, L);
+        else v = axis_phase(a.ph32, x - N1 - N2, a.g.s3, R, L);
+        E1[e] = v;                               // E1, E2, E3 are consecutive
+    }
+    const int nplane = (int)a.nplane;
+    const int pb_n = (nplane + kSieveBlock - 1) / kSieveBlock;
     const int64_t P0 = a.kp_pairs[kp] - a.p_off, P1 = a.kp_pairs[kp + 1] - a.p_off;
     const int *pl = a.pairs;
-    auto pbof = [&](int64_t p) -> int64_t { return ((int64_t)pl[p] % nplane) / kSieveBlock; };
+    auto pbof = [&](int64_t p) -> int64_t { return (int64_t)((pl[p] % nplane) / kSieveBlock); };
     int k1, k2, k3;
     grid_coords(a.g, ik, k1, k2, k3);
-    const float en = a.erel[(int64_t)ik * W_ + lo + n];
+    const float en = a.erel[(int64_t)ik * W + lo + n];
     double wacc = 0;                             // this warp's run sums
     __syncthreads();
     int64_t seg0 = P0;
-    for (int64_t pb = 0; pb < pb_n && seg0 < P1; ++pb) {
+    for (int pb = 0; pb < pb_n && seg0 < P1; ++pb) {
         // the plane block's pairs [seg0, seg1)
-        const int64_t seg1 = lower_bound(seg0, P1, pb + 1, pbof);
+        const int64_t seg1 = lower_bound(seg0, P1, (int64_t)pb + 1, pbof);
         if (seg1 == seg0) continue;
-        const int64_t c_lo = pb * kSieveBlock, c_hi = min(nplane, c_lo + kSieveBlock) - 1;
-        const int q2lo = (int)(c_lo / N3), nq2 = (int)(c_hi / N3) - q2lo + 1;
+        const int c_lo = pb * kSieveBlock, c_hi = min(nplane, c_lo + kSieveBlock) - 1;
+        const int q2lo = c_lo / N3, nq2 = c_hi / N3 - q2lo + 1;
+        // per combination of the block: (j, q3); runs: none yet
+        for (int t = threadIdx.x; t < kSieveBlock; t += kSfThreads) {
+            const int c = c_lo + t, q2 = c / N3;
+            cq[t] = ((q2 - q2lo) << 16) | (c - q2 * N3);
+        }
+        for (int t = threadIdx.x; t < N1; t += kSfThreads) rs[t] = -1;
         // Y over this block's q2 values (all threads)
         for (int e = threadIdx.x; e < D * D * nq2 * X; e += kSfThreads) {
             const int col = e % X, t = e / X;
             const int j = t % nq2, r13 = t / nq2;
             const int R3 = r13 % D, R1 = r13 / D;
+            const float2 *e2 = E2 + (q2lo + j) * D;
             float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int R2 = 0; R2 < D; ++R2) {
-                const float2 p = axis_phase(a.ph32, q2lo + j, a.g.s2, R2 - RC, L);
-                acc = cfmaf(p, gk[((R1 * D + R2) * D + R3) * X + col], acc);
-            }
+            for (int R2 = 0; R2 < D; ++R2) acc = cfmaf(e2[R2], gk[((R1 * D + R2) * D + R3) * X + col], acc);
             Y[((R1 * D + R3) * Q + j) * X + col] = acc;
+        }
+        __syncthreads();
+        // run boundaries: the block's pairs are ordered by q1
+        const int nseg = (int)(seg1 - seg0);
+        for (int t = threadIdx.x; t < nseg; t += kSfThreads) {
+            const int q1 = pl[seg0 + t] / nplane;
+            if (t == 0 || pl[seg0 + t - 1] / nplane != q1) rs[q1] = t;
+            if (t == nseg - 1 || pl[seg0 + t + 1] / nplane != q1) re[q1] = t + 1;
         }
         __syncthreads();
         // runs: warp w takes q1 = w, w + 8, ...
         for (int q1 = wid; q1 < N1; q1 += kSfWarps) {
-            // the run: q in [q1 nplane + c_lo, q1 nplane + c_hi]
-            const int64_t key0 = (int64_t)q1 * nplane + c_lo;
-            auto qof = [&](int64_t p) -> int64_t { return (int64_t)pl[p]; };
-            const int64_t r0 = lower_bound(seg0, seg1, key0, qof);
-            const int64_t r1 = lower_bound(r0, seg1, key0 + (c_hi - c_lo) + 1, qof);
-            if (r1 == r0) continue;
-            // U for this q1
+            const int r0 = rs[q1];
+            if (r0 < 0) continue;
+            const int r1 = re[q1];
+            const float2 *e1 = E1 + q1 * D;
             for (int e = lane; e < D * nq2 * X; e += 32) {
                 const int col = e % X, t = e / X;
                 const int j = t % nq2, R3 = t / nq2;
                 float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int R1 = 0; R1 < D; ++R1) {
-                    const float2 p = axis_phase(a.ph32, q1, a.g.s1, R1 - RC, L);
-                    acc = cfmaf(p, Y[((R1 * D + R3) * Q + j) * X + col], acc);
-                }
+                for (int R1 = 0; R1 < D; ++R1) acc = cfmaf(e1[R1], Y[((R1 * D + R3) * Q + j) * X + col], acc);
                 U[(R3 * Q + j) * X + col] = acc;
             }
             __syncwarp();
+            int b1 = k1 + q1;
+            if (b1 >= N1) b1 -= N1;
+            const int qbase = q1 * nplane + c_lo;
             float rate = 0.f;
-            for (int64_t p = r0 + lane; p < r1; p += 32) {
-                const int q = pl[p];
-                const int c = q % (int)nplane;
-                const int q2 = c / N3, q3 = c % N3;
-                const int j = q2 - q2lo;
-                if ((unsigned)j >= (unsigned)nq2) continue;   // not this run's block (never in sieve order)
+            for (int t = r0 + lane; t < r1; t += 32) {
+                const int q = pl[seg0 + t];
+                const int cl = q - qbase;
+                if ((unsigned)cl > (unsigned)(c_hi - c_lo)) continue;   // never in sieve order
+                const int jq = cq[cl];
+                const int j = jq >> 16, q3 = jq & 0xffff;
+                const float2 *e3 = E3 + q3 * D;
                 float2 G[X];
 #pragma unroll
                 for (int x = 0; x < X; ++x) G[x] = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int R3 = 0; R3 < D; ++R3) {
-                    const float2 p3 = axis_phase(a.ph32, q3, a.g.s3, R3 - RC, L);
+                    const float2 p3 = e3[R3];
                     const float2 *u_ = U + (R3 * Q + j) * X;
 #pragma unroll
                     for (int x = 0; x < X; ++x) G[x] = cfmaf(p3, u_[x], G[x]);
                 }
-                // k + q
-                int b1 = k1 + q / (int)nplane, b2 = k2 + q2, b3 = k3 + q3;
-                if (b1 >= N1) b1 -= N1;
+                int b2 = k2 + q2lo + j, b3 = k3 + q3;
                 if (b2 >= N2) b2 -= N2;
                 if (b3 >= N3) b3 -= N3;
                 const int64_t ikq = ((int64_t)b1 * N2 + b2) * N3 + b3;
@@ -258,7 +279,7 @@ __global__ void __launch_bounds__(kSfThreads) k_scatter_sf(SfArgs a) {
             wacc += (double)rate;
             __syncwarp();                        // U is rewritten by the next run
         }
-        __syncthreads();                         // Y is rewritten by the next plane block
+        __syncthreads();                         // Y, cq and the runs are rewritten next
         seg0 = seg1;
     }
     if (lane == 0) wsum[wid] = wacc;
@@ -270,16 +291,19 @@ __global__ void __launch_bounds__(kSfThreads) k_scatter_sf(SfArgs a) {
     }
 }
 
-size_t sf_smem(int D, int X, int Q) {
-    return sizeof(float2) * ((size_t)D * D * D * X + (size_t)D * D * Q * X + (size_t)kSfWarps * D * Q * X);
+size_t sf_smem(int D, int X, int Q, int N1, int N2, int N3) {
+    return sizeof(float2) * ((size_t)D * D * D * X + (size_t)D * D * Q * X + (size_t)kSfWarps * D * Q * X +
+                             (size_t)(N1 + N2 + N3) * D) +
+           sizeof(int) * ((size_t)kSieveBlock + 2 * (size_t)N1);
 }
 
 template <int W, int NM, int RC>
 void launch_sf(epwi_ctx *c, const SfArgs &a, int nitems) {
-    const size_t sm = sf_smem(2 * RC + 1, NM * W, a.nq2max);
+    const size_t sm = sf_smem(2 * RC + 1, NM * W, a.nq2max, a.g.n1, a.g.n2, a.g.n3);
     EPWI_REQUIRE(sm <= 200 * 1024, EPWI_EUNSUPPORTED,
                  "fp32 mode: the plane-block tables of this grid do not fit in shared memory");
     EPWI_CUDA(cudaFuncSetAttribute(k_scatter_sf<W, NM, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    EPWI_CUDA(cudaFuncSetAttribute(k_scatter_sf<W, NM, RC>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     if (nitems > 0) {
         k_scatter_sf<W, NM, RC><<<(unsigned)nitems, kSfThreads, sm, c->stream>>>(a);
         EPWI_CHECK_LAUNCH();
