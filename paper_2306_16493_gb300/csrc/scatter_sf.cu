@@ -222,8 +222,18 @@ __global__ void __launch_bounds__(kSfThreads, 2) k_scatter_sf(SfArgs a) {
                 for (int R3 = 0; R3 < D; ++R3) {
                     const float2 p3 = e3[R3];
                     const float2 *u_ = U + (R3 * Q + j) * X;
+                    if constexpr (X % 2 == 0) {          // rows of X float2 are 16-byte aligned
+                        const float4 *u4 = reinterpret_cast<const float4 *>(u_);
 #pragma unroll
-                    for (int x = 0; x < X; ++x) G[x] = cfmaf(p3, u_[x], G[x]);
+                        for (int x = 0; x < X / 2; ++x) {
+                            const float4 v = u4[x];
+                            G[2 * x] = cfmaf(p3, make_float2(v.x, v.y), G[2 * x]);
+                            G[2 * x + 1] = cfmaf(p3, make_float2(v.z, v.w), G[2 * x + 1]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int x = 0; x < X; ++x) G[x] = cfmaf(p3, u_[x], G[x]);
+                    }
                 }
                 int b2 = k2 + q2lo + j, b3 = k3 + q3;
                 if (b2 >= N2) b2 -= N2;
@@ -240,6 +250,30 @@ __global__ void __launch_bounds__(kSfThreads, 2) k_scatter_sf(SfArgs a) {
                 float2 ur[NM * NM];
 #pragma unroll
                 for (int x = 0; x < NM * NM; ++x) ur[x] = __ldg(uq + x);
+                // V(k+q), eps - mu and f at k+q: 16-byte loads where W = 4 keeps them aligned
+                float2 Vr[W * W];
+                float emr[W], fmr[W];
+                if constexpr (W == 4) {
+                    const float4 *v4 = reinterpret_cast<const float4 *>(Vq);
+#pragma unroll
+                    for (int x = 0; x < W * W / 2; ++x) {
+                        const float4 v = __ldg(v4 + x);
+                        Vr[2 * x] = make_float2(v.x, v.y);
+                        Vr[2 * x + 1] = make_float2(v.z, v.w);
+                    }
+                    const float4 e4 = __ldg(reinterpret_cast<const float4 *>(a.erel + ikq * W));
+                    const float4 f4 = __ldg(reinterpret_cast<const float4 *>(a.f32 + ikq * W));
+                    emr[0] = e4.x; emr[1] = e4.y; emr[2] = e4.z; emr[3] = e4.w;
+                    fmr[0] = f4.x; fmr[1] = f4.y; fmr[2] = f4.z; fmr[3] = f4.w;
+                } else {
+#pragma unroll
+                    for (int x = 0; x < W * W; ++x) Vr[x] = __ldg(Vq + x);
+#pragma unroll
+                    for (int m = 0; m < W; ++m) {
+                        emr[m] = __ldg(a.erel + ikq * W + m);
+                        fmr[m] = __ldg(a.f32 + ikq * W + m);
+                    }
+                }
 #pragma unroll
                 for (int m = 0; m < W; ++m) {
                     float2 h[NM];
@@ -247,10 +281,10 @@ __global__ void __launch_bounds__(kSfThreads, 2) k_scatter_sf(SfArgs a) {
                     for (int mu = 0; mu < NM; ++mu) {
                         h[mu] = make_float2(0.f, 0.f);
 #pragma unroll
-                        for (int i = 0; i < W; ++i) h[mu] = cfmacf(__ldg(Vq + i * W + m), G[mu * W + i], h[mu]);
+                        for (int i = 0; i < W; ++i) h[mu] = cfmacf(Vr[i * W + m], G[mu * W + i], h[mu]);
                     }
-                    const float em = __ldg(a.erel + ikq * W + m);
-                    const float fm = __ldg(a.f32 + ikq * W + m);
+                    const float em = emr[m];
+                    const float fm = fmr[m];
 #pragma unroll
                     for (int nu = 0; nu < NM; ++nu) {
                         const float w = wq[nu];
