@@ -31,15 +31,15 @@ sys.path.insert(0, ROOT)
 METRIC = "el-ph (k,q)-pairs/s and time-to-σ, mixed-precision vs FP64 at stated error"
 WORKLOAD = dict(workload="al_like_48", system="Al-like fcc, nw=4, 3 modes, 5^3 WS-weighted Re/Rp",
                 grid=48, window_eV=0.3, smear_eV=0.02, T_K=300.0, mu="band centre", seed=2)
-CHOSEN = "fp16x3"
+CHOSEN = "fp32"
 DTYPE = {"fp64": "f64", "tf32x3": "tf32x3 (f32 acc, f64 sums)", "bf16x3": "bf16x3 (f32 acc, f64 sums)",
          "fp16x3": "fp16x3 (f32 acc, f64 sums)", "fp32": "f32 (sum-factorised, f64 sums)"}
 L2_BYTES = 129 * 2 ** 20
-# DRAM bytes (read + write) per (k,q) pair of k_scatter_tc, fp16x3, from one ncu capture of
-# the 24^3 case (255 MB / 19.6 M pairs, ncu --set full).
-# Traffic grows with the pairs processed, so a launch's traffic is this times its pairs.
-# Valid for the kernel version of that capture only.
-TRAFFIC_BYTES_PER_PAIR = {"fp16x3": 13.0}
+# DRAM bytes (read + write) per (k,q) pair of the dominant kernel, from one ncu capture each:
+# k_scatter_tc (fp16x3) at 24^3, 255 MB / 19.6 M pairs; k_scatter_sf (fp32) at 32^3,
+# 630.7 MB / 110.2 M pairs (ncu --set full).  Traffic grows with the pairs processed, so a
+# launch's traffic is this times its pairs.  Valid for the kernel versions of those captures.
+TRAFFIC_BYTES_PER_PAIR = {"fp16x3": 13.0, "fp32": 5.73}
 
 
 def peaks():
@@ -491,7 +491,7 @@ def run_ibte(args):
     import torch
     from paper_2306_16493_gb300 import epwi, synth
     torch.cuda.set_device(0)
-    precision = args.precision
+    precision = args.ibte_precision
     s = synth.time_reversal_symmetric(synth.al_like_system(IBTE["seed"]))
     N = args.grid
     T, eta, win = IBTE["T_K"], IBTE["smear_eV"], IBTE["window_eV"]
@@ -671,6 +671,8 @@ def main():
     ap.add_argument("--learned-samples", type=int, nargs="+", default=[10000, 100000])
     ap.add_argument("--ibte-iters", type=int, default=200, help="al_like_ibte: iteration cap")
     ap.add_argument("--ibte-tol", type=float, default=1e-6, help="al_like_ibte: max |dF| / max |F|")
+    ap.add_argument("--ibte-precision", default="fp16x3", choices=["fp64", "tf32x3", "bf16x3", "fp16x3"],
+                    help="al_like_ibte: precision of the rates and Gamma capture")
     ap.add_argument("--ablation-grid", type=int, default=24, help="ordering_ablation: grid per axis")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -461,10 +461,11 @@ void end_rates(epwi_ctx *c) {
     const double nbar = (double)c->nstates / std::max<int64_t>(1, c->nkp);
     c->stats.scatter_flops = 8.0 * c->nRp * c->nm * c->nw * (double)c->npairs * nbar;
     if (c->opt.precision == EPWI_FP32 && c->rp_cube_r >= 0) {
-        // per (pair, band): the R3 sum, U(k+q) and u(q) rotations (the per-block and per-run
-        // sums are shared and not counted)
+        // per (pair, band): the R3 sum and the rotations of one final band, the least any pair
+        // needs (the per-block and per-run sums are shared, bands out of range are skipped;
+        // neither is counted)
         const double D = 2 * c->rp_cube_r + 1, X = (double)c->nm * c->nw;
-        c->stats.scatter_flops = 8.0 * (D * X + (double)c->nw * c->nw * c->nm + (double)c->nm * c->nm * c->nw) *
+        c->stats.scatter_flops = 8.0 * (D * X + (double)c->nw * c->nm + (double)c->nm * c->nm) *
                                  (double)c->npairs * nbar;
     }
     c->have_rates = true;

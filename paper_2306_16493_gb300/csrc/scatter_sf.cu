@@ -276,6 +276,16 @@ __global__ void __launch_bounds__(kSfThreads, 2) k_scatter_sf(SfArgs a) {
                 }
 #pragma unroll
                 for (int m = 0; m < W; ++m) {
+                    const float em = emr[m];
+                    const float fm = fmr[m];
+                    // a band with no mode inside c eta of either shell adds exactly zero
+                    bool any = false;
+#pragma unroll
+                    for (int nu = 0; nu < NM; ++nu) {
+                        const float w = wq[nu];
+                        any |= w >= 0.f && (fabsf((en + w) - em) <= a.ceta32 || fabsf((en - w) - em) <= a.ceta32);
+                    }
+                    if (!any) continue;
                     float2 h[NM];
 #pragma unroll
                     for (int mu = 0; mu < NM; ++mu) {
@@ -283,8 +293,6 @@ __global__ void __launch_bounds__(kSfThreads, 2) k_scatter_sf(SfArgs a) {
 #pragma unroll
                         for (int i = 0; i < W; ++i) h[mu] = cfmacf(Vr[i * W + m], G[mu * W + i], h[mu]);
                     }
-                    const float em = emr[m];
-                    const float fm = fmr[m];
 #pragma unroll
                     for (int nu = 0; nu < NM; ++nu) {
                         const float w = wq[nu];
