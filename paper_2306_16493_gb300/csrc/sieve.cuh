@@ -64,6 +64,33 @@ __device__ __forceinline__ bool pair_valid(const SieveArgs &a, int nsel, const d
     return false;
 }
 
+// Exact fast reject ahead of pair_valid: pair_valid can only return true through some
+// (n, m) with |e_n - e_m| <= hwmax + lim_extra in FP32, so when no such pair exists the
+// candidate is rejected here with the same outcome.  W = WT is known at compile time: the
+// k+q energies come in one 16-byte load for WT = 4.
+template <int WT>
+__device__ __forceinline__ bool pair_near(const SieveArgs &a, int nsel, const float *en32, int64_t iq,
+                                          int64_t ikq) {
+    const float hm = a.hwmax32[iq];
+    if (hm < 0.f) return false;
+    const float lim = hm + a.lim_extra;
+    float em[WT];
+    if constexpr (WT == 4) {
+        const float4 e = *reinterpret_cast<const float4 *>(a.eps32 + ikq * 4);
+        em[0] = e.x; em[1] = e.y; em[2] = e.z; em[3] = e.w;
+    } else {
+#pragma unroll
+        for (int m = 0; m < WT; ++m) em[m] = a.eps32[ikq * WT + m];
+    }
+    bool near = false;
+    for (int n = 0; n < nsel; ++n) {
+        const float e = en32[n];
+#pragma unroll
+        for (int m = 0; m < WT; ++m) near |= fabsf(e - em[m]) <= lim;
+    }
+    return near;
+}
+
 __device__ __forceinline__ void load_window(const SieveArgs &a, int ik, int lo, int nsel,
                                             double *en, float *en32) {
     if (threadIdx.x < nsel) {
