@@ -123,7 +123,7 @@ __device__ __forceinline__ int64_t plane_kq(const GridInfo &g, int ka2, int ka3,
 // Counts the kept q of each k-point.  With mask != nullptr it also records every decision:
 // the candidate of thread t at (plane block pb, i1) is bit t % 32 of word
 // ((pb / blockDim.x) * N1 + i1) * (blockDim.x / 32) + t / 32 of the k-point's row.
-template <int WT>
+template <int WT, int NMT>
 __global__ void __launch_bounds__(256) k_sieve_count(SieveArgs a, int64_t nkp,
                                                      const int *__restrict__ kpts,
                                                      const int *__restrict__ lo,
@@ -151,9 +151,9 @@ __global__ void __launch_bounds__(256) k_sieve_count(SieveArgs a, int64_t nkp,
         for (int i1 = 0; i1 < a.g.n1; ++i1) {
             const int64_t iq = (int64_t)i1 * nplane + p;
             const int64_t ikq = (int64_t)b1 * nplane + kqp;
-            bool v = inb;
-            if constexpr (WT > 0) v = v && pair_near<WT>(a, nsel, en32, iq, ikq);
-            v = v && pair_valid(a, nsel, en, en32, iq, ikq);
+            bool v;
+            if constexpr (WT > 0) v = inb && pair_valid_t<WT, NMT>(a, nsel, en, en32, iq, ikq);
+            else v = inb && pair_valid(a, nsel, en, en32, iq, ikq);
             c += v;
             if (mrow) {
                 const uint32_t bits = __ballot_sync(0xffffffffu, v);
@@ -344,7 +344,7 @@ void sieve_count(epwi_ctx *c) {
     c->mask_words = (nkp > 0 && words * nkp * 4 <= (int64_t(1) << 31)) ? words : 0;
     if (c->mask_words) c->sieve_mask.ensure(sizeof(uint32_t) * words * nkp);
     if (nkp > 0) {
-        auto kern = c->nw == 4 ? k_sieve_count<4> : k_sieve_count<0>;
+        auto kern = (c->nw == 4 && c->nm == 3) ? k_sieve_count<4, 3> : k_sieve_count<0, 0>;
         kern<<<(unsigned)nkp, kSieveBlock, 0, c->stream>>>(
             a, nkp, c->kpts.as<int>(), c->win_lo.as<int>(), c->win_n.as<int>(),
             c->counts.as<int64_t>(), c->mask_words ? c->sieve_mask.as<uint32_t>() : nullptr,

@@ -64,16 +64,16 @@ __device__ __forceinline__ bool pair_valid(const SieveArgs &a, int nsel, const d
     return false;
 }
 
-// Exact fast reject ahead of pair_valid: pair_valid can only return true through some
-// (n, m) with |e_n - e_m| <= hwmax + lim_extra in FP32, so when no such pair exists the
-// candidate is rejected here with the same outcome.  W = WT is known at compile time: the
-// k+q energies come in one 16-byte load for WT = 4.
-template <int WT>
-__device__ __forceinline__ bool pair_near(const SieveArgs &a, int nsel, const float *en32, int64_t iq,
-                                          int64_t ikq) {
+// pair_valid for compile-time W and N_m: the k+q energies in one load (WT = 4), the mode
+// energies loaded once per candidate, the FP32 tests in pair_valid's arithmetic, and the
+// FP64 re-check of pair_valid for candidates near c eta.  Same outcome as pair_valid.
+template <int WT, int NMT>
+__device__ __forceinline__ bool pair_valid_t(const SieveArgs &a, int nsel, const double *en, const float *en32,
+                                             int64_t iq, int64_t ikq) {
     const float hm = a.hwmax32[iq];
     if (hm < 0.f) return false;
     const float lim = hm + a.lim_extra;
+    const float inner = a.ceta32 - a.delta32, outer = a.ceta32 + a.delta32;
     float em[WT];
     if constexpr (WT == 4) {
         const float4 e = *reinterpret_cast<const float4 *>(a.eps32 + ikq * 4);
@@ -83,12 +83,42 @@ __device__ __forceinline__ bool pair_near(const SieveArgs &a, int nsel, const fl
         for (int m = 0; m < WT; ++m) em[m] = a.eps32[ikq * WT + m];
     }
     bool near = false;
-    for (int n = 0; n < nsel; ++n) {
-        const float e = en32[n];
+    for (int n = 0; n < nsel; ++n)
 #pragma unroll
-        for (int m = 0; m < WT; ++m) near |= fabsf(e - em[m]) <= lim;
+        for (int m = 0; m < WT; ++m) near |= fabsf(en32[n] - em[m]) <= lim;
+    if (!near) return false;
+    float w[NMT];
+#pragma unroll
+    for (int nu = 0; nu < NMT; ++nu) w[nu] = a.hw32[iq * NMT + nu];
+    bool ambiguous = false;
+#pragma unroll
+    for (int m = 0; m < WT; ++m) {
+        for (int n = 0; n < nsel; ++n) {
+            const float d = en32[n] - em[m];
+            if (!(fabsf(d) <= lim)) continue;
+#pragma unroll
+            for (int nu = 0; nu < NMT; ++nu) {
+                if (w[nu] < 0.f) continue;
+                const float xm = fminf(fabsf(d + w[nu]), fabsf(d - w[nu]));
+                if (xm <= inner) return true;
+                if (xm <= outer) ambiguous = true;
+            }
+        }
     }
-    return near;
+    if (!ambiguous) return false;
+    for (int m = 0; m < WT; ++m) {
+        const double emd = a.eps[ikq * WT + m];
+        for (int nu = 0; nu < NMT; ++nu) {
+            const double wd = a.hw[iq * NMT + nu];
+            if (!(wd >= a.omega_min)) continue;
+            for (int n = 0; n < nsel; ++n) {
+                const double x1 = (en[n] + wd) - emd;
+                const double x2 = (en[n] - wd) - emd;
+                if (fabs(x1) <= a.ceta || fabs(x2) <= a.ceta) return true;
+            }
+        }
+    }
+    return false;
 }
 
 __device__ __forceinline__ void load_window(const SieveArgs &a, int ik, int lo, int nsel,
