@@ -671,7 +671,7 @@ def main():
     ap.add_argument("--learned-samples", type=int, nargs="+", default=[10000, 100000])
     ap.add_argument("--ibte-iters", type=int, default=200, help="al_like_ibte: iteration cap")
     ap.add_argument("--ibte-tol", type=float, default=1e-6, help="al_like_ibte: max |dF| / max |F|")
-    ap.add_argument("--ibte-precision", default="fp16x3", choices=["fp64", "tf32x3", "bf16x3", "fp16x3"],
+    ap.add_argument("--ibte-precision", default="fp32", choices=["fp64", "tf32x3", "bf16x3", "fp16x3", "fp32"],
                     help="al_like_ibte: precision of the rates and Gamma capture")
     ap.add_argument("--ablation-grid", type=int, default=24, help="ordering_ablation: grid per axis")
     args = ap.parse_args()

@@ -59,8 +59,9 @@ typedef enum {
     EPWI_FP16X3 = 3, /* Rp->q GEMM on tcgen05 kind::f16 with fp16 operands, 3-term split */
     EPWI_FP32 = 4    /* FP32 Re->k, then the Rp->q sum factorised over the axes of the R_p cube
                         (D N_m W complex MACs per pair instead of D^3 N_m W), FP32 rotations and
-                        delta terms, FP64 sums per state.  epwi_scatter_rates only (EUNSUPPORTED
-                        for the other rate paths); needs R_p to be a full cube and
+                        delta terms, FP64 sums per state.  epwi_scatter_rates and epwi_ibte
+                        (EUNSUPPORTED for importance sampling and epwi_g2); needs R_p to be a
+                        full cube and
                         (nw, modes, half-width) in {(4,3,1), (4,3,2), (1,3,1)} */
 } epwi_precision;
 

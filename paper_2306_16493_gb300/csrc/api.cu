@@ -524,8 +524,6 @@ epwi_status epwi_ibte(epwi_ctx *c, double T, double mu, double eta, double emin,
     return guard(c, [&] {
         EPWI_REQUIRE(max_iter >= 0 && tol >= 0 && std::isfinite(tol), EPWI_EINVAL,
                      "need max_iter >= 0 and a finite tol >= 0");
-        EPWI_REQUIRE(c->opt.precision != EPWI_FP32, EPWI_EUNSUPPORTED,
-                     "the iterative BTE runs in FP64 or a split precision");
         cudaEvent_t e0, e1;
         EPWI_CUDA(cudaEventCreate(&e0));
         EPWI_CUDA(cudaEventCreate(&e1));

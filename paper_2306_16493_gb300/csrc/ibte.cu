@@ -354,6 +354,9 @@ void ibte_prepare(epwi_ctx *c, WorkSet &ws) {
     }
     const size_t eb = fp64 ? sizeof(double) : sizeof(float);
     c->ib_gam.ensure(eb * (size_t)(nent + 1));
+    // the fp32 mode writes only the bands it does not skip (the others are exactly zero)
+    if (c->opt.precision == EPWI_FP32)
+        EPWI_CUDA(cudaMemsetAsync(c->ib_gam.p, 0, eb * (size_t)(nent + 1), c->stream));
     c->ib_stats.n_entries = nent;
     c->ib_stats.entry_bytes = (int32_t)eb;
     ws.pairs_dev = c->ib_pairs.as<int>();

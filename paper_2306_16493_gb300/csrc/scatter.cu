@@ -429,8 +429,8 @@ void process_workset(epwi_ctx *c, const WorkSet &ws, double *g2out, double *tout
     const bool sf = c->opt.precision == EPWI_FP32;
     const bool tc = !sf && c->opt.precision != EPWI_FP64;
     EPWI_REQUIRE(!tc || !tout, EPWI_EINVAL, "per-pair terms need the FP64 path");
-    EPWI_REQUIRE(!sf || (!g2out && !tout && !ws.pair_w && !ws.gam32 && !ws.gam64 && ws.ovr_nsel < 0),
-                 EPWI_EUNSUPPORTED, "the fp32 mode serves the sieved rates of epwi_scatter_rates only");
+    EPWI_REQUIRE(!sf || (!g2out && !tout && !ws.pair_w && !ws.gam64 && ws.ovr_nsel < 0),
+                 EPWI_EUNSUPPORTED, "the fp32 mode serves the sieved rates (and their Gamma) only");
     if (sf) sf_check(c);
     // chunk limits: pairs and Re->k output size
     const int64_t max_pairs = int64_t(1) << 27;

@@ -14,7 +14,9 @@
 // U(k+q) [.] u(q), |g|^2 and the two delta terms, in FP32.
 //
 // One CTA per (window k-point, band), eight warps.  Warps take the runs of a plane block
-// round-robin by q1.  Lane sums are FP32 within a run; the run sums go into per-warp FP64
+// round-robin by q1.  With a Gamma capture (iterative BTE) the CTA also writes its band's row
+// of every pair's Gamma block; rows of bands skipped as out of range stay at the zero the
+// buffer was cleared to.  Lane sums are FP32 within a run; the run sums go into per-warp FP64
 // accumulators, which are added in warp order, so the result is deterministic.
 #include <algorithm>
 
@@ -93,6 +95,8 @@ struct SfArgs {
     double pref;                    // 2 pi / (hbar N_q sqrt(pi) eta)
     double *inv_tau;
     const int2 *items;              // {chunk kp, band}
+    float *gam;                     // Gamma capture (iterative BTE) or nullptr: row n of each
+    const int64_t *goff;            // pair's block, block start goff[chunk pair]
 };
 
 __device__ __forceinline__ float2 axis_phase(const float2 *ph, int x, int s, int R, int L) {
@@ -112,7 +116,7 @@ __device__ __forceinline__ int64_t lower_bound(int64_t lo, int64_t hi, int64_t k
     return lo;
 }
 
-template <int W, int NM, int RC>
+template <int W, int NM, int RC, bool GAM>
 __global__ void __launch_bounds__(kSfThreads, 2) k_scatter_sf(SfArgs a) {
     constexpr int D = 2 * RC + 1;
     constexpr int X = NM * W;                    // columns (mu, i)
@@ -239,6 +243,13 @@ __global__ void __launch_bounds__(kSfThreads, 2) k_scatter_sf(SfArgs a) {
                 if (b2 >= N2) b2 -= N2;
                 if (b3 >= N3) b3 -= N3;
                 const int64_t ikq = ((int64_t)b1 * N2 + b2) * N3 + b3;
+                int lokq = 0, nwkq = 0;
+                int64_t grow = 0;                // this band's row of the pair's Gamma block
+                if constexpr (GAM) {
+                    lokq = __ldg(a.win_lo + ikq);
+                    nwkq = __ldg(a.win_n + ikq);
+                    grow = a.goff[seg0 + t] + (int64_t)n * nwkq - lokq;
+                }
                 const float2 *Vq = a.V32 + ikq * W * W;
                 const float2 *uq = a.u32 + (int64_t)q * NM * NM;
                 float wq[NM], nq[NM];
@@ -293,6 +304,7 @@ __global__ void __launch_bounds__(kSfThreads, 2) k_scatter_sf(SfArgs a) {
 #pragma unroll
                         for (int i = 0; i < W; ++i) h[mu] = cfmacf(Vr[i * W + m], G[mu * W + i], h[mu]);
                     }
+                    float gm = 0.f;                  // Gamma capture: sum over modes
 #pragma unroll
                     for (int nu = 0; nu < NM; ++nu) {
                         const float w = wq[nu];
@@ -313,6 +325,10 @@ __global__ void __launch_bounds__(kSfThreads, 2) k_scatter_sf(SfArgs a) {
                             tt += (1.f + nq[nu] - fm) * __expf(-y * y);
                         }
                         rate = fmaf(g2, tt, rate);
+                        if constexpr (GAM) gm = fmaf(g2, tt, gm);
+                    }
+                    if constexpr (GAM) {
+                        if (m >= lokq && m < lokq + nwkq) a.gam[grow + m] = gm;
                     }
                 }
             }
@@ -339,17 +355,23 @@ size_t sf_smem(int D, int X, int Q, int N1, int N2, int N3) {
            sizeof(int) * ((size_t)kSieveBlock + 2 * (size_t)N1);
 }
 
-template <int W, int NM, int RC>
-void launch_sf(epwi_ctx *c, const SfArgs &a, int nitems) {
+template <int W, int NM, int RC, bool GAM>
+void launch_sf_t(epwi_ctx *c, const SfArgs &a, int nitems) {
     const size_t sm = sf_smem(2 * RC + 1, NM * W, a.nq2max, a.g.n1, a.g.n2, a.g.n3);
     EPWI_REQUIRE(sm <= 200 * 1024, EPWI_EUNSUPPORTED,
                  "fp32 mode: the plane-block tables of this grid do not fit in shared memory");
-    EPWI_CUDA(cudaFuncSetAttribute(k_scatter_sf<W, NM, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    EPWI_CUDA(cudaFuncSetAttribute(k_scatter_sf<W, NM, RC>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    EPWI_CUDA(cudaFuncSetAttribute(k_scatter_sf<W, NM, RC, GAM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    EPWI_CUDA(cudaFuncSetAttribute(k_scatter_sf<W, NM, RC, GAM>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     if (nitems > 0) {
-        k_scatter_sf<W, NM, RC><<<(unsigned)nitems, kSfThreads, sm, c->stream>>>(a);
+        k_scatter_sf<W, NM, RC, GAM><<<(unsigned)nitems, kSfThreads, sm, c->stream>>>(a);
         EPWI_CHECK_LAUNCH();
     }
+}
+
+template <int W, int NM, int RC>
+void launch_sf(epwi_ctx *c, const SfArgs &a, int nitems) {
+    if (a.gam) launch_sf_t<W, NM, RC, true>(c, a, nitems);
+    else launch_sf_t<W, NM, RC, false>(c, a, nitems);
 }
 
 }  // namespace
@@ -420,6 +442,8 @@ void sf_scatter(epwi_ctx *c, const ScatterArgs &sa, int64_t nkp, const int64_t *
         EPWI_CUDA(cudaMemcpyAsync(c->sf_items.p, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice,
                                   c->stream));
     a.items = c->sf_items.as<int2>();
+    a.gam = sa.gam32;
+    a.goff = sa.goff;
     const int ni = (int)items.size();
     if (W == 4 && NM == 3 && r == 2) launch_sf<4, 3, 2>(c, a, ni);
     else if (W == 4 && NM == 3 && r == 1) launch_sf<4, 3, 1>(c, a, ni);

@@ -5,7 +5,8 @@ the split paths) and runs one deterministic step kernel per iteration.  Cases:
   * FP64: 1/tau, F after a fixed number of steps, the converged F and the transport tensors
     from F, on the tiny crystal (6^3) and the Al-like crystal (10^3, ragged pair lists, also
     in a split precision);
-  * split precisions: the same after a fixed number of steps, within 1e-4;
+  * split precisions and the sum-factorised fp32 mode: the same after a fixed number of
+    steps, within 1e-4;
   * 16 bands in the window (two register groups of the step kernel);
   * k-point chunking and repeated runs give bitwise identical F; max_iter = 0 gives v tau.
 """
@@ -83,7 +84,7 @@ def test_fp64_converged_mfp_and_transport(tiny6):
     assert np.abs(res["tr"][0] - res["serta"][0]).max() > 1e-3 * np.abs(res["serta"][0]).max()
 
 
-@pytest.mark.parametrize("precision", ("fp64",) + SPLIT[:1])
+@pytest.mark.parametrize("precision", ("fp64", "fp32") + SPLIT[:1])
 def test_al_like_ragged_pairs(precision):
     s = synth.al_like_system()
     gr, mu, lo, hi, eta = _case(s, (10, 10, 10), 0.3, 0.05)
@@ -98,8 +99,7 @@ def test_al_like_ragged_pairs(precision):
     assert res["st"]["n_entries"] >= ref["A"].nnz
 
 
-@pytest.mark.skipif(not SPLIT, reason="no split-precision modes built")
-@pytest.mark.parametrize("precision", SPLIT)
+@pytest.mark.parametrize("precision", SPLIT + ("fp32",))
 def test_split_precision_fixed_steps(tiny6, precision):
     s, gr, mu, lo, hi, eta = tiny6
     ref = O.ibte(gr, T, mu, eta, lo, hi, max_iter=10, tol=0.0)

@@ -65,6 +65,6 @@ def test_fp32_refuses_what_it_does_not_serve():
     ctx = epwi.Context(precision="fp32", device=0)
     ctx.setup(synth.tiny_system())
     ctx.eigs(4)
-    with pytest.raises(epwi.EpwiError):
-        ctx.ibte(T, 0.0, 0.05, -1e9, 1e9, max_iter=2)
+    with pytest.raises(epwi.EpwiError):           # per-pair |g|^2 of arbitrary pairs
+        ctx.g2(np.array([0, 1], np.int32), np.array([3, 5], np.int32), 0, 2)
     ctx.close()
