@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(kSfThreads, 2) k_scatter_sf(SfArgs a) {
                 int b2 = k2 + q2lo + j, b3 = k3 + q3;
                 if (b2 >= N2) b2 -= N2;
                 if (b3 >= N3) b3 -= N3;
-                const int64_t ikq = ((int64_t)b1 * N2 + b2) * N3 + b3;
+                const int ikq = (b1 * N2 + b2) * N3 + b3;   // nk W^2 < 2^31 (checked on the host)
                 int lokq = 0, nwkq = 0;
                 int64_t grow = 0;                // this band's row of the pair's Gamma block
                 if constexpr (GAM) {
@@ -250,13 +250,13 @@ __global__ void __launch_bounds__(kSfThreads, 2) k_scatter_sf(SfArgs a) {
                     nwkq = __ldg(a.win_n + ikq);
                     grow = a.goff[seg0 + t] + (int64_t)n * nwkq - lokq;
                 }
-                const float2 *Vq = a.V32 + ikq * W * W;
-                const float2 *uq = a.u32 + (int64_t)q * NM * NM;
+                const float2 *Vq = a.V32 + ikq * (W * W);
+                const float2 *uq = a.u32 + q * (NM * NM);
                 float wq[NM], nq[NM];
 #pragma unroll
                 for (int nu = 0; nu < NM; ++nu) {
-                    wq[nu] = __ldg(a.hw32 + (int64_t)q * NM + nu);
-                    nq[nu] = __ldg(a.n32 + (int64_t)q * NM + nu);
+                    wq[nu] = __ldg(a.hw32 + q * NM + nu);
+                    nq[nu] = __ldg(a.n32 + q * NM + nu);
                 }
                 float2 ur[NM * NM];
 #pragma unroll
@@ -380,6 +380,8 @@ size_t sf_state_bytes(const epwi_ctx *c) { return sizeof(float2) * (size_t)c->nR
 
 void sf_check(const epwi_ctx *c) {
     const int W = c->nw, NM = c->nm, r = c->rp_cube_r;
+    EPWI_REQUIRE(c->nk * std::max(W * W, NM * NM) < (int64_t(1) << 31), EPWI_EUNSUPPORTED,
+                 "fp32 mode: grid too large for its 32-bit table offsets");
     EPWI_REQUIRE(r >= 0, EPWI_EUNSUPPORTED, "fp32 mode needs R_p to be the full cube [-r, r]^3");
     EPWI_REQUIRE((W == 4 && NM == 3 && (r == 1 || r == 2)) || (W == 1 && NM == 3 && r == 1),
                  EPWI_EUNSUPPORTED, "fp32 mode built for (nw, modes, R_p half-width) in {(4,3,1), (4,3,2), (1,3,1)}");
