@@ -14,7 +14,7 @@
 // U(k+q) [.] u(q), |g|^2 and the two delta terms, in FP32.
 //
 // One CTA per (window k-point, band), eight warps.  Warps take the runs of a plane block
-// round-robin by q1.  With a Gamma capture (iterative BTE) the CTA also writes its band's row
+// two at a time, round-robin by q1, and walk the pairs of both as one list.  With a Gamma capture (iterative BTE) the CTA also writes its band's row
 // of every pair's Gamma block; rows of bands skipped as out of range stay at the zero the
 // buffer was cleared to.  Lane sums are FP32 within a run; the run sums go into per-warp FP64
 // accumulators, which are added in warp order, so the result is deterministic.
@@ -125,8 +125,8 @@ __global__ void __launch_bounds__(kSfThreads, 2) k_scatter_sf(SfArgs a) {
     const int N1 = a.g.n1, N2 = a.g.n2, N3 = a.g.n3, L = a.g.L;
     float2 *gk = sm;                             // [D^3][X]
     float2 *Y = gk + D * D * D * X;              // [D (R1)][D (R3)][Q][X]
-    float2 *Uall = Y + D * D * Q * X;            // [warp][D (R3)][Q][X]
-    float2 *E1 = Uall + kSfWarps * D * Q * X;    // [N1][D] axis phases e^{2 pi i x R / N}
+    float2 *Uall = Y + D * D * Q * X;            // [warp][2 runs][D (R3)][Q][X]
+    float2 *E1 = Uall + 2 * kSfWarps * D * Q * X;   // [N1][D] axis phases e^{2 pi i x R / N}
     float2 *E2 = E1 + N1 * D;                    // [N2][D]
     float2 *E3 = E2 + N2 * D;                    // [N3][D]
     int *cq = reinterpret_cast<int *>(E3 + N3 * D);   // [kSieveBlock]: (j << 16) | q3 of combination c_lo + t
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kSfThreads, 2) k_scatter_sf(SfArgs a) {
     const int2 item = a.items[blockIdx.x];
     const int kp = item.x, n = item.y;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    float2 *U = Uall + (size_t)wid * D * Q * X;
+    float2 *U = Uall + (size_t)wid * 2 * D * Q * X;
     const int ik = a.kpts[kp];
     const int lo = a.win_lo[ik];
     const int64_t s = a.kp_state[kp] + n;        // global state
@@ -193,26 +193,38 @@ __global__ void __launch_bounds__(kSfThreads, 2) k_scatter_sf(SfArgs a) {
             if (t == nseg - 1 || pl[seg0 + t + 1] / nplane != q1) re[q1] = t + 1;
         }
         __syncthreads();
-        // runs: warp w takes q1 = w, w + 8, ...
-        for (int q1 = wid; q1 < N1; q1 += kSfWarps) {
-            const int r0 = rs[q1];
-            if (r0 < 0) continue;
-            const int r1 = re[q1];
-            const float2 *e1 = E1 + q1 * D;
-            for (int e = lane; e < D * nq2 * X; e += 32) {
-                const int col = e % X, t = e / X;
-                const int j = t % nq2, R3 = t / nq2;
-                float2 acc = make_float2(0.f, 0.f);
+        // runs: warp w takes q1 = w + 16 i and w + 16 i + 8 together (U of both in shared
+        // memory) and walks their pairs as one list, so that short runs share lane rounds
+        for (int qa = wid; qa < N1; qa += 2 * kSfWarps) {
+            const int qb = qa + kSfWarps;
+            const int ra0 = rs[qa];
+            const int na = ra0 < 0 ? 0 : re[qa] - ra0;
+            const int rb0 = qb < N1 ? rs[qb] : -1;
+            const int nb = rb0 < 0 ? 0 : re[qb] - rb0;
+            if (na + nb == 0) continue;
+            for (int h2 = 0; h2 < 2; ++h2) {
+                if ((h2 == 0 ? na : nb) == 0) continue;
+                const float2 *e1 = E1 + (h2 == 0 ? qa : qb) * D;
+                float2 *Uh = U + h2 * D * Q * X;
+                for (int e = lane; e < D * nq2 * X; e += 32) {
+                    const int col = e % X, t = e / X;
+                    const int j = t % nq2, R3 = t / nq2;
+                    float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int R1 = 0; R1 < D; ++R1) acc = cfmaf(e1[R1], Y[((R1 * D + R3) * Q + j) * X + col], acc);
-                U[(R3 * Q + j) * X + col] = acc;
+                    for (int R1 = 0; R1 < D; ++R1) acc = cfmaf(e1[R1], Y[((R1 * D + R3) * Q + j) * X + col], acc);
+                    Uh[(R3 * Q + j) * X + col] = acc;
+                }
             }
             __syncwarp();
-            int b1 = k1 + q1;
-            if (b1 >= N1) b1 -= N1;
-            const int qbase = q1 * nplane + c_lo;
             float rate = 0.f;
-            for (int t = r0 + lane; t < r1; t += 32) {
+            for (int tt0 = lane; tt0 < na + nb; tt0 += 32) {
+                const bool inA = tt0 < na;
+                const int q1 = inA ? qa : qb;
+                const int t = inA ? ra0 + tt0 : rb0 + (tt0 - na);
+                const float2 *Ur = inA ? U : U + D * Q * X;
+                int b1 = k1 + q1;
+                if (b1 >= N1) b1 -= N1;
+                const int qbase = q1 * nplane + c_lo;
                 const int q = pl[seg0 + t];
                 const int cl = q - qbase;
                 if ((unsigned)cl > (unsigned)(c_hi - c_lo)) continue;   // never in sieve order
@@ -225,7 +237,7 @@ __global__ void __launch_bounds__(kSfThreads, 2) k_scatter_sf(SfArgs a) {
 #pragma unroll
                 for (int R3 = 0; R3 < D; ++R3) {
                     const float2 p3 = e3[R3];
-                    const float2 *u_ = U + (R3 * Q + j) * X;
+                    const float2 *u_ = Ur + (R3 * Q + j) * X;
                     if constexpr (X % 2 == 0) {          // rows of X float2 are 16-byte aligned
                         const float4 *u4 = reinterpret_cast<const float4 *>(u_);
 #pragma unroll
@@ -350,7 +362,7 @@ __global__ void __launch_bounds__(kSfThreads, 2) k_scatter_sf(SfArgs a) {
 }
 
 size_t sf_smem(int D, int X, int Q, int N1, int N2, int N3) {
-    return sizeof(float2) * ((size_t)D * D * D * X + (size_t)D * D * Q * X + (size_t)kSfWarps * D * Q * X +
+    return sizeof(float2) * ((size_t)D * D * D * X + (size_t)D * D * Q * X + (size_t)2 * kSfWarps * D * Q * X +
                              (size_t)(N1 + N2 + N3) * D) +
            sizeof(int) * ((size_t)kSieveBlock + 2 * (size_t)N1);
 }
