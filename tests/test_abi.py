@@ -56,3 +56,19 @@ def test_parameter_count_matches_oracle():
     assert epwi.EPWI_MLP_NPARAM == mlp_oracle.N_PARAM
     m = re.search(r"#define EPWI_MLP_NPARAM (\d+)", open(HEADER).read())
     assert int(m.group(1)) == mlp_oracle.N_PARAM
+
+
+def test_default_options_match_the_header():
+    """epwi_default_options is host code: the ctypes mirror of epwi_options reads back the
+    documented defaults, including the fields appended last (tc_a_operand, ordering)."""
+    from paper_2306_16493_gb300 import epwi
+    o = epwi.epwi_default_options()
+    assert o.precision == epwi.EPWI_FP64
+    assert o.sieve_c == 6.0 and o.omega_min_eV == 1e-4
+    assert o.device == 0 and not o.cuda_stream and o.kpoint_chunk == 0
+    assert o.tc_a_operand == 0 and o.ordering == 0
+    # the Python mirror's size equals the struct the library fills (no trailing field lost)
+    import ctypes as C
+    buf = (C.c_uint8 * (C.sizeof(epwi.epwi_options) + 64))(*([0xAB] * (C.sizeof(epwi.epwi_options) + 64)))
+    epwi._lib.epwi_default_options(C.cast(buf, C.c_void_p))
+    assert all(b == 0xAB for b in bytes(buf)[C.sizeof(epwi.epwi_options):])
