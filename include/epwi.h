@@ -252,8 +252,10 @@ epwi_status epwi_g2(epwi_ctx *ctx, int64_t npairs, const int32_t *ik, const int3
  * grid, volume_A3 the cell volume.  Scratch is a fixed 48 KiB device array in the library
  * (held by every GPU that loads it until exit); n_states above 4,194,304 returns
  * EPWI_EUNSUPPORTED.  The first call on each device resolves the array's device address
- * (cudaGetSymbolAddress), so make that first call before any stream capture.  All calls share
- * the array: calls that overlap on the GPU race.  Errors: EINVAL (NULL pointer, T <= 0,
+ * (cudaGetSymbolAddress) and caches it, so make that first call before any stream capture;
+ * two host threads making that first call together store the same address (harmless).  A
+ * device reset in the process (cudaDeviceReset) invalidates the cached address: do not call
+ * this entry point after one.  All calls share the array: calls that overlap on the GPU race.  Errors: EINVAL (NULL pointer, T <= 0,
  * volume <= 0, nk < 1), EUNSUPPORTED (too many states), ECUDA (launch or symbol lookup). */
 epwi_status epwi_conductivity_noalloc(int64_t n_states, const double *eps_dev, const double *vel_dev,
                                       const double *inv_tau_dev, double mu_eV, double T_K,

@@ -10,6 +10,12 @@
 // The array is shared by every call in the process and keeps the last call's contents;
 // each call overwrites every slot it reads, so nothing needs clearing, but two calls that
 // overlap on the GPU (different streams, or different host threads) race on it.
+//
+// The device address of the array is looked up once per device and cached.  Two host
+// threads that make their first call on a device at the same time both store the same
+// address, which is harmless.  A cudaDeviceReset (or any teardown of the primary context)
+// unloads the module, and the array may come back at another address: the cached one is
+// then stale, so this entry point must not be used after a device reset in the same process.
 #include <cuda_runtime.h>
 
 #include <cstdint>
