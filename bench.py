@@ -52,23 +52,33 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def roofline_for(precision, stats, per_launch_traffic=None):
+def fma_peaks(device=0, stream=None):
+    """FP32 and FP64 FMA peaks (TFLOP/s) measured live by the library's throughput probe
+    (epwi_fma_peak: register-only FMA chains on every SM, best of three ~50 ms launches).
+    Falls back to the unit-count figures only if the probe fails."""
+    from paper_2306_16493_gb300 import epwi
+    out = {}
+    for name, fp64, derived in (("fp32", False, FP32_PEAK_TFLOPS), ("fp64", True, FP64_PEAK_TFLOPS)):
+        try:
+            tf, ms = epwi.epwi_fma_peak(fp64, device, stream)
+            out[name] = (tf, f"measured: FMA probe epwi_fma_peak ({name}, best of 3 launches of {ms:.0f} ms)")
+        except Exception as e:                     # noqa: BLE001
+            out[name] = (derived, f"derived from unit counts x 2.07 GHz (probe failed: {e})")
+    return out
+
+
+def roofline_for(precision, stats, per_launch_traffic=None, simt_peaks=None):
     """Dominant kernel: the fused Rp->q + rotation + delta kernel (one launch per chunk)."""
     mp, src = peaks()
     flops = stats["scatter_flops"]
     ms = stats["ms_scatter"]
-    if precision == "fp64":
-        # FP64 ALU: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz = 1.26 TFLOP/s (GB300 FP64 rate)
-        peak = 152 * 4 * 2.07e9 / 1e12
+    simt = simt_peaks or {"fp32": (FP32_PEAK_TFLOPS, "derived from unit counts"),
+                          "fp64": (FP64_PEAK_TFLOPS, "derived from unit counts")}
+    if precision in ("fp64", "fp32"):
+        # CUDA-core FMA work: FP64 path, or the sum-factorised FP32 kernel
+        peak, note = simt[precision]
         bound, unit = "alu", "TFLOP/s"
         achieved = flops / (ms * 1e-3) / 1e12
-        note = "FP64 peak derived: 152 SM x 4 flop/clk x 2.07 GHz"
-    elif precision == "fp32":
-        # sum-factorised FP32 kernel: CUDA-core FMA peak, 152 SM x 128 lanes x 2 flop x 2.07 GHz
-        peak = FP32_PEAK_TFLOPS
-        bound, unit = "alu", "TFLOP/s"
-        achieved = flops / (ms * 1e-3) / 1e12
-        note = "FP32 peak derived: 152 SM x 128 FMA lanes x 2 flop x 2.07 GHz"
     else:
         ratio = 0.5 if precision == "tf32x3" else 1.0
         peak = mp["bf16_tflops"] * ratio
@@ -150,8 +160,9 @@ def reduce_sum_over_ranks(x: float, world: int) -> float:
 
 
 # --------------------------------------------------------------------------- oracle arm
-def oracle_sample(sysm, gr, nkp_sample, seed, T, eta, mu):
-    """Times the FP64 CPU oracle on a seeded sample of k-points of the workload."""
+def oracle_sample(sysm, gr, nkp_sample, seed, T, eta, mu, full=False):
+    """Times the FP64 CPU oracle on a seeded sample of k-points of the workload.  Returns
+    (pairs, seconds), or (pairs, seconds, oracle result) with ``full``."""
     from oracle import epwi_oracle as O
     ik_all, _ = gr.window_states(mu - WORKLOAD["window_eV"], mu + WORKLOAD["window_eV"])
     kp = np.unique(ik_all)
@@ -160,7 +171,32 @@ def oracle_sample(sysm, gr, nkp_sample, seed, T, eta, mu):
     r = O.serta(gr, T, mu, eta, mu - WORKLOAD["window_eV"], mu + WORKLOAD["window_eV"],
                 k_subset=pick)
     dt = time.perf_counter() - t0
-    return r["n_pairs"], dt
+    return (r["n_pairs"], dt, r) if full else (r["n_pairs"], dt)
+
+
+def group_rel_error(ik, n, r, ref_ik, ref_n, ref_r, eps, tol=1e-6):
+    """Largest relative error of 1/tau over degenerate groups (states at one k whose energies
+    differ by < tol eV; only their sums are gauge invariant), over the states of the reference.
+    Each group's error is relative to its own reference rate.  Returns (max, groups)."""
+    def groups(ik_, n_, r_):
+        o = np.lexsort((n_, ik_))
+        ik_, n_, r_ = ik_[o], n_[o], r_[o]
+        out, i = {}, 0
+        while i < len(ik_):
+            j = i + 1
+            while j < len(ik_) and ik_[j] == ik_[i] and abs(eps[ik_[j], n_[j]] - eps[ik_[j - 1], n_[j - 1]]) < tol:
+                j += 1
+            out[(int(ik_[i]), int(n_[i]))] = float(r_[i:j].sum())
+            i = j
+        return out
+    ref = groups(np.asarray(ref_ik), np.asarray(ref_n), np.asarray(ref_r))
+    sel = np.isin(ik, np.unique(ref_ik))
+    got = groups(np.asarray(ik)[sel], np.asarray(n)[sel], np.asarray(r)[sel])
+    if got.keys() != ref.keys():
+        return float("inf"), len(ref)
+    scale = max((abs(v) for v in ref.values()), default=1.0)
+    worst = max((abs(got[k] - v) / max(abs(v), 1e-12 * scale) for k, v in ref.items()), default=0.0)
+    return float(worst), len(ref)
 
 
 def cores_used():
@@ -268,6 +304,9 @@ def run_gpu(args):
     launches = (epwi.epwi_kernel_launches() - launches0) // args.steps
     if world > 1:
         torch.distributed.barrier()
+    gpu_k, gpu_b, gpu_r = ctx.rates()            # the last timed step's rates (not timed)
+    gpu_sig = sig
+    mu_step = 0.5 * sum(ctx.band_range())
     ms = sum(a.elapsed_time(b) for a, b in ev)
     ms_max = reduce_max_over_ranks(ms, world)
     pairs_all = reduce_sum_over_ranks(float(pairs_total), world)
@@ -277,8 +316,9 @@ def run_gpu(args):
                  n_chunks=chunks // args.steps)
     pairs_per_launch = pairs_total / args.steps / max(1, stats["n_chunks"])
     tb = TRAFFIC_BYTES_PER_PAIR.get(precision)
+    simt = fma_peaks(local, stream.cuda_stream)
     roof = roofline_for(precision, stats,
-                        per_launch_traffic=None if tb is None else tb * pairs_per_launch)
+                        per_launch_traffic=None if tb is None else tb * pairs_per_launch, simt_peaks=simt)
 
     # ---- e2e through the C ABI with host buffers
     e2e_steps = max(1, min(args.steps, 3))
@@ -297,16 +337,54 @@ def run_gpu(args):
     e2e_t = reduce_max_over_ranks(e2e_t, world)
     e2e_pairs = reduce_sum_over_ranks(float(e2e_pairs), world)
 
+    # ---- the same workload on the FP64 GPU path: time-to-sigma and the error of this precision
+    fp64 = None
+    if rank == 0 and world == 1 and not args.no_fp64_leg and precision != "fp64":
+        ctx64 = epwi.Context(precision="fp64", device=local, stream=stream.cuda_stream)
+        ctx64.setup(s)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        e0.record(stream)
+        ctx64.eigs(N)
+        lo64, hi64 = ctx64.band_range()
+        mu64 = 0.5 * (lo64 + hi64)
+        _, np64 = ctx64.scatter_rates(T, mu64, eta, mu64 - win, mu64 + win)
+        sig64 = ctx64.conductivity()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        k64, b64, r64 = ctx64.rates()
+        eps64 = ctx64.bands()[0]
+        err64, ng64 = group_rel_error(gpu_k, gpu_b, gpu_r, k64, b64, r64, eps64)
+        fp64 = {"time_to_sigma_ms": ms64, "value": np64 / (ms64 * 1e-3), "unit": "pairs/s",
+                "speedup_of_this_precision": ms64 / (ms_max / args.steps),
+                "pairs": int(np64), "same_pairs": int(np64) == int(pairs_total // args.steps),
+                "rate_max_rel_error_vs_fp64": err64, "rate_groups_compared": ng64,
+                "sigma_rel_frobenius_vs_fp64": float(np.linalg.norm(gpu_sig - sig64) / np.linalg.norm(sig64)),
+                "stated_tolerance": {"inv_tau": 1e-4, "sigma": 1e-4},
+                "steps": 1, "note": "one step of the FP64 path (FP64 Re->k, FP64 Rp->q + rotations + "
+                                    "delta sum) on the same grid, window and smearing, L2 flushed first"}
+        ctx64.close()
+
     line = None
     if rank == 0:
-        cpu = None
+        cpu, err_oracle = None, None
         if world == 1 and not args.no_cpu_baseline:
             _, gr = build_oracle_grid()
             mu = gr.band_centre()
-            p, dt = oracle_sample(s, gr, args.ref_kpoints, 7, T, eta, mu)
+            p, dt, ref = oracle_sample(s, gr, args.ref_kpoints, 7, T, eta, mu, full=True)
             cpu = {"value": p / dt, "unit": "pairs/s", "cores": cores_used(), "kind": "oracle",
                    "sample": f"{args.ref_kpoints} seeded k-points of the 48^3 workload with all their q "
                              f"({p} pairs, {dt:.1f} s, numpy FP64; grid eigensolves excluded)"}
+            if N == WORKLOAD["grid"]:
+                e, ng = group_rel_error(gpu_k, gpu_b, gpu_r, ref["ik"], ref["n"], ref["inv_tau"], gr.eps)
+                err_oracle = {"inv_tau_max_rel_error": e, "groups_compared": ng,
+                              "kpoints": args.ref_kpoints, "mu_abs_diff_eV": abs(mu - mu_step),
+                              "stated_tolerance": 1e-4,
+                              "how": "the last timed step's 1/tau against the FP64 oracle on the "
+                                     "cpu_baseline sample, per degenerate group, relative to each "
+                                     "group's own rate"}
         line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
                 "time_to_sigma_ms": ms_max / args.steps, "pairs_per_step": pairs_total / args.steps,
@@ -318,6 +396,7 @@ def run_gpu(args):
                 "gpu_launches": int(launches),
                 "stage_ms": {k: stats[k] for k in ("ms_eigs", "ms_sieve", "ms_restage", "ms_scatter", "ms_reduce")},
                 "roofline": roof, "clocks": clocks, "cpu_baseline": cpu,
+                "error_vs_oracle": err_oracle, "fp64_gpu": fp64,
                 "e2e": {"value": e2e_pairs / e2e_t, "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h)}}
     ctx.close()
@@ -331,7 +410,8 @@ def run_gpu(args):
 BATCH = dict(workload="batch64", systems="64 seeded cells s = 16a+4b+c: nat=[1,2,4,6][c], "
              "nw=[4,8,16,24][b], grid=[24,36,48,60][a]^3 / scale, R cube side=[3,5,7][(a+b+c)%3]",
              window_eV=0.2, smear_eV=0.02, T_K=300.0, mu="band centre per system")
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SM x 128 FP32 lanes x FMA x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # fallback only: 152 SM x 128 FP32 lanes x FMA x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12     # fallback only: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz
 
 
 def run_batch(args):
@@ -381,6 +461,7 @@ def run_batch(args):
     st = b.stats()
     ms_p = sum(pers) / len(pers)
     achieved = st["scatter_flops"] / (ms_p * 1e-3) / 1e12
+    fp32_peak, fp32_src = fma_peaks(0, stream.cuda_stream)["fp32"]
     tiles = [b.tile(s) for s in range(nsys)]
     line = {"metric": "batched el-ph (k,q)-pairs/s over 64 uneven systems (one graph launch per step)",
             "value": npairs / (ms * 1e-3), "unit": "pairs/s", "n_gpus": 1, "steps": args.steps,
@@ -395,10 +476,10 @@ def run_batch(args):
             "graph": {"nodes": st["graph_nodes"], "persistent_ctas": st["persistent_ctas"],
                       "items": st["n_items"], "smem_bytes": st["smem_bytes"]},
             "stage_ms": {"persistent": ms_p, "rest_of_graph": ms - ms_p, "plan": st["ms_plan"]},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak,
+                         "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
                          "kernel": "k_batch_scatter (persistent, FP32 SIMT)",
-                         "peak_source": "FP32 derived: 152 SM x 128 lanes x 2 flop x 2.07 GHz"},
+                         "peak_source": fp32_src},
             "restage_flops": st["restage_flops"],
             "tiles": {"autotuned": sum(1 for t in tiles if t[2] in (1, 2)),
                       "shapes": sorted({f"{t[0]}x{t[1]}" for t in tiles})},
@@ -540,7 +621,7 @@ def run_ibte(args):
                  "launches_per_step": st["iters"], "peak_source": f"{src} HBM copy bandwidth"}
     roof_sc = roofline_for(precision, dict(scatter_flops=statistics.mean(x["scatter_flops"] for x in sts),
                                            ms_scatter=statistics.mean(x["ms_scatter"] for x in sts),
-                                           n_chunks=st["n_chunks"]))
+                                           n_chunks=st["n_chunks"]), simt_peaks=fma_peaks(0, stream.cuda_stream))
     it_ms = statistics.mean(x["ms_step"] * x["iters"] for x in sts)
     sc_ms = statistics.mean(x["ms_scatter"] for x in sts)
     roof, roof_other = (roof_sc, roof_step) if sc_ms >= it_ms else (roof_step, roof_sc)
@@ -659,6 +740,7 @@ def main():
     ap.add_argument("--grid", type=int, default=WORKLOAD["grid"],
                     help="k and q grid per axis (48 is the benchmark; smaller sizes are for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-leg", action="store_true", help="skip the FP64 GPU comparison step")
     ap.add_argument("--workload", default="al_like",
                     choices=["al_like", "batch64", "si_like_learned", "al_like_ibte", "ordering_ablation"],
                     help="al_like: the benchmark; batch64 and si_like_learned: the batched and "

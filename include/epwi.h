@@ -471,6 +471,17 @@ epwi_status epwi_get_ibte_stats(epwi_ctx *ctx, epwi_ibte_stats *out);
 /* Number of kernels this library has launched in the process so far (all contexts). */
 int64_t epwi_kernel_launches(void);
 
+/* Measured FMA throughput of the device, the denominator of the roofline fractions of the
+ * SIMT kernels (the paper has no counterpart; it reports no roofline).  fp64 = 0 times FP32
+ * FMAs, fp64 = 1 FP64 FMAs: every thread of 8 CTAs per SM runs 8 independent register-only
+ * FMA chains, the launch is sized from a calibration run to about target_ms, and the best of
+ * three timed launches (CUDA events on cuda_stream, NULL = legacy default stream) is returned
+ * in *tflops (2 flop per FMA) and its duration in *ms (may be NULL).  Synchronises the stream.
+ * Allocates a 2 KiB sink buffer for the duration of the call.  Errors: EINVAL (NULL tflops,
+ * target_ms <= 0, fp64 not 0 or 1), ECUDA. */
+epwi_status epwi_fma_peak(int32_t fp64, int32_t device, void *cuda_stream, double target_ms,
+                          double *tflops, double *ms);
+
 /* Statistics of the last epwi_scatter_rates. */
 epwi_status epwi_get_stats(epwi_ctx *ctx, epwi_stats *out);
 

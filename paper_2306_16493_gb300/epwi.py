@@ -116,6 +116,7 @@ def _load() -> C.CDLL:
         "epwi_g2": (I32, [P, I64, P, P, I32, I32, P]),
         "epwi_get_stats": (I32, [P, P]),
         "epwi_kernel_launches": (I64, []),
+        "epwi_fma_peak": (I32, [I32, I32, P, D, P, P]),
         "epwi_conductivity_noalloc": (I32, [I64, P, P, P, D, D, D, I64, P, P]),
         "epwi_mlp_default_train_options": (V, [P]),
         "epwi_mlp_train": (I32, [P, D, D, D, D, D, P, P]),
@@ -315,6 +316,16 @@ def epwi_conductivity_noalloc(n_states: int, eps_dev: int, vel_dev: int, inv_tau
 
 def epwi_kernel_launches() -> int:
     return int(_lib.epwi_kernel_launches())
+
+
+def epwi_fma_peak(fp64: bool, device: int = 0, stream: int | None = None, target_ms: float = 50.0):
+    """Measured FMA throughput (TFLOP/s, ms of the best launch) of FP32 or FP64 FMAs."""
+    tf, ms = C.c_double(), C.c_double()
+    st = _lib.epwi_fma_peak(int(bool(fp64)), int(device), C.c_void_p(stream or 0), float(target_ms),
+                            C.byref(tf), C.byref(ms))
+    if st != 0:
+        raise EpwiError(st, "epwi_fma_peak failed")
+    return tf.value, ms.value
 
 
 def epwi_get_stats(ctx) -> dict:

@@ -13,7 +13,17 @@ import bench  # noqa: E402
 STATS = {"scatter_flops": 8.0e13, "ms_scatter": 100.0, "n_chunks": 10}
 
 
-def test_fp32_roofline_uses_the_derived_cuda_core_peak():
+def test_fp32_roofline_uses_the_measured_simt_peak():
+    probe = {"fp32": (70.0, "measured"), "fp64": (1.2, "measured")}
+    r = bench.roofline_for("fp32", STATS, per_launch_traffic=1.0e9, simt_peaks=probe)
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert r["peak"] == 70.0 and r["peak_source"] == "measured"
+    assert r["achieved"] == pytest.approx(8.0e13 / 0.1 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / 70.0)
+    assert bench.roofline_for("fp64", STATS, simt_peaks=probe)["peak"] == 1.2
+
+
+def test_fp32_roofline_falls_back_to_the_derived_cuda_core_peak():
     r = bench.roofline_for("fp32", STATS, per_launch_traffic=1.0e9)
     assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
     assert r["peak"] == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)

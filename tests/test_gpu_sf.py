@@ -1,16 +1,22 @@
 """GPU parity of the fp32 mode: FP32 Re->k, the Rp->q sum factorised over the axes of the R_p
 cube (per plane block, per q1 run, per pair), FP32 rotations and delta terms, FP64 sums per
 state.  Compared with the FP64 oracle on cubic and non-cubic grids (ragged plane blocks and
-runs), with the FP64 GPU path, across k-point chunking and repeated runs."""
+runs), with the FP64 GPU path, across k-point chunking and repeated runs, and at the 48^3
+benchmark configuration on sampled k-points.
+
+1/tau is compared per degenerate group with the error relative to that group's own rate
+(tests.parity.compare_rates), sigma in Frobenius norm."""
 import numpy as np
 import pytest
 
 from oracle import epwi_oracle as O
 from paper_2306_16493_gb300 import epwi, synth
+from tests.parity import compare_rates, gpu_run, oracle_run, rel_frob
 
 pytestmark = pytest.mark.gpu
 T = 300.0
 TOL = 1e-5          # FP32 interpolation and delta terms, FP64 sums
+SIGMA_TOL = 1e-5
 
 
 def _rates(system, grid, mu, eta, lo, hi, precision="fp32", chunk=0):
@@ -36,10 +42,13 @@ def test_fp32_matches_the_oracle(name, grid, half, eta):
     gr = O.Grids(s, grid)
     mu = gr.band_centre()
     lo, hi = (-1e9, 1e9) if half is None else (mu - half, mu + half)
-    ref = O.serta(gr, T, mu, eta, lo, hi)
-    k, b, r, npairs = _rates(s, grid, mu, eta, lo, hi)
-    assert np.array_equal(k, ref["ik"]) and np.array_equal(b, ref["n"]) and npairs == ref["n_pairs"]
-    assert np.abs(r - ref["inv_tau"]).max() <= TOL * ref["inv_tau"].max()
+    ref = oracle_run(gr, T, mu, eta, lo, hi)
+    out = gpu_run(s, grid, T, mu, eta, lo, hi, precision="fp32")
+    assert out["n_pairs"] == ref["n_pairs"]
+    err, n = compare_rates(out, ref, gr.eps, TOL)
+    assert n > 0 and err <= TOL, err
+    assert rel_frob(out["sigma"], ref["sigma"]) <= SIGMA_TOL
+    out["ctx"].close()
 
 
 def test_fp32_against_fp64_gpu_and_determinism():
@@ -53,6 +62,36 @@ def test_fp32_against_fp64_gpu_and_determinism():
     d = _rates(*args)
     assert np.abs(a[2] - b[2]).max() <= TOL * a[2].max()
     assert np.array_equal(b[2], c[2]) and np.array_equal(b[2], d[2])
+
+
+def test_al_like_48_sampled_fp32():
+    """The benchmark configuration in the benchmark's precision: Al-like 48^3, window +-0.3 eV
+    around the band centre, eta = 20 meV, default k-point chunking.  Eight sampled window
+    k-points are recomputed by the oracle (all their q); the full sigma is compared with the
+    FP64 GPU path on the same grid."""
+    s = synth.al_like_system()
+    N, eta = 48, 0.02
+    ctx = epwi.Context(precision="fp32")
+    ctx.setup(s)
+    ctx.eigs(N)
+    lo, hi = ctx.band_range()
+    mu = 0.5 * (lo + hi)
+    out = gpu_run(s, (N, N, N), T, mu, eta, mu - 0.3, mu + 0.3, precision="fp32", ctx=ctx)
+    assert out["stats"]["n_chunks"] > 1            # several launches, as in the benchmark
+    gr = O.Grids(s, (N, N, N))
+    kp, cnt = ctx.sieve()
+    pick = kp[np.random.default_rng(29).choice(len(kp), 8, replace=False)]
+    ora = oracle_run(gr, T, mu, eta, mu - 0.3, mu + 0.3, k_subset=pick)
+    sel = np.isin(out["ik"], pick)
+    sub = dict(ik=out["ik"][sel], n=out["n"][sel], inv_tau=out["inv_tau"][sel])
+    err, n = compare_rates(sub, ora, gr.eps, TOL)
+    assert n >= 8 and err <= TOL, err
+    assert [int(x) for x in cnt[np.searchsorted(kp, pick)]] == [ora["pairs_per_k"][int(k)] for k in pick]
+    ref64 = gpu_run(s, (N, N, N), T, mu, eta, mu - 0.3, mu + 0.3, precision="fp64", ctx=ctx)
+    err64, _ = compare_rates(out, ref64, gr.eps, TOL)
+    assert err64 <= TOL, err64
+    assert rel_frob(out["sigma"], ref64["sigma"]) <= SIGMA_TOL
+    ctx.close()
 
 
 def test_fp32_refuses_what_it_does_not_serve():

@@ -2,8 +2,10 @@
 
 Stated tolerances (relative): |g|^2 <= 1e-5 norm-wise per batch of pairs, 1/tau <= 1e-4 per
 degenerate group, sigma and mobility <= 1e-4 in Frobenius norm.  fp16x3 and tf32x3 keep ~22
-mantissa bits per operand and meet all three; bf16x3 keeps ~16 bits and is held to the
-looser |g|^2 bound it can reach (its 1/tau and sigma still meet 1e-4)."""
+mantissa bits per operand and meet all three: they are the split modes that meet the stated
+tolerances.  bf16x3 keeps ~16 bits (two 8-bit bf16 terms per operand) and does NOT meet the
+stated |g|^2 bound; it is kept as a measured comparison mode, and its |g|^2 test records the
+1e-4 it reaches so that a regression shows (its 1/tau and sigma still meet 1e-4)."""
 import numpy as np
 import pytest
 
@@ -13,7 +15,7 @@ from tests import models as M
 from tests.parity import compare_rates, gpu_run, oracle_run, rel_frob
 
 pytestmark = pytest.mark.gpu
-G2_TOL = {"fp16x3": 1e-5, "tf32x3": 1e-5, "bf16x3": 1e-4}
+G2_TOL = {"fp16x3": 1e-5, "tf32x3": 1e-5, "bf16x3": 1e-4}   # bf16x3: not the stated 1e-5 (see above)
 RATE_TOL = 1e-4
 MODES = ["fp16x3", "tf32x3", "bf16x3"]
 
