@@ -278,6 +278,23 @@ epwi_status epwi_setup(epwi_ctx *c, const epwi_system *s) {
             if (ok) c->rp_cube_r = rr;
             break;
         }
+        // fp32 mode: R_p embedded in its bounding cube [-r, r]^3 (points outside the set carry
+        // zero weight); g' is built from the weighted g on the first fp32 rates call
+        {
+            int r = 0;
+            for (int i = 0; i < 3 * nRp; ++i) r = std::max(r, std::abs(s->Rp[i]));
+            c->sf_r = r;
+            c->sf_g_ready = false;
+            c->h_rp_cube.clear();
+            if (r <= 6) {
+                const int Dc = 2 * r + 1;
+                c->h_rp_cube.assign((size_t)Dc * Dc * Dc, -1);
+                for (int k = 0; k < nRp; ++k)
+                    c->h_rp_cube[((size_t)(s->Rp[3 * k] + r) * Dc + (s->Rp[3 * k + 1] + r)) * Dc +
+                                 (s->Rp[3 * k + 2] + r)] = k;
+            }
+            c->gsf32.release();
+        }
         // |ghat(k)[rp][mu][i][n]| <= sum_Re sum_j |w g| (|V_jn| <= 1): scale fp16 operands so
         // that this bound maps to 2^14 (no overflow, full mantissa for the split).
         std::vector<double> rp_bound(nRp, 0.0);
@@ -460,12 +477,13 @@ void end_rates(epwi_ctx *c) {
                              c->nw * (c->opt.precision == EPWI_FP64 ? 16 : 8);
     const double nbar = (double)c->nstates / std::max<int64_t>(1, c->nkp);
     c->stats.scatter_flops = 8.0 * c->nRp * c->nm * c->nw * (double)c->npairs * nbar;
-    if (c->opt.precision == EPWI_FP32 && c->rp_cube_r >= 0) {
-        // per (pair, band): the R3 sum and the rotations of one final band, the least any pair
-        // needs (the per-block and per-run sums are shared, bands out of range are skipped;
-        // neither is counted)
-        const double D = 2 * c->rp_cube_r + 1, X = (double)c->nm * c->nw;
-        c->stats.scatter_flops = 8.0 * (D * X + (double)c->nw * c->nm + (double)c->nm * c->nm) *
+    if (c->opt.precision == EPWI_FP32) {
+        // per (pair, band): the last factor of the R_p sum (real coefficients on 2r recombined
+        // forms, 4 flop each per column) and the rotations of one final band, the least any
+        // pair needs (the per-block and per-run sums are shared, bands out of range are
+        // skipped; neither is counted)
+        const double NF = 2.0 * c->sf_r, X = (double)c->nm * c->nw;
+        c->stats.scatter_flops = (4.0 * NF * X + 8.0 * ((double)c->nw * c->nm + (double)c->nm * c->nm)) *
                                  (double)c->npairs * nbar;
     }
     c->have_rates = true;

@@ -160,6 +160,11 @@ struct epwi_ctx {
     DevBuf tc_meta;                // per-tile metadata of the tensor-core kernel
     DevBuf tc_arows;               // gathered-A mode: split phase rows of every grid point
     DevBuf sf_items;               // fp32 mode: (k-point, band) work items of a chunk
+    int sf_r = 0;                  // fp32 mode: half-width of the bounding cube of R_p
+    std::vector<int> h_rp_cube;    // fp32 mode: R_p index of each bounding-cube point, -1 if absent
+    DevBuf gsf32;                  // fp32 mode: g' [Re][cube forms][Nm][W][W] (+-R recombined)
+    bool sf_g_ready = false;       // gsf32 built for the current system
+    DevBuf sf_Vt32;                // fp32 mode: float2 [Nk][m][i], V transposed
     int64_t tc_arows_key = -1;
     bool tc_gather = false;        // use the gathered-A mode where it applies
     int64_t stats_tc_grid = 0;
@@ -195,11 +200,19 @@ struct epwi_ctx {
                          &scan_tmp, &red_tmp, &counts, &tc_ptab, &tc_erel, &tc_f32,
                          &tc_n32, &tc_hw32, &tc_err, &tc_meta, &is_pairs, &is_w,
                          &is_kp_pairs, &sieve_mask, &tc_arows, &ib_pairs, &ib_goff, &ib_gam,
-                         &ib_kpos, &ib_F0, &ib_F, &ib_Fn, &ib_red, &ib_F32, &ib_Fn32, &sf_items};
+                         &ib_kpos, &ib_F0, &ib_F, &ib_Fn, &ib_red, &ib_F32, &ib_Fn32, &sf_items,
+                         &gsf32, &sf_Vt32};
         for (DevBuf *b : all) b->release();
         mlp_free(mlp);
     }
 };
+
+// Uploads a host int vector into b (synchronously ordered on the context stream).
+inline void upload_ints(epwi_ctx *c, DevBuf &b, const std::vector<int> &h) {
+    b.ensure(sizeof(int) * (h.size() + 1));
+    if (!h.empty())
+        EPWI_CUDA(cudaMemcpyAsync(b.p, h.data(), sizeof(int) * h.size(), cudaMemcpyHostToDevice, c->stream));
+}
 
 // ----------------------------------------------------------------------------- complex
 __host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {

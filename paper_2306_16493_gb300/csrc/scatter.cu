@@ -431,7 +431,10 @@ void process_workset(epwi_ctx *c, const WorkSet &ws, double *g2out, double *tout
     EPWI_REQUIRE(!tc || !tout, EPWI_EINVAL, "per-pair terms need the FP64 path");
     EPWI_REQUIRE(!sf || (!g2out && !tout && !ws.pair_w && !ws.gam64 && ws.ovr_nsel < 0),
                  EPWI_EUNSUPPORTED, "the fp32 mode serves the sieved rates (and their Gamma) only");
-    if (sf) sf_check(c);
+    if (sf) {
+        sf_check(c);
+        sf_prepare(c);
+    }
     // chunk limits: pairs and Re->k output size
     const int64_t max_pairs = int64_t(1) << 27;
     const size_t state_bytes = sf ? sf_state_bytes(c) : tc ? tc_state_bytes(c) : sizeof(double2) * nrow;

@@ -107,6 +107,7 @@ void process_kbatch(epwi_ctx *c);
 // fp32 mode (sum-factorised Rp->q, scatter_sf.cu)
 size_t sf_state_bytes(const epwi_ctx *c);
 void sf_check(const epwi_ctx *c);
+void sf_prepare(epwi_ctx *c);
 void sf_restage(epwi_ctx *c, const RestageArgs &ra);
 void sf_scatter(epwi_ctx *c, const ScatterArgs &sa, int64_t nkp, const int64_t *kp_pairs_local, int64_t p_off,
                 const std::vector<int64_t> &h_kp_state_chunk);

@@ -1,23 +1,30 @@
 // Sum-factorised Rp->q stage in FP32 (precision EPWI_FP32), fused with the rotations and the
 // delta sum of Eq. 10.
 //
-// R_p is the full cube [-r, r]^3, so the phase of Eq. 16 factorises per axis:
-// e^{iq.Rp} = e1(q1, R1) e2(q2, R2) e3(q3, R3) with e_a(x, R) = e^{2 pi i x R / N_a}.  The sum
-// over the cube is then three nested sums of D = 2r + 1 terms, and each is done where its
-// result can be shared.  The sieve lists the pairs of a k-point in plane blocks pb of 256
-// consecutive (q2, q3) combinations, then by q1, then by combination.
-//   Y[R1][R3][j]  = sum_R2 e2(q2_j, R2) ghat[R1, R2, R3]   once per plane block (its q2 values j)
-//   U[R3][j]      = sum_R1 e1(q1, R1) Y[R1][R3][j]          once per run (plane block, q1)
-//   G             = sum_R3 e3(q3, R3) U[R3][j(q)]           per pair
-// with ghat = (g P^el) U^dag(k) from the FP32 Re->k stage, every column (mu, i) at once.  A
-// pair costs D N_m W complex MACs instead of D^3 N_m W.  Then, per pair, come the rotations
-// U(k+q) [.] u(q), |g|^2 and the two delta terms, in FP32.
+// Any R_p set is embedded in its bounding cube [-r, r]^3 (vectors outside the set carry zero
+// weight), so the phase of Eq. 16 factorises per axis: e^{iq.Rp} = e1(q1,R1) e2(q2,R2)
+// e3(q3,R3), e_a(x, R) = e^{i theta R}, theta = 2 pi x / N_a.  Along each axis the values at
+// +R and -R are recombined once, at setup, into
+//     v'[0] = v[0],  v'[2R-1] = v[R] + v[-R],  v'[2R] = i (v[R] - v[-R])      (R = 1..r)
+// so that sum_R e^{i theta R} v[R] = v'[0] + sum_R (cos(theta R) v'[2R-1] + sin(theta R) v'[2R]):
+// every stage below is a contraction with REAL coefficients (2 FMAs per complex term instead
+// of 4).  The recombination acts on the R_p index only, so it commutes with the Re->k sum and
+// the U^dag(k) rotation and is applied to g(Re, Rp) itself (k_sf_transform).
 //
-// One CTA per (window k-point, band), eight warps.  Warps take the runs of a plane block
-// two at a time, round-robin by q1, and walk the pairs of both as one list.  With a Gamma capture (iterative BTE) the CTA also writes its band's row
-// of every pair's Gamma block; rows of bands skipped as out of range stay at the zero the
-// buffer was cleared to.  Lane sums are FP32 within a run; the run sums go into per-warp FP64
-// accumulators, which are added in warp order, so the result is deterministic.
+// The sieve lists the pairs of a k-point in plane blocks pb of 256 consecutive (q2, q3)
+// combinations, then by q1, then by combination.  For the state (k, n) of one CTA:
+//   Y[f1][f3][j]  = sum_f2 c2(q2_j)[f2] ghat'[f1][f2][f3]    per plane block and group of q2 values j
+//   U[f3][j]      = sum_f1 c1(q1)[f1]  Y[f1][f3][j]           per run (plane block, q1, q2 group)
+//   G             = sum_f3 c3(q3)[f3]  U[f3][j(q)]            per pair
+// with ghat' = (g' P^el) U^dag(k) from the FP32 Re->k stage, every column (mu, i) at once.
+// U is built for a batch of runs by the whole CTA; then every thread takes pairs of the batch
+// from one flat list.  Per pair, each lane loops over the final bands m that have a mode within
+// c eta of either energy shell (others add exactly zero), and for each band streams the modes
+// mu: h = sum_i conj(V_im(k+q)) G[mu][i], g_nu += h u_mu,nu(q); then |g|^2 and the two delta
+// terms, in FP32.  With a Gamma capture (iterative BTE) the CTA also writes its band's row of
+// every pair's Gamma block (rows of bands out of range stay at the zero the buffer was cleared
+// to).  Lane sums are FP32 within a batch, FP64 across batches, and the CTA adds its threads
+// in a fixed order, so the result is deterministic and independent of k-point chunking.
 #include <algorithm>
 
 #include "epwi_internal.cuh"
@@ -30,7 +37,7 @@ constexpr int kSfThreads = 256;
 constexpr int kSfWarps = kSfThreads / 32;
 
 // Re->k in FP32: ghat32[state][row] = sum_j [sum_Re w e^{ik.Re} g(Re)[row][j]] V_{j, lo+n}(k),
-// row = (rp N_m + mu) W + i; one thread per row, KG k-points per block row.
+// row = (cube form, mu, i); one thread per row, KG k-points per block row.
 template <int WT, int KG>
 __global__ void __launch_bounds__(128) k_restage_f32(RestageArgs a, float2 *__restrict__ out) {
     constexpr int WM = WT ? WT : epc::kMaxW;
@@ -77,19 +84,79 @@ __global__ void __launch_bounds__(128) k_restage_f32(RestageArgs a, float2 *__re
     }
 }
 
+// g'(Re, f1 f2 f3) = (T x T x T) g(Re, cube): along each axis, form 0 is R = 0, form 2R-1 is
+// v[R] + v[-R] and form 2R is i (v[R] - v[-R]).  cube[c] is the index of the R_p vector at
+// cube point c, or -1 (zero weight).  One thread per output element; FP64 sums, FP32 output.
+__global__ void k_sf_transform(int64_t n, int nRp, int Dc, int rc, int rowlen, const int *__restrict__ cube,
+                               const double2 *__restrict__ g64, const float2 *__restrict__ g32,
+                               float2 *__restrict__ out) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    const int e = (int)(idx % rowlen);              // (mu, i, j) within the (Re, form) block
+    const int64_t t = idx / rowlen;
+    const int D3 = Dc * Dc * Dc;
+    const int cf = (int)(t % D3);
+    const int64_t re = t / D3;
+    const int f[3] = {cf / (Dc * Dc), (cf / Dc) % Dc, cf % Dc};
+    int Rv[3][2], nt[3];
+    double2 cv[3][2];
+    for (int a = 0; a < 3; ++a) {
+        if (f[a] == 0) {
+            nt[a] = 1;
+            Rv[a][0] = 0;
+            cv[a][0] = make_double2(1, 0);
+        } else {
+            const int R = (f[a] + 1) / 2;
+            nt[a] = 2;
+            Rv[a][0] = R;
+            Rv[a][1] = -R;
+            if (f[a] & 1) {
+                cv[a][0] = make_double2(1, 0);
+                cv[a][1] = make_double2(1, 0);
+            } else {
+                cv[a][0] = make_double2(0, 1);
+                cv[a][1] = make_double2(0, -1);
+            }
+        }
+    }
+    double2 s = make_double2(0, 0);
+    for (int x = 0; x < nt[0]; ++x)
+        for (int y = 0; y < nt[1]; ++y)
+            for (int z = 0; z < nt[2]; ++z) {
+                const int c = ((Rv[0][x] + rc) * Dc + (Rv[1][y] + rc)) * Dc + (Rv[2][z] + rc);
+                const int rp = cube[c];
+                if (rp < 0) continue;
+                const size_t gi = ((size_t)re * nRp + rp) * rowlen + e;
+                const double2 v = g64 ? g64[gi] : make_double2(g32[gi].x, g32[gi].y);
+                s = cadd(s, cmul(cmul(cmul(cv[0][x], cv[1][y]), cv[2][z]), v));
+            }
+    out[idx] = make_float2((float)s.x, (float)s.y);
+}
+
+// Vt[k][m][i] = V[k][i][m] (FP32): one column of V(k+q) is one contiguous row.
+__global__ void k_transpose_v(int64_t nk, int W, const float2 *__restrict__ V, float2 *__restrict__ Vt) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nk * W * W) return;
+    const int64_t k = idx / (W * W);
+    const int e = (int)(idx % (W * W)), m = e / W, i = e % W;
+    Vt[idx] = V[k * W * W + i * W + m];
+}
+
 struct SfArgs {
     GridInfo g;
-    int64_t nplane;                 // N2 N3
-    int nq2max;                     // largest count of q2 values in one plane block
+    int nplane;                     // N2 N3
+    int jq;                         // q2 values per group (Y and U hold one group)
+    int njg;                        // groups per plane block (over the largest block)
+    int nb;                         // runs per U batch
     const float2 *ph32;             // e^{2 pi i m / L}
-    const float2 *ghat;             // [state - s_base][D^3][N_m][W]
+    const float2 *ghat;             // [state - s_base][D^3 forms][N_m][W]
     const int *kpts, *win_lo, *win_n;
     const int64_t *kp_state;        // chunk k-points' first states (global)
     int64_t s_base;
     const int64_t *kp_pairs;        // chunk-local pair offsets, minus p_off
     int64_t p_off;
     const int *pairs;               // chunk pair list: q index
-    const float2 *V32, *u32;
+    const float2 *Vt32, *u32;
     const float *erel, *f32, *n32, *hw32;
     float ceta32, inv_eta32;
     double pref;                    // 2 pi / (hbar N_q sqrt(pi) eta)
@@ -98,12 +165,6 @@ struct SfArgs {
     float *gam;                     // Gamma capture (iterative BTE) or nullptr: row n of each
     const int64_t *goff;            // pair's block, block start goff[chunk pair]
 };
-
-__device__ __forceinline__ float2 axis_phase(const float2 *ph, int x, int s, int R, int L) {
-    int t = ((x * s) % L) * R % L;
-    if (t < 0) t += L;
-    return ph[t];
-}
 
 // first position in [lo, hi) whose key is >= key (keys ascending)
 template <typename F>
@@ -116,41 +177,62 @@ __device__ __forceinline__ int64_t lower_bound(int64_t lo, int64_t hi, int64_t k
     return lo;
 }
 
+// Shared-memory layout of k_scatter_sf (float2 units first, then floats, then ints).
+struct SfSmem {
+    size_t y, u, cs, ints, bytes;
+};
+__host__ __device__ inline SfSmem sf_smem_layout(int D, int X, int jq, int nb, int N1, int N2, int N3, int njg) {
+    SfSmem s;
+    s.y = (size_t)D * D * jq * X;                          // float2
+    s.u = (size_t)nb * D * jq * X;                         // float2
+    s.cs = (size_t)(N1 + N2 + N3) * (D - 1);               // float: (cos, sin) per R >= 1
+    s.ints = (size_t)kSieveBlock + 2 * (size_t)N1 * njg + (size_t)N1 + (size_t)nb + 2 + 4;
+    s.bytes = sizeof(float2) * (s.y + s.u) + sizeof(float) * s.cs + sizeof(int) * s.ints;
+    return s;
+}
+
 template <int W, int NM, int RC, bool GAM>
-__global__ void __launch_bounds__(kSfThreads, 2) k_scatter_sf(SfArgs a) {
+__global__ void __launch_bounds__(kSfThreads, (W <= 4 ? 3 : 2)) k_scatter_sf(SfArgs a) {
     constexpr int D = 2 * RC + 1;
+    constexpr int NF = D - 1;                    // forms with a cos / sin coefficient
     constexpr int X = NM * W;                    // columns (mu, i)
-    extern __shared__ float2 sm[];
-    const int Q = a.nq2max;
+    constexpr bool V2 = (W % 2) == 0;            // rows of W float2 are 16-byte aligned
+    constexpr int kMuUnroll = NM <= 3 ? NM : 1;  // wide systems: one mode row at a time (registers)
+    extern __shared__ __align__(16) float2 sm[];
     const int N1 = a.g.n1, N2 = a.g.n2, N3 = a.g.n3, L = a.g.L;
-    float2 *gk = sm;                             // [D^3][X]
-    float2 *Y = gk + D * D * D * X;              // [D (R1)][D (R3)][Q][X]
-    float2 *Uall = Y + D * D * Q * X;            // [warp][2 runs][D (R3)][Q][X]
-    float2 *E1 = Uall + 2 * kSfWarps * D * Q * X;   // [N1][D] axis phases e^{2 pi i x R / N}
-    float2 *E2 = E1 + N1 * D;                    // [N2][D]
-    float2 *E3 = E2 + N2 * D;                    // [N3][D]
-    int *cq = reinterpret_cast<int *>(E3 + N3 * D);   // [kSieveBlock]: (j << 16) | q3 of combination c_lo + t
-    int *rs = cq + kSieveBlock;                  // [N1]: run start (relative to the block), -1 if none
-    int *re = rs + N1;                           // [N1]: run end
+    const int JQ = a.jq, NJG = a.njg, NB = a.nb;
+    const SfSmem lay = sf_smem_layout(D, X, JQ, NB, N1, N2, N3, NJG);
+    float2 *Y = sm;                              // [D f1][D f3][JQ][X]
+    float2 *U = Y + lay.y;                       // [NB][D f3][JQ][X]
+    float *CS = reinterpret_cast<float *>(U + lay.u);   // [N1 + N2 + N3][NF]: cos, sin of theta R
+    int *cq = reinterpret_cast<int *>(CS + lay.cs);     // [256]: (j << 16) | q3 of combination t
+    int *ss = cq + kSieveBlock;                  // [N1 NJG]: segment start (relative), -1 if none
+    int *se = ss + N1 * NJG;                     // [N1 NJG]: segment end
+    int *gl = se + N1 * NJG;                     // [N1]: segments (keys) of the current group
+    int *pf = gl + N1;                           // [NB + 1]: pair prefix of the current batch
+    int *nglist = pf + NB + 1;                   // [1]
     __shared__ double wsum[kSfWarps];
     const int2 item = a.items[blockIdx.x];
     const int kp = item.x, n = item.y;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    float2 *U = Uall + (size_t)wid * 2 * D * Q * X;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int ik = a.kpts[kp];
     const int lo = a.win_lo[ik];
     const int64_t s = a.kp_state[kp] + n;        // global state
     const float2 *gs = a.ghat + (size_t)(s - a.s_base) * D * D * D * X;
-    for (int e = threadIdx.x; e < D * D * D * X; e += kSfThreads) gk[e] = gs[e];
-    for (int e = threadIdx.x; e < (N1 + N2 + N3) * D; e += kSfThreads) {
-        const int R = e % D - RC, x = e / D;
-        float2 v;
-        if (x < N1) v = axis_phase(a.ph32, x, a.g.s1, R, L);
-        else if (x < N1 + N2) v = axis_phase(a.ph32, x - N1, a.g.s2, R, L);
-        else v = axis_phase(a.ph32, x - N1 - N2, a.g.s3, R, L);
-        E1[e] = v;                               // E1, E2, E3 are consecutive
+    // cos / sin tables of the three axes (exact integer reduction of x R onto the L roots)
+    for (int e = tid; e < (N1 + N2 + N3) * RC; e += kSfThreads) {
+        const int R = e % RC + 1, x = e / RC;
+        int xx, st;
+        if (x < N1) { xx = x; st = a.g.s1; }
+        else if (x < N1 + N2) { xx = x - N1; st = a.g.s2; }
+        else { xx = x - N1 - N2; st = a.g.s3; }
+        const int t = (int)(((int64_t)xx * st % L) * R % L);
+        const float2 v = a.ph32[t];
+        CS[x * NF + 2 * (R - 1)] = v.x;
+        CS[x * NF + 2 * (R - 1) + 1] = v.y;
     }
-    const int nplane = (int)a.nplane;
+    const float *CS1 = CS, *CS2 = CS + N1 * NF, *CS3 = CS + (N1 + N2) * NF;
+    const int nplane = a.nplane;
     const int pb_n = (nplane + kSieveBlock - 1) / kSieveBlock;
     const int64_t P0 = a.kp_pairs[kp] - a.p_off, P1 = a.kp_pairs[kp + 1] - a.p_off;
     const int *pl = a.pairs;
@@ -158,7 +240,8 @@ __global__ void __launch_bounds__(kSfThreads, 2) k_scatter_sf(SfArgs a) {
     int k1, k2, k3;
     grid_coords(a.g, ik, k1, k2, k3);
     const float en = a.erel[(int64_t)ik * W + lo + n];
-    double wacc = 0;                             // this warp's run sums
+    const float ceta = a.ceta32, ieta = a.inv_eta32;
+    double acc = 0;                              // this thread's batch sums
     __syncthreads();
     int64_t seg0 = P0;
     for (int pb = 0; pb < pb_n && seg0 < P1; ++pb) {
@@ -167,209 +250,279 @@ __global__ void __launch_bounds__(kSfThreads, 2) k_scatter_sf(SfArgs a) {
         if (seg1 == seg0) continue;
         const int c_lo = pb * kSieveBlock, c_hi = min(nplane, c_lo + kSieveBlock) - 1;
         const int q2lo = c_lo / N3, nq2 = c_hi / N3 - q2lo + 1;
-        // per combination of the block: (j, q3); runs: none yet
-        for (int t = threadIdx.x; t < kSieveBlock; t += kSfThreads) {
+        const int njg = (nq2 + JQ - 1) / JQ;
+        for (int t = tid; t < kSieveBlock; t += kSfThreads) {
             const int c = c_lo + t, q2 = c / N3;
             cq[t] = ((q2 - q2lo) << 16) | (c - q2 * N3);
         }
-        for (int t = threadIdx.x; t < N1; t += kSfThreads) rs[t] = -1;
-        // Y over this block's q2 values (all threads)
-        for (int e = threadIdx.x; e < D * D * nq2 * X; e += kSfThreads) {
-            const int col = e % X, t = e / X;
-            const int j = t % nq2, r13 = t / nq2;
-            const int R3 = r13 % D, R1 = r13 / D;
-            const float2 *e2 = E2 + (q2lo + j) * D;
-            float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int R2 = 0; R2 < D; ++R2) acc = cfmaf(e2[R2], gk[((R1 * D + R2) * D + R3) * X + col], acc);
-            Y[((R1 * D + R3) * Q + j) * X + col] = acc;
-        }
+        for (int t = tid; t < N1 * NJG; t += kSfThreads) ss[t] = -1;
         __syncthreads();
-        // run boundaries: the block's pairs are ordered by q1
+        // segments: the block's pairs are ordered by q1, then by combination (so by q2 group)
         const int nseg = (int)(seg1 - seg0);
-        for (int t = threadIdx.x; t < nseg; t += kSfThreads) {
-            const int q1 = pl[seg0 + t] / nplane;
-            if (t == 0 || pl[seg0 + t - 1] / nplane != q1) rs[q1] = t;
-            if (t == nseg - 1 || pl[seg0 + t + 1] / nplane != q1) re[q1] = t + 1;
+        auto keyof = [&](int t) -> int {
+            const int q = pl[seg0 + t];
+            const int q1 = q / nplane;
+            const int j = cq[q - q1 * nplane - c_lo] >> 16;
+            return q1 * NJG + j / JQ;
+        };
+        for (int t = tid; t < nseg; t += kSfThreads) {
+            const int key = keyof(t);
+            if (t == 0 || keyof(t - 1) != key) ss[key] = t;
+            if (t == nseg - 1 || keyof(t + 1) != key) se[key] = t + 1;
         }
         __syncthreads();
-        // runs: warp w takes q1 = w + 16 i and w + 16 i + 8 together (U of both in shared
-        // memory) and walks their pairs as one list, so that short runs share lane rounds
-        for (int qa = wid; qa < N1; qa += 2 * kSfWarps) {
-            const int qb = qa + kSfWarps;
-            const int ra0 = rs[qa];
-            const int na = ra0 < 0 ? 0 : re[qa] - ra0;
-            const int rb0 = qb < N1 ? rs[qb] : -1;
-            const int nb = rb0 < 0 ? 0 : re[qb] - rb0;
-            if (na + nb == 0) continue;
-            for (int h2 = 0; h2 < 2; ++h2) {
-                if ((h2 == 0 ? na : nb) == 0) continue;
-                const float2 *e1 = E1 + (h2 == 0 ? qa : qb) * D;
-                float2 *Uh = U + h2 * D * Q * X;
-                for (int e = lane; e < D * nq2 * X; e += 32) {
-                    const int col = e % X, t = e / X;
-                    const int j = t % nq2, R3 = t / nq2;
-                    float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-                    for (int R1 = 0; R1 < D; ++R1) acc = cfmaf(e1[R1], Y[((R1 * D + R3) * Q + j) * X + col], acc);
-                    Uh[(R3 * Q + j) * X + col] = acc;
+        for (int jg = 0; jg < njg; ++jg) {
+            const int j0 = jg * JQ, jn = min(JQ, nq2 - j0);
+            // the group's non-empty runs, in q1 order (warp 0)
+            if (wid == 0) {
+                int cnt = 0;
+                for (int q0 = 0; q0 < N1; q0 += 32) {
+                    const int q1 = q0 + lane;
+                    const bool on = q1 < N1 && ss[q1 * NJG + jg] >= 0;
+                    const unsigned b = __ballot_sync(0xffffffffu, on);
+                    if (on) gl[cnt + __popc(b & ((1u << lane) - 1u))] = q1;
+                    cnt += __popc(b);
                 }
+                if (lane == 0) *nglist = cnt;
             }
-            __syncwarp();
-            float rate = 0.f;
-            for (int tt0 = lane; tt0 < na + nb; tt0 += 32) {
-                const bool inA = tt0 < na;
-                const int q1 = inA ? qa : qb;
-                const int t = inA ? ra0 + tt0 : rb0 + (tt0 - na);
-                const float2 *Ur = inA ? U : U + D * Q * X;
-                int b1 = k1 + q1;
-                if (b1 >= N1) b1 -= N1;
-                const int qbase = q1 * nplane + c_lo;
-                const int q = pl[seg0 + t];
-                const int cl = q - qbase;
-                if ((unsigned)cl > (unsigned)(c_hi - c_lo)) continue;   // never in sieve order
-                const int jq = cq[cl];
-                const int j = jq >> 16, q3 = jq & 0xffff;
-                const float2 *e3 = E3 + q3 * D;
-                float2 G[X];
+            // Y of this group's q2 values (all threads), read from ghat' (L1 / L2)
+            for (int e = tid; e < D * D * jn * X; e += kSfThreads) {
+                const int col = e % X, t = e / X;
+                const int jj = t % jn, r13 = t / jn;
+                const int f3 = r13 % D, f1 = r13 / D;
+                const float *c2 = CS2 + (q2lo + j0 + jj) * NF;
+                const float2 *src = gs + ((f1 * D) * D + f3) * X + col;
+                float2 v = __ldg(src);                       // form f2 = 0
 #pragma unroll
-                for (int x = 0; x < X; ++x) G[x] = make_float2(0.f, 0.f);
+                for (int f2 = 1; f2 < D; ++f2) {
+                    const float c = c2[f2 - 1];
+                    const float2 w = __ldg(src + f2 * D * X);
+                    v.x = fmaf(c, w.x, v.x);
+                    v.y = fmaf(c, w.y, v.y);
+                }
+                Y[((f1 * D + f3) * JQ + jj) * X + col] = v;
+            }
+            __syncthreads();
+            const int ng = *nglist;
+            for (int b0 = 0; b0 < ng; b0 += NB) {
+                const int nbt = min(NB, ng - b0);
+                // U of the batch's runs
+                for (int e = tid; e < nbt * D * jn * X; e += kSfThreads) {
+                    const int col = e % X, t = e / X;
+                    const int jj = t % jn, t2 = t / jn;
+                    const int f3 = t2 % D, b = t2 / D;
+                    const float *c1 = CS1 + gl[b0 + b] * NF;
+                    const float2 *src = Y + (f3 * JQ + jj) * X + col;
+                    float2 v = src[0];                       // form f1 = 0
 #pragma unroll
-                for (int R3 = 0; R3 < D; ++R3) {
-                    const float2 p3 = e3[R3];
-                    const float2 *u_ = Ur + (R3 * Q + j) * X;
-                    if constexpr (X % 2 == 0) {          // rows of X float2 are 16-byte aligned
-                        const float4 *u4 = reinterpret_cast<const float4 *>(u_);
+                    for (int f1 = 1; f1 < D; ++f1) {
+                        const float c = c1[f1 - 1];
+                        const float2 w = src[f1 * D * JQ * X];
+                        v.x = fmaf(c, w.x, v.x);
+                        v.y = fmaf(c, w.y, v.y);
+                    }
+                    U[((b * D + f3) * JQ + jj) * X + col] = v;
+                }
+                if (wid == 0) {                              // pair prefix of the batch
+                    int len = 0;
+                    if (lane < nbt) {
+                        const int key = gl[b0 + lane] * NJG + jg;
+                        len = se[key] - ss[key];
+                    }
+                    int inc = len;
 #pragma unroll
-                        for (int x = 0; x < X / 2; ++x) {
-                            const float4 v = u4[x];
-                            G[2 * x] = cfmaf(p3, make_float2(v.x, v.y), G[2 * x]);
-                            G[2 * x + 1] = cfmaf(p3, make_float2(v.z, v.w), G[2 * x + 1]);
-                        }
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int t = __shfl_up_sync(0xffffffffu, inc, o);
+                        if (lane >= o) inc += t;
+                    }
+                    if (lane < nbt) pf[lane + 1] = inc;
+                    if (lane == 0) pf[0] = 0;
+                }
+                __syncthreads();
+                float rate = 0.f;
+                const int npb = pf[nbt];
+                for (int i = tid; i < npb; i += kSfThreads) {
+                    int b = 0;                               // slot: pf[b] <= i < pf[b + 1]
+                    while (pf[b + 1] <= i) ++b;
+                    const int q1 = gl[b0 + b];
+                    const int t = ss[q1 * NJG + jg] + (i - pf[b]);
+                    const int64_t p = seg0 + t;
+                    const int q = pl[p];
+                    const int cl = q - (q1 * nplane + c_lo);
+                    const int jq = cq[cl];
+                    const int j = jq >> 16, q3 = jq & 0xffff;
+                    const float2 *Ub = U + ((b * D) * JQ + (j - j0)) * X;   // form f3 at + f3 JQ X
+                    int b1 = k1 + q1, b2 = k2 + q2lo + j, b3 = k3 + q3;
+                    if (b1 >= N1) b1 -= N1;
+                    if (b2 >= N2) b2 -= N2;
+                    if (b3 >= N3) b3 -= N3;
+                    const int ikq = (b1 * N2 + b2) * N3 + b3;   // nk W^2 < 2^31 (checked on the host)
+                    float wq[NM];
+#pragma unroll
+                    for (int nu = 0; nu < NM; ++nu) wq[nu] = __ldg(a.hw32 + q * NM + nu);
+                    float emr[W];
+                    if constexpr (W == 4) {
+                        const float4 e4 = __ldg(reinterpret_cast<const float4 *>(a.erel + ikq * W));
+                        emr[0] = e4.x; emr[1] = e4.y; emr[2] = e4.z; emr[3] = e4.w;
                     } else {
 #pragma unroll
-                        for (int x = 0; x < X; ++x) G[x] = cfmaf(p3, u_[x], G[x]);
+                        for (int m = 0; m < W; ++m) emr[m] = __ldg(a.erel + ikq * W + m);
                     }
-                }
-                int b2 = k2 + q2lo + j, b3 = k3 + q3;
-                if (b2 >= N2) b2 -= N2;
-                if (b3 >= N3) b3 -= N3;
-                const int ikq = (b1 * N2 + b2) * N3 + b3;   // nk W^2 < 2^31 (checked on the host)
-                int lokq = 0, nwkq = 0;
-                int64_t grow = 0;                // this band's row of the pair's Gamma block
-                if constexpr (GAM) {
-                    lokq = __ldg(a.win_lo + ikq);
-                    nwkq = __ldg(a.win_n + ikq);
-                    grow = a.goff[seg0 + t] + (int64_t)n * nwkq - lokq;
-                }
-                const float2 *Vq = a.V32 + ikq * (W * W);
-                const float2 *uq = a.u32 + q * (NM * NM);
-                float wq[NM], nq[NM];
-#pragma unroll
-                for (int nu = 0; nu < NM; ++nu) {
-                    wq[nu] = __ldg(a.hw32 + q * NM + nu);
-                    nq[nu] = __ldg(a.n32 + q * NM + nu);
-                }
-                float2 ur[NM * NM];
-#pragma unroll
-                for (int x = 0; x < NM * NM; ++x) ur[x] = __ldg(uq + x);
-                // V(k+q), eps - mu and f at k+q: 16-byte loads where W = 4 keeps them aligned
-                float2 Vr[W * W];
-                float emr[W], fmr[W];
-                if constexpr (W == 4) {
-                    const float4 *v4 = reinterpret_cast<const float4 *>(Vq);
-#pragma unroll
-                    for (int x = 0; x < W * W / 2; ++x) {
-                        const float4 v = __ldg(v4 + x);
-                        Vr[2 * x] = make_float2(v.x, v.y);
-                        Vr[2 * x + 1] = make_float2(v.z, v.w);
-                    }
-                    const float4 e4 = __ldg(reinterpret_cast<const float4 *>(a.erel + ikq * W));
-                    const float4 f4 = __ldg(reinterpret_cast<const float4 *>(a.f32 + ikq * W));
-                    emr[0] = e4.x; emr[1] = e4.y; emr[2] = e4.z; emr[3] = e4.w;
-                    fmr[0] = f4.x; fmr[1] = f4.y; fmr[2] = f4.z; fmr[3] = f4.w;
-                } else {
-#pragma unroll
-                    for (int x = 0; x < W * W; ++x) Vr[x] = __ldg(Vq + x);
+                    // final bands with a mode inside c eta of either shell (others add zero)
+                    unsigned mask = 0;
 #pragma unroll
                     for (int m = 0; m < W; ++m) {
-                        emr[m] = __ldg(a.erel + ikq * W + m);
-                        fmr[m] = __ldg(a.f32 + ikq * W + m);
-                    }
-                }
+                        bool any = false;
 #pragma unroll
-                for (int m = 0; m < W; ++m) {
-                    const float em = emr[m];
-                    const float fm = fmr[m];
-                    // a band with no mode inside c eta of either shell adds exactly zero
-                    bool any = false;
-#pragma unroll
-                    for (int nu = 0; nu < NM; ++nu) {
-                        const float w = wq[nu];
-                        any |= w >= 0.f && (fabsf((en + w) - em) <= a.ceta32 || fabsf((en - w) - em) <= a.ceta32);
-                    }
-                    if (!any) continue;
-                    float2 h[NM];
-#pragma unroll
-                    for (int mu = 0; mu < NM; ++mu) {
-                        h[mu] = make_float2(0.f, 0.f);
-#pragma unroll
-                        for (int i = 0; i < W; ++i) h[mu] = cfmacf(Vr[i * W + m], G[mu * W + i], h[mu]);
-                    }
-                    float gm = 0.f;                  // Gamma capture: sum over modes
-#pragma unroll
-                    for (int nu = 0; nu < NM; ++nu) {
-                        const float w = wq[nu];
-                        if (w < 0.f) continue;
-                        float2 gv = make_float2(0.f, 0.f);
-#pragma unroll
-                        for (int mu = 0; mu < NM; ++mu) gv = cfmaf(h[mu], ur[mu * NM + nu], gv);
-                        const float g2 = gv.x * gv.x + gv.y * gv.y;
-                        const float x1 = (en + w) - em;
-                        const float x2 = (en - w) - em;
-                        float tt = 0.f;
-                        if (fabsf(x1) <= a.ceta32) {
-                            const float y = x1 * a.inv_eta32;
-                            tt += (nq[nu] + fm) * __expf(-y * y);
+                        for (int nu = 0; nu < NM; ++nu) {
+                            const float w = wq[nu];
+                            any |= w >= 0.f && (fabsf((en + w) - emr[m]) <= ceta || fabsf((en - w) - emr[m]) <= ceta);
                         }
-                        if (fabsf(x2) <= a.ceta32) {
-                            const float y = x2 * a.inv_eta32;
-                            tt += (1.f + nq[nu] - fm) * __expf(-y * y);
-                        }
-                        rate = fmaf(g2, tt, rate);
-                        if constexpr (GAM) gm = fmaf(g2, tt, gm);
+                        if (any) mask |= 1u << m;
                     }
+                    if (!mask) continue;
+                    float c3[NF], nq[NM];
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) c3[f] = CS3[q3 * NF + f];
+#pragma unroll
+                    for (int nu = 0; nu < NM; ++nu) nq[nu] = __ldg(a.n32 + q * NM + nu);
+                    int lokq = 0, nwkq = 0;
+                    int64_t grow = 0;                        // this band's row of the pair's Gamma block
                     if constexpr (GAM) {
-                        if (m >= lokq && m < lokq + nwkq) a.gam[grow + m] = gm;
+                        lokq = __ldg(a.win_lo + ikq);
+                        nwkq = __ldg(a.win_n + ikq);
+                        grow = a.goff[p] + (int64_t)n * nwkq - lokq;
+                    }
+                    const float2 *uq = a.u32 + q * (NM * NM);
+                    while (mask) {
+                        const int m = __ffs(mask) - 1;
+                        mask &= mask - 1;
+                        const float em = __ldg(a.erel + ikq * W + m);
+                        const float fm = __ldg(a.f32 + ikq * W + m);
+                        float2 Vc[W];                        // column m of V(k+q)
+                        const float2 *vp = a.Vt32 + ((int64_t)ikq * W + m) * W;
+                        if constexpr (V2) {
+#pragma unroll
+                            for (int i = 0; i < W / 2; ++i) {
+                                const float4 v = __ldg(reinterpret_cast<const float4 *>(vp) + i);
+                                Vc[2 * i] = make_float2(v.x, v.y);
+                                Vc[2 * i + 1] = make_float2(v.z, v.w);
+                            }
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < W; ++i) Vc[i] = __ldg(vp + i);
+                        }
+                        float2 gv[NM];
+#pragma unroll
+                        for (int nu = 0; nu < NM; ++nu) gv[nu] = make_float2(0.f, 0.f);
+#pragma unroll kMuUnroll
+                        for (int mu = 0; mu < NM; ++mu) {
+                            float2 G[W];
+                            const float2 *u0 = Ub + mu * W;
+                            if constexpr (V2) {
+#pragma unroll
+                                for (int i = 0; i < W / 2; ++i) {
+                                    const float4 v = reinterpret_cast<const float4 *>(u0)[i];
+                                    G[2 * i] = make_float2(v.x, v.y);
+                                    G[2 * i + 1] = make_float2(v.z, v.w);
+                                }
+#pragma unroll
+                                for (int f = 1; f < D; ++f) {
+                                    const float c = c3[f - 1];
+                                    const float4 *uf = reinterpret_cast<const float4 *>(u0 + f * JQ * X);
+#pragma unroll
+                                    for (int i = 0; i < W / 2; ++i) {
+                                        const float4 v = uf[i];
+                                        G[2 * i].x = fmaf(c, v.x, G[2 * i].x);
+                                        G[2 * i].y = fmaf(c, v.y, G[2 * i].y);
+                                        G[2 * i + 1].x = fmaf(c, v.z, G[2 * i + 1].x);
+                                        G[2 * i + 1].y = fmaf(c, v.w, G[2 * i + 1].y);
+                                    }
+                                }
+                            } else {
+#pragma unroll
+                                for (int i = 0; i < W; ++i) G[i] = u0[i];
+#pragma unroll
+                                for (int f = 1; f < D; ++f) {
+                                    const float c = c3[f - 1];
+#pragma unroll
+                                    for (int i = 0; i < W; ++i) {
+                                        const float2 v = u0[f * JQ * X + i];
+                                        G[i].x = fmaf(c, v.x, G[i].x);
+                                        G[i].y = fmaf(c, v.y, G[i].y);
+                                    }
+                                }
+                            }
+                            float2 h = make_float2(0.f, 0.f);
+#pragma unroll
+                            for (int i = 0; i < W; ++i) h = cfmacf(Vc[i], G[i], h);
+#pragma unroll
+                            for (int nu = 0; nu < NM; ++nu) gv[nu] = cfmaf(h, __ldg(uq + mu * NM + nu), gv[nu]);
+                        }
+                        float gm = 0.f;                      // Gamma capture: sum over modes
+#pragma unroll
+                        for (int nu = 0; nu < NM; ++nu) {
+                            const float w = wq[nu];
+                            if (w < 0.f) continue;
+                            const float g2 = gv[nu].x * gv[nu].x + gv[nu].y * gv[nu].y;
+                            const float x1 = (en + w) - em;
+                            const float x2 = (en - w) - em;
+                            float tt = 0.f;
+                            if (fabsf(x1) <= ceta) {
+                                const float y = x1 * ieta;
+                                tt += (nq[nu] + fm) * __expf(-y * y);
+                            }
+                            if (fabsf(x2) <= ceta) {
+                                const float y = x2 * ieta;
+                                tt += (1.f + nq[nu] - fm) * __expf(-y * y);
+                            }
+                            rate = fmaf(g2, tt, rate);
+                            if constexpr (GAM) gm = fmaf(g2, tt, gm);
+                        }
+                        if constexpr (GAM) {
+                            if (m >= lokq && m < lokq + nwkq) a.gam[grow + m] = gm;
+                        }
                     }
                 }
+                acc += (double)rate;
+                __syncthreads();                             // U and pf are rewritten next
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) rate += __shfl_xor_sync(0xffffffffu, rate, o);
-            wacc += (double)rate;
-            __syncwarp();                        // U is rewritten by the next run
+            __syncthreads();                                 // gl, nglist and Y are rewritten next
         }
-        __syncthreads();                         // Y, cq and the runs are rewritten next
         seg0 = seg1;
     }
-    if (lane == 0) wsum[wid] = wacc;
+    // fixed-order sum over the CTA's threads
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) wsum[wid] = acc;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         double t = 0;
         for (int w = 0; w < kSfWarps; ++w) t += wsum[w];
         a.inv_tau[s] = a.pref * t;
     }
 }
 
-size_t sf_smem(int D, int X, int Q, int N1, int N2, int N3) {
-    return sizeof(float2) * ((size_t)D * D * D * X + (size_t)D * D * Q * X + (size_t)2 * kSfWarps * D * Q * X +
-                             (size_t)(N1 + N2 + N3) * D) +
-           sizeof(int) * ((size_t)kSieveBlock + 2 * (size_t)N1);
+struct SfPlan {
+    int jq, njg, nb;
+    size_t smem;
+};
+
+// q2 values per group (jq) and runs per U batch (nb) for the grid: Y and U within budgets that
+// keep two or more CTAs per SM, all of it within the per-CTA limit.
+SfPlan sf_plan(int D, int X, int q2max, int N1, int N2, int N3) {
+    const size_t ybudget = 40 * 1024, ubudget = 28 * 1024;
+    SfPlan p;
+    p.jq = std::max(1, std::min(q2max, (int)(ybudget / (sizeof(float2) * D * D * X))));
+    p.njg = (q2max + p.jq - 1) / p.jq;
+    const size_t slot = sizeof(float2) * (size_t)D * p.jq * X;
+    p.nb = (int)std::max<size_t>(1, std::min<size_t>(32, ubudget / slot));
+    p.smem = sf_smem_layout(D, X, p.jq, p.nb, N1, N2, N3, p.njg).bytes;
+    return p;
 }
 
 template <int W, int NM, int RC, bool GAM>
-void launch_sf_t(epwi_ctx *c, const SfArgs &a, int nitems) {
-    const size_t sm = sf_smem(2 * RC + 1, NM * W, a.nq2max, a.g.n1, a.g.n2, a.g.n3);
+void launch_sf_t(epwi_ctx *c, const SfArgs &a, int nitems, size_t sm) {
     EPWI_REQUIRE(sm <= 200 * 1024, EPWI_EUNSUPPORTED,
                  "fp32 mode: the plane-block tables of this grid do not fit in shared memory");
     EPWI_CUDA(cudaFuncSetAttribute(k_scatter_sf<W, NM, RC, GAM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
@@ -381,25 +534,63 @@ void launch_sf_t(epwi_ctx *c, const SfArgs &a, int nitems) {
 }
 
 template <int W, int NM, int RC>
-void launch_sf(epwi_ctx *c, const SfArgs &a, int nitems) {
-    if (a.gam) launch_sf_t<W, NM, RC, true>(c, a, nitems);
-    else launch_sf_t<W, NM, RC, false>(c, a, nitems);
+void launch_sf(epwi_ctx *c, const SfArgs &a, int nitems, size_t sm) {
+    if (a.gam) launch_sf_t<W, NM, RC, true>(c, a, nitems, sm);
+    else launch_sf_t<W, NM, RC, false>(c, a, nitems, sm);
+}
+
+bool sf_shape_built(int W, int NM, int r) {
+    return (W == 4 && NM == 3 && r >= 1 && r <= 3) || (W == 1 && NM == 3 && r >= 1 && r <= 2) ||
+           (W == 8 && NM == 6 && r >= 1 && r <= 3);
 }
 
 }  // namespace
 
-size_t sf_state_bytes(const epwi_ctx *c) { return sizeof(float2) * (size_t)c->nRp * c->nm * c->nw; }
-
-void sf_check(const epwi_ctx *c) {
-    const int W = c->nw, NM = c->nm, r = c->rp_cube_r;
-    EPWI_REQUIRE(c->nk * std::max(W * W, NM * NM) < (int64_t(1) << 31), EPWI_EUNSUPPORTED,
-                 "fp32 mode: grid too large for its 32-bit table offsets");
-    EPWI_REQUIRE(r >= 0, EPWI_EUNSUPPORTED, "fp32 mode needs R_p to be the full cube [-r, r]^3");
-    EPWI_REQUIRE((W == 4 && NM == 3 && (r == 1 || r == 2)) || (W == 1 && NM == 3 && r == 1),
-                 EPWI_EUNSUPPORTED, "fp32 mode built for (nw, modes, R_p half-width) in {(4,3,1), (4,3,2), (1,3,1)}");
+size_t sf_state_bytes(const epwi_ctx *c) {
+    const size_t Dc = 2 * (size_t)c->sf_r + 1;
+    return sizeof(float2) * Dc * Dc * Dc * c->nm * c->nw;
 }
 
-void sf_restage(epwi_ctx *c, const RestageArgs &ra) {
+void sf_check(const epwi_ctx *c) {
+    const int W = c->nw, NM = c->nm, r = c->sf_r;
+    EPWI_REQUIRE(c->nk * std::max(W * W, NM * NM) < (int64_t(1) << 31), EPWI_EUNSUPPORTED,
+                 "fp32 mode: grid too large for its 32-bit table offsets");
+    EPWI_REQUIRE(sf_shape_built(W, NM, r), EPWI_EUNSUPPORTED,
+                 "fp32 mode built for (nw, modes) in {(4,3), (8,6)} with R_p within |n| <= 3, and (1,3) "
+                 "within |n| <= 2");
+    EPWI_REQUIRE(c->ng[0] * 2 <= 4096 && c->ng[2] <= 0xffff, EPWI_EUNSUPPORTED, "fp32 mode: grid too large");
+}
+
+// Builds what the fp32 mode reads besides the eigen-tables: g' (cube embedding and the +-R
+// recombination of the R_p axes, once per system) and the transposed FP32 V (per eigs call).
+void sf_prepare(epwi_ctx *c) {
+    const int W = c->nw, NM = c->nm;
+    const int Dc = 2 * c->sf_r + 1;
+    if (!c->sf_g_ready) {
+        const int rowlen = NM * W * W;
+        const int64_t n = (int64_t)c->nRe * Dc * Dc * Dc * rowlen;
+        DevBuf cube;
+        upload_ints(c, cube, c->h_rp_cube);
+        c->gsf32.ensure(sizeof(float2) * n);
+        k_sf_transform<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(
+            n, c->nRp, Dc, c->sf_r, rowlen, cube.as<int>(), c->keep_g64 ? c->gw64.as<double2>() : nullptr,
+            c->gw32.as<float2>(), c->gsf32.as<float2>());
+        EPWI_CHECK_LAUNCH();
+        EPWI_CUDA(cudaStreamSynchronize(c->stream));   // cube is freed on return
+        c->sf_g_ready = true;
+    }
+    const int64_t nv = c->nk * W * W;
+    c->sf_Vt32.ensure(sizeof(float2) * nv);
+    k_transpose_v<<<(unsigned)((nv + 255) / 256), 256, 0, c->stream>>>(c->nk, W, c->V32.as<float2>(),
+                                                                      c->sf_Vt32.as<float2>());
+    EPWI_CHECK_LAUNCH();
+}
+
+void sf_restage(epwi_ctx *c, const RestageArgs &ra_in) {
+    RestageArgs ra = ra_in;
+    const int Dc = 2 * c->sf_r + 1;
+    ra.gw32 = c->gsf32.as<float2>();
+    ra.nrow = Dc * Dc * Dc * c->nm * c->nw;
     const int W = ra.W;
     float2 *out = static_cast<float2 *>(ra.ghat_raw);
     auto go = [&](auto kern, int KG) {
@@ -410,6 +601,7 @@ void sf_restage(epwi_ctx *c, const RestageArgs &ra) {
         EPWI_CHECK_LAUNCH();
     };
     if (W == 4) go(k_restage_f32<4, 8>, 8);
+    else if (W == 8) go(k_restage_f32<8, 4>, 4);
     else if (W == 1) go(k_restage_f32<1, 8>, 8);
     else go(k_restage_f32<0, 1>, 1);
 }
@@ -417,16 +609,21 @@ void sf_restage(epwi_ctx *c, const RestageArgs &ra) {
 // Rates of the chunk's states: one CTA per (k-point, band), written straight into inv_tau.
 void sf_scatter(epwi_ctx *c, const ScatterArgs &sa, int64_t nkp, const int64_t *kp_pairs_local, int64_t p_off,
                 const std::vector<int64_t> &h_kp_state_chunk) {
-    const int W = c->nw, NM = c->nm, r = c->rp_cube_r;
+    const int W = c->nw, NM = c->nm, r = c->sf_r;
+    const int D = 2 * r + 1, X = NM * W;
     SfArgs a;
     a.g = sa.g;
-    a.nplane = (int64_t)sa.g.n2 * sa.g.n3;
+    a.nplane = sa.g.n2 * sa.g.n3;
     int q2max = 1;
     for (int64_t pb = 0; pb * kSieveBlock < a.nplane; ++pb) {
         const int64_t c0 = pb * kSieveBlock, c1 = std::min<int64_t>(a.nplane, c0 + kSieveBlock) - 1;
         q2max = std::max<int>(q2max, (int)(c1 / sa.g.n3 - c0 / sa.g.n3 + 1));
     }
-    a.nq2max = q2max;
+    const SfPlan plan = sf_plan(D, X, q2max, sa.g.n1, sa.g.n2, sa.g.n3);
+    EPWI_REQUIRE((int64_t)sa.g.n1 * plan.njg <= 8192, EPWI_EUNSUPPORTED, "fp32 mode: too many runs per plane block");
+    a.jq = plan.jq;
+    a.njg = plan.njg;
+    a.nb = plan.nb;
     a.ph32 = sa.ph32;
     a.ghat = static_cast<const float2 *>(sa.ghat_raw);
     a.kpts = sa.kpts;
@@ -437,7 +634,7 @@ void sf_scatter(epwi_ctx *c, const ScatterArgs &sa, int64_t nkp, const int64_t *
     a.kp_pairs = kp_pairs_local;
     a.p_off = p_off;
     a.pairs = sa.pairs;
-    a.V32 = sa.V32;
+    a.Vt32 = c->sf_Vt32.as<float2>();
     a.u32 = sa.u32;
     a.erel = c->tc_erel.as<float>();
     a.f32 = c->tc_f32.as<float>();
@@ -459,9 +656,15 @@ void sf_scatter(epwi_ctx *c, const ScatterArgs &sa, int64_t nkp, const int64_t *
     a.gam = sa.gam32;
     a.goff = sa.goff;
     const int ni = (int)items.size();
-    if (W == 4 && NM == 3 && r == 2) launch_sf<4, 3, 2>(c, a, ni);
-    else if (W == 4 && NM == 3 && r == 1) launch_sf<4, 3, 1>(c, a, ni);
-    else if (W == 1 && NM == 3 && r == 1) launch_sf<1, 3, 1>(c, a, ni);
+    const size_t sm = plan.smem;
+    if (W == 4 && NM == 3 && r == 1) launch_sf<4, 3, 1>(c, a, ni, sm);
+    else if (W == 4 && NM == 3 && r == 2) launch_sf<4, 3, 2>(c, a, ni, sm);
+    else if (W == 4 && NM == 3 && r == 3) launch_sf<4, 3, 3>(c, a, ni, sm);
+    else if (W == 1 && NM == 3 && r == 1) launch_sf<1, 3, 1>(c, a, ni, sm);
+    else if (W == 1 && NM == 3 && r == 2) launch_sf<1, 3, 2>(c, a, ni, sm);
+    else if (W == 8 && NM == 6 && r == 1) launch_sf<8, 6, 1>(c, a, ni, sm);
+    else if (W == 8 && NM == 6 && r == 2) launch_sf<8, 6, 2>(c, a, ni, sm);
+    else if (W == 8 && NM == 6 && r == 3) launch_sf<8, 6, 3>(c, a, ni, sm);
     else sf_check(c);
     // the host vector of items must outlive the copy
     EPWI_CUDA(cudaStreamSynchronize(c->stream));

@@ -166,6 +166,27 @@ def r_cube(r: int, ws_weights: bool):
     return n.astype(np.int32), w
 
 
+def ws_rset(lat, nsc: int, tol: float = 1e-6):
+    """Wigner-Seitz set of the nsc x nsc x nsc supercell of ``lat``: the lattice vectors R (in
+    lattice coordinates n, R = n @ lat) that are no farther from the origin than from any
+    supercell image nsc T @ lat, with weight 1 / (number of images at that same distance),
+    so that sum(w) = nsc^3.  Unlike ``r_cube`` this set is not a cube in lattice coordinates
+    (for fcc and nsc = 4: 93 vectors up to |n_a| = 3).  Sorted by n (n3 fastest); closed
+    under R -> -R."""
+    lat = np.asarray(lat, float)
+    ax = np.arange(-2 * nsc, 2 * nsc + 1)
+    n = np.stack(np.meshgrid(ax, ax, ax, indexing="ij"), axis=-1).reshape(-1, 3)
+    tr = np.stack(np.meshgrid(*(np.arange(-2, 3),) * 3, indexing="ij"), axis=-1).reshape(-1, 3)
+    R = n @ lat
+    d0 = np.linalg.norm(R, axis=1)
+    dT = np.linalg.norm(R[:, None, :] + ((nsc * tr) @ lat)[None, :, :], axis=-1)
+    eps = tol * nsc * np.abs(lat).max()
+    inside = d0 <= dT.min(axis=1) + eps
+    deg = (np.abs(dT - d0[:, None]) <= eps).sum(axis=1)
+    sel = np.nonzero(inside)[0]
+    return n[sel].astype(np.int32), 1.0 / deg[sel]
+
+
 def _minus_index(R: np.ndarray) -> np.ndarray:
     lut = {tuple(v): i for i, v in enumerate(R.tolist())}
     return np.array([lut[tuple((-v).tolist())] for v in R])
@@ -318,9 +339,9 @@ def _semiconductor(rng: SplitMix64, lat, R, w, nv, nc, gap_ev, sigma_b=0.5, t_s=
 
 
 def make_system(name: str, lat, tau, mass, nw, r, ws, seed, omega_max_ev,
-                n_valence=0, gap_ev=1.1) -> System:
+                n_valence=0, gap_ev=1.1, rset=None) -> System:
     rng = SplitMix64(seed)
-    R, w = r_cube(r, ws)
+    R, w = r_cube(r, ws) if rset is None else rset
     mass = np.asarray(mass, float) * np.ones(len(tau))
     H, i0 = _hamiltonian(rng, lat, R, nw)
     if n_valence:
@@ -342,6 +363,13 @@ def al_like_system(seed: int = 2) -> System:
     """fcc Al-like metal: nw = 4, 3 modes, 5^3 Wigner-Seitz-weighted R-sets."""
     lat, tau = fcc_cell(4.05)
     return make_system("al_like", lat, tau, 27.0, 4, 2, True, seed, 0.040)
+
+
+def al_like_ws_system(seed: int = 2, nsc: int = 4) -> System:
+    """fcc Al-like metal on genuine Wigner-Seitz R-sets: nw = 4, 3 modes, Re = Rp = the WS set
+    of the nsc^3 supercell (93 vectors for nsc = 4, fractional weights summing to 64)."""
+    lat, tau = fcc_cell(4.05)
+    return make_system("al_like_ws", lat, tau, 27.0, 4, 0, False, seed, 0.040, rset=ws_rset(lat, nsc))
 
 
 def si_like_system(seed: int = 3) -> System:

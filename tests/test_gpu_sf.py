@@ -36,6 +36,9 @@ def _rates(system, grid, mu, eta, lo, hi, precision="fp32", chunk=0):
     ("al_like", (10, 10, 10), 0.3, 0.05),
     ("al_like", (12, 7, 9), 0.3, 0.05),
     ("al_like", (6, 18, 17), 0.3, 0.04),
+    ("al_like_ws", (10, 10, 10), 0.3, 0.05),     # genuine Wigner-Seitz R-set, not a cube
+    ("al_like_ws", (9, 20, 15), 0.3, 0.04),      # ... two plane blocks, ragged
+    ("si_like", (6, 5, 4), None, 0.05),          # W = 8, 6 modes, 7^3: q2 groups
 ])
 def test_fp32_matches_the_oracle(name, grid, half, eta):
     s = getattr(synth, f"{name}_system")()
@@ -94,10 +97,28 @@ def test_al_like_48_sampled_fp32():
     ctx.close()
 
 
+def test_si_like_mobility_fp32():
+    """The Si-like semiconductor (W = 8 with 4 valence and 4 conduction Wannier functions,
+    6 modes, 7^3 R-sets) at 12^3: mu from n_c = 1e18 cm^-3, window [CBM, CBM + 0.25 eV],
+    eta = 10 meV; 1/tau per degenerate group and the mobility tensor against the oracle."""
+    s = synth.si_like_system()
+    N, eta, n_c = 12, 0.01, 1e18
+    gr = O.Grids(s, (N, N, N))
+    vbm, cbm = gr.band_edges(4)
+    mu = O.find_mu(gr.eps[:, 4:], gr.nk, s.volume, n_c, T)
+    out = gpu_run(s, (N, N, N), T, mu, eta, cbm, cbm + 0.25, precision="fp32")
+    ora = oracle_run(gr, T, mu, eta, cbm, cbm + 0.25)
+    assert out["n_pairs"] == ora["n_pairs"]
+    err, n = compare_rates(out, ora, gr.eps, TOL)
+    assert n > 0 and err <= TOL, err
+    assert rel_frob(out["ctx"].mobility(n_c), O.mobility(ora["sigma"], n_c)) <= SIGMA_TOL
+    out["ctx"].close()
+
+
 def test_fp32_refuses_what_it_does_not_serve():
     ctx = epwi.Context(precision="fp32", device=0)
-    ctx.setup(synth.si_like_system())
-    ctx.eigs(4)
+    ctx.setup(synth.batch_system(13)[0])          # nw = 24: no fp32 kernel of that shape
+    ctx.eigs((3, 3, 4))
     with pytest.raises(epwi.EpwiError):
         ctx.scatter_rates(T, 0.0, 0.05, -1e9, 1e9)
     ctx.close()

@@ -1,7 +1,12 @@
 """The seeded input generator: the chunked, threaded draw of large complex-normal arrays gives
-exactly the values of the sequential SplitMix64 + Box-Muller stream."""
-import numpy as np
+exactly the values of the sequential SplitMix64 + Box-Muller stream, and the Wigner-Seitz
+R-sets are complete sets of supercell representatives."""
+import itertools
 
+import numpy as np
+import pytest
+
+from paper_2306_16493_gb300 import synth
 from paper_2306_16493_gb300.synth import SplitMix64
 
 
@@ -23,3 +28,27 @@ def test_splitmix64_reference_values():
     r = SplitMix64(0)
     assert [int(x) for x in r.next_u64(3)] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4,
                                                0x06C45D188009454F]
+
+
+@pytest.mark.parametrize("cell,nsc", [(synth.fcc_cell(4.05)[0], 2), (synth.fcc_cell(4.05)[0], 4),
+                                      (synth.diamond_cell(5.43)[0], 3), (np.diag([3.0, 3.5, 4.2]), 3)])
+def test_wigner_seitz_set_is_a_weighted_set_of_supercell_representatives(cell, nsc):
+    """Every residue class of Z^3 mod nsc carries total weight 1 (boundary vectors share it
+    with their equivalent images), so sum(w) = nsc^3 and sum_R w e^{2 pi i m.n / nsc} =
+    nsc^3 delta_{m = 0 mod nsc}; the set is closed under R -> -R with equal weights, and every
+    member is no farther from the origin than any of its supercell images."""
+    n, w = synth.ws_rset(cell, nsc)
+    assert w.sum() == pytest.approx(nsc ** 3, abs=1e-12)
+    cls = {}
+    for v, x in zip(map(tuple, np.mod(n, nsc)), w):
+        cls[v] = cls.get(v, 0.0) + x
+    assert len(cls) == nsc ** 3 and all(abs(x - 1.0) < 1e-12 for x in cls.values())
+    lut = {tuple(v): x for v, x in zip(n.tolist(), w)}
+    assert all(lut.get(tuple((-np.array(v)).tolist())) == x for v, x in lut.items())
+    for m in itertools.product(range(nsc), repeat=3):
+        f = (w * np.exp(2j * np.pi * (n @ np.array(m)) / nsc)).sum()
+        assert abs(f - (nsc ** 3 if m == (0, 0, 0) else 0.0)) < 1e-9
+    R = n @ cell
+    for t in itertools.product((-1, 0, 1), repeat=3):
+        img = R + nsc * (np.array(t) @ cell)
+        assert np.all(np.linalg.norm(R, axis=1) <= np.linalg.norm(img, axis=1) + 1e-9)
