@@ -142,12 +142,31 @@ __global__ void k_transpose_v(int64_t nk, int W, const float2 *__restrict__ V, f
     Vt[idx] = V[k * W * W + i * W + m];
 }
 
+// Division by a divisor fixed at launch (x < 2^31): q = (umulhi(x, m) + x) >> l with
+// l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1 (Granlund & Montgomery, PLDI 1994).
+struct FDiv {
+    uint32_t d, m, l;
+};
+FDiv make_fdiv(uint32_t d) {
+    FDiv f;
+    f.d = d;
+    uint32_t l = 0;
+    while ((uint64_t(1) << l) < d) ++l;
+    f.l = l;
+    f.m = (uint32_t)(((uint64_t(1) << 32) * ((uint64_t(1) << l) - d)) / d + 1);
+    return f;
+}
+__device__ __forceinline__ int fdiv(int x, const FDiv &f) {
+    return (int)((__umulhi((uint32_t)x, f.m) + (uint32_t)x) >> f.l);
+}
+
 struct SfArgs {
     GridInfo g;
     int nplane;                     // N2 N3
-    int jq;                         // q2 values per group (Y and U hold one group)
+    FDiv fplane, fjq;               // division by N2 N3 and by jq
+    int jq;                         // q2 values per group (Y and the U buffers hold one group)
     int njg;                        // groups per plane block (over the largest block)
-    int nb;                         // runs per U batch
+    int pbmax;                      // plane blocks
     const float2 *ph32;             // e^{2 pi i m / L}
     const float2 *ghat;             // [state - s_base][D^3 forms][N_m][W]
     const int *kpts, *win_lo, *win_n;
@@ -157,7 +176,7 @@ struct SfArgs {
     int64_t p_off;
     const int *pairs;               // chunk pair list: q index
     const float2 *Vt32, *u32;
-    const float *erel, *f32, *n32, *hw32;
+    const float *erel, *f32, *n32, *hw32, *hwmax32;
     float ceta32, inv_eta32;
     double pref;                    // 2 pi / (hbar N_q sqrt(pi) eta)
     double *inv_tau;
@@ -181,12 +200,12 @@ __device__ __forceinline__ int64_t lower_bound(int64_t lo, int64_t hi, int64_t k
 struct SfSmem {
     size_t y, u, cs, ints, bytes;
 };
-__host__ __device__ inline SfSmem sf_smem_layout(int D, int X, int jq, int nb, int N1, int N2, int N3, int njg) {
+__host__ __device__ inline SfSmem sf_smem_layout(int D, int X, int jq, int N1, int N2, int N3, int njg, int pbmax) {
     SfSmem s;
-    s.y = (size_t)D * D * jq * X;                          // float2
-    s.u = (size_t)nb * D * jq * X;                         // float2
+    s.y = (size_t)D * D * jq * X;                          // float2: Y of one q2 group
+    s.u = (size_t)kSfWarps * D * jq * X;                   // float2: U of one run per warp
     s.cs = (size_t)(N1 + N2 + N3) * (D - 1);               // float: (cos, sin) per R >= 1
-    s.ints = (size_t)kSieveBlock + 2 * (size_t)N1 * njg + (size_t)N1 + (size_t)nb + 2 + 4;
+    s.ints = (size_t)kSieveBlock + 2 * (size_t)N1 * njg + (size_t)N1 + (size_t)pbmax + 1 + 4;
     s.bytes = sizeof(float2) * (s.y + s.u) + sizeof(float) * s.cs + sizeof(int) * s.ints;
     return s;
 }
@@ -200,21 +219,21 @@ __global__ void __launch_bounds__(kSfThreads, (W <= 4 ? 3 : 2)) k_scatter_sf(SfA
     constexpr int kMuUnroll = NM <= 3 ? NM : 1;  // wide systems: one mode row at a time (registers)
     extern __shared__ __align__(16) float2 sm[];
     const int N1 = a.g.n1, N2 = a.g.n2, N3 = a.g.n3, L = a.g.L;
-    const int JQ = a.jq, NJG = a.njg, NB = a.nb;
-    const SfSmem lay = sf_smem_layout(D, X, JQ, NB, N1, N2, N3, NJG);
+    const int JQ = a.jq, NJG = a.njg;
+    const SfSmem lay = sf_smem_layout(D, X, JQ, N1, N2, N3, NJG, a.pbmax);
     float2 *Y = sm;                              // [D f1][D f3][JQ][X]
-    float2 *U = Y + lay.y;                       // [NB][D f3][JQ][X]
-    float *CS = reinterpret_cast<float *>(U + lay.u);   // [N1 + N2 + N3][NF]: cos, sin of theta R
+    float *CS = reinterpret_cast<float *>(Y + lay.y + lay.u);   // [N1 + N2 + N3][NF]: cos, sin of theta R
     int *cq = reinterpret_cast<int *>(CS + lay.cs);     // [256]: (j << 16) | q3 of combination t
     int *ss = cq + kSieveBlock;                  // [N1 NJG]: segment start (relative), -1 if none
     int *se = ss + N1 * NJG;                     // [N1 NJG]: segment end
-    int *gl = se + N1 * NJG;                     // [N1]: segments (keys) of the current group
-    int *pf = gl + N1;                           // [NB + 1]: pair prefix of the current batch
-    int *nglist = pf + NB + 1;                   // [1]
+    int *gl = se + N1 * NJG;                     // [N1]: runs (q1) of the current group
+    int *pbs = gl + N1;                          // [pbmax + 1]: first pair of each plane block
+    int *nglist = pbs + a.pbmax + 1;             // [1]
     __shared__ double wsum[kSfWarps];
     const int2 item = a.items[blockIdx.x];
     const int kp = item.x, n = item.y;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    float2 *Uw = Y + lay.y + (size_t)wid * D * JQ * X;   // this warp's run: [D f3][JQ][X]
     const int ik = a.kpts[kp];
     const int lo = a.win_lo[ik];
     const int64_t s = a.kp_state[kp] + n;        // global state
@@ -235,19 +254,24 @@ __global__ void __launch_bounds__(kSfThreads, (W <= 4 ? 3 : 2)) k_scatter_sf(SfA
     const int nplane = a.nplane;
     const int pb_n = (nplane + kSieveBlock - 1) / kSieveBlock;
     const int64_t P0 = a.kp_pairs[kp] - a.p_off, P1 = a.kp_pairs[kp + 1] - a.p_off;
-    const int *pl = a.pairs;
-    auto pbof = [&](int64_t p) -> int64_t { return (int64_t)((pl[p] % nplane) / kSieveBlock); };
+    const int *pl = a.pairs + P0;                // this k-point's pairs, relative index
+    const int np = (int)(P1 - P0);
+    // first pair of every plane block (the list is ordered by plane block)
+    for (int pb = tid; pb <= pb_n; pb += kSfThreads)
+        pbs[pb] = (int)lower_bound(0, np, pb, [&](int64_t p) {
+            const int q = pl[p];
+            return (int64_t)((q - fdiv(q, a.fplane) * nplane) / kSieveBlock);
+        });
     int k1, k2, k3;
     grid_coords(a.g, ik, k1, k2, k3);
     const float en = a.erel[(int64_t)ik * W + lo + n];
     const float ceta = a.ceta32, ieta = a.inv_eta32;
-    double acc = 0;                              // this thread's batch sums
+    double acc = 0;                              // this warp's run sums (lane 0)
     __syncthreads();
-    int64_t seg0 = P0;
-    for (int pb = 0; pb < pb_n && seg0 < P1; ++pb) {
-        // the plane block's pairs [seg0, seg1)
-        const int64_t seg1 = lower_bound(seg0, P1, (int64_t)pb + 1, pbof);
-        if (seg1 == seg0) continue;
+    for (int pb = 0; pb < pb_n; ++pb) {
+        const int seg0 = pbs[pb], nseg = pbs[pb + 1] - seg0;   // the plane block's pairs
+        if (nseg == 0) continue;
+        const int *pp = pl + seg0;
         const int c_lo = pb * kSieveBlock, c_hi = min(nplane, c_lo + kSieveBlock) - 1;
         const int q2lo = c_lo / N3, nq2 = c_hi / N3 - q2lo + 1;
         const int njg = (nq2 + JQ - 1) / JQ;
@@ -257,18 +281,26 @@ __global__ void __launch_bounds__(kSfThreads, (W <= 4 ? 3 : 2)) k_scatter_sf(SfA
         }
         for (int t = tid; t < N1 * NJG; t += kSfThreads) ss[t] = -1;
         __syncthreads();
-        // segments: the block's pairs are ordered by q1, then by combination (so by q2 group)
-        const int nseg = (int)(seg1 - seg0);
+        // segments: the block's pairs are ordered by q1, then by combination (so by q2 group);
+        // key = q1 NJG + group, neighbours' keys by shuffle
         auto keyof = [&](int t) -> int {
-            const int q = pl[seg0 + t];
-            const int q1 = q / nplane;
+            const int q = pp[t];
+            const int q1 = fdiv(q, a.fplane);
             const int j = cq[q - q1 * nplane - c_lo] >> 16;
-            return q1 * NJG + j / JQ;
+            return q1 * NJG + fdiv(j, a.fjq);
         };
-        for (int t = tid; t < nseg; t += kSfThreads) {
-            const int key = keyof(t);
-            if (t == 0 || keyof(t - 1) != key) ss[key] = t;
-            if (t == nseg - 1 || keyof(t + 1) != key) se[key] = t + 1;
+        for (int t0 = wid * 32; t0 < nseg; t0 += kSfThreads) {
+            const int t = t0 + lane;
+            const bool on = t < nseg;
+            const int key = on ? keyof(t) : -1;
+            int kprev = __shfl_up_sync(0xffffffffu, key, 1);
+            int knext = __shfl_down_sync(0xffffffffu, key, 1);
+            if (lane == 0 && t > 0 && on) kprev = keyof(t - 1);
+            if (lane == 31 && t + 1 < nseg) knext = keyof(t + 1);
+            if (on) {
+                if (t == 0 || kprev != key) ss[key] = t;
+                if (t == nseg - 1 || knext != key) se[key] = t + 1;
+            }
         }
         __syncthreads();
         for (int jg = 0; jg < njg; ++jg) {
@@ -286,112 +318,122 @@ __global__ void __launch_bounds__(kSfThreads, (W <= 4 ? 3 : 2)) k_scatter_sf(SfA
                 if (lane == 0) *nglist = cnt;
             }
             // Y of this group's q2 values (all threads), read from ghat' (L1 / L2)
-            for (int e = tid; e < D * D * jn * X; e += kSfThreads) {
-                const int col = e % X, t = e / X;
-                const int jj = t % jn, r13 = t / jn;
-                const int f3 = r13 % D, f1 = r13 / D;
-                const float *c2 = CS2 + (q2lo + j0 + jj) * NF;
-                const float2 *src = gs + ((f1 * D) * D + f3) * X + col;
-                float2 v = __ldg(src);                       // form f2 = 0
+            {
+                const int per = jn * X;                 // (jj, col) of one (f1, f3)
+                for (int e = tid; e < D * D * per; e += kSfThreads) {
+                    const int r13 = e / per, e2 = e - r13 * per;
+                    const int jj = e2 / X, col = e2 - jj * X;
+                    const int f3 = r13 % D, f1 = r13 / D;
+                    const float *c2 = CS2 + (q2lo + j0 + jj) * NF;
+                    const float2 *src = gs + ((f1 * D) * D + f3) * X + col;
+                    float2 v = __ldg(src);                   // form f2 = 0
 #pragma unroll
-                for (int f2 = 1; f2 < D; ++f2) {
-                    const float c = c2[f2 - 1];
-                    const float2 w = __ldg(src + f2 * D * X);
-                    v.x = fmaf(c, w.x, v.x);
-                    v.y = fmaf(c, w.y, v.y);
-                }
-                Y[((f1 * D + f3) * JQ + jj) * X + col] = v;
-            }
-            __syncthreads();
-            const int ng = *nglist;
-            for (int b0 = 0; b0 < ng; b0 += NB) {
-                const int nbt = min(NB, ng - b0);
-                // U of the batch's runs
-                for (int e = tid; e < nbt * D * jn * X; e += kSfThreads) {
-                    const int col = e % X, t = e / X;
-                    const int jj = t % jn, t2 = t / jn;
-                    const int f3 = t2 % D, b = t2 / D;
-                    const float *c1 = CS1 + gl[b0 + b] * NF;
-                    const float2 *src = Y + (f3 * JQ + jj) * X + col;
-                    float2 v = src[0];                       // form f1 = 0
-#pragma unroll
-                    for (int f1 = 1; f1 < D; ++f1) {
-                        const float c = c1[f1 - 1];
-                        const float2 w = src[f1 * D * JQ * X];
+                    for (int f2 = 1; f2 < D; ++f2) {
+                        const float c = c2[f2 - 1];
+                        const float2 w = __ldg(src + f2 * D * X);
                         v.x = fmaf(c, w.x, v.x);
                         v.y = fmaf(c, w.y, v.y);
                     }
-                    U[((b * D + f3) * JQ + jj) * X + col] = v;
+                    Y[(r13 * JQ + jj) * X + col] = v;
                 }
-                if (wid == 0) {                              // pair prefix of the batch
-                    int len = 0;
-                    if (lane < nbt) {
-                        const int key = gl[b0 + lane] * NJG + jg;
-                        len = se[key] - ss[key];
-                    }
-                    int inc = len;
+            }
+            __syncthreads();
+            const int ng = *nglist;
+            // runs round-robin over the warps (a fixed assignment keeps the sums deterministic)
+            for (int r = wid; r < ng; r += kSfWarps) {
+                const int q1 = gl[r];
+                const int t0 = ss[q1 * NJG + jg], t1 = se[q1 * NJG + jg];
+                // U of the run: for each form f3, the contiguous (jj, col) row of Y
+                {
+                    float c1[NF];
 #pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int t = __shfl_up_sync(0xffffffffu, inc, o);
-                        if (lane >= o) inc += t;
+                    for (int f = 0; f < NF; ++f) c1[f] = CS1[q1 * NF + f];
+                    if constexpr (X % 2 == 0) {
+                        const int per4 = jn * X / 2;
+#pragma unroll
+                        for (int f3 = 0; f3 < D; ++f3) {
+                            const float4 *src = reinterpret_cast<const float4 *>(Y + (size_t)f3 * JQ * X);
+                            float4 *dst = reinterpret_cast<float4 *>(Uw + (size_t)f3 * JQ * X);
+                            for (int e = lane; e < per4; e += 32) {
+                                float4 v = src[e];
+#pragma unroll
+                                for (int f1 = 1; f1 < D; ++f1) {
+                                    const float c = c1[f1 - 1];
+                                    const float4 w = src[e + f1 * D * JQ * X / 2];
+                                    v.x = fmaf(c, w.x, v.x);
+                                    v.y = fmaf(c, w.y, v.y);
+                                    v.z = fmaf(c, w.z, v.z);
+                                    v.w = fmaf(c, w.w, v.w);
+                                }
+                                dst[e] = v;
+                            }
+                        }
+                    } else {
+                        const int per = jn * X;
+#pragma unroll
+                        for (int f3 = 0; f3 < D; ++f3) {
+                            const float2 *src = Y + (size_t)f3 * JQ * X;
+                            float2 *dst = Uw + (size_t)f3 * JQ * X;
+                            for (int e = lane; e < per; e += 32) {
+                                float2 v = src[e];
+#pragma unroll
+                                for (int f1 = 1; f1 < D; ++f1) {
+                                    const float c = c1[f1 - 1];
+                                    const float2 w = src[e + f1 * D * JQ * X];
+                                    v.x = fmaf(c, w.x, v.x);
+                                    v.y = fmaf(c, w.y, v.y);
+                                }
+                                dst[e] = v;
+                            }
+                        }
                     }
-                    if (lane < nbt) pf[lane + 1] = inc;
-                    if (lane == 0) pf[0] = 0;
                 }
-                __syncthreads();
+                __syncwarp();
                 float rate = 0.f;
-                const int npb = pf[nbt];
-                for (int i = tid; i < npb; i += kSfThreads) {
-                    int b = 0;                               // slot: pf[b] <= i < pf[b + 1]
-                    while (pf[b + 1] <= i) ++b;
-                    const int q1 = gl[b0 + b];
-                    const int t = ss[q1 * NJG + jg] + (i - pf[b]);
-                    const int64_t p = seg0 + t;
-                    const int q = pl[p];
-                    const int cl = q - (q1 * nplane + c_lo);
-                    const int jq = cq[cl];
+                int b1 = k1 + q1;
+                if (b1 >= N1) b1 -= N1;
+                const int qbase = q1 * nplane + c_lo;
+                for (int t = t0 + lane; t < t1; t += 32) {
+                    const int q = pp[t];
+                    const int jq = cq[q - qbase];
                     const int j = jq >> 16, q3 = jq & 0xffff;
-                    const float2 *Ub = U + ((b * D) * JQ + (j - j0)) * X;   // form f3 at + f3 JQ X
-                    int b1 = k1 + q1, b2 = k2 + q2lo + j, b3 = k3 + q3;
-                    if (b1 >= N1) b1 -= N1;
+                    int b2 = k2 + q2lo + j, b3 = k3 + q3;
                     if (b2 >= N2) b2 -= N2;
                     if (b3 >= N3) b3 -= N3;
                     const int ikq = (b1 * N2 + b2) * N3 + b3;   // nk W^2 < 2^31 (checked on the host)
-                    float wq[NM];
-#pragma unroll
-                    for (int nu = 0; nu < NM; ++nu) wq[nu] = __ldg(a.hw32 + q * NM + nu);
+                    // final bands within the largest kept mode energy + c eta of e_nk (a superset
+                    // of the bands with a mode inside c eta of either shell; the others add zero)
+                    const float lim = __ldg(a.hwmax32 + q) + ceta + 1e-5f;
                     float emr[W];
-                    if constexpr (W == 4) {
-                        const float4 e4 = __ldg(reinterpret_cast<const float4 *>(a.erel + ikq * W));
-                        emr[0] = e4.x; emr[1] = e4.y; emr[2] = e4.z; emr[3] = e4.w;
+                    if constexpr (W % 4 == 0) {
+#pragma unroll
+                        for (int m4 = 0; m4 < W / 4; ++m4) {
+                            const float4 e4 = __ldg(reinterpret_cast<const float4 *>(a.erel + ikq * W) + m4);
+                            emr[4 * m4] = e4.x; emr[4 * m4 + 1] = e4.y; emr[4 * m4 + 2] = e4.z; emr[4 * m4 + 3] = e4.w;
+                        }
                     } else {
 #pragma unroll
                         for (int m = 0; m < W; ++m) emr[m] = __ldg(a.erel + ikq * W + m);
                     }
-                    // final bands with a mode inside c eta of either shell (others add zero)
                     unsigned mask = 0;
 #pragma unroll
-                    for (int m = 0; m < W; ++m) {
-                        bool any = false;
-#pragma unroll
-                        for (int nu = 0; nu < NM; ++nu) {
-                            const float w = wq[nu];
-                            any |= w >= 0.f && (fabsf((en + w) - emr[m]) <= ceta || fabsf((en - w) - emr[m]) <= ceta);
-                        }
-                        if (any) mask |= 1u << m;
-                    }
+                    for (int m = 0; m < W; ++m) mask |= (fabsf(en - emr[m]) <= lim ? 1u : 0u) << m;
                     if (!mask) continue;
-                    float c3[NF], nq[NM];
+                    const float2 *Ub = Uw + (j - j0) * X;      // form f3 at + f3 JQ X
+                    float c3[NF], wq[NM], nq[NM];
 #pragma unroll
                     for (int f = 0; f < NF; ++f) c3[f] = CS3[q3 * NF + f];
 #pragma unroll
-                    for (int nu = 0; nu < NM; ++nu) nq[nu] = __ldg(a.n32 + q * NM + nu);
+                    for (int nu = 0; nu < NM; ++nu) {
+                        wq[nu] = __ldg(a.hw32 + q * NM + nu);
+                        nq[nu] = __ldg(a.n32 + q * NM + nu);
+                    }
                     int lokq = 0, nwkq = 0;
                     int64_t grow = 0;                        // this band's row of the pair's Gamma block
                     if constexpr (GAM) {
                         lokq = __ldg(a.win_lo + ikq);
                         nwkq = __ldg(a.win_n + ikq);
-                        grow = a.goff[p] + (int64_t)n * nwkq - lokq;
+                        grow = a.goff[P0 + seg0 + t] + (int64_t)n * nwkq - lokq;
                     }
                     const float2 *uq = a.u32 + q * (NM * NM);
                     while (mask) {
@@ -484,16 +526,14 @@ __global__ void __launch_bounds__(kSfThreads, (W <= 4 ? 3 : 2)) k_scatter_sf(SfA
                         }
                     }
                 }
-                acc += (double)rate;
-                __syncthreads();                             // U and pf are rewritten next
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) rate += __shfl_xor_sync(0xffffffffu, rate, o);
+                acc += (double)rate;                         // runs of this warp in a fixed order
+                __syncwarp();                                // Uw is rewritten by the next run
             }
             __syncthreads();                                 // gl, nglist and Y are rewritten next
         }
-        seg0 = seg1;
     }
-    // fixed-order sum over the CTA's threads
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) wsum[wid] = acc;
     __syncthreads();
     if (tid == 0) {
@@ -504,20 +544,20 @@ __global__ void __launch_bounds__(kSfThreads, (W <= 4 ? 3 : 2)) k_scatter_sf(SfA
 }
 
 struct SfPlan {
-    int jq, njg, nb;
+    int jq, njg, pbmax;
     size_t smem;
 };
 
-// q2 values per group (jq) and runs per U batch (nb) for the grid: Y and U within budgets that
-// keep two or more CTAs per SM, all of it within the per-CTA limit.
+// q2 values per group (jq): Y of one group and one run's U per warp within budgets that keep
+// two or more CTAs per SM.
 SfPlan sf_plan(int D, int X, int q2max, int N1, int N2, int N3) {
-    const size_t ybudget = 40 * 1024, ubudget = 28 * 1024;
+    const size_t ybudget = 40 * 1024, ubudget = 36 * 1024;
     SfPlan p;
-    p.jq = std::max(1, std::min(q2max, (int)(ybudget / (sizeof(float2) * D * D * X))));
+    const size_t per_j = sizeof(float2) * D * X;
+    p.jq = std::max(1, std::min({q2max, (int)(ybudget / (per_j * D)), (int)(ubudget / (per_j * kSfWarps))}));
     p.njg = (q2max + p.jq - 1) / p.jq;
-    const size_t slot = sizeof(float2) * (size_t)D * p.jq * X;
-    p.nb = (int)std::max<size_t>(1, std::min<size_t>(32, ubudget / slot));
-    p.smem = sf_smem_layout(D, X, p.jq, p.nb, N1, N2, N3, p.njg).bytes;
+    p.pbmax = (N2 * N3 + kSieveBlock - 1) / kSieveBlock;
+    p.smem = sf_smem_layout(D, X, p.jq, N1, N2, N3, p.njg, p.pbmax).bytes;
     return p;
 }
 
@@ -620,10 +660,14 @@ void sf_scatter(epwi_ctx *c, const ScatterArgs &sa, int64_t nkp, const int64_t *
         q2max = std::max<int>(q2max, (int)(c1 / sa.g.n3 - c0 / sa.g.n3 + 1));
     }
     const SfPlan plan = sf_plan(D, X, q2max, sa.g.n1, sa.g.n2, sa.g.n3);
-    EPWI_REQUIRE((int64_t)sa.g.n1 * plan.njg <= 8192, EPWI_EUNSUPPORTED, "fp32 mode: too many runs per plane block");
+    EPWI_REQUIRE((int64_t)sa.g.n1 * plan.njg <= 8192 && plan.pbmax <= 8192, EPWI_EUNSUPPORTED,
+                 "fp32 mode: too many runs or plane blocks");
     a.jq = plan.jq;
     a.njg = plan.njg;
-    a.nb = plan.nb;
+    a.pbmax = plan.pbmax;
+    a.fplane = make_fdiv((uint32_t)a.nplane);
+    a.fjq = make_fdiv((uint32_t)plan.jq);
+    a.hwmax32 = c->hwmax32.as<float>();
     a.ph32 = sa.ph32;
     a.ghat = static_cast<const float2 *>(sa.ghat_raw);
     a.kpts = sa.kpts;
