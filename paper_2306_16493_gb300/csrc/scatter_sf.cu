@@ -554,8 +554,9 @@ SfPlan sf_plan(int D, int X, int q2max, int N1, int N2, int N3) {
     const size_t ybudget = 40 * 1024, ubudget = 36 * 1024;
     SfPlan p;
     const size_t per_j = sizeof(float2) * D * X;
-    p.jq = std::max(1, std::min({q2max, (int)(ybudget / (per_j * D)), (int)(ubudget / (per_j * kSfWarps))}));
-    p.njg = (q2max + p.jq - 1) / p.jq;
+    const int jmax = std::max(1, std::min({q2max, (int)(ybudget / (per_j * D)), (int)(ubudget / (per_j * kSfWarps))}));
+    p.njg = (q2max + jmax - 1) / jmax;             // groups of equal size
+    p.jq = (q2max + p.njg - 1) / p.njg;
     p.pbmax = (N2 * N3 + kSieveBlock - 1) / kSieveBlock;
     p.smem = sf_smem_layout(D, X, p.jq, N1, N2, N3, p.njg, p.pbmax).bytes;
     return p;

@@ -168,6 +168,111 @@ __global__ void __launch_bounds__(256) k_sieve_count(SieveArgs a, int64_t nkp,
     if (threadIdx.x == 0) counts[blockIdx.x] = tot;
 }
 
+// k_sieve_count for compile-time W and N_m, with the same candidates, decisions and mask
+// layout, and lanes kept busy.  Every candidate is first prefiltered: any decision that
+// pair_valid_t takes needs some k+q energy within hwmax(q) + c eta + delta of a window energy
+// at k, so a candidate whose k+q energies all lie outside [min window energy - hwmax - pad,
+// max window energy + hwmax + pad] is rejected at once (pad exceeds the FP32 rounding of
+// either form).  The candidates that pass go into a per-warp queue in shared memory; each time
+// 32 are waiting, the warp evaluates them with pair_valid_tail (the unchanged exact test), one
+// per lane, and ORs the decisions into the plane block's mask words, kept in shared memory
+// and written out in k_sieve_count's layout.  Indices are 32-bit (N_k < 2^31, checked).
+constexpr int kQueue = 64;
+template <int WT, int NMT>
+__global__ void __launch_bounds__(256) k_sieve_count_fast(SieveArgs a, const int *__restrict__ kpts,
+                                                          const int *__restrict__ lo,
+                                                          const int *__restrict__ cnt,
+                                                          int64_t *__restrict__ counts,
+                                                          uint32_t *__restrict__ mask,
+                                                          int64_t words_per_kp) {
+    __shared__ double en[epc::kMaxW];
+    __shared__ float en32[epc::kMaxW];
+    __shared__ int64_t sm[33];
+    __shared__ int qiq[8][kQueue], qkq[8][kQueue], qwb[8][kQueue];
+    extern __shared__ uint32_t words[];          // [N1][8]: decisions of the current plane block
+    const int ik = kpts[blockIdx.x];
+    const int nsel = cnt[ik];
+    load_window(a, ik, lo[ik], nsel, en, en32);
+    float elo = en32[0], ehi = en32[0];
+    for (int n = 1; n < nsel; ++n) {
+        elo = fminf(elo, en32[n]);
+        ehi = fmaxf(ehi, en32[n]);
+    }
+    const float pad = a.lim_extra + 1e-4f;
+    int ka1, ka2, ka3;
+    grid_coords(a.g, ik, ka1, ka2, ka3);
+    const int N1 = a.g.n1, nplane = a.g.n2 * a.g.n3;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t *mrow = mask ? mask + (int64_t)blockIdx.x * words_per_kp + wid : nullptr;
+    int *Qi = qiq[wid], *Qk = qkq[wid], *Qw = qwb[wid];
+    // evaluates queue entry e (if valid) and records its decision
+    auto run = [&](int e, bool valid) {
+        if (valid) {
+            const int slot = e & (kQueue - 1);
+            const int iq = Qi[slot], ikq = Qk[slot], wb = Qw[slot];
+            float em[WT];
+            load_kq_energies<WT>(a, ikq, em);
+            if (pair_valid_tail<WT, NMT>(a, nsel, en, en32, iq, ikq, a.hwmax32[iq], em))
+                atomicOr(&words[(wb >> 5) * 8 + wid], 1u << (wb & 31));
+        }
+    };
+    int c = 0;
+    int head = 0, tail = 0;                      // warp-uniform queue positions
+    for (int pb = 0, pbi = 0; pb < nplane; pb += blockDim.x, ++pbi) {
+        const int p = pb + threadIdx.x;
+        const bool inb = p < nplane;
+        const int kqp = inb ? (int)plane_kq(a.g, ka2, ka3, p) : 0;
+        for (int i1 = lane; i1 < N1; i1 += 32) words[i1 * 8 + wid] = 0u;
+        __syncwarp();
+        int b1 = ka1, iq = p;
+        for (int i1 = 0; i1 < N1; ++i1) {
+            bool near = false;
+            int ikq = 0;
+            if (inb) {
+                const float hm = a.hwmax32[iq];
+                if (hm >= 0.f) {
+                    ikq = b1 * nplane + kqp;
+                    float em[WT];
+                    load_kq_energies<WT>(a, ikq, em);
+                    const float lo_ = elo - hm - pad, hi_ = ehi + hm + pad;
+#pragma unroll
+                    for (int m = 0; m < WT; ++m) near |= (em[m] >= lo_) & (em[m] <= hi_);
+                }
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, near);
+            if (near) {
+                const int slot = (tail + __popc(bal & lt)) & (kQueue - 1);
+                Qi[slot] = iq;
+                Qk[slot] = ikq;
+                Qw[slot] = i1 * 32 + lane;
+            }
+            tail += __popc(bal);
+            if (tail - head >= 32) {
+                __syncwarp();
+                run(head + lane, true);
+                head += 32;
+                __syncwarp();
+            }
+            iq += nplane;
+            if (++b1 == N1) b1 = 0;
+        }
+        __syncwarp();
+        run(head + lane, head + lane < tail);    // the rest of the queue
+        head = tail;
+        __syncwarp();
+        for (int i1 = lane; i1 < N1; i1 += 32) {
+            const uint32_t w = words[i1 * 8 + wid];
+            c += __popc(w);
+            if (mrow) mrow[((int64_t)pbi * N1 + i1) * 8] = w;
+        }
+        __syncwarp();
+    }
+    int64_t tot;
+    block_excl_scan((int64_t)c, sm, tot);
+    if (threadIdx.x == 0) counts[blockIdx.x] = tot;
+}
+
 // Pair lists from the decision mask of k_sieve_count, in the same candidate order: each
 // thread takes one mask word, the block scans the word populations in word order, and
 // every thread writes the q of its word's set bits in bit order.
@@ -344,11 +449,20 @@ void sieve_count(epwi_ctx *c) {
     c->mask_words = (nkp > 0 && words * nkp * 4 <= (int64_t(1) << 31)) ? words : 0;
     if (c->mask_words) c->sieve_mask.ensure(sizeof(uint32_t) * words * nkp);
     if (nkp > 0) {
-        auto kern = (c->nw == 4 && c->nm == 3) ? k_sieve_count<4, 3> : k_sieve_count<0, 0>;
-        kern<<<(unsigned)nkp, kSieveBlock, 0, c->stream>>>(
-            a, nkp, c->kpts.as<int>(), c->win_lo.as<int>(), c->win_n.as<int>(),
-            c->counts.as<int64_t>(), c->mask_words ? c->sieve_mask.as<uint32_t>() : nullptr,
-            c->mask_words);
+        uint32_t *mk = c->mask_words ? c->sieve_mask.as<uint32_t>() : nullptr;
+        auto fast = (c->nw == 4 && c->nm == 3) ? k_sieve_count_fast<4, 3>
+                    : (c->nw == 8 && c->nm == 6) ? k_sieve_count_fast<8, 6> : nullptr;
+        const size_t wbytes = sizeof(uint32_t) * 8 * (size_t)c->ng[0];
+        if (fast && c->ng[0] <= 1024 && c->nk < (int64_t(1) << 31) - c->ng[1] * (int64_t)c->ng[2]) {
+            fast<<<(unsigned)nkp, kSieveBlock, wbytes, c->stream>>>(a, c->kpts.as<int>(), c->win_lo.as<int>(),
+                                                                    c->win_n.as<int>(), c->counts.as<int64_t>(),
+                                                                    mk, c->mask_words);
+        } else {
+            auto kern = (c->nw == 4 && c->nm == 3) ? k_sieve_count<4, 3> : k_sieve_count<0, 0>;
+            kern<<<(unsigned)nkp, kSieveBlock, 0, c->stream>>>(
+                a, nkp, c->kpts.as<int>(), c->win_lo.as<int>(), c->win_n.as<int>(), c->counts.as<int64_t>(), mk,
+                c->mask_words);
+        }
         EPWI_CHECK_LAUNCH();
     }
     int64_t np = 0;

@@ -64,24 +64,27 @@ __device__ __forceinline__ bool pair_valid(const SieveArgs &a, int nsel, const d
     return false;
 }
 
-// pair_valid for compile-time W and N_m: the k+q energies in one load (WT = 4), the mode
-// energies loaded once per candidate, the FP32 tests in pair_valid's arithmetic, and the
-// FP64 re-check of pair_valid for candidates near c eta.  Same outcome as pair_valid.
-template <int WT, int NMT>
-__device__ __forceinline__ bool pair_valid_t(const SieveArgs &a, int nsel, const double *en, const float *en32,
-                                             int64_t iq, int64_t ikq) {
-    const float hm = a.hwmax32[iq];
-    if (hm < 0.f) return false;
-    const float lim = hm + a.lim_extra;
-    const float inner = a.ceta32 - a.delta32, outer = a.ceta32 + a.delta32;
-    float em[WT];
-    if constexpr (WT == 4) {
-        const float4 e = *reinterpret_cast<const float4 *>(a.eps32 + ikq * 4);
-        em[0] = e.x; em[1] = e.y; em[2] = e.z; em[3] = e.w;
+// The k+q energies of a candidate (one or two 16-byte loads where WT is a multiple of 4).
+template <int WT>
+__device__ __forceinline__ void load_kq_energies(const SieveArgs &a, int64_t ikq, float (&em)[WT]) {
+    if constexpr (WT % 4 == 0) {
+#pragma unroll
+        for (int m4 = 0; m4 < WT / 4; ++m4) {
+            const float4 e = reinterpret_cast<const float4 *>(a.eps32 + ikq * WT)[m4];
+            em[4 * m4] = e.x; em[4 * m4 + 1] = e.y; em[4 * m4 + 2] = e.z; em[4 * m4 + 3] = e.w;
+        }
     } else {
 #pragma unroll
         for (int m = 0; m < WT; ++m) em[m] = a.eps32[ikq * WT + m];
     }
+}
+
+// pair_valid_t after its loads: hm = hwmax32[iq] >= 0 and em = the k+q energies.
+template <int WT, int NMT>
+__device__ __forceinline__ bool pair_valid_tail(const SieveArgs &a, int nsel, const double *en, const float *en32,
+                                                int64_t iq, int64_t ikq, float hm, const float (&em)[WT]) {
+    const float lim = hm + a.lim_extra;
+    const float inner = a.ceta32 - a.delta32, outer = a.ceta32 + a.delta32;
     bool near = false;
     for (int n = 0; n < nsel; ++n)
 #pragma unroll
@@ -119,6 +122,20 @@ __device__ __forceinline__ bool pair_valid_t(const SieveArgs &a, int nsel, const
         }
     }
     return false;
+}
+
+// pair_valid for compile-time W and N_m (pair_valid_t below): the k+q energies in 16-byte
+// loads, the mode energies loaded once per candidate, the FP32 tests in pair_valid's
+// arithmetic, and the FP64 re-check of pair_valid for candidates near c eta.  Same outcome as
+// pair_valid.
+template <int WT, int NMT>
+__device__ __forceinline__ bool pair_valid_t(const SieveArgs &a, int nsel, const double *en, const float *en32,
+                                             int64_t iq, int64_t ikq) {
+    const float hm = a.hwmax32[iq];
+    if (hm < 0.f) return false;
+    float em[WT];
+    load_kq_energies<WT>(a, ikq, em);
+    return pair_valid_tail<WT, NMT>(a, nsel, en, en32, iq, ikq, hm, em);
 }
 
 __device__ __forceinline__ void load_window(const SieveArgs &a, int ik, int lo, int nsel,
