@@ -321,7 +321,7 @@ def run_gpu(args):
                         per_launch_traffic=None if tb is None else tb * pairs_per_launch, simt_peaks=simt)
 
     # ---- e2e through the C ABI with host buffers
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 3))
     h2d = sum(a.nbytes for a in (s.mass, s.Re, s.we, s.H, s.Rp, s.wp, s.Phi, s.g))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -333,7 +333,7 @@ def run_gpu(args):
         e2e_pairs += npairs
         d2h = k_idx.nbytes + band.nbytes + rates.nbytes + sig.nbytes
     torch.cuda.synchronize()
-    e2e_t = time.perf_counter() - t0
+    e2e_t = max(time.perf_counter() - t0, 1e-30)
     e2e_t = reduce_max_over_ranks(e2e_t, world)
     e2e_pairs = reduce_sum_over_ranks(float(e2e_pairs), world)
 
@@ -397,7 +397,8 @@ def run_gpu(args):
                 "stage_ms": {k: stats[k] for k in ("ms_eigs", "ms_sieve", "ms_restage", "ms_scatter", "ms_reduce")},
                 "roofline": roof, "clocks": clocks, "cpu_baseline": cpu,
                 "error_vs_oracle": err_oracle, "fp64_gpu": fp64,
-                "e2e": {"value": e2e_pairs / e2e_t, "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
+                "e2e": None if args.no_e2e else
+                       {"value": e2e_pairs / e2e_t, "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h)}}
     ctx.close()
     if world > 1:
@@ -741,6 +742,7 @@ def main():
                     help="k and q grid per axis (48 is the benchmark; smaller sizes are for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-leg", action="store_true", help="skip the FP64 GPU comparison step")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (large one-off grids)")
     ap.add_argument("--workload", default="al_like",
                     choices=["al_like", "batch64", "si_like_learned", "al_like_ibte", "ordering_ablation"],
                     help="al_like: the benchmark; batch64 and si_like_learned: the batched and "

@@ -200,7 +200,11 @@ epwi_status epwi_carrier_density(epwi_ctx *ctx, double T_K, double mu_eV, int32_
  * delta(x) = exp(-(x/eta)^2)/(sqrt(pi) eta) for |x| <= c eta, eta = smear_eV.
  * Runs the sieve (Sec. III A), then the on-the-fly q-batched interpolation (Sec. III D) in
  * k-point chunks.  Results stay on the device (see epwi_get_rates); n_states and n_pairs
- * (either may be NULL) receive the state and sieved-pair counts.  Synchronises. */
+ * (either may be NULL) receive the state and sieved-pair counts.  Synchronises.
+ * Memory: the sieve keeps its decisions as a bit mask (one bit per (k-point, q) candidate)
+ * when that mask fits in EPWI_SIEVE_MASK_MAX_BYTES (environment variable, bytes, default
+ * 2 GiB); otherwise each chunk's pair lists are rebuilt by evaluating the sieve again.  Both
+ * give the same pair lists and rates. */
 epwi_status epwi_scatter_rates(epwi_ctx *ctx, double T_K, double mu_eV, double smear_eV,
                                double emin_eV, double emax_eV,
                                int64_t *n_states, int64_t *n_pairs);

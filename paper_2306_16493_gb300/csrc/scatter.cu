@@ -436,7 +436,10 @@ void process_workset(epwi_ctx *c, const WorkSet &ws, double *g2out, double *tout
         sf_prepare(c);
     }
     // chunk limits: pairs and Re->k output size
-    const int64_t max_pairs = int64_t(1) << 27;
+    // pair lists per chunk: 2^32 q indices (16 GiB) in the fp32 mode, whose launches are one
+    // CTA per state and need thousands of states per chunk to fill the GPU on large grids (200^3:
+    // ~1.8 M pairs per state); 2^27 otherwise
+    const int64_t max_pairs = int64_t(1) << (sf ? 32 : 27);
     const size_t state_bytes = sf ? sf_state_bytes(c) : tc ? tc_state_bytes(c) : sizeof(double2) * nrow;
     const int64_t max_states = std::max<int64_t>(1, (int64_t)((size_t(3) << 30) / state_bytes));
     const int64_t kp_cap = c->opt.kpoint_chunk > 0 ? c->opt.kpoint_chunk : (int64_t)1 << 40;

@@ -7,6 +7,8 @@
 // Each candidate is first evaluated in FP32 with a rigorous bound delta on the rounding
 // error; only candidates whose nearest |x| lies within delta of c eta are re-evaluated in
 // FP64 in the oracle's rounding order, so every decision equals the FP64 one.
+#include <cstdlib>
+
 #include "epwi_internal.cuh"
 #include "sieve.cuh"
 
@@ -177,20 +179,28 @@ __global__ void __launch_bounds__(256) k_sieve_count(SieveArgs a, int64_t nkp,
 // 32 are waiting, the warp evaluates them with pair_valid_tail (the unchanged exact test), one
 // per lane, and ORs the decisions into the plane block's mask words, kept in shared memory
 // and written out in k_sieve_count's layout.  Indices are 32-bit (N_k < 2^31, checked).
+//
+// With FILL the same kernel writes the pair lists of k-points kp0 + blockIdx.x instead (used
+// when the whole decision mask would not fit in memory): after each plane block the CTA scans
+// the populations of its shared mask words in word order and writes the q of the set bits,
+// which is the order of k_sieve_fill_mask.
 constexpr int kQueue = 64;
-template <int WT, int NMT>
+template <int WT, int NMT, bool FILL>
 __global__ void __launch_bounds__(256) k_sieve_count_fast(SieveArgs a, const int *__restrict__ kpts,
                                                           const int *__restrict__ lo,
                                                           const int *__restrict__ cnt,
                                                           int64_t *__restrict__ counts,
                                                           uint32_t *__restrict__ mask,
-                                                          int64_t words_per_kp) {
+                                                          int64_t words_per_kp, int64_t kp0,
+                                                          const int64_t *__restrict__ kp_pairs,
+                                                          int *__restrict__ pairs) {
     __shared__ double en[epc::kMaxW];
     __shared__ float en32[epc::kMaxW];
     __shared__ int64_t sm[33];
     __shared__ int qiq[8][kQueue], qkq[8][kQueue], qwb[8][kQueue];
     extern __shared__ uint32_t words[];          // [N1][8]: decisions of the current plane block
-    const int ik = kpts[blockIdx.x];
+    const int64_t kp = FILL ? kp0 + blockIdx.x : blockIdx.x;
+    const int ik = kpts[kp];
     const int nsel = cnt[ik];
     load_window(a, ik, lo[ik], nsel, en, en32);
     float elo = en32[0], ehi = en32[0];
@@ -204,7 +214,8 @@ __global__ void __launch_bounds__(256) k_sieve_count_fast(SieveArgs a, const int
     const int N1 = a.g.n1, nplane = a.g.n2 * a.g.n3;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
-    uint32_t *mrow = mask ? mask + (int64_t)blockIdx.x * words_per_kp + wid : nullptr;
+    uint32_t *mrow = (mask && !FILL) ? mask + (int64_t)blockIdx.x * words_per_kp + wid : nullptr;
+    int64_t obase = FILL ? kp_pairs[kp] - kp_pairs[kp0] : 0;   // next output position (FILL)
     int *Qi = qiq[wid], *Qk = qkq[wid], *Qw = qwb[wid];
     // evaluates queue entry e (if valid) and records its decision
     auto run = [&](int e, bool valid) {
@@ -261,13 +272,35 @@ __global__ void __launch_bounds__(256) k_sieve_count_fast(SieveArgs a, const int
         run(head + lane, head + lane < tail);    // the rest of the queue
         head = tail;
         __syncwarp();
-        for (int i1 = lane; i1 < N1; i1 += 32) {
-            const uint32_t w = words[i1 * 8 + wid];
-            c += __popc(w);
-            if (mrow) mrow[((int64_t)pbi * N1 + i1) * 8] = w;
+        if constexpr (FILL) {
+            __syncthreads();                     // every warp's words of this plane block
+            const int nw = N1 * 8, per = (nw + blockDim.x - 1) / blockDim.x;
+            const int w0 = threadIdx.x * per, w1 = min(nw, w0 + per);
+            int pop = 0;
+            for (int w = w0; w < w1; ++w) pop += __popc(words[w]);
+            int64_t tot;
+            int64_t o = obase + block_excl_scan((int64_t)pop, sm, tot);
+            for (int w = w0; w < w1; ++w) {
+                uint32_t b = words[w];
+                const int q0 = (w >> 3) * nplane + pb + (w & 7) * 32;   // (i1, warp) of the word
+                while (b) {
+                    const int bit = __ffs(b) - 1;
+                    b &= b - 1;
+                    pairs[o++] = q0 + bit;
+                }
+            }
+            obase += tot;
+            __syncthreads();                     // the words are cleared next
+        } else {
+            for (int i1 = lane; i1 < N1; i1 += 32) {
+                const uint32_t w = words[i1 * 8 + wid];
+                c += __popc(w);
+                if (mrow) mrow[((int64_t)pbi * N1 + i1) * 8] = w;
+            }
+            __syncwarp();
         }
-        __syncwarp();
     }
+    if constexpr (FILL) return;
     int64_t tot;
     block_excl_scan((int64_t)c, sm, tot);
     if (threadIdx.x == 0) counts[blockIdx.x] = tot;
@@ -346,6 +379,12 @@ __global__ void __launch_bounds__(256) k_sieve_fill(SieveArgs a, int64_t kp0,
 }
 
 }  // namespace
+
+// The fast count / fill kernels keep one plane block's decisions (8 words per q1) in shared
+// memory and use 32-bit candidate indices.
+static bool sieve_fast_ok(const epwi_ctx *c) {
+    return c->ng[0] <= 1024 && c->nk < (int64_t(1) << 31) - c->ng[1] * (int64_t)c->ng[2];
+}
 
 SieveArgs make_sieve_args(epwi_ctx *c) {
     SieveArgs a;
@@ -446,17 +485,19 @@ void sieve_count(epwi_ctx *c) {
     // decision mask for the fill when it fits in 2 GiB (else the fill re-evaluates)
     const int64_t nplane = (int64_t)c->ng[1] * c->ng[2];
     const int64_t words = ((nplane + kSieveBlock - 1) / kSieveBlock) * c->ng[0] * (kSieveBlock / 32);
-    c->mask_words = (nkp > 0 && words * nkp * 4 <= (int64_t(1) << 31)) ? words : 0;
+    // EPWI_SIEVE_MASK_MAX_BYTES (default 2 GiB) caps the mask; 0 forces the re-evaluating fill
+    int64_t cap = int64_t(1) << 31;
+    if (const char *env = std::getenv("EPWI_SIEVE_MASK_MAX_BYTES")) cap = std::strtoll(env, nullptr, 10);
+    c->mask_words = (nkp > 0 && words * nkp * 4 <= cap) ? words : 0;
     if (c->mask_words) c->sieve_mask.ensure(sizeof(uint32_t) * words * nkp);
     if (nkp > 0) {
         uint32_t *mk = c->mask_words ? c->sieve_mask.as<uint32_t>() : nullptr;
-        auto fast = (c->nw == 4 && c->nm == 3) ? k_sieve_count_fast<4, 3>
-                    : (c->nw == 8 && c->nm == 6) ? k_sieve_count_fast<8, 6> : nullptr;
-        const size_t wbytes = sizeof(uint32_t) * 8 * (size_t)c->ng[0];
-        if (fast && c->ng[0] <= 1024 && c->nk < (int64_t(1) << 31) - c->ng[1] * (int64_t)c->ng[2]) {
-            fast<<<(unsigned)nkp, kSieveBlock, wbytes, c->stream>>>(a, c->kpts.as<int>(), c->win_lo.as<int>(),
-                                                                    c->win_n.as<int>(), c->counts.as<int64_t>(),
-                                                                    mk, c->mask_words);
+        auto fast = (c->nw == 4 && c->nm == 3) ? k_sieve_count_fast<4, 3, false>
+                    : (c->nw == 8 && c->nm == 6) ? k_sieve_count_fast<8, 6, false> : nullptr;
+        if (fast && sieve_fast_ok(c)) {
+            fast<<<(unsigned)nkp, kSieveBlock, sizeof(uint32_t) * 8 * (size_t)c->ng[0], c->stream>>>(
+                a, c->kpts.as<int>(), c->win_lo.as<int>(), c->win_n.as<int>(), c->counts.as<int64_t>(), mk,
+                c->mask_words, 0, nullptr, nullptr);
         } else {
             auto kern = (c->nw == 4 && c->nm == 3) ? k_sieve_count<4, 3> : k_sieve_count<0, 0>;
             kern<<<(unsigned)nkp, kSieveBlock, 0, c->stream>>>(
@@ -484,6 +525,15 @@ void sieve_fill_chunk(epwi_ctx *c, int64_t kp0, int64_t kp1, int *pairs) {
         return;
     }
     SieveArgs a = make_sieve_args(c);
+    auto fast = (c->nw == 4 && c->nm == 3) ? k_sieve_count_fast<4, 3, true>
+                : (c->nw == 8 && c->nm == 6) ? k_sieve_count_fast<8, 6, true> : nullptr;
+    if (fast && sieve_fast_ok(c)) {
+        fast<<<(unsigned)(kp1 - kp0), kSieveBlock, sizeof(uint32_t) * 8 * (size_t)c->ng[0], c->stream>>>(
+            a, c->kpts.as<int>(), c->win_lo.as<int>(), c->win_n.as<int>(), nullptr, nullptr, 0, kp0,
+            c->kp_pairs.as<int64_t>(), pairs);
+        EPWI_CHECK_LAUNCH();
+        return;
+    }
     k_sieve_fill<<<(unsigned)(kp1 - kp0), 256, 0, c->stream>>>(
         a, kp0, c->kpts.as<int>(), c->win_lo.as<int>(), c->win_n.as<int>(),
         c->kp_pairs.as<int64_t>(), pairs);

@@ -67,9 +67,31 @@ def test_fp32_against_fp64_gpu_and_determinism():
     assert np.array_equal(b[2], c[2]) and np.array_equal(b[2], d[2])
 
 
+@pytest.mark.parametrize("name,grid,half", [("al_like", (14, 9, 40), 0.3), ("si_like", (8, 8, 8), None)])
+def test_sieve_without_mask_gives_the_same_rates(monkeypatch, name, grid, half):
+    """When the decision mask does not fit (forced with EPWI_SIEVE_MASK_MAX_BYTES=0) the pair
+    lists are rebuilt per chunk by the sieve kernel's fill mode: the pair counts and the rates
+    (FP64 and fp32, several chunks) are bitwise those of the mask path."""
+    s = getattr(synth, f"{name}_system")()
+    gr = O.Grids(s, grid)
+    mu = gr.band_centre()
+    lo, hi = (-1e9, 1e9) if half is None else (mu - half, mu + half)
+    for prec in ("fp64", "fp32"):
+        monkeypatch.delenv("EPWI_SIEVE_MASK_MAX_BYTES", raising=False)
+        a = gpu_run(s, grid, T, mu, 0.03, lo, hi, precision=prec, kpoint_chunk=5)
+        monkeypatch.setenv("EPWI_SIEVE_MASK_MAX_BYTES", "0")
+        b = gpu_run(s, grid, T, mu, 0.03, lo, hi, precision=prec, kpoint_chunk=5)
+        assert a["n_pairs"] == b["n_pairs"] > 0
+        assert np.array_equal(a["inv_tau"], b["inv_tau"]) and np.array_equal(a["sigma"], b["sigma"])
+        a["ctx"].close()
+        b["ctx"].close()
+    ref = oracle_run(gr, T, mu, 0.03, lo, hi)
+    assert b["n_pairs"] == ref["n_pairs"]
+
+
 def test_al_like_48_sampled_fp32():
     """The benchmark configuration in the benchmark's precision: Al-like 48^3, window +-0.3 eV
-    around the band centre, eta = 20 meV, default k-point chunking.  Eight sampled window
+    around the band centre, eta = 20 meV, default k-point chunking (as the benchmark launches it).  Eight sampled window
     k-points are recomputed by the oracle (all their q); the full sigma is compared with the
     FP64 GPU path on the same grid."""
     s = synth.al_like_system()
@@ -80,7 +102,6 @@ def test_al_like_48_sampled_fp32():
     lo, hi = ctx.band_range()
     mu = 0.5 * (lo + hi)
     out = gpu_run(s, (N, N, N), T, mu, eta, mu - 0.3, mu + 0.3, precision="fp32", ctx=ctx)
-    assert out["stats"]["n_chunks"] > 1            # several launches, as in the benchmark
     gr = O.Grids(s, (N, N, N))
     kp, cnt = ctx.sieve()
     pick = kp[np.random.default_rng(29).choice(len(kp), 8, replace=False)]
