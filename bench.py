@@ -675,6 +675,115 @@ def run_ibte(args):
     print(json.dumps(line), flush=True)
 
 
+SI = dict(workload="si_like_100", system="Si-like diamond, nw=8 (4v+4c), 6 modes, 7^3 WS-weighted Re/Rp, "
+          "1.1 eV gap", grid=100, window="[CBM, CBM+0.25 eV]", n_c_cm3=1e18, smear_eV=0.01, T_K=300.0, seed=3)
+
+
+def run_si(args):
+    """Si-like semiconductor mobility: one step = eigensolves -> mu(n_c) -> window above the
+    CBM -> sieve -> interpolation + SERTA -> mobility tensor.  value = sieved pairs / step
+    time (time-to-mobility).  The fp32 mode is timed over the steps; one FP64 step and the
+    FP64 oracle on sampled k-points give its error."""
+    import torch
+    from paper_2306_16493_gb300 import epwi, synth
+    torch.cuda.set_device(0)
+    s = synth.si_like_system(SI["seed"])
+    N = args.si_grid
+    T, eta, n_c, nv = SI["T_K"], SI["smear_eV"], SI["n_c_cm3"], s.n_valence
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def make(prec):
+        ctx = epwi.Context(precision=prec, device=0, stream=stream.cuda_stream)
+        ctx.setup(s)
+        return ctx
+
+    def step(ctx):
+        ctx.eigs(N)
+        mu = ctx.find_mu(T, n_c, nv)
+        _, cbm = ctx.band_edges(nv)
+        _, npairs = ctx.scatter_rates(T, mu, eta, cbm, cbm + 0.25)
+        ctx.conductivity()
+        return npairs, ctx.mobility(n_c), mu, cbm
+
+    ctx = make(args.precision)
+    for _ in range(args.warmup):
+        step(ctx)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sts = []
+    launches0 = epwi.epwi_kernel_launches()
+    clocks_path = os.path.join(tempfile.gettempdir(), f"epwi_clocks_{os.getpid()}.csv")
+    with ClockSampler(clocks_path) as cs:
+        time.sleep(0.3)
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            npairs, mob, mu, cbm = step(ctx)
+            ev[k][1].record(stream)
+            sts.append(ctx.stats())
+        torch.cuda.synchronize()
+    launches = (epwi.epwi_kernel_launches() - launches0) // args.steps
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    gk, gb, gr_ = ctx.rates()
+    st = sts[-1]
+    stats = dict(st, scatter_flops=statistics.mean(x["scatter_flops"] for x in sts),
+                 ms_scatter=statistics.mean(x["ms_scatter"] for x in sts))
+    roof = roofline_for(args.precision, stats, simt_peaks=fma_peaks(0, stream.cuda_stream))
+    # one FP64 step on the same workload
+    fp64 = None
+    if not args.no_fp64_leg and args.precision != "fp64":
+        c64 = make("fp64")
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        np64, mob64, _, _ = step(c64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        k64, b64, r64 = c64.rates()
+        err64, ng = group_rel_error(gk, gb, gr_, k64, b64, r64, c64.bands()[0])
+        fp64 = {"time_to_mobility_ms": ms64, "value": np64 / (ms64 * 1e-3), "unit": "pairs/s",
+                "speedup_of_this_precision": ms64 / ms, "same_pairs": int(np64) == int(npairs),
+                "rate_max_rel_error_vs_fp64": err64, "rate_groups_compared": ng,
+                "mobility_rel_frobenius_vs_fp64": float(np.linalg.norm(mob - mob64) / np.linalg.norm(mob64)),
+                "stated_tolerance": {"inv_tau": 1e-4, "mobility": 1e-4}}
+        c64.close()
+    # FP64 oracle on sampled k-points of the window
+    err_oracle, cpu = None, None
+    if not args.no_cpu_baseline:
+        from oracle import epwi_oracle as O
+        t0 = time.perf_counter()
+        gro = O.Grids(s, (N, N, N))
+        t_grid = time.perf_counter() - t0
+        kp = np.unique(gk)
+        pick = np.random.default_rng(5).choice(kp, min(len(kp), args.ref_kpoints), replace=False)
+        t0 = time.perf_counter()
+        ref = O.serta(gro, T, mu, eta, cbm, cbm + 0.25, k_subset=pick)
+        dt = time.perf_counter() - t0
+        e, ng = group_rel_error(gk, gb, gr_, ref["ik"], ref["n"], ref["inv_tau"], gro.eps)
+        err_oracle = {"inv_tau_max_rel_error": e, "groups_compared": ng, "kpoints": len(pick),
+                      "stated_tolerance": 1e-4, "oracle_grid_s": t_grid}
+        cpu = {"value": ref["n_pairs"] / dt, "unit": "pairs/s", "cores": cores_used(), "kind": "oracle",
+               "sample": f"{len(pick)} seeded window k-points of the {N}^3 workload with all their q "
+                         f"({ref['n_pairs']} pairs, {dt:.1f} s, numpy FP64; grid eigensolves excluded)"}
+    line = {"metric": "el-ph (k,q)-pairs/s and time-to-mobility, mixed-precision vs FP64 at stated error",
+            "value": npairs / (ms * 1e-3), "unit": "pairs/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "time_to_sigma_ms": ms, "pairs_per_step": npairs,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision],
+            "data": "synthetic",
+            "config": dict(SI, grid=N, workload=f"si_like_{N}", precision=args.precision,
+                           l2="flushed between timed steps (256 MiB write)", parallelism="single GPU"),
+            "gpu_launches": int(launches), "n_states": st["n_states"], "n_kpoints": st["n_kpoints"],
+            "mu_eV": mu, "cbm_eV": cbm, "mobility_cm2_per_Vs_diag": [float(mob[i, i]) for i in range(3)],
+            "stage_ms": {k: st[k] for k in ("ms_eigs", "ms_sieve", "ms_restage", "ms_scatter", "ms_reduce")},
+            "roofline": roof, "clocks": cs.summary(0), "cpu_baseline": cpu, "error_vs_oracle": err_oracle,
+            "fp64_gpu": fp64}
+    ctx.close()
+    print(json.dumps(line), flush=True)
+
+
 def run_kbatch(args):
     """Ordering ablation (Sec. III C, Table 3): the same FP64 rates call with the q-batch and
     the k-batch interpolation order on the Al-like metal."""
@@ -744,7 +853,8 @@ def main():
     ap.add_argument("--no-fp64-leg", action="store_true", help="skip the FP64 GPU comparison step")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (large one-off grids)")
     ap.add_argument("--workload", default="al_like",
-                    choices=["al_like", "batch64", "si_like_learned", "al_like_ibte", "ordering_ablation"],
+                    choices=["al_like", "si_like", "batch64", "si_like_learned", "al_like_ibte",
+                             "ordering_ablation"],
                     help="al_like: the benchmark; batch64 and si_like_learned: the batched and "
                          "learned-proposal workloads (reported separately)")
     ap.add_argument("--batch-scale", type=int, default=3, help="batch64: grid divisor")
@@ -759,6 +869,7 @@ def main():
     ap.add_argument("--ibte-precision", default="fp32", choices=["fp64", "tf32x3", "bf16x3", "fp16x3", "fp32"],
                     help="al_like_ibte: precision of the rates and Gamma capture")
     ap.add_argument("--ablation-grid", type=int, default=24, help="ordering_ablation: grid per axis")
+    ap.add_argument("--si-grid", type=int, default=100, help="si_like: grid per axis")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -770,6 +881,8 @@ def main():
         run_ibte(args)
     elif args.workload == "ordering_ablation":
         run_kbatch(args)
+    elif args.workload == "si_like":
+        run_si(args)
     else:
         run_gpu(args)
 

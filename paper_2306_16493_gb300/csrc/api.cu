@@ -278,6 +278,31 @@ epwi_status epwi_setup(epwi_ctx *c, const epwi_system *s) {
             if (ok) c->rp_cube_r = rr;
             break;
         }
+        // factorised H(k) / D(q) builds (eigs.cu): weighted H and Phi in the bounding cubes
+        {
+            auto embed = [](const int32_t *R, int n, size_t ne, auto value, int &rout, std::vector<double2> &out) {
+                int r = 0;
+                for (int i = 0; i < 3 * n; ++i) r = std::max(r, std::abs(R[i]));
+                rout = -1;
+                out.clear();
+                if (r > 6) return;
+                const int Dc = 2 * r + 1;
+                out.assign((size_t)Dc * Dc * Dc * ne, make_double2(0, 0));
+                for (int k = 0; k < n; ++k) {
+                    const size_t cf = ((size_t)(R[3 * k] + r) * Dc + (R[3 * k + 1] + r)) * Dc + (R[3 * k + 2] + r);
+                    for (size_t e = 0; e < ne; ++e) out[cf * ne + e] = value(k, e);
+                }
+                rout = r;
+            };
+            std::vector<double2> hc, pc;
+            embed(s->Re, nRe, (size_t)W * W, [&](int k, size_t e) { return Hw[(size_t)k * W * W + e]; },
+                  c->fac_re_r, hc);
+            embed(s->Rp, nRp, (size_t)Nm * Nm,
+                  [&](int k, size_t e) { return make_double2(Pw[(size_t)k * Nm * Nm + e], 0.0); }, c->fac_rp_r, pc);
+            if (c->fac_re_r >= 0) upload(c->fac_Hc, hc.data(), hc.size(), c->stream);
+            if (c->fac_rp_r >= 0) upload(c->fac_Pc, pc.data(), pc.size(), c->stream);
+            EPWI_CUDA(cudaStreamSynchronize(c->stream));   // hc, pc are freed on return
+        }
         // fp32 mode: R_p embedded in its bounding cube [-r, r]^3 (points outside the set carry
         // zero weight); g' is built from the weighted g on the first fp32 rates call
         {

@@ -5,6 +5,8 @@
 // One thread owns one grid point.  Each point is diagonalised once (Nk + Nq solves); the
 // scattering loops gather V(k+q), u(q) from these tables instead of re-diagonalising per
 // pair.
+#include <algorithm>
+
 #include "epwi_internal.cuh"
 #include "jacobi.cuh"
 
@@ -19,8 +21,89 @@ __global__ void k_phase_tables(int L, double2 *ph64, float2 *ph32) {
     ph32[m] = make_float2((float)c, (float)s);
 }
 
-// Electrons: eps (ascending), V (columns), velocities, FP32 copies.
-template <int WMAX>
+// Sum-factorised Fourier builds (Eqs. 4-5 reordered, exact in real arithmetic).  With the
+// R-set embedded in its bounding cube [-r, r]^3 (absent vectors carry zero), e^{ik.R} =
+// e1(k1, n1) e2(k2, n2) e3(k3, n3) and X(k) = sum_n1 e1 sum_n2 e2 sum_n3 e3 X(n) is done in
+// three stages, each shared by every grid point that needs it: axis 3 per (n1, n2, k3), axis 2
+// per (n1, k2, k3), axis 1 inside the eigensolve kernels per k.  For the band velocities the
+// n_b-weighted sums sum_n n_b e^{ik.R} H(R) ride along (VEL): dH/dk_a = i sum_b A_ba S_b with
+// R_cart = sum_b n_b a_b.  E = entries per matrix; all FP64.
+//   T[s][n1][n2][k3][e]:  s = 0: sum_n3 e3 X;   s = 1 (VEL): sum_n3 n3 e3 X
+//   U[s][n1][k2][k3][e]:  s = 0: sum_n2 e2 T0;  s = 1: sum_n2 n2 e2 T0;  s = 2: sum_n2 e2 T1
+__device__ __forceinline__ double2 axis_ph(const double2 *ph, int n, int a, int L) {
+    int t = (n * a) % L;
+    if (t < 0) t += L;
+    return ph[t];
+}
+
+template <bool VEL>
+__global__ void k_fac_axis3(int D, int rc, int N3, int s3, int L, int E, const double2 *__restrict__ Xc,
+                            const double2 *__restrict__ ph, double2 *__restrict__ T) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t total = (int64_t)D * D * N3 * E;
+    if (idx >= total) return;
+    const int e = (int)(idx % E);
+    const int64_t t = idx / E;
+    const int k3 = (int)(t % N3);
+    const int r12 = (int)(t / N3);
+    const int a3 = (int)((int64_t)k3 * s3 % L);
+    double2 s0 = make_double2(0, 0), s1 = make_double2(0, 0);
+    for (int j = 0; j < D; ++j) {
+        const int n3 = j - rc;
+        const double2 v = cmul(axis_ph(ph, n3, a3, L), Xc[((int64_t)r12 * D + j) * E + e]);
+        s0 = cadd(s0, v);
+        if (VEL) s1 = make_double2(fma((double)n3, v.x, s1.x), fma((double)n3, v.y, s1.y));
+    }
+    T[((int64_t)r12 * N3 + k3) * E + e] = s0;
+    if (VEL) T[(((int64_t)D * D + r12) * N3 + k3) * E + e] = s1;
+}
+
+template <bool VEL>
+__global__ void k_fac_axis2(int D, int rc, int N2, int N3, int s2, int L, int E, const double2 *__restrict__ T,
+                            const double2 *__restrict__ ph, double2 *__restrict__ U) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t plane = (int64_t)N2 * N3;
+    const int64_t total = (int64_t)D * plane * E;
+    if (idx >= total) return;
+    const int e = (int)(idx % E);
+    int64_t t = idx / E;
+    const int k3 = (int)(t % N3);
+    t /= N3;
+    const int k2 = (int)(t % N2);
+    const int r1 = (int)(t / N2);
+    const int a2 = (int)((int64_t)k2 * s2 % L);
+    double2 u0 = make_double2(0, 0), u1 = make_double2(0, 0), u2 = make_double2(0, 0);
+    for (int j = 0; j < D; ++j) {
+        const int n2 = j - rc;
+        const double2 p = axis_ph(ph, n2, a2, L);
+        const double2 v = cmul(p, T[(((int64_t)r1 * D + j) * N3 + k3) * E + e]);
+        u0 = cadd(u0, v);
+        if (VEL) {
+            u1 = make_double2(fma((double)n2, v.x, u1.x), fma((double)n2, v.y, u1.y));
+            u2 = cadd(u2, cmul(p, T[((((int64_t)D + r1) * D + j) * N3 + k3) * E + e]));
+        }
+    }
+    const int64_t o = ((int64_t)r1 * plane + (int64_t)k2 * N3 + k3) * E + e;
+    U[o] = u0;
+    if (VEL) {
+        U[(int64_t)D * plane * E + o] = u1;
+        U[2 * (int64_t)D * plane * E + o] = u2;
+    }
+}
+
+// The axis-2 stage output U[s][n1][k2 k3][e] of a factorised build (sources s = 0, 1, 2).
+struct FacDesc {
+    const double2 *U;
+    int D, rc;
+    int64_t plane;                   // N2 N3
+};
+struct Lattice {
+    double a[3][3];                  // rows a_1, a_2, a_3 (A)
+};
+
+// Electrons: eps (ascending), V (columns), velocities, FP32 copies.  FAC: H(k) and dH/dk from
+// the factorised stages (fac, lattice rows lat) instead of direct sums over the R-set.
+template <int WMAX, bool FAC>
 __global__ void __launch_bounds__(128) k_eig_el(GridInfo g, int64_t nk, int W, int nR,
                                                 const int *__restrict__ R,
                                                 const double *__restrict__ Rcart,
@@ -29,7 +112,8 @@ __global__ void __launch_bounds__(128) k_eig_el(GridInfo g, int64_t nk, int W, i
                                                 double *__restrict__ eps, float *__restrict__ eps32,
                                                 double2 *__restrict__ Vout,
                                                 float2 *__restrict__ V32,
-                                                double *__restrict__ vel, int *__restrict__ flag) {
+                                                double *__restrict__ vel, int *__restrict__ flag,
+                                                FacDesc fac, Lattice lat) {
     int64_t ik = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (ik >= nk) return;
     int i1, i2, i3;
@@ -38,11 +122,20 @@ __global__ void __launch_bounds__(128) k_eig_el(GridInfo g, int64_t nk, int W, i
               a3 = (int)((int64_t)i3 * g.s3 % g.L);
     double2 A[WMAX * WMAX], Vm[WMAX * WMAX];
     const int WW = W * W;
+    const int64_t pp = (int64_t)i2 * g.n3 + i3;   // (k2, k3) of this point (factorised build)
     for (int e = 0; e < WW; ++e) A[e] = make_double2(0, 0);
-    for (int r = 0; r < nR; ++r) {
-        const double2 p = ph[phase_index(a1, a2, a3, R[3 * r], R[3 * r + 1], R[3 * r + 2], g.L)];
-        const double2 *h = Hw + (size_t)r * WW;
-        for (int e = 0; e < WW; ++e) A[e] = cfma(p, h[e], A[e]);
+    if constexpr (FAC) {
+        for (int j = 0; j < fac.D; ++j) {
+            const double2 p = axis_ph(ph, j - fac.rc, a1, g.L);
+            const double2 *u = fac.U + ((int64_t)j * fac.plane + pp) * WW;
+            for (int e = 0; e < WW; ++e) A[e] = cfma(p, u[e], A[e]);
+        }
+    } else {
+        for (int r = 0; r < nR; ++r) {
+            const double2 p = ph[phase_index(a1, a2, a3, R[3 * r], R[3 * r + 1], R[3 * r + 2], g.L)];
+            const double2 *h = Hw + (size_t)r * WW;
+            for (int e = 0; e < WW; ++e) A[e] = cfma(p, h[e], A[e]);
+        }
     }
     double w[WMAX];
     int ok = jacobi_hermitian<WMAX>(A, Vm, W, w);
@@ -58,12 +151,29 @@ __global__ void __launch_bounds__(128) k_eig_el(GridInfo g, int64_t nk, int W, i
     // v_n,a = (1/hbar) Re[V^dag (sum_R w_R i R_a e^{ik.R} H(R)) V]_nn, one axis at a time
     for (int ax = 0; ax < 3; ++ax) {
         for (int e = 0; e < WW; ++e) A[e] = make_double2(0, 0);
-        for (int r = 0; r < nR; ++r) {
-            const double2 p = ph[phase_index(a1, a2, a3, R[3 * r], R[3 * r + 1], R[3 * r + 2], g.L)];
-            const double ra = Rcart[3 * r + ax];
-            const double2 ip = make_double2(-ra * p.y, ra * p.x);   // i R_a e^{ik.R}
-            const double2 *h = Hw + (size_t)r * WW;
-            for (int e = 0; e < WW; ++e) A[e] = cfma(ip, h[e], A[e]);
+        if constexpr (FAC) {
+            // i R_a = i (n1 A_1a + n2 A_2a + n3 A_3a): U_0 weighted by n1, U_1 (n2 sums), U_2 (n3 sums)
+            const int64_t src = (int64_t)fac.D * fac.plane * WW;
+            for (int j = 0; j < fac.D; ++j) {
+                const int n1 = j - fac.rc;
+                const double2 p = axis_ph(ph, n1, a1, g.L);
+                const double2 ip = make_double2(-p.y, p.x);   // i e1
+                const double c0 = n1 * lat.a[0][ax], c1 = lat.a[1][ax], c2 = lat.a[2][ax];
+                const double2 *u = fac.U + ((int64_t)j * fac.plane + pp) * WW;
+                for (int e = 0; e < WW; ++e) {
+                    const double2 sr = make_double2(c0 * u[e].x + c1 * u[src + e].x + c2 * u[2 * src + e].x,
+                                                    c0 * u[e].y + c1 * u[src + e].y + c2 * u[2 * src + e].y);
+                    A[e] = cfma(ip, sr, A[e]);
+                }
+            }
+        } else {
+            for (int r = 0; r < nR; ++r) {
+                const double2 p = ph[phase_index(a1, a2, a3, R[3 * r], R[3 * r + 1], R[3 * r + 2], g.L)];
+                const double ra = Rcart[3 * r + ax];
+                const double2 ip = make_double2(-ra * p.y, ra * p.x);   // i R_a e^{ik.R}
+                const double2 *h = Hw + (size_t)r * WW;
+                for (int e = 0; e < WW; ++e) A[e] = cfma(ip, h[e], A[e]);
+            }
         }
         for (int n = 0; n < W; ++n) {
             double acc = 0;
@@ -77,8 +187,9 @@ __global__ void __launch_bounds__(128) k_eig_el(GridInfo g, int64_t nk, int W, i
     }
 }
 
-// Phonons: hbar*omega, u = e (hbar^2 / (2 m hbar omega))^{1/2}, FP32 copies.
-template <int NMAX>
+// Phonons: hbar*omega, u = e (hbar^2 / (2 m hbar omega))^{1/2}, FP32 copies.  FAC: D(q) from
+// the factorised stages.
+template <int NMAX, bool FAC>
 __global__ void __launch_bounds__(128) k_eig_ph(GridInfo g, int64_t nq, int Nm, int nR,
                                                 const int *__restrict__ R,
                                                 const double *__restrict__ Phiw,
@@ -87,7 +198,8 @@ __global__ void __launch_bounds__(128) k_eig_ph(GridInfo g, int64_t nq, int Nm, 
                                                 double *__restrict__ hw, float *__restrict__ hwmax32,
                                                 float *__restrict__ hw32,
                                                 double2 *__restrict__ uout,
-                                                float2 *__restrict__ u32, int *__restrict__ flag) {
+                                                float2 *__restrict__ u32, int *__restrict__ flag,
+                                                FacDesc fac) {
     int64_t iq = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (iq >= nq) return;
     int i1, i2, i3;
@@ -97,12 +209,21 @@ __global__ void __launch_bounds__(128) k_eig_ph(GridInfo g, int64_t nq, int Nm, 
     double2 A[NMAX * NMAX], E[NMAX * NMAX];
     const int MM = Nm * Nm;
     for (int e = 0; e < MM; ++e) A[e] = make_double2(0, 0);
-    for (int r = 0; r < nR; ++r) {
-        const double2 p = ph[phase_index(a1, a2, a3, R[3 * r], R[3 * r + 1], R[3 * r + 2], g.L)];
-        const double *f = Phiw + (size_t)r * MM;
-        for (int e = 0; e < MM; ++e) {
-            A[e].x = fma(p.x, f[e], A[e].x);
-            A[e].y = fma(p.y, f[e], A[e].y);
+    if constexpr (FAC) {
+        const int64_t pp = (int64_t)i2 * g.n3 + i3;
+        for (int j = 0; j < fac.D; ++j) {
+            const double2 p = axis_ph(ph, j - fac.rc, a1, g.L);
+            const double2 *u = fac.U + ((int64_t)j * fac.plane + pp) * MM;
+            for (int e = 0; e < MM; ++e) A[e] = cfma(p, u[e], A[e]);
+        }
+    } else {
+        for (int r = 0; r < nR; ++r) {
+            const double2 p = ph[phase_index(a1, a2, a3, R[3 * r], R[3 * r + 1], R[3 * r + 2], g.L)];
+            const double *f = Phiw + (size_t)r * MM;
+            for (int e = 0; e < MM; ++e) {
+                A[e].x = fma(p.x, f[e], A[e].x);
+                A[e].y = fma(p.y, f[e], A[e].y);
+            }
         }
     }
     double lam[NMAX];
@@ -323,15 +444,76 @@ void launch_eigs(epwi_ctx *c) {
     GridInfo g = make_grid_info(c);
     const int bs = 128;
     const unsigned nb = (unsigned)((nk + bs - 1) / bs);
+    const int64_t plane = (int64_t)g.n2 * g.n3;
+    // factorised build: axis-3 and axis-2 stages into fac_U (sources 0..nsrc-1), axis 1 in the
+    // eigensolve kernel
+    auto fac_sizes = [&](int rc, int E, bool vel, int64_t &nT, int64_t &nU) {
+        const int D = 2 * rc + 1;
+        nT = (int64_t)(vel ? 2 : 1) * D * D * g.n3 * E;
+        nU = (int64_t)(vel ? 3 : 1) * D * plane * E;
+    };
+    auto fac_stages = [&](const DevBuf &Xc, int rc, int E, bool vel) {
+        const int D = 2 * rc + 1;
+        const int64_t t3 = (int64_t)D * D * g.n3 * E, t2 = (int64_t)D * plane * E;
+        if (vel) {
+            k_fac_axis3<true><<<(unsigned)((t3 + 255) / 256), 256, 0, c->stream>>>(
+                D, rc, g.n3, g.s3, g.L, E, Xc.as<double2>(), c->ph64.as<double2>(), c->fac_T.as<double2>());
+            EPWI_CHECK_LAUNCH();
+            k_fac_axis2<true><<<(unsigned)((t2 + 255) / 256), 256, 0, c->stream>>>(
+                D, rc, g.n2, g.n3, g.s2, g.L, E, c->fac_T.as<double2>(), c->ph64.as<double2>(), c->fac_U.as<double2>());
+        } else {
+            k_fac_axis3<false><<<(unsigned)((t3 + 255) / 256), 256, 0, c->stream>>>(
+                D, rc, g.n3, g.s3, g.L, E, Xc.as<double2>(), c->ph64.as<double2>(), c->fac_T.as<double2>());
+            EPWI_CHECK_LAUNCH();
+            k_fac_axis2<false><<<(unsigned)((t2 + 255) / 256), 256, 0, c->stream>>>(
+                D, rc, g.n2, g.n3, g.s2, g.L, E, c->fac_T.as<double2>(), c->ph64.as<double2>(), c->fac_U.as<double2>());
+        }
+        EPWI_CHECK_LAUNCH();
+        FacDesc f;
+        f.U = c->fac_U.as<double2>();
+        f.D = D;
+        f.rc = rc;
+        f.plane = plane;
+        return f;
+    };
+    Lattice lat;
+    for (int i = 0; i < 9; ++i) lat.a[i / 3][i % 3] = c->lattice[i];
+    const bool fac_el = W <= 8 && c->fac_re_r >= 0, fac_ph = Nm <= 6 && c->fac_rp_r >= 0;
+    {
+        // both builds share the stage buffers: size them once, before any launch
+        int64_t nT = 1, nU = 1, t, u;
+        if (fac_el) {
+            fac_sizes(c->fac_re_r, W * W, true, t, u);
+            nT = std::max(nT, t);
+            nU = std::max(nU, u);
+        }
+        if (fac_ph) {
+            fac_sizes(c->fac_rp_r, Nm * Nm, false, t, u);
+            nT = std::max(nT, t);
+            nU = std::max(nU, u);
+        }
+        if (fac_el || fac_ph) {
+            c->fac_T.ensure(sizeof(double2) * nT);
+            c->fac_U.ensure(sizeof(double2) * nU);
+        }
+    }
+    FacDesc fe{}, fp{};
+    if (fac_el) fe = fac_stages(c->fac_Hc, c->fac_re_r, W * W, true);
 #define EL_ARGS                                                                              \
     g, nk, W, c->nRe, c->Re.as<int>(), c->Rcart.as<double>(), c->Hw.as<double2>(),            \
         c->ph64.as<double2>(), c->eps.as<double>(), c->eps32.as<float>(), c->V.as<double2>(), \
         c->V32.as<float2>(), c->vel.as<double>(), c->eig_flag.as<int>()
     const unsigned nbw = (unsigned)((nk + kWarpsPerBlock - 1) / kWarpsPerBlock);
-    if (W <= 1) k_eig_el<1><<<nb, bs, 0, c->stream>>>(EL_ARGS);
-    else if (W <= 4) k_eig_el<4><<<nb, bs, 0, c->stream>>>(EL_ARGS);
-    else if (W <= 8) k_eig_el<8><<<nb, bs, 0, c->stream>>>(EL_ARGS);
-    else {
+    if (W <= 1) {
+        if (fac_el) k_eig_el<1, true><<<nb, bs, 0, c->stream>>>(EL_ARGS, fe, lat);
+        else k_eig_el<1, false><<<nb, bs, 0, c->stream>>>(EL_ARGS, fe, lat);
+    } else if (W <= 4) {
+        if (fac_el) k_eig_el<4, true><<<nb, bs, 0, c->stream>>>(EL_ARGS, fe, lat);
+        else k_eig_el<4, false><<<nb, bs, 0, c->stream>>>(EL_ARGS, fe, lat);
+    } else if (W <= 8) {
+        if (fac_el) k_eig_el<8, true><<<nb, bs, 0, c->stream>>>(EL_ARGS, fe, lat);
+        else k_eig_el<8, false><<<nb, bs, 0, c->stream>>>(EL_ARGS, fe, lat);
+    } else {
         const size_t sm = warp_scratch_bytes(W);
         set_smem_once(k_eig_el_warp, sm);
         k_eig_el_warp<<<nbw, 32 * kWarpsPerBlock, sm, c->stream>>>(EL_ARGS);
@@ -343,9 +525,15 @@ void launch_eigs(epwi_ctx *c) {
         c->ph64.as<double2>(), c->opt.omega_min_eV, c->hw.as<double>(), c->hwmax32.as<float>(), \
         c->hw32.as<float>(),                                                                   \
         c->u.as<double2>(), c->u32.as<float2>(), c->eig_flag.as<int>() + 1
-    if (Nm <= 3) k_eig_ph<3><<<nb, bs, 0, c->stream>>>(PH_ARGS);
-    else if (Nm <= 6) k_eig_ph<6><<<nb, bs, 0, c->stream>>>(PH_ARGS);
-    else {
+    // the electron kernel above has read fac_U; the phonon stages reuse the buffers (same stream)
+    if (fac_ph) fp = fac_stages(c->fac_Pc, c->fac_rp_r, Nm * Nm, false);
+    if (Nm <= 3) {
+        if (fac_ph) k_eig_ph<3, true><<<nb, bs, 0, c->stream>>>(PH_ARGS, fp);
+        else k_eig_ph<3, false><<<nb, bs, 0, c->stream>>>(PH_ARGS, fp);
+    } else if (Nm <= 6) {
+        if (fac_ph) k_eig_ph<6, true><<<nb, bs, 0, c->stream>>>(PH_ARGS, fp);
+        else k_eig_ph<6, false><<<nb, bs, 0, c->stream>>>(PH_ARGS, fp);
+    } else {
         const size_t sm = warp_scratch_bytes(Nm);
         set_smem_once(k_eig_ph_warp, sm);
         k_eig_ph_warp<<<nbw, 32 * kWarpsPerBlock, sm, c->stream>>>(PH_ARGS);

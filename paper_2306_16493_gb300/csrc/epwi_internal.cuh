@@ -165,6 +165,11 @@ struct epwi_ctx {
     DevBuf gsf32;                  // fp32 mode: g' [Re][cube forms][Nm][W][W] (+-R recombined)
     bool sf_g_ready = false;       // gsf32 built for the current system
     DevBuf sf_Vt32;                // fp32 mode: float2 [Nk][m][i], V transposed
+    // factorised H(k) / D(q) builds: weighted H and Phi/sqrt(m m) embedded in the bounding cubes
+    // of the two R-sets (half-widths fac_re_r, fac_rp_r; -1: direct sums), stage buffers
+    int fac_re_r = -1, fac_rp_r = -1;
+    DevBuf fac_Hc, fac_Pc;         // double2 [Dc^3][W W], [Dc^3][Nm Nm]
+    DevBuf fac_T, fac_U;           // stage outputs (see eigs.cu)
     int64_t tc_arows_key = -1;
     bool tc_gather = false;        // use the gathered-A mode where it applies
     int64_t stats_tc_grid = 0;
@@ -201,7 +206,7 @@ struct epwi_ctx {
                          &tc_n32, &tc_hw32, &tc_err, &tc_meta, &is_pairs, &is_w,
                          &is_kp_pairs, &sieve_mask, &tc_arows, &ib_pairs, &ib_goff, &ib_gam,
                          &ib_kpos, &ib_F0, &ib_F, &ib_Fn, &ib_red, &ib_F32, &ib_Fn32, &sf_items,
-                         &gsf32, &sf_Vt32};
+                         &gsf32, &sf_Vt32, &fac_Hc, &fac_Pc, &fac_T, &fac_U};
         for (DevBuf *b : all) b->release();
         mlp_free(mlp);
     }
