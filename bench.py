@@ -36,11 +36,11 @@ DTYPE = {"fp64": "f64", "tf32x3": "tf32x3 (f32 acc, f64 sums)", "bf16x3": "bf16x
          "fp16x3": "fp16x3 (f32 acc, f64 sums)", "fp32": "f32 (sum-factorised, f64 sums)"}
 L2_BYTES = 129 * 2 ** 20
 # DRAM bytes (read + write) per (k,q) pair of the dominant kernel, from one ncu capture each:
-# k_scatter_tc (fp16x3) at 24^3, 255 MB / 19.6 M pairs (ncu --set full); k_scatter_sf (fp32)
-# at 32^3, 630.5 MB / 110.2 M pairs (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum).
-# Traffic grows with the pairs processed, so a launch's traffic is this times its pairs.
-# Valid for the kernel versions of those captures.
-TRAFFIC_BYTES_PER_PAIR = {"fp16x3": 13.0, "fp32": 5.72}
+# k_scatter_tc (fp16x3) at 24^3, 255 MB / 19.6 M pairs (ncu --set full); k_scatter_sf (fp32,
+# warp-owned runs) at 32^3, 628.6 + 4.2 MB / 110.2 M pairs (ncu --set full).  Traffic grows with
+# the pairs processed, so a launch's traffic is this times its pairs.  Valid for the kernel
+# versions of those captures.
+TRAFFIC_BYTES_PER_PAIR = {"fp16x3": 13.0, "fp32": 5.74}
 
 
 def peaks():
@@ -396,6 +396,7 @@ def run_gpu(args):
                 "gpu_launches": int(launches),
                 "stage_ms": {k: stats[k] for k in ("ms_eigs", "ms_sieve", "ms_restage", "ms_scatter", "ms_reduce")},
                 "roofline": roof, "clocks": clocks, "cpu_baseline": cpu,
+                "simt_peaks_tflops": {k: v[0] for k, v in simt.items()},
                 "error_vs_oracle": err_oracle, "fp64_gpu": fp64,
                 "e2e": None if args.no_e2e else
                        {"value": e2e_pairs / e2e_t, "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
