@@ -189,7 +189,8 @@ struct epwi_ctx {
     // iterative BTE: Gamma in pair blocks, mean free paths
     bool have_ibte = false;
     DevBuf ib_pairs;               // int32 q index per pair (all k-points of the window)
-    DevBuf ib_goff;                // int64 [npairs + 1] first Gamma entry of each pair
+    DevBuf ib_goff;                // int64 [npairs + 1] first Gamma entry of each pair (capture only)
+    DevBuf ib_wbase;               // int64 [nkp][8] first Gamma entry of each step warp range
     DevBuf ib_gam;                 // double (FP64 path) or float: per pair [n][m in window(k+q)]
     DevBuf ib_kpos;                // int32 [Nk] window k-point of each grid point, -1 outside
     DevBuf ib_F0, ib_F, ib_Fn;     // double [nstates][3] m: v tau, current and next iterate
@@ -205,7 +206,7 @@ struct epwi_ctx {
                          &scan_tmp, &red_tmp, &counts, &tc_ptab, &tc_erel, &tc_f32,
                          &tc_n32, &tc_hw32, &tc_err, &tc_meta, &is_pairs, &is_w,
                          &is_kp_pairs, &sieve_mask, &tc_arows, &ib_pairs, &ib_goff, &ib_gam,
-                         &ib_kpos, &ib_F0, &ib_F, &ib_Fn, &ib_red, &ib_F32, &ib_Fn32, &sf_items,
+                         &ib_kpos, &ib_F0, &ib_F, &ib_Fn, &ib_red, &ib_F32, &ib_Fn32, &sf_items, &ib_wbase,
                          &gsf32, &sf_Vt32, &fac_Hc, &fac_Pc, &fac_T, &fac_U};
         for (DevBuf *b : all) b->release();
         mlp_free(mlp);

@@ -9,7 +9,10 @@
 //
 // After the capture each pair's q index is replaced in place by a step code: the first state
 // of the final k-point's window (sb) and its band count (nw), (sb << 5) | nw.  The step then
-// reads one word per pair and needs no grid arithmetic or table lookups.
+// reads one word per pair and needs no grid arithmetic or table lookups.  The per-pair block
+// offsets are needed only by the capture: afterwards the step keeps one offset per (k-point,
+// warp range) (wbase) and the per-pair array is freed, so the resident index is the step code
+// per pair plus 64 bytes per k-point.
 //
 // Step: one block per window k-point, eight warps splitting its pairs into contiguous ranges,
 // the k-point's bands taken in register groups of 1, 2, 4 or 8 (the smallest that covers the
@@ -32,6 +35,19 @@ namespace {
 constexpr int kIbThreads = 256;
 constexpr int kIbWarps = kIbThreads / 32;
 constexpr int kIbMaxBands = 8;  // bands of k accumulated in registers at a time (at most)
+constexpr int kPpl = 2;         // narrow-window path: pairs per lane whose loads are in flight together
+
+// First Gamma entry of every (k-point, warp range) of k_ib_step (same range formula).
+__global__ void k_ib_wbase(int64_t nkp, const int64_t *__restrict__ kp_pairs, const int64_t *__restrict__ goff,
+                           int64_t *__restrict__ wbase) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nkp * kIbWarps) return;
+    const int64_t kp = t / kIbWarps;
+    const int w = (int)(t % kIbWarps);
+    const int64_t p0 = kp_pairs[kp], np = kp_pairs[kp + 1] - p0;
+    const int64_t wb = p0 + np * w / kIbWarps, we = p0 + np * (w + 1) / kIbWarps;
+    wbase[t] = wb < we ? goff[wb] : 0;
+}
 
 __global__ void k_ib_kpos(int64_t nkp, const int *__restrict__ kpts, int *__restrict__ kpos) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -85,7 +101,8 @@ __global__ void k_ib_f0(int64_t ns, int W, const int *__restrict__ st_k, const i
 template <typename GT>
 struct StepArgs {
     const int *kpts, *win_n;
-    const int64_t *kp_state, *kp_pairs, *goff;
+    const int64_t *kp_state, *kp_pairs;
+    const int64_t *wbase;                 // first Gamma entry of each (k-point, warp range)
     const unsigned *code;                 // per pair (sb << 5) | nw
     const GT *gam;
     const double *inv_tau, *F0, *Fin;
@@ -120,9 +137,8 @@ __device__ __forceinline__ void load_F(const StepArgs<float> &a, int64_t s, floa
 // pairs and final bands m of Gamma[b0+n][m] F_m.
 template <typename GT, int NB, int NBX>
 __device__ __forceinline__ void step_pairs(const StepArgs<GT> &a, int nsel, int b0, int64_t wb, int64_t we,
-                                           int lane, typename Acc<GT>::T (&y)[NB][3]) {
+                                           int64_t off, int lane, typename Acc<GT>::T (&y)[NB][3]) {
     using AT = typename Acc<GT>::T;
-    int64_t off = wb < we ? a.goff[wb] : 0;
     unsigned cnext = wb + lane < we ? __ldg(a.code + wb + lane) : 0u;
     for (int64_t pb = wb; pb < we; pb += 32) {
         const unsigned code = cnext;
@@ -158,9 +174,9 @@ __device__ __forceinline__ void step_pairs(const StepArgs<GT> &a, int nsel, int 
 // the pair's band count) before any multiply, so PPL x JMAX loads are in flight per lane.
 template <typename GT, int NB, int NBX, int JMAX, int PPL>
 __device__ __forceinline__ void step_pairs_narrow(const StepArgs<GT> &a, int nsel, int b0, int64_t wb,
-                                                  int64_t we, int lane, typename Acc<GT>::T (&y)[NB][3]) {
+                                                  int64_t we, int64_t off, int lane,
+                                                  typename Acc<GT>::T (&y)[NB][3]) {
     using AT = typename Acc<GT>::T;
-    int64_t off = wb < we ? a.goff[wb] : 0;
     unsigned cnext[PPL];
 #pragma unroll
     for (int i = 0; i < PPL; ++i) {
@@ -229,6 +245,7 @@ __global__ void __launch_bounds__(kIbThreads, kIbBands <= 2 ? 4 : (kIbBands <= 4
     const int64_t s0 = a.kp_state[kp];
     const int64_t p0 = a.kp_pairs[kp], np = a.kp_pairs[kp + 1] - p0;
     const int64_t wb = p0 + np * wid / kIbWarps, we = p0 + np * (wid + 1) / kIbWarps;
+    const int64_t off = a.wbase[(int64_t)kp * kIbWarps + wid];
     double dmax = 0, fmax_ = 0;
     for (int b0 = 0; b0 < nsel; b0 += kIbBands) {
         const int nb = min(kIbBands, nsel - b0);
@@ -241,16 +258,16 @@ __global__ void __launch_bounds__(kIbThreads, kIbBands <= 2 ? 4 : (kIbBands <= 4
         constexpr bool kNarrow = std::is_same<GT, float>::value && kIbBands == 4;
         if (kNarrow && a.narrow && nb <= 2) {
             if constexpr (kNarrow) {
-                if (nb == 1) step_pairs_narrow<GT, kIbBands, 1, 4, 2>(a, nsel, b0, wb, we, lane, y);
-                else step_pairs_narrow<GT, kIbBands, 2, 4, 2>(a, nsel, b0, wb, we, lane, y);
+                if (nb == 1) step_pairs_narrow<GT, kIbBands, 1, 4, kPpl>(a, nsel, b0, wb, we, off, lane, y);
+                else step_pairs_narrow<GT, kIbBands, 2, 4, kPpl>(a, nsel, b0, wb, we, off, lane, y);
             }
         } else switch (nb) {
-        case 1: step_pairs<GT, kIbBands, 1>(a, nsel, b0, wb, we, lane, y); break;
-        case 2: if constexpr (kIbBands >= 2) step_pairs<GT, kIbBands, 2>(a, nsel, b0, wb, we, lane, y); break;
-        case 3: if constexpr (kIbBands >= 3) step_pairs<GT, kIbBands, 3>(a, nsel, b0, wb, we, lane, y); break;
-        case 4: if constexpr (kIbBands >= 4) step_pairs<GT, kIbBands, 4>(a, nsel, b0, wb, we, lane, y); break;
+        case 1: step_pairs<GT, kIbBands, 1>(a, nsel, b0, wb, we, off, lane, y); break;
+        case 2: if constexpr (kIbBands >= 2) step_pairs<GT, kIbBands, 2>(a, nsel, b0, wb, we, off, lane, y); break;
+        case 3: if constexpr (kIbBands >= 3) step_pairs<GT, kIbBands, 3>(a, nsel, b0, wb, we, off, lane, y); break;
+        case 4: if constexpr (kIbBands >= 4) step_pairs<GT, kIbBands, 4>(a, nsel, b0, wb, we, off, lane, y); break;
         default:
-            if constexpr (kIbBands > 4) step_pairs<GT, kIbBands, kIbBands>(a, nsel, b0, wb, we, lane, y);
+            if constexpr (kIbBands > 4) step_pairs<GT, kIbBands, kIbBands>(a, nsel, b0, wb, we, off, lane, y);
             break;
         }
         // lanes: butterfly in the accumulation type; warps: FP64 in index order
@@ -296,7 +313,7 @@ void launch_step(epwi_ctx *c, const double *Fin, double *Fout, const float4 *Fin
     a.win_n = c->win_n.as<int>();
     a.kp_state = c->kp_state.as<int64_t>();
     a.kp_pairs = c->kp_pairs.as<int64_t>();
-    a.goff = c->ib_goff.as<int64_t>();
+    a.wbase = c->ib_wbase.as<int64_t>();
     a.code = c->ib_pairs.as<unsigned>();
     a.gam = c->ib_gam.as<GT>();
     a.inv_tau = c->inv_tau.as<double>();
@@ -377,8 +394,18 @@ void ibte_iterate(epwi_ctx *c, int max_iter, double tol) {
         c->ib_Fn32.ensure(sizeof(float4) * (ns + 1));
     }
     c->ib_red.ensure(sizeof(unsigned long long) * 2);
-    // the captured pairs' q indices become step codes (the capture is done with them)
+    // the captured pairs' q indices become step codes (the capture is done with them), and the
+    // per-pair offsets become one offset per (k-point, warp range)
     EPWI_REQUIRE(ns < (int64_t(1) << 27), EPWI_EUNSUPPORTED, "iterative BTE needs fewer than 2^27 states");
+    c->ib_wbase.ensure(sizeof(int64_t) * (c->nkp * kIbWarps + 1));
+    if (c->nkp > 0) {
+        const int64_t nt = c->nkp * kIbWarps;
+        k_ib_wbase<<<(unsigned)((nt + 255) / 256), 256, 0, c->stream>>>(
+            c->nkp, c->kp_pairs.as<int64_t>(), c->ib_goff.as<int64_t>(), c->ib_wbase.as<int64_t>());
+        EPWI_CHECK_LAUNCH();
+    }
+    EPWI_CUDA(cudaStreamSynchronize(c->stream));
+    c->ib_goff.release();
     if (c->nkp > 0) {
         k_ib_encode<<<(unsigned)c->nkp, 256, 0, c->stream>>>(
             make_grid_info(c), c->kpts.as<int>(), c->win_n.as<int>(), c->ib_kpos.as<int>(),
