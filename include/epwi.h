@@ -126,6 +126,8 @@ typedef struct {
     double ms_proposal;         /* importance sampling: network scores and cell tables */
     double ms_sampling;         /* importance sampling: draws, merge and weights */
     double proposal_flops;      /* importance sampling: network flops (2 per multiply-add) */
+    int64_t sym_kpoints;        /* symmetry-reduced call: k-points computed (star representatives), else 0 */
+    int64_t sym_states;         /* symmetry-reduced call: states computed, else 0 */
 } epwi_stats;
 
 /* Statistics of the last epwi_ibte. */
@@ -208,6 +210,22 @@ epwi_status epwi_carrier_density(epwi_ctx *ctx, double T_K, double mu_eV, int32_
 epwi_status epwi_scatter_rates(epwi_ctx *ctx, double T_K, double mu_eV, double smear_eV,
                                double emin_eV, double emax_eV,
                                int64_t *n_states, int64_t *n_pairs);
+
+/* Point-group symmetry of the crystal for epwi_scatter_rates: the symmetry-reduced k grids of
+ * the paper's preprocessing (Sec. III A).  kops: nops integer 3x3 matrices (row-major) acting
+ * on grid index vectors, k -> K k modulo N (for lattice operations n -> M n on the lattice
+ * coordinates of the R-sets, K = M^-T).  They must form a group (identity and closure;
+ * nops <= 48); nops = 0 switches the reduction off.  Copied.
+ * With operations set, epwi_scatter_rates needs an N x N x N grid, checks on the device that
+ * eps and hbar omega are invariant on the grid (max |eps(Kk) - eps(k)| <= 1e-9 max(1, |eps|),
+ * |omega(Kq) - omega(q)| <= 1e-9 eV; EINVAL otherwise), computes the sieve and 1/tau only for
+ * the window k-points that represent their star (the lowest grid index), and gives every
+ * member of a star its representative's band window and rates.  epwi_get_rates then returns
+ * every window state; sigma, mobility and transport sum over all of them with each state's own
+ * velocity.  n_pairs counts the pairs computed; epwi_stats.sym_kpoints / sym_states the
+ * representatives.  The iterative BTE refuses to run with operations set (EUNSUPPORTED), and
+ * epwi_get_sieve after a reduced call too.  Errors: EINVAL (nops, NULL kops, not a group). */
+epwi_status epwi_set_symmetry(epwi_ctx *ctx, int32_t nops, const int32_t *kops);
 
 /* Copies the states of the last epwi_scatter_rates (ordered by k index, then band) and
  * their rates to host arrays of capacity >= n_states.  Any output pointer may be NULL.

@@ -451,7 +451,8 @@ namespace {
 
 // Window, sieve count, occupation tables and the work set of a rates call (Sec. III A);
 // 1/tau is zeroed.
-WorkSet begin_rates(epwi_ctx *c, double T, double mu, double eta, double emin, double emax) {
+WorkSet begin_rates(epwi_ctx *c, double T, double mu, double eta, double emin, double emax,
+                    bool sym = false) {
     require_eigs(c);
     EPWI_REQUIRE(T > 0 && eta > 0 && std::isfinite(mu) && !(emin > emax), EPWI_EINVAL,
                  "need T > 0, smear > 0, finite mu and emin <= emax");
@@ -469,7 +470,8 @@ WorkSet begin_rates(epwi_ctx *c, double T, double mu, double eta, double emin, d
     EPWI_CUDA(cudaEventCreate(&e0));
     EPWI_CUDA(cudaEventCreate(&e1));
     cudaEventRecord(e0, c->stream);
-    build_window(c);
+    if (sym) sym_prepare(c);                 // representatives of the stars; invariance check
+    build_window(c, sym ? c->sym_rep.as<int>() : nullptr);
     sieve_count(c);
     cudaEventRecord(e1, c->stream);
     EPWI_CUDA(cudaStreamSynchronize(c->stream));
@@ -551,12 +553,22 @@ epwi_status epwi_scatter_rates(epwi_ctx *c, double T, double mu, double eta, dou
         EPWI_REQUIRE(c->opt.ordering == 0 || c->opt.ordering == 1, EPWI_EINVAL, "ordering must be 0 or 1");
         EPWI_REQUIRE(c->opt.ordering == 0 || c->opt.precision == EPWI_FP64, EPWI_EUNSUPPORTED,
                      "the k-batch ordering is FP64 only");
-        WorkSet ws = begin_rates(c, T, mu, eta, emin, emax);
+        const bool sym = !c->sym_ops.empty();
+        WorkSet ws = begin_rates(c, T, mu, eta, emin, emax, sym);
         if (c->opt.ordering == 1) process_kbatch(c);
         else process_workset(c, ws, nullptr);
         end_rates(c);
         if (c->opt.ordering == 1)      // per pair: n_Re x N_m x W x W complex MACs instead
             c->stats.scatter_flops = 8.0 * c->nRe * c->nm * c->nw * c->nw * (double)c->npairs;
+        if (sym) {
+            // rates of the representatives -> every window state (Sec. III A symmetry)
+            c->stats.sym_kpoints = c->nkp;
+            c->stats.sym_states = c->nstates;
+            sym_expand(c);
+            c->sym_used = true;
+            c->stats.n_kpoints = c->nkp;
+            c->stats.n_states = c->nstates;
+        }
         if (n_states) *n_states = c->nstates;
         if (n_pairs) *n_pairs = c->npairs;
     });
@@ -567,6 +579,8 @@ epwi_status epwi_ibte(epwi_ctx *c, double T, double mu, double eta, double emin,
     return guard(c, [&] {
         EPWI_REQUIRE(max_iter >= 0 && tol >= 0 && std::isfinite(tol), EPWI_EINVAL,
                      "need max_iter >= 0 and a finite tol >= 0");
+        EPWI_REQUIRE(c->sym_ops.empty(), EPWI_EUNSUPPORTED,
+                     "the iterative BTE couples every k-point: clear the symmetry operations first");
         cudaEvent_t e0, e1;
         EPWI_CUDA(cudaEventCreate(&e0));
         EPWI_CUDA(cudaEventCreate(&e1));
@@ -728,6 +742,8 @@ epwi_status epwi_get_sieve(epwi_ctx *c, int64_t cap, int32_t *kpts, int64_t *cou
     return guard(c, [&] {
         require_rates(c);
         EPWI_REQUIRE(!c->have_is, EPWI_ESTATE, "the last rates came from importance sampling");
+        EPWI_REQUIRE(!c->sym_used, EPWI_EUNSUPPORTED,
+                     "the last rates were computed per star: the sieve lists are those of the representatives");
         EPWI_REQUIRE(cap >= c->nkp, EPWI_ETOOSMALL, "capacity below n_kpoints");
         if (kpts && c->nkp)
             EPWI_CUDA(cudaMemcpyAsync(kpts, c->kpts.p, 4 * (size_t)c->nkp, cudaMemcpyDeviceToHost, c->stream));

@@ -191,6 +191,11 @@ struct epwi_ctx {
     DevBuf ib_pairs;               // int32 q index per pair (all k-points of the window)
     DevBuf ib_goff;                // int64 [npairs + 1] first Gamma entry of each pair (capture only)
     DevBuf ib_wbase;               // int64 [nkp][8] first Gamma entry of each step warp range
+
+    // point-group symmetry of the rates (epwi_set_symmetry, sym.cu)
+    std::vector<int> sym_ops;      // [nops][3][3] k-space operations on grid index vectors
+    DevBuf sym_rep;                // int [Nk]: representative (lowest index) of each star
+    bool sym_used = false;         // the last rates call computed representatives only
     DevBuf ib_gam;                 // double (FP64 path) or float: per pair [n][m in window(k+q)]
     DevBuf ib_kpos;                // int32 [Nk] window k-point of each grid point, -1 outside
     DevBuf ib_F0, ib_F, ib_Fn;     // double [nstates][3] m: v tau, current and next iterate
@@ -206,7 +211,7 @@ struct epwi_ctx {
                          &scan_tmp, &red_tmp, &counts, &tc_ptab, &tc_erel, &tc_f32,
                          &tc_n32, &tc_hw32, &tc_err, &tc_meta, &is_pairs, &is_w,
                          &is_kp_pairs, &sieve_mask, &tc_arows, &ib_pairs, &ib_goff, &ib_gam,
-                         &ib_kpos, &ib_F0, &ib_F, &ib_Fn, &ib_red, &ib_F32, &ib_Fn32, &sf_items, &ib_wbase,
+                         &ib_kpos, &ib_F0, &ib_F, &ib_Fn, &ib_red, &ib_F32, &ib_Fn32, &sf_items, &ib_wbase, &sym_rep,
                          &gsf32, &sf_Vt32, &fac_Hc, &fac_Pc, &fac_T, &fac_U};
         for (DevBuf *b : all) b->release();
         mlp_free(mlp);
@@ -289,7 +294,15 @@ void launch_eigs(epwi_ctx *c);
 void scan_exclusive_i64(epwi_ctx *c, const int64_t *in, int64_t *out, int64_t n, int64_t *total);
 double device_reduce_minmax(epwi_ctx *c, const double *x, int64_t n, int64_t stride, int64_t off,
                             bool want_max);
-void build_window(epwi_ctx *c);
+// Window of the current rates call: lo/count per k from eps, then the lists of k-points and
+// states.  rep (optional, symmetry): only k-points that represent their star take part.
+void build_window(epwi_ctx *c, const int *rep = nullptr);
+// The k-point and state lists from the current win_lo / win_n (rep as above).
+void window_lists(epwi_ctx *c, const int *rep = nullptr);
+// Point-group symmetry (sym.cu): representatives and invariance check of the current grid, and
+// the expansion of the representatives' rates to every window state.
+void sym_prepare(epwi_ctx *c);
+void sym_expand(epwi_ctx *c);
 void sieve_count(epwi_ctx *c);
 void occupation_tables(epwi_ctx *c);
 void run_scatter(epwi_ctx *c);

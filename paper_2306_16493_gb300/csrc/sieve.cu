@@ -77,8 +77,7 @@ __global__ void k_scan_apply(const int64_t *in, int64_t n, const int64_t *boff, 
 
 // ------------------------------------------------------------------- window / k_eff
 __global__ void k_window(int64_t nk, int W, const double *__restrict__ eps, double emin,
-                         double emax, int *__restrict__ lo, int *__restrict__ cnt,
-                         int64_t *__restrict__ flag) {
+                         double emax, int *__restrict__ lo, int *__restrict__ cnt) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nk) return;
     int l = 0;
@@ -87,14 +86,24 @@ __global__ void k_window(int64_t nk, int W, const double *__restrict__ eps, doub
     while (h < W && eps[k * W + h] <= emax) ++h;
     lo[k] = l;
     cnt[k] = h - l;
-    flag[k] = (h > l) ? 1 : 0;
+}
+
+// k-points that take part: a window state, and (with symmetry) the representative of its star
+__device__ __forceinline__ bool window_kpoint(int64_t k, const int *cnt, const int *rep) {
+    return cnt[k] > 0 && (!rep || rep[k] == (int)k);
+}
+
+__global__ void k_window_flags(int64_t nk, const int *__restrict__ cnt, const int *__restrict__ rep,
+                               int64_t *__restrict__ flag) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nk) flag[k] = window_kpoint(k, cnt, rep) ? 1 : 0;
 }
 
 __global__ void k_compact_kpts(int64_t nk, const int64_t *__restrict__ pos,
-                               const int *__restrict__ cnt, int *__restrict__ kpts,
+                               const int *__restrict__ cnt, const int *__restrict__ rep, int *__restrict__ kpts,
                                int64_t *__restrict__ nsel) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nk || cnt[k] == 0) return;
+    if (k >= nk || !window_kpoint(k, cnt, rep)) return;
     kpts[pos[k]] = (int)k;
     nsel[pos[k]] = cnt[k];
 }
@@ -443,16 +452,24 @@ void scan_exclusive_i64(epwi_ctx *c, const int64_t *in, int64_t *out, int64_t n,
     bo.release();
 }
 
-void build_window(epwi_ctx *c) {
+void build_window(epwi_ctx *c, const int *rep) {
     const int64_t nk = c->nk;
+    c->sym_used = false;
     c->win_lo.ensure(sizeof(int) * nk);
     c->win_n.ensure(sizeof(int) * nk);
+    const unsigned nb = (unsigned)((nk + 255) / 256);
+    k_window<<<nb, 256, 0, c->stream>>>(nk, c->nw, c->eps.as<double>(), c->emin, c->emax,
+                                       c->win_lo.as<int>(), c->win_n.as<int>());
+    EPWI_CHECK_LAUNCH();
+    window_lists(c, rep);
+}
+
+void window_lists(epwi_ctx *c, const int *rep) {
+    const int64_t nk = c->nk;
     c->counts.ensure(sizeof(int64_t) * (nk + 1));
     c->scan_tmp.ensure(sizeof(int64_t) * (nk + 1));
     const unsigned nb = (unsigned)((nk + 255) / 256);
-    k_window<<<nb, 256, 0, c->stream>>>(nk, c->nw, c->eps.as<double>(), c->emin, c->emax,
-                                       c->win_lo.as<int>(), c->win_n.as<int>(),
-                                       c->counts.as<int64_t>());
+    k_window_flags<<<nb, 256, 0, c->stream>>>(nk, c->win_n.as<int>(), rep, c->counts.as<int64_t>());
     EPWI_CHECK_LAUNCH();
     int64_t nkp = 0;
     scan_exclusive_i64(c, c->counts.as<int64_t>(), c->scan_tmp.as<int64_t>(), nk, &nkp);
@@ -460,7 +477,7 @@ void build_window(epwi_ctx *c) {
     c->kpts.ensure(sizeof(int) * (nkp + 1));
     c->kp_state.ensure(sizeof(int64_t) * (nkp + 1));
     // reuse counts as the per-kp band count
-    k_compact_kpts<<<nb, 256, 0, c->stream>>>(nk, c->scan_tmp.as<int64_t>(), c->win_n.as<int>(),
+    k_compact_kpts<<<nb, 256, 0, c->stream>>>(nk, c->scan_tmp.as<int64_t>(), c->win_n.as<int>(), rep,
                                              c->kpts.as<int>(), c->counts.as<int64_t>());
     EPWI_CHECK_LAUNCH();
     int64_t nst = 0;

@@ -55,7 +55,7 @@ class epwi_stats(C.Structure):
                 ("tc_grid", C.c_int64), ("tc_ctas_per_sm", C.c_int32), ("tc_regs", C.c_int32),
                 ("tc_smem", C.c_int64), ("tc_smem_avail2", C.c_int64),
                 ("ms_proposal", C.c_double), ("ms_sampling", C.c_double),
-                ("proposal_flops", C.c_double)]
+                ("proposal_flops", C.c_double), ("sym_kpoints", C.c_int64), ("sym_states", C.c_int64)]
 
 
 class epwi_ibte_stats(C.Structure):
@@ -117,6 +117,7 @@ def _load() -> C.CDLL:
         "epwi_get_stats": (I32, [P, P]),
         "epwi_kernel_launches": (I64, []),
         "epwi_fma_peak": (I32, [I32, I32, P, D, P, P]),
+        "epwi_set_symmetry": (I32, [P, I32, P]),
         "epwi_conductivity_noalloc": (I32, [I64, P, P, P, D, D, D, I64, P, P]),
         "epwi_mlp_default_train_options": (V, [P]),
         "epwi_mlp_train": (I32, [P, D, D, D, D, D, P, P]),
@@ -632,6 +633,11 @@ class Context:
 
     def phonons(self):
         return epwi_get_phonons(self.h, self.nk, self.nm)
+
+    def set_symmetry(self, kops):
+        """Point-group operations on grid index vectors ([nops][3][3] int), or None to clear."""
+        ops = np.ascontiguousarray(np.zeros((0, 3, 3)) if kops is None else kops, dtype=np.int32)
+        _check(self.h, _lib.epwi_set_symmetry(self.h, int(len(ops)), _ptr(ops) if len(ops) else None))
 
     def sieve(self):
         st = self.stats()

@@ -372,6 +372,62 @@ def al_like_ws_system(seed: int = 2, nsc: int = 4) -> System:
     return make_system("al_like_ws", lat, tau, 27.0, 4, 0, False, seed, 0.040, rset=ws_rset(lat, nsc))
 
 
+def point_group(lat) -> list:
+    """The lattice's point group as integer matrices M acting on lattice coordinates (n -> M n,
+    columns): every M with entries in {-1, 0, 1}, |det M| = 1 and M^T G M = G for the metric
+    G = A A^T (A rows = a_1, a_2, a_3).  48 matrices for fcc and simple cubic."""
+    lat = np.asarray(lat, float)
+    G = lat @ lat.T
+    ops = []
+    for e in np.ndindex(*(3,) * 9):
+        M = np.array(e).reshape(3, 3) - 1
+        if round(abs(np.linalg.det(M))) == 1 and np.allclose(M.T @ G @ M, G, atol=1e-9 * np.abs(G).max()):
+            ops.append(M.astype(np.int64))
+    return ops
+
+
+def kpoint_ops(ops) -> np.ndarray:
+    """The k-space action of lattice operations M: fractional k -> M^{-T} k (integer for a
+    unimodular M), so that e^{2 pi i k.n} is invariant when n -> M n.  [nops][3][3] int32."""
+    return np.array([np.rint(np.linalg.inv(M).T).astype(np.int32) for M in ops])
+
+
+def symmetrize(sysm: System, ops) -> System:
+    """The crystal made invariant under the lattice operations ``ops`` (a group; one atom at the
+    origin, s-like Wannier functions): H(R) is averaged over each orbit, H(M R) = H(R);
+    Phi(M R) = S Phi(R) S^T and g_mu(M Re, M Rp) = sum_nu S_mu,nu g_nu(Re, Rp) with the Cartesian
+    rotation S = A^T M A^{-T}, made exact by group averaging.  Both R-sets must be closed under
+    the group with invariant weights (a Wigner-Seitz set is).  Averaging keeps Hermiticity, the
+    acoustic sum rule and Phi(-R) = Phi(R)^T."""
+    if sysm.nat != 1:
+        raise ValueError("symmetrize: one atom at the origin only")
+    A = sysm.lattice
+    S = [A.T @ M @ np.linalg.inv(A.T) for M in ops]
+
+    def index(R):
+        lut = {tuple(v): i for i, v in enumerate(R.tolist())}
+        idx = []
+        for M in ops:
+            idx.append(np.array([lut[tuple((M @ v).tolist())] for v in R]))
+        return idx
+    ie, ip = index(sysm.Re), index(sysm.Rp)
+    for k in range(len(ops)):
+        if not (np.allclose(sysm.we[ie[k]], sysm.we) and np.allclose(sysm.wp[ip[k]], sysm.wp)):
+            raise ValueError("symmetrize: weights are not invariant")
+    H = sum(sysm.H[ie[k]] for k in range(len(ops))) / len(ops)
+    Phi = sum(np.einsum("ba,rbc,cd->rad", S[k], sysm.Phi[ip[k]], S[k]) for k in range(len(ops))) / len(ops)
+    g = sum(np.einsum("ba,rpbij->rpaij", S[k], sysm.g[ie[k]][:, ip[k]]) for k in range(len(ops))) / len(ops)
+    return dataclasses.replace(sysm, name=sysm.name + "_sym", H=H, Phi=Phi, g=g)
+
+
+def al_like_sym_system(seed: int = 2) -> System:
+    """The Wigner-Seitz Al-like metal (``al_like_ws_system``) made invariant under the 48
+    operations of the fcc point group (``symmetrize``): eps(M^{-T} k) = eps(k) and the SERTA
+    rates are equal on every star of k-points."""
+    s = al_like_ws_system(seed)
+    return symmetrize(s, point_group(s.lattice))
+
+
 def si_like_system(seed: int = 3) -> System:
     """Diamond Si-like semiconductor: nw = 8 (4 valence + 4 conduction), 6 modes, 7^3 R."""
     lat, tau = diamond_cell(5.43)

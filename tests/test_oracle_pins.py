@@ -416,3 +416,25 @@ def test_oracle_matches_stored_golden_values():
     sig, S, kap = O.transport_coefficients(s.volume, gr.nk, v, r["inv_tau"], gr.eps[r["ik"], r["n"]], mu, T)
     for name, t in (("sigma", sig), ("seebeck", S), ("kappa_e", kap)):
         assert np.linalg.norm(t.ravel() - meta[name]) <= 1e-9 * np.linalg.norm(meta[name]), name
+
+
+def test_serta_rates_are_invariant_on_the_stars_of_a_symmetric_crystal():
+    """Pins the symmetry reduction (Sec. III A): on the crystal symmetrised under the fcc point
+    group, the oracle's full-grid 1/tau_n(K k) equals 1/tau_n(k) for all 48 k-space operations
+    K (degenerate-group sums), and sigma of the cubic crystal is isotropic."""
+    s = synth.al_like_sym_system()
+    N, T, eta = 6, 300.0, 0.05
+    gr = O.Grids(s, (N, N, N))
+    mu = gr.band_centre()
+    r = O.serta(gr, T, mu, eta, mu - 0.5, mu + 0.5)
+    rate = {(int(k), int(n)): v for k, n, v in zip(r["ik"], r["n"], r["inv_tau"])}
+    idx = O.grid_indices((N, N, N))
+    worst = 0.0
+    for K in synth.kpoint_ops(synth.point_group(s.lattice)):
+        j = O.flat_index((idx @ K.T) % N, (N, N, N))
+        for (k, n), v in rate.items():
+            worst = max(worst, abs(rate[(int(j[k]), n)] - v) / v)
+    assert worst < 1e-10
+    v = gr.velocities(r["ik"], r["n"])
+    sig = O.conductivity(s.volume, gr.nk, v, r["inv_tau"], gr.eps[r["ik"], r["n"]], mu, T)
+    assert np.allclose(sig, np.trace(sig) / 3 * np.eye(3), rtol=0, atol=1e-10 * np.abs(sig).max())

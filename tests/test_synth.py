@@ -52,3 +52,29 @@ def test_wigner_seitz_set_is_a_weighted_set_of_supercell_representatives(cell, n
     for t in itertools.product((-1, 0, 1), repeat=3):
         img = R + nsc * (np.array(t) @ cell)
         assert np.all(np.linalg.norm(R, axis=1) <= np.linalg.norm(img, axis=1) + 1e-9)
+
+
+def test_point_group_and_symmetric_crystal():
+    """The fcc point group in lattice coordinates has 48 operations and is closed; the
+    symmetrised Al-like crystal has eps(K k) = eps(k) and omega(K q) = omega(q) on a grid for
+    every k-space operation K = M^-T, while the crystal before symmetrisation does not (so the
+    check can fail)."""
+    from oracle import epwi_oracle as O
+    lat = synth.fcc_cell(4.05)[0]
+    ops = synth.point_group(lat)
+    assert len(ops) == 48
+    keys = {tuple(M.ravel()) for M in ops}
+    assert all(tuple((A @ B).ravel()) in keys for A in ops for B in ops)
+    K = synth.kpoint_ops(ops)
+    N = 6
+    idx = O.grid_indices((N, N, N))
+
+    def worst(sysm):
+        gr = O.Grids(sysm, (N, N, N))
+        e = 0.0
+        for k in K:
+            j = O.flat_index((idx @ k.T) % N, (N, N, N))
+            e = max(e, np.abs(gr.eps[j] - gr.eps).max(), np.abs(gr.hw[j] - gr.hw).max())
+        return e
+    assert worst(synth.al_like_sym_system()) < 1e-12
+    assert worst(synth.al_like_ws_system()) > 1e-3
