@@ -785,6 +785,76 @@ def run_si(args):
     print(json.dumps(line), flush=True)
 
 
+def run_sym(args):
+    """Symmetry-reduced k grid (Sec. III A) on the Al-like crystal symmetrised under the fcc
+    point group (48 operations): one step = eigs -> window -> sieve + rates for one k-point per
+    star -> expansion to every window state -> sigma, timed against the same step on the full
+    grid (both in the chosen precision)."""
+    import torch
+    from paper_2306_16493_gb300 import epwi, synth
+    torch.cuda.set_device(0)
+    s = synth.al_like_sym_system(WORKLOAD["seed"])
+    kops = synth.kpoint_ops(synth.point_group(s.lattice))
+    N = args.grid
+    T, eta, win = WORKLOAD["T_K"], WORKLOAD["smear_eV"], WORKLOAD["window_eV"]
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    res = {}
+    for mode in ("full", "reduced"):
+        ctx = epwi.Context(precision=args.precision, device=0, stream=stream.cuda_stream)
+        ctx.setup(s)
+        if mode == "reduced":
+            ctx.set_symmetry(kops)
+
+        def step():
+            ctx.eigs(N)
+            lo, hi = ctx.band_range()
+            mu = 0.5 * (lo + hi)
+            _, npairs = ctx.scatter_rates(T, mu, eta, mu - win, mu + win)
+            return npairs, ctx.conductivity()
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        with ClockSampler(os.path.join(tempfile.gettempdir(), f"epwi_clocks_{os.getpid()}_{mode}.csv")) as cs:
+            time.sleep(0.3)
+            for k in range(args.steps):
+                flush.zero_()
+                ev[k][0].record(stream)
+                npairs, sig = step()
+                ev[k][1].record(stream)
+            torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+        st = ctx.stats()
+        k_, b_, r_ = ctx.rates()
+        res[mode] = {"time_to_sigma_ms": ms, "pairs_computed": int(npairs), "n_states": st["n_states"],
+                     "states_computed": st["sym_states"] or st["n_states"], "stage_ms": {
+                         x: st[x] for x in ("ms_eigs", "ms_sieve", "ms_restage", "ms_scatter")},
+                     "sigma": sig, "rates": (k_, b_, r_), "eps": ctx.bands()[0], "clocks": cs.summary(0)}
+        ctx.close()
+    f, r = res["full"], res["reduced"]
+    err, ng = group_rel_error(r["rates"][0], r["rates"][1], r["rates"][2], f["rates"][0], f["rates"][1],
+                              f["rates"][2], f["eps"])
+    for m in res.values():
+        for key in ("rates", "eps"):
+            m.pop(key)
+    sig_err = float(np.linalg.norm(r["sigma"] - f["sigma"]) / np.linalg.norm(f["sigma"]))
+    for m in res.values():
+        m["sigma_diag_S_per_m"] = [float(m["sigma"][i, i]) for i in range(3)]
+        m.pop("sigma")
+    line = {"metric": "time-to-sigma with the symmetry-reduced k grid vs the full grid",
+            "value": f["time_to_sigma_ms"] / r["time_to_sigma_ms"], "unit": "x", "higher_is_better": True,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "dtype": DTYPE[args.precision],
+            "data": "synthetic", "vs_baseline": None,
+            "config": {"workload": f"al_like_sym_{N}", "system": "Al-like fcc, nw=4, 3 modes, Wigner-Seitz R-sets "
+                       "of the 4^3 supercell (93 vectors), symmetrised under the 48 operations of Oh",
+                       "grid": N, "window_eV": win, "smear_eV": eta, "T_K": T, "precision": args.precision,
+                       "operations": len(kops), "l2": "flushed between timed steps (256 MiB write)"},
+            "full": f, "reduced": r, "rate_max_rel_error_reduced_vs_full": err, "rate_groups_compared": ng,
+            "sigma_rel_frobenius_reduced_vs_full": sig_err}
+    print(json.dumps(line), flush=True)
+
+
 def run_kbatch(args):
     """Ordering ablation (Sec. III C, Table 3): the same FP64 rates call with the q-batch and
     the k-batch interpolation order on the Al-like metal."""
@@ -854,8 +924,8 @@ def main():
     ap.add_argument("--no-fp64-leg", action="store_true", help="skip the FP64 GPU comparison step")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (large one-off grids)")
     ap.add_argument("--workload", default="al_like",
-                    choices=["al_like", "si_like", "batch64", "si_like_learned", "al_like_ibte",
-                             "ordering_ablation"],
+                    choices=["al_like", "si_like", "al_like_sym", "batch64", "si_like_learned",
+                             "al_like_ibte", "ordering_ablation"],
                     help="al_like: the benchmark; batch64 and si_like_learned: the batched and "
                          "learned-proposal workloads (reported separately)")
     ap.add_argument("--batch-scale", type=int, default=3, help="batch64: grid divisor")
@@ -884,6 +954,8 @@ def main():
         run_kbatch(args)
     elif args.workload == "si_like":
         run_si(args)
+    elif args.workload == "al_like_sym":
+        run_sym(args)
     else:
         run_gpu(args)
 
