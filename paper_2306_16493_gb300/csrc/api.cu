@@ -370,6 +370,7 @@ epwi_status epwi_eigs(epwi_ctx *c, const int32_t kgrid[3], const int32_t qgrid[3
         c->have_eigs = c->have_rates = c->have_sigma = false;
         c->tc_ptab_key = -1;
         c->tc_arows_key = -1;
+        c->seg_ready = false;
         for (int a = 0; a < 3; ++a) c->ng[a] = kgrid[a];
         c->nk = nk;
         c->L = (int)L;

@@ -195,6 +195,10 @@ struct epwi_ctx {
     // point-group symmetry of the rates (epwi_set_symmetry, sym.cu)
     std::vector<int> sym_ops;      // [nops][3][3] k-space operations on grid index vectors
     DevBuf sym_rep;                // int [Nk]: representative (lowest index) of each star
+    // sieve pruning table (sieve.cu): band ranges per column segment, built once per eigs call
+    DevBuf seg_ranges;
+    bool seg_ready = false;
+    double hw_max = 0;             // largest mode energy on the grid
     bool sym_used = false;         // the last rates call computed representatives only
     DevBuf ib_gam;                 // double (FP64 path) or float: per pair [n][m in window(k+q)]
     DevBuf ib_kpos;                // int32 [Nk] window k-point of each grid point, -1 outside
@@ -211,7 +215,7 @@ struct epwi_ctx {
                          &scan_tmp, &red_tmp, &counts, &tc_ptab, &tc_erel, &tc_f32,
                          &tc_n32, &tc_hw32, &tc_err, &tc_meta, &is_pairs, &is_w,
                          &is_kp_pairs, &sieve_mask, &tc_arows, &ib_pairs, &ib_goff, &ib_gam,
-                         &ib_kpos, &ib_F0, &ib_F, &ib_Fn, &ib_red, &ib_F32, &ib_Fn32, &sf_items, &ib_wbase, &sym_rep,
+                         &ib_kpos, &ib_F0, &ib_F, &ib_Fn, &ib_red, &ib_F32, &ib_Fn32, &sf_items, &ib_wbase, &sym_rep, &seg_ranges,
                          &gsf32, &sf_Vt32, &fac_Hc, &fac_Pc, &fac_T, &fac_U};
         for (DevBuf *b : all) b->release();
         mlp_free(mlp);

@@ -20,7 +20,15 @@ struct SieveArgs {
     double omega_min, ceta;
     float ceta32, delta32;   // delta32 bounds |x_fp32 - x_fp64| for every candidate
     float lim_extra;         // c eta + delta32
+    // pruning table: band energy ranges (min, max; FP32) over aligned segments of kSegLen
+    // consecutive points along axis 1 of every (axis 2, axis 3) column of the grid,
+    // segr[((col * nseg) + seg) * W + m]; seglim bounds hwmax(q) + the prefilter's pad
+    const float2 *segr;
+    int nseg;
+    float seglim;
 };
+constexpr int kSegLen = 8;
+constexpr int kSegMinGrid = 64;   // grids with fewer axis-1 points skip the table
 
 // Decision for one candidate (k, q).  FP32 evaluates x = (e_n + s w) - e_m for every
 // (n, m, nu, s); a value inside c eta - delta (outside c eta + delta) is decided in FP32,

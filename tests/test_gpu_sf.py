@@ -39,6 +39,7 @@ def _rates(system, grid, mu, eta, lo, hi, precision="fp32", chunk=0):
     ("al_like_ws", (10, 10, 10), 0.3, 0.05),     # genuine Wigner-Seitz R-set, not a cube
     ("al_like_ws", (9, 20, 15), 0.3, 0.04),      # ... two plane blocks, ragged
     ("si_like", (6, 5, 4), None, 0.05),          # W = 8, 6 modes, 7^3: q2 groups
+    ("al_like", (64, 5, 6), 0.3, 0.05),          # >= 64 points on axis 1: the sieve's segment pruning
 ])
 def test_fp32_matches_the_oracle(name, grid, half, eta):
     s = getattr(synth, f"{name}_system")()
@@ -67,7 +68,8 @@ def test_fp32_against_fp64_gpu_and_determinism():
     assert np.array_equal(b[2], c[2]) and np.array_equal(b[2], d[2])
 
 
-@pytest.mark.parametrize("name,grid,half", [("al_like", (14, 9, 40), 0.3), ("si_like", (8, 8, 8), None)])
+@pytest.mark.parametrize("name,grid,half", [("al_like", (14, 9, 40), 0.3), ("si_like", (8, 8, 8), None),
+                                             ("al_like", (66, 4, 5), 0.3)])
 def test_sieve_without_mask_gives_the_same_rates(monkeypatch, name, grid, half):
     """When the decision mask does not fit (forced with EPWI_SIEVE_MASK_MAX_BYTES=0) the pair
     lists are rebuilt per chunk by the sieve kernel's fill mode: the pair counts and the rates
