@@ -310,6 +310,8 @@ epwi_status epwi_setup(epwi_ctx *c, const epwi_system *s) {
             for (int i = 0; i < 3 * nRp; ++i) r = std::max(r, std::abs(s->Rp[i]));
             c->sf_r = r;
             c->sf_g_ready = false;
+            c->gcube_ready = false;
+            c->gcube32.release();
             c->h_rp_cube.clear();
             if (r <= 6) {
                 const int Dc = 2 * r + 1;

@@ -165,6 +165,8 @@ struct epwi_ctx {
     DevBuf gsf32;                  // fp32 mode: g' [Re][cube forms][Nm][W][W] (+-R recombined)
     bool sf_g_ready = false;       // gsf32 built for the current system
     DevBuf sf_Vt32;                // fp32 mode: float2 [Nk][m][i], V transposed
+    DevBuf gcube32;                // split modes, R_p not a cube: weighted g in the bounding cube
+    bool gcube_ready = false;      // gcube32 built for the current system
     // factorised H(k) / D(q) builds: weighted H and Phi/sqrt(m m) embedded in the bounding cubes
     // of the two R-sets (half-widths fac_re_r, fac_rp_r; -1: direct sums), stage buffers
     int fac_re_r = -1, fac_rp_r = -1;
@@ -216,11 +218,19 @@ struct epwi_ctx {
                          &tc_n32, &tc_hw32, &tc_err, &tc_meta, &is_pairs, &is_w,
                          &is_kp_pairs, &sieve_mask, &tc_arows, &ib_pairs, &ib_goff, &ib_gam,
                          &ib_kpos, &ib_F0, &ib_F, &ib_Fn, &ib_red, &ib_F32, &ib_Fn32, &sf_items, &ib_wbase, &sym_rep, &seg_ranges,
-                         &gsf32, &sf_Vt32, &fac_Hc, &fac_Pc, &fac_T, &fac_U};
+                         &gsf32, &sf_Vt32, &gcube32, &fac_Hc, &fac_Pc, &fac_T, &fac_U};
         for (DevBuf *b : all) b->release();
         mlp_free(mlp);
     }
 };
+
+// The R_p set the split-precision path works on: the set itself when it is a full cube
+// [-r, r]^3 in n3-fastest order, else its bounding cube with zero-weight padding (gcube32).
+inline int tc_rp_r(const epwi_ctx *c) { return c->rp_cube_r >= 0 ? c->rp_cube_r : c->sf_r; }
+inline int tc_rp_count(const epwi_ctx *c) {
+    const int D = 2 * tc_rp_r(c) + 1;
+    return c->rp_cube_r >= 0 ? c->nRp : D * D * D;
+}
 
 // Uploads a host int vector into b (synchronously ordered on the context stream).
 inline void upload_ints(epwi_ctx *c, DevBuf &b, const std::vector<int> &h) {

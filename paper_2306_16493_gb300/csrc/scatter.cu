@@ -281,9 +281,10 @@ struct StageTimers {
 int64_t run_chunk(epwi_ctx *c, const WorkSet &ws, const ChunkView &cv, double *g2out, double *tout,
                   int tstride, StageTimers &tm) {
     const int W = c->nw, Nm = c->nm;
-    const int64_t nrow = (int64_t)c->nRp * Nm * W;
     const bool sf = c->opt.precision == EPWI_FP32;
     const bool tc = !sf && c->opt.precision != EPWI_FP64;
+    const int nRp = tc ? tc_rp_count(c) : c->nRp;           // the split modes' view of R_p
+    const int64_t nrow = (int64_t)nRp * Nm * W;
     const size_t state_bytes = sf ? sf_state_bytes(c) : tc ? tc_state_bytes(c) : sizeof(double2) * nrow;
     GridInfo g = make_grid_info(c);
     const int64_t nkpc = cv.kp1 - cv.kp0;
@@ -310,11 +311,11 @@ int64_t run_chunk(epwi_ctx *c, const WorkSet &ws, const ChunkView &cv, double *g
     ra.W = W;
     ra.Nm = Nm;
     ra.nRe = c->nRe;
-    ra.nRp = c->nRp;
+    ra.nRp = nRp;
     ra.nrow = (int)nrow;
     ra.Re = c->Re.as<int>();
     ra.gw64 = c->gw64.as<double2>();
-    ra.gw32 = c->gw32.as<float2>();
+    ra.gw32 = (tc && c->rp_cube_r < 0) ? c->gcube32.as<float2>() : c->gw32.as<float2>();
     ra.ph64 = c->ph64.as<double2>();
     ra.ph32 = c->ph32.as<float2>();
     ra.V64 = c->V.as<double2>();
@@ -341,7 +342,7 @@ int64_t run_chunk(epwi_ctx *c, const WorkSet &ws, const ChunkView &cv, double *g
     sa.g = g;
     sa.W = W;
     sa.Nm = Nm;
-    sa.nRp = c->nRp;
+    sa.nRp = nRp;
     sa.nrow = (int)nrow;
     sa.Rp = c->Rp.as<int>();
     sa.ph64 = c->ph64.as<double2>();
@@ -435,6 +436,7 @@ void process_workset(epwi_ctx *c, const WorkSet &ws, double *g2out, double *tout
         sf_check(c);
         sf_prepare(c);
     }
+    if (tc) tc_prepare(c);
     // chunk limits: pairs and Re->k output size
     // pair lists per chunk: 2^32 q indices (16 GiB) in the fp32 mode, whose launches are one
     // CTA per state and need thousands of states per chunk to fill the GPU on large grids (200^3:

@@ -94,6 +94,7 @@ size_t tc_state_bytes(const epwi_ctx *c);
 void tc_restage(epwi_ctx *c, const RestageArgs &ra);
 void tc_scatter(epwi_ctx *c, const ScatterArgs &sa, int64_t ntiles);
 void tc_tables(epwi_ctx *c);
+void tc_prepare(epwi_ctx *c);
 int tc_check_error(epwi_ctx *c);
 
 // Iterative BTE: pair list, Gamma layout and storage of the current window (sets the Gamma

@@ -981,8 +981,8 @@ void launch_tc(epwi_ctx *c, const ScatterArgs &sa, int64_t ntiles) {
     a.scale_inv2 = std::ldexp(1.0f, -2 * e);
     a.ceta32 = (float)sa.ceta;
     a.inv_eta32 = (float)(1.0 / sa.eta);
-    a.cube_r = c->rp_cube_r;
-    a.nchunk = (c->nRp + 64 / ES - 1) / (64 / ES);
+    a.cube_r = tc_rp_r(c);
+    a.nchunk = (tc_rp_count(c) + 64 / ES - 1) / (64 / ES);
     a.nbg = std::max(1, 48 / NMWP);   // 4 ncp <= 192: two accumulators + A stages fit 512 columns
     a.ncp_max = std::min(sa.nsel_max, a.nbg) * NMWP;
     // TMEM: two accumulators of 4 ncp_max columns, then (A generated in-kernel) NSA A stages
@@ -1076,16 +1076,17 @@ void launch_any(epwi_ctx *c, const ScatterArgs &sa, int64_t nt) {
 
 template <class Op>
 void dispatch_tc(epwi_ctx *c, const ScatterArgs &sa, int64_t nt) {
-    const int W = c->nw, NM = c->nm, r = c->rp_cube_r;
+    const int W = c->nw, NM = c->nm, r = tc_rp_r(c);
     if (W == 1 && NM == 3 && r == 1) launch_any<Op, 1, 3, 1>(c, sa, nt);
     else if (W == 4 && NM == 3 && r == 1) launch_any<Op, 4, 3, 1>(c, sa, nt);
     else if (W == 4 && NM == 3 && r == 2) launch_any<Op, 4, 3, 2>(c, sa, nt);
+    else if (W == 4 && NM == 3 && r == 3) launch_any<Op, 4, 3, 3>(c, sa, nt);
     else if (W == 8 && NM == 6 && r == 3) launch_any<Op, 8, 6, 3>(c, sa, nt);
     else if (W == 8 && NM == 6 && r == 1) launch_any<Op, 8, 6, 1>(c, sa, nt);
     else
         throw EpwiError{EPWI_EUNSUPPORTED,
                         "split-precision path built for (nw, modes, R_p cube half-width) in "
-                        "{(1,3,1), (4,3,1), (4,3,2), (8,6,1), (8,6,3)}"};
+                        "{(1,3,1), (4,3,1), (4,3,2), (4,3,3), (8,6,1), (8,6,3)}"};
 }
 
 }  // namespace
@@ -1093,7 +1094,7 @@ void dispatch_tc(epwi_ctx *c, const ScatterArgs &sa, int64_t nt) {
 size_t tc_state_bytes(const epwi_ctx *c) {
     const int es = c->opt.precision == EPWI_TF32X3 ? 4 : 2;
     const size_t kc = 64 / es;
-    const size_t nchunk = (c->nRp + kc - 1) / kc;
+    const size_t nchunk = (tc_rp_count(c) + kc - 1) / kc;
     const size_t nmwp = (size_t)(c->nm * c->nw + 15) / 16 * 16;
     return nchunk * 6 * nmwp * 64;
 }
@@ -1145,9 +1146,42 @@ void tc_restage(epwi_ctx *c, const RestageArgs &ra) {
     }
 }
 
+// A non-cube R_p set embedded in its bounding cube: gcube32[Re][cube point][mu][i][j] = the
+// weighted g of the R_p vector at that point, or 0.
+__global__ void k_cube_embed(int64_t n, int nRp, int D3, int rowlen, const int *__restrict__ cube,
+                             const float2 *__restrict__ g32, float2 *__restrict__ out) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    const int e = (int)(idx % rowlen);
+    const int64_t t = idx / rowlen;
+    const int cf = (int)(t % D3);
+    const int64_t re = t / D3;
+    const int rp = cube[cf];
+    out[idx] = rp < 0 ? make_float2(0.f, 0.f) : g32[((size_t)re * nRp + rp) * rowlen + e];
+}
+
+// The split-precision view of the R_p set (tc_rp_r, tc_rp_count): for a set that is not a full
+// cube, its bounding cube (half-width <= 3) with the weighted g embedded (gcube32).
+void tc_prepare(epwi_ctx *c) {
+    if (c->rp_cube_r >= 0) return;
+    EPWI_REQUIRE(!c->h_rp_cube.empty() && c->sf_r <= 3, EPWI_EUNSUPPORTED,
+                 "split-precision path: the bounding cube of R_p must have half-width <= 3");
+    if (c->gcube_ready) return;
+    const int D = 2 * c->sf_r + 1, D3 = D * D * D, rowlen = c->nm * c->nw * c->nw;
+    const int64_t n = (int64_t)c->nRe * D3 * rowlen;
+    DevBuf cube;
+    upload_ints(c, cube, c->h_rp_cube);
+    c->gcube32.ensure(sizeof(float2) * n);
+    k_cube_embed<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(n, c->nRp, D3, rowlen, cube.as<int>(),
+                                                                    c->gw32.as<float2>(), c->gcube32.as<float2>());
+    EPWI_CHECK_LAUNCH();
+    EPWI_CUDA(cudaStreamSynchronize(c->stream));   // cube is freed on return
+    c->gcube_ready = true;
+}
+
 void tc_scatter(epwi_ctx *c, const ScatterArgs &sa, int64_t ntiles) {
-    EPWI_REQUIRE(c->rp_cube_r >= 0, EPWI_EUNSUPPORTED,
-                 "split-precision path needs the phonon R-set to be a full cube [-r, r]^3 (n3 fastest)");
+    EPWI_REQUIRE(c->rp_cube_r >= 0 || c->gcube_ready, EPWI_EUNSUPPORTED,
+                 "split-precision path: R_p is neither a full cube nor embedded in one");
     switch (c->opt.precision) {
         case EPWI_FP16X3: dispatch_tc<OpF16>(c, sa, ntiles); break;
         case EPWI_BF16X3: dispatch_tc<OpBF16>(c, sa, ntiles); break;

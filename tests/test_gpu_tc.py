@@ -91,6 +91,24 @@ def test_al_like_12_split(epwi, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp16x3", "tf32x3"])
+def test_wigner_seitz_rset_split(epwi, prec):
+    """A genuine Wigner-Seitz R_p set (93 vectors, not a cube) through the split-precision path,
+    which embeds it in its bounding 7^3 cube with zero weights: 1/tau and sigma against the
+    oracle on a ragged grid."""
+    s = synth.al_like_ws_system()
+    N, T, eta = (10, 9, 11), 300.0, 0.04
+    gr = O.Grids(s, N)
+    mu = gr.band_centre()
+    out = gpu_run(s, N, T, mu, eta, mu - 0.3, mu + 0.3, precision=prec)
+    ora = oracle_run(gr, T, mu, eta, mu - 0.3, mu + 0.3)
+    assert out["n_pairs"] == ora["n_pairs"]
+    err, n = compare_rates(out, ora, gr.eps, RATE_TOL)
+    assert n > 0 and err < RATE_TOL, err
+    assert rel_frob(out["sigma"], ora["sigma"]) < RATE_TOL
+    out["ctx"].close()
+
+
+@pytest.mark.parametrize("prec", ["fp16x3", "tf32x3"])
 def test_si_like_mobility_split(epwi, prec):
     s = synth.si_like_system()
     N, T, eta, n_c = 12, 300.0, 0.01, 1e18
