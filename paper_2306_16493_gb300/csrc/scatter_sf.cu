@@ -133,13 +133,26 @@ __global__ void k_sf_transform(int64_t n, int nRp, int Dc, int rc, int rowlen, c
     out[idx] = make_float2((float)s.x, (float)s.y);
 }
 
-// Vt[k][m][i] = V[k][i][m] (FP32): one column of V(k+q) is one contiguous row.
-__global__ void k_transpose_v(int64_t nk, int W, const float2 *__restrict__ V, float2 *__restrict__ Vt) {
+// Band-major tables of the k+q side (FP32): Vb[m][k][i] = V[k][i][m] and
+// EF[m][k] = (eps_mk - mu, f_mk), so that lanes on consecutive k+q points and one band m read
+// contiguous memory.
+__global__ void k_band_major_v(int64_t nk, int W, const float2 *__restrict__ V, float2 *__restrict__ Vb) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= nk * W * W) return;
-    const int64_t k = idx / (W * W);
-    const int e = (int)(idx % (W * W)), m = e / W, i = e % W;
-    Vt[idx] = V[k * W * W + i * W + m];
+    const int i = (int)(idx % W);
+    const int64_t t = idx / W;
+    const int64_t k = t % nk;
+    const int m = (int)(t / nk);
+    Vb[idx] = V[k * W * W + i * W + m];
+}
+
+__global__ void k_band_major_ef(int64_t nk, int W, const float *__restrict__ erel, const float *__restrict__ f32,
+                                float2 *__restrict__ ef) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nk * W) return;
+    const int64_t k = idx % nk;
+    const int m = (int)(idx / nk);
+    ef[idx] = make_float2(erel[k * W + m], f32[k * W + m]);
 }
 
 // Division by a divisor fixed at launch (x < 2^31): q = (umulhi(x, m) + x) >> l with
@@ -175,7 +188,9 @@ struct SfArgs {
     const int64_t *kp_pairs;        // chunk-local pair offsets, minus p_off
     int64_t p_off;
     const int *pairs;               // chunk pair list: q index
-    const float2 *Vt32, *u32;
+    const float2 *Vb32, *u32;       // Vb32[m][k][i]: band-major columns of V
+    const float2 *ef;               // [m][k]: (eps - mu, f), band-major
+    int64_t nk;
     const float *erel, *f32, *n32, *hw32, *hwmax32;
     float ceta32, inv_eta32;
     double pref;                    // 2 pi / (hbar N_q sqrt(pi) eta)
@@ -217,6 +232,7 @@ __global__ void __launch_bounds__(kSfThreads, (W <= 4 ? 3 : 2)) k_scatter_sf(SfA
     constexpr int X = NM * W;                    // columns (mu, i)
     constexpr bool V2 = (W % 2) == 0;            // rows of W float2 are 16-byte aligned
     constexpr int kMuUnroll = NM <= 3 ? NM : 1;  // wide systems: one mode row at a time (registers)
+    constexpr bool kPreG = X <= 12 && X % 2 == 0;  // G of a pair kept in registers for its bands
     extern __shared__ __align__(16) float2 sm[];
     const int N1 = a.g.n1, N2 = a.g.n2, N3 = a.g.n3, L = a.g.L;
     const int JQ = a.jq, NJG = a.njg;
@@ -349,24 +365,28 @@ __global__ void __launch_bounds__(kSfThreads, (W <= 4 ? 3 : 2)) k_scatter_sf(SfA
 #pragma unroll
                     for (int f = 0; f < NF; ++f) c1[f] = CS1[q1 * NF + f];
                     if constexpr (X % 2 == 0) {
+                        // (f3, e2) over D rows of per4 float4, walked as one list by the lanes
                         const int per4 = jn * X / 2;
-#pragma unroll
-                        for (int f3 = 0; f3 < D; ++f3) {
-                            const float4 *src = reinterpret_cast<const float4 *>(Y + (size_t)f3 * JQ * X);
-                            float4 *dst = reinterpret_cast<float4 *>(Uw + (size_t)f3 * JQ * X);
-                            for (int e = lane; e < per4; e += 32) {
-                                float4 v = src[e];
-#pragma unroll
-                                for (int f1 = 1; f1 < D; ++f1) {
-                                    const float c = c1[f1 - 1];
-                                    const float4 w = src[e + f1 * D * JQ * X / 2];
-                                    v.x = fmaf(c, w.x, v.x);
-                                    v.y = fmaf(c, w.y, v.y);
-                                    v.z = fmaf(c, w.z, v.z);
-                                    v.w = fmaf(c, w.w, v.w);
-                                }
-                                dst[e] = v;
+                        int f3 = 0, e2 = lane;
+                        while (true) {
+                            while (e2 >= per4 && f3 < D) {
+                                e2 -= per4;
+                                ++f3;
                             }
+                            if (f3 >= D) break;
+                            const float4 *src = reinterpret_cast<const float4 *>(Y + (size_t)f3 * JQ * X) + e2;
+                            float4 v = src[0];
+#pragma unroll
+                            for (int f1 = 1; f1 < D; ++f1) {
+                                const float c = c1[f1 - 1];
+                                const float4 w = src[f1 * D * JQ * X / 2];
+                                v.x = fmaf(c, w.x, v.x);
+                                v.y = fmaf(c, w.y, v.y);
+                                v.z = fmaf(c, w.z, v.z);
+                                v.w = fmaf(c, w.w, v.w);
+                            }
+                            reinterpret_cast<float4 *>(Uw + (size_t)f3 * JQ * X)[e2] = v;
+                            e2 += 32;
                         }
                     } else {
                         const int per = jn * X;
@@ -436,13 +456,31 @@ __global__ void __launch_bounds__(kSfThreads, (W <= 4 ? 3 : 2)) k_scatter_sf(SfA
                         grow = a.goff[P0 + seg0 + t] + (int64_t)n * nwkq - lokq;
                     }
                     const float2 *uq = a.u32 + q * (NM * NM);
+                    // small shapes: G (every column) once per pair, shared by its bands
+                    float2 Gp[kPreG ? X : 1];
+                    if constexpr (kPreG) {
+#pragma unroll
+                        for (int x = 0; x < X; ++x) Gp[x] = Ub[x];
+#pragma unroll
+                        for (int f = 1; f < D; ++f) {
+                            const float c = c3[f - 1];
+#pragma unroll
+                            for (int x2 = 0; x2 < X / 2; ++x2) {
+                                const float4 v = reinterpret_cast<const float4 *>(Ub + f * JQ * X)[x2];
+                                Gp[2 * x2].x = fmaf(c, v.x, Gp[2 * x2].x);
+                                Gp[2 * x2].y = fmaf(c, v.y, Gp[2 * x2].y);
+                                Gp[2 * x2 + 1].x = fmaf(c, v.z, Gp[2 * x2 + 1].x);
+                                Gp[2 * x2 + 1].y = fmaf(c, v.w, Gp[2 * x2 + 1].y);
+                            }
+                        }
+                    }
                     while (mask) {
                         const int m = __ffs(mask) - 1;
                         mask &= mask - 1;
-                        const float em = __ldg(a.erel + ikq * W + m);
-                        const float fm = __ldg(a.f32 + ikq * W + m);
+                        const float2 emf = __ldg(a.ef + (int64_t)m * a.nk + ikq);
+                        const float em = emf.x, fm = emf.y;
                         float2 Vc[W];                        // column m of V(k+q)
-                        const float2 *vp = a.Vt32 + ((int64_t)ikq * W + m) * W;
+                        const float2 *vp = a.Vb32 + ((int64_t)m * a.nk + ikq) * W;
                         if constexpr (V2) {
 #pragma unroll
                             for (int i = 0; i < W / 2; ++i) {
@@ -461,7 +499,10 @@ __global__ void __launch_bounds__(kSfThreads, (W <= 4 ? 3 : 2)) k_scatter_sf(SfA
                         for (int mu = 0; mu < NM; ++mu) {
                             float2 G[W];
                             const float2 *u0 = Ub + mu * W;
-                            if constexpr (V2) {
+                            if constexpr (kPreG) {
+#pragma unroll
+                                for (int i = 0; i < W; ++i) G[i] = Gp[mu * W + i];
+                            } else if constexpr (V2) {
 #pragma unroll
                                 for (int i = 0; i < W / 2; ++i) {
                                     const float4 v = reinterpret_cast<const float4 *>(u0)[i];
@@ -603,7 +644,8 @@ void sf_check(const epwi_ctx *c) {
 }
 
 // Builds what the fp32 mode reads besides the eigen-tables: g' (cube embedding and the +-R
-// recombination of the R_p axes, once per system) and the transposed FP32 V (per eigs call).
+// recombination of the R_p axes, once per system) and the band-major FP32 V and (eps - mu, f)
+// tables (per rates call).
 void sf_prepare(epwi_ctx *c) {
     const int W = c->nw, NM = c->nm;
     const int Dc = 2 * c->sf_r + 1;
@@ -620,10 +662,14 @@ void sf_prepare(epwi_ctx *c) {
         EPWI_CUDA(cudaStreamSynchronize(c->stream));   // cube is freed on return
         c->sf_g_ready = true;
     }
-    const int64_t nv = c->nk * W * W;
+    const int64_t nv = c->nk * W * W, ne = c->nk * W;
     c->sf_Vt32.ensure(sizeof(float2) * nv);
-    k_transpose_v<<<(unsigned)((nv + 255) / 256), 256, 0, c->stream>>>(c->nk, W, c->V32.as<float2>(),
-                                                                      c->sf_Vt32.as<float2>());
+    k_band_major_v<<<(unsigned)((nv + 255) / 256), 256, 0, c->stream>>>(c->nk, W, c->V32.as<float2>(),
+                                                                       c->sf_Vt32.as<float2>());
+    EPWI_CHECK_LAUNCH();
+    c->sf_ef.ensure(sizeof(float2) * ne);
+    k_band_major_ef<<<(unsigned)((ne + 255) / 256), 256, 0, c->stream>>>(c->nk, W, c->tc_erel.as<float>(),
+                                                                        c->tc_f32.as<float>(), c->sf_ef.as<float2>());
     EPWI_CHECK_LAUNCH();
 }
 
@@ -679,7 +725,9 @@ void sf_scatter(epwi_ctx *c, const ScatterArgs &sa, int64_t nkp, const int64_t *
     a.kp_pairs = kp_pairs_local;
     a.p_off = p_off;
     a.pairs = sa.pairs;
-    a.Vt32 = c->sf_Vt32.as<float2>();
+    a.Vb32 = c->sf_Vt32.as<float2>();
+    a.ef = c->sf_ef.as<float2>();
+    a.nk = c->nk;
     a.u32 = sa.u32;
     a.erel = c->tc_erel.as<float>();
     a.f32 = c->tc_f32.as<float>();
