@@ -37,10 +37,10 @@ DTYPE = {"fp64": "f64", "tf32x3": "tf32x3 (f32 acc, f64 sums)", "bf16x3": "bf16x
 L2_BYTES = 129 * 2 ** 20
 # DRAM bytes (read + write) per (k,q) pair of the dominant kernel, from one ncu capture each:
 # k_scatter_tc (fp16x3) at 24^3, 255 MB / 19.6 M pairs (ncu --set full); k_scatter_sf (fp32,
-# warp-owned runs) at 32^3, 628.6 + 4.2 MB / 110.2 M pairs (ncu --set full).  Traffic grows with
-# the pairs processed, so a launch's traffic is this times its pairs.  Valid for the kernel
+# band-major k+q tables) at 32^3, 624.1 + 4.2 MB / 110.2 M pairs (ncu --set full).  Traffic grows
+# with the pairs processed, so a launch's traffic is this times its pairs.  Valid for the kernel
 # versions of those captures.
-TRAFFIC_BYTES_PER_PAIR = {"fp16x3": 13.0, "fp32": 5.74}
+TRAFFIC_BYTES_PER_PAIR = {"fp16x3": 13.0, "fp32": 5.70}
 
 
 def peaks():
