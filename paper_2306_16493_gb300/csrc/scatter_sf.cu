@@ -84,6 +84,70 @@ __global__ void __launch_bounds__(128) k_restage_f32(RestageArgs a, float2 *__re
     }
 }
 
+// The same Re->k stage with one thread per (row, j) and 32 k-points per thread: the phases of
+// the block's 32 k-points are staged in shared memory in chunks of 32 R_e and read as
+// broadcasts, g'[Re][row][j] is read once per 32 k-points (coalesced over (row, j)), and the
+// contraction with V_{j,n}(k) is a shuffle reduction over the W lanes of a row.  Sums over R_e
+// run in R_e order; the sum over j is a fixed tree.
+template <int W>
+__global__ void __launch_bounds__(256) k_restage_f32_kb(RestageArgs a, float2 *__restrict__ out) {
+    constexpr int KB = 32, RCH = 32, RPB = 256 / W;   // k-points per block, R_e per chunk, rows per block
+    __shared__ float2 Ps[RCH][KB];
+    const int tid = threadIdx.x, j = tid % W;
+    const int row = blockIdx.x * RPB + tid / W;
+    const int k0 = blockIdx.y * KB;
+    const bool live = row < a.nrow;
+    float2 acc[KB];
+#pragma unroll
+    for (int x = 0; x < KB; ++x) acc[x] = make_float2(0.f, 0.f);
+    for (int re0 = 0; re0 < a.nRe; re0 += RCH) {
+        __syncthreads();                          // Ps of the previous chunk is consumed
+        for (int e = tid; e < RCH * KB; e += 256) {
+            const int rr = e / KB, kk = e % KB, re = re0 + rr;
+            float2 p = make_float2(0.f, 0.f);
+            if (k0 + kk < a.nkp && re < a.nRe) {
+                int i1, i2, i3;
+                grid_coords(a.g, a.kpts[k0 + kk], i1, i2, i3);
+                p = a.ph32[phase_index(i1 * a.g.s1 % a.g.L, i2 * a.g.s2 % a.g.L, i3 * a.g.s3 % a.g.L,
+                                       a.Re[3 * re], a.Re[3 * re + 1], a.Re[3 * re + 2], a.g.L)];
+            }
+            Ps[rr][kk] = p;
+        }
+        __syncthreads();
+        const int nr = min(RCH, a.nRe - re0);
+        if (live) {
+            for (int rr = 0; rr < nr; ++rr) {
+                const float2 gv = __ldg(a.gw32 + ((size_t)(re0 + rr) * a.nrow + row) * W + j);
+#pragma unroll
+                for (int x = 0; x < KB; x += 2) {
+                    const float4 p2 = reinterpret_cast<const float4 *>(&Ps[rr][x])[0];
+                    acc[x] = cfmaf(make_float2(p2.x, p2.y), gv, acc[x]);
+                    acc[x + 1] = cfmaf(make_float2(p2.z, p2.w), gv, acc[x + 1]);
+                }
+            }
+        }
+    }
+    // out[state][row] = sum_j acc[k][j] V_{j, lo+n}(k): lanes j of a row are adjacent
+#pragma unroll
+    for (int x = 0; x < KB; ++x) {
+        const int kp = k0 + x;
+        if (kp >= a.nkp) continue;               // uniform over the block
+        const int ik = a.kpts[kp];
+        const int lo = a.win_lo[ik], ns = a.win_n[ik];
+        const int64_t s0 = a.kp_state[kp] - a.s_base;
+        const float2 *Vk = a.V32 + (int64_t)ik * W * W;
+        for (int np = 0; np < ns; ++np) {
+            float2 o = cmulf(acc[x], Vk[j * W + lo + np]);
+#pragma unroll
+            for (int off = W / 2; off > 0; off >>= 1) {
+                o.x += __shfl_xor_sync(0xffffffffu, o.x, off);
+                o.y += __shfl_xor_sync(0xffffffffu, o.y, off);
+            }
+            if (live && j == 0) out[(s0 + np) * a.nrow + row] = o;
+        }
+    }
+}
+
 // g'(Re, f1 f2 f3) = (T x T x T) g(Re, cube): along each axis, form 0 is R = 0, form 2R-1 is
 // v[R] + v[-R] and form 2R is i (v[R] - v[-R]).  cube[c] is the index of the R_p vector at
 // cube point c, or -1 (zero weight).  One thread per output element; FP64 sums, FP32 output.
@@ -687,8 +751,15 @@ void sf_restage(epwi_ctx *c, const RestageArgs &ra_in) {
         kern<<<grid, 128, sm, c->stream>>>(ra, out);
         EPWI_CHECK_LAUNCH();
     };
+    auto kb = [&](auto kern, int rows_per_block) {
+        dim3 grid((ra.nrow + rows_per_block - 1) / rows_per_block, (unsigned)((ra.nkp + 31) / 32));
+        kern<<<grid, 256, 0, c->stream>>>(ra, out);
+        EPWI_CHECK_LAUNCH();
+    };
+    // measured: the k-blocked kernel pays for the Si-like shape (72 -> 53 ms at 100^3) and not
+    // for W = 4 (6.8 -> 9.2 ms at 48^3)
     if (W == 4) go(k_restage_f32<4, 8>, 8);
-    else if (W == 8) go(k_restage_f32<8, 4>, 4);
+    else if (W == 8) kb(k_restage_f32_kb<8>, 32);
     else if (W == 1) go(k_restage_f32<1, 8>, 8);
     else go(k_restage_f32<0, 1>, 1);
 }
