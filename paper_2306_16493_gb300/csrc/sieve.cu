@@ -203,10 +203,11 @@ __global__ void k_seg_ranges(int N1, int64_t nplane, int W, int nseg, const floa
 // pair_valid_t takes needs some k+q energy within hwmax(q) + c eta + delta of a window energy
 // at k, so a candidate whose k+q energies all lie outside [min window energy - hwmax - pad,
 // max window energy + hwmax + pad] is rejected at once (pad exceeds the FP32 rounding of
-// either form).  The candidates that pass go into a per-warp queue in shared memory; each time
-// 32 are waiting, the warp evaluates them with pair_valid_tail (the unchanged exact test), one
-// per lane, and ORs the decisions into the plane block's mask words, kept in shared memory
-// and written out in k_sieve_count's layout.  Indices are 32-bit (N_k < 2^31, checked).
+// either form).  The candidates that pass go into a per-warp queue in shared memory with the
+// mask of their bands within reach; each time 32 are waiting, the warp evaluates them with
+// pair_valid_bands (the exact test on those bands), one per lane, and ORs the decisions into
+// the plane block's mask words, kept in shared memory and written out in k_sieve_count's
+// layout.  Indices are 32-bit (N_k < 2^31, checked).
 //
 // With FILL the same kernel writes the pair lists of k-points kp0 + blockIdx.x instead (used
 // when the whole decision mask would not fit in memory): after each plane block the CTA scans
@@ -220,7 +221,7 @@ __global__ void k_seg_ranges(int N1, int64_t nplane, int W, int nseg, const floa
 // fail.  A warp whose lanes all reject a segment skips its iterations.
 constexpr int kQueue = 64;
 template <int WT, int NMT, bool FILL>
-__global__ void __launch_bounds__(256) k_sieve_count_fast(SieveArgs a, const int *__restrict__ kpts,
+__global__ void __launch_bounds__(256, 4) k_sieve_count_fast(SieveArgs a, const int *__restrict__ kpts,
                                                           const int *__restrict__ lo,
                                                           const int *__restrict__ cnt,
                                                           int64_t *__restrict__ counts,
@@ -255,10 +256,12 @@ __global__ void __launch_bounds__(256) k_sieve_count_fast(SieveArgs a, const int
     auto run = [&](int e, bool valid) {
         if (valid) {
             const int slot = e & (kQueue - 1);
-            const int iq = Qi[slot], ikq = Qk[slot], wb = Qw[slot];
+            const int iq = Qi[slot], ikq = Qk[slot];
+            const unsigned wq = (unsigned)Qw[slot];          // (i1 * 32 + lane) << 8 | near bands
+            const unsigned wb = wq >> 8;
             float em[WT];
             load_kq_energies<WT>(a, ikq, em);
-            if (pair_valid_tail<WT, NMT>(a, nsel, en, en32, iq, ikq, a.hwmax32[iq], em))
+            if (pair_valid_bands<WT, NMT>(a, nsel, en, en32, iq, ikq, a.hwmax32[iq], em, wq & 0xffu))
                 atomicOr(&words[(wb >> 5) * 8 + wid], 1u << (wb & 31));
         }
     };
@@ -293,7 +296,7 @@ __global__ void __launch_bounds__(256) k_sieve_count_fast(SieveArgs a, const int
                 continue;
             }
             for (int u = 0; u < len; ++u, ++i1) {
-            bool near = false;
+            unsigned nm = 0;                     // bands within reach of a window energy
             int ikq = 0;
             if (segok) {
                 const float hm = a.hwmax32[iq];
@@ -303,15 +306,16 @@ __global__ void __launch_bounds__(256) k_sieve_count_fast(SieveArgs a, const int
                     load_kq_energies<WT>(a, ikq, em);
                     const float lo_ = elo - hm - pad, hi_ = ehi + hm + pad;
 #pragma unroll
-                    for (int m = 0; m < WT; ++m) near |= (em[m] >= lo_) & (em[m] <= hi_);
+                    for (int m = 0; m < WT; ++m) nm |= ((em[m] >= lo_) & (em[m] <= hi_) ? 1u : 0u) << m;
                 }
             }
+            const bool near = nm != 0;
             const unsigned bal = __ballot_sync(0xffffffffu, near);
             if (near) {
                 const int slot = (tail + __popc(bal & lt)) & (kQueue - 1);
                 Qi[slot] = iq;
                 Qk[slot] = ikq;
-                Qw[slot] = i1 * 32 + lane;
+                Qw[slot] = (int)((((unsigned)i1 * 32u + (unsigned)lane) << 8) | nm);
             }
             tail += __popc(bal);
             if (tail - head >= 32) {
