@@ -166,6 +166,7 @@ struct epwi_ctx {
     bool sf_g_ready = false;       // gsf32 built for the current system
     DevBuf sf_Vt32;                // fp32 mode: float2 [m][Nk][i], columns of V band-major
     DevBuf sf_ef;                  // fp32 mode: float2 [m][Nk]: (eps - mu, f), band-major
+    DevBuf sf_uS, sf_wn;           // fp32 mode: float2 [mu nu][Nq] u(q), [nu][Nq] (hbar omega, N)
     DevBuf gcube32;                // split modes, R_p not a cube: weighted g in the bounding cube
     bool gcube_ready = false;      // gcube32 built for the current system
     // factorised H(k) / D(q) builds: weighted H and Phi/sqrt(m m) embedded in the bounding cubes
@@ -219,7 +220,7 @@ struct epwi_ctx {
                          &tc_n32, &tc_hw32, &tc_err, &tc_meta, &is_pairs, &is_w,
                          &is_kp_pairs, &sieve_mask, &tc_arows, &ib_pairs, &ib_goff, &ib_gam,
                          &ib_kpos, &ib_F0, &ib_F, &ib_Fn, &ib_red, &ib_F32, &ib_Fn32, &sf_items, &ib_wbase, &sym_rep, &seg_ranges,
-                         &gsf32, &sf_Vt32, &sf_ef, &gcube32, &fac_Hc, &fac_Pc, &fac_T, &fac_U};
+                         &gsf32, &sf_Vt32, &sf_ef, &sf_uS, &sf_wn, &gcube32, &fac_Hc, &fac_Pc, &fac_T, &fac_U};
         for (DevBuf *b : all) b->release();
         mlp_free(mlp);
     }

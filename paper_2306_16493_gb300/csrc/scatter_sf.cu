@@ -210,6 +210,18 @@ __global__ void k_band_major_v(int64_t nk, int W, const float2 *__restrict__ V, 
     Vb[idx] = V[k * W * W + i * W + m];
 }
 
+// Structure-of-arrays tables of the q side (FP32): uS[mu nu][q] = u_mu,nu(q) and
+// wn[nu][q] = (hbar omega, N), so that lanes on consecutive q read contiguous memory.
+__global__ void k_soa_q(int64_t nq, int NM, const float2 *__restrict__ u, const float *__restrict__ hw,
+                        const float *__restrict__ n, float2 *__restrict__ uS, float2 *__restrict__ wn) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nq * NM * NM) return;
+    const int64_t q = idx % nq;
+    const int e = (int)(idx / nq);
+    uS[idx] = u[q * NM * NM + e];
+    if (e < NM) wn[idx] = make_float2(hw[q * NM + e], n[q * NM + e]);
+}
+
 __global__ void k_band_major_ef(int64_t nk, int W, const float *__restrict__ erel, const float *__restrict__ f32,
                                 float2 *__restrict__ ef) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -254,6 +266,8 @@ struct SfArgs {
     const int *pairs;               // chunk pair list: q index
     const float2 *Vb32, *u32;       // Vb32[m][k][i]: band-major columns of V
     const float2 *ef;               // [m][k]: (eps - mu, f), band-major
+    const float2 *uS;               // [mu nu][q]: u(q), structure of arrays
+    const float2 *wn;               // [nu][q]: (hbar omega, N), structure of arrays
     int64_t nk;
     const float *erel, *f32, *n32, *hw32, *hwmax32;
     float ceta32, inv_eta32;
@@ -509,8 +523,9 @@ __global__ void __launch_bounds__(kSfThreads, (W <= 4 ? 3 : 2)) k_scatter_sf(SfA
                     for (int f = 0; f < NF; ++f) c3[f] = CS3[q3 * NF + f];
 #pragma unroll
                     for (int nu = 0; nu < NM; ++nu) {
-                        wq[nu] = __ldg(a.hw32 + q * NM + nu);
-                        nq[nu] = __ldg(a.n32 + q * NM + nu);
+                        const float2 v = __ldg(a.wn + (int64_t)nu * a.nk + q);
+                        wq[nu] = v.x;
+                        nq[nu] = v.y;
                     }
                     int lokq = 0, nwkq = 0;
                     int64_t grow = 0;                        // this band's row of the pair's Gamma block
@@ -519,7 +534,7 @@ __global__ void __launch_bounds__(kSfThreads, (W <= 4 ? 3 : 2)) k_scatter_sf(SfA
                         nwkq = __ldg(a.win_n + ikq);
                         grow = a.goff[P0 + seg0 + t] + (int64_t)n * nwkq - lokq;
                     }
-                    const float2 *uq = a.u32 + q * (NM * NM);
+                    const float2 *uq = a.uS + q;                     // element e at uq[e * nk]
                     // small shapes: G (every column) once per pair, shared by its bands
                     float2 Gp[kPreG ? X : 1];
                     if constexpr (kPreG) {
@@ -604,7 +619,8 @@ __global__ void __launch_bounds__(kSfThreads, (W <= 4 ? 3 : 2)) k_scatter_sf(SfA
 #pragma unroll
                             for (int i = 0; i < W; ++i) h = cfmacf(Vc[i], G[i], h);
 #pragma unroll
-                            for (int nu = 0; nu < NM; ++nu) gv[nu] = cfmaf(h, __ldg(uq + mu * NM + nu), gv[nu]);
+                            for (int nu = 0; nu < NM; ++nu)
+                                gv[nu] = cfmaf(h, __ldg(uq + (int64_t)(mu * NM + nu) * a.nk), gv[nu]);
                         }
                         float gm = 0.f;                      // Gamma capture: sum over modes
 #pragma unroll
@@ -735,6 +751,13 @@ void sf_prepare(epwi_ctx *c) {
     k_band_major_ef<<<(unsigned)((ne + 255) / 256), 256, 0, c->stream>>>(c->nk, W, c->tc_erel.as<float>(),
                                                                         c->tc_f32.as<float>(), c->sf_ef.as<float2>());
     EPWI_CHECK_LAUNCH();
+    const int64_t nu = c->nk * NM * NM;
+    c->sf_uS.ensure(sizeof(float2) * nu);
+    c->sf_wn.ensure(sizeof(float2) * c->nk * NM);
+    k_soa_q<<<(unsigned)((nu + 255) / 256), 256, 0, c->stream>>>(c->nk, NM, c->u32.as<float2>(), c->tc_hw32.as<float>(),
+                                                                c->tc_n32.as<float>(), c->sf_uS.as<float2>(),
+                                                                c->sf_wn.as<float2>());
+    EPWI_CHECK_LAUNCH();
 }
 
 void sf_restage(epwi_ctx *c, const RestageArgs &ra_in) {
@@ -798,6 +821,8 @@ void sf_scatter(epwi_ctx *c, const ScatterArgs &sa, int64_t nkp, const int64_t *
     a.pairs = sa.pairs;
     a.Vb32 = c->sf_Vt32.as<float2>();
     a.ef = c->sf_ef.as<float2>();
+    a.uS = c->sf_uS.as<float2>();
+    a.wn = c->sf_wn.as<float2>();
     a.nk = c->nk;
     a.u32 = sa.u32;
     a.erel = c->tc_erel.as<float>();
