@@ -436,13 +436,39 @@ epwi_status epwi_find_mu(epwi_ctx *c, double T, double n_c, int32_t nv, double *
         const double *e = c->eps.as<double>();
         double lo = device_reduce_minmax(c, e, c->nk, c->nw, nv, false) - 3.0;
         double hi = device_reduce_minmax(c, e, c->nk, c->nw, c->nw - 1, true) + 3.0;
+        // n(mu) is increasing and nearly exponential below the band edge, so the root of
+        // h(mu) = ln n(mu) - ln n_c is bracketed and found by regula falsi with the Illinois
+        // modification (a retained end's h is halved), falling back to bisection where h is not
+        // finite (n underflowed); stop at the same residual as a bisection: |n - n_c| <= 1e-13 n_c.
+        auto h = [&](double mu, double &n) {
+            n = carrier_density(c, T, mu, nv);
+            return n > 0 ? std::log(n / n_c) : -HUGE_VAL;
+        };
+        double nlo, nhi;
+        double hlo = h(lo, nlo), hhi = h(hi, nhi);
         double mid = 0.5 * (lo + hi);
+        int side = 0;
         for (int it = 0; it < 400; ++it) {
-            mid = 0.5 * (lo + hi);
-            const double n = carrier_density(c, T, mid, nv);
+            if (std::isfinite(hlo) && std::isfinite(hhi) && hhi > hlo) {
+                mid = hi - hhi * (hi - lo) / (hhi - hlo);
+                if (!(mid > lo && mid < hi)) mid = 0.5 * (lo + hi);
+            } else {
+                mid = 0.5 * (lo + hi);
+            }
+            double n;
+            const double hm = h(mid, n);
             if (std::fabs(n - n_c) <= 1e-13 * n_c || hi - lo <= 1e-15) break;
-            if (n < n_c) lo = mid;
-            else hi = mid;
+            if (n < n_c) {
+                lo = mid;
+                hlo = hm;
+                if (side == -1 && std::isfinite(hhi)) hhi *= 0.5;
+                side = -1;
+            } else {
+                hi = mid;
+                hhi = hm;
+                if (side == 1 && std::isfinite(hlo)) hlo *= 0.5;
+                side = 1;
+            }
         }
         *mu_out = mid;
     });

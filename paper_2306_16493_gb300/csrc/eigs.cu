@@ -138,7 +138,8 @@ __global__ void __launch_bounds__(128) k_eig_el(GridInfo g, int64_t nk, int W, i
         }
     }
     double w[WMAX];
-    int ok = jacobi_hermitian<WMAX>(A, Vm, W, w);
+    // FP64 results either way; the mixed solver where the FP64 Jacobi binds (8 x 8)
+    int ok = WMAX >= 8 ? jacobi_hermitian_mixed<WMAX>(A, Vm, W, w) : jacobi_hermitian<WMAX>(A, Vm, W, w);
     if (!ok) atomicAdd(flag, 1);
     for (int n = 0; n < W; ++n) {
         eps[ik * W + n] = w[n];
@@ -227,7 +228,7 @@ __global__ void __launch_bounds__(128) k_eig_ph(GridInfo g, int64_t nq, int Nm, 
         }
     }
     double lam[NMAX];
-    int ok = jacobi_hermitian<NMAX>(A, E, Nm, lam);
+    int ok = NMAX >= 6 ? jacobi_hermitian_mixed<NMAX>(A, E, Nm, lam) : jacobi_hermitian<NMAX>(A, E, Nm, lam);
     if (!ok) atomicAdd(flag, 1);
     float wmax = -1.f;
     for (int nu = 0; nu < Nm; ++nu) {

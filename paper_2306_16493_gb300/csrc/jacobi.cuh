@@ -95,6 +95,108 @@ __host__ __device__ inline int jacobi_hermitian(double2 (&A)[NMAX * NMAX], doubl
     return converged;
 }
 
+// Mixed-precision variant with the same FP64 result (GB300 runs FP64 at 1/64 of the FP32
+// rate): (1) the rotations of jacobi_hermitian in FP32 on a rounded copy of A, until the
+// off-diagonal norm is below ~3e-6 of the full norm (FP32 cannot go much further) or 30 sweeps;
+// (2) those eigenvectors made orthonormal in FP64 (one modified Gram-Schmidt pass, starting
+// from columns orthonormal to FP32 accuracy); (3) B = V1^dag A V1 in FP64, diagonal to FP32
+// accuracy; (4) jacobi_hermitian on B in FP64, which converges in one or two sweeps and
+// handles (near-)degenerate blocks like the plain solver; (5) V = V1 Q.  The stopping rule of
+// the FP64 stage is that of jacobi_hermitian, so the eigenpairs are FP64-accurate.
+template <int NMAX>
+__host__ __device__ inline int jacobi_hermitian_mixed(double2 (&A)[NMAX * NMAX], double2 (&V)[NMAX * NMAX],
+                                                      int n, double *w) {
+    float2 a[NMAX * NMAX], v[NMAX * NMAX];
+    for (int i = 0; i < n * n; ++i) a[i] = make_float2((float)A[i].x, (float)A[i].y);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) v[i * n + j] = make_float2(i == j ? 1.f : 0.f, 0.f);
+    for (int sweep = 0; sweep < 30; ++sweep) {
+        float off = 0, tot = 0;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                const float m2 = a[i * n + j].x * a[i * n + j].x + a[i * n + j].y * a[i * n + j].y;
+                tot += m2;
+                if (i != j) off += m2;
+            }
+        if (off <= 1e-11f * tot) break;
+        for (int p = 0; p < n - 1; ++p) {
+            for (int q = p + 1; q < n; ++q) {
+                const float2 apq = a[p * n + q];
+                const float mag = sqrtf(apq.x * apq.x + apq.y * apq.y);
+                if (mag == 0.f) continue;
+                const float app = a[p * n + p].x, aqq = a[q * n + q].x;
+                const float zeta = (aqq - app) / (2.f * mag);
+                const float t = fabsf(zeta) > 1e18f ? 0.5f / zeta
+                                                    : (zeta >= 0 ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+                const float c = 1.f / sqrtf(1.f + t * t), sn = t * c;
+                const float2 e = make_float2(apq.x / mag, apq.y / mag);
+                const float2 se = make_float2(sn * e.x, sn * e.y), sec = make_float2(sn * e.x, -sn * e.y);
+                for (int r = 0; r < n; ++r) {
+                    const float2 ap = a[r * n + p], aq = a[r * n + q];
+                    a[r * n + p] = make_float2(c * ap.x - (sec.x * aq.x - sec.y * aq.y), c * ap.y - (sec.x * aq.y + sec.y * aq.x));
+                    a[r * n + q] = make_float2(se.x * ap.x - se.y * ap.y + c * aq.x, se.x * ap.y + se.y * ap.x + c * aq.y);
+                    const float2 vp = v[r * n + p], vq = v[r * n + q];
+                    v[r * n + p] = make_float2(c * vp.x - (sec.x * vq.x - sec.y * vq.y), c * vp.y - (sec.x * vq.y + sec.y * vq.x));
+                    v[r * n + q] = make_float2(se.x * vp.x - se.y * vp.y + c * vq.x, se.x * vp.y + se.y * vp.x + c * vq.y);
+                }
+                for (int col = 0; col < n; ++col) {
+                    const float2 bp = a[p * n + col], bq = a[q * n + col];
+                    a[p * n + col] = make_float2(c * bp.x - (se.x * bq.x - se.y * bq.y), c * bp.y - (se.x * bq.y + se.y * bq.x));
+                    a[q * n + col] = make_float2(sec.x * bp.x - sec.y * bp.y + c * bq.x, sec.x * bp.y + sec.y * bp.x + c * bq.y);
+                }
+                a[p * n + q] = make_float2(0.f, 0.f);
+                a[q * n + p] = make_float2(0.f, 0.f);
+                a[p * n + p] = make_float2(app - t * mag, 0.f);
+                a[q * n + q] = make_float2(aqq + t * mag, 0.f);
+            }
+        }
+    }
+    // V1: the FP32 columns, orthonormal in FP64 (modified Gram-Schmidt)
+    double2 V1[NMAX * NMAX];
+    for (int i = 0; i < n * n; ++i) V1[i] = make_double2(v[i].x, v[i].y);
+    for (int j = 0; j < n; ++j) {
+        for (int i = 0; i < j; ++i) {
+            double2 r = make_double2(0, 0);
+            for (int k = 0; k < n; ++k) r = cfmac(V1[k * n + i], V1[k * n + j], r);   // <v_i, v_j>
+            for (int k = 0; k < n; ++k) {
+                const double2 t = cmul(r, V1[k * n + i]);
+                V1[k * n + j] = make_double2(V1[k * n + j].x - t.x, V1[k * n + j].y - t.y);
+            }
+        }
+        double nrm = 0;
+        for (int k = 0; k < n; ++k) nrm += V1[k * n + j].x * V1[k * n + j].x + V1[k * n + j].y * V1[k * n + j].y;
+        const double inv = 1.0 / sqrt(nrm);
+        for (int k = 0; k < n; ++k) V1[k * n + j] = make_double2(V1[k * n + j].x * inv, V1[k * n + j].y * inv);
+    }
+    // B = V1^dag A V1 (FP64), into A; V receives T = A V1 first
+    for (int r = 0; r < n; ++r)
+        for (int j = 0; j < n; ++j) {
+            double2 t = make_double2(0, 0);
+            for (int k = 0; k < n; ++k) t = cfma(A[r * n + k], V1[k * n + j], t);
+            V[r * n + j] = t;
+        }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double2 t = make_double2(0, 0);
+            for (int k = 0; k < n; ++k) t = cfmac(V1[k * n + i], V[k * n + j], t);
+            A[i * n + j] = t;
+        }
+    // Hermitian to rounding: keep the upper triangle's values on both sides
+    for (int i = 0; i < n; ++i) {
+        A[i * n + i].y = 0;
+        for (int j = i + 1; j < n; ++j) A[j * n + i] = make_double2(A[i * n + j].x, -A[i * n + j].y);
+    }
+    double2 Q[NMAX * NMAX];
+    const int ok = jacobi_hermitian<NMAX>(A, Q, n, w);
+    for (int r = 0; r < n; ++r)
+        for (int j = 0; j < n; ++j) {
+            double2 t = make_double2(0, 0);
+            for (int k = 0; k < n; ++k) t = cfma(V1[r * n + k], Q[k * n + j], t);
+            V[r * n + j] = t;
+        }
+    return ok;
+}
+
 // Warp-parallel variant for n <= 32 (one warp per matrix, matrices in shared memory with
 // row stride ld = n + 1).  The same rotation and stopping rule as jacobi_hermitian, applied in
 // the parallel (round-robin) ordering: in each of the n' - 1 rounds of a sweep (n' = n rounded
