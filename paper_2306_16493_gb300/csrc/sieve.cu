@@ -199,15 +199,20 @@ __global__ void k_seg_ranges(int N1, int64_t nplane, int W, int nseg, const floa
 }
 
 // k_sieve_count for compile-time W and N_m, with the same candidates, decisions and mask
-// layout, and lanes kept busy.  Every candidate is first prefiltered: any decision that
-// pair_valid_t takes needs some k+q energy within hwmax(q) + c eta + delta of a window energy
-// at k, so a candidate whose k+q energies all lie outside [min window energy - hwmax - pad,
-// max window energy + hwmax + pad] is rejected at once (pad exceeds the FP32 rounding of
-// either form).  The candidates that pass go into a per-warp queue in shared memory with the
-// mask of their bands within reach; each time 32 are waiting, the warp evaluates them with
-// pair_valid_bands (the exact test on those bands), one per lane, and ORs the decisions into
-// the plane block's mask words, kept in shared memory and written out in k_sieve_count's
-// layout.  Indices are 32-bit (N_k < 2^31, checked).
+// layout.  A candidate is decided from hm = hwmax(q) and the smallest distance
+// dmin = min_{n,m} |e_n(k) - e_m(k+q)| (FP32, n over the window bands, m over all bands):
+// - dmin > hm + c eta + delta: every (n, m, nu, s) has |(e_n + s w_nu) - e_m| > c eta, since
+//   every kept mode has w_nu <= hm and delta bounds the FP32 rounding (reject);
+// - hm <= c eta - 2 delta and dmin <= hm + c eta - delta: for the (n, m) of dmin, the mode of
+//   energy hm with the sign opposite to d = e_n - e_m gives ||d| - hm| <= c eta - delta
+//   (|d| >= hm) or <= hm <= c eta - 2 delta (|d| < hm), so the FP64 test holds (accept);
+// - otherwise pair_valid_tail decides (FP32 per mode, FP64 where ambiguous).
+// Every outcome therefore equals the FP64 evaluation of pair_valid.  The first two cases cover
+// nearly every candidate when the phonon energies lie below c eta (the Gaussian's support is
+// wider than the phonon band); the third runs inline for the few others.  The lanes of a warp
+// take 32 consecutive (q2, q3) combinations of a plane block and 2-4 consecutive q1 per step;
+// their ballots are the plane block's mask words, kept in shared memory and written out in
+// k_sieve_count's layout.  Indices are 32-bit (N_k < 2^31, checked).
 //
 // With FILL the same kernel writes the pair lists of k-points kp0 + blockIdx.x instead (used
 // when the whole decision mask would not fit in memory): after each plane block the CTA scans
@@ -216,10 +221,9 @@ __global__ void k_seg_ranges(int N1, int64_t nplane, int W, int nseg, const floa
 //
 // Segment pruning: the candidates of one k+q column whose axis-1 points lie in one segment of
 // kSegLen (aligned in k+q space, so the same for every lane of a warp) are all rejected at once
-// when no band's energy range over the segment comes within seglim (>= hwmax(q) + pad for every
-// q, with a margin over FP32 rounding) of the window energies: each of their prefilters would
-// fail.  A warp whose lanes all reject a segment skips its iterations.
-constexpr int kQueue = 64;
+// when no band's energy range over the segment comes within seglim (>= hwmax(q) + c eta +
+// delta for every q, with a margin over FP32 rounding) of the window energies.  A warp whose
+// lanes all reject a segment skips its iterations.
 template <int WT, int NMT, bool FILL>
 __global__ void __launch_bounds__(256, 4) k_sieve_count_fast(SieveArgs a, const int *__restrict__ kpts,
                                                           const int *__restrict__ lo,
@@ -232,41 +236,30 @@ __global__ void __launch_bounds__(256, 4) k_sieve_count_fast(SieveArgs a, const 
     __shared__ double en[epc::kMaxW];
     __shared__ float en32[epc::kMaxW];
     __shared__ int64_t sm[33];
-    __shared__ int qiq[8][kQueue], qkq[8][kQueue], qwb[8][kQueue];
     extern __shared__ uint32_t words[];          // [N1][8]: decisions of the current plane block
+    constexpr int kUnr = WT >= 8 ? 2 : 4;        // candidates per step (registers for their energies)
     const int64_t kp = FILL ? kp0 + blockIdx.x : blockIdx.x;
     const int ik = kpts[kp];
     const int nsel = cnt[ik];
     load_window(a, ik, lo[ik], nsel, en, en32);
+    // window energies in registers; absent bands sit far away and never give the minimum
+    float e[WT];
+#pragma unroll
+    for (int n = 0; n < WT; ++n) e[n] = n < nsel ? en32[n] : 3.0e38f;
     float elo = en32[0], ehi = en32[0];
     for (int n = 1; n < nsel; ++n) {
         elo = fminf(elo, en32[n]);
         ehi = fmaxf(ehi, en32[n]);
     }
-    const float pad = a.lim_extra + 1e-4f;
+    const float rej = a.ceta32 + a.delta32, acc = a.ceta32 - a.delta32;
+    const float hm_fast = a.ceta32 - 2.f * a.delta32;
     int ka1, ka2, ka3;
     grid_coords(a.g, ik, ka1, ka2, ka3);
     const int N1 = a.g.n1, nplane = a.g.n2 * a.g.n3;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const unsigned lt = (1u << lane) - 1u;
     uint32_t *mrow = (mask && !FILL) ? mask + (int64_t)blockIdx.x * words_per_kp + wid : nullptr;
     int64_t obase = FILL ? kp_pairs[kp] - kp_pairs[kp0] : 0;   // next output position (FILL)
-    int *Qi = qiq[wid], *Qk = qkq[wid], *Qw = qwb[wid];
-    // evaluates queue entry e (if valid) and records its decision
-    auto run = [&](int e, bool valid) {
-        if (valid) {
-            const int slot = e & (kQueue - 1);
-            const int iq = Qi[slot], ikq = Qk[slot];
-            const unsigned wq = (unsigned)Qw[slot];          // (i1 * 32 + lane) << 8 | near bands
-            const unsigned wb = wq >> 8;
-            float em[WT];
-            load_kq_energies<WT>(a, ikq, em);
-            if (pair_valid_bands<WT, NMT>(a, nsel, en, en32, iq, ikq, a.hwmax32[iq], em, wq & 0xffu))
-                atomicOr(&words[(wb >> 5) * 8 + wid], 1u << (wb & 31));
-        }
-    };
     int c = 0;
-    int head = 0, tail = 0;                      // warp-uniform queue positions
     for (int pb = 0, pbi = 0; pb < nplane; pb += blockDim.x, ++pbi) {
         const int p = pb + threadIdx.x;
         const bool inb = p < nplane;
@@ -295,42 +288,62 @@ __global__ void __launch_bounds__(256, 4) k_sieve_count_fast(SieveArgs a, const 
                 if (b1 >= N1) b1 -= N1;
                 continue;
             }
-            for (int u = 0; u < len; ++u, ++i1) {
-            unsigned nm = 0;                     // bands within reach of a window energy
-            int ikq = 0;
-            if (segok) {
-                const float hm = a.hwmax32[iq];
-                if (hm >= 0.f) {
-                    ikq = b1 * nplane + kqp;
-                    float em[WT];
-                    load_kq_energies<WT>(a, ikq, em);
-                    const float lo_ = elo - hm - pad, hi_ = ehi + hm + pad;
+            for (int u = 0; u < len; u += kUnr) {
+                // kUnr candidates (q1 = i1 .. i1 + kUnr - 1 of this segment): loads first
+                float hm[kUnr], em[kUnr][WT];
 #pragma unroll
-                    for (int m = 0; m < WT; ++m) nm |= ((em[m] >= lo_) & (em[m] <= hi_) ? 1u : 0u) << m;
+                for (int j = 0; j < kUnr; ++j) {
+                    hm[j] = -1.f;
+                    if (segok && u + j < len) {
+                        int bj = b1 + j;
+                        if (bj >= N1) bj -= N1;
+                        hm[j] = a.hwmax32[iq + j * nplane];
+                        load_kq_energies<WT>(a, (int64_t)bj * nplane + kqp, em[j]);
+                    }
                 }
-            }
-            const bool near = nm != 0;
-            const unsigned bal = __ballot_sync(0xffffffffu, near);
-            if (near) {
-                const int slot = (tail + __popc(bal & lt)) & (kQueue - 1);
-                Qi[slot] = iq;
-                Qk[slot] = ikq;
-                Qw[slot] = (int)((((unsigned)i1 * 32u + (unsigned)lane) << 8) | nm);
-            }
-            tail += __popc(bal);
-            if (tail - head >= 32) {
-                __syncwarp();
-                run(head + lane, true);
-                head += 32;
-                __syncwarp();
-            }
-            iq += nplane;
-            if (++b1 == N1) b1 = 0;
+                unsigned vbits = 0, amb = 0;
+#pragma unroll
+                for (int j = 0; j < kUnr; ++j) {
+                    if (hm[j] >= 0.f) {
+                        float d = 3.0e38f;
+#pragma unroll
+                        for (int n = 0; n < WT; ++n) {
+                            if (n < nsel) {
+#pragma unroll
+                                for (int m = 0; m < WT; ++m) d = fminf(d, fabsf(e[n] - em[j][m]));
+                            }
+                        }
+                        if (d <= hm[j] + rej) {
+                            if (hm[j] <= hm_fast && d <= hm[j] + acc) vbits |= 1u << j;
+                            else amb |= 1u << j;
+                        }
+                    }
+                }
+                // the rest: exact per-mode test
+#pragma unroll 1
+                for (int j = 0; j < kUnr; ++j) {
+                    if (!((amb >> j) & 1u)) continue;
+                    int bj = b1 + j;
+                    if (bj >= N1) bj -= N1;
+                    const int64_t ikq = (int64_t)bj * nplane + kqp;
+                    float emj[WT];
+                    load_kq_energies<WT>(a, ikq, emj);
+                    const int64_t iqj = iq + j * nplane;
+                    if (pair_valid_tail<WT, NMT>(a, nsel, en, en32, iqj, ikq, a.hwmax32[iqj], emj))
+                        vbits |= 1u << j;
+                }
+#pragma unroll
+                for (int j = 0; j < kUnr; ++j) {
+                    const unsigned bits = __ballot_sync(0xffffffffu, (vbits >> j) & 1u);
+                    if (lane == 0 && u + j < len) words[(i1 + j) * 8 + wid] = bits;
+                }
+                const int step = min(kUnr, len - u);
+                i1 += step;
+                iq += step * nplane;
+                b1 += step;
+                if (b1 >= N1) b1 -= N1;
             }
         }
-        __syncwarp();
-        run(head + lane, head + lane < tail);    // the rest of the queue
-        head = tail;
         __syncwarp();
         if constexpr (FILL) {
             __syncthreads();                     // every warp's words of this plane block
@@ -367,37 +380,40 @@ __global__ void __launch_bounds__(256, 4) k_sieve_count_fast(SieveArgs a, const 
 }
 
 // Pair lists from the decision mask of k_sieve_count, in the same candidate order: each
-// thread takes one mask word, the block scans the word populations in word order, and
-// every thread writes the q of its word's set bits in bit order.
+// thread takes one mask word, the block scans the word populations in word order, every
+// thread puts the q of its word's set bits (in bit order) at their places in a shared buffer,
+// and the block copies the buffer out with consecutive threads on consecutive pairs.
 __global__ void __launch_bounds__(256) k_sieve_fill_mask(GridInfo g, int64_t kp0,
                                                          const uint32_t *__restrict__ mask,
                                                          int64_t words_per_kp, int count_block,
                                                          const int64_t *__restrict__ kp_pairs,
                                                          int *__restrict__ pairs) {
     __shared__ int64_t sm[33];
+    __shared__ int buf[256 * 32];
     const int64_t kp = kp0 + blockIdx.x;
     const uint32_t *mrow = mask + kp * words_per_kp;
     const int64_t nplane = (int64_t)g.n2 * g.n3;
     const int wpb = count_block >> 5;
-    int64_t base = kp_pairs[kp] - kp_pairs[kp0];
+    int *out = pairs + (kp_pairs[kp] - kp_pairs[kp0]);
     for (int64_t w0 = 0; w0 < words_per_kp; w0 += blockDim.x) {
         const int64_t w = w0 + threadIdx.x;
         uint32_t bits = w < words_per_kp ? mrow[w] : 0u;
         int64_t tot;
-        const int64_t off = block_excl_scan((int64_t)__popc(bits), sm, tot);
+        int o = (int)block_excl_scan((int64_t)__popc(bits), sm, tot);
         if (bits) {
             const int64_t grp = w / wpb;                 // (plane block, i1) group
             const int64_t pbi = grp / g.n1, i1 = grp % g.n1;
-            const int64_t t0 = (w % wpb) * 32;
-            int64_t o = base + off;
+            const int q0 = (int)(i1 * nplane + pbi * count_block + (w % wpb) * 32);
             while (bits) {
                 const int b = __ffs(bits) - 1;
                 bits &= bits - 1;
-                const int64_t p = pbi * count_block + t0 + b;
-                pairs[o++] = (int)(i1 * nplane + p);
+                buf[o++] = q0 + b;
             }
         }
-        base += tot;
+        __syncthreads();
+        for (int i = threadIdx.x; i < (int)tot; i += blockDim.x) out[i] = buf[i];
+        out += tot;
+        __syncthreads();                                 // buf is refilled next
     }
 }
 

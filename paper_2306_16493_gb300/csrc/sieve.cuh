@@ -132,57 +132,9 @@ __device__ __forceinline__ bool pair_valid_tail(const SieveArgs &a, int nsel, co
     return false;
 }
 
-// pair_valid for compile-time W and N_m (pair_valid_t below): the k+q energies in 16-byte
-// loads, the mode energies loaded once per candidate, the FP32 tests in pair_valid's
-// arithmetic, and the FP64 re-check of pair_valid for candidates near c eta.  Same outcome as
-// pair_valid.
-// pair_valid_tail restricted to the final bands in nm (bit m): the FP32 tests of those bands,
-// then the FP64 re-check of those bands if one of them is ambiguous.  Same outcome as
-// pair_valid_tail when nm holds every band m with some window energy within lim + 1e-4 of
-// eps_m(k+q): any other band has |x| > c eta + delta for every mode and sign in FP32, hence
-// |x| > c eta in FP64, and decides nothing.
-template <int WT, int NMT>
-__device__ __forceinline__ bool pair_valid_bands(const SieveArgs &a, int nsel, const double *en,
-                                                 const float *en32, int64_t iq, int64_t ikq, float hm,
-                                                 const float (&em)[WT], unsigned nm) {
-    const float lim = hm + a.lim_extra;
-    const float inner = a.ceta32 - a.delta32, outer = a.ceta32 + a.delta32;
-    float w[NMT];
-#pragma unroll
-    for (int nu = 0; nu < NMT; ++nu) w[nu] = a.hw32[iq * NMT + nu];
-    bool ambiguous = false;
-#pragma unroll
-    for (int m = 0; m < WT; ++m) {
-        if (!((nm >> m) & 1u)) continue;
-        for (int n = 0; n < nsel; ++n) {
-            const float d = en32[n] - em[m];
-            if (!(fabsf(d) <= lim)) continue;
-#pragma unroll
-            for (int nu = 0; nu < NMT; ++nu) {
-                if (w[nu] < 0.f) continue;
-                const float xm = fminf(fabsf(d + w[nu]), fabsf(d - w[nu]));
-                if (xm <= inner) return true;
-                if (xm <= outer) ambiguous = true;
-            }
-        }
-    }
-    if (!ambiguous) return false;
-    for (int m = 0; m < WT; ++m) {
-        if (!((nm >> m) & 1u)) continue;
-        const double emd = a.eps[ikq * WT + m];
-        for (int nu = 0; nu < NMT; ++nu) {
-            const double wd = a.hw[iq * NMT + nu];
-            if (!(wd >= a.omega_min)) continue;
-            for (int n = 0; n < nsel; ++n) {
-                const double x1 = (en[n] + wd) - emd;
-                const double x2 = (en[n] - wd) - emd;
-                if (fabs(x1) <= a.ceta || fabs(x2) <= a.ceta) return true;
-            }
-        }
-    }
-    return false;
-}
-
+// pair_valid for compile-time W and N_m: the k+q energies in 16-byte loads, the mode energies
+// loaded once per candidate, the FP32 tests in pair_valid's arithmetic, and the FP64 re-check
+// of pair_valid for candidates near c eta.  Same outcome as pair_valid.
 template <int WT, int NMT>
 __device__ __forceinline__ bool pair_valid_t(const SieveArgs &a, int nsel, const double *en, const float *en32,
                                              int64_t iq, int64_t ikq) {
