@@ -142,8 +142,10 @@ typedef struct {
     double ms_rates;            /* window, sieve, interpolation, 1/tau and the Gamma capture */
     double ms_iterate;          /* every iteration: step kernels and convergence reads */
     double ms_step;             /* mean device time of one step kernel */
-    double bytes_per_step;      /* algorithmic bytes of one step: q list, Gamma, F0, tau, F
-                                   read and written once */
+    double bytes_per_step;      /* algorithmic bytes of one step: the index, Gamma, F0, tau,
+                                   F read and written once */
+    int64_t index_bytes;        /* the step's index: a 4-byte column word per Gamma entry and
+                                   an 8-byte offset per window k-point */
 } epwi_ibte_stats;
 
 /* Fills *opt with the defaults listed above. */

@@ -192,9 +192,10 @@ struct epwi_ctx {
 
     // iterative BTE: Gamma in pair blocks, mean free paths
     bool have_ibte = false;
-    DevBuf ib_pairs;               // int32 q index per pair (all k-points of the window)
+    DevBuf ib_pairs;               // int32 q index per pair (all k-points of the window; capture only)
     DevBuf ib_goff;                // int64 [npairs + 1] first Gamma entry of each pair (capture only)
-    DevBuf ib_wbase;               // int64 [nkp][8] first Gamma entry of each step warp range
+    DevBuf ib_col;                 // uint32 per Gamma entry: (final state << 5) | band of k (step only)
+    DevBuf ib_ent;                 // int64 [nkp + 1] first Gamma entry of each window k-point
 
     // point-group symmetry of the rates (epwi_set_symmetry, sym.cu)
     std::vector<int> sym_ops;      // [nops][3][3] k-space operations on grid index vectors
@@ -219,7 +220,7 @@ struct epwi_ctx {
                          &scan_tmp, &red_tmp, &counts, &tc_ptab, &tc_erel, &tc_f32,
                          &tc_n32, &tc_hw32, &tc_err, &tc_meta, &is_pairs, &is_w,
                          &is_kp_pairs, &sieve_mask, &tc_arows, &ib_pairs, &ib_goff, &ib_gam,
-                         &ib_kpos, &ib_F0, &ib_F, &ib_Fn, &ib_red, &ib_F32, &ib_Fn32, &sf_items, &ib_wbase, &sym_rep, &seg_ranges,
+                         &ib_kpos, &ib_F0, &ib_F, &ib_Fn, &ib_red, &ib_F32, &ib_Fn32, &sf_items, &ib_col, &ib_ent, &sym_rep, &seg_ranges,
                          &gsf32, &sf_Vt32, &sf_ef, &sf_uS, &sf_wn, &gcube32, &fac_Hc, &fac_Pc, &fac_T, &fac_U};
         for (DevBuf *b : all) b->release();
         mlp_free(mlp);

@@ -7,22 +7,23 @@
 // the summand of Eq. 10 without its constant 2 pi / (hbar N_q sqrt(pi) eta), which the step
 // applies once per state.
 //
-// After the capture each pair's q index is replaced in place by a step code: the first state
-// of the final k-point's window (sb) and its band count (nw), (sb << 5) | nw.  The step then
-// reads one word per pair and needs no grid arithmetic or table lookups.  The per-pair block
-// offsets are needed only by the capture: afterwards the step keeps one offset per (k-point,
-// warp range) (wbase) and the per-pair array is freed, so the resident index is the step code
-// per pair plus 64 bytes per k-point.
+// After the capture every Gamma entry gets a 4-byte column word: the index of its final state
+// (k+q, m) in the window's state list and the band n of k, (s << 5) | n.  The step is then a
+// sparse product over entries, Gamma_e F_s accumulated into the row of band n of k: it reads one
+// column word and one value per entry, gathers F at s, and needs no grid arithmetic or table
+// lookups.  The pair list and the per-pair block offsets serve only the capture and are freed
+// afterwards, so the resident index is the column word per entry plus 8 bytes per k-point
+// (half the bytes of FP64 Gamma, equal to those of FP32 Gamma).
 //
-// Step: one block per window k-point, eight warps splitting its pairs into contiguous ranges,
-// the k-point's bands taken in register groups of 1, 2, 4 or 8 (the smallest that covers the
-// crystal's bands) with the inner loop specialised to the group's exact band count.  With
-// FP32 Gamma (split paths) the lanes accumulate and reduce in FP32 from an FP32 copy of F;
-// the sum over warps, the per-state update and F itself are FP64.
-// A warp takes 32 pairs at a time (the next 32 codes are loaded ahead); a warp scan of the
-// block sizes n_k x n_{k+q} gives each lane its block, and the lane accumulates
-// Gamma[n][m] F_{m,k+q} for its pair.  Per-state sums are reduced in a fixed order (lanes by a
-// butterfly, then warps in index order), so the result does not depend on scheduling.
+// Step: one block per window k-point, its entries split into eight contiguous warp ranges;
+// lanes take entries 32 apart, several at a time with their loads issued together (coalesced
+// column and value loads, F gathers from a table that stays in L2).  The k-point's bands are
+// accumulated in registers in groups of 1, 2, 4 or 8 (the smallest covering the crystal's
+// bands) with the band selection specialised to the window's exact band count (none for one
+// band).  With FP32 Gamma (split paths) the lanes accumulate and reduce in FP32 from an FP32
+// copy of F; the sum over warps, the per-state update and F itself are FP64.  Per-state sums
+// are reduced in a fixed order (lanes by a butterfly, then warps in index order), so the result
+// does not depend on scheduling.
 #include <algorithm>
 #include <cstring>
 #include <type_traits>
@@ -35,19 +36,7 @@ namespace {
 constexpr int kIbThreads = 256;
 constexpr int kIbWarps = kIbThreads / 32;
 constexpr int kIbMaxBands = 8;  // bands of k accumulated in registers at a time (at most)
-constexpr int kPpl = 2;         // narrow-window path: pairs per lane whose loads are in flight together
-
-// First Gamma entry of every (k-point, warp range) of k_ib_step (same range formula).
-__global__ void k_ib_wbase(int64_t nkp, const int64_t *__restrict__ kp_pairs, const int64_t *__restrict__ goff,
-                           int64_t *__restrict__ wbase) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nkp * kIbWarps) return;
-    const int64_t kp = t / kIbWarps;
-    const int w = (int)(t % kIbWarps);
-    const int64_t p0 = kp_pairs[kp], np = kp_pairs[kp + 1] - p0;
-    const int64_t wb = p0 + np * w / kIbWarps, we = p0 + np * (w + 1) / kIbWarps;
-    wbase[t] = wb < we ? goff[wb] : 0;
-}
+constexpr int kIbUnroll = 4;    // entries per lane whose loads are issued together
 
 __global__ void k_ib_kpos(int64_t nkp, const int *__restrict__ kpts, int *__restrict__ kpos) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -65,17 +54,29 @@ __global__ void k_ib_sizes(GridInfo g, const int *__restrict__ kpts, const int *
         sizes[p] = (int64_t)nsel * win_n[kplusq(g, ik, pairs[p])];
 }
 
-// q index -> step code (sb << 5) | nw of the final k-point, in place; one block per k-point
-__global__ void k_ib_encode(GridInfo g, const int *__restrict__ kpts, const int *__restrict__ win_n,
-                            const int *__restrict__ kpos, const int64_t *__restrict__ kp_state,
-                            const int64_t *__restrict__ kp_pairs, unsigned *__restrict__ code) {
+// Column words of the Gamma entries: entry goff[p] + n nw + j of pair p = (k, q) gets
+// ((s + j) << 5) | n, s the first window state of k+q, j its band, n the band of k; and the
+// first entry of every window k-point (ent[nkp] = the entry count).  One block per k-point.
+__global__ void k_ib_columns(GridInfo g, int64_t nkp, const int *__restrict__ kpts, const int *__restrict__ win_n,
+                             const int *__restrict__ kpos, const int64_t *__restrict__ kp_state,
+                             const int64_t *__restrict__ kp_pairs, const int *__restrict__ pairs,
+                             const int64_t *__restrict__ goff, unsigned *__restrict__ col,
+                             int64_t *__restrict__ ent) {
     const int kp = blockIdx.x;
     const int ik = kpts[kp];
+    const int nsel = win_n[ik];
     for (int64_t p = kp_pairs[kp] + threadIdx.x; p < kp_pairs[kp + 1]; p += blockDim.x) {
-        const int64_t ikq = kplusq(g, ik, (int)code[p]);
-        const unsigned nw = (unsigned)win_n[ikq];
-        const unsigned sb = nw ? (unsigned)kp_state[kpos[ikq]] : 0u;
-        code[p] = (sb << 5) | nw;
+        const int64_t ikq = kplusq(g, ik, pairs[p]);
+        const int nw = win_n[ikq];
+        if (nw == 0) continue;
+        const unsigned sb = (unsigned)kp_state[kpos[ikq]];
+        unsigned *c = col + goff[p];
+        for (int n = 0; n < nsel; ++n)
+            for (int j = 0; j < nw; ++j) c[n * nw + j] = ((sb + (unsigned)j) << 5) | (unsigned)n;
+    }
+    if (threadIdx.x == 0) {
+        ent[kp] = goff[kp_pairs[kp]];
+        if (kp == nkp - 1) ent[nkp] = goff[kp_pairs[nkp]];
     }
 }
 
@@ -101,9 +102,9 @@ __global__ void k_ib_f0(int64_t ns, int W, const int *__restrict__ st_k, const i
 template <typename GT>
 struct StepArgs {
     const int *kpts, *win_n;
-    const int64_t *kp_state, *kp_pairs;
-    const int64_t *wbase;                 // first Gamma entry of each (k-point, warp range)
-    const unsigned *code;                 // per pair (sb << 5) | nw
+    const int64_t *kp_state;
+    const int64_t *ent;                   // first Gamma entry of each window k-point
+    const unsigned *col;                  // per entry ((final state) << 5) | band of k
     const GT *gam;
     const double *inv_tau, *F0, *Fin;
     double *Fout;
@@ -111,7 +112,6 @@ struct StepArgs {
     float4 *Fout32;
     double pref;                          // 2 pi / (hbar N_q sqrt(pi) eta), s^-1 per eV^2
     unsigned long long *red;              // [2] max |dF|, max |F| as bit patterns
-    int narrow;                           // every window has <= 4 bands: narrow-window path
 };
 
 // Accumulation type of the lane and warp sums: FP64 with FP64 Gamma; FP32 with FP32 Gamma
@@ -133,146 +133,86 @@ __device__ __forceinline__ void load_F(const StepArgs<float> &a, int64_t s, floa
     z = f.z;
 }
 
-// The warp's pairs [wb, we) for the bands b0 .. b0+NBX-1 of the k-point: y[n] += sum over the
-// pairs and final bands m of Gamma[b0+n][m] F_m.
+// The warp's entries [e0, e1) for the bands b0 .. b0+NBX-1 of the k-point: y[n] += Gamma_e F_s
+// for every entry e whose column word holds state s and band b0 + n.  Lane l takes entries
+// e0 + l, e0 + l + 32, ...; kIbUnroll of them have their column, value and F loads issued
+// before their multiplies.  ALL: every entry's band lies in the group (one group covers the
+// window); otherwise an entry of another group adds zero products.
+template <typename GT, int NB, int NBX, bool ALL>
+__device__ __forceinline__ void step_entries(const StepArgs<GT> &a, int b0, int64_t e0, int64_t e1, int lane,
+                                             typename Acc<GT>::T (&y)[NB][3]) {
+    using AT = typename Acc<GT>::T;
+    for (int64_t eb = e0 + lane; eb < e1; eb += 32 * kIbUnroll) {
+        unsigned cw[kIbUnroll];
+        AT g[kIbUnroll], fx[kIbUnroll], fy[kIbUnroll], fz[kIbUnroll];
+#pragma unroll
+        for (int u = 0; u < kIbUnroll; ++u) {
+            const int64_t e = eb + 32 * u;
+            cw[u] = e < e1 ? __ldg(a.col + e) : 0u;
+            g[u] = e < e1 ? (AT)__ldg(a.gam + e) : AT(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kIbUnroll; ++u) load_F(a, (int64_t)(cw[u] >> 5), fx[u], fy[u], fz[u]);
+#pragma unroll
+        for (int u = 0; u < kIbUnroll; ++u) {
+            if constexpr (NBX == 1 && ALL) {
+                y[0][0] = fma(g[u], fx[u], y[0][0]);
+                y[0][1] = fma(g[u], fy[u], y[0][1]);
+                y[0][2] = fma(g[u], fz[u], y[0][2]);
+            } else {
+                const int n = (int)(cw[u] & 31u) - b0;
+#pragma unroll
+                for (int b = 0; b < NBX; ++b) {
+                    const AT gb = n == b ? g[u] : AT(0);
+                    y[b][0] = fma(gb, fx[u], y[b][0]);
+                    y[b][1] = fma(gb, fy[u], y[b][1]);
+                    y[b][2] = fma(gb, fz[u], y[b][2]);
+                }
+            }
+        }
+    }
+}
+
 template <typename GT, int NB, int NBX>
-__device__ __forceinline__ void step_pairs(const StepArgs<GT> &a, int nsel, int b0, int64_t wb, int64_t we,
-                                           int64_t off, int lane, typename Acc<GT>::T (&y)[NB][3]) {
-    using AT = typename Acc<GT>::T;
-    unsigned cnext = wb + lane < we ? __ldg(a.code + wb + lane) : 0u;
-    for (int64_t pb = wb; pb < we; pb += 32) {
-        const unsigned code = cnext;
-        cnext = pb + 32 + lane < we ? __ldg(a.code + pb + 32 + lane) : 0u;
-        const int nw = (int)(code & 31u);
-        const int64_t sb = (int64_t)(code >> 5);
-        const int size = nsel * nw;
-        int incl = size;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        const int tot = __shfl_sync(0xffffffffu, incl, 31);
-        const GT *gb = a.gam + off + (incl - size) + (int64_t)b0 * nw;
-        for (int j = 0; j < nw; ++j) {
-            AT fx, fy, fz;
-            load_F(a, sb + j, fx, fy, fz);
-#pragma unroll
-            for (int n = 0; n < NBX; ++n) {
-                const AT gv = (AT)__ldg(gb + n * nw + j);
-                y[n][0] = fma(gv, fx, y[n][0]);
-                y[n][1] = fma(gv, fy, y[n][1]);
-                y[n][2] = fma(gv, fz, y[n][2]);
-            }
-        }
-        off += tot;
-    }
+__device__ __forceinline__ void step_group(const StepArgs<GT> &a, bool all, int b0, int64_t e0, int64_t e1, int lane,
+                                           typename Acc<GT>::T (&y)[NB][3]) {
+    if (all) step_entries<GT, NB, NBX, true>(a, b0, e0, e1, lane, y);
+    else step_entries<GT, NB, NBX, false>(a, b0, e0, e1, lane, y);
 }
 
-// Narrow windows (every k+q window <= JMAX bands, this group NBX bands): each lane takes PPL
-// pairs per round (pairs pb + i*32 + lane), issues all their F and Gamma loads (predicated on
-// the pair's band count) before any multiply, so PPL x JMAX loads are in flight per lane.
-template <typename GT, int NB, int NBX, int JMAX, int PPL>
-__device__ __forceinline__ void step_pairs_narrow(const StepArgs<GT> &a, int nsel, int b0, int64_t wb,
-                                                  int64_t we, int64_t off, int lane,
-                                                  typename Acc<GT>::T (&y)[NB][3]) {
+// One block per window k-point; its entries split into eight contiguous warp ranges.  The
+// k-point's bands are taken in groups of NB (the smallest of 1, 2, 4, 8 covering the crystal's
+// bands; wider windows loop over groups).  Lanes reduce by a butterfly in the accumulation
+// type, warps in index order in FP64, so the result does not depend on scheduling.  Entry 0 of
+// an unused column word (col 0, value 0) adds exactly zero.
+template <typename GT, int NB>
+__global__ void __launch_bounds__(kIbThreads, NB <= 4 ? 4 : 2) k_ib_step(StepArgs<GT> a) {
     using AT = typename Acc<GT>::T;
-    unsigned cnext[PPL];
-#pragma unroll
-    for (int i = 0; i < PPL; ++i) {
-        const int64_t p = wb + i * 32 + lane;
-        cnext[i] = p < we ? __ldg(a.code + p) : 0u;
-    }
-    for (int64_t pb = wb; pb < we; pb += 32 * PPL) {
-        unsigned cd[PPL];
-        int64_t base[PPL];
-#pragma unroll
-        for (int i = 0; i < PPL; ++i) {
-            cd[i] = cnext[i];
-            const int64_t p = pb + 32 * PPL + i * 32 + lane;
-            cnext[i] = p < we ? __ldg(a.code + p) : 0u;
-        }
-#pragma unroll
-        for (int i = 0; i < PPL; ++i) {
-            const int size = nsel * (int)(cd[i] & 31u);
-            int incl = size;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int t = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += t;
-            }
-            base[i] = off + (incl - size);
-            off += __shfl_sync(0xffffffffu, incl, 31);
-        }
-        AT f[PPL][JMAX][3], g[PPL][JMAX][NBX];
-#pragma unroll
-        for (int i = 0; i < PPL; ++i) {
-            const int nw = (int)(cd[i] & 31u);
-            const int64_t sb = (int64_t)(cd[i] >> 5);
-#pragma unroll
-            for (int j = 0; j < JMAX; ++j) {
-                f[i][j][0] = f[i][j][1] = f[i][j][2] = 0;
-#pragma unroll
-                for (int n = 0; n < NBX; ++n) g[i][j][n] = 0;
-                if (j < nw) {
-                    load_F(a, sb + j, f[i][j][0], f[i][j][1], f[i][j][2]);
-#pragma unroll
-                    for (int n = 0; n < NBX; ++n) g[i][j][n] = (AT)__ldg(a.gam + base[i] + (int64_t)(b0 + n) * nw + j);
-                }
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < PPL; ++i)
-#pragma unroll
-            for (int j = 0; j < JMAX; ++j)
-#pragma unroll
-                for (int n = 0; n < NBX; ++n) {
-                    y[n][0] = fma(g[i][j][n], f[i][j][0], y[n][0]);
-                    y[n][1] = fma(g[i][j][n], f[i][j][1], y[n][1]);
-                    y[n][2] = fma(g[i][j][n], f[i][j][2], y[n][2]);
-                }
-    }
-}
-
-template <typename GT, int kIbBands>
-__global__ void __launch_bounds__(kIbThreads, kIbBands <= 2 ? 4 : (kIbBands <= 4 ? 3 : 2)) k_ib_step(StepArgs<GT> a) {
-    using AT = typename Acc<GT>::T;
-    __shared__ AT part[kIbWarps][kIbBands][3];
+    __shared__ AT part[kIbWarps][NB][3];
     const int kp = blockIdx.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int ik = a.kpts[kp];
     const int nsel = a.win_n[ik];
     const int64_t s0 = a.kp_state[kp];
-    const int64_t p0 = a.kp_pairs[kp], np = a.kp_pairs[kp + 1] - p0;
-    const int64_t wb = p0 + np * wid / kIbWarps, we = p0 + np * (wid + 1) / kIbWarps;
-    const int64_t off = a.wbase[(int64_t)kp * kIbWarps + wid];
+    const int64_t q0 = a.ent[kp], ne = a.ent[kp + 1] - q0;
+    const int64_t e0 = q0 + ne * wid / kIbWarps, e1 = q0 + ne * (wid + 1) / kIbWarps;
     double dmax = 0, fmax_ = 0;
-    for (int b0 = 0; b0 < nsel; b0 += kIbBands) {
-        const int nb = min(kIbBands, nsel - b0);
-        AT y[kIbBands][3];
+    for (int b0 = 0; b0 < nsel; b0 += NB) {
+        const int nb = min(NB, nsel - b0);
+        AT y[NB][3];
 #pragma unroll
-        for (int n = 0; n < kIbBands; ++n) y[n][0] = y[n][1] = y[n][2] = 0;
+        for (int n = 0; n < NB; ++n) y[n][0] = y[n][1] = y[n][2] = 0;
         // exact band count of this group (uniform over the block)
-        // narrow-window path: FP32 Gamma and 4-band groups (the register budget of the other
-        // instantiations has no room for its staged loads)
-        constexpr bool kNarrow = std::is_same<GT, float>::value && kIbBands == 4;
-        if (kNarrow && a.narrow && nb <= 2) {
-            if constexpr (kNarrow) {
-                if (nb == 1) step_pairs_narrow<GT, kIbBands, 1, 4, kPpl>(a, nsel, b0, wb, we, off, lane, y);
-                else step_pairs_narrow<GT, kIbBands, 2, 4, kPpl>(a, nsel, b0, wb, we, off, lane, y);
-            }
-        } else switch (nb) {
-        case 1: step_pairs<GT, kIbBands, 1>(a, nsel, b0, wb, we, off, lane, y); break;
-        case 2: if constexpr (kIbBands >= 2) step_pairs<GT, kIbBands, 2>(a, nsel, b0, wb, we, off, lane, y); break;
-        case 3: if constexpr (kIbBands >= 3) step_pairs<GT, kIbBands, 3>(a, nsel, b0, wb, we, off, lane, y); break;
-        case 4: if constexpr (kIbBands >= 4) step_pairs<GT, kIbBands, 4>(a, nsel, b0, wb, we, off, lane, y); break;
-        default:
-            if constexpr (kIbBands > 4) step_pairs<GT, kIbBands, kIbBands>(a, nsel, b0, wb, we, off, lane, y);
-            break;
+        const bool all = nsel <= NB;
+        switch (nb) {
+        case 1: step_group<GT, NB, 1>(a, all, b0, e0, e1, lane, y); break;
+        case 2: if constexpr (NB >= 2) step_group<GT, NB, 2>(a, all, b0, e0, e1, lane, y); break;
+        case 3: if constexpr (NB >= 3) step_group<GT, NB, 3>(a, all, b0, e0, e1, lane, y); break;
+        case 4: if constexpr (NB >= 4) step_group<GT, NB, 4>(a, all, b0, e0, e1, lane, y); break;
+        default: if constexpr (NB > 4) step_group<GT, NB, NB>(a, all, b0, e0, e1, lane, y); break;
         }
-        // lanes: butterfly in the accumulation type; warps: FP64 in index order
 #pragma unroll
-        for (int n = 0; n < kIbBands; ++n) {
+        for (int n = 0; n < NB; ++n) {
             if (n >= nb) break;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -300,7 +240,7 @@ __global__ void __launch_bounds__(kIbThreads, kIbBands <= 2 ? 4 : (kIbBands <= 4
         __syncthreads();
     }
     // max is order independent: the bit patterns of non-negative doubles order like the values
-    if (threadIdx.x < 3 * kIbBands && (dmax > 0 || fmax_ > 0)) {
+    if (threadIdx.x < 3 * NB && (dmax > 0 || fmax_ > 0)) {
         atomicMax(&a.red[0], (unsigned long long)__double_as_longlong(dmax));
         atomicMax(&a.red[1], (unsigned long long)__double_as_longlong(fmax_));
     }
@@ -312,9 +252,8 @@ void launch_step(epwi_ctx *c, const double *Fin, double *Fout, const float4 *Fin
     a.kpts = c->kpts.as<int>();
     a.win_n = c->win_n.as<int>();
     a.kp_state = c->kp_state.as<int64_t>();
-    a.kp_pairs = c->kp_pairs.as<int64_t>();
-    a.wbase = c->ib_wbase.as<int64_t>();
-    a.code = c->ib_pairs.as<unsigned>();
+    a.ent = c->ib_ent.as<int64_t>();
+    a.col = c->ib_col.as<unsigned>();
     a.gam = c->ib_gam.as<GT>();
     a.inv_tau = c->inv_tau.as<double>();
     a.F0 = c->ib_F0.as<double>();
@@ -323,7 +262,6 @@ void launch_step(epwi_ctx *c, const double *Fin, double *Fout, const float4 *Fin
     a.Fin32 = Fin32;
     a.Fout32 = Fout32;
     a.pref = 2.0 * epc::kPi / epc::kHbarEVs / (double)c->nk / (sqrt(epc::kPi) * c->eta);
-    a.narrow = c->nw <= 4;
     a.red = c->ib_red.as<unsigned long long>();
     // band group: the smallest of 1, 2, 4, 8 covering the bands (wider windows loop)
     const unsigned grid = (unsigned)c->nkp;
@@ -370,10 +308,10 @@ void ibte_prepare(epwi_ctx *c, WorkSet &ws) {
         sizes.release();
     }
     const size_t eb = fp64 ? sizeof(double) : sizeof(float);
-    c->ib_gam.ensure(eb * (size_t)(nent + 1));
+    const size_t gam_bytes = eb * (size_t)(nent + 1);
+    c->ib_gam.ensure(gam_bytes);
     // the fp32 mode writes only the bands it does not skip (the others are exactly zero)
-    if (c->opt.precision == EPWI_FP32)
-        EPWI_CUDA(cudaMemsetAsync(c->ib_gam.p, 0, eb * (size_t)(nent + 1), c->stream));
+    if (c->opt.precision == EPWI_FP32) EPWI_CUDA(cudaMemsetAsync(c->ib_gam.p, 0, gam_bytes, c->stream));
     c->ib_stats.n_entries = nent;
     c->ib_stats.entry_bytes = (int32_t)eb;
     ws.pairs_dev = c->ib_pairs.as<int>();
@@ -394,24 +332,22 @@ void ibte_iterate(epwi_ctx *c, int max_iter, double tol) {
         c->ib_Fn32.ensure(sizeof(float4) * (ns + 1));
     }
     c->ib_red.ensure(sizeof(unsigned long long) * 2);
-    // the captured pairs' q indices become step codes (the capture is done with them), and the
-    // per-pair offsets become one offset per (k-point, warp range)
+    // the step's index: one column word per Gamma entry and the first entry of every k-point;
+    // the pair list and per-pair offsets are needed only by the capture and are freed here
     EPWI_REQUIRE(ns < (int64_t(1) << 27), EPWI_EUNSUPPORTED, "iterative BTE needs fewer than 2^27 states");
-    c->ib_wbase.ensure(sizeof(int64_t) * (c->nkp * kIbWarps + 1));
-    if (c->nkp > 0) {
-        const int64_t nt = c->nkp * kIbWarps;
-        k_ib_wbase<<<(unsigned)((nt + 255) / 256), 256, 0, c->stream>>>(
-            c->nkp, c->kp_pairs.as<int64_t>(), c->ib_goff.as<int64_t>(), c->ib_wbase.as<int64_t>());
+    const int64_t nkp = c->nkp, nent = c->ib_stats.n_entries;
+    c->ib_ent.ensure(sizeof(int64_t) * (nkp + 1));
+    c->ib_col.ensure(sizeof(unsigned) * (nent + 1));
+    if (nkp > 0) {
+        k_ib_columns<<<(unsigned)nkp, 256, 0, c->stream>>>(
+            make_grid_info(c), nkp, c->kpts.as<int>(), c->win_n.as<int>(), c->ib_kpos.as<int>(),
+            c->kp_state.as<int64_t>(), c->kp_pairs.as<int64_t>(), c->ib_pairs.as<int>(), c->ib_goff.as<int64_t>(),
+            c->ib_col.as<unsigned>(), c->ib_ent.as<int64_t>());
         EPWI_CHECK_LAUNCH();
     }
     EPWI_CUDA(cudaStreamSynchronize(c->stream));
     c->ib_goff.release();
-    if (c->nkp > 0) {
-        k_ib_encode<<<(unsigned)c->nkp, 256, 0, c->stream>>>(
-            make_grid_info(c), c->kpts.as<int>(), c->win_n.as<int>(), c->ib_kpos.as<int>(),
-            c->kp_state.as<int64_t>(), c->kp_pairs.as<int64_t>(), c->ib_pairs.as<unsigned>());
-        EPWI_CHECK_LAUNCH();
-    }
+    c->ib_pairs.release();
     if (ns > 0) {
         k_ib_f0<<<(unsigned)((ns + 255) / 256), 256, 0, c->stream>>>(
             ns, c->nw, c->st_k.as<int>(), c->st_n.as<int>(), c->inv_tau.as<double>(), c->vel.as<double>(),
@@ -463,8 +399,9 @@ void ibte_iterate(epwi_ctx *c, int max_iter, double tol) {
     c->ib_stats.iters = it;
     c->ib_stats.change = change;
     c->ib_stats.ms_step = it > 0 ? ms_steps / it : 0.0;
-    // one step reads the pair codes and Gamma once, F0, 1/tau and F at the states, writes F
-    c->ib_stats.bytes_per_step = 4.0 * (double)c->npairs +
+    // one step reads the column words and Gamma once, F0, 1/tau and F at the states, writes F
+    c->ib_stats.index_bytes = 4 * nent + 8 * (nkp + 1);
+    c->ib_stats.bytes_per_step = (double)c->ib_stats.index_bytes +
                                  (double)c->ib_stats.entry_bytes * (double)c->ib_stats.n_entries +
                                  8.0 * (double)ns * (3 + 1 + 3 + 3);
 }

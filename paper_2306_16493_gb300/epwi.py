@@ -62,7 +62,7 @@ class epwi_ibte_stats(C.Structure):
     _fields_ = [("n_states", C.c_int64), ("n_pairs", C.c_int64), ("n_entries", C.c_int64),
                 ("entry_bytes", C.c_int32), ("iters", C.c_int32), ("change", C.c_double),
                 ("ms_rates", C.c_double), ("ms_iterate", C.c_double), ("ms_step", C.c_double),
-                ("bytes_per_step", C.c_double)]
+                ("bytes_per_step", C.c_double), ("index_bytes", C.c_int64)]
 
 
 class epwi_mlp_train_options(C.Structure):

@@ -97,6 +97,9 @@ def test_al_like_ragged_pairs(precision):
     assert res["st"]["n_pairs"] == O.serta(gr, T, mu, eta, lo, hi)["n_pairs"]
     # one stored value per (pair, n in window(k), m in window(k+q)): at least the nonzeros
     assert res["st"]["n_entries"] >= ref["A"].nnz
+    # the step's index: a column word per entry and an offset per k-point
+    nkp = len(np.unique(res["k"]))
+    assert res["st"]["index_bytes"] == 4 * res["st"]["n_entries"] + 8 * (nkp + 1)
 
 
 @pytest.mark.parametrize("precision", SPLIT + ("fp32",))
@@ -153,3 +156,26 @@ def test_fp64_time_reversal_symmetric_metal_converges_to_the_oracle():
     e = gr.eps[ref["ik"], ref["n"]]
     sig = O.transport_from_F(s.volume, gr.nk, v, ref["F"], e, mu, T)[0]
     assert np.abs(res["tr"][0] - sig).max() <= 1e-9 * np.abs(sig).max()
+
+
+def test_fp32_long_warp_ranges_match_fp64():
+    """Al-like 40^3 with a +-0.5 eV window: each warp's Gamma range is longer than the staged
+    step's shared ring (2048 entries), so the ring wraps within a warp's range.  Eight fixed
+    steps of the fp32 mode against the FP64 path (itself pinned to the oracle on smaller
+    grids)."""
+    s = synth.al_like_system()
+    grid = (40, 40, 40)
+    ctx = epwi.Context(precision="fp64", device=0)
+    ctx.setup(s)
+    ctx.eigs(grid)
+    lo, hi = ctx.band_range()
+    ctx.close()
+    mu, eta = 0.5 * (lo + hi), 0.02
+    ref = _run(s, grid, mu, mu - 0.5, mu + 0.5, eta, 8, 0.0, precision="fp64")
+    res = _run(s, grid, mu, mu - 0.5, mu + 0.5, eta, 8, 0.0, precision="fp32")
+    assert np.array_equal(res["k"], ref["k"]) and np.array_equal(res["b"], ref["b"])
+    assert res["st"]["n_pairs"] == ref["st"]["n_pairs"]
+    nkp = len(np.unique(res["k"]))
+    assert res["st"]["n_entries"] / (8 * nkp) > 2048
+    assert np.abs(res["r"] - ref["r"]).max() <= 1e-4 * ref["r"].max()
+    assert np.abs(res["F"] - ref["F"]).max() <= 1e-4 * np.abs(ref["F"]).max()
