@@ -210,9 +210,10 @@ __global__ void k_seg_ranges(int N1, int64_t nplane, int W, int nseg, const floa
 // Every outcome therefore equals the FP64 evaluation of pair_valid.  The first two cases cover
 // nearly every candidate when the phonon energies lie below c eta (the Gaussian's support is
 // wider than the phonon band); the third runs inline for the few others.  The lanes of a warp
-// take 32 consecutive (q2, q3) combinations of a plane block and 2-4 consecutive q1 per step;
-// their ballots are the plane block's mask words, kept in shared memory and written out in
-// k_sieve_count's layout.  Indices are 32-bit (N_k < 2^31, checked).
+// take 32 consecutive (q2, q3) combinations of a plane block and 2-4 consecutive q1 per step,
+// with the window's band count a compile-time constant (1-4, else a runtime loop); their
+// ballots are the plane block's mask words, kept in shared memory ([warp][q1]) and written out
+// in k_sieve_count's layout.  Indices are 32-bit (N_k < 2^31, checked).
 //
 // With FILL the same kernel writes the pair lists of k-points kp0 + blockIdx.x instead (used
 // when the whole decision mask would not fit in memory): after each plane block the CTA scans
@@ -224,28 +225,17 @@ __global__ void k_seg_ranges(int N1, int64_t nplane, int W, int nseg, const floa
 // when no band's energy range over the segment comes within seglim (>= hwmax(q) + c eta +
 // delta for every q, with a margin over FP32 rounding) of the window energies.  A warp whose
 // lanes all reject a segment skips its iterations.
-template <int WT, int NMT, bool FILL>
-__global__ void __launch_bounds__(256, 4) k_sieve_count_fast(SieveArgs a, const int *__restrict__ kpts,
-                                                          const int *__restrict__ lo,
-                                                          const int *__restrict__ cnt,
-                                                          int64_t *__restrict__ counts,
-                                                          uint32_t *__restrict__ mask,
-                                                          int64_t words_per_kp, int64_t kp0,
-                                                          const int64_t *__restrict__ kp_pairs,
-                                                          int *__restrict__ pairs) {
-    __shared__ double en[epc::kMaxW];
-    __shared__ float en32[epc::kMaxW];
-    __shared__ int64_t sm[33];
-    extern __shared__ uint32_t words[];          // [N1][8]: decisions of the current plane block
+template <int WT, int NMT, bool FILL, int NS>
+__device__ __forceinline__ int64_t sieve_fast_kp(const SieveArgs &a, int nsel, const double *en, const float *en32,
+                                                 int ka1, int ka2, int ka3, uint32_t *words, int64_t *sm,
+                                                 uint32_t *mrow, int64_t obase, int *pairs) {
     constexpr int kUnr = WT >= 8 ? 2 : 4;        // candidates per step (registers for their energies)
-    const int64_t kp = FILL ? kp0 + blockIdx.x : blockIdx.x;
-    const int ik = kpts[kp];
-    const int nsel = cnt[ik];
-    load_window(a, ik, lo[ik], nsel, en, en32);
-    // window energies in registers; absent bands sit far away and never give the minimum
-    float e[WT];
+    constexpr int NSX = NS > 0 ? NS : WT;        // window bands held in registers
+    constexpr int V4 = WT / 4;                   // 16-byte loads per k+q point
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float e[NSX];
 #pragma unroll
-    for (int n = 0; n < WT; ++n) e[n] = n < nsel ? en32[n] : 3.0e38f;
+    for (int n = 0; n < NSX; ++n) e[n] = n < nsel ? en32[n] : 3.0e38f;
     float elo = en32[0], ehi = en32[0];
     for (int n = 1; n < nsel; ++n) {
         elo = fminf(elo, en32[n]);
@@ -253,20 +243,20 @@ __global__ void __launch_bounds__(256, 4) k_sieve_count_fast(SieveArgs a, const 
     }
     const float rej = a.ceta32 + a.delta32, acc = a.ceta32 - a.delta32;
     const float hm_fast = a.ceta32 - 2.f * a.delta32;
-    int ka1, ka2, ka3;
-    grid_coords(a.g, ik, ka1, ka2, ka3);
     const int N1 = a.g.n1, nplane = a.g.n2 * a.g.n3;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    uint32_t *mrow = (mask && !FILL) ? mask + (int64_t)blockIdx.x * words_per_kp + wid : nullptr;
-    int64_t obase = FILL ? kp_pairs[kp] - kp_pairs[kp0] : 0;   // next output position (FILL)
-    int c = 0;
+    const int rowv = nplane * V4;                // float4 per axis-1 row of the energy table
+    const float4 *eps4 = reinterpret_cast<const float4 *>(a.eps32);
+    uint32_t *mw = words + wid * N1;             // this warp's words of the plane block, by q1
+    int64_t c = 0;
     for (int pb = 0, pbi = 0; pb < nplane; pb += blockDim.x, ++pbi) {
         const int p = pb + threadIdx.x;
         const bool inb = p < nplane;
         const int kqp = inb ? (int)plane_kq(a.g, ka2, ka3, p) : 0;
-        for (int i1 = lane; i1 < N1; i1 += 32) words[i1 * 8 + wid] = 0u;
+        const float *hq = a.hwmax32 + p;         // hwmax of q = (q1, p) at hq[q1 * nplane]
+        const float4 *eq = eps4 + (size_t)kqp * V4;   // energies of (b1, kqp) at eq[b1 * rowv]
+        for (int i1 = lane; i1 < N1; i1 += 32) mw[i1] = 0u;
         __syncwarp();
-        int b1 = ka1, iq = p;
+        int b1 = ka1;
         for (int i1 = 0; i1 < N1;) {
             // the segment of b1: iterations up to its end (or the wrap of b1 at N1); without the
             // table (nseg = 0) one segment covers the whole column
@@ -283,22 +273,23 @@ __global__ void __launch_bounds__(256, 4) k_sieve_count_fast(SieveArgs a, const 
             }
             if (!__any_sync(0xffffffffu, segok)) {
                 i1 += len;
-                iq += len * nplane;
                 b1 += len;
                 if (b1 >= N1) b1 -= N1;
                 continue;
             }
             for (int u = 0; u < len; u += kUnr) {
                 // kUnr candidates (q1 = i1 .. i1 + kUnr - 1 of this segment): loads first
-                float hm[kUnr], em[kUnr][WT];
+                float hm[kUnr];
+                float4 em4[kUnr][V4];
 #pragma unroll
                 for (int j = 0; j < kUnr; ++j) {
+                    int bj = b1 + j;
+                    if (bj >= N1) bj -= N1;
                     hm[j] = -1.f;
                     if (segok && u + j < len) {
-                        int bj = b1 + j;
-                        if (bj >= N1) bj -= N1;
-                        hm[j] = a.hwmax32[iq + j * nplane];
-                        load_kq_energies<WT>(a, (int64_t)bj * nplane + kqp, em[j]);
+                        hm[j] = hq[(i1 + j) * nplane];
+#pragma unroll
+                        for (int v = 0; v < V4; ++v) em4[j][v] = eq[bj * rowv + v];
                     }
                 }
                 unsigned vbits = 0, amb = 0;
@@ -307,39 +298,44 @@ __global__ void __launch_bounds__(256, 4) k_sieve_count_fast(SieveArgs a, const 
                     if (hm[j] >= 0.f) {
                         float d = 3.0e38f;
 #pragma unroll
-                        for (int n = 0; n < WT; ++n) {
-                            if (n < nsel) {
+                        for (int n = 0; n < NSX; ++n) {
+                            if (NS == 0 && n >= nsel) break;
 #pragma unroll
-                                for (int m = 0; m < WT; ++m) d = fminf(d, fabsf(e[n] - em[j][m]));
+                            for (int v = 0; v < V4; ++v) {
+                                d = fminf(d, fabsf(e[n] - em4[j][v].x));
+                                d = fminf(d, fabsf(e[n] - em4[j][v].y));
+                                d = fminf(d, fabsf(e[n] - em4[j][v].z));
+                                d = fminf(d, fabsf(e[n] - em4[j][v].w));
                             }
                         }
-                        if (d <= hm[j] + rej) {
-                            if (hm[j] <= hm_fast && d <= hm[j] + acc) vbits |= 1u << j;
-                            else amb |= 1u << j;
-                        }
+                        const bool near = d <= hm[j] + rej;
+                        const bool sure = (hm[j] <= hm_fast) & (d <= hm[j] + acc);
+                        vbits |= (near & sure ? 1u : 0u) << j;
+                        amb |= (near & !sure ? 1u : 0u) << j;
                     }
                 }
-                // the rest: exact per-mode test
-#pragma unroll 1
-                for (int j = 0; j < kUnr; ++j) {
-                    if (!((amb >> j) & 1u)) continue;
+                // the rest: exact per-mode test (loads repeated: rare)
+                while (amb) {
+                    const int j = __ffs(amb) - 1;
+                    amb &= amb - 1;
                     int bj = b1 + j;
                     if (bj >= N1) bj -= N1;
                     const int64_t ikq = (int64_t)bj * nplane + kqp;
+                    const int64_t iqj = (int64_t)(i1 + j) * nplane + p;
                     float emj[WT];
                     load_kq_energies<WT>(a, ikq, emj);
-                    const int64_t iqj = iq + j * nplane;
-                    if (pair_valid_tail<WT, NMT>(a, nsel, en, en32, iqj, ikq, a.hwmax32[iqj], emj))
-                        vbits |= 1u << j;
+                    if (pair_valid_tail<WT, NMT>(a, nsel, en, en32, iqj, ikq, a.hwmax32[iqj], emj)) vbits |= 1u << j;
                 }
+                // ballot j is word i1 + j: lane j keeps it and stores it
+                uint32_t mine = 0u;
 #pragma unroll
                 for (int j = 0; j < kUnr; ++j) {
-                    const unsigned bits = __ballot_sync(0xffffffffu, (vbits >> j) & 1u);
-                    if (lane == 0 && u + j < len) words[(i1 + j) * 8 + wid] = bits;
+                    const uint32_t bits = __ballot_sync(0xffffffffu, (vbits >> j) & 1u);
+                    if (lane == j) mine = bits;
                 }
+                if (lane < kUnr && u + lane < len) mw[i1 + lane] = mine;
                 const int step = min(kUnr, len - u);
                 i1 += step;
-                iq += step * nplane;
                 b1 += step;
                 if (b1 >= N1) b1 -= N1;
             }
@@ -350,11 +346,11 @@ __global__ void __launch_bounds__(256, 4) k_sieve_count_fast(SieveArgs a, const 
             const int nw = N1 * 8, per = (nw + blockDim.x - 1) / blockDim.x;
             const int w0 = threadIdx.x * per, w1 = min(nw, w0 + per);
             int pop = 0;
-            for (int w = w0; w < w1; ++w) pop += __popc(words[w]);
+            for (int w = w0; w < w1; ++w) pop += __popc(words[(w & 7) * N1 + (w >> 3)]);
             int64_t tot;
             int64_t o = obase + block_excl_scan((int64_t)pop, sm, tot);
             for (int w = w0; w < w1; ++w) {
-                uint32_t b = words[w];
+                uint32_t b = words[(w & 7) * N1 + (w >> 3)];
                 const int q0 = (w >> 3) * nplane + pb + (w & 7) * 32;   // (i1, warp) of the word
                 while (b) {
                     const int bit = __ffs(b) - 1;
@@ -366,16 +362,46 @@ __global__ void __launch_bounds__(256, 4) k_sieve_count_fast(SieveArgs a, const 
             __syncthreads();                     // the words are cleared next
         } else {
             for (int i1 = lane; i1 < N1; i1 += 32) {
-                const uint32_t w = words[i1 * 8 + wid];
+                const uint32_t w = mw[i1];
                 c += __popc(w);
                 if (mrow) mrow[((int64_t)pbi * N1 + i1) * 8] = w;
             }
             __syncwarp();
         }
     }
+    return c;
+}
+
+template <int WT, int NMT, bool FILL>
+__global__ void __launch_bounds__(256, 3) k_sieve_count_fast(SieveArgs a, const int *__restrict__ kpts,
+                                                          const int *__restrict__ lo,
+                                                          const int *__restrict__ cnt,
+                                                          int64_t *__restrict__ counts,
+                                                          uint32_t *__restrict__ mask,
+                                                          int64_t words_per_kp, int64_t kp0,
+                                                          const int64_t *__restrict__ kp_pairs,
+                                                          int *__restrict__ pairs) {
+    __shared__ double en[epc::kMaxW];
+    __shared__ float en32[epc::kMaxW];
+    __shared__ int64_t sm[33];
+    extern __shared__ uint32_t words[];          // [8][N1]: decisions of the current plane block
+    const int64_t kp = FILL ? kp0 + blockIdx.x : blockIdx.x;
+    const int ik = kpts[kp];
+    const int nsel = cnt[ik];
+    load_window(a, ik, lo[ik], nsel, en, en32);
+    int ka1, ka2, ka3;
+    grid_coords(a.g, ik, ka1, ka2, ka3);
+    uint32_t *mrow = (mask && !FILL) ? mask + (int64_t)blockIdx.x * words_per_kp + (threadIdx.x >> 5) : nullptr;
+    const int64_t obase = FILL ? kp_pairs[kp] - kp_pairs[kp0] : 0;   // first output position (FILL)
+    int64_t c;
+    switch (nsel) {                              // the window's band count (uniform over the block)
+    case 1: c = sieve_fast_kp<WT, NMT, FILL, 1>(a, nsel, en, en32, ka1, ka2, ka3, words, sm, mrow, obase, pairs); break;
+    case 2: c = sieve_fast_kp<WT, NMT, FILL, 2>(a, nsel, en, en32, ka1, ka2, ka3, words, sm, mrow, obase, pairs); break;
+    default: c = sieve_fast_kp<WT, NMT, FILL, 0>(a, nsel, en, en32, ka1, ka2, ka3, words, sm, mrow, obase, pairs); break;
+    }
     if constexpr (FILL) return;
     int64_t tot;
-    block_excl_scan((int64_t)c, sm, tot);
+    block_excl_scan(c, sm, tot);
     if (threadIdx.x == 0) counts[blockIdx.x] = tot;
 }
 
