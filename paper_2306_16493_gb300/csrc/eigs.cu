@@ -6,6 +6,8 @@
 // scattering loops gather V(k+q), u(q) from these tables instead of re-diagonalising per
 // pair.
 #include <algorithm>
+#include <utility>
+#include <vector>
 
 #include "epwi_internal.cuh"
 #include "jacobi.cuh"
@@ -280,11 +282,13 @@ size_t warp_scratch_bytes(int n) {
     return kWarpsPerBlock * ((per + 15) & ~size_t(15));
 }
 
+// FAC: H(k) and dH/dk from the factorised stages (as in k_eig_el), each lane building its row.
+template <bool FAC>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_eig_el_warp(
     GridInfo g, int64_t nk, int W, int nR, const int *__restrict__ R, const double *__restrict__ Rcart,
     const double2 *__restrict__ Hw, const double2 *__restrict__ ph, double *__restrict__ eps,
     float *__restrict__ eps32, double2 *__restrict__ Vout, float2 *__restrict__ V32,
-    double *__restrict__ vel, int *__restrict__ flag) {
+    double *__restrict__ vel, int *__restrict__ flag, FacDesc fac, Lattice lat) {
     extern __shared__ __align__(16) uint8_t wsm[];
     const int lane = threadIdx.x & 31;
     const int64_t ik = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
@@ -295,12 +299,22 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_eig_el_warp(
     grid_coords(g, ik, i1, i2, i3);
     const int a1 = (int)((int64_t)i1 * g.s1 % g.L), a2 = (int)((int64_t)i2 * g.s2 % g.L),
               a3 = (int)((int64_t)i3 * g.s3 % g.L);
+    const int64_t WW = (int64_t)W * W;
+    const int64_t pp = (int64_t)i2 * g.n3 + i3;   // (k2, k3) of this point (factorised build)
     if (lane < W) {
         for (int j = 0; j < W; ++j) S.A[lane * ld + j] = make_double2(0, 0);
-        for (int r = 0; r < nR; ++r) {
-            const double2 p = ph[phase_index(a1, a2, a3, R[3 * r], R[3 * r + 1], R[3 * r + 2], g.L)];
-            const double2 *h = Hw + (size_t)r * W * W + lane * W;
-            for (int j = 0; j < W; ++j) S.A[lane * ld + j] = cfma(p, h[j], S.A[lane * ld + j]);
+        if constexpr (FAC) {
+            for (int j1 = 0; j1 < fac.D; ++j1) {
+                const double2 p = axis_ph(ph, j1 - fac.rc, a1, g.L);
+                const double2 *u = fac.U + ((int64_t)j1 * fac.plane + pp) * WW + lane * W;
+                for (int j = 0; j < W; ++j) S.A[lane * ld + j] = cfma(p, u[j], S.A[lane * ld + j]);
+            }
+        } else {
+            for (int r = 0; r < nR; ++r) {
+                const double2 p = ph[phase_index(a1, a2, a3, R[3 * r], R[3 * r + 1], R[3 * r + 2], g.L)];
+                const double2 *h = Hw + (size_t)r * W * W + lane * W;
+                for (int j = 0; j < W; ++j) S.A[lane * ld + j] = cfma(p, h[j], S.A[lane * ld + j]);
+            }
         }
     }
     __syncwarp();
@@ -321,12 +335,29 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_eig_el_warp(
         __syncwarp();
         if (lane < W) {
             for (int j = 0; j < W; ++j) S.A[lane * ld + j] = make_double2(0, 0);
-            for (int r = 0; r < nR; ++r) {
-                const double2 p = ph[phase_index(a1, a2, a3, R[3 * r], R[3 * r + 1], R[3 * r + 2], g.L)];
-                const double ra = Rcart[3 * r + ax];
-                const double2 ip = make_double2(-ra * p.y, ra * p.x);
-                const double2 *h = Hw + (size_t)r * W * W + lane * W;
-                for (int j = 0; j < W; ++j) S.A[lane * ld + j] = cfma(ip, h[j], S.A[lane * ld + j]);
+            if constexpr (FAC) {
+                // i R_a = i (n1 A_1a + n2 A_2a + n3 A_3a): U_0 weighted by n1, U_1 (n2 sums), U_2 (n3 sums)
+                const int64_t src = (int64_t)fac.D * fac.plane * WW;
+                for (int j1 = 0; j1 < fac.D; ++j1) {
+                    const int n1 = j1 - fac.rc;
+                    const double2 p = axis_ph(ph, n1, a1, g.L);
+                    const double2 ip = make_double2(-p.y, p.x);   // i e1
+                    const double c0 = n1 * lat.a[0][ax], c1 = lat.a[1][ax], c2 = lat.a[2][ax];
+                    const double2 *u = fac.U + ((int64_t)j1 * fac.plane + pp) * WW + lane * W;
+                    for (int j = 0; j < W; ++j) {
+                        const double2 sr = make_double2(c0 * u[j].x + c1 * u[src + j].x + c2 * u[2 * src + j].x,
+                                                        c0 * u[j].y + c1 * u[src + j].y + c2 * u[2 * src + j].y);
+                        S.A[lane * ld + j] = cfma(ip, sr, S.A[lane * ld + j]);
+                    }
+                }
+            } else {
+                for (int r = 0; r < nR; ++r) {
+                    const double2 p = ph[phase_index(a1, a2, a3, R[3 * r], R[3 * r + 1], R[3 * r + 2], g.L)];
+                    const double ra = Rcart[3 * r + ax];
+                    const double2 ip = make_double2(-ra * p.y, ra * p.x);
+                    const double2 *h = Hw + (size_t)r * W * W + lane * W;
+                    for (int j = 0; j < W; ++j) S.A[lane * ld + j] = cfma(ip, h[j], S.A[lane * ld + j]);
+                }
             }
         }
         __syncwarp();
@@ -343,11 +374,12 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_eig_el_warp(
     }
 }
 
+template <bool FAC>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_eig_ph_warp(
     GridInfo g, int64_t nq, int Nm, int nR, const int *__restrict__ R, const double *__restrict__ Phiw,
     const double *__restrict__ mode_mass, const double2 *__restrict__ ph, double omega_min,
     double *__restrict__ hw, float *__restrict__ hwmax32, float *__restrict__ hw32,
-    double2 *__restrict__ uout, float2 *__restrict__ u32, int *__restrict__ flag) {
+    double2 *__restrict__ uout, float2 *__restrict__ u32, int *__restrict__ flag, FacDesc fac) {
     extern __shared__ __align__(16) uint8_t wsm[];
     const int lane = threadIdx.x & 31;
     const int64_t iq = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
@@ -360,12 +392,21 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_eig_ph_warp(
               a3 = (int)((int64_t)i3 * g.s3 % g.L);
     if (lane < Nm) {
         for (int j = 0; j < Nm; ++j) S.A[lane * ld + j] = make_double2(0, 0);
-        for (int r = 0; r < nR; ++r) {
-            const double2 p = ph[phase_index(a1, a2, a3, R[3 * r], R[3 * r + 1], R[3 * r + 2], g.L)];
-            const double *f = Phiw + (size_t)r * Nm * Nm + lane * Nm;
-            for (int j = 0; j < Nm; ++j) {
-                S.A[lane * ld + j].x = fma(p.x, f[j], S.A[lane * ld + j].x);
-                S.A[lane * ld + j].y = fma(p.y, f[j], S.A[lane * ld + j].y);
+        if constexpr (FAC) {
+            const int64_t pp = (int64_t)i2 * g.n3 + i3;
+            for (int j1 = 0; j1 < fac.D; ++j1) {
+                const double2 p = axis_ph(ph, j1 - fac.rc, a1, g.L);
+                const double2 *u = fac.U + ((int64_t)j1 * fac.plane + pp) * Nm * Nm + lane * Nm;
+                for (int j = 0; j < Nm; ++j) S.A[lane * ld + j] = cfma(p, u[j], S.A[lane * ld + j]);
+            }
+        } else {
+            for (int r = 0; r < nR; ++r) {
+                const double2 p = ph[phase_index(a1, a2, a3, R[3 * r], R[3 * r + 1], R[3 * r + 2], g.L)];
+                const double *f = Phiw + (size_t)r * Nm * Nm + lane * Nm;
+                for (int j = 0; j < Nm; ++j) {
+                    S.A[lane * ld + j].x = fma(p.x, f[j], S.A[lane * ld + j].x);
+                    S.A[lane * ld + j].y = fma(p.y, f[j], S.A[lane * ld + j].y);
+                }
             }
         }
     }
@@ -417,13 +458,22 @@ void launch_phase_tables(epwi_ctx *c) {
 }
 
 // Raises a kernel's dynamic shared-memory limit the first time a larger size is needed
-// (the first launch of each size happens outside any stream capture).
+// (the first launch of each size happens outside any stream capture).  The limit set so far is
+// kept per kernel: kernels of one signature share the template instance.
 template <class K>
 void set_smem_once(K kern, size_t bytes) {
-    static size_t set = 48 * 1024;
-    if (bytes > set) {
+    static std::vector<std::pair<const void *, size_t>> set;
+    const void *key = reinterpret_cast<const void *>(kern);
+    size_t *have = nullptr;
+    for (auto &e : set)
+        if (e.first == key) have = &e.second;
+    if (!have) {
+        set.emplace_back(key, size_t(48 * 1024));
+        have = &set.back().second;
+    }
+    if (bytes > *have) {
         EPWI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-        set = bytes;
+        *have = bytes;
     }
 }
 
@@ -479,7 +529,7 @@ void launch_eigs(epwi_ctx *c) {
     };
     Lattice lat;
     for (int i = 0; i < 9; ++i) lat.a[i / 3][i % 3] = c->lattice[i];
-    const bool fac_el = W <= 8 && c->fac_re_r >= 0, fac_ph = Nm <= 6 && c->fac_rp_r >= 0;
+    const bool fac_el = c->fac_re_r >= 0, fac_ph = c->fac_rp_r >= 0;
     {
         // both builds share the stage buffers: size them once, before any launch
         int64_t nT = 1, nU = 1, t, u;
@@ -516,8 +566,13 @@ void launch_eigs(epwi_ctx *c) {
         else k_eig_el<8, false><<<nb, bs, 0, c->stream>>>(EL_ARGS, fe, lat);
     } else {
         const size_t sm = warp_scratch_bytes(W);
-        set_smem_once(k_eig_el_warp, sm);
-        k_eig_el_warp<<<nbw, 32 * kWarpsPerBlock, sm, c->stream>>>(EL_ARGS);
+        if (fac_el) {
+            set_smem_once(k_eig_el_warp<true>, sm);
+            k_eig_el_warp<true><<<nbw, 32 * kWarpsPerBlock, sm, c->stream>>>(EL_ARGS, fe, lat);
+        } else {
+            set_smem_once(k_eig_el_warp<false>, sm);
+            k_eig_el_warp<false><<<nbw, 32 * kWarpsPerBlock, sm, c->stream>>>(EL_ARGS, fe, lat);
+        }
     }
 #undef EL_ARGS
     EPWI_CHECK_LAUNCH();
@@ -536,8 +591,13 @@ void launch_eigs(epwi_ctx *c) {
         else k_eig_ph<6, false><<<nb, bs, 0, c->stream>>>(PH_ARGS, fp);
     } else {
         const size_t sm = warp_scratch_bytes(Nm);
-        set_smem_once(k_eig_ph_warp, sm);
-        k_eig_ph_warp<<<nbw, 32 * kWarpsPerBlock, sm, c->stream>>>(PH_ARGS);
+        if (fac_ph) {
+            set_smem_once(k_eig_ph_warp<true>, sm);
+            k_eig_ph_warp<true><<<nbw, 32 * kWarpsPerBlock, sm, c->stream>>>(PH_ARGS, fp);
+        } else {
+            set_smem_once(k_eig_ph_warp<false>, sm);
+            k_eig_ph_warp<false><<<nbw, 32 * kWarpsPerBlock, sm, c->stream>>>(PH_ARGS, fp);
+        }
     }
 #undef PH_ARGS
     EPWI_CHECK_LAUNCH();
