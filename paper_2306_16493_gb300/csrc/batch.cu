@@ -8,7 +8,10 @@
 //   2. ONE persistent kernel.  Its CTAs take queue items through an atomic counter and do,
 //      per item, the Rp->q product, the rotations by V(k+q) and u(q), and the Gaussian
 //      delta sum of the SERTA rate (Eq. 16, Eq. 10) in FP32.  Each item's sum is written in
-//      FP64 to its own slot;
+//      FP64 to its own slot.  When R_p is a cube the product is factorised along axis 1: an
+//      item's pairs come in runs of equal q1 (the sieve order), and per run
+//      Z = sum_n1 e^{i q1 n1} ghat[n1][n2 n3] is built once, after which each pair sums only
+//      the D^2 terms e^{i(q2 n2 + q3 n3)} Z[n2 n3] (D^3 -> D^2 terms per pair);
 //   3. fixed-order FP64 reductions of the slots into 1/tau, then sigma per system (Eq. 12).
 // The queue is ordered by per-item cost, largest first.  Results do not depend on which CTA
 // takes which item: every item has its own output slot and the sums run in item order.
@@ -40,6 +43,7 @@ constexpr size_t kSmemCap = 100 * 1024;   // two CTAs per SM (228 KB per SM)
 struct BSys {
     GridInfo g;
     int W, Nm, nRp, NW;           // NW = Nm * W columns of the Rp->q product
+    int rc;                       // R_p is the cube [-rc, rc]^3 in n3-fastest order (else -1)
     int CW, RG;                   // columns per thread group (<= 256), row groups = 256 / CW
     int Mt, KC;                   // tile shape: pairs per item, K chunk
     const int *Rp;
@@ -166,6 +170,9 @@ __global__ void __launch_bounds__(kBT, 2) k_batch_scatter(const BSys *__restrict
     __shared__ int s_item;
     __shared__ int sq[kMaxMt];
     __shared__ int sa[3][kMaxMt];
+    __shared__ int srun[kMaxMt + 1];             // starts of the runs of equal q1 (factorised path)
+    __shared__ int s_nrun;
+    __shared__ float2 se1[13];                   // axis-1 phases of the current run (rc <= 6)
     __shared__ double sred[kBT / 32];
     const int t = threadIdx.x;
     for (;;) {
@@ -205,65 +212,163 @@ __global__ void __launch_bounds__(kBT, 2) k_batch_scatter(const BSys *__restrict
 #pragma unroll
         for (int a = 0; a < kAcc; ++a) acc[a] = make_float2(0.f, 0.f);
         __syncthreads();
-        // ---- Rp -> q: C[p][mu, i] = sum_Rp e^{i q_p . Rp} ghat[Rp][mu][i]; the K chunks of
-        // ghat are copied to shared memory with cp.async, one chunk ahead of the compute
-        const int nch = (S.nRp + KC - 1) / KC;
-        auto issue = [&](int ch) {
-            if (ch < nch) {
-                const int r0 = ch * KC, kc = min(KC, S.nRp - r0);
-                const float2 *src = gh + (int64_t)r0 * NW;
-                float2 *dst = Gs + (size_t)(ch & 1) * KC * NW;
-                if ((NW & 1) == 0) {
-                    for (int e = t; e < kc * NW / 2; e += kBT) cp_async_16(dst + 2 * e, src + 2 * e);
-                } else {
-                    for (int e = t; e < kc * NW; e += kBT) cp_async_8(dst + e, src + e);
+        // runs of equal q1 (the sieve lists a k-point's pairs by plane block, then q1, so the
+        // pairs of one q1 are contiguous): the factorised path needs at least 4 pairs per run
+        const bool fac = S.rc >= 0 && S.rc <= 6 &&
+                         4 * __syncthreads_count(t < cnt && (t == 0 || sa[0][t] != sa[0][t - 1]) ||
+                                                 (t + kBT < cnt && sa[0][t + kBT] != sa[0][t + kBT - 1]))
+                             <= cnt;
+        if (fac && t < 32) {
+            // ordered run starts, by warp 0
+            int nr = 0;
+            for (int p0 = 0; p0 < cnt; p0 += 32) {
+                const int p = p0 + t;
+                unsigned bits = __ballot_sync(0xffffffffu, p < cnt && (p == 0 || sa[0][p] != sa[0][p - 1]));
+                while (bits) {
+                    const int b = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    if (t == 0) srun[nr] = p0 + b;
+                    ++nr;
                 }
             }
-            cp_async_commit_group();
-        };
-        issue(0);
-        for (int ch = 0; ch < nch; ++ch) {
-            issue(ch + 1);
-            const int r0 = ch * KC, kc = min(KC, S.nRp - r0);
-            for (int e = t; e < cnt * KC; e += kBT) {
-                const int p = e / KC, kk = e - p * KC;
-                float2 v = make_float2(0.f, 0.f);
-                if (kk < kc) {
-                    const int *R = S.Rp + 3 * (r0 + kk);
-                    v = S.ph32[phase_index(sa[0][p], sa[1][p], sa[2][p], R[0], R[1], R[2], S.g.L)];
-                }
-                P[p * KP + kk] = v;
+            if (t == 0) {
+                srun[nr] = cnt;
+                s_nrun = nr;
             }
-            cp_async_wait_group<1>();
-            __syncthreads();
-            if (tact) {
-                const float2 *G = Gs + (size_t)(ch & 1) * KC * NW;
-                const int nv = min(npt, (cnt - rg + S.RG - 1) / S.RG);   // valid pairs
-                if (ncol == 1) {
-                    for (int kk = 0; kk < kc; ++kk) {
-                        const float2 g0 = G[kk * NW + cg];
-                        const float2 *pk = P + rg * KP + kk;
+        }
+        __syncthreads();
+        if (fac) {
+            // ---- Rp -> q factorised along axis 1: per K chunk of the (n2, n3) plane,
+            // C[p] += sum_(n2,n3) e^{i(q2 n2 + q3 n3)} Z_q1[n2 n3], Z_q1 = sum_n1 e^{i q1 n1} ghat[n1][n2 n3],
+            // Z built once per run of equal q1 and chunk (the CTA reads ghat from L2)
+            const int rc = S.rc, D = 2 * rc + 1, DD = D * D, L = S.g.L;
+            float2 *Z = Gs;                                   // [KC][NW]
+            const int nchf = (DD + KC - 1) / KC;
+            for (int j = 0; j < s_nrun; ++j) {
+                const int lo = srun[j], hi = srun[j + 1];
+                if (t < D) {
+                    int x = (sa[0][lo] * (t - rc)) % L;
+                    if (x < 0) x += L;
+                    se1[t] = S.ph32[x];                       // e^{i q1 n1}, n1 = t - rc
+                }
+                // this thread's pairs p = rg + i RG inside [lo, hi)
+                unsigned in = 0u;
 #pragma unroll
-                        for (int i = 0; i < kAcc; ++i)
-                            if (i < nv) acc[i] = cfmaf(pk[i * S.RG * KP], g0, acc[i]);
+                for (int i = 0; i < kAcc; ++i) {
+                    const int pi = rg + i * S.RG;
+                    if (i < npt && pi >= lo && pi < hi) in |= 1u << i;
+                }
+                __syncthreads();
+                for (int ch = 0; ch < nchf; ++ch) {
+                    const int r0 = ch * KC, kc = min(KC, DD - r0);
+                    for (int e = t; e < (hi - lo) * KC; e += kBT) {
+                        const int p = lo + e / KC, kk = e % KC;
+                        float2 v = make_float2(0.f, 0.f);
+                        if (kk < kc) {
+                            const int n2 = (r0 + kk) / D - rc, n3 = (r0 + kk) % D - rc;
+                            int x = (sa[1][p] * n2 + sa[2][p] * n3) % L;
+                            if (x < 0) x += L;
+                            v = S.ph32[x];
+                        }
+                        P[p * KP + kk] = v;
                     }
-                } else {
-                    const bool c1 = cg + S.CW < NW;
-                    for (int kk = 0; kk < kc; ++kk) {
-                        const float2 g0 = G[kk * NW + cg];
-                        const float2 g1 = c1 ? G[kk * NW + cg + S.CW] : make_float2(0.f, 0.f);
-                        const float2 *pk = P + rg * KP + kk;
+                    for (int e = t; e < kc * NW; e += kBT) {
+                        const int kk = e / NW, col = e - kk * NW;
+                        const float2 *src = gh + (int64_t)(r0 + kk) * NW + col;
+                        float2 z = make_float2(0.f, 0.f);
+                        for (int j1 = 0; j1 < D; ++j1) z = cfmaf(se1[j1], src[(int64_t)j1 * DD * NW], z);
+                        Z[kk * NW + col] = z;
+                    }
+                    __syncthreads();
+                    if (tact) {
+                        if (ncol == 1) {
+                            for (int kk = 0; kk < kc; ++kk) {
+                                const float2 g0 = Z[kk * NW + cg];
+                                const float2 *pk = P + rg * KP + kk;
 #pragma unroll
-                        for (int i = 0; i < kAcc / 2; ++i)
-                            if (i < nv) {
-                                const float2 pv = pk[i * S.RG * KP];
-                                acc[2 * i] = cfmaf(pv, g0, acc[2 * i]);
-                                acc[2 * i + 1] = cfmaf(pv, g1, acc[2 * i + 1]);
+                                for (int i = 0; i < kAcc; ++i)
+                                    if ((in >> i) & 1u) acc[i] = cfmaf(pk[i * S.RG * KP], g0, acc[i]);
                             }
+                        } else {
+                            const bool c1 = cg + S.CW < NW;
+                            for (int kk = 0; kk < kc; ++kk) {
+                                const float2 g0 = Z[kk * NW + cg];
+                                const float2 g1 = c1 ? Z[kk * NW + cg + S.CW] : make_float2(0.f, 0.f);
+                                const float2 *pk = P + rg * KP + kk;
+#pragma unroll
+                                for (int i = 0; i < kAcc / 2; ++i)
+                                    if ((in >> i) & 1u) {
+                                        const float2 pv = pk[i * S.RG * KP];
+                                        acc[2 * i] = cfmaf(pv, g0, acc[2 * i]);
+                                        acc[2 * i + 1] = cfmaf(pv, g1, acc[2 * i + 1]);
+                                    }
+                            }
+                        }
                     }
+                    __syncthreads();
                 }
             }
-            __syncthreads();
+        } else {
+            // ---- Rp -> q: C[p][mu, i] = sum_Rp e^{i q_p . Rp} ghat[Rp][mu][i]; the K chunks of
+            // ghat are copied to shared memory with cp.async, one chunk ahead of the compute
+            const int nch = (S.nRp + KC - 1) / KC;
+            auto issue = [&](int ch) {
+                if (ch < nch) {
+                    const int r0 = ch * KC, kc = min(KC, S.nRp - r0);
+                    const float2 *src = gh + (int64_t)r0 * NW;
+                    float2 *dst = Gs + (size_t)(ch & 1) * KC * NW;
+                    if ((NW & 1) == 0) {
+                        for (int e = t; e < kc * NW / 2; e += kBT) cp_async_16(dst + 2 * e, src + 2 * e);
+                    } else {
+                        for (int e = t; e < kc * NW; e += kBT) cp_async_8(dst + e, src + e);
+                    }
+                }
+                cp_async_commit_group();
+            };
+            issue(0);
+            for (int ch = 0; ch < nch; ++ch) {
+                issue(ch + 1);
+                const int r0 = ch * KC, kc = min(KC, S.nRp - r0);
+                for (int e = t; e < cnt * KC; e += kBT) {
+                    const int p = e / KC, kk = e - p * KC;
+                    float2 v = make_float2(0.f, 0.f);
+                    if (kk < kc) {
+                        const int *R = S.Rp + 3 * (r0 + kk);
+                        v = S.ph32[phase_index(sa[0][p], sa[1][p], sa[2][p], R[0], R[1], R[2], S.g.L)];
+                    }
+                    P[p * KP + kk] = v;
+                }
+                cp_async_wait_group<1>();
+                __syncthreads();
+                if (tact) {
+                    const float2 *G = Gs + (size_t)(ch & 1) * KC * NW;
+                    const int nv = min(npt, (cnt - rg + S.RG - 1) / S.RG);   // valid pairs
+                    if (ncol == 1) {
+                        for (int kk = 0; kk < kc; ++kk) {
+                            const float2 g0 = G[kk * NW + cg];
+                            const float2 *pk = P + rg * KP + kk;
+    #pragma unroll
+                            for (int i = 0; i < kAcc; ++i)
+                                if (i < nv) acc[i] = cfmaf(pk[i * S.RG * KP], g0, acc[i]);
+                        }
+                    } else {
+                        const bool c1 = cg + S.CW < NW;
+                        for (int kk = 0; kk < kc; ++kk) {
+                            const float2 g0 = G[kk * NW + cg];
+                            const float2 g1 = c1 ? G[kk * NW + cg + S.CW] : make_float2(0.f, 0.f);
+                            const float2 *pk = P + rg * KP + kk;
+    #pragma unroll
+                            for (int i = 0; i < kAcc / 2; ++i)
+                                if (i < nv) {
+                                    const float2 pv = pk[i * S.RG * KP];
+                                    acc[2 * i] = cfmaf(pv, g0, acc[2 * i]);
+                                    acc[2 * i + 1] = cfmaf(pv, g1, acc[2 * i + 1]);
+                                }
+                        }
+                    }
+                }
+                __syncthreads();
+            }
         }
         cp_async_wait_group<0>();
         if (tact) {
@@ -563,6 +668,7 @@ void fill_bsys(epwi_batch *b, int s, int Mt, int KC, BSys &d) {
     d.W = c->nw;
     d.Nm = c->nm;
     d.nRp = c->nRp;
+    d.rc = c->rp_cube_r;
     d.NW = c->nw * c->nm;
     col_groups(d.NW, d.CW, d.RG);
     d.Mt = Mt;
@@ -852,11 +958,22 @@ void plan(epwi_batch *b, bool tune) {
     b->stats.persistent_ctas = b->grid_ctas;
     b->stats.smem_bytes = (int64_t)smem;
     b->stats.ms_plan = ms_plan;
+    // Rp->q flops of the algorithm each system runs: a full R_p sum per pair and band, or for a
+    // cube R_p the axis-1 factorisation (D^2 terms per pair and band, plus one D^3 build of Z
+    // per item, counting one run of equal q1 per item)
+    std::vector<int64_t> sys_items(ns, 0);
+    for (const BItem &it : items) ++sys_items[it.sys];
     double fl = 0, rfl = 0;
     for (int s = 0; s < ns; ++s) {
         epwi_ctx *c = b->sys[s];
         const double nbar = (double)c->nstates / std::max<int64_t>(1, c->nkp);
-        fl += 8.0 * c->nRp * c->nm * c->nw * (double)c->npairs * nbar;
+        const double cols = 8.0 * c->nm * c->nw;
+        if (c->rp_cube_r >= 0 && c->rp_cube_r <= 6) {
+            const double D = 2.0 * c->rp_cube_r + 1;
+            fl += cols * (D * D * (double)c->npairs * nbar + D * D * D * (double)sys_items[s]);
+        } else {
+            fl += cols * c->nRp * (double)c->npairs * nbar;
+        }
         rfl += 8.0 * c->nRe * c->nRp * c->nm * (double)c->nw * c->nw * c->nkp;
     }
     b->stats.scatter_flops = fl;
