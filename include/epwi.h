@@ -409,10 +409,12 @@ typedef struct {
     double ms_plan;             /* device time of the planning pass (incl. autotuning) */
     double ms_graph;            /* last graph launch, whole step */
     double ms_persistent;       /* last graph launch, the persistent kernel */
-    double scatter_flops;       /* algorithmic flops of the Rp->q products (one pass): for a
-                                   cube R_p of side D the axis-1 factorisation, 8 D^2 N_m W per
-                                   pair and band plus 8 D^3 N_m W per item; otherwise
-                                   8 n_Rp N_m W per pair and band */
+    double scatter_flops;       /* algorithmic flops of the persistent kernel (one pass): the
+                                   Rp->q products (for a cube R_p of side D the axis-1
+                                   factorisation, 8 D^2 N_m W per pair and band plus
+                                   8 D^3 N_m W per item; otherwise 8 n_Rp N_m W per pair and
+                                   band) and the rotations (8 W (N_m W + N_m^2) per pair and
+                                   band) */
     double restage_flops;       /* algorithmic flops of the Re->k stages */
 } epwi_batch_stats;
 

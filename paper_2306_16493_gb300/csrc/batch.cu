@@ -958,9 +958,11 @@ void plan(epwi_batch *b, bool tune) {
     b->stats.persistent_ctas = b->grid_ctas;
     b->stats.smem_bytes = (int64_t)smem;
     b->stats.ms_plan = ms_plan;
-    // Rp->q flops of the algorithm each system runs: a full R_p sum per pair and band, or for a
-    // cube R_p the axis-1 factorisation (D^2 terms per pair and band, plus one D^3 build of Z
-    // per item, counting one run of equal q1 per item)
+    // flops of the algorithm each system runs in the persistent kernel: the Rp->q product (a
+    // full R_p sum per pair and band, or for a cube R_p the axis-1 factorisation: D^2 terms per
+    // pair and band, plus one D^3 build of Z per item, counting one run of equal q1 per item)
+    // and the rotations (per pair, band and final band m: V^dag(k+q) C, N_m W complex
+    // multiply-adds, then u(q), N_m^2)
     std::vector<int64_t> sys_items(ns, 0);
     for (const BItem &it : items) ++sys_items[it.sys];
     double fl = 0, rfl = 0;
@@ -974,6 +976,7 @@ void plan(epwi_batch *b, bool tune) {
         } else {
             fl += cols * c->nRp * (double)c->npairs * nbar;
         }
+        fl += 8.0 * c->nw * ((double)c->nm * c->nw + (double)c->nm * c->nm) * (double)c->npairs * nbar;
         rfl += 8.0 * c->nRe * c->nRp * c->nm * (double)c->nw * c->nw * c->nkp;
     }
     b->stats.scatter_flops = fl;
