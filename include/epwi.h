@@ -244,7 +244,8 @@ epwi_status epwi_conductivity(epwi_ctx *ctx, double sigma_Sm[9]);
 epwi_status epwi_mobility(epwi_ctx *ctx, double carriers_per_cm3, double mu_cm2Vs[9]);
 
 /* Copies the eigen-tables: eps [Nk][nw], V [Nk][nw][nw] (row i, column n), vel
- * [Nk][nw][3].  Any pointer may be NULL.  Synchronises. */
+ * [Nk][nw][3].  Any pointer may be NULL.  Synchronises.  (epwi_eigs forms the velocities of
+ * the k-points that a rates window needs; the first request for vel forms the rest.) */
 epwi_status epwi_get_bands(epwi_ctx *ctx, double *eps, epwi_c64 *V, double *vel);
 
 /* Copies hbar*omega [Nq][Nm] (eV) and u [Nq][Nm][Nm] (A, row mu, column nu; zero columns

@@ -381,6 +381,7 @@ epwi_status epwi_eigs(epwi_ctx *c, const int32_t kgrid[3], const int32_t qgrid[3
         EPWI_CUDA(cudaEventCreate(&e1));
         cudaEventRecord(e0, c->stream);
         launch_phase_tables(c);
+        c->vel_defer = true;                 // velocities where a window or epwi_get_bands needs them
         launch_eigs(c);
         cudaEventRecord(e1, c->stream);
         int flag[2];
@@ -752,7 +753,10 @@ epwi_status epwi_get_bands(epwi_ctx *c, double *eps, epwi_c64 *V, double *vel) {
         const size_t nk = (size_t)c->nk, W = (size_t)c->nw;
         if (eps) EPWI_CUDA(cudaMemcpyAsync(eps, c->eps.p, 8 * nk * W, cudaMemcpyDeviceToHost, c->stream));
         if (V) EPWI_CUDA(cudaMemcpyAsync(V, c->V.p, 16 * nk * W * W, cudaMemcpyDeviceToHost, c->stream));
-        if (vel) EPWI_CUDA(cudaMemcpyAsync(vel, c->vel.p, 24 * nk * W, cudaMemcpyDeviceToHost, c->stream));
+        if (vel) {
+            ensure_velocities(c, true);
+            EPWI_CUDA(cudaMemcpyAsync(vel, c->vel.p, 24 * nk * W, cudaMemcpyDeviceToHost, c->stream));
+        }
         EPWI_CUDA(cudaStreamSynchronize(c->stream));
     });
 }

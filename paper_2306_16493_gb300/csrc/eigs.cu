@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(128) k_eig_el(GridInfo g, int64_t nk, int W, i
                                                 double2 *__restrict__ Vout,
                                                 float2 *__restrict__ V32,
                                                 double *__restrict__ vel, int *__restrict__ flag,
-                                                FacDesc fac, Lattice lat) {
+                                                FacDesc fac, Lattice lat, int do_vel) {
     int64_t ik = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (ik >= nk) return;
     int i1, i2, i3;
@@ -151,6 +151,7 @@ __global__ void __launch_bounds__(128) k_eig_el(GridInfo g, int64_t nk, int W, i
         Vout[ik * WW + e] = Vm[e];
         V32[ik * WW + e] = make_float2((float)Vm[e].x, (float)Vm[e].y);
     }
+    if (!do_vel) return;                 // velocities later, for the k-points that need them
     // v_n,a = (1/hbar) Re[V^dag (sum_R w_R i R_a e^{ik.R} H(R)) V]_nn, one axis at a time
     for (int ax = 0; ax < 3; ++ax) {
         for (int e = 0; e < WW; ++e) A[e] = make_double2(0, 0);
@@ -176,6 +177,49 @@ __global__ void __launch_bounds__(128) k_eig_el(GridInfo g, int64_t nk, int W, i
                 const double2 ip = make_double2(-ra * p.y, ra * p.x);   // i R_a e^{ik.R}
                 const double2 *h = Hw + (size_t)r * WW;
                 for (int e = 0; e < WW; ++e) A[e] = cfma(ip, h[e], A[e]);
+            }
+        }
+        for (int n = 0; n < W; ++n) {
+            double acc = 0;
+            for (int i = 0; i < W; ++i) {
+                double2 t = make_double2(0, 0);
+                for (int j = 0; j < W; ++j) t = cfma(A[i * W + j], Vm[j * W + n], t);
+                acc += Vm[i * W + n].x * t.x + Vm[i * W + n].y * t.y;   // Re(conj(V_in) t)
+            }
+            vel[(ik * W + n) * 3 + ax] = acc / epc::kHbarEVs * 1e-10;
+        }
+    }
+}
+
+// Band velocities from the factorised stages and the stored eigenvectors (the velocity part of
+// k_eig_el<WMAX, true>, same arithmetic), for the grid points with win_n > 0 (every point when
+// win_n is NULL).
+template <int WMAX>
+__global__ void __launch_bounds__(128) k_vel_fac(GridInfo g, int64_t nk, int W, const int *__restrict__ win_n,
+                                                 const double2 *__restrict__ ph, const double2 *__restrict__ Vin,
+                                                 double *__restrict__ vel, FacDesc fac, Lattice lat) {
+    const int64_t ik = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ik >= nk || (win_n && win_n[ik] == 0)) return;
+    int i1, i2, i3;
+    grid_coords(g, ik, i1, i2, i3);
+    const int a1 = (int)((int64_t)i1 * g.s1 % g.L);
+    const int WW = W * W;
+    const int64_t pp = (int64_t)i2 * g.n3 + i3;
+    double2 A[WMAX * WMAX], Vm[WMAX * WMAX];
+    for (int e = 0; e < WW; ++e) Vm[e] = Vin[ik * WW + e];
+    const int64_t src = (int64_t)fac.D * fac.plane * WW;
+    for (int ax = 0; ax < 3; ++ax) {
+        for (int e = 0; e < WW; ++e) A[e] = make_double2(0, 0);
+        for (int j = 0; j < fac.D; ++j) {
+            const int n1 = j - fac.rc;
+            const double2 p = axis_ph(ph, n1, a1, g.L);
+            const double2 ip = make_double2(-p.y, p.x);   // i e1
+            const double c0 = n1 * lat.a[0][ax], c1 = lat.a[1][ax], c2 = lat.a[2][ax];
+            const double2 *u = fac.U + ((int64_t)j * fac.plane + pp) * WW;
+            for (int e = 0; e < WW; ++e) {
+                const double2 sr = make_double2(c0 * u[e].x + c1 * u[src + e].x + c2 * u[2 * src + e].x,
+                                                c0 * u[e].y + c1 * u[src + e].y + c2 * u[2 * src + e].y);
+                A[e] = cfma(ip, sr, A[e]);
             }
         }
         for (int n = 0; n < W; ++n) {
@@ -503,7 +547,7 @@ void launch_eigs(epwi_ctx *c) {
         nT = (int64_t)(vel ? 2 : 1) * D * D * g.n3 * E;
         nU = (int64_t)(vel ? 3 : 1) * D * plane * E;
     };
-    auto fac_stages = [&](const DevBuf &Xc, int rc, int E, bool vel) {
+    auto fac_stages = [&](const DevBuf &Xc, int rc, int E, bool vel, DevBuf &Uout) {
         const int D = 2 * rc + 1;
         const int64_t t3 = (int64_t)D * D * g.n3 * E, t2 = (int64_t)D * plane * E;
         if (vel) {
@@ -511,17 +555,17 @@ void launch_eigs(epwi_ctx *c) {
                 D, rc, g.n3, g.s3, g.L, E, Xc.as<double2>(), c->ph64.as<double2>(), c->fac_T.as<double2>());
             EPWI_CHECK_LAUNCH();
             k_fac_axis2<true><<<(unsigned)((t2 + 255) / 256), 256, 0, c->stream>>>(
-                D, rc, g.n2, g.n3, g.s2, g.L, E, c->fac_T.as<double2>(), c->ph64.as<double2>(), c->fac_U.as<double2>());
+                D, rc, g.n2, g.n3, g.s2, g.L, E, c->fac_T.as<double2>(), c->ph64.as<double2>(), Uout.as<double2>());
         } else {
             k_fac_axis3<false><<<(unsigned)((t3 + 255) / 256), 256, 0, c->stream>>>(
                 D, rc, g.n3, g.s3, g.L, E, Xc.as<double2>(), c->ph64.as<double2>(), c->fac_T.as<double2>());
             EPWI_CHECK_LAUNCH();
             k_fac_axis2<false><<<(unsigned)((t2 + 255) / 256), 256, 0, c->stream>>>(
-                D, rc, g.n2, g.n3, g.s2, g.L, E, c->fac_T.as<double2>(), c->ph64.as<double2>(), c->fac_U.as<double2>());
+                D, rc, g.n2, g.n3, g.s2, g.L, E, c->fac_T.as<double2>(), c->ph64.as<double2>(), Uout.as<double2>());
         }
         EPWI_CHECK_LAUNCH();
         FacDesc f;
-        f.U = c->fac_U.as<double2>();
+        f.U = Uout.as<double2>();
         f.D = D;
         f.rc = rc;
         f.plane = plane;
@@ -548,22 +592,32 @@ void launch_eigs(epwi_ctx *c) {
             c->fac_U.ensure(sizeof(double2) * nU);
         }
     }
+    // deferred velocities (thread-per-point solver with the factorised build): the electron
+    // stage output stays in fac_Uel for ensure_velocities
+    const bool defer = c->vel_defer && fac_el && W <= 8;
+    if (defer) {
+        int64_t t, u;
+        fac_sizes(c->fac_re_r, W * W, true, t, u);
+        c->fac_Uel.ensure(sizeof(double2) * u);
+    }
     FacDesc fe{}, fp{};
-    if (fac_el) fe = fac_stages(c->fac_Hc, c->fac_re_r, W * W, true);
+    if (fac_el) fe = fac_stages(c->fac_Hc, c->fac_re_r, W * W, true, defer ? c->fac_Uel : c->fac_U);
+    const int do_vel = defer ? 0 : 1;
+    c->vel_state = defer ? 0 : 2;
 #define EL_ARGS                                                                              \
     g, nk, W, c->nRe, c->Re.as<int>(), c->Rcart.as<double>(), c->Hw.as<double2>(),            \
         c->ph64.as<double2>(), c->eps.as<double>(), c->eps32.as<float>(), c->V.as<double2>(), \
         c->V32.as<float2>(), c->vel.as<double>(), c->eig_flag.as<int>()
     const unsigned nbw = (unsigned)((nk + kWarpsPerBlock - 1) / kWarpsPerBlock);
     if (W <= 1) {
-        if (fac_el) k_eig_el<1, true><<<nb, bs, 0, c->stream>>>(EL_ARGS, fe, lat);
-        else k_eig_el<1, false><<<nb, bs, 0, c->stream>>>(EL_ARGS, fe, lat);
+        if (fac_el) k_eig_el<1, true><<<nb, bs, 0, c->stream>>>(EL_ARGS, fe, lat, do_vel);
+        else k_eig_el<1, false><<<nb, bs, 0, c->stream>>>(EL_ARGS, fe, lat, 1);
     } else if (W <= 4) {
-        if (fac_el) k_eig_el<4, true><<<nb, bs, 0, c->stream>>>(EL_ARGS, fe, lat);
-        else k_eig_el<4, false><<<nb, bs, 0, c->stream>>>(EL_ARGS, fe, lat);
+        if (fac_el) k_eig_el<4, true><<<nb, bs, 0, c->stream>>>(EL_ARGS, fe, lat, do_vel);
+        else k_eig_el<4, false><<<nb, bs, 0, c->stream>>>(EL_ARGS, fe, lat, 1);
     } else if (W <= 8) {
-        if (fac_el) k_eig_el<8, true><<<nb, bs, 0, c->stream>>>(EL_ARGS, fe, lat);
-        else k_eig_el<8, false><<<nb, bs, 0, c->stream>>>(EL_ARGS, fe, lat);
+        if (fac_el) k_eig_el<8, true><<<nb, bs, 0, c->stream>>>(EL_ARGS, fe, lat, do_vel);
+        else k_eig_el<8, false><<<nb, bs, 0, c->stream>>>(EL_ARGS, fe, lat, 1);
     } else {
         const size_t sm = warp_scratch_bytes(W);
         if (fac_el) {
@@ -582,7 +636,7 @@ void launch_eigs(epwi_ctx *c) {
         c->hw32.as<float>(),                                                                   \
         c->u.as<double2>(), c->u32.as<float2>(), c->eig_flag.as<int>() + 1
     // the electron kernel above has read fac_U; the phonon stages reuse the buffers (same stream)
-    if (fac_ph) fp = fac_stages(c->fac_Pc, c->fac_rp_r, Nm * Nm, false);
+    if (fac_ph) fp = fac_stages(c->fac_Pc, c->fac_rp_r, Nm * Nm, false, c->fac_U);
     if (Nm <= 3) {
         if (fac_ph) k_eig_ph<3, true><<<nb, bs, 0, c->stream>>>(PH_ARGS, fp);
         else k_eig_ph<3, false><<<nb, bs, 0, c->stream>>>(PH_ARGS, fp);
@@ -601,4 +655,26 @@ void launch_eigs(epwi_ctx *c) {
     }
 #undef PH_ARGS
     EPWI_CHECK_LAUNCH();
+}
+
+void ensure_velocities(epwi_ctx *c, bool all) {
+    if (c->vel_state == 2 || (!all && c->vel_state == 1)) return;
+    const int W = c->nw;
+    GridInfo g = make_grid_info(c);
+    FacDesc f;
+    f.U = c->fac_Uel.as<double2>();
+    f.rc = c->fac_re_r;
+    f.D = 2 * f.rc + 1;
+    f.plane = (int64_t)g.n2 * g.n3;
+    Lattice lat;
+    for (int i = 0; i < 9; ++i) lat.a[i / 3][i % 3] = c->lattice[i];
+    const int *win = all ? nullptr : c->win_n.as<int>();
+    const unsigned nb = (unsigned)((c->nk + 127) / 128);
+#define VEL_ARGS g, c->nk, W, win, c->ph64.as<double2>(), c->V.as<double2>(), c->vel.as<double>(), f, lat
+    if (W <= 1) k_vel_fac<1><<<nb, 128, 0, c->stream>>>(VEL_ARGS);
+    else if (W <= 4) k_vel_fac<4><<<nb, 128, 0, c->stream>>>(VEL_ARGS);
+    else k_vel_fac<8><<<nb, 128, 0, c->stream>>>(VEL_ARGS);
+#undef VEL_ARGS
+    EPWI_CHECK_LAUNCH();
+    c->vel_state = all ? 2 : 1;
 }

@@ -174,6 +174,12 @@ struct epwi_ctx {
     int fac_re_r = -1, fac_rp_r = -1;
     DevBuf fac_Hc, fac_Pc;         // double2 [Dc^3][W W], [Dc^3][Nm Nm]
     DevBuf fac_T, fac_U;           // stage outputs (see eigs.cu)
+    // band velocities: with vel_defer (set by epwi_eigs) the eigensolve leaves them out and
+    // they are formed from the kept electron stage output fac_Uel for the k-points that need
+    // them: those of each new window, or every point on request (ensure_velocities)
+    bool vel_defer = false;
+    int vel_state = 0;             // 0: none, 1: the current window's k-points, 2: every point
+    DevBuf fac_Uel;
     int64_t tc_arows_key = -1;
     bool tc_gather = false;        // use the gathered-A mode where it applies
     int64_t stats_tc_grid = 0;
@@ -221,7 +227,7 @@ struct epwi_ctx {
                          &tc_n32, &tc_hw32, &tc_err, &tc_meta, &is_pairs, &is_w,
                          &is_kp_pairs, &sieve_mask, &tc_arows, &ib_pairs, &ib_goff, &ib_gam,
                          &ib_kpos, &ib_F0, &ib_F, &ib_Fn, &ib_red, &ib_F32, &ib_Fn32, &sf_items, &ib_col, &ib_ent, &sym_rep, &seg_ranges,
-                         &gsf32, &sf_Vt32, &sf_ef, &sf_uS, &sf_wn, &gcube32, &fac_Hc, &fac_Pc, &fac_T, &fac_U};
+                         &gsf32, &sf_Vt32, &sf_ef, &sf_uS, &sf_wn, &gcube32, &fac_Hc, &fac_Pc, &fac_T, &fac_U, &fac_Uel};
         for (DevBuf *b : all) b->release();
         mlp_free(mlp);
     }
@@ -308,6 +314,9 @@ __host__ __device__ __forceinline__ int phase_index(int a1, int a2, int a3, int 
 GridInfo make_grid_info(const epwi_ctx *c);
 void launch_phase_tables(epwi_ctx *c);
 void launch_eigs(epwi_ctx *c);
+// Band velocities of the window's k-points (all = false; needs win_n) or of every grid point,
+// where the eigensolve deferred them; a no-op otherwise.
+void ensure_velocities(epwi_ctx *c, bool all);
 void scan_exclusive_i64(epwi_ctx *c, const int64_t *in, int64_t *out, int64_t n, int64_t *total);
 double device_reduce_minmax(epwi_ctx *c, const double *x, int64_t n, int64_t stride, int64_t off,
                             bool want_max);

@@ -575,6 +575,8 @@ void build_window(epwi_ctx *c, const int *rep) {
     k_window<<<nb, 256, 0, c->stream>>>(nk, c->nw, c->eps.as<double>(), c->emin, c->emax,
                                        c->win_lo.as<int>(), c->win_n.as<int>());
     EPWI_CHECK_LAUNCH();
+    if (c->vel_state == 1) c->vel_state = 0;     // velocities of an earlier window
+    ensure_velocities(c, false);
     window_lists(c, rep);
 }
 

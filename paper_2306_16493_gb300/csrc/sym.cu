@@ -154,6 +154,8 @@ void sym_expand(epwi_ctx *c) {
         }
         k_sym_window<<<nb, 256, 0, c->stream>>>(nk, c->sym_rep.as<int>(), c->win_lo.as<int>(), c->win_n.as<int>());
         EPWI_CHECK_LAUNCH();
+        if (c->vel_state == 1) c->vel_state = 0;  // members took their representatives' windows
+        ensure_velocities(c, false);
         window_lists(c, nullptr);
         if (c->nstates > 0) {
             k_sym_expand<<<(unsigned)((c->nstates + 255) / 256), 256, 0, c->stream>>>(
