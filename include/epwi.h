@@ -46,7 +46,7 @@ typedef enum {
     EPWI_ETIMEOUT = 5,    /* a bounded device-side wait gave up */
     EPWI_ENUMERIC = 6,    /* non-finite result or eigensolver did not converge */
     EPWI_ETOOSMALL = 7,   /* output capacity smaller than the result */
-    EPWI_EUNSUPPORTED = 8 /* size or mode outside what this build supports */
+    EPWI_EUNSUPPORTED = 8 /* size or mode outside what the library supports */
 } epwi_status;
 
 /* Arithmetic of the g(k,q) interpolation (steps Re->k, Rp->q and the rotations).
