@@ -496,20 +496,26 @@ WorkSet begin_rates(epwi_ctx *c, double T, double mu, double eta, double emin, d
     c->stats.precision = c->opt.precision;
     c->stats.ms_eigs = c->ms_eigs;
     EPWI_CUDA(cudaDeviceGetAttribute(&c->stats.sm_count, cudaDevAttrMultiProcessorCount, c->device));
-    cudaEvent_t e0, e1;
-    EPWI_CUDA(cudaEventCreate(&e0));
-    EPWI_CUDA(cudaEventCreate(&e1));
-    cudaEventRecord(e0, c->stream);
+    // window and sieve (ms_sieve); the window's deferred band velocities count as eigensolve
+    // work (ms_eigs)
+    cudaEvent_t ev[4];
+    for (auto &e : ev) EPWI_CUDA(cudaEventCreate(&e));
+    cudaEventRecord(ev[0], c->stream);
     if (sym) sym_prepare(c);                 // representatives of the stars; invariance check
     build_window(c, sym ? c->sym_rep.as<int>() : nullptr);
+    cudaEventRecord(ev[1], c->stream);
+    ensure_velocities(c, false);
+    cudaEventRecord(ev[2], c->stream);
     sieve_count(c);
-    cudaEventRecord(e1, c->stream);
+    cudaEventRecord(ev[3], c->stream);
     EPWI_CUDA(cudaStreamSynchronize(c->stream));
-    float ms = 0;
-    cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    c->stats.ms_sieve = ms;
+    float ms_w = 0, ms_v = 0, ms_s = 0;
+    cudaEventElapsedTime(&ms_w, ev[0], ev[1]);
+    cudaEventElapsedTime(&ms_v, ev[1], ev[2]);
+    cudaEventElapsedTime(&ms_s, ev[2], ev[3]);
+    for (auto &e : ev) cudaEventDestroy(e);
+    c->stats.ms_sieve = ms_w + ms_s;
+    c->stats.ms_eigs += ms_v;
     occupation_tables(c);
     if (c->nstates > 0)
         EPWI_CUDA(cudaMemsetAsync(c->inv_tau.p, 0, sizeof(double) * c->nstates, c->stream));

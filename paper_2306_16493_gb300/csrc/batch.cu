@@ -818,6 +818,7 @@ void plan(epwi_batch *b, bool tune) {
         const int g3[3] = {b->grids[s][0], b->grids[s][1], b->grids[s][2]};
         check(c, epwi_eigs(c, g3, g3), "epwi_eigs");
         build_window(c);
+        ensure_velocities(c, false);
         sieve_count(c);
         occupation_tables(c);
         tc_tables(c);

@@ -315,7 +315,8 @@ GridInfo make_grid_info(const epwi_ctx *c);
 void launch_phase_tables(epwi_ctx *c);
 void launch_eigs(epwi_ctx *c);
 // Band velocities of the window's k-points (all = false; needs win_n) or of every grid point,
-// where the eigensolve deferred them; a no-op otherwise.
+// where the eigensolve deferred them; a no-op otherwise.  Every builder of a rates window calls
+// it (all = false) after build_window.
 void ensure_velocities(epwi_ctx *c, bool all);
 void scan_exclusive_i64(epwi_ctx *c, const int64_t *in, int64_t *out, int64_t n, int64_t *total);
 double device_reduce_minmax(epwi_ctx *c, const double *x, int64_t n, int64_t stride, int64_t off,

@@ -414,6 +414,7 @@ void mlp_train(epwi_ctx *c, double T, double mu, double eta, double emin, double
     PrecisionGuard pg(c);
     if (!c->mlp || !c->mlp->ready) mlp_init(c, o.seed);
     build_window(c);
+    ensure_velocities(c, false);
     sieve_count(c);
     occupation_tables(c);
     const int64_t nkp = c->nkp;
@@ -566,6 +567,7 @@ void run_is(epwi_ctx *c, double T, double mu, double eta, double emin, double em
     EPWI_CUDA(cudaEventCreate(&e2));
     cudaEventRecord(e0, st);
     build_window(c);
+    ensure_velocities(c, false);
     occupation_tables(c);
     const int64_t nkp = c->nkp, nq = c->nk;
     const bool learned = proposal == EPWI_PROPOSAL_LEARNED;

@@ -576,7 +576,6 @@ void build_window(epwi_ctx *c, const int *rep) {
                                        c->win_lo.as<int>(), c->win_n.as<int>());
     EPWI_CHECK_LAUNCH();
     if (c->vel_state == 1) c->vel_state = 0;     // velocities of an earlier window
-    ensure_velocities(c, false);
     window_lists(c, rep);
 }
 
