@@ -211,7 +211,7 @@ __global__ void k_seg_ranges(int N1, int64_t nplane, int W, int nseg, const floa
 // nearly every candidate when the phonon energies lie below c eta (the Gaussian's support is
 // wider than the phonon band); the third runs inline for the few others.  The lanes of a warp
 // take 32 consecutive (q2, q3) combinations of a plane block and 2-4 consecutive q1 per step,
-// with the window's band count a compile-time constant (1-4, else a runtime loop); their
+// with the window's band count a compile-time constant (1 or 2, else a runtime loop); their
 // ballots are the plane block's mask words, kept in shared memory ([warp][q1]) and written out
 // in k_sieve_count's layout.  Indices are 32-bit (N_k < 2^31, checked).
 //
